@@ -1,0 +1,271 @@
+"""Python access to the FP64 CPU oracle (``tucker_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the independent reference for the
+Tucker/HOSVD of covariance tensors in arXiv:1711.06874.  Only the test suite,
+``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg use it; the
+CUDA library never imports, links or calls anything here.
+
+Parity status of each routine (what pins it) is listed in the C source.  The
+value of the Tucker tensor at the origin compared with the printed table of
+Sec. 4 (Table zero_points) is a sanity check only: the paper does not state
+the box size or whether ALS followed the HOSVD, so that comparison is parity
+unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tucker_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MATERN, SLATER_P, GAUSSIAN = 0, 1, 2
+CELL, VERTEX = 0, 1
+RANK_CAPPED, EPS_UNREACHABLE = 1, 2
+
+
+class Kernel(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("nu", ctypes.c_double),
+        ("ell", ctypes.c_double * 3),
+        ("sigma2", ctypes.c_double),
+        ("p", ctypes.c_double),
+    ]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("b", ctypes.c_double * 3), ("kind", ctypes.c_int)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(os.path.join(_HERE, "tucker_oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        kp, gp = ctypes.POINTER(Kernel), ctypes.POINTER(Grid)
+        sig = {
+            "or_bessel_k_scaled": (d, [d, d]),
+            "or_bessel_k": (d, [d, d]),
+            "or_matern_z": (d, [d, d, d]),
+            "or_kernel_value": (d, [kp, p]),
+            "or_grid_axis": (None, [i, i, d, p]),
+            "or_tensor": (None, [kp, gp, p]),
+            "or_unfold": (None, [p, p, i, p]),
+            "or_gram": (None, [p, p, i, p]),
+            "or_norm2": (d, [p, ctypes.c_longlong]),
+            "or_sym_eig": (i, [i, p, p, p]),
+            "or_unfolding_svd": (i, [p, p, i, p, p]),
+            "or_rank": (i, [p, i, d, d, i, p]),
+            "or_core": (None, [p, p, p, i, p, i, p, i, p, p]),
+            "or_reconstruct": (None, [p, p, p, i, p, i, p, i, p, p]),
+            "or_tucker_point": (d, [p, p, p, i, p, i, p, i, p]),
+            "or_rel_error": (d, [p, p, ctypes.c_longlong]),
+            "or_hosvd": (i, [kp, gp, d, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "or_num_threads": (i, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def make_kernel(kind=MATERN, nu=0.5, ell=1.0, sigma2=1.0, p=1.0) -> Kernel:
+    ell3 = [float(ell)] * 3 if np.isscalar(ell) else [float(v) for v in ell]
+    return Kernel(int(kind), float(nu), (ctypes.c_double * 3)(*ell3), float(sigma2), float(p))
+
+
+def make_grid(n, b=1.0, kind=CELL) -> Grid:
+    n3 = [int(n)] * 3 if np.isscalar(n) else [int(v) for v in n]
+    b3 = [float(b)] * 3 if np.isscalar(b) else [float(v) for v in b]
+    return Grid((ctypes.c_int * 3)(*n3), (ctypes.c_double * 3)(*b3), int(kind))
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def bessel_k(nu: float, z: float) -> float:
+    return _load().or_bessel_k(float(nu), float(z))
+
+
+def bessel_k_scaled(nu: float, z: float) -> float:
+    return _load().or_bessel_k_scaled(float(nu), float(z))
+
+
+def matern_z(nu: float, sigma2: float, z: float) -> float:
+    return _load().or_matern_z(float(nu), float(sigma2), float(z))
+
+
+def kernel_value(kernel: Kernel, x) -> float:
+    x = _f64(x)
+    return _load().or_kernel_value(ctypes.byref(kernel), _ptr(x))
+
+
+def grid_axis(kind: int, n: int, b: float) -> np.ndarray:
+    x = np.empty(n, np.float64)
+    _load().or_grid_axis(int(kind), int(n), float(b), _ptr(x))
+    return x
+
+
+def tensor(kernel: Kernel, grid: Grid) -> np.ndarray:
+    n = tuple(grid.n)
+    F = np.empty(n, np.float64)
+    _load().or_tensor(ctypes.byref(kernel), ctypes.byref(grid), _ptr(F))
+    return F
+
+
+def unfold(F: np.ndarray, mode: int) -> np.ndarray:
+    F = _f64(F)
+    n = _i32(F.shape)
+    A = np.empty((F.shape[mode], F.size // F.shape[mode]), np.float64)
+    _load().or_unfold(_ptr(F), _ptr(n), int(mode), _ptr(A))
+    return A
+
+
+def gram(F: np.ndarray, mode: int) -> np.ndarray:
+    F = _f64(F)
+    n = _i32(F.shape)
+    m = F.shape[mode]
+    G = np.empty((m, m), np.float64)
+    _load().or_gram(_ptr(F), _ptr(n), int(mode), _ptr(G))
+    return G
+
+
+def norm2(X: np.ndarray) -> float:
+    X = _f64(X)
+    return _load().or_norm2(_ptr(X), X.size)
+
+
+def sym_eig(G: np.ndarray):
+    """Returns (lam descending, V with eigenvectors as columns, sweeps)."""
+    G = _f64(G)
+    n = G.shape[0]
+    lam = np.empty(n, np.float64)
+    V = np.empty((n, n), np.float64)
+    sweeps = _load().or_sym_eig(n, _ptr(G), _ptr(lam), _ptr(V))
+    return lam, V, sweeps
+
+
+def unfolding_svd(F: np.ndarray, mode: int):
+    F = _f64(F)
+    n = _i32(F.shape)
+    m = F.shape[mode]
+    s = np.empty(m, np.float64)
+    U = np.empty((m, m), np.float64)
+    _load().or_unfolding_svd(_ptr(F), _ptr(n), int(mode), _ptr(s), _ptr(U))
+    return s, U
+
+
+def rank(lam: np.ndarray, normF2: float, eps: float, rmax: int):
+    lam = _f64(lam)
+    flags = np.zeros(1, np.int32)
+    r = _load().or_rank(_ptr(lam), lam.size, float(normF2), float(eps), int(rmax), _ptr(flags))
+    return r, int(flags[0])
+
+
+def core(F: np.ndarray, U, r) -> np.ndarray:
+    F = _f64(F)
+    n = _i32(F.shape)
+    U = [_f64(u) for u in U]
+    r = _i32(r)
+    B = np.empty(tuple(int(v) for v in r), np.float64)
+    _load().or_core(_ptr(F), _ptr(n), _ptr(U[0]), U[0].shape[1], _ptr(U[1]), U[1].shape[1],
+                    _ptr(U[2]), U[2].shape[1], _ptr(r), _ptr(B))
+    return B
+
+
+def reconstruct(B: np.ndarray, U, n) -> np.ndarray:
+    B = _f64(B)
+    r = _i32(B.shape)
+    U = [_f64(u) for u in U]
+    n = _i32(n)
+    X = np.empty(tuple(int(v) for v in n), np.float64)
+    _load().or_reconstruct(_ptr(B), _ptr(r), _ptr(U[0]), U[0].shape[1], _ptr(U[1]), U[1].shape[1],
+                           _ptr(U[2]), U[2].shape[1], _ptr(n), _ptr(X))
+    return X
+
+
+def tucker_point(B: np.ndarray, U, idx) -> float:
+    B = _f64(B)
+    r = _i32(B.shape)
+    U = [_f64(u) for u in U]
+    idx = _i32(idx)
+    return _load().or_tucker_point(_ptr(B), _ptr(r), _ptr(U[0]), U[0].shape[1], _ptr(U[1]),
+                                   U[1].shape[1], _ptr(U[2]), U[2].shape[1], _ptr(idx))
+
+
+def rel_error(F: np.ndarray, X: np.ndarray) -> float:
+    F = _f64(F)
+    X = _f64(X)
+    return _load().or_rel_error(_ptr(F), _ptr(X), F.size)
+
+
+def hosvd(kernel: Kernel, grid: Grid, eps: float, rmax=None, rfix=None) -> dict:
+    """Full HOSVD of the sampled covariance (Sec. 3.2) with the eps rank rule."""
+    n = [int(v) for v in grid.n]
+    rmax = _i32(n if rmax is None else ([rmax] * 3 if np.isscalar(rmax) else rmax))
+    rfix = _i32([0, 0, 0] if rfix is None else ([rfix] * 3 if np.isscalar(rfix) else rfix))
+    ranks = np.zeros(3, np.int32)
+    flags = np.zeros(3, np.int32)
+    U = [np.empty((m, m), np.float64) for m in n]
+    lam = [np.empty(m, np.float64) for m in n]
+    B = np.empty(n[0] * n[1] * n[2], np.float64)
+    out = np.zeros(3, np.float64)
+    rc = _load().or_hosvd(ctypes.byref(kernel), ctypes.byref(grid), float(eps), _ptr(rmax),
+                          _ptr(rfix), _ptr(ranks), _ptr(flags), _ptr(U[0]), _ptr(U[1]),
+                          _ptr(U[2]), _ptr(lam[0]), _ptr(lam[1]), _ptr(lam[2]), _ptr(B), _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle hosvd failed")
+    r = [int(v) for v in ranks]
+    return {
+        "ranks": r,
+        "flags": [int(v) for v in flags],
+        "U": [U[m][:, : r[m]].copy() for m in range(3)],
+        "U_all": U,
+        "lam": lam,
+        "core": B[: r[0] * r[1] * r[2]].reshape(r).copy(),
+        "normF2": float(out[0]),
+        "rel_error": float(out[1]),
+        "core_norm2": float(out[2]),
+    }

@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one oracle routine to something other than itself: a closed
+form, an identity, a library routine on a special case, brute force on tiny
+inputs, or a value printed in the paper.  The mutation tests at the end plant
+plausible mistakes (on the CPU, in the oracle's inputs and outputs) and show
+that the pins catch them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# K_nu and the Matern function (Sec. 2.2, Eq. (Matern))
+# --------------------------------------------------------------------------
+ZS = [1e-4, 3e-3, 0.052, 0.09, 0.5, 1.0, 1.9, 2.0, 2.1, 5.7, 13.4, 38.7, 77.3, 250.0]
+
+
+@pytest.mark.parametrize("z", ZS)
+def test_bessel_half_integer_closed_forms(orc, z):
+    # K_{1/2}, K_{3/2}, K_{5/2} are elementary (K_{n+1/2} closed forms).
+    base = math.sqrt(math.pi / (2 * z))
+    want = {
+        0.5: base,
+        1.5: base * (1 + 1 / z),
+        2.5: base * (1 + 3 / z + 3 / z ** 2),
+    }
+    for nu, w in want.items():
+        got = orc.bessel_k_scaled(nu, z)  # K * e^z
+        assert abs(got - w) <= 2e-15 * abs(w), (nu, z, got, w)
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.8, 1.2, 2.3, 3.7])
+def test_bessel_order_recurrence(orc, nu):
+    # K_{nu+1}(z) - K_{nu-1}(z) = (2 nu / z) K_nu(z)
+    for z in ZS[:-1]:
+        kp = orc.bessel_k_scaled(nu + 1, z)
+        km = orc.bessel_k_scaled(nu - 1, z)
+        k0 = orc.bessel_k_scaled(nu, z)
+        assert abs((kp - km) - 2 * nu / z * k0) <= 5e-15 * kp, (nu, z)
+
+
+def test_bessel_matches_scipy(orc):
+    sp = pytest.importorskip("scipy.special")
+    # scipy's kv itself carries errors up to ~5e-14 near z = 2
+    for nu in [0.3, 0.5, 1.2, 2.5]:
+        for z in ZS[:-1]:
+            a, b = orc.bessel_k(nu, z), float(sp.kv(nu, z))
+            assert abs(a - b) <= 2e-13 * abs(b), (nu, z, a, b)
+
+
+def test_bessel_matches_mpmath(orc):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for nu in [0.3, 1.2, 2.5, 0.75]:
+        for z in [1e-3, 0.5, 2.0, 13.4, 77.3]:
+            ex = float(mp.besselk(nu, z) * mp.e ** z)
+            got = orc.bessel_k_scaled(nu, z)
+            assert abs(got - ex) <= 2e-15 * ex, (nu, z, got, ex)
+
+
+@pytest.mark.parametrize("z", [1e-6, 0.09, 0.7, 3.0, 13.4, 38.7])
+def test_matern_closed_forms(orc, z):
+    # nu = 1/2 is the exponential model (Sec. 2.2); 3/2 and 5/2 follow from
+    # the elementary K_{n+1/2}.  Here z = sqrt(2 nu) r / ell.
+    s2 = 1.7
+    want = {
+        0.5: s2 * math.exp(-z),
+        1.5: s2 * (1 + z) * math.exp(-z),
+        2.5: s2 * (1 + z + z * z / 3) * math.exp(-z),
+    }
+    for nu, w in want.items():
+        got = orc.matern_z(nu, s2, z)
+        # z^nu e^-z is formed as exp(nu log z - z): rounding of the exponent
+        # costs about |nu log z| + z ulps
+        assert abs(got - w) <= (4 + abs(nu * math.log(z)) + z) * 2.3e-16 * w, (nu, z, got, w)
+
+
+def test_matern_small_r_limit_and_origin(orc):
+    assert orc.matern_z(1.2, 2.5, 0.0) == 2.5
+    # C(z) = sigma2 (1 - O(z^2)) for nu > 1
+    assert abs(orc.matern_z(1.2, 2.5, 1e-6) / 2.5 - 1) < 1e-10
+    assert abs(orc.matern_z(0.3, 1.0, 1e-12) - 1) < 1e-6
+
+
+def test_matern_gaussian_limit(orc):
+    # nu -> infinity gives the Gaussian model (Sec. 2.2): C -> exp(-r^2 / (2 ell^2))
+    for rho in [0.5, 1.0, 1.5]:
+        nu = 200.0
+        got = orc.matern_z(nu, 1.0, math.sqrt(2 * nu) * rho)
+        assert abs(got - math.exp(-rho * rho / 2)) < 3e-3 * math.exp(-rho * rho / 2) + 1e-3
+
+
+def test_kernel_value_anisotropic(orc):
+    # r_A^2 = sum x_a^2 / ell_a^2 (Sec. 2.2, diagonal A)
+    k = orc.make_kernel(orc.MATERN, nu=1.5, ell=[0.3, 0.5, 0.7], sigma2=1.3)
+    x = [0.1, -0.2, 0.35]
+    ra = math.sqrt(sum((xi / li) ** 2 for xi, li in zip(x, [0.3, 0.5, 0.7])))
+    z = math.sqrt(3.0) * ra
+    assert abs(orc.kernel_value(k, x) - 1.3 * (1 + z) * math.exp(-z)) < 1e-15
+    ks = orc.make_kernel(orc.SLATER_P, ell=1.0, p=0.2)
+    assert abs(orc.kernel_value(ks, [0.3, 0.4, 0.0]) - math.exp(-(0.5 ** 0.2))) < 1e-15
+    kg = orc.make_kernel(orc.GAUSSIAN, ell=0.5, sigma2=2.0)
+    assert abs(orc.kernel_value(kg, [0.1, 0.2, 0.3]) - 2.0 * math.exp(-0.14 / 0.25)) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Grid and collocation tensor (Sec. 3.7, Eq. (grid_points))
+# --------------------------------------------------------------------------
+def test_grid_axes(orc):
+    np.testing.assert_array_equal(orc.grid_axis(orc.CELL, 4, 1.0), [-0.75, -0.25, 0.25, 0.75])
+    np.testing.assert_array_equal(orc.grid_axis(orc.VERTEX, 5, 2.0), [-2.0, -1.0, 0.0, 1.0, 2.0])
+    x = orc.grid_axis(orc.CELL, 64, 1.0)
+    np.testing.assert_allclose(x, -1 + (np.arange(64) + 0.5) * 2 / 64, rtol=0, atol=1e-16)
+
+
+def test_tensor_entries_and_symmetry(orc):
+    k = orc.make_kernel(orc.MATERN, nu=1.2, ell=[0.2, 0.3, 0.4])
+    g = orc.make_grid([5, 6, 7], b=[1.0, 0.8, 1.2])
+    F = orc.tensor(k, g)
+    xs = [orc.grid_axis(orc.CELL, n, b) for n, b in zip([5, 6, 7], [1.0, 0.8, 1.2])]
+    for (i, j, l) in [(0, 0, 0), (2, 3, 4), (4, 5, 6), (1, 2, 0)]:
+        assert F[i, j, l] == orc.kernel_value(k, [xs[0][i], xs[1][j], xs[2][l]])
+    # even function on a symmetric grid (mirrored coordinates agree to rounding)
+    np.testing.assert_allclose(F, F[::-1, :, :], rtol=1e-14)
+    np.testing.assert_allclose(F, F[:, ::-1, ::-1], rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Unfolding and Gram (Sec. 3.2, Fig. Unfolding)
+# --------------------------------------------------------------------------
+def test_unfolding_matches_numpy(orc):
+    rng = np.random.default_rng(0)
+    F = rng.standard_normal((3, 4, 5))
+    np.testing.assert_array_equal(orc.unfold(F, 0), F.reshape(3, 20))
+    np.testing.assert_array_equal(orc.unfold(F, 1), F.transpose(1, 0, 2).reshape(4, 15))
+    np.testing.assert_array_equal(orc.unfold(F, 2), F.transpose(2, 0, 1).reshape(5, 12))
+
+
+def test_gram_against_matmul_and_trace(orc):
+    rng = np.random.default_rng(1)
+    F = rng.random((6, 7, 9))
+    for m in range(3):
+        A = np.moveaxis(F, m, 0).reshape(F.shape[m], -1)
+        G = orc.gram(F, m)
+        np.testing.assert_allclose(G, A @ A.T, rtol=1e-14)
+        assert abs(np.trace(G) - orc.norm2(F)) <= 1e-14 * orc.norm2(F)
+
+
+def test_gram_isotropy_and_persymmetry(orc):
+    k = orc.make_kernel(orc.MATERN, nu=0.8, ell=0.25)
+    F = orc.tensor(k, orc.make_grid(12))
+    G = [orc.gram(F, m) for m in range(3)]
+    np.testing.assert_allclose(G[0], G[1], rtol=1e-15)
+    np.testing.assert_allclose(G[0], G[2], rtol=1e-15)
+    np.testing.assert_allclose(G[0], G[0][::-1, ::-1], rtol=1e-14)  # mirrored grid points round differently
+
+
+# --------------------------------------------------------------------------
+# Jacobi eigensolver
+# --------------------------------------------------------------------------
+def test_sym_eig_random(orc):
+    rng = np.random.default_rng(2)
+    for n in [1, 2, 5, 17, 40]:
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        lam, V, _ = orc.sym_eig(A)
+        ref = np.sort(np.linalg.eigvalsh(A))[::-1]
+        np.testing.assert_allclose(lam, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-14)
+        np.testing.assert_allclose(V @ np.diag(lam) @ V.T, A, atol=2e-14 * np.abs(A).max() * n)
+        # canonical sign: largest |entry| in the first half of each column is positive
+        h = (n + 1) // 2
+        for j in range(n):
+            i = int(np.argmax(np.abs(V[:h, j])))
+            assert V[i, j] > 0
+
+
+def test_sym_eig_graded_psd(orc):
+    # geometric spectrum like the Grams here: eigenvalues resolved to u * lam_1
+    rng = np.random.default_rng(3)
+    n = 30
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = 10.0 ** (-np.arange(n) * 0.7)
+    A = (Q * d) @ Q.T
+    lam, V, _ = orc.sym_eig(A)
+    np.testing.assert_allclose(lam, d, rtol=0, atol=4e-16 * n)
+    for j in range(8):  # well separated leading vectors
+        assert abs(abs(V[:, j] @ Q[:, j]) - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# HOSVD (Sec. 3.2) against brute force and structural facts
+# --------------------------------------------------------------------------
+def _principal_sines(U, W):
+    # sines of the principal angles: singular values of (I - U U^T) W
+    # (1 - cos^2 would lose half the digits)
+    return np.linalg.svd(W - U @ (U.T @ W), compute_uv=False)
+
+
+def test_hosvd_small_matches_numpy_svd_of_unfoldings(orc):
+    k = orc.make_kernel(orc.MATERN, nu=1.2, ell=[0.4, 0.6, 0.9])
+    g = orc.make_grid([6, 7, 8])
+    F = orc.tensor(k, g)
+    res = orc.hosvd(k, g, 0.0, rfix=[6, 7, 8])
+    for m in range(3):
+        A = np.moveaxis(F, m, 0).reshape(F.shape[m], -1)
+        Us, s, _ = np.linalg.svd(A, full_matrices=False)
+        lam = res["lam"][m]
+        np.testing.assert_allclose(lam, s ** 2, rtol=0, atol=2e-14 * s[0] ** 2)
+        # leading well-separated singular vectors agree as subspaces
+        for j in range(3):
+            assert _principal_sines(res["U_all"][m][:, : j + 1], Us[:, : j + 1]).max() < 1e-10
+
+
+def test_hosvd_second_route_one_sided_jacobi(orc):
+    k = orc.make_kernel(orc.MATERN, nu=0.5, ell=0.3)
+    F = orc.tensor(k, orc.make_grid(8))
+    for m in range(3):
+        sig, U = orc.unfolding_svd(F, m)
+        lam, V, _ = orc.sym_eig(orc.gram(F, m))
+        np.testing.assert_allclose(sig ** 2, lam, rtol=0, atol=1e-14 * lam[0])
+        for j in range(4):
+            assert abs(abs(U[:, j] @ V[:, j]) - 1) < 1e-12
+
+
+def test_gaussian_is_rank_one(orc):
+    # exp(-|x|^2/ell^2) = prod_a exp(-x_a^2/ell^2): a rank-1 tensor (Sec. 3.1, 4.4)
+    k = orc.make_kernel(orc.GAUSSIAN, ell=0.4)
+    res = orc.hosvd(k, orc.make_grid(16), 1e-6)
+    assert res["ranks"] == [1, 1, 1]
+    assert res["rel_error"] <= 1e-14
+
+
+def test_full_rank_is_exact(orc):
+    k = orc.make_kernel(orc.MATERN, nu=0.5, ell=0.3)
+    res = orc.hosvd(k, orc.make_grid([9, 10, 11]), 0.0, rfix=[9, 10, 11])
+    assert res["rel_error"] <= 1e-13
+    assert abs(res["core_norm2"] - res["normF2"]) <= 1e-14 * res["normF2"]
+
+
+@pytest.mark.parametrize("nu,ell,eps", [(0.5, 0.3, 1e-4), (1.2, 0.2, 1e-6), (2.5, 0.1, 1e-6), (0.3, 0.05, 1e-4)])
+def test_hosvd_error_bound(orc, nu, ell, eps):
+    # |F - X|^2 <= sum_k sum_{i > r_k} lam_i^(k)  (HOSVD bound), and the eps split
+    k = orc.make_kernel(orc.MATERN, nu=nu, ell=ell)
+    res = orc.hosvd(k, orc.make_grid(20), eps)
+    disc = sum(np.clip(res["lam"][m][res["ranks"][m]:], 0, None).sum() for m in range(3))
+    e2 = res["rel_error"] ** 2 * res["normF2"]
+    assert e2 <= disc * (1 + 1e-9) + 1e-28 * res["normF2"]
+    assert res["rel_error"] <= eps
+    # orthogonal factors: |F - X|^2 = |F|^2 - |B|^2
+    assert abs(e2 - (res["normF2"] - res["core_norm2"])) <= 1e-13 * res["normF2"]
+
+
+def test_sigma2_scaling_invariance(orc):
+    g = orc.make_grid(14)
+    a = orc.hosvd(orc.make_kernel(orc.MATERN, nu=1.2, ell=0.2, sigma2=1.0), g, 1e-6)
+    b = orc.hosvd(orc.make_kernel(orc.MATERN, nu=1.2, ell=0.2, sigma2=3.5), g, 1e-6)
+    assert a["ranks"] == b["ranks"]
+    assert abs(a["rel_error"] - b["rel_error"]) <= 1e-12
+    for m in range(3):
+        assert _principal_sines(a["U"][m][:, :4], b["U"][m][:, :4]).max() < 1e-10
+    np.testing.assert_allclose(b["core"][0, 0, 0], 3.5 * a["core"][0, 0, 0], rtol=1e-13)
+
+
+def test_d2_reduces_to_matrix_svd(orc):
+    # For d = 2 the orthogonal Tucker decomposition is the SVD (Sec. 3.1).
+    k = orc.make_kernel(orc.MATERN, nu=1.5, ell=[0.3, 0.5, 1.0])
+    g = orc.make_grid([9, 7, 1])
+    F = orc.tensor(k, g)
+    M = F[:, :, 0]
+    U, s, Vt = np.linalg.svd(M)
+    res = orc.hosvd(k, g, 0.0, rfix=[7, 7, 1])
+    B = res["core"][:, :, 0]
+    np.testing.assert_allclose(np.abs(np.diag(B)), s, rtol=0, atol=1e-14 * s[0])
+    off = B - np.diag(np.diag(B))
+    assert np.abs(off).max() <= 1e-13 * s[0]
+    for j in range(3):
+        assert abs(abs(res["U"][0][:, j] @ U[:, j]) - 1) < 1e-12
+        assert abs(abs(res["U"][1][:, j] @ Vt[j]) - 1) < 1e-12
+
+
+def test_rank_rule_by_hand(orc):
+    lam = np.array([1.0, 1e-2, 1e-4, 1e-6, -1e-18])
+    nf = lam[:4].sum()
+    # thr = eps^2 nf / 3; discarded(r) = sum_{i >= r} lam_i^+ (0-based)
+    assert orc.rank(lam, nf, math.sqrt(3 * 2e-6 / nf), 10) == (3, 0)   # 1e-6 <= 2e-6 < 1.01e-4
+    assert orc.rank(lam, nf, math.sqrt(3 * 1e-6 / nf), 10)[0] == 3    # boundary is inclusive
+    assert orc.rank(lam, nf, math.sqrt(3 * 0.99e-6 / nf), 10)[0] == 4
+    assert orc.rank(lam, nf, 1.0, 10)[0] == 1
+    r, f = orc.rank(lam, nf, 1e-12, 2)
+    assert r == 2 and f & orc.RANK_CAPPED
+    assert orc.rank(lam, nf, 1e-9, 10)[1] & orc.EPS_UNREACHABLE
+
+
+def test_core_and_reconstruct_match_einsum(orc):
+    rng = np.random.default_rng(4)
+    F = rng.standard_normal((5, 6, 7))
+    U = [np.linalg.qr(rng.standard_normal((n, n)))[0][:, :r] for n, r in zip(F.shape, (2, 3, 4))]
+    B = orc.core(F, U, [2, 3, 4])
+    np.testing.assert_allclose(B, np.einsum("ijk,ia,jb,kc->abc", F, *U), atol=1e-13)
+    X = orc.reconstruct(B, U, F.shape)
+    np.testing.assert_allclose(X, np.einsum("abc,ia,jb,kc->ijk", B, *U), atol=1e-13)
+    assert abs(orc.tucker_point(B, U, [1, 2, 3]) - X[1, 2, 3]) < 1e-13
+    assert abs(orc.rel_error(F, X) - np.linalg.norm(F - X) / np.linalg.norm(F)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# The paper's printed table (Sec. 4, Table zero_points): sanity only
+# --------------------------------------------------------------------------
+def test_zero_points_table_sanity(orc):
+    rows = {}
+    with open(os.path.join(GOLDEN, "zero_points.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                v = line.split()
+                rows[int(v[0])] = [float(t) for t in v[1:]]
+    n = 129
+    # Reading: box b = 5 (not stated in the paper); HOSVD without ALS.
+    k = orc.make_kernel(orc.SLATER_P, ell=1.0, p=1.0)
+    g = orc.make_grid(n, b=5.0, kind=orc.VERTEX)
+    F = orc.tensor(k, g)
+    assert F[n // 2, n // 2, n // 2] == 1.0
+    lam, V, _ = orc.sym_eig(orc.gram(F, 0))
+    for r in range(1, 10):
+        U = [V[:, :r]] * 3
+        err = 1 - orc.tucker_point(orc.core(F, U, [r] * 3), U, [n // 2] * 3)
+        want = rows[129][r - 1]
+        assert want / 1.35 <= err <= want * 1.35, (r, err, want)
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each must make a pin fail
+# --------------------------------------------------------------------------
+def test_planted_transposed_factor_is_caught(orc):
+    # a transposed factor breaks the HOSVD bound at truncated rank
+    k = orc.make_kernel(orc.MATERN, nu=0.5, ell=[0.3, 0.4, 0.5])
+    g = orc.make_grid([6, 7, 8])
+    F = orc.tensor(k, g)
+    res = orc.hosvd(k, g, 0.0, rfix=[6, 7, 8])
+    U, lam = res["U_all"], res["lam"]
+    r = [3, 3, 3]
+    bound = sum(np.clip(lam[m][r[m]:], 0, None).sum() for m in range(3)) / res["normF2"]
+    good = [U[0][:, :3], U[1][:, :3], U[2][:, :3]]
+    bad = [U[0][:, :3], U[1][:, :3], U[2].T[:, :3].copy()]
+    eg = orc.rel_error(F, orc.reconstruct(orc.core(F, good, r), good, F.shape))
+    eb = orc.rel_error(F, orc.reconstruct(orc.core(F, bad, r), bad, F.shape))
+    assert eg ** 2 <= bound * (1 + 1e-9)
+    assert eb ** 2 > bound * 10
+
+
+def test_planted_dropped_gram_term_is_caught(orc):
+    k = orc.make_kernel(orc.MATERN, nu=1.2, ell=0.3)
+    F = orc.tensor(k, orc.make_grid(8))
+    G = orc.gram(F, 0)
+    Fd = F.copy()
+    Fd[:, -1, -1] = 0.0  # one column of the unfolding dropped
+    Gd = orc.gram(Fd, 0)
+    # trace(G) = |F|^2 catches the dropped column
+    assert abs(np.trace(Gd) - orc.norm2(F)) > 1e-10 * orc.norm2(F)
+    assert abs(np.trace(G) - orc.norm2(F)) <= 1e-14 * orc.norm2(F)
+
+
+def test_planted_wrong_sign_in_bessel_is_caught(orc):
+    # K_{nu+1} + K_{nu-1} in place of the difference fails the recurrence pin
+    nu, z = 1.2, 0.7
+    kp, km, k0 = (orc.bessel_k(nu + 1, z), orc.bessel_k(nu - 1, z), orc.bessel_k(nu, z))
+    assert abs((kp + km) - 2 * nu / z * k0) > 1e-3 * kp
