@@ -1,0 +1,170 @@
+/*
+ * tucker_matern.h -- C-ABI of the GB300 (sm_103a) library that computes the
+ * Tucker (HOSVD) approximation of Matern, p-Slater and Gaussian covariance
+ * functions sampled on an n1 x n2 x n3 axis-parallel grid, after
+ * Litvinenko, Keyes, Khoromskaia, Khoromskij, Matthies, "Tucker tensor
+ * analysis of Matern functions in spatial statistics" (arXiv:1711.06874).
+ *
+ * Conventions for every entry point
+ *  - Return value: TK_OK (0) or a positive tk_status code.  Nothing throws
+ *    across this interface.  tk_last_error(ctx) gives a message for the last
+ *    failure on that context.
+ *  - Invalid arguments return TK_EINVAL before any work is enqueued and
+ *    leave outputs untouched.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; entry points that must return host
+ *    values (ranks, error norms) synchronise that stream before returning.
+ *  - Arrays are row-major, FP64 unless stated.  "device" pointers are CUDA
+ *    global-memory addresses on the context's device; "host" pointers are
+ *    ordinary CPU memory.  The caller owns every pointer it passes; the
+ *    library owns tk_ctx and tk_result and everything inside them.
+ *  - A context serialises the calls made on it; use one context per host
+ *    thread for concurrency.
+ */
+#ifndef TUCKER_MATERN_H
+#define TUCKER_MATERN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TK_OK = 0,
+  TK_EINVAL = 1,   /* argument out of range */
+  TK_ENOMEM = 2,   /* device or host allocation failed */
+  TK_ECUDA = 3,    /* a CUDA call failed (message in tk_last_error) */
+  TK_ETIMEOUT = 4, /* a bounded device wait ran out; results are invalid */
+  TK_EBUSY = 5,    /* serving: the ticket is not finished yet */
+  TK_ENOTFOUND = 6 /* serving: unknown ticket */
+} tk_status;
+
+/* Covariance kinds.
+ *  TK_MATERN   Sec. 2.2, Eq. (Matern): C = sigma2 2^(1-nu)/Gamma(nu) z^nu K_nu(z),
+ *              z = sqrt(2 nu) r_A, with the anisotropic distance of Sec. 2.2,
+ *              r_A^2 = sum_a x_a^2 / ell_a^2 (A = diag(1/ell_a^2)).
+ *  TK_SLATER_P Sec. 3.7, Eq. (exp_p): C = sigma2 exp(-r_A^p).
+ *  TK_GAUSSIAN the nu -> infinity limit of Sec. 2.2: C = sigma2 exp(-r_A^2);
+ *              a rank-one tensor (Sec. 4.4). */
+typedef enum { TK_MATERN = 0, TK_SLATER_P = 1, TK_GAUSSIAN = 2 } tk_kind;
+
+/* Grid kinds.  Coordinates of axis a, 0-based index i:
+ *  TK_CELL_CENTRED x_i = -b_a + (i + 1/2) 2 b_a / n_a
+ *  TK_VERTEX       x_i = -b_a + i 2 b_a / (n_a - 1)   (Sec. 3.7, Eq. (grid_points)) */
+typedef enum { TK_CELL_CENTRED = 0, TK_VERTEX = 1 } tk_grid_kind;
+
+/* Arithmetic of the two contractions (Gram and core).  The eigensolve and the
+ * rank decision are FP64 in every mode.
+ *  TK_FP64        FP64 on the CUDA cores (the plain path).
+ *  TK_SLICED_BF16 Gram as exact products of 8-bit BF16 slices on the tcgen05
+ *                 tensor cores, FP32 chunk sums promoted to FP64 (FP64-class). */
+typedef enum { TK_FP64 = 0, TK_SLICED_BF16 = 1 } tk_precision;
+
+/* Result flags, per mode. */
+enum {
+  TK_RANK_CAPPED = 1u,                /* the eps rule wanted more than rmax */
+  TK_EPS_UNREACHABLE_AT_PRECISION = 2u /* eps^2 |F|^2 / 3 is below 10 u_eff n |F|^2 */
+};
+
+typedef struct {
+  int32_t kind;     /* tk_kind */
+  double nu;        /* Matern smoothness, > 0 */
+  double ell[3];    /* per-axis length scale, > 0 */
+  double sigma2;    /* variance, > 0 */
+  double p;         /* p-Slater exponent, > 0 */
+} tk_kernel;
+
+typedef struct {
+  int32_t n[3];     /* grid points per axis, 2 <= n <= 1024 */
+  double b[3];      /* half-width of the box [-b, b], > 0 */
+  int32_t kind;     /* tk_grid_kind */
+} tk_grid;
+
+typedef struct {
+  double eps;       /* relative Frobenius tolerance, >= 0 (Task 1, Sec. 2.1) */
+  int32_t rmax[3];  /* rank caps, 1 <= rmax <= 88 */
+  int32_t rfix[3];  /* > 0: use this rank for the mode instead of the eps rule */
+  int32_t precision;          /* tk_precision */
+  int32_t isotropic_shortcut; /* 1: when the three Grams are equal by symmetry
+                                 (equal n, b, ell), form and solve one of them */
+  int32_t reserved[4];        /* must be zero */
+} tk_opts;
+
+typedef struct tk_ctx tk_ctx;
+typedef struct tk_result tk_result;
+
+const char* tk_strerror(int status);
+const char* tk_last_error(const tk_ctx* ctx);
+/* Version string of the library build. */
+const char* tk_version(void);
+
+/* Creates a context on CUDA device `device` (TK_EINVAL if out of range). */
+int tk_create(tk_ctx** ctx, int device);
+/* Frees the context and its workspace; results created on it must be freed first. */
+void tk_destroy(tk_ctx* ctx);
+/* Default options: eps 1e-6, rmax 32, rfix 0, TK_SLICED_BF16, shortcut on. */
+void tk_default_opts(tk_opts* opts);
+
+/* ---------------------------------------------------------------------------
+ * Whole solve: Task 1 of Sec. 2.1 by the HOSVD of Sec. 3.2.
+ *   (a) sample C on the grid (collocation tensor, Sec. 3.7),
+ *   (b) form G_k = F_(k) F_(k)^T for the three unfoldings (Fig. Unfolding),
+ *   (c) take the leading eigenvectors of each G_k as the factor U_k, the rank
+ *       r_k being the smallest r whose discarded eigenvalue sum is
+ *       <= eps^2 |F|^2 / 3 (capped at rmax), sign fixed so that the entry of
+ *       largest magnitude among the first ceil(n_k/2) is positive,
+ *   (d) core B = F x_1 U_1^T x_2 U_2^T x_3 U_3^T (Sec. 3.1, 3.2), mode 3 first.
+ * On TK_OK *out owns device copies of U_k (n_k x r_k) and B (r1 x r2 x r3).
+ * Synchronises `stream` once to read the three ranks.
+ * ------------------------------------------------------------------------- */
+int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
+              tk_result** out, void* stream);
+
+/* Ranks and flags of a result (host arrays of 3). */
+int tk_ranks(const tk_result* res, int32_t r[3], uint32_t flags[3]);
+/* Factor U_mode (n_mode x r_mode, row-major, orthonormal columns) into dst.
+ * on_device: 1 = dst is device memory, 0 = host memory. */
+int tk_factor(const tk_result* res, int mode, double* dst, int on_device, void* stream);
+/* Core B (r1 x r2 x r3, row-major) into dst. */
+int tk_core(const tk_result* res, double* dst, int on_device, void* stream);
+/* Leading eigenvalues of G_mode (descending) computed by the solve; writes
+ * min(count, available) values to the host array dst and returns that number
+ * through *written. */
+int tk_eigenvalues(const tk_result* res, int mode, double* dst, int count, int* written);
+/* |F|^2 of the sampled tensor (compensated FP64 sum), host scalar. */
+int tk_norm2(const tk_result* res, double* normF2);
+
+/* X = B x_1 U_1 x_2 U_2 x_3 U_3 into dst (device, n1 n2 n3 FP64). */
+int tk_reconstruct(tk_ctx* ctx, const tk_result* res, double* dst, void* stream);
+/* Eq. (FNorm): |F - X|_F / |F|_F by direct subtraction with compensated FP64
+ * sums, where F is resampled from (kernel, grid) and X is never stored.
+ * Writes the host scalar *out; synchronises `stream`. */
+int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, const tk_grid* grid,
+                 double* out, void* stream);
+void tk_result_free(tk_result* res);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points (one step of the path each, device buffers in and out).
+ * ------------------------------------------------------------------------- */
+/* Collocation tensor F (device, n1 n2 n3 FP64) of Sec. 3.7. */
+int tk_eval(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, double* F, void* stream);
+/* Gram G = F_(mode) F_(mode)^T (device, n_mode x n_mode FP64) of the device
+ * tensor F (n[0] n[1] n[2] FP64), in the arithmetic `precision`. */
+int tk_gram(tk_ctx* ctx, const double* F, const int32_t n[3], int mode, int precision, double* G,
+            void* stream);
+/* Leading m eigenpairs of the symmetric PSD device matrix G (n x n):
+ * lam (device, m, descending) and V (device, n x m, orthonormal columns,
+ * canonical signs).  1 <= m <= min(n, 96). */
+int tk_sym_eig(tk_ctx* ctx, const double* G, int n, int m, double* lam, double* V, void* stream);
+/* Core B (device, r1 r2 r3) = F x_1 U1^T x_2 U2^T x_3 U3^T for the device
+ * tensor F (n[0] n[1] n[2]) and device factors U_k (n_k x r_k). */
+int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* U1,
+                const double* U2, const double* U3, const int32_t r[3], int precision, double* B,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_MATERN_H */

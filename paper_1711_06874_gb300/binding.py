@@ -1,0 +1,244 @@
+"""ctypes binding of libtucker_matern (the C-ABI in include/tucker_matern.h).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library.  Device buffers are PyTorch CUDA tensors (``data_ptr()``), streams
+are ``torch.cuda.Stream`` handles.  The library is loaded on first use; if
+it is missing or cannot load, the call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtucker_matern.so")
+
+TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_ETIMEOUT, TK_EBUSY, TK_ENOTFOUND = range(7)
+TK_MATERN, TK_SLATER_P, TK_GAUSSIAN = 0, 1, 2
+TK_CELL_CENTRED, TK_VERTEX = 0, 1
+TK_FP64, TK_SLICED_BF16 = 0, 1
+TK_RANK_CAPPED, TK_EPS_UNREACHABLE_AT_PRECISION = 1, 2
+
+# every function the header declares, with (restype, argtypes)
+_c = ctypes
+_vp, _i32, _u32, _dbl = _c.c_void_p, _c.c_int32, _c.c_uint32, _c.c_double
+
+
+class Kernel(_c.Structure):
+    _fields_ = [("kind", _i32), ("nu", _dbl), ("ell", _dbl * 3), ("sigma2", _dbl), ("p", _dbl)]
+
+
+class Grid(_c.Structure):
+    _fields_ = [("n", _i32 * 3), ("b", _dbl * 3), ("kind", _i32)]
+
+
+class Opts(_c.Structure):
+    _fields_ = [("eps", _dbl), ("rmax", _i32 * 3), ("rfix", _i32 * 3), ("precision", _i32),
+                ("isotropic_shortcut", _i32), ("reserved", _i32 * 4)]
+
+
+SIGNATURES = {
+    "tk_strerror": (_c.c_char_p, [_c.c_int]),
+    "tk_last_error": (_c.c_char_p, [_vp]),
+    "tk_version": (_c.c_char_p, []),
+    "tk_create": (_c.c_int, [_c.POINTER(_vp), _c.c_int]),
+    "tk_destroy": (None, [_vp]),
+    "tk_default_opts": (None, [_c.POINTER(Opts)]),
+    "tk_tucker": (_c.c_int, [_vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(Opts),
+                             _c.POINTER(_vp), _vp]),
+    "tk_ranks": (_c.c_int, [_vp, _c.POINTER(_i32), _c.POINTER(_u32)]),
+    "tk_factor": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int, _vp]),
+    "tk_core": (_c.c_int, [_vp, _vp, _c.c_int, _vp]),
+    "tk_eigenvalues": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
+    "tk_norm2": (_c.c_int, [_vp, _c.POINTER(_dbl)]),
+    "tk_reconstruct": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "tk_rel_error": (_c.c_int, [_vp, _vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(_dbl), _vp]),
+    "tk_result_free": (None, [_vp]),
+    "tk_eval": (_c.c_int, [_vp, _c.POINTER(Kernel), _c.POINTER(Grid), _vp, _vp]),
+    "tk_gram": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _c.c_int, _c.c_int, _vp, _vp]),
+    "tk_sym_eig": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _vp, _vp, _vp]),
+    "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
+                               _vp, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it is missing (no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtucker_matern.so not found at {path}; run __graft_entry__.build()")
+        lib = _c.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != TK_OK:
+        lib = load()
+        msg = lib.tk_strerror(rc).decode()
+        if ctx is not None and ctx.value:
+            detail = lib.tk_last_error(ctx).decode()
+            if detail:
+                msg += ": " + detail
+        raise TuckerError(rc, msg)
+
+
+def make_kernel(prob: workloads.Problem) -> Kernel:
+    return Kernel(prob.kind, prob.nu, (_dbl * 3)(*prob.ell), prob.sigma2, prob.p)
+
+
+def make_grid(prob: workloads.Problem) -> Grid:
+    return Grid((_i32 * 3)(*prob.n), (_dbl * 3)(*prob.b), prob.grid)
+
+
+def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True) -> Opts:
+    o = Opts()
+    load().tk_default_opts(_c.byref(o))
+    o.eps = prob.eps
+    o.rmax = (_i32 * 3)(*prob.rmax)
+    o.rfix = (_i32 * 3)(*rfix)
+    o.precision = precision
+    o.isotropic_shortcut = 1 if shortcut else 0
+    return o
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.ptr = _vp()
+        _check(self.lib.tk_create(_c.byref(self.ptr), int(device)))
+        self.device = device
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            self.lib.tk_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- whole solve -------------------------------------------------------
+    def tucker(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True,
+               stream=None) -> "Result":
+        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut)
+        out = _vp()
+        _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
+                                  _stream_ptr(stream)), self.ptr)
+        return Result(self, out, prob)
+
+    # ---- stage entry points (device tensors in and out) --------------------
+    def eval(self, prob: workloads.Problem, F, stream=None):
+        k, g = make_kernel(prob), make_grid(prob)
+        _check(self.lib.tk_eval(self.ptr, _c.byref(k), _c.byref(g), F.data_ptr(), _stream_ptr(stream)),
+               self.ptr)
+
+    def gram(self, F, mode: int, G, precision=TK_FP64, stream=None):
+        n = (_i32 * 3)(*F.shape)
+        _check(self.lib.tk_gram(self.ptr, F.data_ptr(), n, int(mode), int(precision), G.data_ptr(),
+                                _stream_ptr(stream)), self.ptr)
+
+    def sym_eig(self, G, m: int, lam, V, stream=None):
+        _check(self.lib.tk_sym_eig(self.ptr, G.data_ptr(), int(G.shape[0]), int(m), lam.data_ptr(),
+                                   V.data_ptr(), _stream_ptr(stream)), self.ptr)
+
+    def ttm_core(self, F, U, B, precision=TK_FP64, stream=None):
+        n = (_i32 * 3)(*F.shape)
+        r = (_i32 * 3)(*B.shape)
+        _check(self.lib.tk_ttm_core(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(),
+                                    U[2].data_ptr(), r, int(precision), B.data_ptr(), _stream_ptr(stream)),
+               self.ptr)
+
+
+@dataclass
+class Result:
+    ctx: Context
+    ptr: _vp
+    prob: workloads.Problem
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def free(self):
+        if self.ptr is not None and self.ptr.value:
+            self.ctx.lib.tk_result_free(self.ptr)
+        self.ptr = None
+
+    @property
+    def ranks(self):
+        r = (_i32 * 3)()
+        f = (_u32 * 3)()
+        _check(self.ctx.lib.tk_ranks(self.ptr, r, f))
+        return [int(v) for v in r], [int(v) for v in f]
+
+    def factor(self, mode: int) -> np.ndarray:
+        r, _ = self.ranks
+        out = np.empty((self.prob.n[mode], r[mode]), np.float64)
+        _check(self.ctx.lib.tk_factor(self.ptr, int(mode), out.ctypes.data, 0, None), self.ctx.ptr)
+        return out
+
+    def core(self) -> np.ndarray:
+        r, _ = self.ranks
+        out = np.empty(tuple(r), np.float64)
+        _check(self.ctx.lib.tk_core(self.ptr, out.ctypes.data, 0, None), self.ctx.ptr)
+        return out
+
+    def eigenvalues(self, mode: int, count: int = 96) -> np.ndarray:
+        out = np.empty(count, np.float64)
+        w = _c.c_int(0)
+        _check(self.ctx.lib.tk_eigenvalues(self.ptr, int(mode), out.ctypes.data, count, _c.byref(w)))
+        return out[: w.value].copy()
+
+    @property
+    def norm2(self) -> float:
+        v = _dbl(0)
+        _check(self.ctx.lib.tk_norm2(self.ptr, _c.byref(v)))
+        return v.value
+
+    def reconstruct(self, dst, stream=None):
+        _check(self.ctx.lib.tk_reconstruct(self.ctx.ptr, self.ptr, dst.data_ptr(), _stream_ptr(stream)),
+               self.ctx.ptr)
+
+    def rel_error(self, stream=None) -> float:
+        k, g = make_kernel(self.prob), make_grid(self.prob)
+        v = _dbl(0)
+        _check(self.ctx.lib.tk_rel_error(self.ctx.ptr, self.ptr, _c.byref(k), _c.byref(g), _c.byref(v),
+                                         _stream_ptr(stream)), self.ctx.ptr)
+        return v.value

@@ -1,0 +1,510 @@
+// C-ABI of libtucker_matern: argument checks, workspace planning, and the
+// order of the stages of the HOSVD (Sec. 3.2): sample F, |F|^2, Gram per
+// mode, leading eigenpairs and rank per mode, then the core by chained TTMs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tk_internal.h"
+
+namespace tk {
+
+void fail(int status, const std::string& msg) { throw Error{status, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    fail(TK_ECUDA, m);
+  }
+}
+
+void Workspace::reserve(size_t need, cudaStream_t s) {
+  used = 0;
+  if (need <= bytes) return;
+  if (base) {
+    check_cuda(cudaStreamSynchronize(s), "workspace sync");
+    check_cuda(cudaDeviceSynchronize(), "workspace sync");
+    check_cuda(cudaFree(base), "cudaFree(workspace)");
+    base = nullptr;
+    bytes = 0;
+  }
+  const size_t want = std::max(need, bytes + bytes / 4);
+  if (cudaMalloc(&base, want) != cudaSuccess) {
+    cudaGetLastError();
+    base = nullptr;
+    if (cudaMalloc(&base, need) != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      fail(TK_ENOMEM, "cannot allocate device workspace of " + std::to_string(need) + " bytes");
+    }
+    bytes = need;
+  } else {
+    bytes = want;
+  }
+}
+
+void Workspace::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  bytes = used = 0;
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+namespace {
+
+constexpr int kMaxN = 1024;
+constexpr int kMaxRank = 88;
+constexpr int kMargin = 8;  // extra subspace columns beyond the rank cap
+
+template <class Fn>
+int guard(tk_ctx* ctx, Fn&& fn) {
+  try {
+    fn();
+    return TK_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->last_error = "host allocation failed";
+    return TK_ENOMEM;
+  } catch (...) {
+    if (ctx) ctx->last_error = "unexpected exception";
+    return TK_ECUDA;
+  }
+}
+
+void check_kernel(const tk_kernel* k) {
+  if (!k) fail(TK_EINVAL, "kernel is NULL");
+  if (k->kind < TK_MATERN || k->kind > TK_GAUSSIAN) fail(TK_EINVAL, "unknown kernel kind");
+  for (int a = 0; a < 3; ++a)
+    if (!(k->ell[a] > 0.0) || !std::isfinite(k->ell[a])) fail(TK_EINVAL, "ell must be > 0");
+  if (!(k->sigma2 > 0.0) || !std::isfinite(k->sigma2)) fail(TK_EINVAL, "sigma2 must be > 0");
+  if (k->kind == TK_MATERN && (!(k->nu > 0.0) || !(k->nu <= 50.0)))
+    fail(TK_EINVAL, "nu must be in (0, 50]");
+  if (k->kind == TK_SLATER_P && (!(k->p > 0.0) || !(k->p <= 8.0))) fail(TK_EINVAL, "p must be in (0, 8]");
+}
+
+void check_grid(const tk_grid* g) {
+  if (!g) fail(TK_EINVAL, "grid is NULL");
+  if (g->kind != TK_CELL_CENTRED && g->kind != TK_VERTEX) fail(TK_EINVAL, "unknown grid kind");
+  for (int a = 0; a < 3; ++a) {
+    if (g->n[a] < 2 || g->n[a] > kMaxN) fail(TK_EINVAL, "n must be in [2, 1024]");
+    if (!(g->b[a] > 0.0) || !std::isfinite(g->b[a])) fail(TK_EINVAL, "b must be > 0");
+  }
+}
+
+void check_opts(const tk_opts* o) {
+  if (!o) fail(TK_EINVAL, "opts is NULL");
+  if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) fail(TK_EINVAL, "eps must be >= 0");
+  for (int a = 0; a < 3; ++a) {
+    if (o->rmax[a] < 1 || o->rmax[a] > kMaxRank) fail(TK_EINVAL, "rmax must be in [1, 88]");
+    if (o->rfix[a] < 0 || o->rfix[a] > kMaxRank) fail(TK_EINVAL, "rfix must be in [0, 88]");
+  }
+  if (o->precision != TK_FP64 && o->precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
+  for (int i = 0; i < 4; ++i)
+    if (o->reserved[i] != 0) fail(TK_EINVAL, "reserved fields must be zero");
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void set_device(tk_ctx* ctx) { TK_CUDA(cudaSetDevice(ctx->device)); }
+
+// Subspace size for mode a: rank cap (or fixed rank) plus a margin, at most n.
+int subspace_m(const tk_opts& o, int n, int a) {
+  const int want = std::max(o.rmax[a], o.rfix[a]) + kMargin;
+  return std::min(std::min(want, n), 96);
+}
+
+bool shortcut_ok(const tk_kernel& k, const tk_grid& g, const tk_opts& o) {
+  return o.isotropic_shortcut && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.b[0] == g.b[1] &&
+         g.b[1] == g.b[2] && k.ell[0] == k.ell[1] && k.ell[1] == k.ell[2] &&
+         o.rmax[0] == o.rmax[1] && o.rmax[1] == o.rmax[2] && o.rfix[0] == o.rfix[1] &&
+         o.rfix[1] == o.rfix[2];
+}
+
+// TTM chain of Sec. 3.1/3.2 (mode 3, then 2, then 1), FP64 GEMMs.
+// U_k: n_k x r_k with leading dimension ld_k (row-major).
+void ttm_core_f64(const double* F, const int n[3], const double* U1, int ld1, const double* U2,
+                  int ld2, const double* U3, int ld3, const int r[3], double* T1, double* T2,
+                  double* B, cudaStream_t s) {
+  const int n1 = n[0], n2 = n[1], n3 = n[2], r1 = r[0], r2 = r[1], r3 = r[2];
+  // T1[ij][c] = sum_l F[ij][l] U3[l][c]
+  GemmDesc a{n1 * n2, r3, n3, 1, F, 0, n3, 1, U3, 0, ld3, 1, T1, 0, r3, 1};
+  gemm_f64(a, s);
+  // T2[i][b][c] = sum_j U2[j][b] T1[i][j][c]
+  GemmDesc b{r2, r3, n2, n1, U2, 0, 1, ld2, T1, (long long)n2 * r3, r3, 1, T2, (long long)r2 * r3, r3, 1};
+  gemm_f64(b, s);
+  // B[a][bc] = sum_i U1[i][a] T2[i][bc]
+  GemmDesc c{r1, r2 * r3, n1, 1, U1, 0, 1, ld1, T2, 0, (long long)r2 * r3, 1, B, 0, (long long)r2 * r3, 1};
+  gemm_f64(c, s);
+}
+
+size_t ttm_scratch_doubles(const int n[3], const int r[3]) {
+  return (size_t)n[0] * n[1] * r[2] + (size_t)n[0] * r[1] * r[2];
+}
+
+// W2 (n1 n2 x r3) = B x_1 U1 x_2 U2, the reconstruction up to the last mode.
+void recon_w2(const double* B, const int r[3], const double* U1, int ld1, const double* U2, int ld2,
+              const int n[3], double* W1, double* W2, cudaStream_t s) {
+  const int n1 = n[0], n2 = n[1], r1 = r[0], r2 = r[1], r3 = r[2];
+  // W1[i][bc] = sum_a U1[i][a] B[a][bc]
+  GemmDesc a{n1, r2 * r3, r1, 1, U1, 0, ld1, 1, B, 0, (long long)r2 * r3, 1, W1, 0, (long long)r2 * r3, 1};
+  gemm_f64(a, s);
+  // W2[i][j][c] = sum_b U2[j][b] W1[i][b][c]
+  GemmDesc b{n2, r3, r2, n1, U2, 0, ld2, 1, W1, (long long)r2 * r3, r3, 1, W2, (long long)n2 * r3, r3, 1};
+  gemm_f64(b, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tk_version(void) { return "tucker_matern 0.1 (sm_103a)"; }
+
+const char* tk_strerror(int status) {
+  switch (status) {
+    case TK_OK: return "ok";
+    case TK_EINVAL: return "invalid argument";
+    case TK_ENOMEM: return "out of memory";
+    case TK_ECUDA: return "CUDA error";
+    case TK_ETIMEOUT: return "device wait timed out";
+    case TK_EBUSY: return "not ready";
+    case TK_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+const char* tk_last_error(const tk_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+void tk_default_opts(tk_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps = 1e-6;
+  for (int a = 0; a < 3; ++a) o->rmax[a] = 32;
+  o->precision = TK_SLICED_BF16;
+  o->isotropic_shortcut = 1;
+}
+
+int tk_create(tk_ctx** out, int device) {
+  if (!out) return TK_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return TK_ECUDA;
+  }
+  if (device < 0 || device >= count) return TK_EINVAL;
+  tk_ctx* ctx = new (std::nothrow) tk_ctx();
+  if (!ctx) return TK_ENOMEM;
+  ctx->device = device;
+  int rc = guard(ctx, [&] {
+    TK_CUDA(cudaSetDevice(device));
+    TK_CUDA(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+  });
+  if (rc != TK_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return TK_OK;
+}
+
+void tk_destroy(tk_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->ws.release();
+  delete ctx;
+}
+
+void tk_result_free(tk_result* res) {
+  if (!res) return;
+  if (res->ctx) cudaSetDevice(res->ctx->device);
+  for (int a = 0; a < 3; ++a)
+    if (res->U[a]) cudaFree(res->U[a]);
+  if (res->core) cudaFree(res->core);
+  delete res;
+}
+
+int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
+              tk_result** out, void* stream) {
+  if (!ctx || !out) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  tk_result* res = nullptr;
+  int rc = guard(ctx, [&] {
+    check_kernel(kernel);
+    check_grid(grid);
+    check_opts(opts);
+    if (opts->precision == TK_SLICED_BF16) fail(TK_EINVAL, "TK_SLICED_BF16 is not available in this build");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    const tk_opts& o = *opts;
+    const int* n = grid->n;
+    const size_t N = (size_t)n[0] * n[1] * n[2];
+    const bool one = shortcut_ok(*kernel, *grid, o);
+    const int nmodes = one ? 1 : 3;
+    int m[3];
+    for (int a = 0; a < 3; ++a) m[a] = subspace_m(o, n[a], a);
+    size_t gram_scr = 0, eig_scr = 0;
+    for (int a = 0; a < nmodes; ++a) {
+      gram_scr = std::max(gram_scr, gram_f64_scratch_doubles(n, a));
+      eig_scr = std::max(eig_scr, sym_eig_scratch_doubles(n[a], m[a]));
+    }
+    int rcap[3];
+    for (int a = 0; a < 3; ++a) rcap[a] = std::max(o.rmax[a], o.rfix[a]);
+    size_t need = carve_bytes<double>(N) + carve_bytes<double>(eval_scratch_doubles(*kernel, *grid)) +
+                  carve_bytes<double>(norm2_scratch_doubles(N)) + carve_bytes<double>(gram_scr) +
+                  carve_bytes<double>(eig_scr) + carve_bytes<double>(64) + carve_bytes<int>(64) +
+                  carve_bytes<double>(ttm_scratch_doubles(n, rcap));
+    for (int a = 0; a < 3; ++a)
+      need += carve_bytes<double>((size_t)n[a] * n[a]) + carve_bytes<double>((size_t)n[a] * m[a]) +
+              carve_bytes<double>(m[a]);
+    ctx->ws.reserve(need, s);
+    Workspace& ws = ctx->ws;
+    double* F = ws.take<double>(N);
+    double* table = ws.take<double>(std::max<size_t>(1, eval_scratch_doubles(*kernel, *grid)));
+    double* nscr = ws.take<double>(norm2_scratch_doubles(N));
+    double* gscr = ws.take<double>(std::max<size_t>(1, gram_scr));
+    double* escr = ws.take<double>(eig_scr);
+    double* small = ws.take<double>(64);  // [0] |F|^2, [1..3] traces
+    int* ranks_dev = ws.take<int>(64);
+    double* ttm = ws.take<double>(ttm_scratch_doubles(n, rcap));
+    double *G[3], *V[3], *lam[3];
+    for (int a = 0; a < 3; ++a) {
+      G[a] = ws.take<double>((size_t)n[a] * n[a]);
+      V[a] = ws.take<double>((size_t)n[a] * m[a]);
+      lam[a] = ws.take<double>(m[a]);
+    }
+    eval_tensor_f64(*kernel, *grid, F, table, s);
+    norm2_f64(F, N, small, nscr, s);
+    for (int a = 0; a < nmodes; ++a) {
+      gram_f64(F, n, a, G[a], gscr, s);
+      sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
+      rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], std::ldexp(1.0, -53),
+                n[a], ranks_dev + 2 * a, s);
+    }
+    int hr[6];
+    double hsmall[4];
+    TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 2 * nmodes, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(hsmall, small, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    res = new tk_result();
+    res->ctx = ctx;
+    res->precision = o.precision;
+    for (int a = 0; a < 3; ++a) {
+      res->n[a] = n[a];
+      res->m[a] = m[a];
+      res->lam[a].resize(m[a]);
+    }
+    for (int a = 0; a < nmodes; ++a)
+      TK_CUDA(cudaMemcpyAsync(res->lam[a].data(), lam[a], sizeof(double) * m[a], cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    for (int a = 0; a < 3; ++a) {
+      const int src = one ? 0 : a;
+      res->r[a] = hr[2 * src];
+      res->flags[a] = (uint32_t)hr[2 * src + 1];
+      if (one && a > 0) res->lam[a] = res->lam[0];
+    }
+    res->normF2 = hsmall[0];
+    const int* r = res->r;
+    for (int a = 0; a < 3; ++a) {
+      TK_CUDA(cudaMalloc(&res->U[a], sizeof(double) * (size_t)n[a] * r[a]));
+      const int src = one ? 0 : a;
+      // first r columns of V (n x m, ld m) into U (n x r, ld r)
+      TK_CUDA(cudaMemcpy2DAsync(res->U[a], sizeof(double) * r[a], V[src], sizeof(double) * m[src],
+                                sizeof(double) * r[a], n[a], cudaMemcpyDeviceToDevice, s));
+    }
+    TK_CUDA(cudaMalloc(&res->core, sizeof(double) * (size_t)r[0] * r[1] * r[2]));
+    double* T1 = ttm;
+    double* T2 = ttm + (size_t)n[0] * n[1] * r[2];
+    ttm_core_f64(F, n, res->U[0], r[0], res->U[1], r[1], res->U[2], r[2], r, T1, T2, res->core, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+  if (rc != TK_OK) {
+    if (res) tk_result_free(res);
+    return rc;
+  }
+  *out = res;
+  return TK_OK;
+}
+
+int tk_ranks(const tk_result* res, int32_t r[3], uint32_t flags[3]) {
+  if (!res || !r) return TK_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    r[a] = res->r[a];
+    if (flags) flags[a] = res->flags[a];
+  }
+  return TK_OK;
+}
+
+int tk_factor(const tk_result* res, int mode, double* dst, int on_device, void* stream) {
+  if (!res || !dst || mode < 0 || mode > 2) return TK_EINVAL;
+  return guard(res->ctx, [&] {
+    set_device(res->ctx);
+    cudaStream_t s = as_stream(stream);
+    TK_CUDA(cudaMemcpyAsync(dst, res->U[mode], sizeof(double) * (size_t)res->n[mode] * res->r[mode],
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_core(const tk_result* res, double* dst, int on_device, void* stream) {
+  if (!res || !dst) return TK_EINVAL;
+  return guard(res->ctx, [&] {
+    set_device(res->ctx);
+    cudaStream_t s = as_stream(stream);
+    TK_CUDA(cudaMemcpyAsync(dst, res->core, sizeof(double) * (size_t)res->r[0] * res->r[1] * res->r[2],
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_eigenvalues(const tk_result* res, int mode, double* dst, int count, int* written) {
+  if (!res || !dst || mode < 0 || mode > 2 || count < 0) return TK_EINVAL;
+  const int k = std::min<int>(count, (int)res->lam[mode].size());
+  std::memcpy(dst, res->lam[mode].data(), sizeof(double) * k);
+  if (written) *written = k;
+  return TK_OK;
+}
+
+int tk_norm2(const tk_result* res, double* normF2) {
+  if (!res || !normF2) return TK_EINVAL;
+  *normF2 = res->normF2;
+  return TK_OK;
+}
+
+int tk_reconstruct(tk_ctx* ctx, const tk_result* res, double* dst, void* stream) {
+  if (!ctx || !res || !dst) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    const int* n = res->n;
+    const int* r = res->r;
+    const size_t w1 = (size_t)n[0] * r[1] * r[2], w2 = (size_t)n[0] * n[1] * r[2];
+    ctx->ws.reserve(carve_bytes<double>(w1) + carve_bytes<double>(w2), s);
+    double* W1 = ctx->ws.take<double>(w1);
+    double* W2 = ctx->ws.take<double>(w2);
+    recon_w2(res->core, r, res->U[0], r[0], res->U[1], r[1], n, W1, W2, s);
+    GemmDesc d{n[0] * n[1], n[2], r[2], 1, W2, 0, r[2], 1, res->U[2], 0, 1, r[2], dst, 0, n[2], 1};
+    gemm_f64(d, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, const tk_grid* grid,
+                 double* out, void* stream) {
+  if (!ctx || !res || !out) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    check_kernel(kernel);
+    check_grid(grid);
+    for (int a = 0; a < 3; ++a)
+      if (grid->n[a] != res->n[a]) fail(TK_EINVAL, "grid does not match the result");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    const int* n = res->n;
+    const int* r = res->r;
+    const size_t N = (size_t)n[0] * n[1] * n[2];
+    const size_t w1 = (size_t)n[0] * r[1] * r[2], w2 = (size_t)n[0] * n[1] * r[2];
+    GemmDesc d{n[0] * n[1], n[2], r[2], 1, nullptr, 0, r[2], 1, res->U[2], 0, 1, r[2], nullptr, 0, n[2], 1};
+    const size_t parts = gemm_err_partials(d);
+    ctx->ws.reserve(carve_bytes<double>(N) + carve_bytes<double>(eval_scratch_doubles(*kernel, *grid) + 1) +
+                        carve_bytes<double>(w1) + carve_bytes<double>(w2) + carve_bytes<double>(parts) +
+                        carve_bytes<double>(8),
+                    s);
+    double* F = ctx->ws.take<double>(N);
+    double* table = ctx->ws.take<double>(eval_scratch_doubles(*kernel, *grid) + 1);
+    double* W1 = ctx->ws.take<double>(w1);
+    double* W2 = ctx->ws.take<double>(w2);
+    double* part = ctx->ws.take<double>(parts);
+    double* sums = ctx->ws.take<double>(8);
+    eval_tensor_f64(*kernel, *grid, F, table, s);
+    recon_w2(res->core, r, res->U[0], r[0], res->U[1], r[1], n, W1, W2, s);
+    d.A = W2;
+    gemm_f64_err(d, F, part, sums, s);
+    double h[2];
+    TK_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    *out = std::sqrt(h[0] / h[1]);
+  });
+}
+
+int tk_eval(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, double* F, void* stream) {
+  if (!ctx || !F) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    check_kernel(kernel);
+    check_grid(grid);
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    ctx->ws.reserve(carve_bytes<double>(eval_scratch_doubles(*kernel, *grid) + 1), s);
+    double* table = ctx->ws.take<double>(eval_scratch_doubles(*kernel, *grid) + 1);
+    eval_tensor_f64(*kernel, *grid, F, table, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_gram(tk_ctx* ctx, const double* F, const int32_t n[3], int mode, int precision, double* G,
+            void* stream) {
+  if (!ctx || !F || !G || !n || mode < 0 || mode > 2) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    int nn[3] = {n[0], n[1], n[2]};
+    for (int a = 0; a < 3; ++a)
+      if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
+    if (precision != TK_FP64) fail(TK_EINVAL, "only TK_FP64 is available in this build");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    ctx->ws.reserve(carve_bytes<double>(gram_f64_scratch_doubles(nn, mode)), s);
+    double* scr = ctx->ws.take<double>(gram_f64_scratch_doubles(nn, mode));
+    gram_f64(F, nn, mode, G, scr, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_sym_eig(tk_ctx* ctx, const double* G, int n, int m, double* lam, double* V, void* stream) {
+  if (!ctx || !G || !lam || !V) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    if (n < 1 || n > kMaxN || m < 1 || m > std::min(n, 96)) fail(TK_EINVAL, "need 1 <= m <= min(n, 96)");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    ctx->ws.reserve(carve_bytes<double>(sym_eig_scratch_doubles(n, m)), s);
+    double* scr = ctx->ws.take<double>(sym_eig_scratch_doubles(n, m));
+    sym_eig_topm(G, n, m, lam, V, nullptr, scr, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* U1, const double* U2,
+                const double* U3, const int32_t r[3], int precision, double* B, void* stream) {
+  if (!ctx || !F || !n || !U1 || !U2 || !U3 || !r || !B) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    int nn[3] = {n[0], n[1], n[2]}, rr[3] = {r[0], r[1], r[2]};
+    for (int a = 0; a < 3; ++a) {
+      if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
+      if (rr[a] < 1 || rr[a] > nn[a]) fail(TK_EINVAL, "need 1 <= r <= n");
+    }
+    if (precision != TK_FP64) fail(TK_EINVAL, "only TK_FP64 is available in this build");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    ctx->ws.reserve(carve_bytes<double>((size_t)nn[0] * nn[1] * rr[2]) +
+                        carve_bytes<double>((size_t)nn[0] * rr[1] * rr[2]),
+                    s);
+    double* T1 = ctx->ws.take<double>((size_t)nn[0] * nn[1] * rr[2]);
+    double* T2 = ctx->ws.take<double>((size_t)nn[0] * rr[1] * rr[2]);
+    ttm_core_f64(F, nn, U1, rr[0], U2, rr[1], U3, rr[2], rr, T1, T2, B, s);
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"

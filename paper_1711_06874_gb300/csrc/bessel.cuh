@@ -1,0 +1,121 @@
+// Modified Bessel function of the second kind K_nu(x), real order nu >= 0,
+// x > 0, in FP64, and the Matern covariance of Sec. 2.2, Eq. (Matern):
+//   C(r) = sigma2 2^(1-nu) / Gamma(nu) z^nu K_nu(z),  z = sqrt(2 nu) r / ell.
+//
+// The paper names K_nu but gives no method.  This file uses, by name:
+//  * Temme's series (N. M. Temme, J. Comput. Phys. 19 (1975) 324) for
+//    K_mu, K_{mu+1} with |mu| <= 1/2 and x <= 1.5;
+//  * for x > 1.5, Temme's representation K_mu(x) = sqrt(pi) (2x)^mu e^-x
+//    U(mu+1/2, 2mu+1, 2x) through the Tricomi function U.  With
+//    U_k = U(mu+1/2+k, 2mu+1, 2x) the contiguous relation of U in its first
+//    parameter gives ((k+1/2)^2 - mu^2) U_{k+1} = 2(k+x) U_k - U_{k-1}; U_k is
+//    its minimal solution, so the ratios U_k/U_{k-1} come from the backward
+//    recurrence (Miller's algorithm), and the sum
+//      sum_k (1/2-mu)_k (1/2+mu)_k / k! U_k = (2x)^(-mu-1/2)
+//    (the Laplace integral of U summed under the integral sign) normalises
+//    them, as in the Thompson-Barnett (Comput. Phys. Commun. 47 (1987) 245)
+//    treatment.  Differentiating the U representation gives
+//      K_{mu+1} / K_mu = (x + mu + 1/2 - (1/4 - mu^2) U_1/U_0) / x;
+//  * forward recurrence K_{m+1} = K_{m-1} + (2m/x) K_m up to nu = N + mu.
+//
+// Gamma_1(mu), Gamma_2(mu), Gamma(1 +- mu) and log Gamma(nu) depend on nu
+// only; the host computes them once per kernel (tk_nu_consts) from the
+// Taylor series log Gamma(1+mu) = -gamma mu + sum_{k>=2} (-1)^k zeta(k) mu^k / k,
+// which has no cancellation as mu -> 0.
+#pragma once
+
+#include <math.h>
+
+#ifdef __CUDACC__
+#define TK_HD __host__ __device__ __forceinline__
+#else
+#define TK_HD inline
+#endif
+
+struct tk_nu_consts {
+  double nu;        // order
+  double mu;        // nu - nord, in [-1/2, 1/2)
+  int nord;         // nu = nord + mu
+  double gam1;      // (1/Gamma(1-mu) - 1/Gamma(1+mu)) / (2 mu)
+  double gam2;      // (1/Gamma(1-mu) + 1/Gamma(1+mu)) / 2
+  double gpmu;      // Gamma(1 + mu)
+  double gmmu;      // Gamma(1 - mu)
+  double mupi_sin;  // mu pi / sin(mu pi)
+  double pref_log;  // (1 - nu) ln 2 - log Gamma(nu)
+};
+
+// K_mu(x) and K_{mu+1}(x), both multiplied by e^x, for |mu| <= 1/2, x > 0.
+TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu, double* kmu1) {
+  const double mu = c.mu;
+  if (x <= 1.5) {
+    // Temme's series (the terms grow like I_mu(x) while K_mu falls like e^-x,
+    // so the series is kept to x <= 1.5 where that cancellation stays small).
+    const double lx = log(2.0 / x);
+    const double sig = mu * lx;
+    const double shs = (fabs(sig) < 1e-8) ? 1.0 + sig * sig / 6.0 : sinh(sig) / sig;
+    double f = c.mupi_sin * (cosh(sig) * c.gam1 + shs * lx * c.gam2);
+    const double e = exp(sig);  // (2/x)^mu
+    double p = 0.5 * e * c.gpmu;
+    double q = 0.5 / e * c.gmmu;
+    double ck = 1.0;
+    const double x2 = 0.25 * x * x;
+    double s0 = f, s1 = p;
+    for (int k = 1; k < 200; ++k) {
+      const double dk = (double)k;
+      f = (dk * f + p + q) / (dk * dk - mu * mu);
+      p /= (dk - mu);
+      q /= (dk + mu);
+      ck *= x2 / dk;
+      const double d0 = ck * f;
+      const double d1 = ck * (p - dk * f);
+      s0 += d0;
+      s1 += d1;
+      if (fabs(d0) < 1e-17 * fabs(s0) && fabs(d1) < 1e-17 * fabs(s1)) break;
+    }
+    const double ex = exp(x);
+    *kmu = s0 * ex;
+    *kmu1 = s1 * (2.0 / x) * ex;
+    return;
+  }
+  // Tricomi-U representation, Miller's backward recurrence.
+  // The backward recurrence reaches 1e-17 with N of about 12 + 180/x terms.
+  const int N = 12 + (int)ceil(180.0 / x);  // at most 132 for x > 1.5
+  const double mu2 = mu * mu;
+  double ratio[136];  // ratio[k] = U_k / U_{k-1}, k = 1..N
+  double rnext = 0.0;
+  for (int k = N; k >= 1; --k) {
+    const double dk = (double)k;
+    rnext = 1.0 / (2.0 * (dk + x) - ((dk + 0.5) * (dk + 0.5) - mu2) * rnext);
+    ratio[k] = rnext;
+  }
+  double s = 1.0, ck = 1.0, pk = 1.0;
+  for (int k = 1; k <= N; ++k) {
+    const double dk = (double)k;
+    ck *= ((dk - 0.5) * (dk - 0.5) - mu2) / dk;
+    pk *= ratio[k];
+    s += ck * pk;
+  }
+  const double k0 = sqrt(3.141592653589793238 / (2.0 * x)) / s;
+  *kmu = k0;
+  *kmu1 = k0 * (x + mu + 0.5 - (0.25 - mu2) * ratio[1]) / x;
+}
+
+// K_nu(x) e^x for the order in c (nu = nord + mu), x > 0.
+TK_HD double tk_bessel_k_scaled(const tk_nu_consts& c, double x) {
+  double km, kp;
+  tk_bessel_k_pair_scaled(c, x, &km, &kp);
+  if (c.nord == 0) return km;
+  for (int k = 1; k < c.nord; ++k) {
+    const double kn = km + (2.0 * (c.mu + (double)k) / x) * kp;
+    km = kp;
+    kp = kn;
+  }
+  return kp;
+}
+
+// Matern covariance at z = sqrt(2 nu) r / ell; C(0) = sigma2 is the limit.
+TK_HD double tk_matern_z(const tk_nu_consts& c, double sigma2, double z) {
+  if (z <= 0.0) return sigma2;
+  const double lp = c.pref_log + c.nu * log(z) - z;
+  return sigma2 * exp(lp) * tk_bessel_k_scaled(c, z);
+}

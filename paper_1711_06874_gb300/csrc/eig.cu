@@ -1,0 +1,401 @@
+// (c) Leading eigenpairs of the Gram matrices and the rank decision, FP64.
+//
+// Sec. 3.2 takes the leading left singular vectors of each unfolding A_(k);
+// they are the leading eigenvectors of G_k = A_(k) A_(k)^T.  Only the first
+// r_k <= rmax are used, and G_k has a geometrically decaying spectrum, so the
+// solver works on an m-dimensional dominant subspace, m = rank cap + margin:
+//   Y = G Omega (Omega from a counter-based hash), Q = qr(Y), repeated once
+//   more with Y = G Q (subspace iteration), then the Rayleigh-Ritz matrix
+//   H = Q^T G Q is diagonalised by cyclic Jacobi rotations (parallel
+//   round-robin ordering, one CTA, shared memory) and the Ritz vectors are
+//   U = Q V_H.  When m equals n the Jacobi method runs on G itself.
+// All arithmetic is FP64.  Eigenvectors get the sign convention: the entry of
+// largest magnitude among the first ceil(n/2) is positive (lowest index on an
+// exact tie).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "tk_internal.h"
+
+namespace tk {
+
+namespace {
+
+constexpr int kMaxM = 96;  // largest Jacobi problem held in shared memory
+
+// ---------------------------------------------------------------------------
+// Counter-based pseudo-random start block: splitmix64 of (seed, index).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double hash_uniform(unsigned long long seed, unsigned long long idx) {
+  unsigned long long z = seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+__global__ void k_random(double* X, long long len, unsigned long long seed) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    X[t] = hash_uniform(seed, (unsigned long long)t);
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of a column-major n x m block Y (ld = n) in one CTA; writes
+// the explicit orthonormal factor Q (column-major, ld = n).  Y is destroyed.
+// ---------------------------------------------------------------------------
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];  // same order in every thread
+  return s;
+}
+
+__global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, int n, int m) {
+  __shared__ double beta[kMaxM];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < m; ++j) {
+    double* y = Y + (long long)j * n;
+    double ss = 0.0;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) ss += y[i] * y[i];
+    const double alpha2 = block_sum(ss, red);
+    const double alpha = sqrt(alpha2);
+    const double x0 = y[j];
+    __syncthreads();
+    if (alpha == 0.0) {
+      if (threadIdx.x == 0) beta[j] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    // v = x + sign(x0) alpha e1, beta = 2 / v^T v
+    const double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
+    const double vtv = alpha2 - x0 * x0 + v0 * v0;
+    if (threadIdx.x == 0) {
+      y[j] = v0;
+      beta[j] = 2.0 / vtv;
+    }
+    __syncthreads();
+    const double bj = beta[j];
+    // trailing columns: one warp per column
+    for (int c = j + 1 + w; c < m; c += nw) {
+      double* yc = Y + (long long)c * n;
+      double d = 0.0;
+      for (int i = j + lane; i < n; i += 32) d += y[i] * yc[i];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const double f = bj * d;
+      for (int i = j + lane; i < n; i += 32) yc[i] -= f * y[i];
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{m-1} [I; 0]
+  for (int c = 0; c < m; ++c)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Q[(long long)c * n + i] = (i == c) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    const double bj = beta[j];
+    const double* v = Y + (long long)j * n;
+    if (bj != 0.0) {
+      for (int c = j + w; c < m; c += nw) {
+        double* qc = Q + (long long)c * n;
+        double d = 0.0;
+        for (int i = j + lane; i < n; i += 32) d += v[i] * qc[i];
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const double f = bj * d;
+        for (int i = j + lane; i < n; i += 32) qc[i] -= f * v[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cyclic Jacobi on a symmetric m x m matrix (row-major, ld = m) in one CTA.
+// Parallel ordering: the circle method pairs the mp (even) indices into
+// mp/2 disjoint planes per step, mp - 1 steps per sweep; each step applies
+// the mp/2 rotations to rows, then to columns and to V.  A rotation is skipped
+// when |a_pq| <= 1e-18 |A|_F; sweeps stop when none is applied.
+// Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Hin, int m, double* lam,
+                                                double* Vout, int* sweeps_out) {
+  extern __shared__ double sm[];
+  const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
+  double* A = sm;
+  double* V = A + mp * mp;
+  double* cs = V + mp * mp;  // c, s per pair
+  int* pp = (int*)(cs + mp);
+  int* qq = pp + mp / 2;
+  int* flag = qq + mp / 2;
+  __shared__ double red[32];
+  for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
+    const int i = e / mp, j = e % mp;
+    A[e] = (i < m && j < m) ? Hin[i * m + j] : 0.0;
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  double fs = 0.0;
+  for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) fs += A[e] * A[e];
+  const double tau = 1e-18 * sqrt(block_sum(fs, red));
+  int sweep = 0;
+  for (sweep = 1; sweep <= 60; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int st = 0; st < mp - 1; ++st) {
+      if (threadIdx.x < mp / 2) {
+        const int k = threadIdx.x;
+        // positions k and mp-1-k; position 0 is fixed, others rotate by st
+        const int pos0 = k, pos1 = mp - 1 - k;
+        const int a = (pos0 == 0) ? 0 : 1 + (pos0 - 1 + st) % (mp - 1);
+        const int b = 1 + (pos1 - 1 + st) % (mp - 1);
+        const int p = min(a, b), q = max(a, b);
+        pp[k] = p;
+        qq[k] = q;
+        const double apq = A[p * mp + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > tau) {
+          const double app = A[p * mp + p], aqq = A[q * mp + q];
+          const double theta = (aqq - app) / (2.0 * apq);
+          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+          *flag = 1;
+        }
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // rows p, q  <-  J^T A
+      for (int e = threadIdx.x; e < (mp / 2) * mp; e += blockDim.x) {
+        const int k = e / mp, col = e % mp;
+        const double s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const double c = cs[2 * k];
+        const int p = pp[k], q = qq[k];
+        const double ap = A[p * mp + col], aq = A[q * mp + col];
+        A[p * mp + col] = c * ap - s * aq;
+        A[q * mp + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q  <-  A J ; V <- V J
+      for (int e = threadIdx.x; e < (mp / 2) * mp; e += blockDim.x) {
+        const int k = e / mp, row = e % mp;
+        const double s = cs[2 * k + 1];
+        if (s == 0.0) continue;
+        const double c = cs[2 * k];
+        const int p = pp[k], q = qq[k];
+        const double ap = A[row * mp + p], aq = A[row * mp + q];
+        A[row * mp + p] = c * ap - s * aq;
+        A[row * mp + q] = s * ap + c * aq;
+        const double vp = V[row * mp + p], vq = V[row * mp + q];
+        V[row * mp + p] = c * vp - s * vq;
+        V[row * mp + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      if (threadIdx.x < mp / 2 && cs[2 * threadIdx.x + 1] != 0.0) {
+        const int p = pp[threadIdx.x], q = qq[threadIdx.x];
+        A[p * mp + q] = 0.0;
+        A[q * mp + p] = 0.0;
+      }
+      __syncthreads();
+    }
+    const int any = *flag;
+    __syncthreads();
+    if (!any) break;
+  }
+  // sort descending by rank counting (ties by index), drop the pad
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double li = A[i * mp + i];
+    int pos = 0;
+    for (int j = 0; j < m; ++j) {
+      const double lj = A[j * mp + j];
+      pos += (lj > li) || (lj == li && j < i);
+    }
+    lam[pos] = li;
+    for (int r = 0; r < m; ++r) Vout[r * m + pos] = V[r * mp + i];
+  }
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// Canonical sign of each column of V (n x m row-major, ld = m).
+__global__ void k_canonical_sign(double* V, int n, int m) {
+  const int col = blockIdx.x;
+  const int half = (n + 1) / 2;
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  double best = -1.0;
+  int idx = 0;
+  for (int i = threadIdx.x; i < half; i += blockDim.x) {
+    const double a = fabs(V[(long long)i * m + col]);
+    if (a > best) {
+      best = a;
+      idx = i;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = idx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double o = bv[threadIdx.x + w];
+      const int oi = bi[threadIdx.x + w];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = V[(long long)bi[0] * m + col] < 0.0;
+  if (flip)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) V[(long long)i * m + col] = -V[(long long)i * m + col];
+}
+
+__global__ void k_trace(const double* G, int n, double* out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0, c = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double x = G[(long long)i * n + i];
+      const double t = s + x;
+      c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    out[0] = s + c;
+  }
+}
+
+__global__ void k_symmetrize(double* H, int m) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e / m, j = e % m;
+    if (i < j) {
+      const double v = 0.5 * (H[i * m + j] + H[j * m + i]);
+      H[i * m + j] = v;
+      H[j * m + i] = v;
+    }
+  }
+}
+
+__global__ void k_copy_rows(const double* G, double* H, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) H[e] = G[e];
+}
+
+// Truncation rule (Task 1, Sec. 2.1, with the HOSVD bound of Sec. 3.2):
+// the smallest r >= 1 whose discarded sum, tail beyond the m computed
+// eigenvalues (trace - their sum) plus the clamped computed ones from r on,
+// summed smallest first, is <= eps^2 |F|^2 / 3; capped at rmax.
+__global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2,
+                       double eps, int rmax, int rfix, double u_eff, int n, int* out) {
+  if (threadIdx.x != 0) return;
+  const double nf = normF2[0];
+  const double thr = eps * eps * nf / 3.0;
+  double sum = 0.0, sc = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double t = sum + lam[i];
+    sc += (fabs(sum) >= fabs(lam[i])) ? (sum - t) + lam[i] : (lam[i] - t) + sum;
+    sum = t;
+  }
+  double extra = trace[0] - (sum + sc);
+  if (!(extra > 0.0) || m >= n) extra = 0.0;
+  int r = m + 1;  // "more than computed"
+  double ts = extra, tc = 0.0;
+  if (ts <= thr) r = m;
+  for (int q = m - 1; q >= 1; --q) {
+    const double x = lam[q] > 0.0 ? lam[q] : 0.0;
+    const double t = ts + x;
+    tc += (fabs(ts) >= x) ? (ts - t) + x : (x - t) + ts;
+    ts = t;
+    if (ts + tc <= thr) r = q;
+  }
+  int flags = 0;
+  if (rfix > 0) {
+    r = rfix;
+  } else if (r > rmax) {
+    r = rmax;
+    flags |= TK_RANK_CAPPED;
+  }
+  if (thr < 10.0 * u_eff * (double)n * nf) flags |= TK_EPS_UNREACHABLE_AT_PRECISION;
+  out[0] = r;
+  out[1] = flags;
+}
+
+}  // namespace
+
+size_t sym_eig_scratch_doubles(int n, int m) {
+  // Omega/Y, Q, W (n x m each), H, V_H (m x m each), trace, sweeps
+  return 3ull * n * m + 2ull * m * m + 64 + (size_t)n * n;
+}
+
+static size_t jacobi_smem(int m) {
+  const int mp = (m + 1) & ~1;
+  return (2ull * mp * mp + mp) * sizeof(double) + (mp + 4) * sizeof(int);
+}
+
+void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
+                  double* scratch, cudaStream_t s) {
+  if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+  static bool attr_set = false;
+  if (!attr_set) {
+    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)jacobi_smem(kMaxM)));
+    attr_set = true;
+  }
+  double* Y = scratch;
+  double* Q = Y + (size_t)n * m;
+  double* W = Q + (size_t)n * m;
+  double* H = W + (size_t)n * m;
+  double* VH = H + (size_t)m * m;
+  double* misc = VH + (size_t)m * m;  // [0] trace, [8..] sweeps
+  k_trace<<<1, 32, 0, s>>>(G, n, trace_out ? trace_out : misc);
+  TK_LAUNCH("k_trace");
+  if (m == n) {
+    // whole matrix: Jacobi on G directly
+    k_copy_rows<<<64, 256, 0, s>>>(G, H, n);
+    TK_LAUNCH("k_copy_rows");
+    k_jacobi<<<1, 512, jacobi_smem(m), s>>>(H, m, lam, VH, (int*)(misc + 8));
+    TK_LAUNCH("k_jacobi");
+    TK_CUDA(cudaMemcpyAsync(V, VH, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToDevice, s));
+  } else {
+    k_random<<<64, 256, 0, s>>>(Y, (long long)n * m, 0x1711068740ull);
+    TK_LAUNCH("k_random");
+    // Y <- G Omega (column-major n x m), two passes of subspace iteration
+    for (int pass = 0; pass < 2; ++pass) {
+      const double* src = (pass == 0) ? Y : Q;
+      double* dst = (pass == 0) ? W : Y;
+      GemmDesc d{n, m, n, 1, G, 0, n, 1, src, 0, 1, n, dst, 0, 1, n};
+      gemm_f64(d, s);
+      if (pass == 0) {
+        TK_CUDA(cudaMemcpyAsync(Y, W, sizeof(double) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
+      }
+      k_householder_qr<<<1, 512, 0, s>>>(Y, Q, n, m);
+      TK_LAUNCH("k_householder_qr");
+    }
+    // W = G Q ; H = Q^T W
+    GemmDesc d1{n, m, n, 1, G, 0, n, 1, Q, 0, 1, n, W, 0, 1, n};
+    gemm_f64(d1, s);
+    GemmDesc d2{m, m, n, 1, Q, 0, n, 1, W, 0, 1, n, H, 0, m, 1};
+    gemm_f64(d2, s);
+    k_symmetrize<<<4, 256, 0, s>>>(H, m);
+    TK_LAUNCH("k_symmetrize");
+    k_jacobi<<<1, 512, jacobi_smem(m), s>>>(H, m, lam, VH, (int*)(misc + 8));
+    TK_LAUNCH("k_jacobi");
+    // Ritz vectors V = Q V_H (row-major n x m)
+    GemmDesc d3{n, m, m, 1, Q, 0, 1, n, VH, 0, m, 1, V, 0, m, 1};
+    gemm_f64(d3, s);
+  }
+  k_canonical_sign<<<m, 256, 0, s>>>(V, n, m);
+  TK_LAUNCH("k_canonical_sign");
+}
+
+void rank_rule(const double* lam, int m, const double* trace, const double* normF2, double eps,
+               int rmax, int rfix, double u_eff, int n, int* rank_out, cudaStream_t s) {
+  k_rank<<<1, 32, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n, rank_out);
+  TK_LAUNCH("k_rank");
+}
+
+}  // namespace tk

@@ -1,0 +1,202 @@
+// (a) Sampling the covariance on the grid: the collocation tensor of Sec. 3.7,
+//     F[i1][i2][i3] = C(x_i1, x_i2, x_i3), with C of Sec. 2.2 (Matern), the
+//     p-Slater function of Eq. (exp_p) or the Gaussian limit.
+//
+// Distinct-value table.  On both grid kinds the coordinate of index i is
+// x_i = h (2i - (n-1)) with h = b/n (cell-centred) or b/(n-1) (vertex), so on
+// a cubic grid with isotropic ell, r^2 = h^2 s with the integer
+// s = a_i^2 + a_j^2 + a_k^2, a = 2i - (n-1).  For even n every a is odd and
+// s = 3 (mod 8); for odd n every a is even and s = 0 (mod 4).  The kernel is
+// therefore evaluated once per admissible s (about n^2 / 3 values instead of
+// n^3), and the tensor is a gather from that table.  Anisotropic ell or a
+// non-cubic grid use the per-point kernel.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "nu_consts.h"
+#include "tk_internal.h"
+
+namespace tk {
+
+KernelDev make_kernel_dev(const tk_kernel& k) {
+  KernelDev d{};
+  d.kind = k.kind;
+  d.sigma2 = k.sigma2;
+  d.p = k.p;
+  for (int a = 0; a < 3; ++a) d.inv_ell[a] = 1.0 / k.ell[a];
+  d.sqrt2nu = (k.kind == TK_MATERN) ? std::sqrt(2.0 * k.nu) : 0.0;
+  d.nuc = make_nu_consts(k.kind == TK_MATERN ? k.nu : 0.5);
+  return d;
+}
+
+GridDev make_grid_dev(const tk_grid& g) {
+  GridDev d{};
+  for (int a = 0; a < 3; ++a) {
+    const int n = g.n[a];
+    const double b = g.b[a];
+    if (g.kind == TK_VERTEX) {
+      d.ax[a].dx = 2.0 * b / (double)(n - 1);
+      d.ax[a].x0 = -b;
+    } else {
+      d.ax[a].dx = 2.0 * b / (double)n;
+      d.ax[a].x0 = -b + 0.5 * d.ax[a].dx;
+    }
+    d.ax[a].n = n;
+  }
+  return d;
+}
+
+bool table_applicable(const tk_kernel& k, const tk_grid& g) {
+  return g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.b[0] == g.b[1] && g.b[1] == g.b[2] &&
+         k.ell[0] == k.ell[1] && k.ell[1] == k.ell[2];
+}
+
+// Covariance as a function of the scaled squared distance r_A^2.
+__device__ __forceinline__ double cov_value(const KernelDev& k, double ra2) {
+  const double ra = sqrt(ra2);
+  if (k.kind == TK_MATERN) return tk_matern_z(k.nuc, k.sigma2, k.sqrt2nu * ra);
+  if (k.kind == TK_SLATER_P) return (ra2 == 0.0) ? k.sigma2 : k.sigma2 * exp(-pow(ra, k.p));
+  return k.sigma2 * exp(-ra2);
+}
+
+static inline long long table_size(int n) {
+  if (n % 2 == 0) return (3LL * (n - 1) * (n - 1) - 3) / 8 + 1;
+  const long long h = (n - 1) / 2;
+  return 3 * h * h + 1;
+}
+
+size_t eval_scratch_doubles(const tk_kernel& k, const tk_grid& g) {
+  return table_applicable(k, g) ? (size_t)table_size(g.n[0]) : 0;
+}
+
+// T[q] = C(h sqrt(s) / ell) with s = 8q + 3 (even n) or s = 4q (odd n).
+__global__ void k_table(KernelDev k, double hs, int even, long long Q, double* T) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
+    T[q] = cov_value(k, hs * hs * s);
+  }
+}
+
+// F[i][j][l] = T[q(s)], one block per (i, j) row, threads along l.
+__global__ void k_gather(const double* __restrict__ T, int n, int even, double* __restrict__ F) {
+  const long long rows = (long long)n * n;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = (int)(row / n), j = (int)(row % n);
+    const int ai = 2 * i - (n - 1), aj = 2 * j - (n - 1);
+    const int sij = ai * ai + aj * aj;
+    double* out = F + row * n;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      const int al = 2 * l - (n - 1);
+      const int s = sij + al * al;
+      out[l] = __ldg(T + (even ? (s - 3) >> 3 : s >> 2));
+    }
+  }
+}
+
+// Per-point evaluation for anisotropic ell or non-cubic grids.
+__global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F) {
+  const int n1 = g.ax[0].n, n2 = g.ax[1].n, n3 = g.ax[2].n;
+  const long long rows = (long long)n1 * n2;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = (int)(row / n2), j = (int)(row % n2);
+    const double u = (g.ax[0].x0 + i * g.ax[0].dx) * k.inv_ell[0];
+    const double v = (g.ax[1].x0 + j * g.ax[1].dx) * k.inv_ell[1];
+    const double uv = u * u + v * v;
+    for (int l = threadIdx.x; l < n3; l += blockDim.x) {
+      const double w = (g.ax[2].x0 + l * g.ax[2].dx) * k.inv_ell[2];
+      F[row * n3 + l] = cov_value(k, uv + w * w);
+    }
+  }
+}
+
+void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* table,
+                     cudaStream_t s) {
+  const KernelDev k = make_kernel_dev(kh);
+  const GridDev g = make_grid_dev(gh);
+  if (table_applicable(kh, gh)) {
+    const int n = gh.n[0];
+    const long long Q = table_size(n);
+    const double h = (gh.kind == TK_VERTEX) ? gh.b[0] / (double)(n - 1) : gh.b[0] / (double)n;
+    const int even = (n % 2 == 0);
+    const int tb = 128;
+    const long long nb = (Q + tb - 1) / tb;
+    k_table<<<(unsigned)(nb < 4096 ? nb : 4096), tb, 0, s>>>(k, h * k.inv_ell[0], even, Q, table);
+    TK_LAUNCH("k_table");
+    const long long rows = (long long)n * n;
+    k_gather<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), n < 256 ? 128 : 256, 0, s>>>(
+        table, n, even, F);
+    TK_LAUNCH("k_gather");
+  } else {
+    const long long rows = (long long)gh.n[0] * gh.n[1];
+    k_eval_general<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), 128, 0, s>>>(k, g, F);
+    TK_LAUNCH("k_eval_general");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// |x|^2: each thread keeps a Neumaier pair over a fixed slice; blocks reduce
+// in a fixed tree; one block sums the block partials in index order.  The
+// result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+static constexpr int kNormBlocks = 608;  // 4 x 152 SMs
+static constexpr int kNormThreads = 256;
+
+size_t norm2_scratch_doubles(size_t) { return 2 * kNormBlocks; }
+
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x))
+    c += (s - t) + x;
+  else
+    c += (x - t) + s;
+  s = t;
+}
+
+__global__ void k_norm2_partial(const double* __restrict__ x, long long len, double* part) {
+  double s = 0.0, c = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    neumaier(s, c, v * v);
+  }
+  __shared__ double ss[kNormThreads], sc[kNormThreads];
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a = ss[threadIdx.x], ac = sc[threadIdx.x];
+      neumaier(a, ac, ss[threadIdx.x + w]);
+      ac += sc[threadIdx.x + w];
+      ss[threadIdx.x] = a;
+      sc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ss[0];
+    part[2 * blockIdx.x + 1] = sc[0];
+  }
+}
+
+__global__ void k_norm2_final(const double* part, int nparts, double* out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+      neumaier(s, c, part[2 * b]);
+      c += part[2 * b + 1];
+    }
+    out[0] = s + c;
+  }
+}
+
+void norm2_f64(const double* x, size_t len, double* out_dev, double* scratch, cudaStream_t s) {
+  k_norm2_partial<<<kNormBlocks, kNormThreads, 0, s>>>(x, (long long)len, scratch);
+  TK_LAUNCH("k_norm2_partial");
+  k_norm2_final<<<1, 32, 0, s>>>(scratch, kNormBlocks, out_dev);
+  TK_LAUNCH("k_norm2_final");
+}
+
+}  // namespace tk

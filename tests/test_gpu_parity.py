@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Every step of the hot path is compared element by element on the same seeded
+inputs, at sizes the oracle finishes in seconds that span several 64-wide
+tiles and a ragged tail; the whole solve is compared at the small Slater
+configuration and at ragged anisotropic shapes.  Tolerances (FP64 path):
+  tensor      |F - F_or| <= 5e-14 |F|_max     (K_nu to ~2e-15, grid rounding)
+  Gram        |G - G_or| <= 1e-13 |G|_max     (FP64 sums of n^2 terms)
+  eigen       |lam - lam_or| <= 1e-13 lam_1; principal angles <= 1e-10 on the
+              leading columns whose gaps exceed 1e-6 lam_1
+  core/recon  |B| to 1e-12 |F|; |X - X_or| <= max(1e-12, 100 u / eps) |F|
+  ranks       equal, except when the oracle's discarded sum lies within a
+              factor 1 +- 0.5 of the threshold (then +-1), or both are capped.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests._util import U64, near_threshold, principal_sines, separated_prefix
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_06874_gb300 import binding
+
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def wl():
+    from paper_1711_06874_gb300 import workloads
+
+    return workloads
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------------------
+# (a) sampling
+# ---------------------------------------------------------------------------
+EVAL_CASES = [
+    dict(kind=0, nu=1.2, ell=0.2, n=64),                      # table path, even n
+    dict(kind=0, nu=0.5, ell=0.3, n=33),                      # table path, odd n
+    dict(kind=0, nu=2.5, ell=0.1, n=40, grid=1),              # vertex grid, even n
+    dict(kind=0, nu=0.3, ell=0.05, n=31, grid=1),             # vertex grid, odd n (r = 0 at centre)
+    dict(kind=0, nu=1.7, ell=(0.2, 0.35, 0.5), n=(20, 24, 28)),  # general per-point path
+    dict(kind=1, p=0.2, ell=1.0, n=24, b=5.0, grid=1),        # p-Slater
+    dict(kind=2, ell=0.4, n=(17, 9, 30), b=(1.0, 0.5, 2.0)),  # Gaussian, non-cubic
+]
+
+
+@pytest.mark.parametrize("case", EVAL_CASES)
+def test_eval_matches_oracle(ctx, orc, wl, case):
+    prob = wl.problem(**case)
+    F = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ctx.eval(prob, F)
+    ref = orc.tensor(wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc))
+    got = F.cpu().numpy()
+    assert np.abs(got - ref).max() <= 5e-14 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# (b) Gram, all three unfoldings, ragged tiles
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(70, 45, 33), (64, 64, 64), (5, 130, 9), (2, 2, 2)])
+def test_gram_fp64_matches_oracle(ctx, orc, shape):
+    rng = np.random.default_rng(17)
+    Fh = rng.random(shape)
+    F = _dev(Fh)
+    for mode in range(3):
+        m = shape[mode]
+        G = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        ctx.gram(F, mode, G)
+        ref = orc.gram(Fh, mode)
+        assert np.abs(G.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max(), mode
+
+
+# ---------------------------------------------------------------------------
+# (c) eigenpairs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(64, 28), (130, 40), (48, 48), (97, 96), (9, 1)])
+def test_sym_eig_matches_oracle(ctx, orc, wl, n, m):
+    prob = wl.problem(0, nu=0.9, ell=0.25, n=(n, 20, 24))
+    Fh = orc.tensor(wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc))
+    Gh = orc.gram(Fh, 0)
+    lam_o, V_o, _ = orc.sym_eig(Gh)
+    G = _dev(Gh)
+    lam = torch.empty(m, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, m), dtype=torch.float64, device="cuda")
+    ctx.sym_eig(G, m, lam, V)
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    np.testing.assert_allclose(lam, lam_o[:m], rtol=0, atol=1e-13 * lam_o[0])
+    np.testing.assert_allclose(V.T @ V, np.eye(m), atol=1e-13)
+    rp = min(separated_prefix(lam_o[:m]), m - 1 if m < n else m)
+    for j in range(1, rp + 1):
+        assert principal_sines(V_o[:, :j], V[:, :j]).max() <= 1e-10, j
+    # canonical sign on separated columns
+    for j in range(rp):
+        assert np.dot(V[:, j], V_o[:, j]) > 0
+
+
+# ---------------------------------------------------------------------------
+# (d) core by chained TTMs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,r", [((40, 48, 56), (5, 7, 9)), ((64, 64, 64), (11, 11, 11)),
+                                     ((3, 70, 5), (1, 2, 5))])
+def test_ttm_core_matches_oracle(ctx, orc, shape, r):
+    rng = np.random.default_rng(5)
+    Fh = rng.standard_normal(shape)
+    U = [np.linalg.qr(rng.standard_normal((n, n)))[0][:, :k].copy() for n, k in zip(shape, r)]
+    ref = orc.core(Fh, U, r)
+    B = torch.empty(r, dtype=torch.float64, device="cuda")
+    ctx.ttm_core(_dev(Fh), [_dev(u) for u in U], B)
+    assert np.abs(B.cpu().numpy() - ref).max() <= 1e-13 * np.abs(Fh).max() * math.sqrt(Fh.size)
+
+
+# ---------------------------------------------------------------------------
+# Whole solve against the oracle
+# ---------------------------------------------------------------------------
+def _compare_solution(orc, wl, res, prob, precision_u=U64):
+    kern, grid = wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc)
+    ref = orc.hosvd(kern, grid, prob.eps, rmax=list(prob.rmax))
+    ranks, flags = res.ranks
+    for a in range(3):
+        if ranks[a] != ref["ranks"][a]:
+            both_capped = ranks[a] == prob.rmax[a] and ref["ranks"][a] == prob.rmax[a]
+            ok = (abs(ranks[a] - ref["ranks"][a]) <= 1
+                  and near_threshold(ref["lam"][a], ref["normF2"], prob.eps, ref["ranks"][a]))
+            assert both_capped or ok or (ref["flags"][a] & 2 and flags[a] & 2), (a, ranks, ref["ranks"])
+    F = orc.tensor(kern, grid)
+    nF = math.sqrt(ref["normF2"])
+    assert abs(res.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
+    U = [res.factor(a) for a in range(3)]
+    B = res.core()
+    for a in range(3):
+        np.testing.assert_allclose(U[a].T @ U[a], np.eye(ranks[a]), atol=1e-13)
+    # core norm
+    if ranks == ref["ranks"]:
+        assert abs(np.linalg.norm(B) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
+        X = orc.reconstruct(B, U, prob.n)
+        Xo = orc.reconstruct(ref["core"], ref["U"], prob.n)
+        tol = max(1e-12, 100 * precision_u / max(prob.eps, 1e-300))
+        assert np.linalg.norm(X - Xo) <= tol * nF
+        for a in range(3):
+            rp = min(separated_prefix(ref["lam"][a][: ranks[a] + 1]), ranks[a])
+            if rp:
+                assert principal_sines(ref["U"][a][:, :rp], U[a][:, :rp]).max() <= 1e-10
+    # error: GPU rel_error (direct subtraction on the device) vs the oracle's on the GPU factors
+    e_gpu = res.rel_error()
+    e_or = orc.rel_error(F, orc.reconstruct(B, U, prob.n))
+    assert abs(e_gpu - e_or) <= 1e-10 * e_or + 1e-15
+    if not any(flags):
+        assert e_gpu <= prob.eps * (1 + 1e-6)
+    return ref, e_gpu
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
+def test_tucker_slater_n64_matches_oracle(ctx, orc, wl, eps):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.slater_n64(eps)
+    res = ctx.tucker(prob, precision=binding.TK_FP64)
+    ref, e = _compare_solution(orc, wl, res, prob)
+    if eps >= 1e-6:
+        assert res.ranks[0] == ref["ranks"]
+        assert e <= 2 * ref["rel_error"]
+
+
+@pytest.mark.parametrize("case", [
+    dict(nu=1.2, ell=(0.25, 0.3, 0.4), n=(40, 48, 70), eps=1e-6, rmax=24),
+    dict(nu=2.5, ell=0.15, n=(33, 33, 33), eps=1e-5, rmax=16, grid=1),
+    dict(nu=0.7, ell=0.2, n=(66, 66, 66), eps=1e-6, rmax=30),
+])
+def test_tucker_ragged_matches_oracle(ctx, orc, wl, case):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, **case)
+    for shortcut in (True, False):
+        res = ctx.tucker(prob, precision=binding.TK_FP64, shortcut=shortcut)
+        _compare_solution(orc, wl, res, prob)
+
+
+def test_gaussian_rank_one_on_gpu(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(2, ell=0.4, n=48, eps=1e-6, rmax=8)
+    res = ctx.tucker(prob, precision=binding.TK_FP64)
+    assert res.ranks[0] == [1, 1, 1]
+    assert res.rel_error() <= 1e-13
+
+
+def test_full_rank_is_exact_on_gpu(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, nu=0.5, ell=0.3, n=(12, 10, 14), eps=0.0, rmax=14)
+    res = ctx.tucker(prob, precision=binding.TK_FP64, rfix=(12, 10, 14))
+    assert res.ranks[0] == [12, 10, 14]
+    assert res.rel_error() <= 1e-13
+    assert abs(float(np.sum(res.core() ** 2)) - res.norm2) <= 1e-13 * res.norm2
+
+
+def test_reconstruct_matches_oracle(ctx, orc, wl):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, nu=1.2, ell=0.2, n=(20, 30, 40), eps=1e-5, rmax=12)
+    res = ctx.tucker(prob, precision=binding.TK_FP64)
+    X = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    res.reconstruct(X)
+    U = [res.factor(a) for a in range(3)]
+    ref = orc.reconstruct(res.core(), U, prob.n)
+    assert np.abs(X.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_invalid_arguments_are_rejected(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    bad = [wl.problem(0, nu=0.0), wl.problem(0, ell=-1.0), wl.problem(0, n=1), wl.problem(0, eps=-1.0),
+           wl.problem(0, rmax=0), wl.problem(0, rmax=89), wl.problem(0, n=2000)]
+    for prob in bad:
+        with pytest.raises(binding.TuckerError) as ei:
+            ctx.tucker(prob, precision=binding.TK_FP64)
+        assert ei.value.status == binding.TK_EINVAL
