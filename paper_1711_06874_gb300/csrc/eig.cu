@@ -313,8 +313,9 @@ __global__ void k_rank(const double* lam, int m, const double* trace, const doub
     if (ts + tc <= thr) r = q;
   }
   int flags = 0;
+  if (r > m) r = m + 1;
   if (rfix > 0) {
-    r = rfix;
+    r = rfix < m ? rfix : m;
   } else if (r > rmax) {
     r = rmax;
     flags |= TK_RANK_CAPPED;
