@@ -62,7 +62,6 @@ namespace {
 
 constexpr int kMaxN = 1024;
 constexpr int kMaxRank = 88;
-constexpr int kMargin = 8;  // extra subspace columns beyond the rank cap
 
 template <class Fn>
 int guard(tk_ctx* ctx, Fn&& fn) {
@@ -117,10 +116,10 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 void set_device(tk_ctx* ctx) { TK_CUDA(cudaSetDevice(ctx->device)); }
 
-// Subspace size for mode a: rank cap (or fixed rank) plus a margin, at most n.
+// Eigenpairs computed for mode a: the rank cap (or fixed rank), at most n.
+// The eigensolver adds its own margin columns to the subspace.
 int subspace_m(const tk_opts& o, int n, int a) {
-  const int want = std::max(o.rmax[a], o.rfix[a]) + kMargin;
-  return std::min(std::min(want, n), 96);
+  return std::min(std::max(o.rmax[a], o.rfix[a]), n);
 }
 
 bool shortcut_ok(const tk_kernel& k, const tk_grid& g, const tk_opts& o) {

@@ -327,9 +327,16 @@ __global__ void k_rank(const double* lam, int m, const double* trace, const doub
 
 }  // namespace
 
+// The subspace carries kMargin columns beyond the m requested pairs (up to
+// n and kMaxM) so that the m leading Ritz pairs converge.
+constexpr int kMargin = 8;
+
+static int subspace_cols(int n, int m) { return std::min(std::min(n, kMaxM), m + kMargin); }
+
 size_t sym_eig_scratch_doubles(int n, int m) {
-  // Omega/Y, Q, W (n x m each), H, V_H (m x m each), trace, sweeps
-  return 3ull * n * m + 2ull * m * m + 64 + (size_t)n * n;
+  const int ms = subspace_cols(n, m);
+  // Omega/Y, Q, W (n x ms each), H, V_H (ms x ms each), Ritz values, misc
+  return 3ull * n * ms + 2ull * ms * ms + ms + 64 + (size_t)n * n;
 }
 
 static size_t jacobi_smem(int m) {
@@ -346,49 +353,51 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
                                  (int)jacobi_smem(kMaxM)));
     attr_set = true;
   }
+  const int ms = subspace_cols(n, m);
   double* Y = scratch;
-  double* Q = Y + (size_t)n * m;
-  double* W = Q + (size_t)n * m;
-  double* H = W + (size_t)n * m;
-  double* VH = H + (size_t)m * m;
-  double* misc = VH + (size_t)m * m;  // [0] trace, [8..] sweeps
+  double* Q = Y + (size_t)n * ms;
+  double* W = Q + (size_t)n * ms;
+  double* H = W + (size_t)n * ms;
+  double* VH = H + (size_t)ms * ms;
+  double* lsub = VH + (size_t)ms * ms;
+  double* misc = lsub + ms;  // [0] trace, [8..] sweeps
   k_trace<<<1, 32, 0, s>>>(G, n, trace_out ? trace_out : misc);
   TK_LAUNCH("k_trace");
-  if (m == n) {
+  if (ms == n) {
     // whole matrix: Jacobi on G directly
     k_copy_rows<<<64, 256, 0, s>>>(G, H, n);
     TK_LAUNCH("k_copy_rows");
-    k_jacobi<<<1, 512, jacobi_smem(m), s>>>(H, m, lam, VH, (int*)(misc + 8));
+    k_jacobi<<<1, 512, jacobi_smem(n), s>>>(H, n, lsub, VH, (int*)(misc + 8));
     TK_LAUNCH("k_jacobi");
-    TK_CUDA(cudaMemcpyAsync(V, VH, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToDevice, s));
+    // first m columns of V_H (n x n) into V (n x m)
+    TK_CUDA(cudaMemcpy2DAsync(V, sizeof(double) * m, VH, sizeof(double) * n, sizeof(double) * m, n,
+                              cudaMemcpyDeviceToDevice, s));
   } else {
-    k_random<<<64, 256, 0, s>>>(Y, (long long)n * m, 0x1711068740ull);
+    k_random<<<64, 256, 0, s>>>(Y, (long long)n * ms, 0x1711068740ull);
     TK_LAUNCH("k_random");
-    // Y <- G Omega (column-major n x m), two passes of subspace iteration
+    // two passes of subspace iteration on column-major n x ms blocks
     for (int pass = 0; pass < 2; ++pass) {
       const double* src = (pass == 0) ? Y : Q;
-      double* dst = (pass == 0) ? W : Y;
-      GemmDesc d{n, m, n, 1, G, 0, n, 1, src, 0, 1, n, dst, 0, 1, n};
+      GemmDesc d{n, ms, n, 1, G, 0, n, 1, src, 0, 1, n, W, 0, 1, n};
       gemm_f64(d, s);
-      if (pass == 0) {
-        TK_CUDA(cudaMemcpyAsync(Y, W, sizeof(double) * (size_t)n * m, cudaMemcpyDeviceToDevice, s));
-      }
-      k_householder_qr<<<1, 512, 0, s>>>(Y, Q, n, m);
+      TK_CUDA(cudaMemcpyAsync(Y, W, sizeof(double) * (size_t)n * ms, cudaMemcpyDeviceToDevice, s));
+      k_householder_qr<<<1, 512, 0, s>>>(Y, Q, n, ms);
       TK_LAUNCH("k_householder_qr");
     }
     // W = G Q ; H = Q^T W
-    GemmDesc d1{n, m, n, 1, G, 0, n, 1, Q, 0, 1, n, W, 0, 1, n};
+    GemmDesc d1{n, ms, n, 1, G, 0, n, 1, Q, 0, 1, n, W, 0, 1, n};
     gemm_f64(d1, s);
-    GemmDesc d2{m, m, n, 1, Q, 0, n, 1, W, 0, 1, n, H, 0, m, 1};
+    GemmDesc d2{ms, ms, n, 1, Q, 0, n, 1, W, 0, 1, n, H, 0, ms, 1};
     gemm_f64(d2, s);
-    k_symmetrize<<<4, 256, 0, s>>>(H, m);
+    k_symmetrize<<<4, 256, 0, s>>>(H, ms);
     TK_LAUNCH("k_symmetrize");
-    k_jacobi<<<1, 512, jacobi_smem(m), s>>>(H, m, lam, VH, (int*)(misc + 8));
+    k_jacobi<<<1, 512, jacobi_smem(ms), s>>>(H, ms, lsub, VH, (int*)(misc + 8));
     TK_LAUNCH("k_jacobi");
-    // Ritz vectors V = Q V_H (row-major n x m)
-    GemmDesc d3{n, m, m, 1, Q, 0, 1, n, VH, 0, m, 1, V, 0, m, 1};
+    // leading m Ritz vectors V = Q V_H[:, :m] (row-major n x m)
+    GemmDesc d3{n, m, ms, 1, Q, 0, 1, n, VH, 0, ms, 1, V, 0, m, 1};
     gemm_f64(d3, s);
   }
+  TK_CUDA(cudaMemcpyAsync(lam, lsub, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   k_canonical_sign<<<m, 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }
