@@ -164,6 +164,29 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
                 const double* U2, const double* U3, const int32_t r[3], int precision, double* B,
                 void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Diagnostics (no counterpart in the paper): per-stage device time and the
+ * number of kernels the library launched.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  TK_STAGE_EVAL = 0,  /* sampling F (table + gather, or per point) */
+  TK_STAGE_NORM = 1,  /* |F|^2 */
+  TK_STAGE_GRAM = 2,  /* Gram matrices, all modes */
+  TK_STAGE_EIG = 3,   /* eigenpairs, all modes */
+  TK_STAGE_RANK = 4,  /* rank rule and factor extraction */
+  TK_STAGE_CORE = 5,  /* TTM chain */
+  TK_STAGE_ERROR = 6, /* tk_rel_error */
+  TK_NSTAGES = 7
+} tk_stage;
+/* on = 1 starts recording CUDA events around every stage of later calls on
+ * this context and zeroes the totals; on = 0 stops. */
+int tk_profile_enable(tk_ctx* ctx, int on);
+/* Accumulated device milliseconds and call counts per stage (host arrays of
+ * TK_NSTAGES), for the calls made since profiling was enabled. */
+int tk_profile_read(tk_ctx* ctx, double ms[7], int64_t calls[7]);
+/* Kernels launched by the library in this process so far. */
+uint64_t tk_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

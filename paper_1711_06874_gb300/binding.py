@@ -65,7 +65,12 @@ SIGNATURES = {
     "tk_sym_eig": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _vp, _vp, _vp]),
     "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
                                _vp, _vp]),
+    "tk_profile_enable": (_c.c_int, [_vp, _c.c_int]),
+    "tk_profile_read": (_c.c_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_c.c_int64)]),
+    "tk_kernel_launches": (_c.c_uint64, []),
 }
+
+STAGES = ["eval", "norm", "gram", "eig", "rank", "core", "error"]
 
 _lock = threading.Lock()
 _lib = None
@@ -160,6 +165,20 @@ class Context:
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
         return Result(self, out, prob)
+
+    # ---- diagnostics ----------------------------------------------------------
+    def profile(self, on: bool = True):
+        _check(self.lib.tk_profile_enable(self.ptr, 1 if on else 0), self.ptr)
+
+    def profile_read(self) -> dict:
+        ms = (_dbl * 7)()
+        calls = (_c.c_int64 * 7)()
+        _check(self.lib.tk_profile_read(self.ptr, ms, calls), self.ptr)
+        return {name: (ms[i], int(calls[i])) for i, name in enumerate(STAGES)}
+
+    @staticmethod
+    def kernel_launches() -> int:
+        return int(load().tk_kernel_launches())
 
     # ---- stage entry points (device tensors in and out) --------------------
     def eval(self, prob: workloads.Problem, F, stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,60 @@ void Workspace::reserve(size_t need, cudaStream_t s) {
   } else {
     bytes = want;
   }
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+void Profiler::begin(int stage, cudaStream_t s) {
+  if (!on) return;
+  Pending p{stage, get(), get()};
+  check_cuda(cudaEventRecord(p.a, s), "cudaEventRecord");
+  pending.push_back(p);
+}
+
+void Profiler::end(cudaStream_t s) {
+  if (!on || pending.empty()) return;
+  check_cuda(cudaEventRecord(pending.back().b, s), "cudaEventRecord");
+}
+
+void Profiler::collect() {
+  for (auto& p : pending) {
+    float ms_ = 0.f;
+    if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
+      ms[p.stage] += ms_;
+      calls[p.stage] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+void Profiler::reset() {
+  for (int i = 0; i < TK_NSTAGES; ++i) {
+    ms[i] = 0.0;
+    calls[i] = 0;
+  }
+}
+
+void Profiler::release() {
+  collect();
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
 }
 
 void Workspace::release() {
@@ -220,6 +275,7 @@ void tk_destroy(tk_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  ctx->prof.release();
   ctx->ws.release();
   delete ctx;
 }
@@ -259,36 +315,54 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     }
     int rcap[3];
     for (int a = 0; a < 3; ++a) rcap[a] = std::max(o.rmax[a], o.rfix[a]);
-    size_t need = carve_bytes<double>(N) + carve_bytes<double>(eval_scratch_doubles(*kernel, *grid)) +
-                  carve_bytes<double>(norm2_scratch_doubles(N)) + carve_bytes<double>(gram_scr) +
-                  carve_bytes<double>(eig_scr) + carve_bytes<double>(64) + carve_bytes<int>(64) +
-                  carve_bytes<double>(ttm_scratch_doubles(n, rcap));
+    // workspace layout: one list of sizes drives both the reservation and the carves
+    const size_t sz[8] = {N,
+                          std::max<size_t>(1, eval_scratch_doubles(*kernel, *grid)),
+                          norm2_scratch_doubles(N),
+                          std::max<size_t>(1, gram_scr),
+                          eig_scr,
+                          64,
+                          ttm_scratch_doubles(n, rcap),
+                          0};
+    size_t need = carve_bytes<int>(64);
+    for (int i = 0; i < 7; ++i) need += carve_bytes<double>(sz[i]);
     for (int a = 0; a < 3; ++a)
       need += carve_bytes<double>((size_t)n[a] * n[a]) + carve_bytes<double>((size_t)n[a] * m[a]) +
               carve_bytes<double>(m[a]);
     ctx->ws.reserve(need, s);
     Workspace& ws = ctx->ws;
-    double* F = ws.take<double>(N);
-    double* table = ws.take<double>(std::max<size_t>(1, eval_scratch_doubles(*kernel, *grid)));
-    double* nscr = ws.take<double>(norm2_scratch_doubles(N));
-    double* gscr = ws.take<double>(std::max<size_t>(1, gram_scr));
-    double* escr = ws.take<double>(eig_scr);
-    double* small = ws.take<double>(64);  // [0] |F|^2, [1..3] traces
+    double* F = ws.take<double>(sz[0]);
+    double* table = ws.take<double>(sz[1]);
+    double* nscr = ws.take<double>(sz[2]);
+    double* gscr = ws.take<double>(sz[3]);
+    double* escr = ws.take<double>(sz[4]);
+    double* small = ws.take<double>(sz[5]);  // [0] |F|^2, [1..3] traces
+    double* ttm = ws.take<double>(sz[6]);
     int* ranks_dev = ws.take<int>(64);
-    double* ttm = ws.take<double>(ttm_scratch_doubles(n, rcap));
     double *G[3], *V[3], *lam[3];
     for (int a = 0; a < 3; ++a) {
       G[a] = ws.take<double>((size_t)n[a] * n[a]);
       V[a] = ws.take<double>((size_t)n[a] * m[a]);
       lam[a] = ws.take<double>(m[a]);
     }
+    Profiler& pf = ctx->prof;
+    pf.begin(TK_STAGE_EVAL, s);
     eval_tensor_f64(*kernel, *grid, F, table, s);
+    pf.end(s);
+    pf.begin(TK_STAGE_NORM, s);
     norm2_f64(F, N, small, nscr, s);
+    pf.end(s);
     for (int a = 0; a < nmodes; ++a) {
+      pf.begin(TK_STAGE_GRAM, s);
       gram_f64(F, n, a, G[a], gscr, s);
+      pf.end(s);
+      pf.begin(TK_STAGE_EIG, s);
       sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
+      pf.end(s);
+      pf.begin(TK_STAGE_RANK, s);
       rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], std::ldexp(1.0, -53),
                 n[a], ranks_dev + 2 * a, s);
+      pf.end(s);
     }
     int hr[6];
     double hsmall[4];
@@ -323,8 +397,11 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     TK_CUDA(cudaMalloc(&res->core, sizeof(double) * (size_t)r[0] * r[1] * r[2]));
     double* T1 = ttm;
     double* T2 = ttm + (size_t)n[0] * n[1] * r[2];
+    pf.begin(TK_STAGE_CORE, s);
     ttm_core_f64(F, n, res->U[0], r[0], res->U[1], r[1], res->U[2], r[2], r, T1, T2, res->core, s);
+    pf.end(s);
     TK_CUDA(cudaStreamSynchronize(s));
+    pf.collect();
   });
   if (rc != TK_OK) {
     if (res) tk_result_free(res);
@@ -425,13 +502,16 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
     double* W2 = ctx->ws.take<double>(w2);
     double* part = ctx->ws.take<double>(parts);
     double* sums = ctx->ws.take<double>(8);
+    ctx->prof.begin(TK_STAGE_ERROR, s);
     eval_tensor_f64(*kernel, *grid, F, table, s);
     recon_w2(res->core, r, res->U[0], r[0], res->U[1], r[1], n, W1, W2, s);
     d.A = W2;
     gemm_f64_err(d, F, part, sums, s);
+    ctx->prof.end(s);
     double h[2];
     TK_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
+    ctx->prof.collect();
     *out = std::sqrt(h[0] / h[1]);
   });
 }
@@ -505,5 +585,28 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
     TK_CUDA(cudaStreamSynchronize(s));
   });
 }
+
+int tk_profile_enable(tk_ctx* ctx, int on) {
+  if (!ctx) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    set_device(ctx);
+    ctx->prof.collect();
+    ctx->prof.reset();
+    ctx->prof.on = (on != 0);
+  });
+}
+
+int tk_profile_read(tk_ctx* ctx, double ms[7], int64_t calls[7]) {
+  if (!ctx || !ms || !calls) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  for (int i = 0; i < TK_NSTAGES; ++i) {
+    ms[i] = ctx->prof.ms[i];
+    calls[i] = ctx->prof.calls[i];
+  }
+  return TK_OK;
+}
+
+uint64_t tk_kernel_launches(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -21,8 +21,10 @@ struct Error {
 
 [[noreturn]] void fail(int status, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+// Counts the library's kernel launches (diagnostics, tk_kernel_launches).
+void count_launch();
 #define TK_CUDA(call) ::tk::check_cuda((call), #call)
-#define TK_LAUNCH(what) ::tk::check_cuda(cudaGetLastError(), what)
+#define TK_LAUNCH(what) (::tk::count_launch(), ::tk::check_cuda(cudaGetLastError(), what))
 
 // Device workspace owned by a context: grows, never shrinks until destroyed.
 struct Workspace {
@@ -120,12 +122,35 @@ void rank_rule(const double* lam, int m, const double* trace, const double* norm
 
 }  // namespace tk
 
+namespace tk {
+// Per-stage device time of a context, from CUDA events recorded around each
+// stage when profiling is on (tk_profile_enable).
+struct Profiler {
+  bool on = false;
+  double ms[TK_NSTAGES] = {};
+  long long calls[TK_NSTAGES] = {};
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void begin(int stage, cudaStream_t s);
+  void end(cudaStream_t s);
+  void collect();  // after the stream is synchronised
+  void reset();
+  void release();
+};
+}  // namespace tk
+
 struct tk_ctx {
   int device = 0;
   std::mutex mu;
   tk::Workspace ws;
   std::string last_error;
   int sm_count = 0;
+  tk::Profiler prof;
 };
 
 struct tk_result {

@@ -231,3 +231,35 @@ def test_invalid_arguments_are_rejected(ctx, wl):
         with pytest.raises(binding.TuckerError) as ei:
             ctx.tucker(prob, precision=binding.TK_FP64)
         assert ei.value.status == binding.TK_EINVAL
+
+
+def test_fresh_context_per_shape(orc, wl):
+    """Workspace sizing on a new context (no larger earlier reservation to hide behind)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_06874_gb300 import binding
+
+    for case in [dict(nu=1.2, ell=(0.25, 0.3, 0.35), n=(24, 28, 32), eps=1e-6, rmax=16),
+                 dict(nu=0.5, ell=0.3, n=(16, 16, 16), eps=1e-4, rmax=8)]:
+        c = binding.Context(0)
+        prob = wl.problem(0, **case)
+        res = c.tucker(prob, precision=binding.TK_FP64)
+        ref = orc.hosvd(wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc), prob.eps, rmax=list(prob.rmax))
+        assert res.ranks[0] == ref["ranks"]
+        res.free()
+        c.close()
+
+
+def test_profile_and_launch_counter(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, nu=1.2, ell=0.2, n=32, eps=1e-6, rmax=12)
+    l0 = binding.Context.kernel_launches()
+    ctx.profile(True)
+    res = ctx.tucker(prob, precision=binding.TK_FP64)
+    res.rel_error()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    assert binding.Context.kernel_launches() > l0 + 5
+    for stage in ("eval", "norm", "gram", "eig", "rank", "core", "error"):
+        assert prof[stage][1] >= 1 and prof[stage][0] > 0.0, stage
