@@ -164,6 +164,23 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
                 const double* U2, const double* U3, const int32_t r[3], int precision, double* B,
                 void* stream);
 
+/* Allocation-free variant of tk_gram with precision TK_FP64 (no counterpart
+ * in the paper).  Some callers cannot allocate device memory: code embedded in
+ * a host application whose own allocator has reserved the GPU's memory,
+ * real-time loops that must not pay cudaMalloc's latency or its implicit
+ * synchronisation, and plugins that are only handed pointers.  This entry
+ * point takes no context, performs no cudaMalloc, cudaFree or other
+ * allocation, and keeps its split-K partial sums in a fixed 8 MiB device
+ * array that every GPU loading this library holds until the process exits;
+ * n[a] must lie in [1, 1024] (TK_EINVAL otherwise), which always fits.
+ * F (device, n[0] n[1] n[2] FP64) and G (device, n_mode x n_mode FP64) are the
+ * caller's; the result equals tk_gram's.  Runs on the current CUDA device and
+ * only enqueues on `stream` (no synchronisation).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Calls share the array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU race. */
+int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): per-stage device time and the
  * number of kernels the library launched.

@@ -65,6 +65,7 @@ SIGNATURES = {
     "tk_sym_eig": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _vp, _vp, _vp]),
     "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
                                _vp, _vp]),
+    "tk_gram_noalloc": (_c.c_int, [_vp, _c.POINTER(_i32), _c.c_int, _vp, _vp]),
     "tk_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "tk_profile_read": (_c.c_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_c.c_int64)]),
     "tk_kernel_launches": (_c.c_uint64, []),

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tk_internal.h"
 
@@ -163,6 +164,80 @@ void gram_f64(const double* F, const int n[3], int mode, double* G, double* scra
       scratch, p.nsplit, p.ntiles, n[mode], G);
   TK_LAUNCH("k_gram_reduce");
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 Gram (tk_gram_noalloc).
+//
+// Same kernels and arithmetic as gram_f64, but the split-K partial sums live
+// in a fixed file-scope device array instead of caller- or library-allocated
+// memory, for callers that must not allocate device memory.  Every GPU that
+// loads the library holds this array (8 MiB) until the process exits.  In
+// host code `g_gram_scratch` only names a host-side stand-in, so its device
+// address is looked up once per device with cudaGetSymbolAddress (with that
+// device current) and passed to the kernel.  The partial blocks are written
+// in full before they are read, so nothing needs clearing between calls; two
+// calls whose work overlaps on the GPU share the array and race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;  // 8 MiB
+static __device__ __align__(256) double g_gram_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+}  // namespace tk
+
+extern "C" int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, void* stream) {
+  using namespace tk;
+  if (!F || !G || !n || mode < 0 || mode > 2) return TK_EINVAL;
+  int nn[3] = {n[0], n[1], n[2]};
+  for (int a = 0; a < 3; ++a)
+    if (nn[a] < 1 || nn[a] > 1024) return TK_EINVAL;  // n outside [1, 1024]
+  GramPlan p = gram_plan(nn, mode);
+  const size_t per_split = (size_t)p.npairs * TB * TB;
+  if (per_split > kNoAllocScratchDoubles) return TK_EINVAL;  // cannot happen for n <= 1024
+  if ((size_t)p.nsplit * per_split > kNoAllocScratchDoubles) {
+    // fewer, longer K splits so that the partial sums fit the fixed array
+    const long long cap = (long long)(kNoAllocScratchDoubles / per_split);
+    p.kc = ((p.K + cap - 1) / cap + KS - 1) / KS * KS;
+    p.nsplit = (int)((p.K + p.kc - 1) / p.kc);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return TK_ECUDA;
+  }
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void* addr = nullptr;
+      if (cudaGetSymbolAddress(&addr, g_gram_scratch) != cudaSuccess || !addr) {
+        cudaGetLastError();
+        return TK_ECUDA;
+      }
+      g_scratch_ptr[dev] = static_cast<double*>(addr);
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Unfold u{mode, nn[0], nn[1], nn[2]};
+  k_gram_f64<<<dim3(p.npairs, p.nsplit), NT, 0, s>>>(F, u, nn[mode], p.K, p.kc, p.ntiles, scratch);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return TK_ECUDA;
+  const long long total = (long long)p.npairs * TB * TB;
+  k_gram_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
+      scratch, p.nsplit, p.ntiles, nn[mode], G);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return TK_ECUDA;
+  return TK_OK;
+}
+
+namespace tk {
 
 // ---------------------------------------------------------------------------
 // Strided batched GEMM.
