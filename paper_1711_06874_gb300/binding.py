@@ -23,6 +23,7 @@ TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_ETIMEOUT, TK_EBUSY, TK_ENOTFOUND = ran
 TK_MATERN, TK_SLATER_P, TK_GAUSSIAN = 0, 1, 2
 TK_CELL_CENTRED, TK_VERTEX = 0, 1
 TK_FP64, TK_SLICED_BF16 = 0, 1
+SLICED_AVAILABLE = True  # tensor-core Gram from exact BF16 slices is built
 TK_RANK_CAPPED, TK_EPS_UNREACHABLE_AT_PRECISION = 1, 2
 
 # every function the header declares, with (restype, argtypes)

@@ -298,7 +298,6 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     check_kernel(kernel);
     check_grid(grid);
     check_opts(opts);
-    if (opts->precision == TK_SLICED_BF16) fail(TK_EINVAL, "TK_SLICED_BF16 is not available in this build");
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
     const tk_opts& o = *opts;
@@ -308,9 +307,11 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     const int nmodes = one ? 1 : 3;
     int m[3];
     for (int a = 0; a < 3; ++a) m[a] = subspace_m(o, n[a], a);
+    const bool sliced = (o.precision == TK_SLICED_BF16);
     size_t gram_scr = 0, eig_scr = 0;
     for (int a = 0; a < nmodes; ++a) {
-      gram_scr = std::max(gram_scr, gram_f64_scratch_doubles(n, a));
+      gram_scr = std::max(gram_scr, sliced ? (gram_sliced_scratch_bytes(n, a) + 7) / 8
+                                           : gram_f64_scratch_doubles(n, a));
       eig_scr = std::max(eig_scr, sym_eig_scratch_doubles(n[a], m[a]));
     }
     int rcap[3];
@@ -338,7 +339,8 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     double* escr = ws.take<double>(sz[4]);
     double* small = ws.take<double>(sz[5]);  // [0] |F|^2, [1..3] traces
     double* ttm = ws.take<double>(sz[6]);
-    int* ranks_dev = ws.take<int>(64);
+    int* ranks_dev = ws.take<int>(64);  // [0..5] ranks and flags, [8] timeout flag
+    TK_CUDA(cudaMemsetAsync(ranks_dev, 0, sizeof(int) * 64, s));
     double *G[3], *V[3], *lam[3];
     for (int a = 0; a < 3; ++a) {
       G[a] = ws.take<double>((size_t)n[a] * n[a]);
@@ -354,19 +356,22 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     pf.end(s);
     for (int a = 0; a < nmodes; ++a) {
       pf.begin(TK_STAGE_GRAM, s);
-      gram_f64(F, n, a, G[a], gscr, s);
+      if (sliced)
+        gram_sliced_bf16(F, n, a, G[a], gscr, ranks_dev + 8, s);
+      else
+        gram_f64(F, n, a, G[a], gscr, s);
       pf.end(s);
       pf.begin(TK_STAGE_EIG, s);
       sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
       pf.end(s);
       pf.begin(TK_STAGE_RANK, s);
-      rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], std::ldexp(1.0, -53),
+      rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
                 n[a], ranks_dev + 2 * a, s);
       pf.end(s);
     }
-    int hr[6];
+    int hr[16];
     double hsmall[4];
-    TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 2 * nmodes, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(hsmall, small, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     res = new tk_result();
     res->ctx = ctx;
@@ -379,6 +384,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     for (int a = 0; a < nmodes; ++a)
       TK_CUDA(cudaMemcpyAsync(res->lam[a].data(), lam[a], sizeof(double) * m[a], cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
+    if (hr[8] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
     for (int a = 0; a < 3; ++a) {
       const int src = one ? 0 : a;
       res->r[a] = hr[2 * src];
@@ -539,13 +545,26 @@ int tk_gram(tk_ctx* ctx, const double* F, const int32_t n[3], int mode, int prec
     int nn[3] = {n[0], n[1], n[2]};
     for (int a = 0; a < 3; ++a)
       if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
-    if (precision != TK_FP64) fail(TK_EINVAL, "only TK_FP64 is available in this build");
+    if (precision != TK_FP64 && precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
-    ctx->ws.reserve(carve_bytes<double>(gram_f64_scratch_doubles(nn, mode)), s);
-    double* scr = ctx->ws.take<double>(gram_f64_scratch_doubles(nn, mode));
-    gram_f64(F, nn, mode, G, scr, s);
-    TK_CUDA(cudaStreamSynchronize(s));
+    if (precision == TK_FP64) {
+      ctx->ws.reserve(carve_bytes<double>(gram_f64_scratch_doubles(nn, mode)), s);
+      double* scr = ctx->ws.take<double>(gram_f64_scratch_doubles(nn, mode));
+      gram_f64(F, nn, mode, G, scr, s);
+      TK_CUDA(cudaStreamSynchronize(s));
+    } else {
+      const size_t b = gram_sliced_scratch_bytes(nn, mode);
+      ctx->ws.reserve(carve_bytes<char>(b) + carve_bytes<int>(4), s);
+      char* scr = ctx->ws.take<char>(b);
+      int* err = ctx->ws.take<int>(4);
+      TK_CUDA(cudaMemsetAsync(err, 0, sizeof(int) * 4, s));
+      gram_sliced_bf16(F, nn, mode, G, scr, err, s);
+      int h = 0;
+      TK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      if (h != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+    }
   });
 }
 

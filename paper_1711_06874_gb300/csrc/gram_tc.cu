@@ -1,0 +1,463 @@
+// (b) Gram G = A A^T of an unfolding A = F_(k) (Sec. 3.2) on the tcgen05
+// tensor cores with FP64-class accuracy, from exact BF16 slices.
+//
+// Slicing (after Ozaki, Ogita, Oishi and Rump's error-free splitting).  Each
+// row i of A is scaled by 2^-e_i with e_i the binary exponent of its largest
+// entry, so every scaled entry x lies in (-1, 1).  It is then written exactly
+// as x = sum_{s<6} d_s 2^(-7-8s) + O(2^-48) with balanced integer digits
+// |d_s| <= 128 (d_s = round of the remaining scaled residual), and slice s
+// stores d_s 2^(-7-8s): at most 8 significant bits, so exact in BF16.
+//
+// Products.  slice_s(i) slice_t(j) = d d' 2^(-14-8(s+t)) is exact, and the
+// pairs of equal weight w = s + t share an accumulator in TMEM:
+//   w = 0, 1, 2  -> three exact FP32 accumulators: every partial sum is an
+//                   integer multiple of 2^(-14-8w) below 2^24 of those units as
+//                   long as (w+1) * 256 * 2^14 <= 2^24, i.e. for chunks of 256 K;
+//   w = 3, 4, 5  -> one FP32 accumulator; its rounding is 2^-24 of a term that
+//                   is itself 2^-24 of the leading one;
+//   w >= 6       -> dropped (2^-48 of the leading term).
+// Every 256-deep K chunk the epilogue warps move the four accumulators into a
+// 64-bit integer accumulator in units of 2^-38 (exact for w <= 2), so the
+// chunk sums carry no rounding; the split-K partials are FP64 and are summed
+// in index order with the row scales 2^(e_i + e_j) applied.
+//
+// Kernel layout (one CTA per 128 x 128 tile pair and K range):
+//   warp 0       TMA producer: 6 slices x 128 rows x 32 K of A (and of B off
+//                the diagonal) per stage, SWIZZLE_64B, two stages;
+//   warp 1       TMEM owner (512 columns = 4 accumulators of 128) and the
+//                single-thread tcgen05.mma issuer (21 slice pairs x 2 K steps);
+//   warps 2..17  epilogue: TMEM -> registers -> int64, one TMEM lane quadrant
+//                and one 32-column quarter each.
+// Every mbarrier wait is bounded; on a timeout the kernel raises a flag, lets
+// in-flight copies and MMAs finish (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "tc_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+namespace {
+
+constexpr int kSlices = 6;
+constexpr int kMaxWeight = 5;          // pairs with s + t <= 5 are kept (21 pairs)
+constexpr int kTile = 128;             // M = N = 128
+constexpr int kKB = 32;                // K per stage (64-byte rows, SWIZZLE_64B)
+constexpr int kChunkBlocks = 8;        // 8 x 32 = 256 K per exact chunk
+constexpr int kStages = 2;
+constexpr int kSliceTileBytes = kTile * kKB * 2;           // 8 KB
+constexpr int kOperandBytes = kSlices * kSliceTileBytes;   // 48 KB
+constexpr int kStageBytes = 2 * kOperandBytes;             // 96 KB (A and B)
+constexpr int kThreads = 576;                              // 18 warps
+constexpr int kEpiWarps = 16;
+constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+// Slice pairs (s, t) with s + t <= kMaxWeight, in order of weight.
+constexpr int kPairs = 21;
+__constant__ int kPairS[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ int kPairT[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+static_assert(kPairs == (kMaxWeight + 1) * (kMaxWeight + 2) / 2, "pair table covers s + t <= kMaxWeight");
+
+// Row exponents: e_i with max_c |A(i,c)| < 2^e_i (frexp), -1000 for a zero row.
+__device__ __forceinline__ long long unfold_at(int mode, int n1, int n2, int n3, int row, long long c) {
+  if (mode == 0) return (long long)row * n2 * n3 + c;
+  if (mode == 1) {
+    const long long i = c / n3, l = c - i * n3;
+    return (i * n2 + row) * n3 + l;
+  }
+  return c * n3 + row;
+}
+
+__global__ void k_rowmax(const double* __restrict__ F, int mode, int n1, int n2, int n3, long long K,
+                         unsigned long long* __restrict__ rowmax_bits) {
+  // grid: (row blocks of 32 rows for mode 2 / one row for modes 0,1, K chunks)
+  if (mode == 2) {
+    const int row = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int nrows = n3;
+    double m = 0.0;
+    if (row < nrows)
+      for (long long c = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5); c < K;
+           c += (long long)gridDim.y * (blockDim.x >> 5))
+        m = fmax(m, fabs(F[c * n3 + row]));
+    if (row < nrows) atomicMax(rowmax_bits + row, (unsigned long long)__double_as_longlong(m));
+  } else {
+    const int row = blockIdx.x;
+    double m = 0.0;
+    for (long long c = blockIdx.y * (long long)blockDim.x + threadIdx.x; c < K;
+         c += (long long)gridDim.y * blockDim.x)
+      m = fmax(m, fabs(F[unfold_at(mode, n1, n2, n3, row, c)]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rowmax_bits + row, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__global__ void k_rowexp(const unsigned long long* __restrict__ rowmax_bits, int nrows, int* __restrict__ rowexp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+    const double m = __longlong_as_double((long long)rowmax_bits[i]);
+    int e = -1000;
+    if (m > 0.0) frexp(m, &e);
+    rowexp[i] = e;
+  }
+}
+
+// Slices of one unfolding, written K-major: S[s][row][c], row stride Kp (a
+// multiple of 32, zero padded).  32 x 32 tiles through shared memory so that
+// both the read of F and the write of S are coalesced for every mode.
+__global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, int n3, int nrows, long long K,
+                        long long Kp, const int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32;
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  // load: for mode 2 rows are contiguous in F, otherwise columns are
+  for (int q = ty; q < 32; q += 8) {
+    int row;
+    long long c;
+    if (mode == 2) {
+      row = r0 + tx;
+      c = c0 + q;
+    } else {
+      row = r0 + q;
+      c = c0 + tx;
+    }
+    double v = 0.0;
+    if (row < nrows && c < K) v = F[unfold_at(mode, n1, n2, n3, row, c)];
+    if (mode == 2)
+      tile[tx][q] = v;  // [row][c]
+    else
+      tile[q][tx] = v;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)nrows * Kp;
+  for (int q = ty; q < 32; q += 8) {
+    const int row = r0 + q;
+    const long long c = c0 + tx;
+    if (row >= nrows || c >= Kp) continue;
+    double x = tile[q][tx];
+    const int e = rowexp[row];
+    x = (e > -1000) ? ldexp(x, -e) * 128.0 : 0.0;  // |x| < 128 after scaling by 2^(7 - e)
+    const size_t base = (size_t)row * Kp + c;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      const double d = rint(x);  // balanced digit, |d| <= 128
+      x = (x - d) * 256.0;       // exact
+      S[s * plane + base] = __float2bfloat16_rn((float)ldexp(d, -7 - 8 * s));
+    }
+  }
+}
+
+struct TcArgs {
+  int nrows;
+  int ntiles;
+  int npairs;
+  int kblocks_per_split;  // k-blocks (of 32) per CTA
+  int kblocks_total;
+  double* partials;       // [split][pair][128][128]
+  int* err;
+};
+
+__device__ __forceinline__ void pair_of(int p, int ntiles, int& ti, int& tj) {
+  int t = p;
+  ti = 0;
+  while (t >= ntiles - ti) {
+    t -= ntiles - ti;
+    ++ti;
+  }
+  tj = ti + t;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+  uint64_t* full = bars;            // [kStages]
+  uint64_t* empty = bars + 2;       // [kStages]
+  uint64_t* acc_full = bars + 4;
+  uint64_t* acc_empty = bars + 5;
+  uint64_t* drain = bars + 6;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ti, tj;
+  pair_of(blockIdx.x, args.ntiles, ti, tj);
+  const bool diag = (ti == tj);
+  const int kb0 = blockIdx.y * args.kblocks_per_split;
+  const int kb1 = min(kb0 + args.kblocks_per_split, args.kblocks_total);
+  const int nkb = kb1 - kb0;
+  const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kEpiWarps);
+    tc::mbar_init(drain, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint32_t bytes = diag ? kOperandBytes : 2 * kOperandBytes;
+      int issued = 0;
+      for (int k = 0; k < nkb; ++k) {
+        const int st = k % kStages;
+        const uint32_t use = k / kStages;
+        if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
+        unsigned char* sa = smem + st * kStageBytes;
+        tc::mbar_expect_tx(&full[st], bytes);
+        tc::tma_load_3d(sa, &tmap, &full[st], (kb0 + k) * kKB, ti * kTile, 0);
+        if (!diag) tc::tma_load_3d(sa + kOperandBytes, &tmap, &full[st], (kb0 + k) * kKB, tj * kTile, 0);
+        issued = k + 1;
+      }
+      // copies still in flight must land before the CTA exits
+      for (int k = max(0, issued - kStages); k < issued; ++k)
+        tc::mbar_wait(&full[k % kStages], (k / kStages) & 1, args.err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile);
+      bool ok = true;
+      int k = 0;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        if (ch > 0 && !tc::mbar_wait(acc_empty, (ch - 1) & 1, args.err)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int kend = min(nkb, (ch + 1) * kChunkBlocks);
+        uint32_t first_mask = 0xFu;  // accumulator not yet written in this chunk
+        for (; k < kend; ++k) {
+          const int st = k % kStages;
+          if (!tc::mbar_wait(&full[st], (k / kStages) & 1, args.err)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          unsigned char* sa = smem + st * kStageBytes;
+          unsigned char* sb = diag ? sa : sa + kOperandBytes;
+          // descriptors of slice 0; slice s and K step kk add (s * 8 KB + kk * 32 B) / 16
+          const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
+          const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
+#pragma unroll 1
+          for (int pidx = 0; pidx < kPairs; ++pidx) {
+            const int s = kPairS[pidx], t = kPairT[pidx];
+            const int acc = (s + t < 3) ? s + t : 3;
+            const uint32_t dt = tmem + acc * kTile;
+            const uint32_t accum = (first_mask >> acc) & 1u ? 0u : 1u;
+            first_mask &= ~(1u << acc);
+            tc::mma_bf16(dt, da0 + (uint64_t)(s * (kSliceTileBytes >> 4)), db0 + (uint64_t)(t * (kSliceTileBytes >> 4)),
+                         idesc, accum);
+            tc::mma_bf16(dt, da0 + (uint64_t)(s * (kSliceTileBytes >> 4) + 2),
+                         db0 + (uint64_t)(t * (kSliceTileBytes >> 4) + 2), idesc, 1u);
+          }
+          tc::mma_commit(&empty[st]);  // frees the stage once these MMAs finish
+        }
+        if (ok) tc::mma_commit(acc_full);
+      }
+      // every MMA issued must finish before TMEM is released
+      tc::mma_commit(drain);
+      tc::mbar_wait(drain, 0, args.err);
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> int64 ----------------
+    const int q = warp & 3;              // TMEM lane quadrant of this warp
+    const int quarter = (warp - 2) >> 2;  // 32-column quarter
+    const int row = q * 32 + lane;
+    long long V[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) V[j] = 0;
+    bool ok = true;
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + quarter * 32;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!tc::mbar_wait(acc_full, ch & 1, args.err)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      // w = 0, 1, 2 are integer multiples of 2^-14, 2^-22, 2^-30; the merged
+      // w = 3..5 accumulator is rounded to units of 2^-38
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t r[8];
+        tc::tmem_ld8(base + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 16384.0f) * (1LL << 24);
+        tc::tmem_ld8(base + kTile + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 4194304.0f) * (1LL << 16);
+        tc::tmem_ld8(base + 2 * kTile + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 1073741824.0f) * (1LL << 8);
+        tc::tmem_ld8(base + 3 * kTile + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 274877906944.0f);
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty);
+    }
+    if (ok) {
+      double* out = args.partials + ((size_t)blockIdx.y * args.npairs + blockIdx.x) * kTile * kTile +
+                    (size_t)row * kTile + quarter * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[j] = (double)V[j] * 3.637978807091713e-12;  // 2^-38
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// G[gi][gj] = 2^(e_gi + e_gj) sum_split P[split][pair][r][c], both triangles.
+__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int ntiles, int n,
+                            const int* __restrict__ rowexp, double* __restrict__ G) {
+  const int npairs = ntiles * (ntiles + 1) / 2;
+  const long long total = (long long)npairs * kTile * kTile;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int pr = (int)(e / (kTile * kTile));
+    const int rc = (int)(e % (kTile * kTile));
+    int ti, tj;
+    pair_of(pr, ntiles, ti, tj);
+    const int gi = ti * kTile + rc / kTile, gj = tj * kTile + rc % kTile;
+    if (gi >= n || gj >= n) continue;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += P[((long long)sp * npairs + pr) * kTile * kTile + rc];
+    const int ei = rowexp[gi], ej = rowexp[gj];
+    const double v = (ei > -1000 && ej > -1000) ? ldexp(s, ei + ej) : 0.0;
+    G[(long long)gi * n + gj] = v;
+    G[(long long)gj * n + gi] = v;
+  }
+}
+
+struct TcPlan {
+  int nrows, ntiles, npairs, nsplit, kb_per_split, kb_total;
+  long long K, Kp;
+};
+
+TcPlan tc_plan(const int n[3], int mode, int sm_count) {
+  TcPlan p;
+  p.nrows = n[mode];
+  p.K = (long long)n[0] * n[1] * n[2] / p.nrows;
+  p.Kp = (p.K + kKB - 1) / kKB * kKB;
+  p.kb_total = (int)(p.Kp / kKB);
+  p.ntiles = (p.nrows + kTile - 1) / kTile;
+  p.npairs = p.ntiles * (p.ntiles + 1) / 2;
+  // one wave: about sm_count CTAs, splits made of whole 256-deep chunks
+  const int chunks = (p.kb_total + kChunkBlocks - 1) / kChunkBlocks;
+  int want = std::max(1, sm_count / p.npairs);
+  want = std::min(want, chunks);
+  const int chunks_per_split = (chunks + want - 1) / want;
+  p.kb_per_split = chunks_per_split * kChunkBlocks;
+  p.nsplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;
+  return p;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+}  // namespace
+
+size_t gram_sliced_scratch_bytes(const int n[3], int mode) {
+  const TcPlan p = tc_plan(n, mode, 152);
+  size_t b = 0;
+  b += carve_bytes<unsigned long long>(p.nrows);                        // row max bits
+  b += carve_bytes<int>(p.nrows);                                       // row exponents
+  b += carve_bytes<__nv_bfloat16>((size_t)kSlices * p.nrows * p.Kp);    // slices
+  b += carve_bytes<double>((size_t)p.nsplit * p.npairs * kTile * kTile);  // partials
+  return b + 4096;
+}
+
+void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
+                      cudaStream_t s) {
+  // one plan (for 152 SMs) fixes both the scratch layout and the grid
+  TcPlan p = tc_plan(n, mode, 152);
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    char* q = base + off;
+    off += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  unsigned long long* rowmax = (unsigned long long*)carve(sizeof(unsigned long long) * p.nrows);
+  int* rowexp = (int*)carve(sizeof(int) * p.nrows);
+  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)kSlices * p.nrows * p.Kp);
+  double* P = (double*)carve(sizeof(double) * (size_t)p.nsplit * p.npairs * kTile * kTile);
+
+  TK_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * p.nrows, s));
+  if (mode == 2) {
+    dim3 g((p.nrows + 31) / 32, (unsigned)std::min<long long>(1024, (p.K + 7) / 8));
+    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax);
+  } else {
+    dim3 g(p.nrows, (unsigned)std::min<long long>(64, (p.K + 255) / 256));
+    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax);
+  }
+  TK_LAUNCH("k_rowmax");
+  k_rowexp<<<(p.nrows + 255) / 256, 256, 0, s>>>(rowmax, p.nrows, rowexp);
+  TK_LAUNCH("k_rowexp");
+  {
+    dim3 g((unsigned)(p.Kp / 32), (p.nrows + 31) / 32);
+    k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S);
+    TK_LAUNCH("k_slice");
+  }
+  // tensor map over the slices: dims (Kp, nrows, 6), box (32, 128, 6), 64-byte swizzle
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  cuuint64_t dims[3] = {(cuuint64_t)p.Kp, (cuuint64_t)p.nrows, (cuuint64_t)kSlices};
+  cuuint64_t strides[2] = {(cuuint64_t)p.Kp * 2, (cuuint64_t)p.Kp * 2 * p.nrows};
+  cuuint32_t box[3] = {kKB, kTile, kSlices};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(TK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  TcArgs a{p.nrows, p.ntiles, p.npairs, p.kb_per_split, p.kb_total, P, err};
+  k_gram_tc<<<dim3(p.npairs, p.nsplit), kThreads, kSmemBytes, s>>>(map, a);
+  TK_LAUNCH("k_gram_tc");
+  const long long total = (long long)p.npairs * kTile * kTile;
+  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, p.nsplit, p.ntiles,
+                                                                                      p.nrows, rowexp, G);
+  TK_LAUNCH("k_tc_reduce");
+}
+
+}  // namespace tk

@@ -88,10 +88,13 @@ void norm2_f64(const double* x, size_t len, double* out_dev, double* scratch, cu
 size_t gram_f64_scratch_doubles(const int n[3], int mode);
 void gram_f64(const double* F, const int n[3], int mode, double* G, double* scratch, cudaStream_t s);
 
-// (b) Gram from exact BF16 slices on the tcgen05 tensor cores.
+// (b) Gram from exact BF16 slices on the tcgen05 tensor cores.  `err` (device
+// int) is raised if a bounded wait inside the kernel ran out.
 size_t gram_sliced_scratch_bytes(const int n[3], int mode);
-void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch,
+void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s);
+// unit roundoff of the Gram of each precision (for the eps-unreachable flag)
+inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 : 0x1p-48; }
 
 // General strided batched FP64 GEMM: C[b](i,j) = sum_k A[b](i,k) B[b](k,j)
 struct GemmDesc {

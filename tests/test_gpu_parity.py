@@ -263,3 +263,88 @@ def test_profile_and_launch_counter(ctx, wl):
     assert binding.Context.kernel_launches() > l0 + 5
     for stage in ("eval", "norm", "gram", "eig", "rank", "core", "error"):
         assert prof[stage][1] >= 1 and prof[stage][0] > 0.0, stage
+
+
+# ---------------------------------------------------------------------------
+# Mixed path: Gram from exact BF16 slices on the tcgen05 tensor cores
+# ---------------------------------------------------------------------------
+U_SLICED = 2.0 ** -48
+
+
+@pytest.mark.parametrize("shape", [(70, 45, 33), (64, 64, 64), (200, 3, 5), (130, 9, 40), (2, 2, 2), (256, 16, 16)])
+def test_gram_sliced_matches_oracle(ctx, orc, shape):
+    from paper_1711_06874_gb300 import binding
+
+    rng = np.random.default_rng(23)
+    Fh = rng.random(shape) * np.exp(-3 * rng.random(shape))  # entries over about 1.3 decades
+    F = _dev(Fh)
+    for mode in range(3):
+        m = shape[mode]
+        G = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        ctx.gram(F, mode, G, precision=binding.TK_SLICED_BF16)
+        ref = orc.gram(Fh, mode)
+        err = np.abs(G.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= 1e-13, (shape, mode, err)
+
+
+def test_gram_sliced_exact_on_integer_grid(ctx):
+    """Entries with few significant bits are represented exactly by the slices."""
+    from paper_1711_06874_gb300 import binding
+
+    rng = np.random.default_rng(3)
+    Fh = rng.integers(-1000, 1000, size=(96, 40, 50)).astype(np.float64)
+    F = _dev(Fh)
+    for mode in range(3):
+        A = np.moveaxis(Fh, mode, 0).reshape(Fh.shape[mode], -1).astype(np.int64)
+        exact = (A @ A.T).astype(np.float64)
+        G = torch.empty(exact.shape, dtype=torch.float64, device="cuda")
+        ctx.gram(F, mode, G, precision=binding.TK_SLICED_BF16)
+        np.testing.assert_array_equal(G.cpu().numpy(), exact)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
+def test_tucker_sliced_slater_n64_matches_oracle(ctx, orc, wl, eps):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.slater_n64(eps)
+    res = ctx.tucker(prob, precision=binding.TK_SLICED_BF16)
+    ref, e = _compare_solution(orc, wl, res, prob, precision_u=U_SLICED)
+    assert e <= 2 * ref["rel_error"] or res.ranks[1][0]
+
+
+@pytest.mark.parametrize("case", [
+    dict(nu=1.2, ell=(0.25, 0.3, 0.4), n=(40, 48, 70), eps=1e-6, rmax=24),
+    dict(nu=0.7, ell=0.2, n=(66, 66, 66), eps=1e-6, rmax=30),
+    dict(nu=2.5, ell=0.1, n=(130, 20, 24), eps=1e-5, rmax=24),
+])
+def test_tucker_sliced_ragged_matches_oracle(ctx, orc, wl, case):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, **case)
+    res = ctx.tucker(prob, precision=binding.TK_SLICED_BF16)
+    ref, e = _compare_solution(orc, wl, res, prob, precision_u=U_SLICED)
+    assert e <= 2 * ref["rel_error"]
+
+
+def test_tucker_bench_workload_full_size(ctx, orc, wl):
+    """The benchmark's n = 256 workload in its launch configuration, both paths, against the oracle."""
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.matern_n256(1e-6)
+    ref = orc.hosvd(wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc), prob.eps, rmax=list(prob.rmax))
+    nF = math.sqrt(ref["normF2"])
+    for precision in (binding.TK_FP64, binding.TK_SLICED_BF16):
+        res = ctx.tucker(prob, precision=precision)
+        ranks, flags = res.ranks
+        assert ranks == ref["ranks"], (precision, ranks, ref["ranks"])
+        assert abs(res.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
+        B = res.core()
+        assert abs(np.linalg.norm(B) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
+        U = [res.factor(a) for a in range(3)]
+        rp = min(separated_prefix(ref["lam"][0][: ranks[0] + 1]), ranks[0])
+        assert principal_sines(ref["U"][0][:, :rp], U[0][:, :rp]).max() <= 1e-10
+        e = res.rel_error()
+        assert e <= prob.eps and e <= 2 * ref["rel_error"], (precision, e, ref["rel_error"])
+        lam = res.eigenvalues(0)
+        k = min(len(lam), ranks[0] + 2)
+        np.testing.assert_allclose(lam[:k], ref["lam"][0][:k], rtol=0, atol=1e-13 * ref["lam"][0][0])
