@@ -10,24 +10,26 @@
 //
 // Products.  slice_s(i) slice_t(j) = d d' 2^(-14-8(s+t)) is exact, and the
 // pairs of equal weight w = s + t share an accumulator in TMEM:
-//   w = 0, 1, 2  -> three exact FP32 accumulators: every partial sum is an
-//                   integer multiple of 2^(-14-8w) below 2^24 of those units as
-//                   long as (w+1) * 256 * 2^14 <= 2^24, i.e. for chunks of 256 K;
-//   w = 3, 4, 5  -> one FP32 accumulator; its rounding is 2^-24 of a term that
-//                   is itself 2^-24 of the leading one;
+//   w = 0 .. 3   -> four exact FP32 accumulators: every partial sum is an
+//                   integer multiple of 2^(-14-8w) of at most 2^24 of those
+//                   units while (w+1) * 256 * 2^14 <= 2^24, i.e. for 256-deep
+//                   K chunks (the tensor core's FP32 sums are exact there);
+//   w = 4, 5     -> one FP32 accumulator; the tensor core truncates, which
+//                   costs about 2^-17 of a term that is 2^-32 of the leading one;
 //   w >= 6       -> dropped (2^-48 of the leading term).
-// Every 256-deep K chunk the epilogue warps move the four accumulators into a
-// 64-bit integer accumulator in units of 2^-38 (exact for w <= 2), so the
+// Every 256-deep K chunk the epilogue warps move the five accumulators into a
+// 64-bit integer accumulator in units of 2^-44 (exact for w <= 3), so the
 // chunk sums carry no rounding; the split-K partials are FP64 and are summed
 // in index order with the row scales 2^(e_i + e_j) applied.
 //
-// Kernel layout (one CTA per 128 x 128 tile pair and K range):
-//   warp 0       TMA producer: 6 slices x 128 rows x 32 K of A (and of B off
-//                the diagonal) per stage, SWIZZLE_64B, two stages;
-//   warp 1       TMEM owner (512 columns = 4 accumulators of 128) and the
+// Kernel layout (one CTA per 128 x 96 block of G touching its upper triangle,
+// and one K range):
+//   warp 0       TMA producer: 6 slices x 128 rows (A) and 6 x 96 rows (B) x
+//                32 K per stage, SWIZZLE_64B, two stages;
+//   warp 1       TMEM owner (5 accumulators of 96 columns) and the
 //                single-thread tcgen05.mma issuer (21 slice pairs x 2 K steps);
 //   warps 2..17  epilogue: TMEM -> registers -> int64, one TMEM lane quadrant
-//                and one 32-column quarter each.
+//                and one 24-column group each.
 // Every mbarrier wait is bounded; on a timeout the kernel raises a flag, lets
 // in-flight copies and MMAs finish (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -49,15 +51,20 @@ namespace {
 
 constexpr int kSlices = 6;
 constexpr int kMaxWeight = 5;          // pairs with s + t <= 5 are kept (21 pairs)
-constexpr int kTile = 128;             // M = N = 128
+constexpr int kTM = 128;               // rows of a block of G (M)
+constexpr int kTN = 96;                // columns of a block of G (N)
+constexpr int kAcc = 5;                // accumulators: w = 0, 1, 2, 3 and w = 4..5
 constexpr int kKB = 32;                // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int kChunkBlocks = 8;        // 8 x 32 = 256 K per exact chunk
 constexpr int kStages = 2;
-constexpr int kSliceTileBytes = kTile * kKB * 2;           // 8 KB
-constexpr int kOperandBytes = kSlices * kSliceTileBytes;   // 48 KB
-constexpr int kStageBytes = 2 * kOperandBytes;             // 96 KB (A and B)
-constexpr int kThreads = 576;                              // 18 warps
+constexpr int kSliceBytesA = kTM * kKB * 2;            // 8 KB
+constexpr int kSliceBytesB = kTN * kKB * 2;            // 6 KB
+constexpr int kOperandBytesA = kSlices * kSliceBytesA;  // 48 KB
+constexpr int kOperandBytesB = kSlices * kSliceBytesB;  // 36 KB
+constexpr int kStageBytes = kOperandBytesA + kOperandBytesB;  // 84 KB
+constexpr int kThreads = 576;                          // 18 warps
 constexpr int kEpiWarps = 16;
+constexpr int kEpiCols = kTN / 4;                      // 24 columns per epilogue warp
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
 // Slice pairs (s, t) with s + t <= kMaxWeight, in order of weight.
@@ -65,6 +72,7 @@ constexpr int kPairs = 21;
 __constant__ int kPairS[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
 __constant__ int kPairT[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
 static_assert(kPairs == (kMaxWeight + 1) * (kMaxWeight + 2) / 2, "pair table covers s + t <= kMaxWeight");
+static_assert(kAcc * kTN <= 512, "accumulators fit in TMEM");
 
 // Row exponents: e_i with max_c |A(i,c)| < 2^e_i (frexp), -1000 for a zero row.
 __device__ __forceinline__ long long unfold_at(int mode, int n1, int n2, int n3, int row, long long c) {
@@ -156,26 +164,48 @@ __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, 
 
 struct TcArgs {
   int nrows;
-  int ntiles;
-  int npairs;
+  int nrt, nct;           // row tiles (of 128) and column tiles (of 96)
+  int nblocks;            // blocks of G touching the upper triangle
   int kblocks_per_split;  // k-blocks (of 32) per CTA
   int kblocks_total;
-  double* partials;       // [split][pair][128][128]
+  double* partials;       // [split][block][128][96]
   int* err;
 };
 
-__device__ __forceinline__ void pair_of(int p, int ntiles, int& ti, int& tj) {
-  int t = p;
-  ti = 0;
-  while (t >= ntiles - ti) {
-    t -= ntiles - ti;
-    ++ti;
+// Block b (in row-major order over blocks with i*128 < (j+1)*96) -> (i, j).
+__host__ __device__ __forceinline__ void block_of(int b, int nrt, int nct, int& bi, int& bj) {
+  for (int i = 0; i < nrt; ++i) {
+    const int j0 = (i * kTM) / kTN;
+    const int cnt = nct - j0;
+    if (b < cnt) {
+      bi = i;
+      bj = j0 + b;
+      return;
+    }
+    b -= cnt;
   }
-  tj = ti + t;
+  bi = nrt;
+  bj = nct;
+}
+
+__host__ __device__ __forceinline__ int block_count(int nrt, int nct) {
+  int c = 0;
+  for (int i = 0; i < nrt; ++i) {
+    const int j0 = (i * kTM) / kTN;
+    c += (nct > j0) ? nct - j0 : 0;
+  }
+  return c;
+}
+
+// Index of block (i, j) in that order.
+__device__ __forceinline__ int block_index(int i, int j, int nct) {
+  int b = 0;
+  for (int r = 0; r < i; ++r) b += nct - (r * kTM) / kTN;
+  return b + j - (i * kTM) / kTN;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gram_tc(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
+    k_gram_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, TcArgs args) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
@@ -187,9 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = (uint32_t*)(bars + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int ti, tj;
-  pair_of(blockIdx.x, args.ntiles, ti, tj);
-  const bool diag = (ti == tj);
+  int bi, bj;
+  block_of(blockIdx.x, args.nrt, args.nct, bi, bj);
   const int kb0 = blockIdx.y * args.kblocks_per_split;
   const int kb1 = min(kb0 + args.kblocks_per_split, args.kblocks_total);
   const int nkb = kb1 - kb0;
@@ -214,16 +243,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const uint32_t bytes = diag ? kOperandBytes : 2 * kOperandBytes;
       int issued = 0;
       for (int k = 0; k < nkb; ++k) {
         const int st = k % kStages;
         const uint32_t use = k / kStages;
         if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
         unsigned char* sa = smem + st * kStageBytes;
-        tc::mbar_expect_tx(&full[st], bytes);
-        tc::tma_load_3d(sa, &tmap, &full[st], (kb0 + k) * kKB, ti * kTile, 0);
-        if (!diag) tc::tma_load_3d(sa + kOperandBytes, &tmap, &full[st], (kb0 + k) * kKB, tj * kTile, 0);
+        tc::mbar_expect_tx(&full[st], kStageBytes);
+        tc::tma_load_3d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0);
+        tc::tma_load_3d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0);
         issued = k + 1;
       }
       // copies still in flight must land before the CTA exits
@@ -233,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile);
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
       bool ok = true;
       int k = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
@@ -243,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_after_sync();
         const int kend = min(nkb, (ch + 1) * kChunkBlocks);
-        uint32_t first_mask = 0xFu;  // accumulator not yet written in this chunk
+        uint32_t first_mask = (1u << kAcc) - 1;  // accumulator not yet written in this chunk
         for (; k < kend; ++k) {
           const int st = k % kStages;
           if (!tc::mbar_wait(&full[st], (k / kStages) & 1, args.err)) {
@@ -252,21 +280,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::fence_after_sync();
           unsigned char* sa = smem + st * kStageBytes;
-          unsigned char* sb = diag ? sa : sa + kOperandBytes;
-          // descriptors of slice 0; slice s and K step kk add (s * 8 KB + kk * 32 B) / 16
+          unsigned char* sb = sa + kOperandBytesA;
+          // descriptors of slice 0; slice s and K step kk add (s * slice bytes + kk * 32 B) / 16
           const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
           const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
 #pragma unroll 1
           for (int pidx = 0; pidx < kPairs; ++pidx) {
             const int s = kPairS[pidx], t = kPairT[pidx];
-            const int acc = (s + t < 3) ? s + t : 3;
-            const uint32_t dt = tmem + acc * kTile;
-            const uint32_t accum = (first_mask >> acc) & 1u ? 0u : 1u;
+            const int acc = (s + t < 4) ? s + t : 4;
+            const uint32_t dt = tmem + acc * kTN;
+            const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
             first_mask &= ~(1u << acc);
-            tc::mma_bf16(dt, da0 + (uint64_t)(s * (kSliceTileBytes >> 4)), db0 + (uint64_t)(t * (kSliceTileBytes >> 4)),
-                         idesc, accum);
-            tc::mma_bf16(dt, da0 + (uint64_t)(s * (kSliceTileBytes >> 4) + 2),
-                         db0 + (uint64_t)(t * (kSliceTileBytes >> 4) + 2), idesc, 1u);
+            const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
+            const uint64_t db = db0 + (uint64_t)(t * (kSliceBytesB >> 4));
+            tc::mma_bf16(dt, da, db, idesc, accum);
+            tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
           }
           tc::mma_commit(&empty[st]);  // frees the stage once these MMAs finish
         }
@@ -278,50 +306,55 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue: TMEM -> int64 ----------------
-    const int q = warp & 3;              // TMEM lane quadrant of this warp
-    const int quarter = (warp - 2) >> 2;  // 32-column quarter
+    const int q = warp & 3;             // TMEM lane quadrant of this warp
+    const int grp = (warp - 2) >> 2;    // 24-column group
     const int row = q * 32 + lane;
-    long long V[32];
+    long long V[kEpiCols];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) V[j] = 0;
+    for (int j = 0; j < kEpiCols; ++j) V[j] = 0;
     bool ok = true;
-    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + quarter * 32;
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + grp * kEpiCols;
     for (int ch = 0; ch < nchunks; ++ch) {
       if (!tc::mbar_wait(acc_full, ch & 1, args.err)) {
         ok = false;
         break;
       }
       tc::fence_after_sync();
-      // w = 0, 1, 2 are integer multiples of 2^-14, 2^-22, 2^-30; the merged
-      // w = 3..5 accumulator is rounded to units of 2^-38
+      // w = 0..3 are integer multiples of 2^(-14-8w): exact into units of
+      // 2^-44; the w = 4..5 accumulator is rounded to that unit
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
+      for (int h = 0; h < kEpiCols / 8; ++h) {
         uint32_t r[8];
         tc::tmem_ld8(base + h * 8, r);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 16384.0f) * (1LL << 24);
-        tc::tmem_ld8(base + kTile + h * 8, r);
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 16384.0f) * (1LL << 30);
+        tc::tmem_ld8(base + kTN + h * 8, r);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 4194304.0f) * (1LL << 16);
-        tc::tmem_ld8(base + 2 * kTile + h * 8, r);
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 4194304.0f) * (1LL << 22);
+        tc::tmem_ld8(base + 2 * kTN + h * 8, r);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 1073741824.0f) * (1LL << 8);
-        tc::tmem_ld8(base + 3 * kTile + h * 8, r);
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 1073741824.0f) * (1LL << 14);
+        tc::tmem_ld8(base + 3 * kTN + h * 8, r);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 274877906944.0f);
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 274877906944.0f) * (1LL << 6);
+        tc::tmem_ld8(base + 4 * kTN + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 17592186044416.0f);
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(acc_empty);
     }
     if (ok) {
-      double* out = args.partials + ((size_t)blockIdx.y * args.npairs + blockIdx.x) * kTile * kTile +
-                    (size_t)row * kTile + quarter * 32;
+      double* out = args.partials + ((size_t)blockIdx.y * args.nblocks + blockIdx.x) * kTM * kTN +
+                    (size_t)row * kTN + grp * kEpiCols;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) out[j] = (double)V[j] * 3.637978807091713e-12;  // 2^-38
+      for (int j = 0; j < kEpiCols; ++j) out[j] = (double)V[j] * 5.684341886080802e-14;  // 2^-44
     }
   }
   tc::fence_before_sync();
@@ -330,21 +363,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-// G[gi][gj] = 2^(e_gi + e_gj) sum_split P[split][pair][r][c], both triangles.
-__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int ntiles, int n,
+// G[gi][gj] = G[gj][gi] = 2^(e_gi + e_gj) sum_split P[split][block(gi, gj)][..], gi <= gj.
+__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int nct, int nblocks, int n,
                             const int* __restrict__ rowexp, double* __restrict__ G) {
-  const int npairs = ntiles * (ntiles + 1) / 2;
-  const long long total = (long long)npairs * kTile * kTile;
+  const long long total = (long long)n * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int pr = (int)(e / (kTile * kTile));
-    const int rc = (int)(e % (kTile * kTile));
-    int ti, tj;
-    pair_of(pr, ntiles, ti, tj);
-    const int gi = ti * kTile + rc / kTile, gj = tj * kTile + rc % kTile;
-    if (gi >= n || gj >= n) continue;
+    const int gi = (int)(e / n), gj = (int)(e % n);
+    if (gi > gj) continue;
+    const int bi = gi / kTM, bj = gj / kTN;
+    const int b = block_index(bi, bj, nct);
+    const size_t off = (size_t)(gi - bi * kTM) * kTN + (gj - bj * kTN);
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += P[((long long)sp * npairs + pr) * kTile * kTile + rc];
+    for (int sp = 0; sp < nsplit; ++sp) s += P[((size_t)sp * nblocks + b) * kTM * kTN + off];
     const int ei = rowexp[gi], ej = rowexp[gj];
     const double v = (ei > -1000 && ej > -1000) ? ldexp(s, ei + ej) : 0.0;
     G[(long long)gi * n + gj] = v;
@@ -353,7 +384,7 @@ __global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int ntiles
 }
 
 struct TcPlan {
-  int nrows, ntiles, npairs, nsplit, kb_per_split, kb_total;
+  int nrows, nrt, nct, nblocks, nsplit, kb_per_split, kb_total;
   long long K, Kp;
 };
 
@@ -363,11 +394,14 @@ TcPlan tc_plan(const int n[3], int mode, int sm_count) {
   p.K = (long long)n[0] * n[1] * n[2] / p.nrows;
   p.Kp = (p.K + kKB - 1) / kKB * kKB;
   p.kb_total = (int)(p.Kp / kKB);
-  p.ntiles = (p.nrows + kTile - 1) / kTile;
-  p.npairs = p.ntiles * (p.ntiles + 1) / 2;
-  // one wave: about sm_count CTAs, splits made of whole 256-deep chunks
+  p.nrt = (p.nrows + kTM - 1) / kTM;
+  p.nct = (p.nrows + kTN - 1) / kTN;
+  p.nblocks = block_count(p.nrt, p.nct);
+  // about one wave of CTAs; splits of whole 256-deep chunks, at most 256 chunks
+  // each so that the int64 sums stay below 2^62
   const int chunks = (p.kb_total + kChunkBlocks - 1) / kChunkBlocks;
-  int want = std::max(1, sm_count / p.npairs);
+  int want = std::max(1, sm_count / p.nblocks);
+  want = std::max(want, (chunks + 255) / 256);
   want = std::min(want, chunks);
   const int chunks_per_split = (chunks + want - 1) / want;
   p.kb_per_split = chunks_per_split * kChunkBlocks;
@@ -381,7 +415,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   std::call_once(once, [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
     else
@@ -390,22 +425,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long Kp, int nrows, int box_rows) {
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nrows, (cuuint64_t)kSlices};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * nrows};
+  cuuint32_t box[3] = {kKB, (cuuint32_t)box_rows, kSlices};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(TK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return map;
+}
+
 }  // namespace
 
 size_t gram_sliced_scratch_bytes(const int n[3], int mode) {
   const TcPlan p = tc_plan(n, mode, 152);
   size_t b = 0;
-  b += carve_bytes<unsigned long long>(p.nrows);                        // row max bits
-  b += carve_bytes<int>(p.nrows);                                       // row exponents
-  b += carve_bytes<__nv_bfloat16>((size_t)kSlices * p.nrows * p.Kp);    // slices
-  b += carve_bytes<double>((size_t)p.nsplit * p.npairs * kTile * kTile);  // partials
+  b += carve_bytes<unsigned long long>(p.nrows);                          // row max bits
+  b += carve_bytes<int>(p.nrows);                                         // row exponents
+  b += carve_bytes<__nv_bfloat16>((size_t)kSlices * p.nrows * p.Kp);      // slices
+  b += carve_bytes<double>((size_t)p.nsplit * p.nblocks * kTM * kTN);     // partials
   return b + 4096;
 }
 
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s) {
   // one plan (for 152 SMs) fixes both the scratch layout and the grid
-  TcPlan p = tc_plan(n, mode, 152);
+  const TcPlan p = tc_plan(n, mode, 152);
   char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   size_t off = 0;
   auto carve = [&](size_t bytes) {
@@ -416,7 +464,7 @@ void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void
   unsigned long long* rowmax = (unsigned long long*)carve(sizeof(unsigned long long) * p.nrows);
   int* rowexp = (int*)carve(sizeof(int) * p.nrows);
   __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)kSlices * p.nrows * p.Kp);
-  double* P = (double*)carve(sizeof(double) * (size_t)p.nsplit * p.npairs * kTile * kTile);
+  double* P = (double*)carve(sizeof(double) * (size_t)p.nsplit * p.nblocks * kTM * kTN);
 
   TK_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * p.nrows, s));
   if (mode == 2) {
@@ -434,28 +482,19 @@ void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void
     k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S);
     TK_LAUNCH("k_slice");
   }
-  // tensor map over the slices: dims (Kp, nrows, 6), box (32, 128, 6), 64-byte swizzle
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
-  CUtensorMap map;
-  std::memset(&map, 0, sizeof(map));
-  cuuint64_t dims[3] = {(cuuint64_t)p.Kp, (cuuint64_t)p.nrows, (cuuint64_t)kSlices};
-  cuuint64_t strides[2] = {(cuuint64_t)p.Kp * 2, (cuuint64_t)p.Kp * 2 * p.nrows};
-  cuuint32_t box[3] = {kKB, kTile, kSlices};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) fail(TK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, kTM);
+  const CUtensorMap mapB = slice_map(enc, S, p.Kp, p.nrows, kTN);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   });
-  TcArgs a{p.nrows, p.ntiles, p.npairs, p.kb_per_split, p.kb_total, P, err};
-  k_gram_tc<<<dim3(p.npairs, p.nsplit), kThreads, kSmemBytes, s>>>(map, a);
+  TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.kb_per_split, p.kb_total, P, err};
+  k_gram_tc<<<dim3(p.nblocks, p.nsplit), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
   TK_LAUNCH("k_gram_tc");
-  const long long total = (long long)p.npairs * kTile * kTile;
-  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, p.nsplit, p.ntiles,
+  const long long total = (long long)p.nrows * p.nrows;
+  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks,
                                                                                       p.nrows, rowexp, G);
   TK_LAUNCH("k_tc_reduce");
 }
