@@ -57,10 +57,20 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, int n, int m) {
+// The panel Y (n x m) and the factor Q live in shared memory when 2 n m
+// doubles fit (otherwise in global memory); one warp per trailing column.
+template <bool kShared>
+__global__ void __launch_bounds__(1024) k_householder_qr(double* Yg, double* Qg, int n, int m) {
+  extern __shared__ double qr_sm[];
   __shared__ double beta[kMaxM];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* Y = kShared ? qr_sm : Yg;
+  double* Q = kShared ? qr_sm + (size_t)n * m : Qg;
+  if (kShared) {
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = Yg[e];
+    __syncthreads();
+  }
   for (int j = 0; j < m; ++j) {
     double* y = Y + (long long)j * n;
     double ss = 0.0;
@@ -83,7 +93,6 @@ __global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, in
     }
     __syncthreads();
     const double bj = beta[j];
-    // trailing columns: one warp per column
     for (int c = j + 1 + w; c < m; c += nw) {
       double* yc = Y + (long long)c * n;
       double d = 0.0;
@@ -95,8 +104,10 @@ __global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, in
     __syncthreads();
   }
   // Q = H_0 ... H_{m-1} [I; 0]
-  for (int c = 0; c < m; ++c)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Q[(long long)c * n + i] = (i == c) ? 1.0 : 0.0;
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+    const int c = e / n, i = e % n;
+    Q[e] = (i == c) ? 1.0 : 0.0;
+  }
   __syncthreads();
   for (int j = m - 1; j >= 0; --j) {
     const double bj = beta[j];
@@ -113,6 +124,8 @@ __global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, in
     }
     __syncthreads();
   }
+  if (kShared)
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) Qg[e] = Q[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -123,16 +136,17 @@ __global__ void __launch_bounds__(512) k_householder_qr(double* Y, double* Q, in
 // when |a_pq| <= 1e-18 |A|_F; sweeps stop when none is applied.
 // Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Hin, int m, double* lam,
-                                                double* Vout, int* sweeps_out) {
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Hin, int m, double* lam,
+                                                 double* Vout, int* sweeps_out) {
   extern __shared__ double sm[];
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
+  const int np = mp / 2;        // planes per step
   double* A = sm;
   double* V = A + mp * mp;
-  double* cs = V + mp * mp;  // c, s per pair
+  double* cs = V + mp * mp;  // c, s per plane
   int* pp = (int*)(cs + mp);
-  int* qq = pp + mp / 2;
-  int* flag = qq + mp / 2;
+  int* qq = pp + np;
+  int* flag = qq + np;
   __shared__ double red[32];
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
     const int i = e / mp, j = e % mp;
@@ -148,9 +162,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Hin, 
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int st = 0; st < mp - 1; ++st) {
-      if (threadIdx.x < mp / 2) {
+      // planes of this step and their rotations
+      if (threadIdx.x < np) {
         const int k = threadIdx.x;
-        // positions k and mp-1-k; position 0 is fixed, others rotate by st
         const int pos0 = k, pos1 = mp - 1 - k;
         const int a = (pos0 == 0) ? 0 : 1 + (pos0 - 1 + st) % (mp - 1);
         const int b = 1 + (pos1 - 1 + st) % (mp - 1);
@@ -171,37 +185,52 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Hin, 
         cs[2 * k + 1] = s;
       }
       __syncthreads();
-      // rows p, q  <-  J^T A
-      for (int e = threadIdx.x; e < (mp / 2) * mp; e += blockDim.x) {
-        const int k = e / mp, col = e % mp;
-        const double s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        const double c = cs[2 * k];
-        const int p = pp[k], q = qq[k];
-        const double ap = A[p * mp + col], aq = A[q * mp + col];
-        A[p * mp + col] = c * ap - s * aq;
-        A[q * mp + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q  <-  A J ; V <- V J
-      for (int e = threadIdx.x; e < (mp / 2) * mp; e += blockDim.x) {
-        const int k = e / mp, row = e % mp;
-        const double s = cs[2 * k + 1];
-        if (s == 0.0) continue;
-        const double c = cs[2 * k];
-        const int p = pp[k], q = qq[k];
-        const double ap = A[row * mp + p], aq = A[row * mp + q];
-        A[row * mp + p] = c * ap - s * aq;
-        A[row * mp + q] = s * ap + c * aq;
-        const double vp = V[row * mp + p], vq = V[row * mp + q];
-        V[row * mp + p] = c * vp - s * vq;
-        V[row * mp + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      if (threadIdx.x < mp / 2 && cs[2 * threadIdx.x + 1] != 0.0) {
-        const int p = pp[threadIdx.x], q = qq[threadIdx.x];
-        A[p * mp + q] = 0.0;
-        A[q * mp + p] = 0.0;
+      // A <- J^T A J on every 2 x 2 block (plane a rows, plane b columns),
+      // upper blocks computed and mirrored; V <- V J on plane column pairs
+      const int nblk = np * (np + 1) / 2;
+      for (int e = threadIdx.x; e < nblk + np * mp; e += blockDim.x) {
+        if (e < nblk) {
+          int a = 0, r = e;
+          while (r >= np - a) {
+            r -= np - a;
+            ++a;
+          }
+          const int b = a + r;
+          const double ca = cs[2 * a], sa = cs[2 * a + 1], cb = cs[2 * b], sb = cs[2 * b + 1];
+          if (sa == 0.0 && sb == 0.0) continue;
+          const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
+          const double m00 = A[pa * mp + pb], m01 = A[pa * mp + qb], m10 = A[qa * mp + pb], m11 = A[qa * mp + qb];
+          // rows: [c -s; s c] M
+          const double r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+          const double r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+          // columns: (.) [c s; -s c]
+          double n00 = cb * r00 - sb * r01, n01 = sb * r00 + cb * r01;
+          double n10 = cb * r10 - sb * r11, n11 = sb * r10 + cb * r11;
+          if (a == b && sa != 0.0) {
+            n01 = 0.0;
+            n10 = 0.0;
+          }
+          A[pa * mp + pb] = n00;
+          A[pa * mp + qb] = n01;
+          A[qa * mp + pb] = n10;
+          A[qa * mp + qb] = n11;
+          if (a != b) {
+            A[pb * mp + pa] = n00;
+            A[qb * mp + pa] = n01;
+            A[pb * mp + qa] = n10;
+            A[qb * mp + qa] = n11;
+          }
+        } else {
+          const int f = e - nblk;
+          const int k = f / mp, row = f % mp;
+          const double s = cs[2 * k + 1];
+          if (s == 0.0) continue;
+          const double c = cs[2 * k];
+          const int p = pp[k], q = qq[k];
+          const double vp = V[row * mp + p], vq = V[row * mp + q];
+          V[row * mp + p] = c * vp - s * vq;
+          V[row * mp + q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }
@@ -258,15 +287,26 @@ __global__ void k_canonical_sign(double* V, int n, int m) {
 }
 
 __global__ void k_trace(const double* G, int n, double* out) {
+  __shared__ double ss[256], sc[256];
+  double s = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = G[(long long)i * n + i];
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0, c = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double x = G[(long long)i * n + i];
-      const double t = s + x;
-      c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-      s = t;
+    double a = 0.0, ac = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const double x = ss[t], u = a + x;
+      ac += (fabs(a) >= fabs(x)) ? (a - u) + x : (x - u) + a;
+      a = u;
+      ac += sc[t];
     }
-    out[0] = s + c;
+    out[0] = a + ac;
   }
 }
 
@@ -339,6 +379,18 @@ size_t sym_eig_scratch_doubles(int n, int m) {
   return 3ull * n * ms + 2ull * ms * ms + ms + 64 + (size_t)n * n;
 }
 
+static constexpr size_t kQrSmemMax = 200 * 1024;
+
+static void householder_qr(double* Y, double* Q, int n, int m, cudaStream_t s) {
+  const size_t need = 2ull * n * m * sizeof(double);
+  if (need <= kQrSmemMax) {
+    k_householder_qr<true><<<1, 1024, need, s>>>(Y, Q, n, m);
+  } else {
+    k_householder_qr<false><<<1, 1024, 0, s>>>(Y, Q, n, m);
+  }
+  TK_LAUNCH("k_householder_qr");
+}
+
 static size_t jacobi_smem(int m) {
   const int mp = (m + 1) & ~1;
   return (2ull * mp * mp + mp) * sizeof(double) + (mp + 4) * sizeof(int);
@@ -351,6 +403,8 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
   if (!attr_set) {
     TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)jacobi_smem(kMaxM)));
+    TK_CUDA(cudaFuncSetAttribute(k_householder_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kQrSmemMax));
     attr_set = true;
   }
   const int ms = subspace_cols(n, m);
@@ -361,13 +415,13 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
   double* VH = H + (size_t)ms * ms;
   double* lsub = VH + (size_t)ms * ms;
   double* misc = lsub + ms;  // [0] trace, [8..] sweeps
-  k_trace<<<1, 32, 0, s>>>(G, n, trace_out ? trace_out : misc);
+  k_trace<<<1, 256, 0, s>>>(G, n, trace_out ? trace_out : misc);
   TK_LAUNCH("k_trace");
   if (ms == n) {
     // whole matrix: Jacobi on G directly
     k_copy_rows<<<64, 256, 0, s>>>(G, H, n);
     TK_LAUNCH("k_copy_rows");
-    k_jacobi<<<1, 512, jacobi_smem(n), s>>>(H, n, lsub, VH, (int*)(misc + 8));
+    k_jacobi<<<1, 1024, jacobi_smem(n), s>>>(H, n, lsub, VH, (int*)(misc + 8));
     TK_LAUNCH("k_jacobi");
     // first m columns of V_H (n x n) into V (n x m)
     TK_CUDA(cudaMemcpy2DAsync(V, sizeof(double) * m, VH, sizeof(double) * n, sizeof(double) * m, n,
@@ -381,8 +435,7 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
       GemmDesc d{n, ms, n, 1, G, 0, n, 1, src, 0, 1, n, W, 0, 1, n};
       gemm_f64(d, s);
       TK_CUDA(cudaMemcpyAsync(Y, W, sizeof(double) * (size_t)n * ms, cudaMemcpyDeviceToDevice, s));
-      k_householder_qr<<<1, 512, 0, s>>>(Y, Q, n, ms);
-      TK_LAUNCH("k_householder_qr");
+      householder_qr(Y, Q, n, ms, s);
     }
     // W = G Q ; H = Q^T W
     GemmDesc d1{n, ms, n, 1, G, 0, n, 1, Q, 0, 1, n, W, 0, 1, n};
@@ -391,7 +444,7 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
     gemm_f64(d2, s);
     k_symmetrize<<<4, 256, 0, s>>>(H, ms);
     TK_LAUNCH("k_symmetrize");
-    k_jacobi<<<1, 512, jacobi_smem(ms), s>>>(H, ms, lsub, VH, (int*)(misc + 8));
+    k_jacobi<<<1, 1024, jacobi_smem(ms), s>>>(H, ms, lsub, VH, (int*)(misc + 8));
     TK_LAUNCH("k_jacobi");
     // leading m Ritz vectors V = Q V_H[:, :m] (row-major n x m)
     GemmDesc d3{n, m, ms, 1, Q, 0, 1, n, VH, 0, ms, 1, V, 0, m, 1};

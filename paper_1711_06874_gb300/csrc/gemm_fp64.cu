@@ -240,175 +240,258 @@ extern "C" int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, do
 namespace tk {
 
 // ---------------------------------------------------------------------------
-// Strided batched GEMM.
+// Strided batched GEMM.  Tile shapes (BM x BN, 16-deep K steps, 256 threads
+// as 16 x 16, each thread BM/16 x BN/16 outputs) are picked from the output
+// shape so that rank-sized dimensions do not waste a 64-wide tile; products
+// with few outputs use one warp per output instead.
 // ---------------------------------------------------------------------------
 namespace {
 
-__device__ __forceinline__ void load_a_tile(const GemmDesc& d, const double* A, int i0, int k0,
-                                            double (*S)[TB + 1]) {
+template <int BM, int BN>
+__device__ __forceinline__ void load_tiles(const GemmDesc& d, const double* A, const double* B, int i0, int j0, int k0,
+                                           double (*As)[BM + 1], double (*Bs)[BN + 1]) {
   const int t = threadIdx.x;
-  if (d.sAk == 1) {
-    const int i = t >> 2, kq = (t & 3) * 4;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = k0 + kq + q;
-      S[kq + q][i] = (i0 + i < d.M && k < d.K) ? A[(long long)(i0 + i) * d.sAi + k] : 0.0;
+  for (int q = 0; q < BM / 16; ++q) {
+    const int e = t + 256 * q;
+    int i, k;
+    if (d.sAk == 1) {
+      i = e / KS;
+      k = e % KS;
+    } else {
+      k = e / BM;
+      i = e % BM;
     }
-  } else {
-    const int kk = t >> 4, iq = (t & 15) * 4;
+    const int gi = i0 + i, gk = k0 + k;
+    As[k][i] = (gi < d.M && gk < d.K) ? A[(long long)gi * d.sAi + (long long)gk * d.sAk] : 0.0;
+  }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + iq + q, k = k0 + kk;
-      S[kk][iq + q] = (i < d.M && k < d.K) ? A[(long long)i * d.sAi + (long long)k * d.sAk] : 0.0;
+  for (int q = 0; q < BN / 16; ++q) {
+    const int e = t + 256 * q;
+    int j, k;
+    if (d.sBj == 1) {
+      k = e / BN;
+      j = e % BN;
+    } else {
+      j = e / KS;
+      k = e % KS;
     }
+    const int gj = j0 + j, gk = k0 + k;
+    Bs[k][j] = (gj < d.N && gk < d.K) ? B[(long long)gk * d.sBk + (long long)gj * d.sBj] : 0.0;
   }
 }
 
-__device__ __forceinline__ void load_b_tile(const GemmDesc& d, const double* B, int k0, int j0,
-                                            double (*S)[TB + 1]) {
-  const int t = threadIdx.x;
-  if (d.sBk == 1 && d.sBj != 1) {
-    const int j = t >> 2, kq = (t & 3) * 4;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = k0 + kq + q;
-      S[kq + q][j] = (j0 + j < d.N && k < d.K) ? B[k + (long long)(j0 + j) * d.sBj] : 0.0;
-    }
-  } else {
-    const int kk = t >> 4, jq = (t & 15) * 4;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = j0 + jq + q, k = k0 + kk;
-      S[kk][jq + q] = (j < d.N && k < d.K) ? B[(long long)k * d.sBk + (long long)j * d.sBj] : 0.0;
-    }
-  }
+__device__ __forceinline__ void neum(double& s, double& c, double x) {
+  const double t = s + x;
+  c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+  s = t;
 }
 
-template <bool kErr>
+template <int BM, int BN, bool kErr>
 __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, const double* __restrict__ R,
                                                   double* __restrict__ partials) {
-  __shared__ double As[KS][TB + 1];
-  __shared__ double Bs[KS][TB + 1];
+  constexpr int RM = BM / 16, RN = BN / 16;
+  __shared__ double As[KS][BM + 1];
+  __shared__ double Bs[KS][BN + 1];
   const int b = blockIdx.z;
   const double* A = d.A + (long long)b * d.sAb;
   const double* B = d.B + (long long)b * d.sBb;
-  const int i0 = blockIdx.y * TB, j0 = blockIdx.x * TB;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
+  double acc[RM][RN];
+#pragma unroll
+  for (int p = 0; p < RM; ++p)
+#pragma unroll
+    for (int q = 0; q < RN; ++q) acc[p][q] = 0.0;
   for (int k0 = 0; k0 < d.K; k0 += KS) {
-    load_a_tile(d, A, i0, k0, As);
-    load_b_tile(d, B, k0, j0, Bs);
+    load_tiles<BM, BN>(d, A, B, i0, j0, k0, As, Bs);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
-      double a[4], bb[4];
+      double a[RM], bb[RN];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[k][ty * 4 + q];
-        bb[q] = Bs[k][tx * 4 + q];
-      }
+      for (int p = 0; p < RM; ++p) a[p] = As[k][ty * RM + p];
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int q = 0; q < RN; ++q) bb[q] = Bs[k][tx * RN + q];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], bb[q], acc[p][q]);
+      for (int p = 0; p < RM; ++p)
+#pragma unroll
+        for (int q = 0; q < RN; ++q) acc[p][q] = fma(a[p], bb[q], acc[p][q]);
     }
     __syncthreads();
   }
   if (!kErr) {
     double* C = d.C + (long long)b * d.sCb;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < RM; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + ty * 4 + p, j = j0 + tx * 4 + q;
+      for (int q = 0; q < RN; ++q) {
+        const int i = i0 + ty * RM + p, j = j0 + tx * RN + q;
         if (i < d.M && j < d.N) C[(long long)i * d.sCi + (long long)j * d.sCj] = acc[p][q];
       }
   } else {
     const double* Rb = R + (long long)b * d.sCb;
     double ds = 0.0, dc = 0.0, fs = 0.0, fc = 0.0;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < RM; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + ty * 4 + p, j = j0 + tx * 4 + q;
+      for (int q = 0; q < RN; ++q) {
+        const int i = i0 + ty * RM + p, j = j0 + tx * RN + q;
         if (i < d.M && j < d.N) {
           const double r = Rb[(long long)i * d.sCi + (long long)j * d.sCj];
           const double e = r - acc[p][q];
-          double t = ds + e * e;
-          dc += (fabs(ds) >= e * e) ? (ds - t) + e * e : (e * e - t) + ds;
-          ds = t;
-          t = fs + r * r;
-          fc += (fabs(fs) >= r * r) ? (fs - t) + r * r : (r * r - t) + fs;
-          fs = t;
+          neum(ds, dc, e * e);
+          neum(fs, fc, r * r);
         }
       }
+    // fixed-shape tree over the block's threads, compensation carried along
     __shared__ double red[4][NT];
     red[0][threadIdx.x] = ds;
     red[1][threadIdx.x] = dc;
     red[2][threadIdx.x] = fs;
     red[3][threadIdx.x] = fc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-      for (int t = 0; t < NT; ++t) {
-        double v = red[0][t], tt = s0 + v;
-        c0 += (fabs(s0) >= fabs(v)) ? (s0 - tt) + v : (v - tt) + s0;
-        s0 = tt;
-        c0 += red[1][t];
-        v = red[2][t];
-        tt = s1 + v;
-        c1 += (fabs(s1) >= fabs(v)) ? (s1 - tt) + v : (v - tt) + s1;
-        s1 = tt;
-        c1 += red[3][t];
+    for (int w = NT / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        double s0 = red[0][threadIdx.x], c0 = red[1][threadIdx.x] + red[1][threadIdx.x + w];
+        neum(s0, c0, red[0][threadIdx.x + w]);
+        double s1 = red[2][threadIdx.x], c1 = red[3][threadIdx.x] + red[3][threadIdx.x + w];
+        neum(s1, c1, red[2][threadIdx.x + w]);
+        red[0][threadIdx.x] = s0;
+        red[1][threadIdx.x] = c0;
+        red[2][threadIdx.x] = s1;
+        red[3][threadIdx.x] = c1;
       }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
       const long long blin = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-      partials[4 * blin + 0] = s0;
-      partials[4 * blin + 1] = c0;
-      partials[4 * blin + 2] = s1;
-      partials[4 * blin + 3] = c1;
+      partials[4 * blin + 0] = red[0][0];
+      partials[4 * blin + 1] = red[1][0];
+      partials[4 * blin + 2] = red[2][0];
+      partials[4 * blin + 3] = red[3][0];
     }
   }
 }
 
-__global__ void k_err_final(const double* part, long long nparts, double* out) {
-  if (threadIdx.x != 0) return;
+// Sum of (R - C)^2 and R^2 partials: 1024 threads, each a Neumaier sum over a
+// fixed stride of blocks, then a fixed tree.
+__global__ void __launch_bounds__(1024) k_err_final(const double* part, long long nparts, double* out) {
   double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-  for (long long b = 0; b < nparts; ++b) {
-    double v = part[4 * b], t = s0 + v;
-    c0 += (fabs(s0) >= fabs(v)) ? (s0 - t) + v : (v - t) + s0;
-    s0 = t;
+  for (long long b = threadIdx.x; b < nparts; b += blockDim.x) {
+    neum(s0, c0, part[4 * b]);
     c0 += part[4 * b + 1];
-    v = part[4 * b + 2];
-    t = s1 + v;
-    c1 += (fabs(s1) >= fabs(v)) ? (s1 - t) + v : (v - t) + s1;
-    s1 = t;
+    neum(s1, c1, part[4 * b + 2]);
     c1 += part[4 * b + 3];
   }
-  out[0] = s0 + c0;
-  out[1] = s1 + c1;
+  __shared__ double red[4][1024];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = c0;
+  red[2][threadIdx.x] = s1;
+  red[3][threadIdx.x] = c1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a0 = red[0][threadIdx.x], a1 = red[1][threadIdx.x] + red[1][threadIdx.x + w];
+      neum(a0, a1, red[0][threadIdx.x + w]);
+      double b0 = red[2][threadIdx.x], b1 = red[3][threadIdx.x] + red[3][threadIdx.x + w];
+      neum(b0, b1, red[2][threadIdx.x + w]);
+      red[0][threadIdx.x] = a0;
+      red[1][threadIdx.x] = a1;
+      red[2][threadIdx.x] = b0;
+      red[3][threadIdx.x] = b1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = red[0][0] + red[1][0];
+    out[1] = red[2][0] + red[3][0];
+  }
 }
 
-dim3 gemm_grid(const GemmDesc& d) { return dim3((d.N + TB - 1) / TB, (d.M + TB - 1) / TB, d.batch); }
+// One warp per output element; lanes stride over K, fixed shuffle tree.
+__global__ void k_gemm_warp(GemmDesc d) {
+  const long long per_batch = (long long)d.M * d.N;
+  const long long total = per_batch * d.batch;
+  const int lane = threadIdx.x & 31;
+  for (long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; o < total;
+       o += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int b = (int)(o / per_batch);
+    const long long r = o - (long long)b * per_batch;
+    const int i = (int)(r / d.N), j = (int)(r % d.N);
+    const double* A = d.A + (long long)b * d.sAb + (long long)i * d.sAi;
+    const double* B = d.B + (long long)b * d.sBb + (long long)j * d.sBj;
+    double acc = 0.0;
+    for (int k = lane; k < d.K; k += 32) acc = fma(A[(long long)k * d.sAk], B[(long long)k * d.sBk], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) d.C[(long long)b * d.sCb + (long long)i * d.sCi + (long long)j * d.sCj] = acc;
+  }
+}
+
+enum class Tile { k64x64, k128x32, k256x16, k16x16 };
+
+Tile pick_tile(const GemmDesc& d) {
+  if (d.M <= 16 && d.N <= 16) return Tile::k16x16;
+  if (d.N <= 16) return Tile::k256x16;
+  if (d.N <= 32) return Tile::k128x32;
+  return Tile::k64x64;
+}
+
+template <int BM, int BN>
+dim3 grid_of(const GemmDesc& d) {
+  return dim3((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.batch);
+}
+
+template <int BM, int BN, bool kErr>
+void launch(const GemmDesc& d, const double* R, double* partials, cudaStream_t s) {
+  k_gemm_f64<BM, BN, kErr><<<grid_of<BM, BN>(d), NT, 0, s>>>(d, R, partials);
+  TK_LAUNCH("k_gemm_f64");
+}
+
+template <bool kErr>
+dim3 dispatch(const GemmDesc& d, const double* R, double* partials, cudaStream_t s, bool run) {
+  switch (pick_tile(d)) {
+    case Tile::k16x16:
+      if (run) launch<16, 16, kErr>(d, R, partials, s);
+      return grid_of<16, 16>(d);
+    case Tile::k256x16:
+      if (run) launch<256, 16, kErr>(d, R, partials, s);
+      return grid_of<256, 16>(d);
+    case Tile::k128x32:
+      if (run) launch<128, 32, kErr>(d, R, partials, s);
+      return grid_of<128, 32>(d);
+    default:
+      if (run) launch<64, 64, kErr>(d, R, partials, s);
+      return grid_of<64, 64>(d);
+  }
+}
 
 }  // namespace
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  k_gemm_f64<false><<<gemm_grid(d), NT, 0, s>>>(d, nullptr, nullptr);
-  TK_LAUNCH("k_gemm_f64");
+  const dim3 g = dispatch<false>(d, nullptr, nullptr, s, false);
+  const long long ctas = (long long)g.x * g.y * g.z;
+  const long long outs = (long long)d.M * d.N * d.batch;
+  if (ctas < 76 && outs <= (1LL << 18)) {
+    // few tiles: one warp per output keeps every SM busy
+    const long long warps = outs;
+    const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 4096);
+    k_gemm_warp<<<blocks, 256, 0, s>>>(d);
+    TK_LAUNCH("k_gemm_warp");
+    return;
+  }
+  dispatch<false>(d, nullptr, nullptr, s, true);
 }
 
 size_t gemm_err_partials(const GemmDesc& d) {
-  const dim3 g = gemm_grid(d);
+  const dim3 g = dispatch<true>(d, nullptr, nullptr, nullptr, false);
   return 4ull * g.x * g.y * g.z;
 }
 
-void gemm_f64_err(const GemmDesc& d, const double* R, double* partials, double* out_dev,
-                  cudaStream_t s) {
-  const dim3 g = gemm_grid(d);
-  k_gemm_f64<true><<<g, NT, 0, s>>>(d, R, partials);
-  TK_LAUNCH("k_gemm_f64_err");
-  k_err_final<<<1, 32, 0, s>>>(partials, (long long)g.x * g.y * g.z, out_dev);
+void gemm_f64_err(const GemmDesc& d, const double* R, double* partials, double* out_dev, cudaStream_t s) {
+  const dim3 g = dispatch<true>(d, R, partials, s, true);
+  k_err_final<<<1, 1024, 0, s>>>(partials, (long long)g.x * g.y * g.z, out_dev);
   TK_LAUNCH("k_err_final");
 }
 

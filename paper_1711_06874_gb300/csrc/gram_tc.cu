@@ -3,10 +3,10 @@
 //
 // Slicing (after Ozaki, Ogita, Oishi and Rump's error-free splitting).  Each
 // row i of A is scaled by 2^-e_i with e_i the binary exponent of its largest
-// entry, so every scaled entry x lies in (-1, 1).  It is then written exactly
-// as x = sum_{s<6} d_s 2^(-7-8s) + O(2^-48) with balanced integer digits
-// |d_s| <= 128 (d_s = round of the remaining scaled residual), and slice s
-// stores d_s 2^(-7-8s): at most 8 significant bits, so exact in BF16.
+// entry, so every scaled entry x lies in (-1, 1).  x 2^47 is rounded to an
+// integer and cut into balanced base-256 digits, x = sum_{s<6} d_s 2^(-7-8s)
+// + O(2^-48) with |d_s| <= 128, using integer operations on the FP64 bits;
+// slice s stores d_s 2^(-7-8s): at most 8 significant bits, exact in BF16.
 //
 // Products.  slice_s(i) slice_t(j) = d d' 2^(-14-8(s+t)) is exact, and the
 // pairs of equal weight w = s + t share an accumulator in TMEM:
@@ -149,16 +149,31 @@ __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, 
     const int row = r0 + q;
     const long long c = c0 + tx;
     if (row >= nrows || c >= Kp) continue;
-    double x = tile[q][tx];
+    // T = round(|x| 2^(47 - e)) from the FP64 bits with integer operations
+    // (|x| < 2^e, so T < 2^47), then balanced base-256 digits from the bottom:
+    // x 2^(7 - e) = sum_s d_s 2^(-8s) + O(2^-41), |d_s| <= 128.
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[q][tx]);
+    const int ex = (int)((bits >> 52) & 0x7FF);
     const int e = rowexp[row];
-    x = (e > -1000) ? ldexp(x, -e) * 128.0 : 0.0;  // |x| < 128 after scaling by 2^(7 - e)
+    long long T = 0;
+    if (ex != 0 && e > -1000) {
+      const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int rs = 1028 + e - ex;  // right shift of the 53-bit mantissa, >= 6
+      if (rs < 64) T = (long long)((mant + (1ull << (rs - 1))) >> rs);
+      if (bits >> 63) T = -T;
+    }
+    int d[kSlices];
+#pragma unroll
+    for (int s = kSlices - 1; s >= 1; --s) {
+      const long long r = ((T + 128) & 255) - 128;
+      d[s] = (int)r;
+      T = (T - r) >> 8;
+    }
+    d[0] = (int)T;
     const size_t base = (size_t)row * Kp + c;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-      const double d = rint(x);  // balanced digit, |d| <= 128
-      x = (x - d) * 256.0;       // exact
-      S[s * plane + base] = __float2bfloat16_rn((float)ldexp(d, -7 - 8 * s));
-    }
+    for (int s = 0; s < kSlices; ++s)
+      S[s * plane + base] = __float2bfloat16_rn(__int2float_rn(d[s]) * __int_as_float((127 - 7 - 8 * s) << 23));
   }
 }
 
