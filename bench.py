@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Matérn Tucker-HOSVD solves/s at rel err 1e-6 vs FP64 path; p50/p99 latency"
 WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, eps=1e-6, "
-            "rank cap 32; one solve (sample, Gram, eigenpairs, ranks, core, rel_error) per step")
+            "rank cap 64; one solve (sample, Gram, eigenpairs, ranks, core, rel_error) per step")
 
 
 def parse():

@@ -351,44 +351,65 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     pf.begin(TK_STAGE_EVAL, s);
     eval_tensor_f64(*kernel, *grid, F, table, s);
     pf.end(s);
-    pf.begin(TK_STAGE_NORM, s);
-    norm2_f64(F, N, small, nscr, s);
-    pf.end(s);
+    // Gram, then the leading eigenpairs in two phases: first 16 pairs (enough
+    // whenever the rank is below 16), then the full rank cap only for the
+    // modes whose rank rule asks for more than the pairs computed.
+    int mA[3];
+    for (int a = 0; a < 3; ++a) mA[a] = (o.rfix[a] > 0) ? m[a] : std::min(m[a], 16);
     for (int a = 0; a < nmodes; ++a) {
       pf.begin(TK_STAGE_GRAM, s);
       if (sliced)
-        gram_sliced_bf16(F, n, a, G[a], gscr, ranks_dev + 8, s);
+        gram_sliced_bf16(F, n, a, G[a], gscr, ranks_dev + 16, s);
       else
         gram_f64(F, n, a, G[a], gscr, s);
       pf.end(s);
       pf.begin(TK_STAGE_EIG, s);
-      sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
+      sym_eig_topm(G[a], n[a], mA[a], lam[a], V[a], small + 1 + a, escr, s);
       pf.end(s);
       pf.begin(TK_STAGE_RANK, s);
-      rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
-                n[a], ranks_dev + 2 * a, s);
+      rank_rule(lam[a], mA[a], small + 1 + a, small + 1, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
+                n[a], ranks_dev + 4 * a, s);
       pf.end(s);
     }
-    int hr[16];
+    int hr[20];
     double hsmall[4];
-    TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaMemcpyAsync(hsmall, small, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 20, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    if (hr[16] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+    bool again = false;
+    for (int a = 0; a < nmodes; ++a) {
+      if (mA[a] < m[a] && hr[4 * a + 2] > mA[a]) {
+        pf.begin(TK_STAGE_EIG, s);
+        sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
+        pf.end(s);
+        pf.begin(TK_STAGE_RANK, s);
+        rank_rule(lam[a], m[a], small + 1 + a, small + 1, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
+                  n[a], ranks_dev + 4 * a, s);
+        pf.end(s);
+        mA[a] = m[a];
+        again = true;
+      }
+    }
+    if (again) {
+      TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 20, cudaMemcpyDeviceToHost, s));
+    }
+    // |F|^2 = trace(G_1) (compensated), the same sum in another order
+    TK_CUDA(cudaMemcpyAsync(hsmall, small + 1, sizeof(double) * 1, cudaMemcpyDeviceToHost, s));
     res = new tk_result();
     res->ctx = ctx;
     res->precision = o.precision;
     for (int a = 0; a < 3; ++a) {
       res->n[a] = n[a];
-      res->m[a] = m[a];
-      res->lam[a].resize(m[a]);
+      res->m[a] = mA[one ? 0 : a];
+      res->lam[a].resize(res->m[a]);
     }
     for (int a = 0; a < nmodes; ++a)
-      TK_CUDA(cudaMemcpyAsync(res->lam[a].data(), lam[a], sizeof(double) * m[a], cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaMemcpyAsync(res->lam[a].data(), lam[a], sizeof(double) * mA[a], cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
-    if (hr[8] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
     for (int a = 0; a < 3; ++a) {
       const int src = one ? 0 : a;
-      res->r[a] = hr[2 * src];
-      res->flags[a] = (uint32_t)hr[2 * src + 1];
+      res->r[a] = hr[4 * src];
+      res->flags[a] = (uint32_t)hr[4 * src + 1];
       if (one && a > 0) res->lam[a] = res->lam[0];
     }
     res->normF2 = hsmall[0];
@@ -397,7 +418,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
       TK_CUDA(cudaMalloc(&res->U[a], sizeof(double) * (size_t)n[a] * r[a]));
       const int src = one ? 0 : a;
       // first r columns of V (n x m, ld m) into U (n x r, ld r)
-      TK_CUDA(cudaMemcpy2DAsync(res->U[a], sizeof(double) * r[a], V[src], sizeof(double) * m[src],
+      TK_CUDA(cudaMemcpy2DAsync(res->U[a], sizeof(double) * r[a], V[src], sizeof(double) * mA[src],
                                 sizeof(double) * r[a], n[a], cudaMemcpyDeviceToDevice, s));
     }
     TK_CUDA(cudaMalloc(&res->core, sizeof(double) * (size_t)r[0] * r[1] * r[2]));
@@ -509,10 +530,13 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
     double* part = ctx->ws.take<double>(parts);
     double* sums = ctx->ws.take<double>(8);
     ctx->prof.begin(TK_STAGE_ERROR, s);
-    eval_tensor_f64(*kernel, *grid, F, table, s);
+    // F is resampled: the distinct-value table feeds the error epilogue
+    // directly on cubic isotropic grids, otherwise F is written out first
+    const bool tab = eval_table_f64(*kernel, *grid, table, s);
+    if (!tab) eval_tensor_f64(*kernel, *grid, F, table, s);
     recon_w2(res->core, r, res->U[0], r[0], res->U[1], r[1], n, W1, W2, s);
     d.A = W2;
-    gemm_f64_err(d, F, part, sums, s);
+    gemm_f64_err(d, tab ? nullptr : F, tab ? table : nullptr, n[0], part, sums, s);
     ctx->prof.end(s);
     double h[2];
     TK_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -32,6 +32,11 @@
 #define TK_HD inline
 #endif
 
+// Terms of Temme's series and of the backward recurrence that are
+// precomputed per order, so the device loops need no division.
+constexpr int kTemmeTerms = 48;   // x <= 1.5 converges in about 25 terms
+constexpr int kMillerTerms = 133;  // N = 12 + ceil(180 / x) <= 132 for x > 1.5
+
 struct tk_nu_consts {
   double nu;        // order
   double mu;        // nu - nord, in [-1/2, 1/2)
@@ -42,6 +47,11 @@ struct tk_nu_consts {
   double gmmu;      // Gamma(1 - mu)
   double mupi_sin;  // mu pi / sin(mu pi)
   double pref_log;  // (1 - nu) ln 2 - log Gamma(nu)
+  double inv_k2mu2[kTemmeTerms];  // 1 / (k^2 - mu^2)
+  double inv_kmmu[kTemmeTerms];   // 1 / (k - mu)
+  double inv_kpmu[kTemmeTerms];   // 1 / (k + mu)
+  double inv_k[kTemmeTerms];      // 1 / k
+  double Ck[kMillerTerms];        // (1/2 - mu)_k (1/2 + mu)_k / k!
 };
 
 // K_mu(x) and K_{mu+1}(x), both multiplied by e^x, for |mu| <= 1/2, x > 0.
@@ -60,12 +70,12 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
     double ck = 1.0;
     const double x2 = 0.25 * x * x;
     double s0 = f, s1 = p;
-    for (int k = 1; k < 200; ++k) {
+    for (int k = 1; k < kTemmeTerms; ++k) {
       const double dk = (double)k;
-      f = (dk * f + p + q) / (dk * dk - mu * mu);
-      p /= (dk - mu);
-      q /= (dk + mu);
-      ck *= x2 / dk;
+      f = (dk * f + p + q) * c.inv_k2mu2[k];
+      p *= c.inv_kmmu[k];
+      q *= c.inv_kpmu[k];
+      ck *= x2 * c.inv_k[k];
       const double d0 = ck * f;
       const double d1 = ck * (p - dk * f);
       s0 += d0;
@@ -77,27 +87,32 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
     *kmu1 = s1 * (2.0 / x) * ex;
     return;
   }
-  // Tricomi-U representation, Miller's backward recurrence.
-  // The backward recurrence reaches 1e-17 with N of about 12 + 180/x terms.
+  // Tricomi-U representation, Miller's backward recurrence on the
+  // unnormalised minimal solution u_k (u_{N+1} = 0, u_N = 1), accumulating
+  // sum_k C_k u_k on the way; S = sum / u_0 and U_1/U_0 = u_1 / u_0.
+  // The recurrence reaches 1e-17 with N of about 12 + 180/x terms; values are
+  // rescaled by 2^-600 whenever they pass 2^600.
   const int N = 12 + (int)ceil(180.0 / x);  // at most 132 for x > 1.5
   const double mu2 = mu * mu;
-  double ratio[136];  // ratio[k] = U_k / U_{k-1}, k = 1..N
-  double rnext = 0.0;
+  double u_next = 0.0, u = 1.0;  // u_{k+1}, u_k at k = N
+  double acc = c.Ck[N];
   for (int k = N; k >= 1; --k) {
     const double dk = (double)k;
-    rnext = 1.0 / (2.0 * (dk + x) - ((dk + 0.5) * (dk + 0.5) - mu2) * rnext);
-    ratio[k] = rnext;
+    const double u_prev = 2.0 * (dk + x) * u - ((dk + 0.5) * (dk + 0.5) - mu2) * u_next;  // u_{k-1}
+    u_next = u;
+    u = u_prev;
+    acc += c.Ck[k - 1] * u;
+    if (fabs(u) > 0x1p600) {
+      u *= 0x1p-600;
+      u_next *= 0x1p-600;
+      acc *= 0x1p-600;
+    }
   }
-  double s = 1.0, ck = 1.0, pk = 1.0;
-  for (int k = 1; k <= N; ++k) {
-    const double dk = (double)k;
-    ck *= ((dk - 0.5) * (dk - 0.5) - mu2) / dk;
-    pk *= ratio[k];
-    s += ck * pk;
-  }
-  const double k0 = sqrt(3.141592653589793238 / (2.0 * x)) / s;
+  // here u = u_0, u_next = u_1
+  const double inv_u0 = 1.0 / u;
+  const double k0 = sqrt(3.141592653589793238 / (2.0 * x)) / (acc * inv_u0);
   *kmu = k0;
-  *kmu1 = k0 * (x + mu + 0.5 - (0.25 - mu2) * ratio[1]) / x;
+  *kmu1 = k0 * (x + mu + 0.5 - (0.25 - mu2) * (u_next * inv_u0)) / x;
 }
 
 // K_nu(x) e^x for the order in c (nu = nord + mu), x > 0.

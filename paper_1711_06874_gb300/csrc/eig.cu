@@ -354,6 +354,7 @@ __global__ void k_rank(const double* lam, int m, const double* trace, const doub
   }
   int flags = 0;
   if (r > m) r = m + 1;
+  out[2] = r;  // before the cap; m + 1 means "more than the m computed"
   if (rfix > 0) {
     r = rfix < m ? rfix : m;
   } else if (r > rmax) {

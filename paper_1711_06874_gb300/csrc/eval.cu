@@ -111,6 +111,19 @@ __global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F) {
   }
 }
 
+bool eval_table_f64(const tk_kernel& kh, const tk_grid& gh, double* table, cudaStream_t s) {
+  if (!table_applicable(kh, gh)) return false;
+  const KernelDev k = make_kernel_dev(kh);
+  const int n = gh.n[0];
+  const long long Q = table_size(n);
+  const double h = (gh.kind == TK_VERTEX) ? gh.b[0] / (double)(n - 1) : gh.b[0] / (double)n;
+  const int tb = 64;
+  const long long nb = (Q + tb - 1) / tb;
+  k_table<<<(unsigned)(nb < 8192 ? nb : 8192), tb, 0, s>>>(k, h * k.inv_ell[0], n % 2 == 0, Q, table);
+  TK_LAUNCH("k_table");
+  return true;
+}
+
 void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* table,
                      cudaStream_t s) {
   const KernelDev k = make_kernel_dev(kh);
@@ -120,9 +133,9 @@ void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* 
     const long long Q = table_size(n);
     const double h = (gh.kind == TK_VERTEX) ? gh.b[0] / (double)(n - 1) : gh.b[0] / (double)n;
     const int even = (n % 2 == 0);
-    const int tb = 128;
+    const int tb = 64;
     const long long nb = (Q + tb - 1) / tb;
-    k_table<<<(unsigned)(nb < 4096 ? nb : 4096), tb, 0, s>>>(k, h * k.inv_ell[0], even, Q, table);
+    k_table<<<(unsigned)(nb < 8192 ? nb : 8192), tb, 0, s>>>(k, h * k.inv_ell[0], even, Q, table);
     TK_LAUNCH("k_table");
     const long long rows = (long long)n * n;
     k_gather<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), n < 256 ? 128 : 256, 0, s>>>(

@@ -287,9 +287,24 @@ __device__ __forceinline__ void neum(double& s, double& c, double x) {
   s = t;
 }
 
+// Reference values of the error epilogue: an array in C's layout, or (for
+// the cubic isotropic grid) the distinct-value table, F(ij, l) = T[q(s)] with
+// s = a_i^2 + a_j^2 + a_l^2, a = 2 idx - (n - 1), row ij = i n + j.
+struct ErrRef {
+  const double* R;
+  const double* T;
+  int n;
+  int even;
+  __device__ __forceinline__ double at(const GemmDesc& d, const double* Rb, int i, int j) const {
+    if (T == nullptr) return Rb[(long long)i * d.sCi + (long long)j * d.sCj];
+    const int ai = 2 * (i / n) - (n - 1), aj = 2 * (i % n) - (n - 1), al = 2 * j - (n - 1);
+    const int sq = ai * ai + aj * aj + al * al;
+    return __ldg(T + (even ? (sq - 3) >> 3 : sq >> 2));
+  }
+};
+
 template <int BM, int BN, bool kErr>
-__global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, const double* __restrict__ R,
-                                                  double* __restrict__ partials) {
+__global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double* __restrict__ partials) {
   constexpr int RM = BM / 16, RN = BN / 16;
   __shared__ double As[KS][BM + 1];
   __shared__ double Bs[KS][BN + 1];
@@ -330,7 +345,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, const double* __res
         if (i < d.M && j < d.N) C[(long long)i * d.sCi + (long long)j * d.sCj] = acc[p][q];
       }
   } else {
-    const double* Rb = R + (long long)b * d.sCb;
+    const double* Rb = ref.R ? ref.R + (long long)b * d.sCb : nullptr;
     double ds = 0.0, dc = 0.0, fs = 0.0, fc = 0.0;
 #pragma unroll
     for (int p = 0; p < RM; ++p)
@@ -338,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, const double* __res
       for (int q = 0; q < RN; ++q) {
         const int i = i0 + ty * RM + p, j = j0 + tx * RN + q;
         if (i < d.M && j < d.N) {
-          const double r = Rb[(long long)i * d.sCi + (long long)j * d.sCj];
+          const double r = ref.at(d, Rb, i, j);
           const double e = r - acc[p][q];
           neum(ds, dc, e * e);
           neum(fs, fc, r * r);
@@ -443,13 +458,13 @@ dim3 grid_of(const GemmDesc& d) {
 }
 
 template <int BM, int BN, bool kErr>
-void launch(const GemmDesc& d, const double* R, double* partials, cudaStream_t s) {
+void launch(const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s) {
   k_gemm_f64<BM, BN, kErr><<<grid_of<BM, BN>(d), NT, 0, s>>>(d, R, partials);
   TK_LAUNCH("k_gemm_f64");
 }
 
 template <bool kErr>
-dim3 dispatch(const GemmDesc& d, const double* R, double* partials, cudaStream_t s, bool run) {
+dim3 dispatch(const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s, bool run) {
   switch (pick_tile(d)) {
     case Tile::k16x16:
       if (run) launch<16, 16, kErr>(d, R, partials, s);
@@ -470,7 +485,7 @@ dim3 dispatch(const GemmDesc& d, const double* R, double* partials, cudaStream_t
 
 void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   if (d.M <= 0 || d.N <= 0 || d.batch <= 0) return;
-  const dim3 g = dispatch<false>(d, nullptr, nullptr, s, false);
+  const dim3 g = dispatch<false>(d, ErrRef{}, nullptr, s, false);
   const long long ctas = (long long)g.x * g.y * g.z;
   const long long outs = (long long)d.M * d.N * d.batch;
   if (ctas < 76 && outs <= (1LL << 18)) {
@@ -481,16 +496,18 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
     TK_LAUNCH("k_gemm_warp");
     return;
   }
-  dispatch<false>(d, nullptr, nullptr, s, true);
+  dispatch<false>(d, ErrRef{}, nullptr, s, true);
 }
 
 size_t gemm_err_partials(const GemmDesc& d) {
-  const dim3 g = dispatch<true>(d, nullptr, nullptr, nullptr, false);
+  const dim3 g = dispatch<true>(d, ErrRef{}, nullptr, nullptr, false);
   return 4ull * g.x * g.y * g.z;
 }
 
-void gemm_f64_err(const GemmDesc& d, const double* R, double* partials, double* out_dev, cudaStream_t s) {
-  const dim3 g = dispatch<true>(d, R, partials, s, true);
+void gemm_f64_err(const GemmDesc& d, const double* R, const double* table, int table_n, double* partials,
+                  double* out_dev, cudaStream_t s) {
+  ErrRef ref{R, table, table_n, table_n % 2 == 0};
+  const dim3 g = dispatch<true>(d, ref, partials, s, true);
   k_err_final<<<1, 1024, 0, s>>>(partials, (long long)g.x * g.y * g.z, out_dev);
   TK_LAUNCH("k_err_final");
 }

@@ -61,6 +61,19 @@ inline tk_nu_consts make_nu_consts(double nu) {
   const double pi = 3.141592653589793238;
   c.mupi_sin = (fabs(mu) < 1e-12) ? 1.0 : (mu * pi) / sin(mu * pi);
   c.pref_log = (1.0 - nu) * log(2.0) - lgamma(nu);
+  for (int k = 0; k < kTemmeTerms; ++k) {
+    const double dk = (double)k;
+    c.inv_k2mu2[k] = (k == 0) ? 0.0 : 1.0 / (dk * dk - mu * mu);
+    c.inv_kmmu[k] = (k == 0) ? 0.0 : 1.0 / (dk - mu);
+    c.inv_kpmu[k] = (k == 0) ? 0.0 : 1.0 / (dk + mu);
+    c.inv_k[k] = (k == 0) ? 0.0 : 1.0 / dk;
+  }
+  // C_k = prod_{j <= k} ((j - 1/2)^2 - mu^2) / j; zero from k = 1 when mu = +-1/2
+  c.Ck[0] = 1.0;
+  for (int k = 1; k < kMillerTerms; ++k) {
+    const double dk = (double)k;
+    c.Ck[k] = c.Ck[k - 1] * (((dk - 0.5) * (dk - 0.5) - mu * mu) / dk);
+  }
   return c;
 }
 

@@ -79,6 +79,8 @@ bool table_applicable(const tk_kernel& k, const tk_grid& g);
 void eval_tensor_f64(const tk_kernel& k, const tk_grid& g, double* F, double* table_scratch,
                      cudaStream_t s);
 size_t eval_scratch_doubles(const tk_kernel& k, const tk_grid& g);
+// Only the distinct-value table (when table_applicable); returns false otherwise.
+bool eval_table_f64(const tk_kernel& k, const tk_grid& g, double* table, cudaStream_t s);
 
 // |F|^2 with compensated per-thread sums and a fixed-order final sum.
 size_t norm2_scratch_doubles(size_t len);
@@ -112,14 +114,17 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s);
 // partials go to `partials` (2 * gridsize doubles), then a fixed-order sum
 // writes out_dev[0] = |R - C|^2, out_dev[1] = |R|^2.
 size_t gemm_err_partials(const GemmDesc& d);
-void gemm_f64_err(const GemmDesc& d, const double* R, double* partials, double* out_dev,
-                  cudaStream_t s);
+// With table != nullptr the reference is read from the distinct-value table
+// of the cubic isotropic grid with table_n points per axis (R unused).
+void gemm_f64_err(const GemmDesc& d, const double* R, const double* table, int table_n, double* partials,
+                  double* out_dev, cudaStream_t s);
 
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
 void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
                   double* scratch, cudaStream_t s);
-// rank rule on device; writes rank and flags for one mode into rank_out[0], rank_out[1].
+// rank rule on device; writes for one mode rank_out[0] = rank, [1] = flags,
+// [2] = rank before the cap (m + 1 when more than the m computed pairs are needed).
 void rank_rule(const double* lam, int m, const double* trace, const double* normF2, double eps,
                int rmax, int rfix, double u_eff, int n, int* rank_out, cudaStream_t s);
 
