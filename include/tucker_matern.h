@@ -187,7 +187,7 @@ int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, vo
  * ------------------------------------------------------------------------- */
 typedef enum {
   TK_STAGE_EVAL = 0,  /* sampling F (table + gather, or per point) */
-  TK_STAGE_NORM = 1,  /* |F|^2 */
+  TK_STAGE_NORM = 1,  /* |F|^2 when not read off the Gram trace (tk_tucker reads the trace) */
   TK_STAGE_GRAM = 2,  /* Gram matrices, all modes */
   TK_STAGE_EIG = 3,   /* eigenpairs, all modes */
   TK_STAGE_RANK = 4,  /* rank rule and factor extraction */

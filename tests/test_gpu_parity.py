@@ -274,7 +274,7 @@ def test_profile_and_launch_counter(ctx, wl):
     prof = ctx.profile_read()
     ctx.profile(False)
     assert binding.Context.kernel_launches() > l0 + 5
-    for stage in ("eval", "norm", "gram", "eig", "rank", "core", "error"):
+    for stage in ("eval", "gram", "eig", "rank", "core", "error"):  # |F|^2 comes from trace(G)
         assert prof[stage][1] >= 1 and prof[stage][0] > 0.0, stage
 
 
