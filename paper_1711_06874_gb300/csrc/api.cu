@@ -319,7 +319,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     // workspace layout: one list of sizes drives both the reservation and the carves
     const size_t sz[8] = {N,
                           std::max<size_t>(1, eval_scratch_doubles(*kernel, *grid)),
-                          norm2_scratch_doubles(N),
+                          eval_rowsq_doubles(*grid),
                           std::max<size_t>(1, gram_scr),
                           eig_scr,
                           64,
@@ -349,7 +349,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     }
     Profiler& pf = ctx->prof;
     pf.begin(TK_STAGE_EVAL, s);
-    eval_tensor_f64(*kernel, *grid, F, table, s);
+    eval_tensor_f64(*kernel, *grid, F, table, s, nscr, small);  // |F|^2 to small[0]
     pf.end(s);
     // Gram, then the leading eigenpairs in two phases: first 16 pairs (enough
     // whenever the rank is below 16), then the full rank cap only for the
@@ -367,7 +367,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
       sym_eig_topm(G[a], n[a], mA[a], lam[a], V[a], small + 1 + a, escr, s);
       pf.end(s);
       pf.begin(TK_STAGE_RANK, s);
-      rank_rule(lam[a], mA[a], small + 1 + a, small + 1, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
+      rank_rule(lam[a], mA[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
                 n[a], ranks_dev + 4 * a, s);
       pf.end(s);
     }
@@ -383,7 +383,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
         sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
         pf.end(s);
         pf.begin(TK_STAGE_RANK, s);
-        rank_rule(lam[a], m[a], small + 1 + a, small + 1, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
+        rank_rule(lam[a], m[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
                   n[a], ranks_dev + 4 * a, s);
         pf.end(s);
         mA[a] = m[a];
@@ -393,8 +393,7 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     if (again) {
       TK_CUDA(cudaMemcpyAsync(hr, ranks_dev, sizeof(int) * 20, cudaMemcpyDeviceToHost, s));
     }
-    // |F|^2 = trace(G_1) (compensated), the same sum in another order
-    TK_CUDA(cudaMemcpyAsync(hsmall, small + 1, sizeof(double) * 1, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(hsmall, small, sizeof(double) * 1, cudaMemcpyDeviceToHost, s));
     res = new tk_result();
     res->ctx = ctx;
     res->precision = o.precision;
@@ -521,8 +520,9 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
     const size_t parts = gemm_err_partials(d);
     ctx->ws.reserve(carve_bytes<double>(N) + carve_bytes<double>(eval_scratch_doubles(*kernel, *grid) + 1) +
                         carve_bytes<double>(w1) + carve_bytes<double>(w2) + carve_bytes<double>(parts) +
-                        carve_bytes<double>(8),
+                        carve_bytes<double>(8) + carve_bytes<double>(eval_rowsq_doubles(*grid)),
                     s);
+    double* rowsq = ctx->ws.take<double>(eval_rowsq_doubles(*grid));
     double* F = ctx->ws.take<double>(N);
     double* table = ctx->ws.take<double>(eval_scratch_doubles(*kernel, *grid) + 1);
     double* W1 = ctx->ws.take<double>(w1);
@@ -533,7 +533,7 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
     // F is resampled: the distinct-value table feeds the error epilogue
     // directly on cubic isotropic grids, otherwise F is written out first
     const bool tab = eval_table_f64(*kernel, *grid, table, s);
-    if (!tab) eval_tensor_f64(*kernel, *grid, F, table, s);
+    if (!tab) eval_tensor_f64(*kernel, *grid, F, table, s, rowsq, nullptr);
     recon_w2(res->core, r, res->U[0], r[0], res->U[1], r[1], n, W1, W2, s);
     d.A = W2;
     gemm_f64_err(d, tab ? nullptr : F, tab ? table : nullptr, n[0], part, sums, s);
@@ -554,9 +554,12 @@ int tk_eval(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, double* F
     check_grid(grid);
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
-    ctx->ws.reserve(carve_bytes<double>(eval_scratch_doubles(*kernel, *grid) + 1), s);
+    ctx->ws.reserve(carve_bytes<double>(eval_scratch_doubles(*kernel, *grid) + 1) +
+                        carve_bytes<double>(eval_rowsq_doubles(*grid)),
+                    s);
     double* table = ctx->ws.take<double>(eval_scratch_doubles(*kernel, *grid) + 1);
-    eval_tensor_f64(*kernel, *grid, F, table, s);
+    double* rowsq = ctx->ws.take<double>(eval_rowsq_doubles(*grid));
+    eval_tensor_f64(*kernel, *grid, F, table, s, rowsq, nullptr);
     TK_CUDA(cudaStreamSynchronize(s));
   });
 }

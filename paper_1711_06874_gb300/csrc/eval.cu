@@ -79,24 +79,45 @@ __global__ void k_table(KernelDev k, double hs, int even, long long Q, double* T
   }
 }
 
-// F[i][j][l] = T[q(s)], one block per (i, j) row, threads along l.
-__global__ void k_gather(const double* __restrict__ T, int n, int even, double* __restrict__ F) {
+// Sum of squares of one row across the block, fixed tree (deterministic).
+__device__ __forceinline__ double block_row_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// F[i][j][l] = T[q(s)], one block per (i, j) row, threads along l; the sum of
+// squares of each row goes to rowsq[row].
+__global__ void k_gather(const double* __restrict__ T, int n, int even, double* __restrict__ F,
+                         double* __restrict__ rowsq) {
+  __shared__ double red[32];
   const long long rows = (long long)n * n;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const int i = (int)(row / n), j = (int)(row % n);
     const int ai = 2 * i - (n - 1), aj = 2 * j - (n - 1);
     const int sij = ai * ai + aj * aj;
     double* out = F + row * n;
+    double sq = 0.0;
     for (int l = threadIdx.x; l < n; l += blockDim.x) {
       const int al = 2 * l - (n - 1);
       const int s = sij + al * al;
-      out[l] = __ldg(T + (even ? (s - 3) >> 3 : s >> 2));
+      const double v = __ldg(T + (even ? (s - 3) >> 3 : s >> 2));
+      out[l] = v;
+      sq = fma(v, v, sq);
     }
+    const double t = block_row_sum(sq, red);
+    if (threadIdx.x == 0) rowsq[row] = t;
   }
 }
 
-// Per-point evaluation for anisotropic ell or non-cubic grids.
-__global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F) {
+// Per-point evaluation for anisotropic ell or non-cubic grids (row sums of
+// squares as in k_gather).
+__global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F, double* __restrict__ rowsq) {
+  __shared__ double red[32];
   const int n1 = g.ax[0].n, n2 = g.ax[1].n, n3 = g.ax[2].n;
   const long long rows = (long long)n1 * n2;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -104,11 +125,43 @@ __global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F) {
     const double u = (g.ax[0].x0 + i * g.ax[0].dx) * k.inv_ell[0];
     const double v = (g.ax[1].x0 + j * g.ax[1].dx) * k.inv_ell[1];
     const double uv = u * u + v * v;
+    double sq = 0.0;
     for (int l = threadIdx.x; l < n3; l += blockDim.x) {
       const double w = (g.ax[2].x0 + l * g.ax[2].dx) * k.inv_ell[2];
-      F[row * n3 + l] = cov_value(k, uv + w * w);
+      const double val = cov_value(k, uv + w * w);
+      F[row * n3 + l] = val;
+      sq = fma(val, val, sq);
     }
+    const double t = block_row_sum(sq, red);
+    if (threadIdx.x == 0) rowsq[row] = t;
   }
+}
+
+// |F|^2 = sum of the row sums: 1024 threads, Neumaier over a fixed stride,
+// then a fixed tree.
+__global__ void __launch_bounds__(1024) k_rowsq_final(const double* __restrict__ rowsq, long long rows,
+                                                      double* out) {
+  __shared__ double rs[1024], rc[1024];
+  double s = 0.0, c = 0.0;
+  for (long long r = threadIdx.x; r < rows; r += blockDim.x) {
+    const double x = rowsq[r], t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a = rs[threadIdx.x], ac = rc[threadIdx.x] + rc[threadIdx.x + w];
+      const double x = rs[threadIdx.x + w], t = a + x;
+      ac += (fabs(a) >= fabs(x)) ? (a - t) + x : (x - t) + a;
+      rs[threadIdx.x] = t;
+      rc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = rs[0] + rc[0];
 }
 
 bool eval_table_f64(const tk_kernel& kh, const tk_grid& gh, double* table, cudaStream_t s) {
@@ -125,7 +178,7 @@ bool eval_table_f64(const tk_kernel& kh, const tk_grid& gh, double* table, cudaS
 }
 
 void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* table,
-                     cudaStream_t s) {
+                     cudaStream_t s, double* rowsq, double* normF2) {
   const KernelDev k = make_kernel_dev(kh);
   const GridDev g = make_grid_dev(gh);
   if (table_applicable(kh, gh)) {
@@ -139,14 +192,20 @@ void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* 
     TK_LAUNCH("k_table");
     const long long rows = (long long)n * n;
     k_gather<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), n < 256 ? 128 : 256, 0, s>>>(
-        table, n, even, F);
+        table, n, even, F, rowsq);
     TK_LAUNCH("k_gather");
   } else {
     const long long rows = (long long)gh.n[0] * gh.n[1];
-    k_eval_general<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), 128, 0, s>>>(k, g, F);
+    k_eval_general<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), 128, 0, s>>>(k, g, F, rowsq);
     TK_LAUNCH("k_eval_general");
   }
+  if (normF2) {
+    k_rowsq_final<<<1, 1024, 0, s>>>(rowsq, (long long)gh.n[0] * gh.n[1], normF2);
+    TK_LAUNCH("k_rowsq_final");
+  }
 }
+
+size_t eval_rowsq_doubles(const tk_grid& g) { return (size_t)g.n[0] * g.n[1]; }
 
 // ---------------------------------------------------------------------------
 // |x|^2: each thread keeps a Neumaier pair over a fixed slice; blocks reduce

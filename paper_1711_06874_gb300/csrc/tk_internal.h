@@ -75,9 +75,11 @@ GridDev make_grid_dev(const tk_grid& g);
 bool table_applicable(const tk_kernel& k, const tk_grid& g);
 
 // ---- stage launchers (all enqueue on `s`, no synchronisation) ----
-// (a) collocation tensor, FP64
+// (a) collocation tensor, FP64.  rowsq (n1 n2 doubles) receives the sum of
+// squares of every (i1, i2) row; when normF2 is given, |F|^2 is written there.
 void eval_tensor_f64(const tk_kernel& k, const tk_grid& g, double* F, double* table_scratch,
-                     cudaStream_t s);
+                     cudaStream_t s, double* rowsq, double* normF2);
+size_t eval_rowsq_doubles(const tk_grid& g);
 size_t eval_scratch_doubles(const tk_kernel& k, const tk_grid& g);
 // Only the distinct-value table (when table_applicable); returns false otherwise.
 bool eval_table_f64(const tk_kernel& k, const tk_grid& g, double* table, cudaStream_t s);
