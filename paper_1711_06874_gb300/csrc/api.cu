@@ -364,7 +364,8 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
         gram_f64(F, n, a, G[a], gscr, s);
       pf.end(s);
       pf.begin(TK_STAGE_EIG, s);
-      sym_eig_topm(G[a], n[a], mA[a], lam[a], V[a], small + 1 + a, escr, s);
+      // every G_k here is persymmetric (symmetric grid, even covariance)
+      sym_eig_topm_persym(G[a], n[a], mA[a], lam[a], V[a], small + 1 + a, ranks_dev + 4 * a + 3, escr, s);
       pf.end(s);
       pf.begin(TK_STAGE_RANK, s);
       rank_rule(lam[a], mA[a], small + 1 + a, small, o.eps, o.rmax[a], o.rfix[a], gram_u_eff(o.precision),
@@ -378,7 +379,8 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     if (hr[16] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
     bool again = false;
     for (int a = 0; a < nmodes; ++a) {
-      if (mA[a] < m[a] && hr[4 * a + 2] > mA[a]) {
+      // more pairs than computed, or a half of the split may have held back a pair
+      if ((mA[a] < m[a] && hr[4 * a + 2] > mA[a]) || hr[4 * a + 3] != 0) {
         pf.begin(TK_STAGE_EIG, s);
         sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
         pf.end(s);

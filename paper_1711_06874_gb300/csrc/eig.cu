@@ -59,9 +59,21 @@ __device__ double block_sum(double v, double* red) {
 
 // The panel Y (n x m) and the factor Q live in shared memory when 2 n m
 // doubles fit (otherwise in global memory); one warp per trailing column.
+struct QrProb {
+  double* Y;
+  double* Q;
+  int n, m;
+};
+struct QrBatch {
+  QrProb p[2];  // one problem per CTA
+};
+
 template <bool kShared>
-__global__ void __launch_bounds__(1024) k_householder_qr(double* Yg, double* Qg, int n, int m) {
+__global__ void __launch_bounds__(1024) k_householder_qr(QrBatch batch) {
   extern __shared__ double qr_sm[];
+  double* Yg = batch.p[blockIdx.x].Y;
+  double* Qg = batch.p[blockIdx.x].Q;
+  const int n = batch.p[blockIdx.x].n, m = batch.p[blockIdx.x].m;
   __shared__ double beta[kMaxM];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -136,9 +148,24 @@ __global__ void __launch_bounds__(1024) k_householder_qr(double* Yg, double* Qg,
 // when |a_pq| <= 1e-18 |A|_F; sweeps stop when none is applied.
 // Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Hin, int m, double* lam,
-                                                 double* Vout, int* sweeps_out) {
+struct JacProb {
+  const double* H;
+  int m;
+  double* lam;
+  double* V;
+  int* sweeps;
+};
+struct JacBatch {
+  JacProb p[2];  // one problem per CTA
+};
+
+__global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
   extern __shared__ double sm[];
+  const double* __restrict__ Hin = batch.p[blockIdx.x].H;
+  const int m = batch.p[blockIdx.x].m;
+  double* lam = batch.p[blockIdx.x].lam;
+  double* Vout = batch.p[blockIdx.x].V;
+  int* sweeps_out = batch.p[blockIdx.x].sweeps;
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
   const int np = mp / 2;        // planes per step
   double* A = sm;
@@ -325,6 +352,76 @@ __global__ void k_copy_rows(const double* G, double* H, int n) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) H[e] = G[e];
 }
 
+// Persymmetric split.  G is symmetric and G(i, j) = G(n-1-i, n-1-j) (a
+// symmetric grid and an even covariance), so its eigenvectors are even or odd
+// under the flip i -> n-1-i.  In the orthonormal basis (e_i +- e_{n-1-i})/sqrt2
+// (and e_c for the centre c of an odd n) G is block diagonal:
+//   Ge(i, j) = G(i, j) + G(i, n-1-j),  Go(i, j) = G(i, j) - G(i, n-1-j),  i, j < n/2,
+//   Ge(i, c) = Ge(c, i) = sqrt2 G(i, c),  Ge(c, c) = G(c, c)   (odd n).
+__global__ void k_persym_split(const double* __restrict__ G, int n, double* __restrict__ Ge,
+                               double* __restrict__ Go) {
+  const int ho = n / 2, he = n - ho;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < he * he; e += gridDim.x * blockDim.x) {
+    const int i = e / he, j = e % he;
+    double ve;
+    if (i < ho && j < ho) {
+      const double a = G[(long long)i * n + j], b = G[(long long)i * n + (n - 1 - j)];
+      ve = a + b;
+      Go[i * ho + j] = a - b;
+    } else if (i < ho) {
+      ve = 1.4142135623730950488 * G[(long long)i * n + ho];
+    } else if (j < ho) {
+      ve = 1.4142135623730950488 * G[(long long)ho * n + j];
+    } else {
+      ve = G[(long long)ho * n + ho];
+    }
+    Ge[e] = ve;
+  }
+}
+
+// Top m of the union of the two halves' eigenpairs (each sorted descending),
+// vectors expanded to length n: even y -> (y_i, y_i) / sqrt2 (centre y_c),
+// odd y -> (y_i, -y_i) / sqrt2 (centre 0).  flag = 1 when one half gave all
+// the pairs it computed while holding more, i.e. the top m may be incomplete.
+__global__ void k_persym_merge(const double* __restrict__ le, const double* __restrict__ Ve, int me,
+                               const double* __restrict__ lo, const double* __restrict__ Vo, int mo, int n, int m,
+                               double* __restrict__ lam, double* __restrict__ V, int* flag) {
+  __shared__ int src[kMaxM], idx[kMaxM];
+  const int ho = n / 2, he = n - ho;
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int k = 0; k < m; ++k) {
+      const bool take_e = (b >= mo) || (a < me && le[a] >= lo[b]);
+      src[k] = take_e ? 0 : 1;
+      idx[k] = take_e ? a++ : b++;
+      lam[k] = take_e ? le[idx[k]] : lo[idx[k]];
+    }
+    if (flag) *flag = ((a == me && me < he) || (b == mo && mo < ho)) ? 1 : 0;
+  }
+  __syncthreads();
+  const double r2 = 0.70710678118654752440;
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+    const int i = e / m, k = e % m;
+    double v;
+    if (src[k] == 0) {
+      if (i < ho)
+        v = r2 * Ve[i * me + idx[k]];
+      else if (i >= he)
+        v = r2 * Ve[(n - 1 - i) * me + idx[k]];
+      else
+        v = Ve[ho * me + idx[k]];  // centre of an odd n
+    } else {
+      if (i < ho)
+        v = r2 * Vo[i * mo + idx[k]];
+      else if (i >= he)
+        v = -r2 * Vo[(n - 1 - i) * mo + idx[k]];
+      else
+        v = 0.0;
+    }
+    V[(long long)i * m + k] = v;
+  }
+}
+
 // Truncation rule (Task 1, Sec. 2.1, with the HOSVD bound of Sec. 3.2):
 // the smallest r >= 1 whose discarded sum, tail beyond the m computed
 // eigenvalues (trace - their sum) plus the clamped computed ones from r on,
@@ -374,84 +471,179 @@ constexpr int kMargin = 8;
 
 static int subspace_cols(int n, int m) { return std::min(std::min(n, kMaxM), m + kMargin); }
 
-size_t sym_eig_scratch_doubles(int n, int m) {
+static size_t one_problem_doubles(int n, int m) {
   const int ms = subspace_cols(n, m);
   // Omega/Y, Q, W (n x ms each), H, V_H (ms x ms each), Ritz values, misc
   return 3ull * n * ms + 2ull * ms * ms + ms + 64 + (size_t)n * n;
 }
 
-static constexpr size_t kQrSmemMax = 200 * 1024;
-
-static void householder_qr(double* Y, double* Q, int n, int m, cudaStream_t s) {
-  const size_t need = 2ull * n * m * sizeof(double);
-  if (need <= kQrSmemMax) {
-    k_householder_qr<true><<<1, 1024, need, s>>>(Y, Q, n, m);
-  } else {
-    k_householder_qr<false><<<1, 1024, 0, s>>>(Y, Q, n, m);
-  }
-  TK_LAUNCH("k_householder_qr");
+size_t sym_eig_scratch_doubles(int n, int m) {
+  // the persymmetric path: two halves with their blocks, pairs and vectors
+  const int ho = n / 2, he = n - ho;
+  const int mh = std::min(he, (m + 1) / 2 + 4);
+  const size_t split = (size_t)he * he + (size_t)ho * ho + 2ull * mh + (size_t)he * mh + (size_t)ho * mh +
+                       one_problem_doubles(he, std::min(he, mh)) + one_problem_doubles(std::max(ho, 1), std::min(std::max(ho, 1), mh)) + 256;
+  return std::max(one_problem_doubles(n, m), split);
 }
+
+static constexpr size_t kQrSmemMax = 200 * 1024;
 
 static size_t jacobi_smem(int m) {
   const int mp = (m + 1) & ~1;
   return (2ull * mp * mp + mp) * sizeof(double) + (mp + 4) * sizeof(int);
 }
 
-void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
-                  double* scratch, cudaStream_t s) {
-  if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+static void set_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
-    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)jacobi_smem(kMaxM)));
+    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxM)));
     TK_CUDA(cudaFuncSetAttribute(k_householder_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kQrSmemMax));
     attr_set = true;
   }
-  const int ms = subspace_cols(n, m);
-  double* Y = scratch;
-  double* Q = Y + (size_t)n * ms;
-  double* W = Q + (size_t)n * ms;
-  double* H = W + (size_t)n * ms;
-  double* VH = H + (size_t)ms * ms;
-  double* lsub = VH + (size_t)ms * ms;
-  double* misc = lsub + ms;  // [0] trace, [8..] sweeps
+}
+
+// One eigenproblem of the batch: leading m pairs of the symmetric n x n G.
+struct EigProb {
+  const double* G;
+  int n, m;
+  double* lam;  // m
+  double* V;    // n x m, row-major
+  double* scr;  // one_problem_doubles(n, m)
+};
+
+// Up to two problems whose QR and Jacobi steps run as one launch (a CTA each).
+static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
+  set_attrs();
+  struct Work {
+    int ms;
+    double *Y, *Q, *W, *H, *VH, *lsub, *misc;
+  } w[2];
+  for (int b = 0; b < count; ++b) {
+    const int n = pr[b].n;
+    w[b].ms = subspace_cols(n, pr[b].m);
+    w[b].Y = pr[b].scr;
+    w[b].Q = w[b].Y + (size_t)n * w[b].ms;
+    w[b].W = w[b].Q + (size_t)n * w[b].ms;
+    w[b].H = w[b].W + (size_t)n * w[b].ms;
+    w[b].VH = w[b].H + (size_t)w[b].ms * w[b].ms;
+    w[b].lsub = w[b].VH + (size_t)w[b].ms * w[b].ms;
+    w[b].misc = w[b].lsub + w[b].ms;
+  }
+  // problems small enough for Jacobi on the whole matrix
+  {
+    JacBatch jb{};
+    int nj = 0;
+    size_t smem = 0;
+    for (int b = 0; b < count; ++b) {
+      if (w[b].ms != pr[b].n) continue;
+      const int n = pr[b].n;
+      k_copy_rows<<<64, 256, 0, s>>>(pr[b].G, w[b].H, n);
+      TK_LAUNCH("k_copy_rows");
+      jb.p[nj++] = JacProb{w[b].H, n, w[b].lsub, w[b].VH, (int*)(w[b].misc + 8)};
+      smem = std::max(smem, jacobi_smem(n));
+    }
+    if (nj) {
+      k_jacobi<<<nj, 1024, smem, s>>>(jb);
+      TK_LAUNCH("k_jacobi");
+    }
+    for (int b = 0; b < count; ++b) {
+      if (w[b].ms != pr[b].n) continue;
+      const int n = pr[b].n, m = pr[b].m;
+      TK_CUDA(cudaMemcpy2DAsync(pr[b].V, sizeof(double) * m, w[b].VH, sizeof(double) * n, sizeof(double) * m, n,
+                                cudaMemcpyDeviceToDevice, s));
+      TK_CUDA(cudaMemcpyAsync(pr[b].lam, w[b].lsub, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // the others: two passes of subspace iteration, then Rayleigh-Ritz
+  int idx[2], nr = 0;
+  for (int b = 0; b < count; ++b)
+    if (w[b].ms != pr[b].n) idx[nr++] = b;
+  if (nr == 0) return;
+  for (int t = 0; t < nr; ++t) {
+    const int b = idx[t];
+    k_random<<<64, 256, 0, s>>>(w[b].Y, (long long)pr[b].n * w[b].ms, 0x1711068740ull + (unsigned)pr[b].n);
+    TK_LAUNCH("k_random");
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    QrBatch qb{};
+    size_t smem = 0;
+    bool shared = true;
+    for (int t = 0; t < nr; ++t) {
+      const int b = idx[t], n = pr[b].n, ms = w[b].ms;
+      const double* src = (pass == 0) ? w[b].Y : w[b].Q;
+      GemmDesc d{n, ms, n, 1, pr[b].G, 0, n, 1, src, 0, 1, n, w[b].W, 0, 1, n};
+      gemm_f64(d, s);
+      TK_CUDA(cudaMemcpyAsync(w[b].Y, w[b].W, sizeof(double) * (size_t)n * ms, cudaMemcpyDeviceToDevice, s));
+      qb.p[t] = QrProb{w[b].Y, w[b].Q, n, ms};
+      const size_t need = 2ull * n * ms * sizeof(double);
+      smem = std::max(smem, need);
+      if (need > kQrSmemMax) shared = false;
+    }
+    if (shared)
+      k_householder_qr<true><<<nr, 1024, smem, s>>>(qb);
+    else
+      k_householder_qr<false><<<nr, 1024, 0, s>>>(qb);
+    TK_LAUNCH("k_householder_qr");
+  }
+  JacBatch jb{};
+  size_t smem = 0;
+  for (int t = 0; t < nr; ++t) {
+    const int b = idx[t], n = pr[b].n, ms = w[b].ms;
+    GemmDesc d1{n, ms, n, 1, pr[b].G, 0, n, 1, w[b].Q, 0, 1, n, w[b].W, 0, 1, n};
+    gemm_f64(d1, s);
+    GemmDesc d2{ms, ms, n, 1, w[b].Q, 0, n, 1, w[b].W, 0, 1, n, w[b].H, 0, ms, 1};
+    gemm_f64(d2, s);
+    k_symmetrize<<<4, 256, 0, s>>>(w[b].H, ms);
+    TK_LAUNCH("k_symmetrize");
+    jb.p[t] = JacProb{w[b].H, ms, w[b].lsub, w[b].VH, (int*)(w[b].misc + 8)};
+    smem = std::max(smem, jacobi_smem(ms));
+  }
+  k_jacobi<<<nr, 1024, smem, s>>>(jb);
+  TK_LAUNCH("k_jacobi");
+  for (int t = 0; t < nr; ++t) {
+    const int b = idx[t], n = pr[b].n, ms = w[b].ms, m = pr[b].m;
+    // leading m Ritz vectors V = Q V_H[:, :m] (row-major n x m)
+    GemmDesc d3{n, m, ms, 1, w[b].Q, 0, 1, n, w[b].VH, 0, ms, 1, pr[b].V, 0, m, 1};
+    gemm_f64(d3, s);
+    TK_CUDA(cudaMemcpyAsync(pr[b].lam, w[b].lsub, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out, double* scratch,
+                  cudaStream_t s) {
+  if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+  double* scr = scratch;
+  double* misc = scratch + one_problem_doubles(n, m) - 64;
   k_trace<<<1, 256, 0, s>>>(G, n, trace_out ? trace_out : misc);
   TK_LAUNCH("k_trace");
-  if (ms == n) {
-    // whole matrix: Jacobi on G directly
-    k_copy_rows<<<64, 256, 0, s>>>(G, H, n);
-    TK_LAUNCH("k_copy_rows");
-    k_jacobi<<<1, 1024, jacobi_smem(n), s>>>(H, n, lsub, VH, (int*)(misc + 8));
-    TK_LAUNCH("k_jacobi");
-    // first m columns of V_H (n x n) into V (n x m)
-    TK_CUDA(cudaMemcpy2DAsync(V, sizeof(double) * m, VH, sizeof(double) * n, sizeof(double) * m, n,
-                              cudaMemcpyDeviceToDevice, s));
-  } else {
-    k_random<<<64, 256, 0, s>>>(Y, (long long)n * ms, 0x1711068740ull);
-    TK_LAUNCH("k_random");
-    // two passes of subspace iteration on column-major n x ms blocks
-    for (int pass = 0; pass < 2; ++pass) {
-      const double* src = (pass == 0) ? Y : Q;
-      GemmDesc d{n, ms, n, 1, G, 0, n, 1, src, 0, 1, n, W, 0, 1, n};
-      gemm_f64(d, s);
-      TK_CUDA(cudaMemcpyAsync(Y, W, sizeof(double) * (size_t)n * ms, cudaMemcpyDeviceToDevice, s));
-      householder_qr(Y, Q, n, ms, s);
-    }
-    // W = G Q ; H = Q^T W
-    GemmDesc d1{n, ms, n, 1, G, 0, n, 1, Q, 0, 1, n, W, 0, 1, n};
-    gemm_f64(d1, s);
-    GemmDesc d2{ms, ms, n, 1, Q, 0, n, 1, W, 0, 1, n, H, 0, ms, 1};
-    gemm_f64(d2, s);
-    k_symmetrize<<<4, 256, 0, s>>>(H, ms);
-    TK_LAUNCH("k_symmetrize");
-    k_jacobi<<<1, 1024, jacobi_smem(ms), s>>>(H, ms, lsub, VH, (int*)(misc + 8));
-    TK_LAUNCH("k_jacobi");
-    // leading m Ritz vectors V = Q V_H[:, :m] (row-major n x m)
-    GemmDesc d3{n, m, ms, 1, Q, 0, 1, n, VH, 0, ms, 1, V, 0, m, 1};
-    gemm_f64(d3, s);
-  }
-  TK_CUDA(cudaMemcpyAsync(lam, lsub, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  EigProb p{G, n, m, lam, V, scr};
+  eig_batch(&p, 1, s);
+  k_canonical_sign<<<m, 256, 0, s>>>(V, n, m);
+  TK_LAUNCH("k_canonical_sign");
+}
+
+void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* flag,
+                         double* scratch, cudaStream_t s) {
+  if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+  const int ho = n / 2, he = n - ho;
+  const int me = std::min(he, (m + 1) / 2 + 4), mo = std::min(ho, (m + 1) / 2 + 4);
+  double* Ge = scratch;
+  double* Go = Ge + (size_t)he * he;
+  double* le = Go + (size_t)ho * ho;
+  double* lo = le + me;
+  double* Ve = lo + mo;
+  double* Vo = Ve + (size_t)he * me;
+  double* s0 = Vo + (size_t)ho * mo;
+  double* s1 = s0 + one_problem_doubles(he, me);
+  k_trace<<<1, 256, 0, s>>>(G, n, trace_out);
+  TK_LAUNCH("k_trace");
+  k_persym_split<<<64, 256, 0, s>>>(G, n, Ge, Go);
+  TK_LAUNCH("k_persym_split");
+  EigProb p[2] = {{Ge, he, me, le, Ve, s0}, {Go, ho, mo, lo, Vo, s1}};
+  eig_batch(p, 2, s);
+  k_persym_merge<<<1, 256, 0, s>>>(le, Ve, me, lo, Vo, mo, n, m, lam, V, flag);
+  TK_LAUNCH("k_persym_merge");
   k_canonical_sign<<<m, 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }

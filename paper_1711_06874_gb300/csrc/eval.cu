@@ -90,18 +90,19 @@ __device__ __forceinline__ double block_row_sum(double v, double* red) {
   return s;
 }
 
-// F[i][j][l] = T[q(s)], one block per (i, j) row, threads along l; the sum of
-// squares of each row goes to rowsq[row].
+// F[i][j][l] = T[q(s)], one block per (i, j) row at a time (grid-stride),
+// threads along l.  Each block sums the squares of everything it wrote and
+// leaves one partial per block in part[blockIdx.x].
 __global__ void k_gather(const double* __restrict__ T, int n, int even, double* __restrict__ F,
-                         double* __restrict__ rowsq) {
+                         double* __restrict__ part) {
   __shared__ double red[32];
   const long long rows = (long long)n * n;
+  double sq = 0.0;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const int i = (int)(row / n), j = (int)(row % n);
     const int ai = 2 * i - (n - 1), aj = 2 * j - (n - 1);
     const int sij = ai * ai + aj * aj;
     double* out = F + row * n;
-    double sq = 0.0;
     for (int l = threadIdx.x; l < n; l += blockDim.x) {
       const int al = 2 * l - (n - 1);
       const int s = sij + al * al;
@@ -109,32 +110,32 @@ __global__ void k_gather(const double* __restrict__ T, int n, int even, double* 
       out[l] = v;
       sq = fma(v, v, sq);
     }
-    const double t = block_row_sum(sq, red);
-    if (threadIdx.x == 0) rowsq[row] = t;
   }
+  const double t = block_row_sum(sq, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// Per-point evaluation for anisotropic ell or non-cubic grids (row sums of
+// Per-point evaluation for anisotropic ell or non-cubic grids (block sums of
 // squares as in k_gather).
-__global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F, double* __restrict__ rowsq) {
+__global__ void k_eval_general(KernelDev k, GridDev g, double* __restrict__ F, double* __restrict__ part) {
   __shared__ double red[32];
   const int n1 = g.ax[0].n, n2 = g.ax[1].n, n3 = g.ax[2].n;
   const long long rows = (long long)n1 * n2;
+  double sq = 0.0;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const int i = (int)(row / n2), j = (int)(row % n2);
     const double u = (g.ax[0].x0 + i * g.ax[0].dx) * k.inv_ell[0];
     const double v = (g.ax[1].x0 + j * g.ax[1].dx) * k.inv_ell[1];
     const double uv = u * u + v * v;
-    double sq = 0.0;
     for (int l = threadIdx.x; l < n3; l += blockDim.x) {
       const double w = (g.ax[2].x0 + l * g.ax[2].dx) * k.inv_ell[2];
       const double val = cov_value(k, uv + w * w);
       F[row * n3 + l] = val;
       sq = fma(val, val, sq);
     }
-    const double t = block_row_sum(sq, red);
-    if (threadIdx.x == 0) rowsq[row] = t;
   }
+  const double t = block_row_sum(sq, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // |F|^2 = sum of the row sums: 1024 threads, Neumaier over a fixed stride,
@@ -164,6 +165,11 @@ __global__ void __launch_bounds__(1024) k_rowsq_final(const double* __restrict__
   if (threadIdx.x == 0) out[0] = rs[0] + rc[0];
 }
 
+// Blocks of the tensor-writing kernels: a fixed count (so the partial sums of
+// squares, one per block, are reduced in a fixed order), or fewer for tiny grids.
+static constexpr int kEvalBlocks = 1216;  // 8 per SM
+static unsigned eval_blocks(long long rows) { return (unsigned)(rows < kEvalBlocks ? rows : kEvalBlocks); }
+
 bool eval_table_f64(const tk_kernel& kh, const tk_grid& gh, double* table, cudaStream_t s) {
   if (!table_applicable(kh, gh)) return false;
   const KernelDev k = make_kernel_dev(kh);
@@ -191,21 +197,20 @@ void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* 
     k_table<<<(unsigned)(nb < 8192 ? nb : 8192), tb, 0, s>>>(k, h * k.inv_ell[0], even, Q, table);
     TK_LAUNCH("k_table");
     const long long rows = (long long)n * n;
-    k_gather<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), n < 256 ? 128 : 256, 0, s>>>(
-        table, n, even, F, rowsq);
+    k_gather<<<eval_blocks(rows), n < 256 ? 128 : 256, 0, s>>>(table, n, even, F, rowsq);
     TK_LAUNCH("k_gather");
   } else {
     const long long rows = (long long)gh.n[0] * gh.n[1];
-    k_eval_general<<<(unsigned)(rows < 65535 * 4 ? rows : 65535 * 4), 128, 0, s>>>(k, g, F, rowsq);
+    k_eval_general<<<eval_blocks(rows), 128, 0, s>>>(k, g, F, rowsq);
     TK_LAUNCH("k_eval_general");
   }
   if (normF2) {
-    k_rowsq_final<<<1, 1024, 0, s>>>(rowsq, (long long)gh.n[0] * gh.n[1], normF2);
+    k_rowsq_final<<<1, 1024, 0, s>>>(rowsq, (long long)eval_blocks((long long)gh.n[0] * gh.n[1]), normF2);
     TK_LAUNCH("k_rowsq_final");
   }
 }
 
-size_t eval_rowsq_doubles(const tk_grid& g) { return (size_t)g.n[0] * g.n[1]; }
+size_t eval_rowsq_doubles(const tk_grid&) { return kEvalBlocks; }
 
 // ---------------------------------------------------------------------------
 // |x|^2: each thread keeps a Neumaier pair over a fixed slice; blocks reduce

@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double*
       }
   } else {
     const double* Rb = ref.R ? ref.R + (long long)b * d.sCb : nullptr;
+    // plain FP64 sums over this thread's outputs; compensation starts at the tree
     double ds = 0.0, dc = 0.0, fs = 0.0, fc = 0.0;
 #pragma unroll
     for (int p = 0; p < RM; ++p)
@@ -355,8 +356,8 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double*
         if (i < d.M && j < d.N) {
           const double r = ref.at(d, Rb, i, j);
           const double e = r - acc[p][q];
-          neum(ds, dc, e * e);
-          neum(fs, fc, r * r);
+          ds = fma(e, e, ds);
+          fs = fma(r, r, fs);
         }
       }
     // fixed-shape tree over the block's threads, compensation carried along
