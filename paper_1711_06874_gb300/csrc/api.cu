@@ -379,8 +379,10 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     if (hr[16] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
     bool again = false;
     for (int a = 0; a < nmodes; ++a) {
-      // more pairs than computed, or a half of the split may have held back a pair
-      if ((mA[a] < m[a] && hr[4 * a + 2] > mA[a]) || hr[4 * a + 3] != 0) {
+      // the rank needs more pairs than are certain: more than computed, or
+      // beyond the pairs the split guarantees
+      const int needed = o.rfix[a] > 0 ? o.rfix[a] : hr[4 * a + 2];
+      if ((mA[a] < m[a] && hr[4 * a + 2] > mA[a]) || needed > hr[4 * a + 3]) {
         pf.begin(TK_STAGE_EIG, s);
         sym_eig_topm(G[a], n[a], m[a], lam[a], V[a], small + 1 + a, escr, s);
         pf.end(s);

@@ -381,8 +381,9 @@ __global__ void k_persym_split(const double* __restrict__ G, int n, double* __re
 
 // Top m of the union of the two halves' eigenpairs (each sorted descending),
 // vectors expanded to length n: even y -> (y_i, y_i) / sqrt2 (centre y_c),
-// odd y -> (y_i, -y_i) / sqrt2 (centre 0).  flag = 1 when one half gave all
-// the pairs it computed while holding more, i.e. the top m may be incomplete.
+// odd y -> (y_i, -y_i) / sqrt2 (centre 0).  *safe = number of leading merged
+// pairs that are certainly the leading pairs of G: those above the last
+// computed eigenvalue of every half that has eigenvalues left uncomputed.
 __global__ void k_persym_merge(const double* __restrict__ le, const double* __restrict__ Ve, int me,
                                const double* __restrict__ lo, const double* __restrict__ Vo, int mo, int n, int m,
                                double* __restrict__ lam, double* __restrict__ V, int* flag) {
@@ -396,7 +397,14 @@ __global__ void k_persym_merge(const double* __restrict__ le, const double* __re
       idx[k] = take_e ? a++ : b++;
       lam[k] = take_e ? le[idx[k]] : lo[idx[k]];
     }
-    if (flag) *flag = ((a == me && me < he) || (b == mo && mo < ho)) ? 1 : 0;
+    if (flag) {
+      double t = -INFINITY;
+      if (me < he) t = fmax(t, le[me - 1]);
+      if (mo < ho) t = fmax(t, lo[mo - 1]);
+      int safe = 0;
+      while (safe < m && lam[safe] > t) ++safe;
+      *flag = safe;
+    }
   }
   __syncthreads();
   const double r2 = 0.70710678118654752440;

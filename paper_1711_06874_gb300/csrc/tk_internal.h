@@ -126,9 +126,10 @@ size_t sym_eig_scratch_doubles(int n, int m);
 void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
                   double* scratch, cudaStream_t s);
 // Same, for a persymmetric G (G(i,j) = G(n-1-i, n-1-j)): the even and odd
-// halves are solved side by side; *flag (device) is set to 1 when the top m
-// might be incomplete (then use sym_eig_topm).  Same scratch size.
-void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* flag,
+// halves are solved side by side; *safe (device int) receives how many of the
+// leading pairs are certainly exact (a rank above it needs sym_eig_topm).
+// Same scratch size.
+void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* safe,
                          double* scratch, cudaStream_t s);
 // rank rule on device; writes for one mode rank_out[0] = rank, [1] = flags,
 // [2] = rank before the cap (m + 1 when more than the m computed pairs are needed).
