@@ -46,15 +46,21 @@ __global__ void k_random(double* X, long long len, unsigned long long seed) {
 // Householder QR of a column-major n x m block Y (ld = n) in one CTA; writes
 // the explicit orthonormal factor Q (column-major, ld = n).  Y is destroyed.
 // ---------------------------------------------------------------------------
+// Sum over the block, the same value in every thread: warp sums, then warp 0
+// adds the warp partials in a fixed tree and broadcasts through red[32].
 __device__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];  // same order in every thread
-  return s;
+  if (w == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // The panel Y (n x m) and the factor Q live in shared memory when 2 n m
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(1024) k_householder_qr(QrBatch batch) {
   double* Qg = batch.p[blockIdx.x].Q;
   const int n = batch.p[blockIdx.x].n, m = batch.p[blockIdx.x].m;
   __shared__ double beta[kMaxM];
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* Y = kShared ? qr_sm : Yg;
   double* Q = kShared ? qr_sm + (size_t)n * m : Qg;
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
   int* pp = (int*)(cs + mp);
   int* qq = pp + np;
   int* flag = qq + np;
-  __shared__ double red[32];
+  __shared__ double red[33];
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
     const int i = e / mp, j = e % mp;
     A[e] = (i < m && j < m) ? Hin[i * m + j] : 0.0;
@@ -201,12 +207,25 @@ __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
         const double apq = A[p * mp + q];
         double c = 1.0, s = 0.0;
         if (fabs(apq) > tau) {
-          const double app = A[p * mp + p], aqq = A[q * mp + q];
-          const double theta = (aqq - app) / (2.0 * apq);
-          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
-          *flag = 1;
+          // The angle only steers convergence, so it is taken in FP32; (c, s)
+          // are then made orthonormal to FP64 precision by two Newton steps on
+          // c^2 + s^2 = 1, so the rotation applied is exactly orthogonal.
+          // scale by 2^-e (e the exponent of a_pq) so both fit FP32 at any |A|
+          const int e = ((__double2hiint(apq) >> 20) & 0x7FF) - 1023;
+          const double sc = __hiloint2double((1023 - e) << 20, 0);
+          const float theta = (float)((A[q * mp + q] - A[p * mp + p]) * sc) / (2.0f * (float)(apq * sc));
+          const float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+          const float cf = rsqrtf(fmaf(t, t, 1.0f));
+          c = (double)cf;
+          s = (double)(t * cf);
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const double g = fma(c, c, s * s);
+            const double k = fma(-0.5, g, 1.5);
+            c *= k;
+            s *= k;
+          }
+          if (s != 0.0) *flag = 1;
         }
         cs[2 * k] = c;
         cs[2 * k + 1] = s;
@@ -233,10 +252,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
           // columns: (.) [c s; -s c]
           double n00 = cb * r00 - sb * r01, n01 = sb * r00 + cb * r01;
           double n10 = cb * r10 - sb * r11, n11 = sb * r10 + cb * r11;
-          if (a == b && sa != 0.0) {
-            n01 = 0.0;
-            n10 = 0.0;
-          }
+          if (a == b) n01 = n10 = 0.5 * (n01 + n10);  // keep the block exactly symmetric
           A[pa * mp + pb] = n00;
           A[pa * mp + qb] = n01;
           A[qa * mp + pb] = n10;
