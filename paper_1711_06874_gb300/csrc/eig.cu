@@ -75,11 +75,8 @@ struct QrBatch {
 };
 
 template <bool kShared>
-__global__ void __launch_bounds__(1024) k_householder_qr(QrBatch batch) {
+__device__ void qr_body(double* Yg, double* Qg, int n, int m) {
   extern __shared__ double qr_sm[];
-  double* Yg = batch.p[blockIdx.x].Y;
-  double* Qg = batch.p[blockIdx.x].Q;
-  const int n = batch.p[blockIdx.x].n, m = batch.p[blockIdx.x].m;
   __shared__ double beta[kMaxM];
   __shared__ double red[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -146,6 +143,17 @@ __global__ void __launch_bounds__(1024) k_householder_qr(QrBatch batch) {
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) Qg[e] = Q[e];
 }
 
+template <bool kShared>
+__global__ void __launch_bounds__(1024) k_householder_qr(QrBatch batch) {
+  qr_body<kShared>(batch.p[blockIdx.x].Y, batch.p[blockIdx.x].Q, batch.p[blockIdx.x].n, batch.p[blockIdx.x].m);
+}
+
+// One problem per CTA at Y + b * stride, Q + b * stride (uniform sizes).
+template <bool kShared>
+__global__ void __launch_bounds__(1024) k_householder_qr_strided(double* Y, double* Q, int n, int m, long long stride) {
+  qr_body<kShared>(Y + blockIdx.x * stride, Q + blockIdx.x * stride, n, m);
+}
+
 // ---------------------------------------------------------------------------
 // Cyclic Jacobi on a symmetric m x m matrix (row-major, ld = m) in one CTA.
 // Parallel ordering: the circle method pairs the mp (even) indices into
@@ -165,13 +173,8 @@ struct JacBatch {
   JacProb p[2];  // one problem per CTA
 };
 
-__global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
+__device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, double* Vout, int* sweeps_out) {
   extern __shared__ double sm[];
-  const double* __restrict__ Hin = batch.p[blockIdx.x].H;
-  const int m = batch.p[blockIdx.x].m;
-  double* lam = batch.p[blockIdx.x].lam;
-  double* Vout = batch.p[blockIdx.x].V;
-  int* sweeps_out = batch.p[blockIdx.x].sweeps;
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
   const int np = mp / 2;        // planes per step
   double* A = sm;
@@ -295,9 +298,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
-// Canonical sign of each column of V (n x m row-major, ld = m).
+__global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
+  const JacProb& p = batch.p[blockIdx.x];
+  jacobi_body(p.H, p.m, p.lam, p.V, p.sweeps);
+}
+
+// One m x m problem per CTA: H + b * m^2 -> lam + b * m, V + b * m^2.
+__global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V) {
+  const long long b = blockIdx.x;
+  jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr);
+}
+
+// Canonical sign of each column of V (n x m row-major, ld = m); instance blockIdx.y.
 __global__ void k_canonical_sign(double* V, int n, int m) {
   const int col = blockIdx.x;
+  V += (size_t)blockIdx.y * n * m;
   const int half = (n + 1) / 2;
   __shared__ double bv[256];
   __shared__ int bi[256];
@@ -331,6 +346,8 @@ __global__ void k_canonical_sign(double* V, int n, int m) {
 
 __global__ void k_trace(const double* G, int n, double* out) {
   __shared__ double ss[256], sc[256];
+  G += (size_t)blockIdx.x * n * n;  // instance of a batch
+  out += blockIdx.x;
   double s = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double x = G[(long long)i * n + i];
@@ -364,6 +381,22 @@ __global__ void k_symmetrize(double* H, int m) {
   }
 }
 
+__global__ void k_symmetrize_batch(double* H, int m, int B) {
+  const long long total = (long long)B * m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / ((long long)m * m);
+    const int r = (int)(e - b * m * m);
+    const int i = r / m, j = r % m;
+    if (i < j) {
+      double* Hb = H + b * m * m;
+      const double v = 0.5 * (Hb[i * m + j] + Hb[j * m + i]);
+      Hb[i * m + j] = v;
+      Hb[j * m + i] = v;
+    }
+  }
+}
+
 __global__ void k_copy_rows(const double* G, double* H, int n) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) H[e] = G[e];
 }
@@ -377,6 +410,10 @@ __global__ void k_copy_rows(const double* G, double* H, int n) {
 __global__ void k_persym_split(const double* __restrict__ G, int n, double* __restrict__ Ge,
                                double* __restrict__ Go) {
   const int ho = n / 2, he = n - ho;
+  // instance blockIdx.y of a batch laid out [b][n][n] -> [b][he][he], [b][ho][ho]
+  G += (size_t)blockIdx.y * n * n;
+  Ge += (size_t)blockIdx.y * he * he;
+  Go += (size_t)blockIdx.y * ho * ho;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < he * he; e += gridDim.x * blockDim.x) {
     const int i = e / he, j = e % he;
     double ve;
@@ -405,6 +442,16 @@ __global__ void k_persym_merge(const double* __restrict__ le, const double* __re
                                double* __restrict__ lam, double* __restrict__ V, int* flag) {
   __shared__ int src[kMaxM], idx[kMaxM];
   const int ho = n / 2, he = n - ho;
+  {  // instance blockIdx.x of a batch
+    const size_t b = blockIdx.x;
+    le += b * me;
+    lo += b * mo;
+    Ve += b * he * me;
+    Vo += b * ho * mo;
+    lam += b * m;
+    V += b * n * m;
+    if (flag) flag += b * 4;
+  }
   if (threadIdx.x == 0) {
     int a = 0, b = 0;
     for (int k = 0; k < m; ++k) {
@@ -450,10 +497,8 @@ __global__ void k_persym_merge(const double* __restrict__ le, const double* __re
 // the smallest r >= 1 whose discarded sum, tail beyond the m computed
 // eigenvalues (trace - their sum) plus the clamped computed ones from r on,
 // summed smallest first, is <= eps^2 |F|^2 / 3; capped at rmax.
-__global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2,
-                       double eps, int rmax, int rfix, double u_eff, int n, int* out) {
-  if (threadIdx.x != 0) return;
-  const double nf = normF2[0];
+__device__ void rank_body(const double* lam, int m, double trace, double nf, double eps, int rmax, int rfix,
+                          double u_eff, int n, int* out) {
   const double thr = eps * eps * nf / 3.0;
   double sum = 0.0, sc = 0.0;
   for (int i = 0; i < m; ++i) {
@@ -461,7 +506,7 @@ __global__ void k_rank(const double* lam, int m, const double* trace, const doub
     sc += (fabs(sum) >= fabs(lam[i])) ? (sum - t) + lam[i] : (lam[i] - t) + sum;
     sum = t;
   }
-  double extra = trace[0] - (sum + sc);
+  double extra = trace - (sum + sc);
   if (!(extra > 0.0) || m >= n) extra = 0.0;
   int r = m + 1;  // "more than computed"
   double ts = extra, tc = 0.0;
@@ -485,6 +530,18 @@ __global__ void k_rank(const double* lam, int m, const double* trace, const doub
   if (thr < 10.0 * u_eff * (double)n * nf) flags |= TK_EPS_UNREACHABLE_AT_PRECISION;
   out[0] = r;
   out[1] = flags;
+}
+
+__global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2, double eps, int rmax,
+                       int rfix, double u_eff, int n, int* out) {
+  if (threadIdx.x == 0) rank_body(lam, m, trace[0], normF2[0], eps, rmax, rfix, u_eff, n, out);
+}
+
+// One instance per thread: lam + b m, trace[b], normF2[b], eps[b], rmax[b], out + 4 b.
+__global__ void k_rank_batch(const double* lam, int m, const double* trace, const double* normF2, const double* epsv,
+                             const int* rmaxv, int rfix, double u_eff, int n, int B, int* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) rank_body(lam + (size_t)b * m, m, trace[b], normF2[b], epsv[b], rmaxv[b], rfix, u_eff, n, out + 4 * b);
 }
 
 }  // namespace
@@ -670,6 +727,131 @@ void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, 
   TK_LAUNCH("k_persym_merge");
   k_canonical_sign<<<m, 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
+}
+
+// ---------------------------------------------------------------------------
+// B instances with the same n and m (persymmetric Grams G: [b][n][n]).  The
+// even halves of all instances form one uniform group and the odd halves
+// another; each group's GEMMs are one batched launch and its QR and Jacobi
+// steps one launch with a CTA per problem.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HalfGroup {
+  int nh, mh, ms;
+  double *Gh, *Y, *Q, *W, *H, *VH, *lsub, *lam, *V;
+};
+
+size_t group_doubles(int nh, int mh, int B) {
+  const int ms = subspace_cols(nh, mh);
+  return (size_t)B * ((size_t)nh * nh + 3ull * nh * ms + 2ull * ms * ms + ms + mh + (size_t)nh * mh) + 1024;
+}
+
+HalfGroup carve_group(double*& p, int nh, int mh, int B) {
+  HalfGroup g;
+  g.nh = nh;
+  g.mh = mh;
+  g.ms = subspace_cols(nh, mh);
+  auto take = [&](size_t n) {
+    double* q = p;
+    p += (n + 31) & ~size_t(31);
+    return q;
+  };
+  g.Gh = take((size_t)B * nh * nh);
+  g.Y = take((size_t)B * nh * g.ms);
+  g.Q = take((size_t)B * nh * g.ms);
+  g.W = take((size_t)B * nh * g.ms);
+  g.H = take((size_t)B * g.ms * g.ms);
+  g.VH = take((size_t)B * g.ms * g.ms);
+  g.lsub = take((size_t)B * g.ms);
+  g.lam = take((size_t)B * mh);
+  g.V = take((size_t)B * nh * mh);
+  return g;
+}
+
+void solve_group(const HalfGroup& g, int B, cudaStream_t s) {
+  const int nh = g.nh, ms = g.ms, mh = g.mh;
+  if (nh == 0) return;
+  if (ms == nh) {
+    // whole matrices: Jacobi directly
+    TK_CUDA(cudaMemcpyAsync(g.H, g.Gh, sizeof(double) * (size_t)B * nh * nh, cudaMemcpyDeviceToDevice, s));
+  } else {
+    k_random<<<256, 256, 0, s>>>(g.Y, (long long)B * nh * ms, 0x1711068740ull + (unsigned)nh);
+    TK_LAUNCH("k_random");
+    const size_t need = 2ull * nh * ms * sizeof(double);
+    for (int pass = 0; pass < 2; ++pass) {
+      const double* src = (pass == 0) ? g.Y : g.Q;
+      GemmDesc d{nh, ms, nh, B, g.Gh, (long long)nh * nh, nh, 1, src, (long long)nh * ms, 1, nh,
+                 g.W, (long long)nh * ms, 1, nh};
+      gemm_f64(d, s);
+      TK_CUDA(cudaMemcpyAsync(g.Y, g.W, sizeof(double) * (size_t)B * nh * ms, cudaMemcpyDeviceToDevice, s));
+      if (need <= kQrSmemMax)
+        k_householder_qr_strided<true><<<B, 1024, need, s>>>(g.Y, g.Q, nh, ms, (long long)nh * ms);
+      else
+        k_householder_qr_strided<false><<<B, 1024, 0, s>>>(g.Y, g.Q, nh, ms, (long long)nh * ms);
+      TK_LAUNCH("k_householder_qr_strided");
+    }
+    GemmDesc d1{nh, ms, nh, B, g.Gh, (long long)nh * nh, nh, 1, g.Q, (long long)nh * ms, 1, nh,
+                g.W, (long long)nh * ms, 1, nh};
+    gemm_f64(d1, s);
+    GemmDesc d2{ms, ms, nh, B, g.Q, (long long)nh * ms, nh, 1, g.W, (long long)nh * ms, 1, nh,
+                g.H, (long long)ms * ms, ms, 1};
+    gemm_f64(d2, s);
+    k_symmetrize_batch<<<(unsigned)std::min<long long>(((long long)B * ms * ms + 255) / 256, 4096), 256, 0, s>>>(g.H, ms, B);
+    TK_LAUNCH("k_symmetrize_batch");
+  }
+  k_jacobi_strided<<<B, 1024, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
+  TK_LAUNCH("k_jacobi_strided");
+  if (ms == nh) {
+    // first mh columns of V_H (ms x ms) into V (nh x mh)
+    TK_CUDA(cudaMemcpy2DAsync(g.V, sizeof(double) * mh, g.VH, sizeof(double) * ms, sizeof(double) * mh,
+                              (size_t)B * nh, cudaMemcpyDeviceToDevice, s));
+  } else {
+    GemmDesc d3{nh, mh, ms, B, g.Q, (long long)nh * ms, 1, nh, g.VH, (long long)ms * ms, ms, 1,
+                g.V, (long long)nh * mh, mh, 1};
+    gemm_f64(d3, s);
+  }
+  TK_CUDA(cudaMemcpy2DAsync(g.lam, sizeof(double) * mh, g.lsub, sizeof(double) * ms, sizeof(double) * mh, B,
+                            cudaMemcpyDeviceToDevice, s));
+}
+
+}  // namespace
+
+size_t sym_eig_persym_batch_scratch_doubles(int n, int m, int B) {
+  const int ho = n / 2, he = n - ho;
+  const int me = std::min(he, (m + 1) / 2 + 4), mo = std::min(ho, (m + 1) / 2 + 4);
+  return group_doubles(he, me, B) + group_doubles(ho, mo, B) + 4096;
+}
+
+void sym_eig_persym_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, int* safe,
+                          double* scratch, cudaStream_t s) {
+  if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+  set_attrs();
+  TK_CUDA(cudaFuncSetAttribute(k_householder_qr_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kQrSmemMax));
+  TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)jacobi_smem(kMaxM)));
+  const int ho = n / 2, he = n - ho;
+  const int me = std::min(he, (m + 1) / 2 + 4), mo = std::min(ho, (m + 1) / 2 + 4);
+  double* p = scratch;
+  const HalfGroup ge = carve_group(p, he, me, B);
+  const HalfGroup go = carve_group(p, ho, mo, B);
+  k_trace<<<B, 256, 0, s>>>(G, n, trace);
+  TK_LAUNCH("k_trace");
+  k_persym_split<<<dim3(64, B), 256, 0, s>>>(G, n, ge.Gh, go.Gh);
+  TK_LAUNCH("k_persym_split");
+  solve_group(ge, B, s);
+  solve_group(go, B, s);
+  k_persym_merge<<<B, 256, 0, s>>>(ge.lam, ge.V, me, go.lam, go.V, mo, n, m, lam, V, safe);
+  TK_LAUNCH("k_persym_merge");
+  k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
+  TK_LAUNCH("k_canonical_sign");
+}
+
+void rank_rule_batch(const double* lam, int m, const double* trace, const double* normF2, const double* eps,
+                     const int* rmax, int rfix, double u_eff, int n, int B, int* out, cudaStream_t s) {
+  k_rank_batch<<<(B + 127) / 128, 128, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n, B, out);
+  TK_LAUNCH("k_rank_batch");
 }
 
 void rank_rule(const double* lam, int m, const double* trace, const double* normF2, double eps,

@@ -116,6 +116,32 @@ __global__ void k_rowexp(const unsigned long long* __restrict__ rowmax_bits, int
   }
 }
 
+// Balanced base-256 digits of x 2^(7 - e): T = round(|x| 2^(47 - e)) from the
+// FP64 bits with integer operations (|x| < 2^e, so T < 2^47), then digits from
+// the bottom: x 2^(7 - e) = sum_s d_s 2^(-8s) + O(2^-41), |d_s| <= 128.
+__device__ __forceinline__ void slice_digits(double xv, int e, int (&d)[kSlices]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long T = 0;
+  if (ex != 0 && e > -1000) {
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int rs = 1028 + e - ex;  // right shift of the 53-bit mantissa, >= 6
+    if (rs < 64) T = (long long)((mant + (1ull << (rs - 1))) >> rs);
+    if (bits >> 63) T = -T;
+  }
+#pragma unroll
+  for (int s = kSlices - 1; s >= 1; --s) {
+    const long long r = ((T + 128) & 255) - 128;
+    d[s] = (int)r;
+    T = (T - r) >> 8;
+  }
+  d[0] = (int)T;
+}
+
+__device__ __forceinline__ __nv_bfloat16 slice_value(int d, int s) {
+  return __float2bfloat16_rn(__int2float_rn(d) * __int_as_float((127 - 7 - 8 * s) << 23));  // d 2^(-7-8s)
+}
+
 // Slices of one unfolding, written K-major: S[s][row][c], row stride Kp (a
 // multiple of 32, zero padded).  32 x 32 tiles through shared memory so that
 // both the read of F and the write of S are coalesced for every mode.
@@ -149,31 +175,58 @@ __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, 
     const int row = r0 + q;
     const long long c = c0 + tx;
     if (row >= nrows || c >= Kp) continue;
-    // T = round(|x| 2^(47 - e)) from the FP64 bits with integer operations
-    // (|x| < 2^e, so T < 2^47), then balanced base-256 digits from the bottom:
-    // x 2^(7 - e) = sum_s d_s 2^(-8s) + O(2^-41), |d_s| <= 128.
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[q][tx]);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    const int e = rowexp[row];
-    long long T = 0;
-    if (ex != 0 && e > -1000) {
-      const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const int rs = 1028 + e - ex;  // right shift of the 53-bit mantissa, >= 6
-      if (rs < 64) T = (long long)((mant + (1ull << (rs - 1))) >> rs);
-      if (bits >> 63) T = -T;
-    }
     int d[kSlices];
-#pragma unroll
-    for (int s = kSlices - 1; s >= 1; --s) {
-      const long long r = ((T + 128) & 255) - 128;
-      d[s] = (int)r;
-      T = (T - r) >> 8;
-    }
-    d[0] = (int)T;
+    slice_digits(tile[q][tx], rowexp[row], d);
     const size_t base = (size_t)row * Kp + c;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s)
-      S[s * plane + base] = __float2bfloat16_rn(__int2float_rn(d[s]) * __int_as_float((127 - 7 - 8 * s) << 23));
+    for (int s = 0; s < kSlices; ++s) S[s * plane + base] = slice_value(d[s], s);
+  }
+}
+
+// The same slices for B cubic isotropic tensors given by their distinct-value
+// tables (F_b(i, j, k) = T_b[q(a_i^2 + a_j^2 + a_k^2)], a = 2 idx - (n - 1)),
+// mode-1 unfolding: row i, column c = j n + k.  F is never written.
+__device__ __forceinline__ double table_value(const double* Tb, int n, int even, int i, int j, int k) {
+  const int ai = 2 * i - (n - 1), aj = 2 * j - (n - 1), ak = 2 * k - (n - 1);
+  const int sq = ai * ai + aj * aj + ak * ak;
+  return __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2));
+}
+
+__global__ void k_rowexp_table(const double* __restrict__ T, long long tq, int n, int even, int* __restrict__ rowexp) {
+  __shared__ double red[32];
+  const int i = blockIdx.x, b = blockIdx.y;
+  const double* Tb = T + (size_t)b * tq;
+  double m = 0.0;
+  for (int c = threadIdx.x; c < n * n; c += blockDim.x) m = fmax(m, fabs(table_value(Tb, n, even, i, c / n, c % n)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+    int e = -1000;
+    if (v > 0.0) frexp(v, &e);
+    rowexp[(size_t)b * n + i] = e;
+  }
+}
+
+__global__ void k_slice_table(const double* __restrict__ T, long long tq, int n, int even, long long Kp, int B,
+                              const int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S) {
+  const long long K = (long long)n * n;
+  const long long per = (long long)n * Kp;
+  const long long total = per * B;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const long long r = e - (long long)b * per;
+    const int row = (int)(r / Kp);
+    const long long c = r - (long long)row * Kp;
+    int d[kSlices] = {0, 0, 0, 0, 0, 0};
+    if (c < K) slice_digits(table_value(T + (size_t)b * tq, n, even, row, (int)(c / n), (int)(c % n)),
+                            rowexp[(size_t)b * n + row], d);
+    __nv_bfloat16* Sb = S + (size_t)b * kSlices * per + r;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) Sb[(size_t)s * per] = slice_value(d[s], s);
   }
 }
 
@@ -181,9 +234,10 @@ struct TcArgs {
   int nrows;
   int nrt, nct;           // row tiles (of 128) and column tiles (of 96)
   int nblocks;            // blocks of G touching the upper triangle
+  int nsplit;             // K splits per instance
   int kblocks_per_split;  // k-blocks (of 32) per CTA
   int kblocks_total;
-  double* partials;       // [split][block][128][96]
+  double* partials;       // [instance][split][block][128][96]
   int* err;
 };
 
@@ -232,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = (uint32_t*)(bars + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int inst = blockIdx.z;  // instance of a batch (one slice tensor each)
   int bi, bj;
   block_of(blockIdx.x, args.nrt, args.nct, bi, bj);
   const int kb0 = blockIdx.y * args.kblocks_per_split;
@@ -265,8 +320,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
         unsigned char* sa = smem + st * kStageBytes;
         tc::mbar_expect_tx(&full[st], kStageBytes);
-        tc::tma_load_3d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0);
-        tc::tma_load_3d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0);
+        tc::tma_load_4d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0, inst);
+        tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0, inst);
         issued = k + 1;
       }
       // copies still in flight must land before the CTA exits
@@ -366,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) tc::mbar_arrive(acc_empty);
     }
     if (ok) {
-      double* out = args.partials + ((size_t)blockIdx.y * args.nblocks + blockIdx.x) * kTM * kTN +
+      double* out = args.partials + (((size_t)inst * args.nsplit + blockIdx.y) * args.nblocks + blockIdx.x) * kTM * kTN +
                     (size_t)row * kTN + grp * kEpiCols;
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) out[j] = (double)V[j] * 5.684341886080802e-14;  // 2^-44
@@ -378,23 +433,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-// G[gi][gj] = G[gj][gi] = 2^(e_gi + e_gj) sum_split P[split][block(gi, gj)][..], gi <= gj.
-__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int nct, int nblocks, int n,
+// G_b[gi][gj] = G_b[gj][gi] = 2^(e_gi + e_gj) sum_split P[b][split][block(gi, gj)][..],
+// gi <= gj, for every instance b (row exponents rowexp[b * n + i]).
+__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
                             const int* __restrict__ rowexp, double* __restrict__ G) {
-  const long long total = (long long)n * n;
+  const long long per = (long long)n * n;
+  const long long total = per * B;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int gi = (int)(e / n), gj = (int)(e % n);
+    const int b = (int)(e / per);
+    const long long r = e - (long long)b * per;
+    const int gi = (int)(r / n), gj = (int)(r % n);
     if (gi > gj) continue;
     const int bi = gi / kTM, bj = gj / kTN;
-    const int b = block_index(bi, bj, nct);
+    const int blk = block_index(bi, bj, nct);
     const size_t off = (size_t)(gi - bi * kTM) * kTN + (gj - bj * kTN);
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += P[((size_t)sp * nblocks + b) * kTM * kTN + off];
-    const int ei = rowexp[gi], ej = rowexp[gj];
+    for (int sp = 0; sp < nsplit; ++sp) s += P[(((size_t)b * nsplit + sp) * nblocks + blk) * kTM * kTN + off];
+    const int ei = rowexp[(size_t)b * n + gi], ej = rowexp[(size_t)b * n + gj];
     const double v = (ei > -1000 && ej > -1000) ? ldexp(s, ei + ej) : 0.0;
-    G[(long long)gi * n + gj] = v;
-    G[(long long)gj * n + gi] = v;
+    double* Gb = G + (size_t)b * per;
+    Gb[(long long)gi * n + gj] = v;
+    Gb[(long long)gj * n + gi] = v;
   }
 }
 
@@ -403,7 +463,7 @@ struct TcPlan {
   long long K, Kp;
 };
 
-TcPlan tc_plan(const int n[3], int mode, int sm_count) {
+TcPlan tc_plan(const int n[3], int mode, int sm_count, int B = 1) {
   TcPlan p;
   p.nrows = n[mode];
   p.K = (long long)n[0] * n[1] * n[2] / p.nrows;
@@ -415,7 +475,7 @@ TcPlan tc_plan(const int n[3], int mode, int sm_count) {
   // about one wave of CTAs; splits of whole 256-deep chunks, at most 256 chunks
   // each so that the int64 sums stay below 2^62
   const int chunks = (p.kb_total + kChunkBlocks - 1) / kChunkBlocks;
-  int want = std::max(1, sm_count / p.nblocks);
+  int want = std::max(1, sm_count / (p.nblocks * B));
   want = std::max(want, (chunks + 255) / 256);
   want = std::min(want, chunks);
   const int chunks_per_split = (chunks + want - 1) / want;
@@ -440,17 +500,40 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long Kp, int nrows, int box_rows) {
+// Slices of B instances, [b][s][row][Kp] bf16: dims (Kp, nrows, 6, B).
+CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long Kp, int nrows, int B,
+                      int box_rows) {
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nrows, (cuuint64_t)kSlices};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * nrows};
-  cuuint32_t box[3] = {kKB, (cuuint32_t)box_rows, kSlices};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)nrows, (cuuint64_t)kSlices, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * nrows, (cuuint64_t)Kp * 2 * nrows * kSlices};
+  cuuint32_t box[4] = {kKB, (cuuint32_t)box_rows, kSlices, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, S, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) fail(TK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return map;
+}
+
+// The tensor-core Gram and its reduction over B instances whose slices are
+// at S ([b][s][row][Kp]) and row exponents at rowexp ([b][row]).
+void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, double* P, double* G, int* err,
+                 cudaStream_t s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, B, kTM);
+  const CUtensorMap mapB = slice_map(enc, S, p.Kp, p.nrows, B, kTN);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.nsplit, p.kb_per_split, p.kb_total, P, err};
+  k_gram_tc<<<dim3(p.nblocks, p.nsplit, B), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
+  TK_LAUNCH("k_gram_tc");
+  const long long total = (long long)p.nrows * p.nrows * B;
+  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks,
+                                                                                      p.nrows, B, rowexp, G);
+  TK_LAUNCH("k_tc_reduce");
 }
 
 }  // namespace
@@ -497,21 +580,41 @@ void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void
     k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S);
     TK_LAUNCH("k_slice");
   }
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
-  const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, kTM);
-  const CUtensorMap mapB = slice_map(enc, S, p.Kp, p.nrows, kTN);
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  });
-  TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.kb_per_split, p.kb_total, P, err};
-  k_gram_tc<<<dim3(p.nblocks, p.nsplit), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
-  TK_LAUNCH("k_gram_tc");
-  const long long total = (long long)p.nrows * p.nrows;
-  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks,
-                                                                                      p.nrows, rowexp, G);
-  TK_LAUNCH("k_tc_reduce");
+  run_tc_gram(p, 1, S, rowexp, P, G, err, s);
+}
+
+size_t gram_sliced_table_scratch_bytes(int n, int B) {
+  const int nn[3] = {n, n, n};
+  const TcPlan p = tc_plan(nn, 0, 152, B);
+  size_t b = 0;
+  b += carve_bytes<int>((size_t)B * n);                                          // row exponents
+  b += carve_bytes<__nv_bfloat16>((size_t)B * kSlices * n * p.Kp);                // slices
+  b += carve_bytes<double>((size_t)B * p.nsplit * p.nblocks * kTM * kTN);       // partials
+  return b + 4096;
+}
+
+void gram_sliced_table(const double* T, long long tq, int n, int B, double* G, void* scratch, int* err,
+                       cudaStream_t s) {
+  const int nn[3] = {n, n, n};
+  const TcPlan p = tc_plan(nn, 0, 152, B);
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    char* q = base + off;
+    off += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  int* rowexp = (int*)carve(sizeof(int) * (size_t)B * n);
+  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * n * p.Kp);
+  double* P = (double*)carve(sizeof(double) * (size_t)B * p.nsplit * p.nblocks * kTM * kTN);
+  const int even = (n % 2 == 0);
+  k_rowexp_table<<<dim3(n, B), 256, 0, s>>>(T, tq, n, even, rowexp);
+  TK_LAUNCH("k_rowexp_table");
+  const long long total = (long long)B * n * p.Kp;
+  k_slice_table<<<(unsigned)std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, s>>>(T, tq, n, even, p.Kp,
+                                                                                              B, rowexp, S);
+  TK_LAUNCH("k_slice_table");
+  run_tc_gram(p, B, S, rowexp, P, G, err, s);
 }
 
 }  // namespace tk

@@ -97,6 +97,11 @@ void gram_f64(const double* F, const int n[3], int mode, double* G, double* scra
 size_t gram_sliced_scratch_bytes(const int n[3], int mode);
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s);
+// Gram (mode 1) of B cubic isotropic tensors given by their distinct-value
+// tables (T + b * tq, n points per axis), without writing F; G: [b][n][n].
+size_t gram_sliced_table_scratch_bytes(int n, int B);
+void gram_sliced_table(const double* T, long long tq, int n, int B, double* G, void* scratch, int* err,
+                       cudaStream_t s);
 // unit roundoff of the Gram of each precision (for the eps-unreachable flag)
 inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 : 0x1p-48; }
 
@@ -131,6 +136,14 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
 // Same scratch size.
 void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* safe,
                          double* scratch, cudaStream_t s);
+// B instances with the same n and m: G [b][n][n] -> lam [b][m], V [b][n][m],
+// trace [b], safe [b * 4] (certain leading pairs per instance).
+size_t sym_eig_persym_batch_scratch_doubles(int n, int m, int B);
+void sym_eig_persym_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, int* safe,
+                          double* scratch, cudaStream_t s);
+// rank rule for B instances: out [b * 4 + 0..2] as rank_rule, eps [b], rmax [b]
+void rank_rule_batch(const double* lam, int m, const double* trace, const double* normF2, const double* eps,
+                     const int* rmax, int rfix, double u_eff, int n, int B, int* out, cudaStream_t s);
 // rank rule on device; writes for one mode rank_out[0] = rank, [1] = flags,
 // [2] = rank before the cap (m + 1 when more than the m computed pairs are needed).
 void rank_rule(const double* lam, int m, const double* trace, const double* normF2, double eps,
