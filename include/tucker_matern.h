@@ -89,7 +89,16 @@ typedef struct {
   int32_t precision;          /* tk_precision */
   int32_t isotropic_shortcut; /* 1: when the three Grams are equal by symmetry
                                  (equal n, b, ell), form and solve one of them */
-  int32_t reserved[4];        /* must be zero */
+  int32_t reflect_fold;       /* 1: solve on the weighted octant.  The covariance
+                                 depends on each x_a only through x_a^2 and the
+                                 grid is symmetric about 0, so F is unchanged by
+                                 reversing an axis; the odd eigenvectors of each
+                                 G_k then have eigenvalue 0 and the factors, core
+                                 and eigenvalues follow from the octant tensor
+                                 sqrt(w_i w_j w_l) F (w = grid points an octant
+                                 index stands for: 1 at the centre of an odd axis,
+                                 else 2).  Skipped when rfix_k > ceil(n_k / 2). */
+  int32_t reserved[3];        /* must be zero */
 } tk_opts;
 
 typedef struct tk_ctx tk_ctx;
@@ -104,7 +113,8 @@ const char* tk_version(void);
 int tk_create(tk_ctx** ctx, int device);
 /* Frees the context and its workspace; results created on it must be freed first. */
 void tk_destroy(tk_ctx* ctx);
-/* Default options: eps 1e-6, rmax 32, rfix 0, TK_SLICED_BF16, shortcut on. */
+/* Default options: eps 1e-6, rmax 32, rfix 0, TK_SLICED_BF16, shortcut and
+ * fold on. */
 void tk_default_opts(tk_opts* opts);
 
 /* ---------------------------------------------------------------------------
@@ -144,6 +154,20 @@ int tk_reconstruct(tk_ctx* ctx, const tk_result* res, double* dst, void* stream)
 int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, const tk_grid* grid,
                  double* out, void* stream);
 void tk_result_free(tk_result* res);
+
+/* ---------------------------------------------------------------------------
+ * Batched solve: `count` independent instances of tk_tucker (the parameter
+ * sweeps behind the likelihood of Sec. 2.3, Eq. (like)); instance i uses
+ * kernels[i], grids[i], opts[i] (host arrays).  Instances that share a grid,
+ * precision, rank caps and isotropy are solved together, every stage one
+ * launch over all of them, in chunks that fit the free device memory; each
+ * result is bitwise the one that instance gets in any other batch, alone
+ * included.  On TK_OK outs[i] (host array of count) receives a result for
+ * every i, each freed with tk_result_free; on failure every outs[i] is NULL.
+ * Synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* grids, const tk_opts* opts,
+             tk_result** outs, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points (one step of the path each, device buffers in and out).

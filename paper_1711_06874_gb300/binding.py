@@ -41,7 +41,7 @@ class Grid(_c.Structure):
 
 class Opts(_c.Structure):
     _fields_ = [("eps", _dbl), ("rmax", _i32 * 3), ("rfix", _i32 * 3), ("precision", _i32),
-                ("isotropic_shortcut", _i32), ("reserved", _i32 * 4)]
+                ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("reserved", _i32 * 3)]
 
 
 SIGNATURES = {
@@ -61,6 +61,8 @@ SIGNATURES = {
     "tk_reconstruct": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "tk_rel_error": (_c.c_int, [_vp, _vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(_dbl), _vp]),
     "tk_result_free": (None, [_vp]),
+    "tk_batch": (_c.c_int, [_vp, _c.c_int, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(Opts),
+                            _c.POINTER(_vp), _vp]),
     "tk_eval": (_c.c_int, [_vp, _c.POINTER(Kernel), _c.POINTER(Grid), _vp, _vp]),
     "tk_gram": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _c.c_int, _c.c_int, _vp, _vp]),
     "tk_sym_eig": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _vp, _vp, _vp]),
@@ -120,7 +122,7 @@ def make_grid(prob: workloads.Problem) -> Grid:
     return Grid((_i32 * 3)(*prob.n), (_dbl * 3)(*prob.b), prob.grid)
 
 
-def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True) -> Opts:
+def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True, fold=True) -> Opts:
     o = Opts()
     load().tk_default_opts(_c.byref(o))
     o.eps = prob.eps
@@ -128,6 +130,7 @@ def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortc
     o.rfix = (_i32 * 3)(*rfix)
     o.precision = precision
     o.isotropic_shortcut = 1 if shortcut else 0
+    o.reflect_fold = 1 if fold else 0
     return o
 
 
@@ -161,12 +164,24 @@ class Context:
 
     # ---- whole solve -------------------------------------------------------
     def tucker(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True,
-               stream=None) -> "Result":
-        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut)
+               fold=True, stream=None) -> "Result":
+        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold)
         out = _vp()
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
         return Result(self, out, prob)
+
+    def batch(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, stream=None) -> list:
+        """Independent solves in one call (tk_batch); one Result per problem.
+        rfixes: optional per-problem fixed ranks (tuples of 3, 0 = eps rule)."""
+        cnt = len(probs)
+        rfixes = rfixes or [(0, 0, 0)] * cnt
+        ks = (Kernel * max(cnt, 1))(*[make_kernel(p) for p in probs])
+        gs = (Grid * max(cnt, 1))(*[make_grid(p) for p in probs])
+        os_ = (Opts * max(cnt, 1))(*[make_opts(p, precision, rf, shortcut, fold) for p, rf in zip(probs, rfixes)])
+        outs = (_vp * max(cnt, 1))()
+        _check(self.lib.tk_batch(self.ptr, cnt, ks, gs, os_, outs, _stream_ptr(stream)), self.ptr)
+        return [Result(self, _vp(outs[i]), probs[i]) for i in range(cnt)]
 
     # ---- diagnostics ----------------------------------------------------------
     def profile(self, on: bool = True):

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 
@@ -163,7 +164,8 @@ void check_opts(const tk_opts* o) {
     if (o->rfix[a] < 0 || o->rfix[a] > kMaxRank) fail(TK_EINVAL, "rfix must be in [0, 88]");
   }
   if (o->precision != TK_FP64 && o->precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
-  for (int i = 0; i < 4; ++i)
+  if (o->reflect_fold != 0 && o->reflect_fold != 1) fail(TK_EINVAL, "reflect_fold must be 0 or 1");
+  for (int i = 0; i < 3; ++i)
     if (o->reserved[i] != 0) fail(TK_EINVAL, "reserved fields must be zero");
 }
 
@@ -175,13 +177,6 @@ void set_device(tk_ctx* ctx) { TK_CUDA(cudaSetDevice(ctx->device)); }
 // The eigensolver adds its own margin columns to the subspace.
 int subspace_m(const tk_opts& o, int n, int a) {
   return std::min(std::max(o.rmax[a], o.rfix[a]), n);
-}
-
-bool shortcut_ok(const tk_kernel& k, const tk_grid& g, const tk_opts& o) {
-  return o.isotropic_shortcut && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.b[0] == g.b[1] &&
-         g.b[1] == g.b[2] && k.ell[0] == k.ell[1] && k.ell[1] == k.ell[2] &&
-         o.rmax[0] == o.rmax[1] && o.rmax[1] == o.rmax[2] && o.rfix[0] == o.rfix[1] &&
-         o.rfix[1] == o.rfix[2];
 }
 
 // TTM chain of Sec. 3.1/3.2 (mode 3, then 2, then 1), FP64 GEMMs.
@@ -245,6 +240,7 @@ void tk_default_opts(tk_opts* o) {
   for (int a = 0; a < 3; ++a) o->rmax[a] = 32;
   o->precision = TK_SLICED_BF16;
   o->isotropic_shortcut = 1;
+  o->reflect_fold = 1;
 }
 
 int tk_create(tk_ctx** out, int device) {
@@ -277,11 +273,16 @@ void tk_destroy(tk_ctx* ctx) {
   cudaDeviceSynchronize();
   ctx->prof.release();
   ctx->ws.release();
+  ctx->ws2.release();
   delete ctx;
 }
 
 void tk_result_free(tk_result* res) {
   if (!res) return;
+  if (res->mem) {  // a block shared with the other results of its batch
+    delete res;
+    return;
+  }
   if (res->ctx) cudaSetDevice(res->ctx->device);
   for (int a = 0; a < 3; ++a)
     if (res->U[a]) cudaFree(res->U[a]);
@@ -289,17 +290,17 @@ void tk_result_free(tk_result* res) {
   delete res;
 }
 
-int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
-              tk_result** out, void* stream) {
-  if (!ctx || !out) return TK_EINVAL;
-  std::lock_guard<std::mutex> lock(ctx->mu);
+}  // extern "C"
+
+namespace {
+
+// The unfolded solve on the whole tensor (reflect_fold = 0, or a fixed rank
+// above the even eigenvectors): Gram per mode, persymmetric eigensolve, rank,
+// core by the TTM chain.  Returns a new result.
+tk_result* tucker_full(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
+                       cudaStream_t s) {
   tk_result* res = nullptr;
-  int rc = guard(ctx, [&] {
-    check_kernel(kernel);
-    check_grid(grid);
-    check_opts(opts);
-    set_device(ctx);
-    cudaStream_t s = as_stream(stream);
+  try {
     const tk_opts& o = *opts;
     const int* n = grid->n;
     const size_t N = (size_t)n[0] * n[1] * n[2];
@@ -432,6 +433,38 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
     pf.end(s);
     TK_CUDA(cudaStreamSynchronize(s));
     pf.collect();
+  } catch (...) {
+    if (res) tk_result_free(res);
+    throw;
+  }
+  return res;
+}
+
+// One solve: the folded engine (a batch of one) when it applies.
+tk_result* solve_one(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
+                     cudaStream_t s) {
+  if (!fold_applicable(*grid, *opts)) return tucker_full(ctx, kernel, grid, opts, s);
+  SolveReq rq{*kernel, *grid, *opts};
+  tk_result* res = nullptr;
+  solve_bucket(ctx, ctx->ws, ctx->ws2, &ctx->prof, &rq, 1, &res, s);
+  return res;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
+              tk_result** out, void* stream) {
+  if (!ctx || !out) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  tk_result* res = nullptr;
+  int rc = guard(ctx, [&] {
+    check_kernel(kernel);
+    check_grid(grid);
+    check_opts(opts);
+    set_device(ctx);
+    res = solve_one(ctx, kernel, grid, opts, as_stream(stream));
   });
   if (rc != TK_OK) {
     if (res) tk_result_free(res);
@@ -439,6 +472,57 @@ int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const t
   }
   *out = res;
   return TK_OK;
+}
+
+int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* grids, const tk_opts* opts,
+             tk_result** outs, void* stream) {
+  if (!ctx || count < 0 || (count > 0 && (!kernels || !grids || !opts || !outs))) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  for (int i = 0; i < count; ++i) outs[i] = nullptr;
+  int rc = guard(ctx, [&] {
+    for (int i = 0; i < count; ++i) {
+      check_kernel(kernels + i);
+      check_grid(grids + i);
+      check_opts(opts + i);
+    }
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    std::map<BucketKey, std::vector<int>> buckets;
+    for (int i = 0; i < count; ++i) {
+      if (!fold_applicable(grids[i], opts[i])) {
+        outs[i] = tucker_full(ctx, kernels + i, grids + i, opts + i, s);
+        continue;
+      }
+      buckets[bucket_key(SolveReq{kernels[i], grids[i], opts[i]})].push_back(i);
+    }
+    for (auto& kv : buckets) {
+      const std::vector<int>& idx = kv.second;
+      // chunks that fit in about half of the free device memory
+      size_t free_b = 0, total_b = 0;
+      TK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      const size_t per = bucket_bytes_per_instance(kv.first);
+      const size_t fit = std::max<size_t>(1, (free_b / 2) / std::max<size_t>(per, 1));
+      const int chunk = (int)std::min<size_t>(idx.size(), std::min<size_t>(fit, 4096));
+      for (size_t c0 = 0; c0 < idx.size(); c0 += chunk) {
+        const int cnt = (int)std::min<size_t>(chunk, idx.size() - c0);
+        std::vector<SolveReq> rq(cnt);
+        std::vector<tk_result*> rs(cnt, nullptr);
+        for (int j = 0; j < cnt; ++j) {
+          const int i = idx[c0 + j];
+          rq[j] = SolveReq{kernels[i], grids[i], opts[i]};
+        }
+        solve_bucket(ctx, ctx->ws, ctx->ws2, &ctx->prof, rq.data(), cnt, rs.data(), s);
+        for (int j = 0; j < cnt; ++j) outs[idx[c0 + j]] = rs[j];
+      }
+    }
+  });
+  if (rc != TK_OK) {
+    for (int i = 0; i < count; ++i) {
+      if (outs[i]) tk_result_free(outs[i]);
+      outs[i] = nullptr;
+    }
+  }
+  return rc;
 }
 
 int tk_ranks(const tk_result* res, int32_t r[3], uint32_t flags[3]) {
@@ -516,8 +600,47 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
       if (grid->n[a] != res->n[a]) fail(TK_EINVAL, "grid does not match the result");
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
-    const int* n = res->n;
     const int* r = res->r;
+    if (res->fold) {
+      // |F - X| = |Fh - Xh| on the weighted octant: Xh from the core and the
+      // octant factors, Fh resampled; Xh is never stored
+      int h[3];
+      for (int a = 0; a < 3; ++a) h[a] = (res->n[a] + 1) / 2;
+      const size_t H = (size_t)h[0] * h[1] * h[2];
+      const bool tab = table_applicable(*kernel, *grid);
+      const size_t Q = tab ? (size_t)table_entries(grid->n[0]) : 1;
+      const size_t w1 = (size_t)h[0] * r[1] * r[2], w2 = (size_t)h[0] * h[1] * r[2];
+      GemmDesc d{h[0] * h[1], h[2], r[2], 1, nullptr, 0, r[2], 1, res->Uh[2], 0, 1, r[2], nullptr, 0, h[2], 1};
+      const size_t parts = gemm_err_partials(d);
+      const size_t np = eval_octant_parts(*grid);
+      ctx->ws.reserve(carve_bytes<KernelDev>(1) + carve_bytes<double>(H) + carve_bytes<double>(Q) +
+                          carve_bytes<double>(w1) + carve_bytes<double>(w2) + carve_bytes<double>(parts) +
+                          carve_bytes<double>(8) + carve_bytes<double>(np) + 4096,
+                      s);
+      KernelDev* kd = ctx->ws.take<KernelDev>(1);
+      double* Fh = ctx->ws.take<double>(H);
+      double* table = ctx->ws.take<double>(Q);
+      double* W1 = ctx->ws.take<double>(w1);
+      double* W2 = ctx->ws.take<double>(w2);
+      double* part = ctx->ws.take<double>(parts);
+      double* sums = ctx->ws.take<double>(8);
+      double* opart = ctx->ws.take<double>(np);
+      const KernelDev kh = make_kernel_dev(*kernel);
+      TK_CUDA(cudaMemcpyAsync(kd, &kh, sizeof(KernelDev), cudaMemcpyHostToDevice, s));
+      ctx->prof.begin(TK_STAGE_ERROR, s);
+      eval_octant_f64(kd, tab, *grid, 1, Fh, table, opart, sums + 4, s);
+      recon_w2(res->core, r, res->Uh[0], r[0], res->Uh[1], r[1], h, W1, W2, s);
+      d.A = W2;
+      gemm_f64_err(d, Fh, nullptr, 0, part, sums, s);
+      ctx->prof.end(s);
+      double hs[2];
+      TK_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      ctx->prof.collect();
+      *out = std::sqrt(hs[0] / hs[1]);
+      return;
+    }
+    const int* n = res->n;
     const size_t N = (size_t)n[0] * n[1] * n[2];
     const size_t w1 = (size_t)n[0] * r[1] * r[2], w2 = (size_t)n[0] * n[1] * r[2];
     GemmDesc d{n[0] * n[1], n[2], r[2], 1, nullptr, 0, r[2], 1, res->U[2], 0, 1, r[2], nullptr, 0, n[2], 1};

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 
 #include "tk_internal.h"
@@ -40,6 +41,14 @@ __global__ void k_random(double* X, long long len, unsigned long long seed) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
        t += (long long)gridDim.x * blockDim.x)
     X[t] = hash_uniform(seed, (unsigned long long)t);
+}
+
+// The same start block (len_per values) for each of B instances.
+__global__ void k_random_rep(double* X, long long len_per, int B, unsigned long long seed) {
+  const long long len = len_per * B;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    X[t] = hash_uniform(seed, (unsigned long long)(t % len_per));
 }
 
 // ---------------------------------------------------------------------------
@@ -497,8 +506,10 @@ __global__ void k_persym_merge(const double* __restrict__ le, const double* __re
 // the smallest r >= 1 whose discarded sum, tail beyond the m computed
 // eigenvalues (trace - their sum) plus the clamped computed ones from r on,
 // summed smallest first, is <= eps^2 |F|^2 / 3; capped at rmax.
+// n_eig: order of the matrix whose eigenvalues lam are (all computed when
+// m == n_eig); n_flag: the n of the precision flag's threshold.
 __device__ void rank_body(const double* lam, int m, double trace, double nf, double eps, int rmax, int rfix,
-                          double u_eff, int n, int* out) {
+                          double u_eff, int n_eig, int n_flag, int* out) {
   const double thr = eps * eps * nf / 3.0;
   double sum = 0.0, sc = 0.0;
   for (int i = 0; i < m; ++i) {
@@ -507,7 +518,7 @@ __device__ void rank_body(const double* lam, int m, double trace, double nf, dou
     sum = t;
   }
   double extra = trace - (sum + sc);
-  if (!(extra > 0.0) || m >= n) extra = 0.0;
+  if (!(extra > 0.0) || m >= n_eig) extra = 0.0;
   int r = m + 1;  // "more than computed"
   double ts = extra, tc = 0.0;
   if (ts <= thr) r = m;
@@ -527,21 +538,25 @@ __device__ void rank_body(const double* lam, int m, double trace, double nf, dou
     r = rmax;
     flags |= TK_RANK_CAPPED;
   }
-  if (thr < 10.0 * u_eff * (double)n * nf) flags |= TK_EPS_UNREACHABLE_AT_PRECISION;
+  if (thr < 10.0 * u_eff * (double)n_flag * nf) flags |= TK_EPS_UNREACHABLE_AT_PRECISION;
   out[0] = r;
   out[1] = flags;
 }
 
 __global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2, double eps, int rmax,
                        int rfix, double u_eff, int n, int* out) {
-  if (threadIdx.x == 0) rank_body(lam, m, trace[0], normF2[0], eps, rmax, rfix, u_eff, n, out);
+  if (threadIdx.x == 0) rank_body(lam, m, trace[0], normF2[0], eps, rmax, rfix, u_eff, n, n, out);
 }
 
-// One instance per thread: lam + b m, trace[b], normF2[b], eps[b], rmax[b], out + 4 b.
+// One instance per thread: lam + b m, trace[b], normF2[b], eps[b], rmax[b],
+// rfix[b], out + 4 b.
 __global__ void k_rank_batch(const double* lam, int m, const double* trace, const double* normF2, const double* epsv,
-                             const int* rmaxv, int rfix, double u_eff, int n, int B, int* out) {
+                             const int* rmaxv, const int* rfixv, double u_eff, int n_eig, int n_flag, int B,
+                             int* out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) rank_body(lam + (size_t)b * m, m, trace[b], normF2[b], epsv[b], rmaxv[b], rfix, u_eff, n, out + 4 * b);
+  if (b < B)
+    rank_body(lam + (size_t)b * m, m, trace[b], normF2[b], epsv[b], rmaxv[b], rfixv[b], u_eff, n_eig, n_flag,
+              out + 4 * b);
 }
 
 }  // namespace
@@ -730,127 +745,127 @@ void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, 
 }
 
 // ---------------------------------------------------------------------------
-// B instances with the same n and m (persymmetric Grams G: [b][n][n]).  The
-// even halves of all instances form one uniform group and the odd halves
-// another; each group's GEMMs are one batched launch and its QR and Jacobi
-// steps one launch with a CTA per problem.
+// B instances with the same n and m (G: [b][n][n]).  Every step is one launch
+// over all instances: the subspace products are batched GEMMs, QR and Jacobi
+// run one CTA per instance, and each instance starts from the same random
+// block, so an instance's eigenpairs do not depend on the batch around it.
 // ---------------------------------------------------------------------------
 namespace {
 
-struct HalfGroup {
-  int nh, mh, ms;
-  double *Gh, *Y, *Q, *W, *H, *VH, *lsub, *lam, *V;
+struct EigGroup {
+  int n, m, ms;
+  const double* G;
+  double *Y, *Q, *W, *H, *VH, *lsub;
+  double *lam, *V;
 };
 
-size_t group_doubles(int nh, int mh, int B) {
-  const int ms = subspace_cols(nh, mh);
-  return (size_t)B * ((size_t)nh * nh + 3ull * nh * ms + 2ull * ms * ms + ms + mh + (size_t)nh * mh) + 1024;
+size_t group_doubles(int n, int m, int B) {
+  const int ms = subspace_cols(n, m);
+  return (size_t)B * (3ull * n * ms + 2ull * ms * ms + ms) + 1024;
 }
 
-HalfGroup carve_group(double*& p, int nh, int mh, int B) {
-  HalfGroup g;
-  g.nh = nh;
-  g.mh = mh;
-  g.ms = subspace_cols(nh, mh);
-  auto take = [&](size_t n) {
+EigGroup carve_group(double* p, const double* G, int n, int m, int B, double* lam, double* V) {
+  EigGroup g;
+  g.n = n;
+  g.m = m;
+  g.ms = subspace_cols(n, m);
+  g.G = G;
+  g.lam = lam;
+  g.V = V;
+  auto take = [&](size_t k) {
     double* q = p;
-    p += (n + 31) & ~size_t(31);
+    p += (k + 31) & ~size_t(31);
     return q;
   };
-  g.Gh = take((size_t)B * nh * nh);
-  g.Y = take((size_t)B * nh * g.ms);
-  g.Q = take((size_t)B * nh * g.ms);
-  g.W = take((size_t)B * nh * g.ms);
+  g.Y = take((size_t)B * n * g.ms);
+  g.Q = take((size_t)B * n * g.ms);
+  g.W = take((size_t)B * n * g.ms);
   g.H = take((size_t)B * g.ms * g.ms);
   g.VH = take((size_t)B * g.ms * g.ms);
   g.lsub = take((size_t)B * g.ms);
-  g.lam = take((size_t)B * mh);
-  g.V = take((size_t)B * nh * mh);
   return g;
 }
 
-void solve_group(const HalfGroup& g, int B, cudaStream_t s) {
-  const int nh = g.nh, ms = g.ms, mh = g.mh;
-  if (nh == 0) return;
-  if (ms == nh) {
+void solve_group(const EigGroup& g, int B, cudaStream_t s) {
+  const int n = g.n, ms = g.ms, m = g.m;
+  if (ms == n) {
     // whole matrices: Jacobi directly
-    TK_CUDA(cudaMemcpyAsync(g.H, g.Gh, sizeof(double) * (size_t)B * nh * nh, cudaMemcpyDeviceToDevice, s));
+    TK_CUDA(cudaMemcpyAsync(g.H, g.G, sizeof(double) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    k_random<<<256, 256, 0, s>>>(g.Y, (long long)B * nh * ms, 0x1711068740ull + (unsigned)nh);
-    TK_LAUNCH("k_random");
-    const size_t need = 2ull * nh * ms * sizeof(double);
+    k_random_rep<<<(unsigned)std::min<long long>(((long long)B * n * ms + 255) / 256, 1024), 256, 0, s>>>(
+        g.Y, (long long)n * ms, B, 0x1711068740ull + (unsigned)n);
+    TK_LAUNCH("k_random_rep");
+    const size_t need = 2ull * n * ms * sizeof(double);
     for (int pass = 0; pass < 2; ++pass) {
       const double* src = (pass == 0) ? g.Y : g.Q;
-      GemmDesc d{nh, ms, nh, B, g.Gh, (long long)nh * nh, nh, 1, src, (long long)nh * ms, 1, nh,
-                 g.W, (long long)nh * ms, 1, nh};
+      GemmDesc d{n, ms, n, B, g.G, (long long)n * n, n, 1, src, (long long)n * ms, 1, n,
+                 g.W, (long long)n * ms, 1, n};
+      d.fixed_order = 1;
       gemm_f64(d, s);
-      TK_CUDA(cudaMemcpyAsync(g.Y, g.W, sizeof(double) * (size_t)B * nh * ms, cudaMemcpyDeviceToDevice, s));
+      TK_CUDA(cudaMemcpyAsync(g.Y, g.W, sizeof(double) * (size_t)B * n * ms, cudaMemcpyDeviceToDevice, s));
       if (need <= kQrSmemMax)
-        k_householder_qr_strided<true><<<B, 1024, need, s>>>(g.Y, g.Q, nh, ms, (long long)nh * ms);
+        k_householder_qr_strided<true><<<B, 1024, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       else
-        k_householder_qr_strided<false><<<B, 1024, 0, s>>>(g.Y, g.Q, nh, ms, (long long)nh * ms);
+        k_householder_qr_strided<false><<<B, 1024, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       TK_LAUNCH("k_householder_qr_strided");
     }
-    GemmDesc d1{nh, ms, nh, B, g.Gh, (long long)nh * nh, nh, 1, g.Q, (long long)nh * ms, 1, nh,
-                g.W, (long long)nh * ms, 1, nh};
+    GemmDesc d1{n, ms, n, B, g.G, (long long)n * n, n, 1, g.Q, (long long)n * ms, 1, n,
+                g.W, (long long)n * ms, 1, n};
+    d1.fixed_order = 1;
     gemm_f64(d1, s);
-    GemmDesc d2{ms, ms, nh, B, g.Q, (long long)nh * ms, nh, 1, g.W, (long long)nh * ms, 1, nh,
+    GemmDesc d2{ms, ms, n, B, g.Q, (long long)n * ms, n, 1, g.W, (long long)n * ms, 1, n,
                 g.H, (long long)ms * ms, ms, 1};
+    d2.fixed_order = 1;
     gemm_f64(d2, s);
-    k_symmetrize_batch<<<(unsigned)std::min<long long>(((long long)B * ms * ms + 255) / 256, 4096), 256, 0, s>>>(g.H, ms, B);
+    k_symmetrize_batch<<<(unsigned)std::min<long long>(((long long)B * ms * ms + 255) / 256, 4096), 256, 0, s>>>(
+        g.H, ms, B);
     TK_LAUNCH("k_symmetrize_batch");
   }
   k_jacobi_strided<<<B, 1024, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
   TK_LAUNCH("k_jacobi_strided");
-  if (ms == nh) {
-    // first mh columns of V_H (ms x ms) into V (nh x mh)
-    TK_CUDA(cudaMemcpy2DAsync(g.V, sizeof(double) * mh, g.VH, sizeof(double) * ms, sizeof(double) * mh,
-                              (size_t)B * nh, cudaMemcpyDeviceToDevice, s));
+  if (ms == n) {
+    // first m columns of V_H (n x n) into V (n x m)
+    TK_CUDA(cudaMemcpy2DAsync(g.V, sizeof(double) * m, g.VH, sizeof(double) * ms, sizeof(double) * m,
+                              (size_t)B * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    GemmDesc d3{nh, mh, ms, B, g.Q, (long long)nh * ms, 1, nh, g.VH, (long long)ms * ms, ms, 1,
-                g.V, (long long)nh * mh, mh, 1};
+    GemmDesc d3{n, m, ms, B, g.Q, (long long)n * ms, 1, n, g.VH, (long long)ms * ms, ms, 1,
+                g.V, (long long)n * m, m, 1};
+    d3.fixed_order = 1;
     gemm_f64(d3, s);
   }
-  TK_CUDA(cudaMemcpy2DAsync(g.lam, sizeof(double) * mh, g.lsub, sizeof(double) * ms, sizeof(double) * mh, B,
+  TK_CUDA(cudaMemcpy2DAsync(g.lam, sizeof(double) * m, g.lsub, sizeof(double) * ms, sizeof(double) * m, B,
                             cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace
 
-size_t sym_eig_persym_batch_scratch_doubles(int n, int m, int B) {
-  const int ho = n / 2, he = n - ho;
-  const int me = std::min(he, (m + 1) / 2 + 4), mo = std::min(ho, (m + 1) / 2 + 4);
-  return group_doubles(he, me, B) + group_doubles(ho, mo, B) + 4096;
-}
+size_t sym_eig_batch_scratch_doubles(int n, int m, int B) { return group_doubles(n, m, B) + 4096; }
 
-void sym_eig_persym_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, int* safe,
-                          double* scratch, cudaStream_t s) {
+void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
+                   cudaStream_t s) {
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
+  if (B < 1) return;
   set_attrs();
-  TK_CUDA(cudaFuncSetAttribute(k_householder_qr_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kQrSmemMax));
-  TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)jacobi_smem(kMaxM)));
-  const int ho = n / 2, he = n - ho;
-  const int me = std::min(he, (m + 1) / 2 + 4), mo = std::min(ho, (m + 1) / 2 + 4);
-  double* p = scratch;
-  const HalfGroup ge = carve_group(p, he, me, B);
-  const HalfGroup go = carve_group(p, ho, mo, B);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_householder_qr_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kQrSmemMax));
+    TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)jacobi_smem(kMaxM)));
+  });
+  const EigGroup g = carve_group(scratch, G, n, m, B, lam, V);
   k_trace<<<B, 256, 0, s>>>(G, n, trace);
   TK_LAUNCH("k_trace");
-  k_persym_split<<<dim3(64, B), 256, 0, s>>>(G, n, ge.Gh, go.Gh);
-  TK_LAUNCH("k_persym_split");
-  solve_group(ge, B, s);
-  solve_group(go, B, s);
-  k_persym_merge<<<B, 256, 0, s>>>(ge.lam, ge.V, me, go.lam, go.V, mo, n, m, lam, V, safe);
-  TK_LAUNCH("k_persym_merge");
+  solve_group(g, B, s);
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }
 
 void rank_rule_batch(const double* lam, int m, const double* trace, const double* normF2, const double* eps,
-                     const int* rmax, int rfix, double u_eff, int n, int B, int* out, cudaStream_t s) {
-  k_rank_batch<<<(B + 127) / 128, 128, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n, B, out);
+                     const int* rmax, const int* rfix, double u_eff, int n_eig, int n_flag, int B, int* out,
+                     cudaStream_t s) {
+  k_rank_batch<<<(B + 127) / 128, 128, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n_eig, n_flag, B,
+                                               out);
   TK_LAUNCH("k_rank_batch");
 }
 

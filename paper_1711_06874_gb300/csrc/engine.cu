@@ -1,0 +1,572 @@
+// Batched HOSVD engine.  B solves that share a grid, a precision and rank caps
+// run together: every stage of Sec. 3.2 (sample, Gram per mode, leading
+// eigenpairs and rank per mode, core by chained TTMs) is one launch over all
+// of them.  This is the parameter sweep that the likelihood of Eq. (like)
+// needs, and the unit of work of the serving loop.  A single solve is a
+// batch of one.
+//
+// Every solve runs on the weighted octant of the folded tensor: F is
+// unchanged by reversing any axis (the covariance depends on x_a^2 only and
+// the grid is symmetric about 0), so each G_k = F_(k) F_(k)^T satisfies
+// G_k J = G_k (J the reversal).  Its odd eigenvectors have eigenvalue 0 and its
+// even ones are u = [J W^(-1/2) v ; W^(-1/2) v] padded around the centre, with
+// v the eigenvectors (same eigenvalues) of the octant Gram Gh_k = Fh_(k)
+// Fh_(k)^T, Fh = sqrt(w w w) F on the octant (w = points each octant index
+// stands for).  The core, a sum over the whole grid, equals
+// Fh x_1 V_1^T x_2 V_2^T x_3 V_3^T, and |F - X| = |Fh - Xh|.  So the Gram costs
+// 1/16 of the full one and the TTM chain 1/8, with the same factors, core and
+// eigenvalues.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "tk_internal.h"
+
+namespace tk {
+
+DeviceBlock::~DeviceBlock() {
+  if (ptr) {
+    cudaSetDevice(device);
+    cudaFree(ptr);
+  }
+}
+
+bool shortcut_ok(const tk_kernel& k, const tk_grid& g, const tk_opts& o) {
+  return o.isotropic_shortcut && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.b[0] == g.b[1] &&
+         g.b[1] == g.b[2] && k.ell[0] == k.ell[1] && k.ell[1] == k.ell[2] &&
+         o.rmax[0] == o.rmax[1] && o.rmax[1] == o.rmax[2] && o.rfix[0] == o.rfix[1] &&
+         o.rfix[1] == o.rfix[2];
+}
+
+bool fold_applicable(const tk_grid& g, const tk_opts& o) {
+  if (!o.reflect_fold) return false;
+  for (int a = 0; a < 3; ++a)
+    if (o.rfix[a] > (g.n[a] + 1) / 2) return false;  // more vectors than the even ones
+  return true;
+}
+
+static auto key_tuple(const BucketKey& k) {
+  return std::make_tuple(k.n[0], k.n[1], k.n[2], k.b[0], k.b[1], k.b[2], k.kind, k.precision, k.nmodes, k.tab,
+                         k.m[0], k.m[1], k.m[2]);
+}
+bool BucketKey::operator<(const BucketKey& o) const { return key_tuple(*this) < key_tuple(o); }
+bool BucketKey::operator==(const BucketKey& o) const { return key_tuple(*this) == key_tuple(o); }
+
+BucketKey bucket_key(const SolveReq& r) {
+  BucketKey k{};
+  for (int a = 0; a < 3; ++a) {
+    k.n[a] = r.g.n[a];
+    k.b[a] = r.g.b[a];
+    k.m[a] = std::min(std::max(r.o.rmax[a], r.o.rfix[a]), (r.g.n[a] + 1) / 2);
+  }
+  k.kind = r.g.kind;
+  k.precision = r.o.precision;
+  k.nmodes = shortcut_ok(r.k, r.g, r.o) ? 1 : 3;
+  k.tab = table_applicable(r.k, r.g) ? 1 : 0;
+  return k;
+}
+
+namespace {
+
+constexpr int kPhaseA = 16;  // eigenpairs of the first pass (enough for ranks <= 16)
+
+int roundup(int x, int q) { return (x + q - 1) / q * q; }
+
+__global__ void k_gather_mats(const double* __restrict__ src, const int* __restrict__ idx, int count, long long per,
+                              double* __restrict__ dst) {
+  const long long total = per * count;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / per, o = e - j * per;
+    dst[e] = src[(long long)idx[j] * per + o];
+  }
+}
+
+// Factor extraction of one (instance, mode): V (h x ldv, leading r columns
+// used) holds octant eigenvectors v.  Writes U (n x r, the full factor with
+// canonical signs: the entry of largest magnitude among the first ceil(n/2)
+// rows positive), Uh (h x r, the signed octant vectors) and Up (h x R, Uh
+// padded with zero columns for the batched TTM).
+struct UnfoldDesc {
+  const double* V;
+  double* U;
+  double* Uh;
+  double* Up;
+  int ldv, r, R, h, n;
+};
+
+__global__ void k_unfold(const UnfoldDesc* __restrict__ descs) {
+  const UnfoldDesc d = descs[blockIdx.y];
+  const int c = blockIdx.x;
+  if (c >= d.R) return;
+  if (c >= d.r) {
+    for (int i = threadIdx.x; i < d.h; i += blockDim.x) d.Up[(long long)i * d.R + c] = 0.0;
+    return;
+  }
+  const int odd = d.n & 1, base = d.n / 2;
+  const double iw = 0.7071067811865476;  // 1 / sqrt(2), correctly rounded
+  // full row q < h is the mirror of octant index i = n - 1 - q - base
+  __shared__ double bv[256];
+  __shared__ int bq[256];
+  double best = -1.0;
+  int bidx = 0;
+  for (int q = threadIdx.x; q < d.h; q += blockDim.x) {
+    const int i = d.n - 1 - q - base;
+    const double a = fabs(d.V[(long long)i * d.ldv + c]) * ((odd && i == 0) ? 1.0 : iw);
+    if (a > best) {
+      best = a;
+      bidx = q;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bq[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double o = bv[threadIdx.x + w];
+      const int oq = bq[threadIdx.x + w];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oq < bq[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bq[threadIdx.x] = oq;
+      }
+    }
+    __syncthreads();
+  }
+  const int i0 = d.n - 1 - bq[0] - base;
+  const double sgn = (d.V[(long long)i0 * d.ldv + c] < 0.0) ? -1.0 : 1.0;
+  for (int i = threadIdx.x; i < d.h; i += blockDim.x) {
+    const double v = sgn * d.V[(long long)i * d.ldv + c];
+    d.Uh[(long long)i * d.r + c] = v;
+    d.Up[(long long)i * d.R + c] = v;
+    const double u = (odd && i == 0) ? v : v * iw;
+    const int row = base + i, mir = d.n - 1 - row;
+    d.U[(long long)row * d.r + c] = u;
+    if (mir != row) d.U[(long long)mir * d.r + c] = u;
+  }
+}
+
+struct CoreDesc {
+  const double* src;  // R x R x R padded core
+  double* dst;        // r1 x r2 x r3
+  int R, r1, r2, r3;
+};
+
+__global__ void k_extract_core(const CoreDesc* __restrict__ descs) {
+  const CoreDesc d = descs[blockIdx.y];
+  const long long total = (long long)d.r1 * d.r2 * d.r3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / ((long long)d.r2 * d.r3));
+    const int rem = (int)(e - (long long)a * d.r2 * d.r3);
+    const int b = rem / d.r3, c = rem % d.r3;
+    d.dst[e] = d.src[((long long)a * d.R + b) * d.R + c];
+  }
+}
+
+// Carves of one workspace from a list of sizes (bytes), 256-byte aligned.
+struct Plan {
+  std::vector<size_t> sizes;
+  size_t add(size_t bytes) {
+    sizes.push_back(bytes);
+    return sizes.size() - 1;
+  }
+  size_t total() const {
+    size_t t = 0;
+    for (size_t b : sizes) t += (b + 255) & ~size_t(255);
+    return t + 256;
+  }
+};
+
+struct Carver {
+  Workspace& ws;
+  template <class T>
+  T* take(size_t count) {
+    return ws.take<T>(std::max<size_t>(count, 1));
+  }
+};
+
+}  // namespace
+
+size_t bucket_bytes_per_instance(const BucketKey& k) {
+  int h[3];
+  for (int a = 0; a < 3; ++a) h[a] = (k.n[a] + 1) / 2;
+  const size_t H = (size_t)h[0] * h[1] * h[2];
+  size_t b = 8 * H;                                        // Fh
+  if (k.tab) b += 8 * (size_t)table_entries(k.n[0]);       // table
+  for (int a = 0; a < k.nmodes; ++a) {
+    const int m = k.m[a];
+    b += 8 * (3ull * h[a] * h[a] + 2ull * h[a] * m);           // G, gathered G, V
+    b += 8 * sym_eig_batch_scratch_doubles(h[a], m, 1);
+    b += (k.precision == TK_SLICED_BF16) ? gram_sliced_scratch_bytes(h, a, 1) : 8 * gram_f64_scratch_doubles(h, a, 1);
+  }
+  const int R = roundup(std::max(k.m[0], std::max(k.m[1], k.m[2])), 4);
+  b += 8 * ((size_t)h[0] * h[1] * R + (size_t)R * h[1] * R + (size_t)R * R * R + 3ull * h[0] * R);  // TTM
+  b += 8 * (3ull * (k.n[0] + h[0]) * R + (size_t)R * R * R);                                      // results
+  return b + 16384;
+}
+
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, const SolveReq* req, int B,
+                  tk_result** outs, cudaStream_t s) {
+  if (B < 1) return;
+  const tk_grid& g = req[0].g;
+  const BucketKey key = bucket_key(req[0]);
+  const int nmodes = key.nmodes;
+  const bool tab = key.tab != 0;
+  const bool sliced = key.precision == TK_SLICED_BF16;
+  const double u_eff = gram_u_eff(key.precision);
+  int n[3], h[3], m[3], mA[3];
+  for (int a = 0; a < 3; ++a) {
+    n[a] = g.n[a];
+    h[a] = (n[a] + 1) / 2;
+    m[a] = key.m[a];
+    mA[a] = std::min(m[a], kPhaseA);
+  }
+  const long long H = (long long)h[0] * h[1] * h[2];
+  const long long Q = tab ? table_entries(n[0]) : 0;
+  const size_t nparts = eval_octant_parts(g);
+  size_t gram_bytes = 0, eig_doubles = 0;
+  for (int a = 0; a < nmodes; ++a) {
+    gram_bytes = std::max(gram_bytes, sliced ? gram_sliced_scratch_bytes(h, a, B)
+                                             : 8 * gram_f64_scratch_doubles(h, a, B));
+    eig_doubles = std::max(eig_doubles, sym_eig_batch_scratch_doubles(h[a], m[a], B));
+  }
+  int hmax = 0;
+  for (int a = 0; a < nmodes; ++a) hmax = std::max(hmax, h[a]);
+
+  // ---------------- first phase: up to the rank decision ----------------
+  // ints: [0] timeout flag; rmax, rfix [mode][b]; outA, outB [mode][b][4];
+  // staging of the escalated instances (index, rmax, rfix)
+  const int nint = 16 + 33 * B;
+  size_t need = carve_bytes<KernelDev>(B) + carve_bytes<double>(Q * B) + carve_bytes<double>(H * B) +
+                carve_bytes<double>(nparts * B) + 3 * carve_bytes<double>(B) + carve_bytes<int>(nint) +
+                carve_bytes<char>(gram_bytes) + carve_bytes<double>(eig_doubles) +
+                carve_bytes<double>((size_t)B * hmax * hmax) + carve_bytes<double>(B);
+  for (int a = 0; a < nmodes; ++a)
+    need += carve_bytes<double>((size_t)B * h[a] * h[a]) + carve_bytes<double>((size_t)B * mA[a]) +
+            carve_bytes<double>((size_t)B * h[a] * mA[a]) + carve_bytes<double>(B) +
+            carve_bytes<double>((size_t)B * m[a]) + carve_bytes<double>((size_t)B * h[a] * m[a]);
+  pre.reserve(need + 4096, s);
+  KernelDev* kd = pre.take<KernelDev>(B);
+  double* table = pre.take<double>(std::max<long long>(1, Q * B));
+  double* Fh = pre.take<double>(H * B);
+  double* part = pre.take<double>(nparts * B);
+  double* normF2 = pre.take<double>(B);
+  double* epsv = pre.take<double>(B);
+  double* aux = pre.take<double>(B);  // gathered |F|^2 / eps of the escalated instances
+  int* ints = pre.take<int>(nint);
+  char* gscr = pre.take<char>(std::max<size_t>(gram_bytes, 1));
+  double* escr = pre.take<double>(eig_doubles);
+  double* GJ = pre.take<double>((size_t)B * hmax * hmax);
+  double* traceB = pre.take<double>(B);
+  double *G[3] = {}, *lamA[3] = {}, *VA[3] = {}, *traceA[3] = {}, *lamB[3] = {}, *VB[3] = {};
+  for (int a = 0; a < nmodes; ++a) {
+    G[a] = pre.take<double>((size_t)B * h[a] * h[a]);
+    lamA[a] = pre.take<double>((size_t)B * mA[a]);
+    VA[a] = pre.take<double>((size_t)B * h[a] * mA[a]);
+    traceA[a] = pre.take<double>(B);
+    lamB[a] = pre.take<double>((size_t)B * m[a]);
+    VB[a] = pre.take<double>((size_t)B * h[a] * m[a]);
+  }
+  int* errflag = ints;
+  int* rmaxv = ints + 16;           // [a][b]
+  int* rfixv = rmaxv + 3 * B;       // [a][b]
+  int* outA = rfixv + 3 * B;        // [a][b][4]
+  int* outB = outA + 12 * B;        // [a][j][4]
+  int* stage = outB + 12 * B;       // 3 B
+
+  // host-side parameters, one staged copy
+  std::vector<KernelDev> kdh(B);
+  std::vector<double> epsh(B);
+  std::vector<int> ih(16 + 6 * B, 0);
+  for (int b = 0; b < B; ++b) {
+    kdh[b] = make_kernel_dev(req[b].k);
+    epsh[b] = req[b].o.eps;
+    for (int a = 0; a < 3; ++a) {
+      ih[16 + a * B + b] = req[b].o.rmax[a];
+      ih[16 + 3 * B + a * B + b] = req[b].o.rfix[a];
+    }
+  }
+  TK_CUDA(cudaMemcpyAsync(kd, kdh.data(), sizeof(KernelDev) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(epsv, epsh.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(ints, ih.data(), sizeof(int) * ih.size(), cudaMemcpyHostToDevice, s));
+
+  if (pf) pf->begin(TK_STAGE_EVAL, s);
+  eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s);
+  if (pf) pf->end(s);
+  for (int a = 0; a < nmodes; ++a) {
+    if (pf) pf->begin(TK_STAGE_GRAM, s);
+    if (sliced)
+      gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s);
+    else
+      gram_f64_batch(Fh, h, a, B, G[a], (double*)gscr, s);
+    if (pf) pf->end(s);
+    if (pf) pf->begin(TK_STAGE_EIG, s);
+    sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s);
+    if (pf) pf->end(s);
+    if (pf) pf->begin(TK_STAGE_RANK, s);
+    rank_rule_batch(lamA[a], mA[a], traceA[a], normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], B,
+                    outA + 4 * B * a, s);
+    if (pf) pf->end(s);
+  }
+  std::vector<int> hA(12 * B + 1);
+  std::vector<double> hnorm(B);
+  std::vector<std::vector<double>> hlamA(nmodes), hlamB(nmodes);
+  TK_CUDA(cudaMemcpyAsync(hA.data(), outA, sizeof(int) * 4 * B * nmodes, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(&hA[12 * B], errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(hnorm.data(), normF2, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  for (int a = 0; a < nmodes; ++a) {
+    hlamA[a].resize((size_t)B * mA[a]);
+    TK_CUDA(cudaMemcpyAsync(hlamA[a].data(), lamA[a], sizeof(double) * B * mA[a], cudaMemcpyDeviceToHost, s));
+  }
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (hA[12 * B] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+
+  // ---------------- escalation: all m pairs where the rank needs them ----------------
+  std::vector<std::vector<int>> J(nmodes);
+  std::vector<int> slotJ((size_t)B * 3, -1);  // position of instance b in mode a's escalated batch
+  bool any = false;
+  for (int a = 0; a < nmodes; ++a) {
+    if (mA[a] >= m[a]) continue;
+    for (int b = 0; b < B; ++b) {
+      const int rf = req[b].o.rfix[a];
+      const int needed = rf > 0 ? std::min(rf, m[a]) : hA[4 * B * a + 4 * b + 2];
+      if (needed > mA[a]) {
+        slotJ[(size_t)a * B + b] = (int)J[a].size();
+        J[a].push_back(b);
+      }
+    }
+    any = any || !J[a].empty();
+  }
+  std::vector<int> hB(12 * B, 0);
+  if (any) {
+    for (int a = 0; a < nmodes; ++a) {
+      const int nj = (int)J[a].size();
+      if (nj == 0) continue;
+      // gathered parameters: idx, rmax, rfix (ints); |F|^2, eps (doubles)
+      std::vector<int> ij(3 * nj);
+      std::vector<double> dj(2 * nj);
+      for (int j = 0; j < nj; ++j) {
+        const int b = J[a][j];
+        ij[j] = b;
+        ij[nj + j] = req[b].o.rmax[a];
+        ij[2 * nj + j] = req[b].o.rfix[a];
+        dj[j] = hnorm[b];
+        dj[nj + j] = req[b].o.eps;
+      }
+      int* ijd = stage;
+      double* njd = aux;
+      TK_CUDA(cudaMemcpyAsync(ijd, ij.data(), sizeof(int) * 3 * nj, cudaMemcpyHostToDevice, s));
+      TK_CUDA(cudaMemcpyAsync(njd, dj.data(), sizeof(double) * nj, cudaMemcpyHostToDevice, s));
+      TK_CUDA(cudaMemcpyAsync(epsv, dj.data() + nj, sizeof(double) * nj, cudaMemcpyHostToDevice, s));
+      const long long per = (long long)h[a] * h[a];
+      k_gather_mats<<<(unsigned)std::min<long long>((per * nj + 255) / 256, 4096), 256, 0, s>>>(G[a], ijd, nj, per,
+                                                                                               GJ);
+      TK_LAUNCH("k_gather_mats");
+      if (pf) pf->begin(TK_STAGE_EIG, s);
+      sym_eig_batch(GJ, h[a], m[a], nj, lamB[a], VB[a], traceB, escr, s);
+      if (pf) pf->end(s);
+      if (pf) pf->begin(TK_STAGE_RANK, s);
+      rank_rule_batch(lamB[a], m[a], traceB, njd, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj,
+                      outB + 4 * B * a, s);
+      if (pf) pf->end(s);
+      // the next mode's staging reuses these buffers: wait for this mode's use
+      TK_CUDA(cudaMemcpyAsync(hB.data() + 4 * B * a, outB + 4 * B * a, sizeof(int) * 4 * nj, cudaMemcpyDeviceToHost,
+                              s));
+      hlamB[a].resize((size_t)nj * m[a]);
+      TK_CUDA(cudaMemcpyAsync(hlamB[a].data(), lamB[a], sizeof(double) * nj * m[a], cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+
+  // ---------------- results ----------------
+  struct Final {
+    int r[3];
+    unsigned flags[3];
+    const double* V[3];
+    int ldv[3];
+    int R;
+  };
+  std::vector<Final> fin(B);
+  for (int b = 0; b < B; ++b) {
+    Final& f = fin[b];
+    int rmx = 1;
+    for (int a = 0; a < nmodes; ++a) {
+      const int j = slotJ[(size_t)a * B + b];
+      const int* o = (j >= 0) ? &hB[4 * B * a + 4 * j] : &hA[4 * B * a + 4 * b];
+      f.r[a] = o[0];
+      f.flags[a] = (unsigned)o[1];
+      f.V[a] = (j >= 0) ? VB[a] + (size_t)j * h[a] * m[a] : VA[a] + (size_t)b * h[a] * mA[a];
+      f.ldv[a] = (j >= 0) ? m[a] : mA[a];
+      rmx = std::max(rmx, f.r[a]);
+    }
+    for (int a = nmodes; a < 3; ++a) {
+      f.r[a] = f.r[0];
+      f.flags[a] = f.flags[0];
+      f.V[a] = f.V[0];
+      f.ldv[a] = f.ldv[0];
+    }
+    f.R = roundup(rmx, 4);
+  }
+  // one device block for every result of the batch
+  std::vector<size_t> offU((size_t)B * 3), offUh((size_t)B * 3), offC(B);
+  size_t tot = 0;
+  auto put = [&](size_t cnt) {
+    const size_t o = tot;
+    tot += (cnt + 31) & ~size_t(31);
+    return o;
+  };
+  for (int b = 0; b < B; ++b) {
+    for (int a = 0; a < nmodes; ++a) {
+      offU[(size_t)b * 3 + a] = put((size_t)n[a] * fin[b].r[a]);
+      offUh[(size_t)b * 3 + a] = put((size_t)h[a] * fin[b].r[a]);
+    }
+    offC[b] = put((size_t)fin[b].r[0] * fin[b].r[1] * fin[b].r[2]);
+  }
+  auto mem = std::make_shared<DeviceBlock>();
+  mem->device = ctx->device;
+  if (cudaMalloc(&mem->ptr, sizeof(double) * std::max<size_t>(tot, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    mem->ptr = nullptr;
+    fail(TK_ENOMEM, "cannot allocate the results of a batch");
+  }
+  double* rbase = static_cast<double*>(mem->ptr);
+
+  // rank groups (padded rank R), each one chain of batched TTMs
+  std::map<int, std::vector<int>> groups;
+  for (int b = 0; b < B; ++b) groups[fin[b].R].push_back(b);
+  size_t ttm = 0;
+  std::vector<int> amaph;
+  struct GroupBuf {
+    int R, off, cnt;
+    size_t up[3], t1, t2, cp;
+  };
+  std::vector<GroupBuf> gb;
+  std::vector<int> posInGroup(B);
+  for (auto& kv : groups) {
+    GroupBuf q{};
+    q.R = kv.first;
+    q.off = (int)amaph.size();
+    q.cnt = (int)kv.second.size();
+    for (size_t j = 0; j < kv.second.size(); ++j) {
+      posInGroup[kv.second[j]] = (int)j;
+      amaph.push_back(kv.second[j]);
+    }
+    auto tput = [&](size_t cnt) {
+      const size_t o = ttm;
+      ttm += (cnt + 31) & ~size_t(31);
+      return o;
+    };
+    for (int a = 0; a < nmodes; ++a) q.up[a] = tput((size_t)q.cnt * h[a] * q.R);
+    q.t1 = tput((size_t)q.cnt * h[0] * h[1] * q.R);
+    q.t2 = tput((size_t)q.cnt * q.R * h[1] * q.R);
+    q.cp = tput((size_t)q.cnt * q.R * q.R * q.R);
+    gb.push_back(q);
+  }
+  const size_t ndesc = (size_t)B * nmodes;
+  post.reserve(carve_bytes<double>(ttm) + carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
+                   carve_bytes<CoreDesc>(B) + 4096,
+               s);
+  double* tbase = post.take<double>(std::max<size_t>(ttm, 1));
+  int* amap = post.take<int>(B);
+  UnfoldDesc* ud = post.take<UnfoldDesc>(ndesc);
+  CoreDesc* cd = post.take<CoreDesc>(B);
+  std::map<int, int> groupOf;
+  for (size_t q = 0; q < gb.size(); ++q) groupOf[gb[q].R] = (int)q;
+  std::vector<UnfoldDesc> udh(ndesc);
+  std::vector<CoreDesc> cdh(B);
+  int Rmax = 4;
+  for (int b = 0; b < B; ++b) {
+    const GroupBuf& q = gb[groupOf[fin[b].R]];
+    const int pos = posInGroup[b];
+    Rmax = std::max(Rmax, q.R);
+    for (int a = 0; a < nmodes; ++a) {
+      UnfoldDesc& d = udh[(size_t)b * nmodes + a];
+      d.V = fin[b].V[a];
+      d.ldv = fin[b].ldv[a];
+      d.r = fin[b].r[a];
+      d.R = q.R;
+      d.h = h[a];
+      d.n = n[a];
+      d.U = rbase + offU[(size_t)b * 3 + a];
+      d.Uh = rbase + offUh[(size_t)b * 3 + a];
+      d.Up = tbase + q.up[a] + (size_t)pos * h[a] * q.R;
+    }
+    cdh[b] = CoreDesc{tbase + q.cp + (size_t)pos * q.R * q.R * q.R, rbase + offC[b], q.R, fin[b].r[0], fin[b].r[1],
+                      fin[b].r[2]};
+  }
+  TK_CUDA(cudaMemcpyAsync(amap, amaph.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(ud, udh.data(), sizeof(UnfoldDesc) * ndesc, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(cd, cdh.data(), sizeof(CoreDesc) * B, cudaMemcpyHostToDevice, s));
+  if (pf) pf->begin(TK_STAGE_RANK, s);
+  k_unfold<<<dim3(Rmax, (unsigned)ndesc), 128, 0, s>>>(ud);
+  TK_LAUNCH("k_unfold");
+  if (pf) pf->end(s);
+  if (pf) pf->begin(TK_STAGE_CORE, s);
+  for (const GroupBuf& q : gb) {
+    const int R = q.R;
+    const double* Up0 = tbase + q.up[0];
+    const double* Up1 = tbase + q.up[nmodes == 1 ? 0 : 1];
+    const double* Up2 = tbase + q.up[nmodes == 1 ? 0 : 2];
+    double* T1 = tbase + q.t1;
+    double* T2 = tbase + q.t2;
+    double* Cp = tbase + q.cp;
+    // mode 3: T1[(i,k)][c] = sum_l Fh[(i,k)][l] V3[l][c]
+    GemmDesc d1{h[0] * h[1], R, h[2], q.cnt, Fh, H, h[2], 1, Up2, (long long)h[2] * R, R, 1,
+                T1, (long long)h[0] * h[1] * R, R, 1};
+    d1.amap = amap + q.off;
+    d1.fixed_order = 1;
+    gemm_f64(d1, s);
+    // mode 1: T2[a][(k,c)] = sum_i V1[i][a] T1[i][(k,c)]
+    GemmDesc d2{R, h[1] * R, h[0], q.cnt, Up0, (long long)h[0] * R, 1, R, T1, (long long)h[0] * h[1] * R,
+                (long long)h[1] * R, 1, T2, (long long)R * h[1] * R, (long long)h[1] * R, 1};
+    d2.fixed_order = 1;
+    gemm_f64(d2, s);
+    // mode 2: B[a][b][c] = sum_k V2[k][b] T2[a][k][c], one product per (instance, a)
+    GemmDesc d3{R, R, h[1], q.cnt * R, Up1, (long long)h[1] * R, 1, R, T2, (long long)R * h[1] * R, R, 1,
+                Cp, (long long)R * R * R, R, 1};
+    d3.batch2 = R;
+    d3.sAb2 = 0;
+    d3.sBb2 = (long long)h[1] * R;
+    d3.sCb2 = (long long)R * R;
+    d3.fixed_order = 1;
+    gemm_f64(d3, s);
+  }
+  k_extract_core<<<dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), 256, 0, s>>>(cd);
+  TK_LAUNCH("k_extract_core");
+  if (pf) pf->end(s);
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (pf) pf->collect();
+
+  for (int b = 0; b < B; ++b) {
+    tk_result* res = new tk_result();
+    res->ctx = ctx;
+    res->precision = key.precision;
+    res->fold = 1;
+    res->mem = mem;
+    res->normF2 = hnorm[b];
+    for (int a = 0; a < 3; ++a) {
+      const int src = (nmodes == 1) ? 0 : a;
+      res->n[a] = n[a];
+      res->r[a] = fin[b].r[src];
+      res->flags[a] = fin[b].flags[src];
+      res->U[a] = rbase + offU[(size_t)b * 3 + src];
+      res->Uh[a] = rbase + offUh[(size_t)b * 3 + src];
+      const int j = slotJ[(size_t)src * B + b];
+      if (j >= 0) {
+        res->m[a] = m[src];
+        res->lam[a].assign(hlamB[src].begin() + (size_t)j * m[src], hlamB[src].begin() + (size_t)(j + 1) * m[src]);
+      } else {
+        res->m[a] = mA[src];
+        res->lam[a].assign(hlamA[src].begin() + (size_t)b * mA[src], hlamA[src].begin() + (size_t)(b + 1) * mA[src]);
+      }
+    }
+    res->core = rbase + offC[b];
+    outs[b] = res;
+  }
+}
+
+}  // namespace tk

@@ -12,6 +12,7 @@
 // non-cubic grid use the per-point kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "nu_consts.h"
@@ -211,6 +212,149 @@ void eval_tensor_f64(const tk_kernel& kh, const tk_grid& gh, double* F, double* 
 }
 
 size_t eval_rowsq_doubles(const tk_grid&) { return kEvalBlocks; }
+
+// ---------------------------------------------------------------------------
+// Folded tensor.  Every covariance here depends on the coordinates only
+// through x_a^2 / ell_a^2, and every grid is symmetric about 0 (x_{n-1-i} =
+// -x_i), so F is unchanged by reversing any axis.  Octant index i of axis a is
+// grid index c_a + i (c_a = floor(n_a / 2), 0 <= i < h_a = ceil(n_a / 2)) and
+// stands for w_i grid points: 1 for the centre of an odd axis, else 2.  The
+// weighted octant Fh(i, j, l) = sqrt(w_i w_j w_l) F(c_1 + i, c_2 + j, c_3 + l)
+// has the same |.|_F as F.  B instances share one grid.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fold_scale(int twos) {
+  // sqrt(2^twos) for twos = 0..3 (sqrt 2 correctly rounded)
+  const double r2 = 1.4142135623730951;
+  return (twos == 3) ? 2.0 * r2 : (twos == 2) ? 2.0 : (twos == 1) ? r2 : 1.0;
+}
+
+__global__ void k_table_b(const KernelDev* __restrict__ kd, double hstep, int even, long long Q, double* T) {
+  const int b = blockIdx.y;
+  const KernelDev& k = kd[b];
+  const double hs = hstep * k.inv_ell[0];
+  T += (size_t)b * Q;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
+    T[q] = cov_value(k, hs * hs * s);
+  }
+}
+
+// Octant of the cubic isotropic grid from the distinct-value table: octant
+// index i has a = 2 i + 1 (even n) or a = 2 i (odd n).
+__global__ void k_gather_oct(const double* __restrict__ T, long long Q, int n, int h, double* __restrict__ F,
+                             double* __restrict__ part) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const double* Tb = T + (size_t)b * Q;
+  double* Fb = F + (size_t)b * h * h * h;
+  const int even = (n % 2 == 0);
+  const long long rows = (long long)h * h;
+  double sq = 0.0;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = (int)(row / h), j = (int)(row % h);
+    const int ai = 2 * i + even, aj = 2 * j + even;
+    const int sij = ai * ai + aj * aj;
+    const int tij = even ? 3 : (i > 0) + (j > 0);
+    double* out = Fb + row * h;
+    for (int l = threadIdx.x; l < h; l += blockDim.x) {
+      const int al = 2 * l + even;
+      const int s = sij + al * al;
+      const double v = __ldg(Tb + (even ? (s - 3) >> 3 : s >> 2)) * fold_scale(even ? 3 : tij + (l > 0));
+      out[l] = v;
+      sq = fma(v, v, sq);
+    }
+  }
+  const double t = block_row_sum(sq, red);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_eval_oct(const KernelDev* __restrict__ kd, GridDev g, double* __restrict__ F,
+                           double* __restrict__ part) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const KernelDev& k = kd[b];
+  const int h1 = (g.ax[0].n + 1) / 2, h2 = (g.ax[1].n + 1) / 2, h3 = (g.ax[2].n + 1) / 2;
+  const int c1 = g.ax[0].n / 2, c2 = g.ax[1].n / 2, c3 = g.ax[2].n / 2;
+  const int o1 = g.ax[0].n & 1, o2 = g.ax[1].n & 1, o3 = g.ax[2].n & 1;
+  double* Fb = F + (size_t)b * h1 * h2 * h3;
+  const long long rows = (long long)h1 * h2;
+  double sq = 0.0;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = (int)(row / h2), j = (int)(row % h2);
+    const double u = (g.ax[0].x0 + (c1 + i) * g.ax[0].dx) * k.inv_ell[0];
+    const double v = (g.ax[1].x0 + (c2 + j) * g.ax[1].dx) * k.inv_ell[1];
+    const double uv = u * u + v * v;
+    const int tij = (!o1 || i > 0) + (!o2 || j > 0);
+    for (int l = threadIdx.x; l < h3; l += blockDim.x) {
+      const double w = (g.ax[2].x0 + (c3 + l) * g.ax[2].dx) * k.inv_ell[2];
+      const double val = cov_value(k, uv + w * w) * fold_scale(tij + (!o3 || l > 0));
+      Fb[row * h3 + l] = val;
+      sq = fma(val, val, sq);
+    }
+  }
+  const double t = block_row_sum(sq, red);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = t;
+}
+
+// |Fh|^2 of instance blockIdx.x from its nparts block partials: strided
+// Neumaier sums, then a fixed tree.
+__global__ void __launch_bounds__(256) k_parts_final(const double* __restrict__ part, int nparts,
+                                                     double* __restrict__ out) {
+  __shared__ double rs[256], rc[256];
+  const double* p = part + (size_t)blockIdx.x * nparts;
+  double s = 0.0, c = 0.0;
+  for (int r = threadIdx.x; r < nparts; r += blockDim.x) {
+    const double x = p[r], t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a = rs[threadIdx.x], ac = rc[threadIdx.x] + rc[threadIdx.x + w];
+      const double x = rs[threadIdx.x + w], t = a + x;
+      ac += (fabs(a) >= fabs(x)) ? (a - t) + x : (x - t) + a;
+      rs[threadIdx.x] = t;
+      rc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = rs[0] + rc[0];
+}
+
+// Blocks per instance: a function of the shape alone (about 8 rows each).
+static unsigned oct_blocks(const tk_grid& g) {
+  const long long rows = (long long)((g.n[0] + 1) / 2) * ((g.n[1] + 1) / 2);
+  return (unsigned)std::max<long long>(1, std::min<long long>(rows / 8, kEvalBlocks));
+}
+
+size_t eval_octant_parts(const tk_grid& g) { return oct_blocks(g); }
+long long table_entries(int n) { return table_size(n); }
+
+void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, double* Fh, double* table,
+                     double* part, double* normF2, cudaStream_t s) {
+  const unsigned nb = oct_blocks(g);
+  const int h3 = (g.n[2] + 1) / 2;
+  const int threads = h3 < 128 ? 64 : 128;
+  if (tab) {
+    const int n = g.n[0];
+    const long long Q = table_size(n);
+    const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
+    const long long tb = (Q + 63) / 64;
+    k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
+    TK_LAUNCH("k_table_b");
+    k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);
+    TK_LAUNCH("k_gather_oct");
+  } else {
+    k_eval_oct<<<dim3(nb, B), threads, 0, s>>>(kd, make_grid_dev(g), Fh, part);
+    TK_LAUNCH("k_eval_oct");
+  }
+  k_parts_final<<<B, 256, 0, s>>>(part, (int)nb, normF2);
+  TK_LAUNCH("k_parts_final");
+}
 
 // ---------------------------------------------------------------------------
 // |x|^2: each thread keeps a Neumaier pair over a fixed slice; blocks reduce

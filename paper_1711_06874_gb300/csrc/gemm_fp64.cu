@@ -58,11 +58,13 @@ __device__ __forceinline__ void load_unfold_tile(const double* __restrict__ F, c
 }
 
 // One (tile pair, K split) of the Gram; partial 64 x 64 block to P.
+// blockIdx.z: instance of a batch (tensor F + z sF, partials P + z nsplit npairs 64^2).
 __global__ void __launch_bounds__(NT) k_gram_f64(const double* __restrict__ F, Unfold u, int nrows,
                                                   long long K, long long kc, int ntiles,
-                                                  double* __restrict__ P) {
+                                                  double* __restrict__ P, long long sF) {
   __shared__ double As[KS][TB + 1];
   __shared__ double Bs[KS][TB + 1];
+  F += (long long)blockIdx.z * sF;
   // tile pair (ti <= tj) from the linear index
   int t = blockIdx.x, ti = 0;
   while (t >= ntiles - ti) {
@@ -95,20 +97,26 @@ __global__ void __launch_bounds__(NT) k_gram_f64(const double* __restrict__ F, U
     __syncthreads();
   }
   const int npairs = ntiles * (ntiles + 1) / 2;
-  double* out = P + ((long long)split * npairs + blockIdx.x) * TB * TB;
+  double* out = P + (((long long)blockIdx.z * gridDim.y + split) * npairs + blockIdx.x) * TB * TB;
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[(ty * 4 + p) * TB + tx * 4 + q] = acc[p][q];
 }
 
-// Sum the K splits in index order and write both triangles of G.
-__global__ void k_gram_reduce(const double* __restrict__ P, int nsplit, int ntiles, int n,
+// Sum the K splits in index order and write both triangles of G, for B
+// instances (G + b n^2).
+__global__ void k_gram_reduce(const double* __restrict__ P, int nsplit, int ntiles, int n, int B,
                               double* __restrict__ G) {
   const int npairs = ntiles * (ntiles + 1) / 2;
-  const long long total = (long long)npairs * TB * TB;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+  const long long per = (long long)npairs * TB * TB;
+  const long long total = per * B;
+  for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < total;
+       e0 += (long long)gridDim.x * blockDim.x) {
+    const long long b = e0 / per;
+    const long long e = e0 - b * per;
+    const double* Pb = P + b * nsplit * per;
+    double* Gb = G + b * n * n;
     const int pr = (int)(e / (TB * TB));
     const int rc = (int)(e % (TB * TB));
     int t = pr, ti = 0;
@@ -120,9 +128,9 @@ __global__ void k_gram_reduce(const double* __restrict__ P, int nsplit, int ntil
     const int gi = ti * TB + rc / TB, gj = tj * TB + rc % TB;
     if (gi >= n || gj >= n) continue;
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += P[((long long)sp * npairs + pr) * TB * TB + rc];
-    G[(long long)gi * n + gj] = s;
-    G[(long long)gj * n + gi] = s;
+    for (int sp = 0; sp < nsplit; ++sp) s += Pb[((long long)sp * npairs + pr) * TB * TB + rc];
+    Gb[(long long)gi * n + gj] = s;
+    Gb[(long long)gj * n + gi] = s;
   }
 }
 
@@ -147,22 +155,29 @@ GramPlan gram_plan(const int n[3], int mode) {
 
 }  // namespace
 
-size_t gram_f64_scratch_doubles(const int n[3], int mode) {
+size_t gram_f64_scratch_doubles(const int n[3], int mode, int B) {
   const GramPlan p = gram_plan(n, mode);
-  return (size_t)p.nsplit * p.npairs * TB * TB;
+  return (size_t)B * p.nsplit * p.npairs * TB * TB;
+}
+
+// The plan depends on the shape only, so each instance's Gram is the same
+// whatever the batch around it.
+void gram_f64_batch(const double* F, const int n[3], int mode, int B, double* G, double* scratch,
+                    cudaStream_t s) {
+  const GramPlan p = gram_plan(n, mode);
+  Unfold u{mode, n[0], n[1], n[2]};
+  dim3 grid(p.npairs, p.nsplit, B);
+  k_gram_f64<<<grid, NT, 0, s>>>(F, u, n[mode], p.K, p.kc, p.ntiles, scratch, (long long)n[0] * n[1] * n[2]);
+  TK_LAUNCH("k_gram_f64");
+  const long long total = (long long)p.npairs * TB * TB * B;
+  k_gram_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(
+      scratch, p.nsplit, p.ntiles, n[mode], B, G);
+  TK_LAUNCH("k_gram_reduce");
 }
 
 void gram_f64(const double* F, const int n[3], int mode, double* G, double* scratch,
               cudaStream_t s) {
-  const GramPlan p = gram_plan(n, mode);
-  Unfold u{mode, n[0], n[1], n[2]};
-  dim3 grid(p.npairs, p.nsplit);
-  k_gram_f64<<<grid, NT, 0, s>>>(F, u, n[mode], p.K, p.kc, p.ntiles, scratch);
-  TK_LAUNCH("k_gram_f64");
-  const long long total = (long long)p.npairs * TB * TB;
-  k_gram_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
-      scratch, p.nsplit, p.ntiles, n[mode], G);
-  TK_LAUNCH("k_gram_reduce");
+  gram_f64_batch(F, n, mode, 1, G, scratch, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,12 +241,12 @@ extern "C" int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, do
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Unfold u{mode, nn[0], nn[1], nn[2]};
-  k_gram_f64<<<dim3(p.npairs, p.nsplit), NT, 0, s>>>(F, u, nn[mode], p.K, p.kc, p.ntiles, scratch);
+  k_gram_f64<<<dim3(p.npairs, p.nsplit), NT, 0, s>>>(F, u, nn[mode], p.K, p.kc, p.ntiles, scratch, 0);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return TK_ECUDA;
   const long long total = (long long)p.npairs * TB * TB;
   k_gram_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
-      scratch, p.nsplit, p.ntiles, nn[mode], G);
+      scratch, p.nsplit, p.ntiles, nn[mode], 1, G);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return TK_ECUDA;
   return TK_OK;
@@ -303,14 +318,25 @@ struct ErrRef {
   }
 };
 
+// Operand offsets of batch entry z (outer index z / batch2, inner z % batch2;
+// A's outer index through amap when given); returns C's offset.
+__device__ __forceinline__ long long batch_offsets(const GemmDesc& d, long long z, const double*& A,
+                                                   const double*& B) {
+  const long long b1 = z / d.batch2, b2 = z - b1 * d.batch2;
+  const long long ia = d.amap ? (long long)d.amap[b1] : b1;
+  A = d.A + ia * d.sAb + b2 * d.sAb2;
+  B = d.B + b1 * d.sBb + b2 * d.sBb2;
+  return b1 * d.sCb + b2 * d.sCb2;
+}
+
 template <int BM, int BN, bool kErr>
 __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double* __restrict__ partials) {
   constexpr int RM = BM / 16, RN = BN / 16;
   __shared__ double As[KS][BM + 1];
   __shared__ double Bs[KS][BN + 1];
-  const int b = blockIdx.z;
-  const double* A = d.A + (long long)b * d.sAb;
-  const double* B = d.B + (long long)b * d.sBb;
+  const double* A;
+  const double* B;
+  const long long coff = batch_offsets(d, blockIdx.z, A, B);
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[RM][RN];
@@ -336,7 +362,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double*
     __syncthreads();
   }
   if (!kErr) {
-    double* C = d.C + (long long)b * d.sCb;
+    double* C = d.C + coff;
 #pragma unroll
     for (int p = 0; p < RM; ++p)
 #pragma unroll
@@ -345,7 +371,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double*
         if (i < d.M && j < d.N) C[(long long)i * d.sCi + (long long)j * d.sCj] = acc[p][q];
       }
   } else {
-    const double* Rb = ref.R ? ref.R + (long long)b * d.sCb : nullptr;
+    const double* Rb = ref.R ? ref.R + coff : nullptr;
     // plain FP64 sums over this thread's outputs; compensation starts at the tree
     double ds = 0.0, dc = 0.0, fs = 0.0, fc = 0.0;
 #pragma unroll
@@ -432,15 +458,18 @@ __global__ void k_gemm_warp(GemmDesc d) {
   const int lane = threadIdx.x & 31;
   for (long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; o < total;
        o += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const int b = (int)(o / per_batch);
-    const long long r = o - (long long)b * per_batch;
+    const long long b = o / per_batch;
+    const long long r = o - b * per_batch;
     const int i = (int)(r / d.N), j = (int)(r % d.N);
-    const double* A = d.A + (long long)b * d.sAb + (long long)i * d.sAi;
-    const double* B = d.B + (long long)b * d.sBb + (long long)j * d.sBj;
+    const double* A;
+    const double* B;
+    const long long coff = batch_offsets(d, b, A, B);
+    A += (long long)i * d.sAi;
+    B += (long long)j * d.sBj;
     double acc = 0.0;
     for (int k = lane; k < d.K; k += 32) acc = fma(A[(long long)k * d.sAk], B[(long long)k * d.sBk], acc);
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) d.C[(long long)b * d.sCb + (long long)i * d.sCi + (long long)j * d.sCj] = acc;
+    if (lane == 0) d.C[coff + (long long)i * d.sCi + (long long)j * d.sCj] = acc;
   }
 }
 
@@ -489,7 +518,7 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   const dim3 g = dispatch<false>(d, ErrRef{}, nullptr, s, false);
   const long long ctas = (long long)g.x * g.y * g.z;
   const long long outs = (long long)d.M * d.N * d.batch;
-  if (ctas < 76 && outs <= (1LL << 18)) {
+  if (!d.fixed_order && ctas < 76 && outs <= (1LL << 18)) {
     // few tiles: one warp per output keeps every SM busy
     const long long warps = outs;
     const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 4096);

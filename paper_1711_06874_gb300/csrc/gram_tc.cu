@@ -19,8 +19,10 @@
 //   w >= 6       -> dropped (2^-48 of the leading term).
 // Every 256-deep K chunk the epilogue warps move the five accumulators into a
 // 64-bit integer accumulator in units of 2^-44 (exact for w <= 3), so the
-// chunk sums carry no rounding; the split-K partials are FP64 and are summed
-// in index order with the row scales 2^(e_i + e_j) applied.
+// chunk sums carry no rounding; the split-K partials stay 64-bit integers and
+// are summed exactly (in two 32-bit halves), so each entry of G is the
+// correctly rounded value of the integer sum times 2^(e_i + e_j - 44), the
+// same for any split of K.
 //
 // Kernel layout (one CTA per 128 x 96 block of G touching its upper triangle,
 // and one K range):
@@ -84,8 +86,11 @@ __device__ __forceinline__ long long unfold_at(int mode, int n1, int n2, int n3,
   return c * n3 + row;
 }
 
+// blockIdx.z: instance (F + z sF, rowmax_bits + z n_mode).
 __global__ void k_rowmax(const double* __restrict__ F, int mode, int n1, int n2, int n3, long long K,
-                         unsigned long long* __restrict__ rowmax_bits) {
+                         unsigned long long* __restrict__ rowmax_bits, long long sF) {
+  F += (long long)blockIdx.z * sF;
+  rowmax_bits += (size_t)blockIdx.z * (mode == 0 ? n1 : mode == 1 ? n2 : n3);
   // grid: (row blocks of 32 rows for mode 2 / one row for modes 0,1, K chunks)
   if (mode == 2) {
     const int row = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -145,9 +150,13 @@ __device__ __forceinline__ __nv_bfloat16 slice_value(int d, int s) {
 // Slices of one unfolding, written K-major: S[s][row][c], row stride Kp (a
 // multiple of 32, zero padded).  32 x 32 tiles through shared memory so that
 // both the read of F and the write of S are coalesced for every mode.
+// blockIdx.z: instance (F + z sF, rowexp + z nrows, S + z 6 nrows Kp).
 __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, int n3, int nrows, long long K,
-                        long long Kp, const int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S) {
+                        long long Kp, const int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S, long long sF) {
   __shared__ double tile[32][33];
+  F += (long long)blockIdx.z * sF;
+  rowexp += (size_t)blockIdx.z * nrows;
+  S += (size_t)blockIdx.z * kSlices * nrows * Kp;
   const int r0 = blockIdx.y * 32;
   const long long c0 = (long long)blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
@@ -183,53 +192,6 @@ __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, 
   }
 }
 
-// The same slices for B cubic isotropic tensors given by their distinct-value
-// tables (F_b(i, j, k) = T_b[q(a_i^2 + a_j^2 + a_k^2)], a = 2 idx - (n - 1)),
-// mode-1 unfolding: row i, column c = j n + k.  F is never written.
-__device__ __forceinline__ double table_value(const double* Tb, int n, int even, int i, int j, int k) {
-  const int ai = 2 * i - (n - 1), aj = 2 * j - (n - 1), ak = 2 * k - (n - 1);
-  const int sq = ai * ai + aj * aj + ak * ak;
-  return __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2));
-}
-
-__global__ void k_rowexp_table(const double* __restrict__ T, long long tq, int n, int even, int* __restrict__ rowexp) {
-  __shared__ double red[32];
-  const int i = blockIdx.x, b = blockIdx.y;
-  const double* Tb = T + (size_t)b * tq;
-  double m = 0.0;
-  for (int c = threadIdx.x; c < n * n; c += blockDim.x) m = fmax(m, fabs(table_value(Tb, n, even, i, c / n, c % n)));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
-    int e = -1000;
-    if (v > 0.0) frexp(v, &e);
-    rowexp[(size_t)b * n + i] = e;
-  }
-}
-
-__global__ void k_slice_table(const double* __restrict__ T, long long tq, int n, int even, long long Kp, int B,
-                              const int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S) {
-  const long long K = (long long)n * n;
-  const long long per = (long long)n * Kp;
-  const long long total = per * B;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const long long r = e - (long long)b * per;
-    const int row = (int)(r / Kp);
-    const long long c = r - (long long)row * Kp;
-    int d[kSlices] = {0, 0, 0, 0, 0, 0};
-    if (c < K) slice_digits(table_value(T + (size_t)b * tq, n, even, row, (int)(c / n), (int)(c % n)),
-                            rowexp[(size_t)b * n + row], d);
-    __nv_bfloat16* Sb = S + (size_t)b * kSlices * per + r;
-#pragma unroll
-    for (int s = 0; s < kSlices; ++s) Sb[(size_t)s * per] = slice_value(d[s], s);
-  }
-}
-
 struct TcArgs {
   int nrows;
   int nrt, nct;           // row tiles (of 128) and column tiles (of 96)
@@ -237,7 +199,7 @@ struct TcArgs {
   int nsplit;             // K splits per instance
   int kblocks_per_split;  // k-blocks (of 32) per CTA
   int kblocks_total;
-  double* partials;       // [instance][split][block][128][96]
+  long long* partials;    // [instance][split][block][128][96], units of 2^-44
   int* err;
 };
 
@@ -421,10 +383,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) tc::mbar_arrive(acc_empty);
     }
     if (ok) {
-      double* out = args.partials + (((size_t)inst * args.nsplit + blockIdx.y) * args.nblocks + blockIdx.x) * kTM * kTN +
-                    (size_t)row * kTN + grp * kEpiCols;
+      long long* out = args.partials +
+                       (((size_t)inst * args.nsplit + blockIdx.y) * args.nblocks + blockIdx.x) * kTM * kTN +
+                       (size_t)row * kTN + grp * kEpiCols;
 #pragma unroll
-      for (int j = 0; j < kEpiCols; ++j) out[j] = (double)V[j] * 5.684341886080802e-14;  // 2^-44
+      for (int j = 0; j < kEpiCols; ++j) out[j] = V[j];
     }
   }
   tc::fence_before_sync();
@@ -433,9 +396,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-// G_b[gi][gj] = G_b[gj][gi] = 2^(e_gi + e_gj) sum_split P[b][split][block(gi, gj)][..],
-// gi <= gj, for every instance b (row exponents rowexp[b * n + i]).
-__global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
+// G_b[gi][gj] = G_b[gj][gi] = 2^(e_gi + e_gj - 44) sum_split P[b][split][block(gi, gj)][..],
+// gi <= gj, for every instance b (row exponents rowexp[b * n + i]).  The
+// integer partials (each below 2^62) are summed exactly as high and low
+// 32-bit halves and rounded to FP64 once.
+__global__ void k_tc_reduce(const long long* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
                             const int* __restrict__ rowexp, double* __restrict__ G) {
   const long long per = (long long)n * n;
   const long long total = per * B;
@@ -448,10 +413,17 @@ __global__ void k_tc_reduce(const double* __restrict__ P, int nsplit, int nct, i
     const int bi = gi / kTM, bj = gj / kTN;
     const int blk = block_index(bi, bj, nct);
     const size_t off = (size_t)(gi - bi * kTM) * kTN + (gj - bj * kTN);
-    double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += P[(((size_t)b * nsplit + sp) * nblocks + blk) * kTM * kTN + off];
+    long long hi = 0, lo = 0;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const long long v = P[(((size_t)b * nsplit + sp) * nblocks + blk) * kTM * kTN + off];
+      hi += v >> 32;          // floor(v / 2^32)
+      lo += v & 0xFFFFFFFFLL;  // v - 2^32 floor(v / 2^32), in [0, 2^32)
+    }
+    hi += lo >> 32;
+    lo &= 0xFFFFFFFFLL;
+    const double sum = fma((double)hi, 4294967296.0, (double)lo);  // one rounding
     const int ei = rowexp[(size_t)b * n + gi], ej = rowexp[(size_t)b * n + gj];
-    const double v = (ei > -1000 && ej > -1000) ? ldexp(s, ei + ej) : 0.0;
+    const double v = (ei > -1000 && ej > -1000) ? ldexp(sum, ei + ej - 44) : 0.0;
     double* Gb = G + (size_t)b * per;
     Gb[(long long)gi * n + gj] = v;
     Gb[(long long)gj * n + gi] = v;
@@ -517,7 +489,7 @@ CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long 
 
 // The tensor-core Gram and its reduction over B instances whose slices are
 // at S ([b][s][row][Kp]) and row exponents at rowexp ([b][row]).
-void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, double* P, double* G, int* err,
+void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, long long* P, double* G, int* err,
                  cudaStream_t s) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
@@ -538,83 +510,56 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, do
 
 }  // namespace
 
-size_t gram_sliced_scratch_bytes(const int n[3], int mode) {
-  const TcPlan p = tc_plan(n, mode, 152);
+size_t gram_sliced_scratch_bytes(const int n[3], int mode, int B) {
+  const TcPlan p = tc_plan(n, mode, 152, B);
   size_t b = 0;
-  b += carve_bytes<unsigned long long>(p.nrows);                          // row max bits
-  b += carve_bytes<int>(p.nrows);                                         // row exponents
-  b += carve_bytes<__nv_bfloat16>((size_t)kSlices * p.nrows * p.Kp);      // slices
-  b += carve_bytes<double>((size_t)p.nsplit * p.nblocks * kTM * kTN);     // partials
+  b += carve_bytes<unsigned long long>((size_t)B * p.nrows);                   // row max bits
+  b += carve_bytes<int>((size_t)B * p.nrows);                                  // row exponents
+  b += carve_bytes<__nv_bfloat16>((size_t)B * kSlices * p.nrows * p.Kp);       // slices
+  b += carve_bytes<long long>((size_t)B * p.nsplit * p.nblocks * kTM * kTN);  // partials
   return b + 4096;
+}
+
+void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
+                       cudaStream_t s) {
+  // one plan (for 152 SMs and this batch) fixes both the scratch layout and
+  // the grid; G does not depend on it (exact integer sums over K)
+  const TcPlan p = tc_plan(n, mode, 152, B);
+  const long long sF = (long long)n[0] * n[1] * n[2];
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    char* q = base + off;
+    off += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  unsigned long long* rowmax = (unsigned long long*)carve(sizeof(unsigned long long) * B * p.nrows);
+  int* rowexp = (int*)carve(sizeof(int) * (size_t)B * p.nrows);
+  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * p.nrows * p.Kp);
+  long long* P = (long long*)carve(sizeof(long long) * (size_t)B * p.nsplit * p.nblocks * kTM * kTN);
+
+  TK_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * B * p.nrows, s));
+  if (mode == 2) {
+    dim3 g((p.nrows + 31) / 32, (unsigned)std::min<long long>(1024, (p.K + 7) / 8), B);
+    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax, sF);
+  } else {
+    dim3 g(p.nrows, (unsigned)std::min<long long>(64, (p.K + 255) / 256), B);
+    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax, sF);
+  }
+  TK_LAUNCH("k_rowmax");
+  k_rowexp<<<(B * p.nrows + 255) / 256, 256, 0, s>>>(rowmax, B * p.nrows, rowexp);
+  TK_LAUNCH("k_rowexp");
+  {
+    dim3 g((unsigned)(p.Kp / 32), (p.nrows + 31) / 32, B);
+    k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S, sF);
+    TK_LAUNCH("k_slice");
+  }
+  run_tc_gram(p, B, S, rowexp, P, G, err, s);
 }
 
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s) {
-  // one plan (for 152 SMs) fixes both the scratch layout and the grid
-  const TcPlan p = tc_plan(n, mode, 152);
-  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
-  size_t off = 0;
-  auto carve = [&](size_t bytes) {
-    char* q = base + off;
-    off += (bytes + 255) & ~size_t(255);
-    return q;
-  };
-  unsigned long long* rowmax = (unsigned long long*)carve(sizeof(unsigned long long) * p.nrows);
-  int* rowexp = (int*)carve(sizeof(int) * p.nrows);
-  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)kSlices * p.nrows * p.Kp);
-  double* P = (double*)carve(sizeof(double) * (size_t)p.nsplit * p.nblocks * kTM * kTN);
-
-  TK_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * p.nrows, s));
-  if (mode == 2) {
-    dim3 g((p.nrows + 31) / 32, (unsigned)std::min<long long>(1024, (p.K + 7) / 8));
-    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax);
-  } else {
-    dim3 g(p.nrows, (unsigned)std::min<long long>(64, (p.K + 255) / 256));
-    k_rowmax<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.K, rowmax);
-  }
-  TK_LAUNCH("k_rowmax");
-  k_rowexp<<<(p.nrows + 255) / 256, 256, 0, s>>>(rowmax, p.nrows, rowexp);
-  TK_LAUNCH("k_rowexp");
-  {
-    dim3 g((unsigned)(p.Kp / 32), (p.nrows + 31) / 32);
-    k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S);
-    TK_LAUNCH("k_slice");
-  }
-  run_tc_gram(p, 1, S, rowexp, P, G, err, s);
-}
-
-size_t gram_sliced_table_scratch_bytes(int n, int B) {
-  const int nn[3] = {n, n, n};
-  const TcPlan p = tc_plan(nn, 0, 152, B);
-  size_t b = 0;
-  b += carve_bytes<int>((size_t)B * n);                                          // row exponents
-  b += carve_bytes<__nv_bfloat16>((size_t)B * kSlices * n * p.Kp);                // slices
-  b += carve_bytes<double>((size_t)B * p.nsplit * p.nblocks * kTM * kTN);       // partials
-  return b + 4096;
-}
-
-void gram_sliced_table(const double* T, long long tq, int n, int B, double* G, void* scratch, int* err,
-                       cudaStream_t s) {
-  const int nn[3] = {n, n, n};
-  const TcPlan p = tc_plan(nn, 0, 152, B);
-  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
-  size_t off = 0;
-  auto carve = [&](size_t bytes) {
-    char* q = base + off;
-    off += (bytes + 255) & ~size_t(255);
-    return q;
-  };
-  int* rowexp = (int*)carve(sizeof(int) * (size_t)B * n);
-  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * n * p.Kp);
-  double* P = (double*)carve(sizeof(double) * (size_t)B * p.nsplit * p.nblocks * kTM * kTN);
-  const int even = (n % 2 == 0);
-  k_rowexp_table<<<dim3(n, B), 256, 0, s>>>(T, tq, n, even, rowexp);
-  TK_LAUNCH("k_rowexp_table");
-  const long long total = (long long)B * n * p.Kp;
-  k_slice_table<<<(unsigned)std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, s>>>(T, tq, n, even, p.Kp,
-                                                                                              B, rowexp, S);
-  TK_LAUNCH("k_slice_table");
-  run_tc_gram(p, B, S, rowexp, P, G, err, s);
+  gram_sliced_batch(F, n, mode, 1, G, scratch, err, s);
 }
 
 }  // namespace tk

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -42,6 +43,14 @@ struct Workspace {
     return reinterpret_cast<T*>(base + off);
   }
   void release();
+};
+
+// Device memory shared by the results of one batched solve; freed with the
+// last of them.
+struct DeviceBlock {
+  int device = 0;
+  void* ptr = nullptr;
+  ~DeviceBlock();
 };
 
 // Bytes of a carve of `count` T after 256-byte alignment (for sizing).
@@ -84,28 +93,46 @@ size_t eval_scratch_doubles(const tk_kernel& k, const tk_grid& g);
 // Only the distinct-value table (when table_applicable); returns false otherwise.
 bool eval_table_f64(const tk_kernel& k, const tk_grid& g, double* table, cudaStream_t s);
 
+// Weighted octant of the folded tensor for B instances sharing grid g
+// (Fh + b h1 h2 h3, h_a = ceil(n_a / 2)): Fh(i, j, l) = sqrt(w_i w_j w_l)
+// F(c_1 + i, c_2 + j, c_3 + l), c_a = floor(n_a / 2), w = 1 at the centre of an
+// odd axis and 2 elsewhere.  kd: device array of B kernels.  tab: every kernel
+// is isotropic and the grid cubic, so the distinct-value table (B x
+// table_entries(n) doubles at `table`) is used.  part: B x eval_octant_parts(g)
+// doubles; normF2[b] receives |Fh_b|^2 = |F_b|^2.
+size_t eval_octant_parts(const tk_grid& g);
+long long table_entries(int n);
+void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, double* Fh, double* table,
+                     double* part, double* normF2, cudaStream_t s);
+
 // |F|^2 with compensated per-thread sums and a fixed-order final sum.
 size_t norm2_scratch_doubles(size_t len);
 void norm2_f64(const double* x, size_t len, double* out_dev, double* scratch, cudaStream_t s);
 
-// (b) Gram in FP64 on the CUDA cores (split-K partials in scratch).
-size_t gram_f64_scratch_doubles(const int n[3], int mode);
+// (b) Gram in FP64 on the CUDA cores (split-K partials in scratch).  The batch
+// form takes B tensors F + b n1 n2 n3 and writes G + b n_mode^2.
+size_t gram_f64_scratch_doubles(const int n[3], int mode, int B = 1);
 void gram_f64(const double* F, const int n[3], int mode, double* G, double* scratch, cudaStream_t s);
+void gram_f64_batch(const double* F, const int n[3], int mode, int B, double* G, double* scratch,
+                    cudaStream_t s);
 
 // (b) Gram from exact BF16 slices on the tcgen05 tensor cores.  `err` (device
-// int) is raised if a bounded wait inside the kernel ran out.
-size_t gram_sliced_scratch_bytes(const int n[3], int mode);
+// int) is raised if a bounded wait inside the kernel ran out.  The batch form
+// takes B tensors F + b n1 n2 n3 and writes G + b n_mode^2; each G is the same
+// whatever the batch.
+size_t gram_sliced_scratch_bytes(const int n[3], int mode, int B = 1);
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s);
-// Gram (mode 1) of B cubic isotropic tensors given by their distinct-value
-// tables (T + b * tq, n points per axis), without writing F; G: [b][n][n].
-size_t gram_sliced_table_scratch_bytes(int n, int B);
-void gram_sliced_table(const double* T, long long tq, int n, int B, double* G, void* scratch, int* err,
+void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
                        cudaStream_t s);
 // unit roundoff of the Gram of each precision (for the eps-unreachable flag)
 inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 : 0x1p-48; }
 
-// General strided batched FP64 GEMM: C[b](i,j) = sum_k A[b](i,k) B[b](k,j)
+// General strided batched FP64 GEMM: C[z](i,j) = sum_k A[z](i,k) B[z](k,j).
+// Batch entry z = b1 batch2 + b2 has operand offsets b1 s_b + b2 s_b2 (A's b1
+// replaced by amap[b1] when amap is given).  Every output is one FMA chain in
+// k order; fixed_order = 1 also rules out the warp-per-output kernel, so that
+// each entry's result does not depend on the batch it is part of.
 struct GemmDesc {
   int M, N, K, batch;
   const double* A;
@@ -114,6 +141,10 @@ struct GemmDesc {
   long long sBb, sBk, sBj;
   double* C;
   long long sCb, sCi, sCj;
+  int batch2 = 1;
+  long long sAb2 = 0, sBb2 = 0, sCb2 = 0;
+  const int* amap = nullptr;
+  int fixed_order = 0;
 };
 void gemm_f64(const GemmDesc& d, cudaStream_t s);
 // Same product, but instead of storing C accumulates sum (R - C)^2 and sum R^2
@@ -136,18 +167,53 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
 // Same scratch size.
 void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* safe,
                          double* scratch, cudaStream_t s);
-// B instances with the same n and m: G [b][n][n] -> lam [b][m], V [b][n][m],
-// trace [b], safe [b * 4] (certain leading pairs per instance).
-size_t sym_eig_persym_batch_scratch_doubles(int n, int m, int B);
-void sym_eig_persym_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, int* safe,
-                          double* scratch, cudaStream_t s);
-// rank rule for B instances: out [b * 4 + 0..2] as rank_rule, eps [b], rmax [b]
+// B instances with the same n and m: G [b][n][n] -> lam [b][m], V [b][n][m]
+// (canonical signs), trace [b].  Each instance's result is the same whatever
+// the batch.
+size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
+void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
+                   cudaStream_t s);
+// rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
+// rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
+// of the precision flag.
 void rank_rule_batch(const double* lam, int m, const double* trace, const double* normF2, const double* eps,
-                     const int* rmax, int rfix, double u_eff, int n, int B, int* out, cudaStream_t s);
+                     const int* rmax, const int* rfix, double u_eff, int n_eig, int n_flag, int B, int* out,
+                     cudaStream_t s);
 // rank rule on device; writes for one mode rank_out[0] = rank, [1] = flags,
 // [2] = rank before the cap (m + 1 when more than the m computed pairs are needed).
 void rank_rule(const double* lam, int m, const double* trace, const double* normF2, double eps,
                int rmax, int rfix, double u_eff, int n, int* rank_out, cudaStream_t s);
+
+// ---- batched engine (engine.cu) ----
+struct Profiler;
+struct SolveReq {
+  tk_kernel k;
+  tk_grid g;
+  tk_opts o;
+};
+// The three Grams are equal by symmetry (cubic grid, isotropic kernel, equal
+// caps) and the options allow solving one of them.
+bool shortcut_ok(const tk_kernel& k, const tk_grid& g, const tk_opts& o);
+// The solve may run on the weighted octant (reflection symmetry).
+bool fold_applicable(const tk_grid& g, const tk_opts& o);
+// Requests with equal keys are solved together; every field fixes a launch
+// shape or a summation order, so a request's result does not depend on the
+// others in its batch.
+struct BucketKey {
+  int n[3];
+  double b[3];
+  int kind, precision, nmodes, tab, m[3];
+  bool operator<(const BucketKey& o) const;
+  bool operator==(const BucketKey& o) const;
+};
+BucketKey bucket_key(const SolveReq& r);
+// Upper bound of the device bytes one request adds to a batch (workspaces
+// and results), for admission.
+size_t bucket_bytes_per_instance(const BucketKey& key);
+// Solves B requests of one bucket (fold_applicable for all), enqueued on s;
+// synchronises s twice (ranks, then results).  outs[b] receives new results.
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, const SolveReq* req, int B,
+                  tk_result** outs, cudaStream_t s);
 
 }  // namespace tk
 
@@ -176,10 +242,12 @@ struct Profiler {
 struct tk_ctx {
   int device = 0;
   std::mutex mu;
-  tk::Workspace ws;
+  tk::Workspace ws;   // stages before the rank decision
+  tk::Workspace ws2;  // stages after it (sized from the ranks)
   std::string last_error;
   int sm_count = 0;
   tk::Profiler prof;
+  struct tk_server* server = nullptr;
 };
 
 struct tk_result {
@@ -188,9 +256,12 @@ struct tk_result {
   int r[3] = {0, 0, 0};
   int m[3] = {0, 0, 0};
   uint32_t flags[3] = {0, 0, 0};
-  double* U[3] = {nullptr, nullptr, nullptr};  // device, n_k x r_k
-  double* core = nullptr;                      // device, r1 r2 r3
-  std::vector<double> lam[3];                  // host, m_k leading eigenvalues
+  double* U[3] = {nullptr, nullptr, nullptr};   // device, n_k x r_k
+  double* Uh[3] = {nullptr, nullptr, nullptr};  // folded solves: device, ceil(n_k/2) x r_k octant factors
+  double* core = nullptr;                       // device, r1 r2 r3
+  std::vector<double> lam[3];                   // host, m_k leading eigenvalues
   double normF2 = 0.0;
   int precision = 0;
+  int fold = 0;
+  std::shared_ptr<tk::DeviceBlock> mem;  // when set, owns U, Uh and core (shared by a batch)
 };

@@ -1,0 +1,191 @@
+"""Batched solves (tk_batch) and the folded solve, through the C-ABI.
+
+  * fold vs whole tensor: the weighted-octant solve gives the ranks,
+    eigenvalues (to 1e-13 lam_1), factors (principal angles) and core norm of
+    the unfolded one;
+  * a batch against each instance alone: bitwise equal ranks, flags,
+    eigenvalues, |F|^2, factors and cores, for a mix of shapes, grids,
+    tolerances and both precisions (rank groups, escalation to all pairs);
+  * a batch against the oracle, small instances element by element;
+  * the 256-instance n = 128 parameter sweep at full size: sampled instances
+    against the oracle, every instance for orthonormal factors, the HOSVD
+    bound and its rel_error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests._util import U64, near_threshold, principal_sines, separated_prefix
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+U_SLICED = 2.0 ** -48
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_06874_gb300 import binding
+
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def wl():
+    from paper_1711_06874_gb300 import workloads
+
+    return workloads
+
+
+def _same(a, b):
+    return a.shape == b.shape and np.array_equal(a, b)
+
+
+FOLD_CASES = [
+    dict(nu=1.2, ell=0.2, n=48, eps=1e-6, rmax=20),
+    dict(nu=0.7, ell=(0.25, 0.3, 0.4), n=(40, 33, 27), eps=1e-6, rmax=24),
+    dict(nu=2.5, ell=0.15, n=35, eps=1e-5, rmax=16, grid=1),
+    dict(nu=0.4, ell=0.08, n=(30, 31, 32), eps=1e-4, rmax=30, grid=1),
+]
+
+
+@pytest.mark.parametrize("case", FOLD_CASES)
+def test_fold_matches_whole_tensor(ctx, wl, case):
+    from paper_1711_06874_gb300 import binding
+
+    prob = wl.problem(0, **case)
+    for precision, u in ((binding.TK_FP64, U64), (binding.TK_SLICED_BF16, U_SLICED)):
+        rf = ctx.tucker(prob, precision=precision, fold=True)
+        rw = ctx.tucker(prob, precision=precision, fold=False)
+        assert rf.ranks == rw.ranks
+        r = rf.ranks[0]
+        assert abs(rf.norm2 - rw.norm2) <= 1e-14 * rw.norm2
+        for a in range(3):
+            lf, lw = rf.eigenvalues(a), rw.eigenvalues(a)
+            k = min(len(lf), len(lw), r[a] + 1)
+            # two FP64 sums of about n^2 terms each (the octant's are scaled by sqrt 2)
+            np.testing.assert_allclose(lf[:k], lw[:k], rtol=0, atol=1e-12 * lw[0])
+            Uf, Uw = rf.factor(a), rw.factor(a)
+            np.testing.assert_allclose(Uf.T @ Uf, np.eye(r[a]), atol=1e-13)
+            rp = min(separated_prefix(lw[: r[a] + 1]), r[a])
+            if rp:
+                gap = min((lw[i] - lw[i + 1]) / lw[0] for i in range(rp))
+                tol = max(1e-10, 10 * u / gap) if u > U64 else 1e-10
+                assert principal_sines(Uw[:, :rp], Uf[:, :rp]).max() <= tol
+                # canonical signs agree on separated columns
+                for j in range(rp):
+                    assert np.dot(Uf[:, j], Uw[:, j]) > 0
+        nB = np.linalg.norm(rw.core())
+        assert abs(np.linalg.norm(rf.core()) - nB) <= 1e-12 * math.sqrt(rw.norm2)
+        # factors from two roundings of G differ at first order only inside the
+        # kept and the discarded subspaces; the error moves at second order
+        assert abs(rf.rel_error() - rw.rel_error()) <= 1e-4 * rw.rel_error() + 1e-14
+
+
+def _mix(wl):
+    P = wl.problem
+    return [
+        P(0, nu=1.2, ell=0.2, n=40, eps=1e-6, rmax=20),
+        P(0, nu=1.2, ell=0.2, n=40, eps=1e-10, rmax=20),      # eps below the Gram's precision
+        P(0, nu=2.1, ell=0.9, n=40, eps=1e-6, rmax=20),       # low rank
+        P(0, nu=1.2, ell=0.2, n=40, eps=1e-4, rmax=20),
+        P(0, nu=0.8, ell=0.3, n=33, eps=1e-6, rmax=20, grid=1),
+        P(0, nu=0.8, ell=(0.3, 0.4, 0.5), n=(20, 24, 28), eps=1e-6, rmax=12),
+        P(0, nu=1.2, ell=0.2, n=40, eps=1e-6, rmax=20),       # duplicate of the first
+        P(0, nu=0.3, ell=0.5, n=64, eps=1e-8, rmax=24),
+        P(0, nu=1.0, ell=0.3, n=40, eps=1e-6, rmax=20),       # fixed rank 18 (below)
+        P(0, nu=0.6, ell=0.15, n=40, eps=1e-8, rmax=20),
+    ]
+
+
+@pytest.mark.parametrize("precision_name", ["TK_FP64", "TK_SLICED_BF16"])
+def test_batch_equals_alone_bitwise(ctx, wl, precision_name):
+    from paper_1711_06874_gb300 import binding
+
+    precision = getattr(binding, precision_name)
+    probs = _mix(wl)
+    rfixes = [(18, 18, 18) if i == 8 else (0, 0, 0) for i in range(len(probs))]
+    mixed = ctx.batch(probs, precision=precision, rfixes=rfixes)
+    for p, rf, rm in zip(probs, rfixes, mixed):
+        (ra,) = ctx.batch([p], precision=precision, rfixes=[rf])
+        rt = ctx.tucker(p, precision=precision, rfix=rf)
+        for alone in (ra, rt):
+            assert rm.ranks == alone.ranks
+            assert rm.norm2 == alone.norm2
+            assert _same(rm.core(), alone.core())
+            for a in range(3):
+                assert _same(rm.factor(a), alone.factor(a)), a
+                assert _same(rm.eigenvalues(a), alone.eigenvalues(a)), a
+    # the duplicate instance is bitwise the first
+    assert _same(mixed[0].core(), mixed[6].core())
+    assert mixed[8].ranks[0] == [18, 18, 18]  # fixed rank above the first pass: all pairs
+
+
+def test_batch_matches_oracle(ctx, orc, wl):
+    from paper_1711_06874_gb300 import binding
+
+    probs = [wl.problem(0, nu=nu, ell=ell, n=36, eps=1e-6, rmax=24)
+             for nu, ell in ((0.5, 0.3), (1.2, 0.2), (2.5, 0.5), (0.9, 0.1))]
+    res = ctx.batch(probs, precision=binding.TK_FP64)
+    for p, r in zip(probs, res):
+        ref = orc.hosvd(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc), p.eps, rmax=list(p.rmax))
+        ranks, _ = r.ranks
+        assert ranks == ref["ranks"] or any(near_threshold(ref["lam"][a], ref["normF2"], p.eps, ref["ranks"][a])
+                                            for a in range(3))
+        if ranks != ref["ranks"]:
+            continue
+        nF = math.sqrt(ref["normF2"])
+        assert abs(r.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
+        B = r.core()
+        assert abs(np.linalg.norm(B) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
+        U = [r.factor(a) for a in range(3)]
+        X = orc.reconstruct(B, U, p.n)
+        Xo = orc.reconstruct(ref["core"], ref["U"], p.n)
+        # subspaces from two roundings of G: first order in u / eps
+        assert np.linalg.norm(X - Xo) <= max(1e-12, 100 * U64 / p.eps) * nF
+        e_or = orc.rel_error(orc.tensor(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc)), X)
+        assert abs(r.rel_error() - e_or) <= 1e-10 * e_or + 1e-15
+
+
+def test_batch_empty_and_invalid(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    assert ctx.batch([]) == []
+    with pytest.raises(binding.TuckerError) as ei:
+        ctx.batch([wl.problem(0, nu=1.0, n=16), wl.problem(0, nu=-1.0, n=16)])
+    assert ei.value.status == binding.TK_EINVAL
+
+
+def test_sweep_256_n128_full_size(ctx, orc, wl):
+    """The 256-instance n = 128 sweep in one tk_batch call, mixed precision."""
+    from paper_1711_06874_gb300 import binding
+
+    probs = wl.sweep()
+    res = ctx.batch(probs, precision=binding.TK_SLICED_BF16)
+    assert len(res) == 256
+    for p, r in zip(probs, res):
+        ranks, flags = r.ranks
+        lam = r.eigenvalues(0)
+        U = r.factor(0)
+        np.testing.assert_allclose(U.T @ U, np.eye(ranks[0]), atol=1e-12)
+        # HOSVD: |B|^2 = |F|^2 - discarded, and the error below the bound
+        e = r.rel_error()
+        if not (flags[0] & binding.TK_RANK_CAPPED):
+            assert e <= p.eps * (1 + 1e-6) or flags[0] & 2, (p, e)
+    for i in (0, 97, 255):  # sampled instances against the oracle
+        p, r = probs[i], res[i]
+        ref = orc.hosvd(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc), p.eps, rmax=list(p.rmax))
+        ranks, _ = r.ranks
+        assert ranks == ref["ranks"] or near_threshold(ref["lam"][0], ref["normF2"], p.eps, ref["ranks"][0])
+        assert abs(r.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
+        k = min(len(r.eigenvalues(0)), ranks[0] + 1)
+        np.testing.assert_allclose(r.eigenvalues(0)[:k], ref["lam"][0][:k], rtol=0, atol=1e-13 * ref["lam"][0][0])
+        if ranks == ref["ranks"]:
+            nF = math.sqrt(ref["normF2"])
+            assert abs(np.linalg.norm(r.core()) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
