@@ -1,15 +1,19 @@
 #!/usr/bin/env python3
 """Throughput of the Tucker/HOSVD of a Matern covariance tensor on GB300.
 
-Workload (one step = one whole solve through the C-ABI): Matern nu = 1.2,
-ell = 0.2, sigma2 = 1 on the 256^3 cell-centred grid in [-1, 1]^3, eps = 1e-6:
-sample F, |F|^2, Gram of the unfoldings, leading eigenpairs and ranks, core
-by chained TTMs, then the relative Frobenius error by direct subtraction.
+Default workload (one step = one whole solve through the C-ABI): Matern
+nu = 1.2, ell = 0.2, sigma2 = 1 on the 256^3 cell-centred grid in [-1, 1]^3,
+eps = 1e-6: sample F, Gram of the unfoldings, leading eigenpairs and ranks,
+core by chained TTMs, then the relative Frobenius error by direct
+subtraction.  --workload sweep: one step = the 256-instance n = 128 parameter
+sweep in one tk_batch call.  --workload serving: the 2000-request Poisson
+stream replayed in real time through the serving loop.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload single|sweep|serving]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs independent
-replicas of the solve (the path has no exchange step) and rank 0 prints.
+replicas of the workload (the path has no exchange step) and rank 0 prints.
 """
 from __future__ import annotations
 
@@ -29,6 +33,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Matérn Tucker-HOSVD solves/s at rel err 1e-6 vs FP64 path; p50/p99 latency"
 WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, eps=1e-6, "
             "rank cap 64; one solve (sample, Gram, eigenpairs, ranks, core, rel_error) per step")
+SWEEP = ("256 Matern instances, n=128^3 cell-centred grid on [-1,1]^3, nu~U[0.3,2.5], ell~logU[0.05,1], "
+         "sigma2=1, eps=1e-6, rank cap 64, seeded PCG64(1711); one tk_batch call per step")
+SERVING = ("2000 requests, Poisson arrivals 200/s, n uniform over {64,128,256,384}, nu~U[0.3,2.5], "
+           "ell~logU[0.05,1], eps over {1e-4,1e-6,1e-8}, rank cap 64, seeded PCG64(6874); "
+           "replayed in real time through the serving loop")
+FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 at 2070 MHz (nominal; the pipe the eigensolver and TTMs run on)
 
 
 def parse():
@@ -39,6 +49,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "sliced"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="single", choices=["single", "sweep", "serving"])
     return p.parse_args()
 
 
@@ -165,6 +176,58 @@ def run_reference(args):
     return 0
 
 
+def _flush_l2(torch, buf, stream):
+    with torch.cuda.stream(stream):
+        buf.add_(1.0)
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def _roofline(prof, steps, prob, ranks, precision, clocks, peaks, peak_src):
+    """Roofline of the stage with the largest share of the step (stage events
+    recorded by the library on the solve's stream)."""
+    from paper_1711_06874_gb300 import binding
+
+    n = prob.n[0]
+    h = (n + 1) // 2
+    r = max(ranks)
+    R = (r + 3) // 4 * 4
+    m = 16  # first-pass eigenpairs
+    ms = min(h, m + 8)
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = FP64_TFLOPS_NOMINAL * sm_mhz / 2070.0
+    # algorithmic FP64 flops per launch of each stage (one mode: isotropic shortcut)
+    work = {
+        "eig": 2.0 * (3 * h * h * ms + 2 * 2 * h * ms * ms + 2 * h * ms * ms + 40 * ms ** 3 + h * ms * m),
+        "core": 2.0 * (h * h * h * R + R * h * h * R + R * R * h * R),
+        "error": 2.0 * (h * r * r * r + h * h * r * r + h * h * h * r) + 3.0 * h ** 3,
+    }
+    if precision == binding.TK_FP64:
+        work["gram"] = 2.0 * h * (h + 1) / 2 * h * h
+    stages = {k: v for k, v in prof.items() if v[1] > 0 and k in ("eval", "gram", "eig", "core", "error", "rank")}
+    top = max(stages, key=lambda k: stages[k][0])
+    ms_launch = stages[top][0] / stages[top][1]
+    if top == "gram" and precision != binding.TK_FP64:
+        issued = 21 * 2.0 * 128 * 96 * (h * h) * (((h + 95) // 96) * ((h + 127) // 128))
+        ach = issued / (ms_launch * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        return {"kernel": "gram stage (k_gram_tc, sliced BF16)", "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"bf16_tflops_sustained ({peak_src}), issued slice products",
+                "stage_ms_per_launch": ms_launch}
+    if top in work:
+        ach = work[top] / (ms_launch * 1e-3) / 1e12
+        return {"kernel": f"{top} stage (FP64)", "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock",
+                "algorithmic_flop_per_launch": work[top], "stage_ms_per_launch": ms_launch}
+    return {"kernel": f"{top} stage", "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "stage_ms_per_launch": ms_launch}
+
+
 def run_ours(args):
     import torch
 
@@ -178,12 +241,71 @@ def run_ours(args):
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local_rank)
     ctx = binding.Context(local_rank)
-    prob = workloads.matern_n256(1e-6)
     prec_name = args.precision
     if prec_name == "auto":
         prec_name = "sliced" if getattr(binding, "SLICED_AVAILABLE", False) else "fp64"
     precision = binding.TK_SLICED_BF16 if prec_name == "sliced" else binding.TK_FP64
     stream = torch.cuda.Stream()
+    # written between timed steps so that no step starts with a warm L2 (129 MB)
+    flush = torch.zeros(64 << 20, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(step, steps, warmup, profile=False):
+        """Per-step CUDA events on the solve stream; L2 flushed between steps."""
+        for _ in range(warmup):
+            step()
+        if profile:
+            ctx.profile(True)
+        l0 = binding.Context.kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        out = None
+        for k in range(steps):
+            _flush_l2(torch, flush, stream)
+            ev[k][0].record(stream)
+            out = step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = binding.Context.kernel_launches() - l0
+        lat = [a.elapsed_time(b) for a, b in ev]
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile(False)
+        return allmax(sum(lat)), lat, launches, prof, out
+
+    peaks, peak_src = load_peaks()
+    if args.workload == "single":
+        line = bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier,
+                            allmax, world, peaks, peak_src)
+    elif args.workload == "sweep":
+        line = bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, world, peaks,
+                           peak_src)
+    else:
+        line = bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier, allmax, world,
+                 peaks, peak_src):
+    rank, local_rank, _ = dist_info()
+    prob = workloads.matern_n256(1e-6)
 
     def solve(p):
         res = ctx.tucker(prob, precision=p, stream=stream)
@@ -192,54 +314,18 @@ def run_ours(args):
         res.free()
         return err, ranks
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def timed(p, steps, warmup, profile=False):
-        for _ in range(warmup):
-            solve(p)
-        if profile:
-            ctx.profile(True)
-        l0 = binding.Context.kernel_launches()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        t0.record(stream)
-        out = None
-        for k in range(steps):
-            ev[k][0].record(stream)
-            out = solve(p)
-            ev[k][1].record(stream)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        launches = binding.Context.kernel_launches() - l0
-        ms = t0.elapsed_time(t1)
-        lat = sorted(a.elapsed_time(b) for a, b in ev)
-        prof = ctx.profile_read() if profile else None
-        if profile:
-            ctx.profile(False)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, lat, launches, prof, out
-
     sampler = ClockSampler(local_rank)
     for _ in range(args.warmup):
         solve(precision)
     sampler.start()
-    ms, lat, launches, prof, (err, (ranks, flags)) = timed(precision, args.steps, 0, profile=True)
+    ms, lat, launches, prof, (err, (ranks, flags)) = timed(lambda: solve(precision), args.steps, 0, profile=True)
     clocks = sampler.stop()
     value = args.steps * world / (ms / 1000.0)
 
     # the plain FP64 GPU path on the same workload (comparison of the metric)
     if precision != binding.TK_FP64:
         k64 = max(3, min(args.steps, 10))
-        ms64, lat64, _, _, (err64, _) = timed(binding.TK_FP64, k64, 1)
+        ms64, lat64, _, _, (err64, _) = timed(lambda: solve(binding.TK_FP64), k64, 1)
         fp64 = {"value": k64 * world / (ms64 / 1000.0), "ms_per_step": ms64 / k64, "rel_error": err64}
     else:
         fp64 = {"value": value, "ms_per_step": ms / args.steps, "rel_error": err, "note": "this line is the FP64 path"}
@@ -261,57 +347,133 @@ def run_ours(args):
         d2h = sum(u.nbytes for u in U) + B.nbytes + 8
         res.free()
     torch.cuda.synchronize()
-    te = time.perf_counter() - te
-    if dist is not None:
-        t = torch.tensor([te], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = allmax(time.perf_counter() - te)
     e2e = {"value": ke * world / te, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # roofline of the dominant stage (largest share of the profiled step)
-    peaks, peak_src = load_peaks()
     stage_ms = {k: v[0] / max(1, args.steps) for k, v in prof.items()}
-    n = prob.n[0]
-    nmodes = 1  # isotropic shortcut: one Gram and one eigensolve per solve
-    gram_launch_ms = prof["gram"][0] / max(1, prof["gram"][1])
-    gram_flop = n * (n + 1) / 2 * n * n * 2.0  # unique entries of one G_k, K = n^2 products each
-    if precision == binding.TK_FP64:
-        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        fp64_peak_tflops = 1.25 * sm_mhz / 2070.0  # nominal 1.25 TFLOP/s at 2070 MHz, scaled by the clock
-        achieved = gram_flop / (gram_launch_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_gram_f64 (+ split-K reduce)", "bound": "alu", "achieved": achieved,
-                "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops,
-                "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock",
-                "algorithmic_flop_per_launch": gram_flop}
-    else:
-        tc_peak = peaks["bf16_tflops_sustained"]
-        achieved = gram_flop / (gram_launch_ms * 1e-3) / 1e12
-        roof = {"kernel": "gram (sliced BF16)", "bound": "tensor", "achieved": achieved, "peak": tc_peak,
-                "unit": "TFLOP/s", "frac": achieved / tc_peak, "traffic": None,
-                "peak_source": f"bf16_tflops_sustained ({peak_src})", "algorithmic_flop_per_launch": gram_flop}
-
+    roof = _roofline(prof, args.steps, prob, ranks[:1], precision, clocks, peaks, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if precision == binding.TK_FP64 else "bf16-slices/f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": prec_name, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: F (134 MB FP64) is resampled every step",
-                   "isotropic_shortcut": True},
+                   "l2": "flushed between steps (512 MB written on the solve stream, outside the step events)",
+                   "isotropic_shortcut": True, "reflect_fold": True},
         "rel_error": err, "ranks": ranks, "flags": flags,
-        "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+        "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
         "fp64_path": fp64, "e2e": e2e, "gpu_launches": launches, "stages_ms_per_step": stage_ms,
         "roofline": roof, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line
+
+
+def bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, world, peaks, peak_src):
+    rank, local_rank, _ = dist_info()
+    probs = workloads.sweep()
+
+    def step(p=precision):
+        rs = ctx.batch(probs, precision=p, stream=stream)
+        ranks = [r.ranks[0][0] for r in rs]
+        for r in rs:
+            r.free()
+        return ranks
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, lat, launches, prof, ranks = timed(step, args.steps, args.warmup, profile=True)
+    clocks = sampler.stop()
+    value = len(probs) * args.steps * world / (ms / 1000.0)
+    # accuracy of every instance, outside the timed region
+    rs = ctx.batch(probs, precision=precision, stream=stream)
+    errs = [r.rel_error(stream=stream) for r in rs]
+    flags = [r.ranks[1][0] for r in rs]
+    for r in rs:
+        r.free()
+    ok = sum(1 for e, p, f in zip(errs, probs, flags) if e <= p.eps * (1 + 1e-6) or (f & binding.TK_RANK_CAPPED))
+    fp64 = None
+    if precision != binding.TK_FP64:
+        k64 = max(2, min(args.steps, 3))
+        ms64, _, _, _, _ = timed(lambda: step(binding.TK_FP64), k64, 1)
+        fp64 = {"value": len(probs) * k64 * world / (ms64 / 1000.0), "ms_per_step": ms64 / k64}
+    line = {
+        "metric": "Matern Tucker-HOSVD solves/s, 256-instance n=128 sweep (tk_batch)", "value": value,
+        "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == binding.TK_FP64 else "bf16-slices/f64", "data": "synthetic",
+        "config": {"workload": SWEEP, "precision": prec_name, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps; the batch's octant tensors (537 MB) exceed L2"},
+        "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
+        "ranks": {"min": min(ranks), "max": max(ranks), "mean": sum(ranks) / len(ranks)},
+        "rel_error": {"max": max(errs), "within_eps_or_capped": ok, "count": len(errs)},
+        "fp64_path": fp64, "gpu_launches": launches,
+        "stages_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()}, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t = time.perf_counter()
+        for p in probs[:2]:
+            oracle.hosvd(workloads.oracle_kernel(p, oracle), workloads.oracle_grid(p, oracle), p.eps,
+                         rmax=list(p.rmax))
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": 2 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"first 2 of the 256 sweep instances, whole FP64 oracle solves "
+                                          f"({dt:.1f} s), extrapolated per solve"}
+    return line
+
+
+def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax):
+    rank, local_rank, _ = dist_info()
+    stream = workloads.serving_stream()
+
+    def replay(p, reqs):
+        ctx.serve_start(workers=2)
+        t0 = time.perf_counter()
+        tickets = []
+        for at, q in reqs:
+            d = at - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append((time.perf_counter() - t0, ctx.submit(q, precision=p)))
+        lats, ends = [], []
+        for ts, t in tickets:
+            res, lat = ctx.poll(t, wait_s=600.0)
+            res.free()
+            lats.append(lat)
+            ends.append(ts + lat)
+        stats = ctx.serve_stats()
+        ctx.serve_stop()
+        span = max(ends)
+        return len(reqs) / span, lats, stats
+
+    # warm-up: a few requests of every size
+    warm = [(0.0, workloads.problem(0, nu=1.0, ell=0.3, n=n, eps=1e-6, rmax=64)) for n in (64, 128, 256, 384)]
+    replay(precision, warm)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    value, lats, stats = replay(precision, stream)
+    clocks = sampler.stop()
+    fp64 = None
+    if precision != binding.TK_FP64:
+        replay(binding.TK_FP64, warm)
+        v64, l64, s64 = replay(binding.TK_FP64, stream)
+        fp64 = {"value": v64, "latency_ms": {"p50": 1000 * statistics.median(l64), "p99": 1000 * _pct(l64, 0.99)},
+                "batches": s64["batches"]}
+    lat_ms = [1000 * x for x in lats]
+    return {
+        "metric": "Matern Tucker-HOSVD serving solves/s with p50/p99 latency", "value": value * world,
+        "unit": "solves/s", "n_gpus": world, "steps": len(stream), "warmup": len(warm),
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == binding.TK_FP64 else "bf16-slices/f64", "data": "synthetic",
+        "config": {"workload": SERVING, "precision": prec_name, "workers": 2,
+                   "l2": "requests of up to 24 MB octant tensors stream through; no flush"},
+        "latency_ms": {"p50": statistics.median(lat_ms), "p99": _pct(lat_ms, 0.99), "max": max(lat_ms)},
+        "serve_stats": stats, "fp64_path": fp64, "clocks": clocks,
+    }
 
 
 def main():

@@ -170,6 +170,50 @@ int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* gr
              tk_result** outs, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): a request loop with continuous
+ * batching on the context's device.  Worker threads, each with its own CUDA
+ * stream, take the oldest queued request together with every queued request
+ * of the same shape (grid, precision, rank caps; any kernel and eps) that the
+ * memory budget admits, and solve them as one tk_batch-style batch; requests
+ * arriving meanwhile form the next batches, so work from several batches
+ * overlaps on the device.  Results (factors, cores) stay in device memory
+ * until taken.  A request's result is bitwise the one tk_tucker returns for it
+ * alone.  Requests need reflect_fold = 1 and rfix_k <= ceil(n_k / 2).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t workers;      /* concurrent batches (streams), 1..8; default 2 */
+  int32_t max_batch;    /* most requests per batch, 1..4096; default 256 */
+  double mem_fraction;  /* share of the device memory free at start (and at
+                           each admission) that batches may plan for,
+                           (0, 0.95]; default 0.8 */
+  int32_t reserved[4];  /* must be zero */
+} tk_serve_opts;
+
+typedef struct {
+  uint64_t submitted, completed, failed;  /* requests */
+  uint64_t batches, max_batch_seen;       /* batches launched, largest one */
+  uint64_t bytes_budget, bytes_peak;      /* admission budget, largest planned in-flight bytes */
+  uint64_t queued, in_flight_batches;     /* now */
+} tk_serve_stats;
+
+void tk_default_serve_opts(tk_serve_opts* opts);
+/* Starts the loop (TK_EINVAL if already serving or opts out of range). */
+int tk_serve_start(tk_ctx* ctx, const tk_serve_opts* opts);
+/* Finishes every queued request, stops the workers and frees the results
+ * not taken (TK_EINVAL if not serving).  tk_destroy calls it. */
+int tk_serve_stop(tk_ctx* ctx);
+/* Queues one solve (host structs, copied); *ticket identifies it.  Returns
+ * at once; TK_EINVAL for invalid arguments or when not serving. */
+int tk_submit(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts, uint64_t* ticket);
+/* Takes the result of a ticket, waiting up to wait_s seconds (0: no wait).
+ * TK_EBUSY: not finished yet; TK_ENOTFOUND: unknown or already taken ticket.
+ * Otherwise the ticket is consumed: TK_OK with *out the result (free it with
+ * tk_result_free) and *latency_s (may be NULL) the seconds from tk_submit to
+ * the end of its batch; or the status of a failed solve with *out NULL. */
+int tk_poll(tk_ctx* ctx, uint64_t ticket, tk_result** out, double* latency_s, double wait_s);
+int tk_serve_read_stats(tk_ctx* ctx, tk_serve_stats* out);
+
+/* ---------------------------------------------------------------------------
  * Stage entry points (one step of the path each, device buffers in and out).
  * ------------------------------------------------------------------------- */
 /* Collocation tensor F (device, n1 n2 n3 FP64) of Sec. 3.7. */

@@ -44,6 +44,15 @@ class Opts(_c.Structure):
                 ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("reserved", _i32 * 3)]
 
 
+class ServeOpts(_c.Structure):
+    _fields_ = [("workers", _i32), ("max_batch", _i32), ("mem_fraction", _dbl), ("reserved", _i32 * 4)]
+
+
+class ServeStats(_c.Structure):
+    _fields_ = [(name, _c.c_uint64) for name in ("submitted", "completed", "failed", "batches", "max_batch_seen",
+                                                  "bytes_budget", "bytes_peak", "queued", "in_flight_batches")]
+
+
 SIGNATURES = {
     "tk_strerror": (_c.c_char_p, [_c.c_int]),
     "tk_last_error": (_c.c_char_p, [_vp]),
@@ -69,6 +78,13 @@ SIGNATURES = {
     "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
                                _vp, _vp]),
     "tk_gram_noalloc": (_c.c_int, [_vp, _c.POINTER(_i32), _c.c_int, _vp, _vp]),
+    "tk_default_serve_opts": (None, [_c.POINTER(ServeOpts)]),
+    "tk_serve_start": (_c.c_int, [_vp, _c.POINTER(ServeOpts)]),
+    "tk_serve_stop": (_c.c_int, [_vp]),
+    "tk_submit": (_c.c_int, [_vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(Opts),
+                             _c.POINTER(_c.c_uint64)]),
+    "tk_poll": (_c.c_int, [_vp, _c.c_uint64, _c.POINTER(_vp), _c.POINTER(_dbl), _dbl]),
+    "tk_serve_read_stats": (_c.c_int, [_vp, _c.POINTER(ServeStats)]),
     "tk_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "tk_profile_read": (_c.c_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_c.c_int64)]),
     "tk_kernel_launches": (_c.c_uint64, []),
@@ -182,6 +198,40 @@ class Context:
         outs = (_vp * max(cnt, 1))()
         _check(self.lib.tk_batch(self.ptr, cnt, ks, gs, os_, outs, _stream_ptr(stream)), self.ptr)
         return [Result(self, _vp(outs[i]), probs[i]) for i in range(cnt)]
+
+    # ---- serving ----------------------------------------------------------------
+    def serve_start(self, workers=2, max_batch=256, mem_fraction=0.8):
+        o = ServeOpts()
+        self.lib.tk_default_serve_opts(_c.byref(o))
+        o.workers, o.max_batch, o.mem_fraction = int(workers), int(max_batch), float(mem_fraction)
+        _check(self.lib.tk_serve_start(self.ptr, _c.byref(o)), self.ptr)
+        self._tickets = {}
+
+    def serve_stop(self):
+        _check(self.lib.tk_serve_stop(self.ptr), self.ptr)
+
+    def submit(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0)) -> int:
+        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix)
+        t = _c.c_uint64(0)
+        _check(self.lib.tk_submit(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(t)), self.ptr)
+        self._tickets[t.value] = prob
+        return t.value
+
+    def poll(self, ticket: int, wait_s: float = 0.0):
+        """(Result, latency seconds) when done, None while running; raises on a failed solve."""
+        out = _vp()
+        lat = _dbl(0)
+        rc = self.lib.tk_poll(self.ptr, _c.c_uint64(ticket), _c.byref(out), _c.byref(lat), float(wait_s))
+        if rc == TK_EBUSY:
+            return None
+        prob = self._tickets.pop(ticket, None)
+        _check(rc, self.ptr)
+        return Result(self, out, prob), lat.value
+
+    def serve_stats(self) -> dict:
+        st = ServeStats()
+        _check(self.lib.tk_serve_read_stats(self.ptr, _c.byref(st)), self.ptr)
+        return {name: int(getattr(st, name)) for name, _ in ServeStats._fields_}
 
     # ---- diagnostics ----------------------------------------------------------
     def profile(self, on: bool = True):

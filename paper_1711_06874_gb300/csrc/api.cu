@@ -9,7 +9,9 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <set>
 #include <string>
 
 #include "tk_internal.h"
@@ -25,21 +27,21 @@ void check_cuda(cudaError_t e, const char* what) {
   }
 }
 
+// Growth is stream-ordered (cudaFreeAsync / cudaMallocAsync on the stream of
+// the work that uses the workspace), so it never synchronises the device.
 void Workspace::reserve(size_t need, cudaStream_t s) {
   used = 0;
   if (need <= bytes) return;
   if (base) {
-    check_cuda(cudaStreamSynchronize(s), "workspace sync");
-    check_cuda(cudaDeviceSynchronize(), "workspace sync");
-    check_cuda(cudaFree(base), "cudaFree(workspace)");
+    check_cuda(cudaFreeAsync(base, s), "cudaFreeAsync(workspace)");
     base = nullptr;
     bytes = 0;
   }
   const size_t want = std::max(need, bytes + bytes / 4);
-  if (cudaMalloc(&base, want) != cudaSuccess) {
+  if (cudaMallocAsync((void**)&base, want, s) != cudaSuccess) {
     cudaGetLastError();
     base = nullptr;
-    if (cudaMalloc(&base, need) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&base, need, s) != cudaSuccess) {
       cudaGetLastError();
       base = nullptr;
       fail(TK_ENOMEM, "cannot allocate device workspace of " + std::to_string(need) + " bytes");
@@ -48,6 +50,17 @@ void Workspace::reserve(size_t need, cudaStream_t s) {
   } else {
     bytes = want;
   }
+}
+
+void once_per_device(const void* key, void (*fn)()) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({key, dev})) return;
+  fn();
+  done.insert({key, dev});
 }
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -105,7 +118,7 @@ void Profiler::release() {
 }
 
 void Workspace::release() {
-  if (base) cudaFree(base);
+  if (base) cudaFreeAsync(base, 0);
   base = nullptr;
   bytes = used = 0;
 }
@@ -170,6 +183,21 @@ void check_opts(const tk_opts* o) {
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+int tk::validate_request(const tk_kernel* k, const tk_grid* g, const tk_opts* o) {
+  try {
+    check_kernel(k);
+    check_grid(g);
+    check_opts(o);
+  } catch (const Error& e) {
+    return e.status;
+  }
+  return TK_OK;
+}
+
+namespace {
 
 void set_device(tk_ctx* ctx) { TK_CUDA(cudaSetDevice(ctx->device)); }
 
@@ -269,6 +297,7 @@ int tk_create(tk_ctx** out, int device) {
 
 void tk_destroy(tk_ctx* ctx) {
   if (!ctx) return;
+  tk_serve_stop(ctx);  // no-op when not serving
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   ctx->prof.release();

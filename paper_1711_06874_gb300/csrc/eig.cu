@@ -353,30 +353,26 @@ __global__ void k_canonical_sign(double* V, int n, int m) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) V[(long long)i * m + col] = -V[(long long)i * m + col];
 }
 
+// trace of G + blockIdx.x n^2 (instance of a batch): Neumaier pairs per lane
+// over a fixed stride, then a fixed shuffle tree (one warp).
 __global__ void k_trace(const double* G, int n, double* out) {
-  __shared__ double ss[256], sc[256];
-  G += (size_t)blockIdx.x * n * n;  // instance of a batch
-  out += blockIdx.x;
+  G += (size_t)blockIdx.x * n * n;
+  const int lane = threadIdx.x;
   double s = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = lane; i < n; i += 32) {
     const double x = G[(long long)i * n + i];
     const double t = s + x;
     c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
     s = t;
   }
-  ss[threadIdx.x] = s;
-  sc[threadIdx.x] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, ac = 0.0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const double x = ss[t], u = a + x;
-      ac += (fabs(a) >= fabs(x)) ? (a - u) + x : (x - u) + a;
-      a = u;
-      ac += sc[t];
-    }
-    out[0] = a + ac;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_xor_sync(0xffffffffu, s, o);
+    const double xc = __shfl_xor_sync(0xffffffffu, c, o);
+    const double t = s + x;
+    c += ((fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s) + xc;
+    s = t;
   }
+  if (lane == 0) out[blockIdx.x] = s + c;
 }
 
 __global__ void k_symmetrize(double* H, int m) {
@@ -589,15 +585,17 @@ static size_t jacobi_smem(int m) {
   return (2ull * mp * mp + mp) * sizeof(double) + (mp + 4) * sizeof(int);
 }
 
-static void set_attrs() {
-  static bool attr_set = false;
-  if (!attr_set) {
-    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxM)));
-    TK_CUDA(cudaFuncSetAttribute(k_householder_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kQrSmemMax));
-    attr_set = true;
-  }
+static void set_attrs_once() {
+  TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxM)));
+  TK_CUDA(cudaFuncSetAttribute(k_householder_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kQrSmemMax));
+  TK_CUDA(cudaFuncSetAttribute(k_householder_qr_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kQrSmemMax));
+  TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)jacobi_smem(kMaxM)));
 }
+
+static void set_attrs() { once_per_device((const void*)&set_attrs_once, set_attrs_once); }
 
 // One eigenproblem of the batch: leading m pairs of the symmetric n x n G.
 struct EigProb {
@@ -711,7 +709,7 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   double* scr = scratch;
   double* misc = scratch + one_problem_doubles(n, m) - 64;
-  k_trace<<<1, 256, 0, s>>>(G, n, trace_out ? trace_out : misc);
+  k_trace<<<1, 32, 0, s>>>(G, n, trace_out ? trace_out : misc);
   TK_LAUNCH("k_trace");
   EigProb p{G, n, m, lam, V, scr};
   eig_batch(&p, 1, s);
@@ -732,7 +730,7 @@ void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, 
   double* Vo = Ve + (size_t)he * me;
   double* s0 = Vo + (size_t)ho * mo;
   double* s1 = s0 + one_problem_doubles(he, me);
-  k_trace<<<1, 256, 0, s>>>(G, n, trace_out);
+  k_trace<<<1, 32, 0, s>>>(G, n, trace_out);
   TK_LAUNCH("k_trace");
   k_persym_split<<<64, 256, 0, s>>>(G, n, Ge, Go);
   TK_LAUNCH("k_persym_split");
@@ -846,15 +844,8 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   if (B < 1) return;
   set_attrs();
-  static std::once_flag once;
-  std::call_once(once, [] {
-    TK_CUDA(cudaFuncSetAttribute(k_householder_qr_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kQrSmemMax));
-    TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)jacobi_smem(kMaxM)));
-  });
   const EigGroup g = carve_group(scratch, G, n, m, B, lam, V);
-  k_trace<<<B, 256, 0, s>>>(G, n, trace);
+  k_trace<<<B, 32, 0, s>>>(G, n, trace);
   TK_LAUNCH("k_trace");
   solve_group(g, B, s);
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);

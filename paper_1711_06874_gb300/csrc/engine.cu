@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -28,10 +29,32 @@
 
 namespace tk {
 
+// A process-wide non-blocking stream per device for releasing result blocks:
+// stream-ordered frees do not synchronise the device (the caller guarantees
+// that no work still reads a result it frees).
+static cudaStream_t free_stream(int device) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = streams.find(device);
+  if (it != streams.end()) return it->second;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  streams[device] = s;
+  return s;
+}
+
 DeviceBlock::~DeviceBlock() {
   if (ptr) {
     cudaSetDevice(device);
-    cudaFree(ptr);
+    cudaStream_t s = free_stream(device);
+    if (!s || cudaFreeAsync(ptr, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ptr);
+    }
   }
 }
 
@@ -166,28 +189,6 @@ __global__ void k_extract_core(const CoreDesc* __restrict__ descs) {
     d.dst[e] = d.src[((long long)a * d.R + b) * d.R + c];
   }
 }
-
-// Carves of one workspace from a list of sizes (bytes), 256-byte aligned.
-struct Plan {
-  std::vector<size_t> sizes;
-  size_t add(size_t bytes) {
-    sizes.push_back(bytes);
-    return sizes.size() - 1;
-  }
-  size_t total() const {
-    size_t t = 0;
-    for (size_t b : sizes) t += (b + 255) & ~size_t(255);
-    return t + 256;
-  }
-};
-
-struct Carver {
-  Workspace& ws;
-  template <class T>
-  T* take(size_t count) {
-    return ws.take<T>(std::max<size_t>(count, 1));
-  }
-};
 
 }  // namespace
 
@@ -428,7 +429,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   }
   auto mem = std::make_shared<DeviceBlock>();
   mem->device = ctx->device;
-  if (cudaMalloc(&mem->ptr, sizeof(double) * std::max<size_t>(tot, 1)) != cudaSuccess) {
+  if (cudaMallocAsync(&mem->ptr, sizeof(double) * std::max<size_t>(tot, 1), s) != cudaSuccess) {
     cudaGetLastError();
     mem->ptr = nullptr;
     fail(TK_ENOMEM, "cannot allocate the results of a batch");

@@ -473,13 +473,32 @@ __global__ void k_gemm_warp(GemmDesc d) {
   }
 }
 
-enum class Tile { k64x64, k128x32, k256x16, k16x16 };
+// Output tiles (BM x BN); every one sums each output in the same k order.
+struct TileShape {
+  int bm, bn;
+};
+constexpr TileShape kTiles[] = {{64, 64}, {128, 32}, {256, 16}, {32, 64}, {64, 32}, {128, 16}, {16, 128},
+                                {32, 32}, {64, 16}, {16, 64}, {16, 16}};
+constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
 
-Tile pick_tile(const GemmDesc& d) {
-  if (d.M <= 16 && d.N <= 16) return Tile::k16x16;
-  if (d.N <= 16) return Tile::k256x16;
-  if (d.N <= 32) return Tile::k128x32;
-  return Tile::k64x64;
+// Largest tile that still fills a wave of CTAs with little padding; with too
+// few outputs for a wave, the tile giving the most CTAs.
+int pick_tile(const GemmDesc& d) {
+  auto ctas = [&](int t) {
+    return (long long)((d.M + kTiles[t].bm - 1) / kTiles[t].bm) * ((d.N + kTiles[t].bn - 1) / kTiles[t].bn) *
+           d.batch;
+  };
+  auto waste = [&](int t) {
+    const double pm = (double)((d.M + kTiles[t].bm - 1) / kTiles[t].bm) * kTiles[t].bm;
+    const double pn = (double)((d.N + kTiles[t].bn - 1) / kTiles[t].bn) * kTiles[t].bn;
+    return pm * pn / ((double)d.M * d.N);
+  };
+  for (int t = 0; t < kNumTiles; ++t)
+    if (ctas(t) >= 152 && waste(t) <= 1.34) return t;
+  int best = kNumTiles - 1;
+  for (int t = 0; t < kNumTiles; ++t)
+    if (waste(t) <= 2.0 && ctas(t) > ctas(best)) best = t;
+  return best;
 }
 
 template <int BM, int BN>
@@ -493,22 +512,22 @@ void launch(const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s
   TK_LAUNCH("k_gemm_f64");
 }
 
+template <int I, bool kErr>
+dim3 dispatch_at(int t, const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s, bool run) {
+  if constexpr (I < kNumTiles) {
+    if (t == I) {
+      if (run) launch<kTiles[I].bm, kTiles[I].bn, kErr>(d, R, partials, s);
+      return grid_of<kTiles[I].bm, kTiles[I].bn>(d);
+    }
+    return dispatch_at<I + 1, kErr>(t, d, R, partials, s, run);
+  } else {
+    return dim3(0, 0, 0);
+  }
+}
+
 template <bool kErr>
 dim3 dispatch(const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s, bool run) {
-  switch (pick_tile(d)) {
-    case Tile::k16x16:
-      if (run) launch<16, 16, kErr>(d, R, partials, s);
-      return grid_of<16, 16>(d);
-    case Tile::k256x16:
-      if (run) launch<256, 16, kErr>(d, R, partials, s);
-      return grid_of<256, 16>(d);
-    case Tile::k128x32:
-      if (run) launch<128, 32, kErr>(d, R, partials, s);
-      return grid_of<128, 32>(d);
-    default:
-      if (run) launch<64, 64, kErr>(d, R, partials, s);
-      return grid_of<64, 64>(d);
-  }
+  return dispatch_at<0, kErr>(pick_tile(d), d, R, partials, s, run);
 }
 
 }  // namespace

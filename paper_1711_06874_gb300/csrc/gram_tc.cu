@@ -495,9 +495,8 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
   const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, B, kTM);
   const CUtensorMap mapB = slice_map(enc, S, p.Kp, p.nrows, B, kTN);
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  once_per_device((const void*)&k_gram_tc, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   });
   TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.nsplit, p.kb_per_split, p.kb_total, P, err};
   k_gram_tc<<<dim3(p.nblocks, p.nsplit, B), kThreads, kSmemBytes, s>>>(mapA, mapB, a);

@@ -27,6 +27,10 @@ void count_launch();
 #define TK_CUDA(call) ::tk::check_cuda((call), #call)
 #define TK_LAUNCH(what) (::tk::count_launch(), ::tk::check_cuda(cudaGetLastError(), what))
 
+// Runs fn once for each (key, current CUDA device) pair, thread-safe; for
+// per-device settings such as a kernel's shared-memory limit.
+void once_per_device(const void* key, void (*fn)());
+
 // Device workspace owned by a context: grows, never shrinks until destroyed.
 struct Workspace {
   char* base = nullptr;
@@ -207,6 +211,8 @@ struct BucketKey {
   bool operator==(const BucketKey& o) const;
 };
 BucketKey bucket_key(const SolveReq& r);
+// Argument checks of a solve request (TK_OK or TK_EINVAL), no side effects.
+int validate_request(const tk_kernel* k, const tk_grid* g, const tk_opts* o);
 // Upper bound of the device bytes one request adds to a batch (workspaces
 // and results), for admission.
 size_t bucket_bytes_per_instance(const BucketKey& key);
@@ -247,7 +253,8 @@ struct tk_ctx {
   std::string last_error;
   int sm_count = 0;
   tk::Profiler prof;
-  struct tk_server* server = nullptr;
+  std::mutex server_mu;
+  std::shared_ptr<struct tk_server> server;  // serving loop, when started
 };
 
 struct tk_result {
