@@ -83,12 +83,34 @@ struct QrBatch {
   QrProb p[2];  // one problem per CTA
 };
 
+// X[:, c] -= beta v (v^T X[:, c]) for c in [c0, c1), rows j..n-1 (v = X-like
+// column with ld n).  Each warp takes four columns at a time, eight lanes per
+// column: 8-way partial dot products, a 3-level shuffle tree, then the update.
+__device__ __forceinline__ void reflect_cols(const double* v, double* X, int n, int j, int c0, int c1, double beta,
+                                             int gsub, int l8, int w, int nw) {
+  for (int cb = c0 + 4 * w; cb < c1; cb += 4 * nw) {
+    const int c = cb + gsub;
+    const bool act = c < c1;
+    double* xc = X + (long long)(act ? c : c0) * n;
+    double d = 0.0;
+    if (act)
+      for (int i = j + l8; i < n; i += 8) d = fma(v[i], xc[i], d);
+    d += __shfl_xor_sync(0xffffffffu, d, 4);
+    d += __shfl_xor_sync(0xffffffffu, d, 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    const double f = beta * d;
+    if (act)
+      for (int i = j + l8; i < n; i += 8) xc[i] = fma(-f, v[i], xc[i]);
+  }
+}
+
 template <bool kShared>
 __device__ void qr_body(double* Yg, double* Qg, int n, int m) {
   extern __shared__ double qr_sm[];
   __shared__ double beta[kMaxM];
   __shared__ double red[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gsub = lane >> 3, l8 = lane & 7;
   double* Y = kShared ? qr_sm : Yg;
   double* Q = kShared ? qr_sm + (size_t)n * m : Qg;
   if (kShared) {
@@ -117,14 +139,7 @@ __device__ void qr_body(double* Yg, double* Qg, int n, int m) {
     }
     __syncthreads();
     const double bj = beta[j];
-    for (int c = j + 1 + w; c < m; c += nw) {
-      double* yc = Y + (long long)c * n;
-      double d = 0.0;
-      for (int i = j + lane; i < n; i += 32) d += y[i] * yc[i];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      const double f = bj * d;
-      for (int i = j + lane; i < n; i += 32) yc[i] -= f * y[i];
-    }
+    reflect_cols(y, Y, n, j, j + 1, m, bj, gsub, l8, w, nw);
     __syncthreads();
   }
   // Q = H_0 ... H_{m-1} [I; 0]
@@ -135,17 +150,7 @@ __device__ void qr_body(double* Yg, double* Qg, int n, int m) {
   __syncthreads();
   for (int j = m - 1; j >= 0; --j) {
     const double bj = beta[j];
-    const double* v = Y + (long long)j * n;
-    if (bj != 0.0) {
-      for (int c = j + w; c < m; c += nw) {
-        double* qc = Q + (long long)c * n;
-        double d = 0.0;
-        for (int i = j + lane; i < n; i += 32) d += v[i] * qc[i];
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        const double f = bj * d;
-        for (int i = j + lane; i < n; i += 32) qc[i] -= f * v[i];
-      }
-    }
+    if (bj != 0.0) reflect_cols(Y + (long long)j * n, Q, n, j, j, m, bj, gsub, l8, w, nw);
     __syncthreads();
   }
   if (kShared)
@@ -164,11 +169,108 @@ __global__ void __launch_bounds__(1024) k_householder_qr_strided(double* Y, doub
 }
 
 // ---------------------------------------------------------------------------
+// First pass of the subspace iteration in FP32 (one CTA per instance): G is
+// rounded to FP32 in shared memory, Y = G Omega (Omega from the hash, the
+// same start block for every instance), and Y's Householder QR in FP32 gives
+// the start block Q0 (written in FP64, column-major n x ms) of the FP64 pass.
+// Only its span matters, and the FP64 pass that follows fixes its accuracy.
+// ---------------------------------------------------------------------------
+__device__ float block_sum_f(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    float t = (lane < nw) ? red[lane] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__device__ __forceinline__ void reflect_cols_f(const float* v, float* X, int n, int j, int c0, int c1, float beta,
+                                               int w, int nw, int lane) {
+  for (int c = c0 + w; c < c1; c += nw) {
+    float* xc = X + (long long)c * n;
+    float d = 0.0f;
+    for (int i = j + lane; i < n; i += 32) d = fmaf(v[i], xc[i], d);
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const float f = beta * d;
+    for (int i = j + lane; i < n; i += 32) xc[i] = fmaf(-f, v[i], xc[i]);
+  }
+}
+
+size_t start32_smem(int n, int ms) { return sizeof(float) * ((size_t)n * n + 2ull * n * ms); }
+
+__global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, int n, int ms,
+                                                  unsigned long long seed, double* __restrict__ Q0) {
+  extern __shared__ float s32[];
+  __shared__ float beta[kMaxM];
+  __shared__ float red[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float* Gs = s32;             // n x n
+  float* Y = Gs + n * n;       // n x ms, column-major
+  float* W = Y + n * ms;       // Omega, then Q
+  G += (size_t)blockIdx.x * n * n;
+  Q0 += (size_t)blockIdx.x * n * ms;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Gs[e] = (float)G[e];
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = (float)hash_uniform(seed, (unsigned long long)e);
+  __syncthreads();
+  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i coalesced)
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    const float* om = W + (long long)c * n;
+    float acc = 0.0f;
+    for (int k = 0; k < n; ++k) acc = fmaf(Gs[k * n + i], om[k], acc);
+    Y[e] = acc;
+  }
+  __syncthreads();
+  for (int j = 0; j < ms; ++j) {
+    float* y = Y + (long long)j * n;
+    float ss = 0.0f;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) ss = fmaf(y[i], y[i], ss);
+    const float alpha2 = block_sum_f(ss, red);
+    const float alpha = sqrtf(alpha2);
+    const float x0 = y[j];
+    __syncthreads();
+    if (!(alpha > 0.0f)) {
+      if (threadIdx.x == 0) beta[j] = 0.0f;
+      __syncthreads();
+      continue;
+    }
+    const float v0 = x0 + (x0 >= 0.0f ? alpha : -alpha);
+    const float vtv = alpha2 - x0 * x0 + v0 * v0;
+    if (threadIdx.x == 0) {
+      y[j] = v0;
+      beta[j] = 2.0f / vtv;
+    }
+    __syncthreads();
+    reflect_cols_f(y, Y, n, j, j + 1, ms, beta[j], w, nw, lane);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    W[e] = (i == c) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  for (int j = ms - 1; j >= 0; --j) {
+    const float bj = beta[j];
+    if (bj != 0.0f) reflect_cols_f(Y + (long long)j * n, W, n, j, j, ms, bj, w, nw, lane);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) Q0[e] = (double)W[e];
+}
+
+// ---------------------------------------------------------------------------
 // Cyclic Jacobi on a symmetric m x m matrix (row-major, ld = m) in one CTA.
 // Parallel ordering: the circle method pairs the mp (even) indices into
 // mp/2 disjoint planes per step, mp - 1 steps per sweep; each step applies
 // the mp/2 rotations to rows, then to columns and to V.  A rotation is skipped
-// when |a_pq| <= 1e-18 |A|_F; sweeps stop when none is applied.
+// when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself
+// (such a rotation moves only vectors whose eigenvalues lie in the rounding
+// noise); sweeps stop when none is applied.
 // Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
 // ---------------------------------------------------------------------------
 struct JacProb {
@@ -201,7 +303,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   __syncthreads();
   double fs = 0.0;
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) fs += A[e] * A[e];
-  const double tau = 1e-18 * sqrt(block_sum(fs, red));
+  const double tau = 0x1p-53 * sqrt(block_sum(fs, red));
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
@@ -579,6 +681,7 @@ size_t sym_eig_scratch_doubles(int n, int m) {
 }
 
 static constexpr size_t kQrSmemMax = 200 * 1024;
+static constexpr size_t kStart32SmemMax = 200 * 1024;
 
 static size_t jacobi_smem(int m) {
   const int mp = (m + 1) & ~1;
@@ -593,6 +696,7 @@ static void set_attrs_once() {
                                (int)kQrSmemMax));
   TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)jacobi_smem(kMaxM)));
+  TK_CUDA(cudaFuncSetAttribute(k_start32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStart32SmemMax));
 }
 
 static void set_attrs() { once_per_device((const void*)&set_attrs_once, set_attrs_once); }
@@ -790,22 +894,36 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
     // whole matrices: Jacobi directly
     TK_CUDA(cudaMemcpyAsync(g.H, g.G, sizeof(double) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    k_random_rep<<<(unsigned)std::min<long long>(((long long)B * n * ms + 255) / 256, 1024), 256, 0, s>>>(
-        g.Y, (long long)n * ms, B, 0x1711068740ull + (unsigned)n);
-    TK_LAUNCH("k_random_rep");
+    const unsigned long long seed = 0x1711068740ull + (unsigned)n;
     const size_t need = 2ull * n * ms * sizeof(double);
-    for (int pass = 0; pass < 2; ++pass) {
-      const double* src = (pass == 0) ? g.Y : g.Q;
-      GemmDesc d{n, ms, n, B, g.G, (long long)n * n, n, 1, src, (long long)n * ms, 1, n,
-                 g.W, (long long)n * ms, 1, n};
-      d.fixed_order = 1;
-      gemm_f64(d, s);
-      TK_CUDA(cudaMemcpyAsync(g.Y, g.W, sizeof(double) * (size_t)B * n * ms, cudaMemcpyDeviceToDevice, s));
+    auto qr = [&]() {
       if (need <= kQrSmemMax)
         k_householder_qr_strided<true><<<B, 1024, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       else
         k_householder_qr_strided<false><<<B, 1024, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       TK_LAUNCH("k_householder_qr_strided");
+    };
+    auto power = [&](const double* src) {  // Y = G src
+      GemmDesc d{n, ms, n, B, g.G, (long long)n * n, n, 1, src, (long long)n * ms, 1, n,
+                 g.Y, (long long)n * ms, 1, n};
+      d.fixed_order = 1;
+      gemm_f64(d, s);
+    };
+    if (start32_smem(n, ms) <= kStart32SmemMax) {
+      // FP32 pass from the random block, then one FP64 pass
+      k_start32<<<B, 1024, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q);
+      TK_LAUNCH("k_start32");
+      power(g.Q);
+      qr();
+    } else {
+      // two FP64 passes from the random block
+      k_random_rep<<<(unsigned)std::min<long long>(((long long)B * n * ms + 255) / 256, 1024), 256, 0, s>>>(
+          g.W, (long long)n * ms, B, seed);
+      TK_LAUNCH("k_random_rep");
+      power(g.W);
+      qr();
+      power(g.Q);
+      qr();
     }
     GemmDesc d1{n, ms, n, B, g.G, (long long)n * n, n, 1, g.Q, (long long)n * ms, 1, n,
                 g.W, (long long)n * ms, 1, n};
