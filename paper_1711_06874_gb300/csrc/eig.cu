@@ -72,8 +72,107 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// Householder QR of a column-major n x m panel Y in shared memory, with the
+// explicit orthonormal factor Q (n x m, same layout) written to Qs.  Groups
+// of eight lanes own one column each (four columns per warp).  In step j the
+// group owning column j + 1 also takes that column's new squared norm and its
+// reflector scalars, so a step needs one barrier and no block-wide reduction:
+//   v = x + sign(x_0) |x| e_0, beta = 2 / v^T v, H_j = I - beta v v^T.
+template <class T>
+__device__ __forceinline__ void reflector(T alpha2, T x0, T& v0, T& beta) {
+  if (!(alpha2 > T(0))) {
+    v0 = x0;
+    beta = T(0);
+    return;
+  }
+  const T alpha = sqrt(alpha2);
+  v0 = x0 + (x0 >= T(0) ? alpha : -alpha);
+  beta = T(2) / (alpha2 - x0 * x0 + v0 * v0);
+}
+
+template <class T>
+__device__ __forceinline__ T group_sum8(T d) {
+  d += __shfl_xor_sync(0xffffffffu, d, 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+template <class T>
+__device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gsub = lane >> 3, l8 = lane & 7;
+  // reflector of column 0
+  if (w == 0) {
+    T s2 = T(0);
+    for (int i = lane; i < n; i += 32) s2 += Y[i] * Y[i];
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) reflector(s2, Y[0], v0s[0], beta[0]);
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const T* y = Y + (long long)j * n;
+    const T v0 = v0s[j], bj = beta[j];
+    for (int cb = j + 1 + 4 * w; cb < m; cb += 4 * nw) {
+      const int c = cb + gsub;
+      const bool act = c < m;
+      T* xc = Y + (long long)(act ? c : j + 1) * n;
+      T d = T(0);
+      if (act && bj != T(0)) {
+        if (l8 == 0) d = v0 * xc[j];
+        for (int i = j + 1 + l8; i < n; i += 8) d += y[i] * xc[i];
+      }
+      d = group_sum8(d);
+      const T f = bj * d;
+      T s2 = T(0);
+      if (act) {
+        if (f != T(0)) {
+          if (l8 == 0) xc[j] -= f * v0;
+          for (int i = j + 1 + l8; i < n; i += 8) {
+            const T x = xc[i] - f * y[i];
+            xc[i] = x;
+            s2 += x * x;
+          }
+        } else {
+          for (int i = j + 1 + l8; i < n; i += 8) s2 += xc[i] * xc[i];
+        }
+      }
+      s2 = group_sum8(s2);
+      // the group of column j + 1 sets that column's reflector for the next step
+      if (c == j + 1 && l8 == 0) reflector(s2, xc[j + 1], v0s[j + 1], beta[j + 1]);
+    }
+    if (threadIdx.x == 0) Y[(long long)j * n + j] = v0;  // head of v_j, read in the Q phase
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{m-1} [I; 0], applied from the right end
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    Qs[e] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    const T bj = beta[j];
+    const T* v = Y + (long long)j * n;
+    if (bj != T(0)) {
+      for (int cb = j + 4 * w; cb < m; cb += 4 * nw) {
+        const int c = cb + gsub;
+        const bool act = c < m;
+        T* qc = Qs + (long long)(act ? c : j) * n;
+        T d = T(0);
+        if (act)
+          for (int i = j + l8; i < n; i += 8) d += v[i] * qc[i];
+        d = group_sum8(d);
+        const T f = bj * d;
+        if (act)
+          for (int i = j + l8; i < n; i += 8) qc[i] -= f * v[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // The panel Y (n x m) and the factor Q live in shared memory when 2 n m
-// doubles fit (otherwise in global memory); one warp per trailing column.
+// doubles fit (otherwise in global memory).
 struct QrProb {
   double* Y;
   double* Q;
@@ -83,76 +182,18 @@ struct QrBatch {
   QrProb p[2];  // one problem per CTA
 };
 
-// X[:, c] -= beta v (v^T X[:, c]) for c in [c0, c1), rows j..n-1 (v = X-like
-// column with ld n).  Each warp takes four columns at a time, eight lanes per
-// column: 8-way partial dot products, a 3-level shuffle tree, then the update.
-__device__ __forceinline__ void reflect_cols(const double* v, double* X, int n, int j, int c0, int c1, double beta,
-                                             int gsub, int l8, int w, int nw) {
-  for (int cb = c0 + 4 * w; cb < c1; cb += 4 * nw) {
-    const int c = cb + gsub;
-    const bool act = c < c1;
-    double* xc = X + (long long)(act ? c : c0) * n;
-    double d = 0.0;
-    if (act)
-      for (int i = j + l8; i < n; i += 8) d = fma(v[i], xc[i], d);
-    d += __shfl_xor_sync(0xffffffffu, d, 4);
-    d += __shfl_xor_sync(0xffffffffu, d, 2);
-    d += __shfl_xor_sync(0xffffffffu, d, 1);
-    const double f = beta * d;
-    if (act)
-      for (int i = j + l8; i < n; i += 8) xc[i] = fma(-f, v[i], xc[i]);
-  }
-}
-
 template <bool kShared>
 __device__ void qr_body(double* Yg, double* Qg, int n, int m) {
   extern __shared__ double qr_sm[];
-  __shared__ double beta[kMaxM];
-  __shared__ double red[33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gsub = lane >> 3, l8 = lane & 7;
+  __shared__ double beta[kMaxM + 1];
+  __shared__ double v0s[kMaxM + 1];
   double* Y = kShared ? qr_sm : Yg;
   double* Q = kShared ? qr_sm + (size_t)n * m : Qg;
   if (kShared) {
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = Yg[e];
     __syncthreads();
   }
-  for (int j = 0; j < m; ++j) {
-    double* y = Y + (long long)j * n;
-    double ss = 0.0;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) ss += y[i] * y[i];
-    const double alpha2 = block_sum(ss, red);
-    const double alpha = sqrt(alpha2);
-    const double x0 = y[j];
-    __syncthreads();
-    if (alpha == 0.0) {
-      if (threadIdx.x == 0) beta[j] = 0.0;
-      __syncthreads();
-      continue;
-    }
-    // v = x + sign(x0) alpha e1, beta = 2 / v^T v
-    const double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
-    const double vtv = alpha2 - x0 * x0 + v0 * v0;
-    if (threadIdx.x == 0) {
-      y[j] = v0;
-      beta[j] = 2.0 / vtv;
-    }
-    __syncthreads();
-    const double bj = beta[j];
-    reflect_cols(y, Y, n, j, j + 1, m, bj, gsub, l8, w, nw);
-    __syncthreads();
-  }
-  // Q = H_0 ... H_{m-1} [I; 0]
-  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-    const int c = e / n, i = e % n;
-    Q[e] = (i == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int j = m - 1; j >= 0; --j) {
-    const double bj = beta[j];
-    if (bj != 0.0) reflect_cols(Y + (long long)j * n, Q, n, j, j, m, bj, gsub, l8, w, nw);
-    __syncthreads();
-  }
+  qr_panel<double>(Y, Q, n, m, beta, v0s);
   if (kShared)
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) Qg[e] = Q[e];
 }
@@ -175,41 +216,13 @@ __global__ void __launch_bounds__(1024) k_householder_qr_strided(double* Y, doub
 // the start block Q0 (written in FP64, column-major n x ms) of the FP64 pass.
 // Only its span matters, and the FP64 pass that follows fixes its accuracy.
 // ---------------------------------------------------------------------------
-__device__ float block_sum_f(float v, float* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    float t = (lane < nw) ? red[lane] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-__device__ __forceinline__ void reflect_cols_f(const float* v, float* X, int n, int j, int c0, int c1, float beta,
-                                               int w, int nw, int lane) {
-  for (int c = c0 + w; c < c1; c += nw) {
-    float* xc = X + (long long)c * n;
-    float d = 0.0f;
-    for (int i = j + lane; i < n; i += 32) d = fmaf(v[i], xc[i], d);
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    const float f = beta * d;
-    for (int i = j + lane; i < n; i += 32) xc[i] = fmaf(-f, v[i], xc[i]);
-  }
-}
-
 size_t start32_smem(int n, int ms) { return sizeof(float) * ((size_t)n * n + 2ull * n * ms); }
 
 __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, int n, int ms,
                                                   unsigned long long seed, double* __restrict__ Q0) {
   extern __shared__ float s32[];
-  __shared__ float beta[kMaxM];
-  __shared__ float red[33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ float beta[kMaxM + 1];
+  __shared__ float v0s[kMaxM + 1];
   float* Gs = s32;             // n x n
   float* Y = Gs + n * n;       // n x ms, column-major
   float* W = Y + n * ms;       // Omega, then Q
@@ -227,39 +240,7 @@ __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, 
     Y[e] = acc;
   }
   __syncthreads();
-  for (int j = 0; j < ms; ++j) {
-    float* y = Y + (long long)j * n;
-    float ss = 0.0f;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) ss = fmaf(y[i], y[i], ss);
-    const float alpha2 = block_sum_f(ss, red);
-    const float alpha = sqrtf(alpha2);
-    const float x0 = y[j];
-    __syncthreads();
-    if (!(alpha > 0.0f)) {
-      if (threadIdx.x == 0) beta[j] = 0.0f;
-      __syncthreads();
-      continue;
-    }
-    const float v0 = x0 + (x0 >= 0.0f ? alpha : -alpha);
-    const float vtv = alpha2 - x0 * x0 + v0 * v0;
-    if (threadIdx.x == 0) {
-      y[j] = v0;
-      beta[j] = 2.0f / vtv;
-    }
-    __syncthreads();
-    reflect_cols_f(y, Y, n, j, j + 1, ms, beta[j], w, nw, lane);
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
-    const int c = e / n, i = e - c * n;
-    W[e] = (i == c) ? 1.0f : 0.0f;
-  }
-  __syncthreads();
-  for (int j = ms - 1; j >= 0; --j) {
-    const float bj = beta[j];
-    if (bj != 0.0f) reflect_cols_f(Y + (long long)j * n, W, n, j, j, ms, bj, w, nw, lane);
-    __syncthreads();
-  }
+  qr_panel<float>(Y, W, n, ms, beta, v0s);
   for (int e = threadIdx.x; e < n * ms; e += blockDim.x) Q0[e] = (double)W[e];
 }
 
@@ -742,7 +723,7 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
       smem = std::max(smem, jacobi_smem(n));
     }
     if (nj) {
-      k_jacobi<<<nj, 1024, smem, s>>>(jb);
+      k_jacobi<<<nj, 256, smem, s>>>(jb);
       TK_LAUNCH("k_jacobi");
     }
     for (int b = 0; b < count; ++b) {
@@ -779,9 +760,9 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
       if (need > kQrSmemMax) shared = false;
     }
     if (shared)
-      k_householder_qr<true><<<nr, 1024, smem, s>>>(qb);
+      k_householder_qr<true><<<nr, 256, smem, s>>>(qb);
     else
-      k_householder_qr<false><<<nr, 1024, 0, s>>>(qb);
+      k_householder_qr<false><<<nr, 256, 0, s>>>(qb);
     TK_LAUNCH("k_householder_qr");
   }
   JacBatch jb{};
@@ -797,7 +778,7 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
     jb.p[t] = JacProb{w[b].H, ms, w[b].lsub, w[b].VH, (int*)(w[b].misc + 8)};
     smem = std::max(smem, jacobi_smem(ms));
   }
-  k_jacobi<<<nr, 1024, smem, s>>>(jb);
+  k_jacobi<<<nr, 256, smem, s>>>(jb);
   TK_LAUNCH("k_jacobi");
   for (int t = 0; t < nr; ++t) {
     const int b = idx[t], n = pr[b].n, ms = w[b].ms, m = pr[b].m;
@@ -898,9 +879,9 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
     const size_t need = 2ull * n * ms * sizeof(double);
     auto qr = [&]() {
       if (need <= kQrSmemMax)
-        k_householder_qr_strided<true><<<B, 1024, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
+        k_householder_qr_strided<true><<<B, 256, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       else
-        k_householder_qr_strided<false><<<B, 1024, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
+        k_householder_qr_strided<false><<<B, 256, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       TK_LAUNCH("k_householder_qr_strided");
     };
     auto power = [&](const double* src) {  // Y = G src
@@ -911,7 +892,7 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
     };
     if (start32_smem(n, ms) <= kStart32SmemMax) {
       // FP32 pass from the random block, then one FP64 pass
-      k_start32<<<B, 1024, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q);
+      k_start32<<<B, 256, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q);
       TK_LAUNCH("k_start32");
       power(g.Q);
       qr();
@@ -937,7 +918,7 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
         g.H, ms, B);
     TK_LAUNCH("k_symmetrize_batch");
   }
-  k_jacobi_strided<<<B, 1024, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
+  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
   TK_LAUNCH("k_jacobi_strided");
   if (ms == n) {
     // first m columns of V_H (n x n) into V (n x m)
