@@ -231,13 +231,27 @@ __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, 
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) Gs[e] = (float)G[e];
   for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = (float)hash_uniform(seed, (unsigned long long)e);
   __syncthreads();
-  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i coalesced)
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
-    const int c = e / n, i = e - c * n;
+  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i
+  // coalesced); four rows n4 apart per thread as independent chains
+  const int n4 = (n + 3) / 4;
+  for (int e = threadIdx.x; e < n4 * ms; e += blockDim.x) {
+    const int c = e / n4, i = e - c * n4;
     const float* om = W + (long long)c * n;
-    float acc = 0.0f;
-    for (int k = 0; k < n; ++k) acc = fmaf(Gs[k * n + i], om[k], acc);
-    Y[e] = acc;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    const int i1 = min(i + n4, n - 1), i2 = min(i + 2 * n4, n - 1), i3 = min(i + 3 * n4, n - 1);
+    for (int k = 0; k < n; ++k) {
+      const float o = om[k];
+      const float* gk = Gs + k * n;
+      a0 = fmaf(gk[i], o, a0);
+      a1 = fmaf(gk[i1], o, a1);
+      a2 = fmaf(gk[i2], o, a2);
+      a3 = fmaf(gk[i3], o, a3);
+    }
+    float* yc = Y + (long long)c * n;
+    yc[i] = a0;
+    if (i + n4 < n) yc[i + n4] = a1;
+    if (i + 2 * n4 < n) yc[i + 2 * n4] = a2;
+    if (i + 3 * n4 < n) yc[i + 3 * n4] = a3;
   }
   __syncthreads();
   qr_panel<float>(Y, W, n, ms, beta, v0s);
@@ -249,9 +263,10 @@ __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, 
 // Parallel ordering: the circle method pairs the mp (even) indices into
 // mp/2 disjoint planes per step, mp - 1 steps per sweep; each step applies
 // the mp/2 rotations to rows, then to columns and to V.  A rotation is skipped
-// when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself
-// (such a rotation moves only vectors whose eigenvalues lie in the rounding
-// noise); sweeps stop when none is applied.
+// when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself,
+// or when both diagonal entries are below 64 u |A|_F (a plane inside the
+// rounding-noise block, whose vectors the matrix does not determine; its
+// trace is kept).  Sweeps stop when no rotation is applied.
 // Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
 // ---------------------------------------------------------------------------
 struct JacProb {
@@ -284,7 +299,9 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   __syncthreads();
   double fs = 0.0;
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) fs += A[e] * A[e];
-  const double tau = 0x1p-53 * sqrt(block_sum(fs, red));
+  const double normA = sqrt(block_sum(fs, red));
+  const double tau = 0x1p-53 * normA;
+  const double noise_diag = 0x1p-47 * normA;  // 64 u |A|_F
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
@@ -301,7 +318,10 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
         qq[k] = q;
         const double apq = A[p * mp + q];
         double c = 1.0, s = 0.0;
-        if (fabs(apq) > tau) {
+        // two indices whose diagonals both lie in the rounding noise of the
+        // matrix are left alone: their eigenvectors carry no information
+        const bool noise = fabs(A[p * mp + p]) <= noise_diag && fabs(A[q * mp + q]) <= noise_diag;
+        if (fabs(apq) > tau && !noise) {
           // The angle only steers convergence, so it is taken in FP32; (c, s)
           // are then made orthonormal to FP64 precision by two Newton steps on
           // c^2 + s^2 = 1, so the rotation applied is exactly orthogonal.
