@@ -163,6 +163,56 @@ def test_gram_isotropy_and_persymmetry(orc):
     np.testing.assert_allclose(G[0], G[0][::-1, ::-1], rtol=1e-14)  # mirrored grid points round differently
 
 
+REFLECT_CASES = [  # (n, ell, grid kind): even/odd axes, anisotropic, both grids
+    ((10, 9, 7), (0.3, 0.5, 0.7), 0),
+    ((8, 11, 6), (0.4, 0.2, 0.9), 1),
+    ((9, 9, 9), (0.25, 0.25, 0.25), 1),
+]
+
+
+def _octant(F):
+    """sqrt(w_i w_j w_l) F on the upper octant, w = 1 at an odd axis' centre, else 2."""
+    out = F[tuple(slice(m // 2, m) for m in F.shape)].copy()
+    for a, m in enumerate(F.shape):
+        w = np.full(m - m // 2, 2.0)
+        if m % 2:
+            w[0] = 1.0
+        shp = [1, 1, 1]
+        shp[a] = -1
+        out *= np.sqrt(w).reshape(shp)
+    return out
+
+
+@pytest.mark.parametrize("case", REFLECT_CASES)
+def test_gram_odd_half_vanishes(orc, case):
+    """C depends on x_a only through x_a^2 and the grid is symmetric, so rows
+    i and n-1-i of every unfolding coincide: G_k J = G_k, and G_k has at most
+    ceil(n_k/2) nonzero eigenvalues."""
+    n, ell, kind = case
+    F = orc.tensor(orc.make_kernel(orc.MATERN, nu=1.3, ell=list(ell)), orc.make_grid(list(n), kind=kind))
+    for m in range(3):
+        G = orc.gram(F, m)
+        np.testing.assert_allclose(G[:, ::-1], G, rtol=0, atol=1e-14 * np.abs(G).max())
+        lam, _, _ = orc.sym_eig(G)
+        h = (n[m] + 1) // 2
+        assert np.abs(lam[h:]).max(initial=0.0) <= 1e-14 * lam[0]
+
+
+@pytest.mark.parametrize("case", REFLECT_CASES)
+def test_octant_gram_has_the_even_spectrum(orc, case):
+    """The weighted octant keeps |F| and its Gram has the leading eigenvalues
+    of G_k (numpy on the octant against the oracle on the whole tensor)."""
+    n, ell, kind = case
+    F = orc.tensor(orc.make_kernel(orc.MATERN, nu=0.9, ell=list(ell)), orc.make_grid(list(n), kind=kind))
+    Fh = _octant(F)
+    assert abs(np.sum(Fh ** 2) - np.sum(F ** 2)) <= 1e-14 * np.sum(F ** 2)
+    for m in range(3):
+        lam, _, _ = orc.sym_eig(orc.gram(F, m))
+        A = np.moveaxis(Fh, m, 0).reshape(Fh.shape[m], -1)
+        mu = np.sort(np.linalg.eigvalsh(A @ A.T))[::-1]
+        np.testing.assert_allclose(mu, lam[: len(mu)], rtol=0, atol=1e-13 * lam[0])
+
+
 # --------------------------------------------------------------------------
 # Jacobi eigensolver
 # --------------------------------------------------------------------------
