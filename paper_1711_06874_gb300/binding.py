@@ -158,6 +158,19 @@ def _stream_ptr(stream) -> int | None:
     return int(getattr(stream, "cuda_stream", stream))
 
 
+class BatchArgs:
+    """The C structs of a batch of problems, marshalled once."""
+
+    def __init__(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None):
+        self.probs = list(probs)
+        self.count = len(self.probs)
+        rfixes = rfixes or [(0, 0, 0)] * self.count
+        n = max(self.count, 1)
+        self.ks = (Kernel * n)(*[make_kernel(p) for p in self.probs])
+        self.gs = (Grid * n)(*[make_grid(p) for p in self.probs])
+        self.os = (Opts * n)(*[make_opts(p, precision, rf, shortcut, fold) for p, rf in zip(self.probs, rfixes)])
+
+
 class Context:
     """One library context on one CUDA device."""
 
@@ -189,15 +202,13 @@ class Context:
 
     def batch(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, stream=None) -> list:
         """Independent solves in one call (tk_batch); one Result per problem.
+        probs: a list of Problems, or BatchArgs built once beforehand.
         rfixes: optional per-problem fixed ranks (tuples of 3, 0 = eps rule)."""
-        cnt = len(probs)
-        rfixes = rfixes or [(0, 0, 0)] * cnt
-        ks = (Kernel * max(cnt, 1))(*[make_kernel(p) for p in probs])
-        gs = (Grid * max(cnt, 1))(*[make_grid(p) for p in probs])
-        os_ = (Opts * max(cnt, 1))(*[make_opts(p, precision, rf, shortcut, fold) for p, rf in zip(probs, rfixes)])
+        args = probs if isinstance(probs, BatchArgs) else BatchArgs(probs, precision, shortcut, fold, rfixes)
+        cnt = args.count
         outs = (_vp * max(cnt, 1))()
-        _check(self.lib.tk_batch(self.ptr, cnt, ks, gs, os_, outs, _stream_ptr(stream)), self.ptr)
-        return [Result(self, _vp(outs[i]), probs[i]) for i in range(cnt)]
+        _check(self.lib.tk_batch(self.ptr, cnt, args.ks, args.gs, args.os, outs, _stream_ptr(stream)), self.ptr)
+        return [Result(self, _vp(outs[i]), args.probs[i]) for i in range(cnt)]
 
     # ---- serving ----------------------------------------------------------------
     def serve_start(self, workers=2, max_batch=256, mem_fraction=0.8):

@@ -52,6 +52,7 @@ struct tk_nu_consts {
   double inv_kpmu[kTemmeTerms];   // 1 / (k + mu)
   double inv_k[kTemmeTerms];      // 1 / k
   double Ck[kMillerTerms];        // (1/2 - mu)_k (1/2 + mu)_k / k!
+  double Mk[kMillerTerms];        // (k + 1/2)^2 - mu^2, the recurrence's second coefficient
 };
 
 // K_mu(x) and K_{mu+1}(x), both multiplied by e^x, for |mu| <= 1/2, x > 0.
@@ -94,21 +95,25 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
   // rescaled by 2^-600 whenever they pass 2^600.
   const int N = 12 + (int)ceil(180.0 / x);  // at most 132 for x > 1.5
   const double mu2 = mu * mu;
+  const double x2 = 2.0 * x;
   double u_next = 0.0, u = 1.0;  // u_{k+1}, u_k at k = N
   double acc = c.Ck[N];
+  double dk2 = 2.0 * (double)N;  // 2 k
   for (int k = N; k >= 1; --k) {
-    const double dk = (double)k;
-    const double u_prev = 2.0 * (dk + x) * u - ((dk + 0.5) * (dk + 0.5) - mu2) * u_next;  // u_{k-1}
+    // u_{k-1} = 2 (k + x) u_k - ((k + 1/2)^2 - mu^2) u_{k+1}
+    const double u_prev = fma(dk2 + x2, u, -c.Mk[k] * u_next);
     u_next = u;
     u = u_prev;
-    acc += c.Ck[k - 1] * u;
-    if (fabs(u) > 0x1p600) {
+    acc = fma(c.Ck[k - 1], u, acc);
+    dk2 -= 2.0;
+    // |u| grows by at most 2 (k + x) per step (far below 2^100 for any x the
+    // grids produce): a check every 4 steps keeps it below 2^1000
+    if ((k & 3) == 0 && fabs(u) > 0x1p600) {
       u *= 0x1p-600;
       u_next *= 0x1p-600;
       acc *= 0x1p-600;
     }
   }
-  // here u = u_0, u_next = u_1
   const double inv_u0 = 1.0 / u;
   const double k0 = sqrt(3.141592653589793238 / (2.0 * x)) / (acc * inv_u0);
   *kmu = k0;

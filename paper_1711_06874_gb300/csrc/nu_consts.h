@@ -33,6 +33,20 @@ inline double zeta_em(int s) {
   return sum;
 }
 
+// zeta(k) / k for k = 2 .. 64, computed once (they do not depend on nu).
+struct ZetaTable {
+  double zk[65];
+  ZetaTable() {
+    zk[0] = zk[1] = 0.0;
+    for (int k = 2; k <= 64; ++k) zk[k] = zeta_em(k) / (double)k;
+  }
+};
+
+inline const ZetaTable& zeta_table() {
+  static const ZetaTable t;  // thread-safe one-time initialisation
+  return t;
+}
+
 inline tk_nu_consts make_nu_consts(double nu) {
   tk_nu_consts c;
   c.nu = nu;
@@ -45,7 +59,7 @@ inline tk_nu_consts make_nu_consts(double nu) {
   double pw = 1.0;  // (mu^2)^floor(k/2)
   for (int k = 2; k <= 64; ++k) {
     if (k % 2 == 0) pw *= m2;
-    const double z = zeta_em(k) / (double)k;
+    const double z = zeta_table().zk[k];
     if (k % 2 == 0)
       E += z * pw;   // zeta(k) mu^k / k
     else
@@ -73,6 +87,10 @@ inline tk_nu_consts make_nu_consts(double nu) {
   for (int k = 1; k < kMillerTerms; ++k) {
     const double dk = (double)k;
     c.Ck[k] = c.Ck[k - 1] * (((dk - 0.5) * (dk - 0.5) - mu * mu) / dk);
+  }
+  for (int k = 0; k < kMillerTerms; ++k) {
+    const double dk = (double)k;
+    c.Mk[k] = (dk + 0.5) * (dk + 0.5) - mu * mu;
   }
   return c;
 }
