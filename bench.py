@@ -381,10 +381,10 @@ def bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stre
     probs = workloads.sweep()
 
     # the C structs of the 256 requests are marshalled once, like inputs already resident
-    args = {p: binding.BatchArgs(probs, precision=p) for p in {precision, binding.TK_FP64}}
+    bargs = {p: binding.BatchArgs(probs, precision=p) for p in {precision, binding.TK_FP64}}
 
     def step(p=precision):
-        return ctx.batch(args[p], stream=stream)
+        return ctx.batch(bargs[p], stream=stream)
 
     def cleanup(rs):
         ranks = [r.ranks[0][0] for r in rs]

@@ -298,7 +298,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   if (pf) pf->begin(TK_STAGE_EVAL, s);
   eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s);
   if (pf) pf->end(s);
-  for (int a = 0; a < nmodes; ++a) {
+  // modes in reverse order: the slices of mode 1 stay in the Gram scratch for
+  // the tensor-core TTM
+  for (int a = nmodes - 1; a >= 0; --a) {
     if (pf) pf->begin(TK_STAGE_GRAM, s);
     if (sliced)
       gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s);
@@ -468,10 +470,18 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
     gb.push_back(q);
   }
   const size_t ndesc = (size_t)B * nmodes;
+  // first TTM on the tensor cores from the Gram's slices when the layout allows
+  const SliceView sv = sliced ? gram_slices_view(gscr, h, 0, B) : SliceView{nullptr, nullptr, 0, 0};
+  const bool tc_ttm = sliced && h[2] % 8 == 0 && sv.Kp == (long long)h[1] * h[2] && sv.nrows == h[0];
+  size_t ttm_scr = 0;
+  if (tc_ttm)
+    for (const GroupBuf& q : gb)
+      if (q.R <= 96) ttm_scr = std::max(ttm_scr, ttm_sliced_scratch_bytes(h[2], q.R, q.cnt));
   post.reserve(carve_bytes<double>(ttm) + carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
-                   carve_bytes<CoreDesc>(B) + 4096,
+                   carve_bytes<CoreDesc>(B) + carve_bytes<char>(ttm_scr) + 4096,
                s);
   double* tbase = post.take<double>(std::max<size_t>(ttm, 1));
+  char* tscr = post.take<char>(std::max<size_t>(ttm_scr, 1));
   int* amap = post.take<int>(B);
   UnfoldDesc* ud = post.take<UnfoldDesc>(ndesc);
   CoreDesc* cd = post.take<CoreDesc>(B);
@@ -516,11 +526,15 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
     double* T2 = tbase + q.t2;
     double* Cp = tbase + q.cp;
     // mode 3: T1[(i,k)][c] = sum_l Fh[(i,k)][l] V3[l][c]
-    GemmDesc d1{h[0] * h[1], R, h[2], q.cnt, Fh, H, h[2], 1, Up2, (long long)h[2] * R, R, 1,
-                T1, (long long)h[0] * h[1] * R, R, 1};
-    d1.amap = amap + q.off;
-    d1.fixed_order = 1;
-    gemm_f64(d1, s);
+    if (tc_ttm && R <= 96) {
+      ttm_mode3_sliced(sv, h, amap + q.off, q.cnt, B, Up2, R, T1, tscr, errflag, s);
+    } else {
+      GemmDesc d1{h[0] * h[1], R, h[2], q.cnt, Fh, H, h[2], 1, Up2, (long long)h[2] * R, R, 1,
+                  T1, (long long)h[0] * h[1] * R, R, 1};
+      d1.amap = amap + q.off;
+      d1.fixed_order = 1;
+      gemm_f64(d1, s);
+    }
     // mode 1: T2[a][(k,c)] = sum_i V1[i][a] T1[i][(k,c)]
     GemmDesc d2{R, h[1] * R, h[0], q.cnt, Up0, (long long)h[0] * R, 1, R, T1, (long long)h[0] * h[1] * R,
                 (long long)h[1] * R, 1, T2, (long long)R * h[1] * R, (long long)h[1] * R, 1};
@@ -539,8 +553,11 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   k_extract_core<<<dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), 256, 0, s>>>(cd);
   TK_LAUNCH("k_extract_core");
   if (pf) pf->end(s);
+  int herr = 0;
+  TK_CUDA(cudaMemcpyAsync(&herr, errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   if (pf) pf->collect();
+  if (herr != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
 
   for (int b = 0; b < B; ++b) {
     tk_result* res = new tk_result();

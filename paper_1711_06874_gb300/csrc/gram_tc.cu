@@ -44,6 +44,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "slices.cuh"
 #include "tc_common.cuh"
 #include "tk_internal.h"
 
@@ -51,8 +52,6 @@ namespace tk {
 
 namespace {
 
-constexpr int kSlices = 6;
-constexpr int kMaxWeight = 5;          // pairs with s + t <= 5 are kept (21 pairs)
 constexpr int kTM = 128;               // rows of a block of G (M)
 constexpr int kTN = 96;                // columns of a block of G (N)
 constexpr int kAcc = 5;                // accumulators: w = 0, 1, 2, 3 and w = 4..5
@@ -69,11 +68,6 @@ constexpr int kEpiWarps = 16;
 constexpr int kEpiCols = kTN / 4;                      // 24 columns per epilogue warp
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
-// Slice pairs (s, t) with s + t <= kMaxWeight, in order of weight.
-constexpr int kPairs = 21;
-__constant__ int kPairS[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ int kPairT[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
-static_assert(kPairs == (kMaxWeight + 1) * (kMaxWeight + 2) / 2, "pair table covers s + t <= kMaxWeight");
 static_assert(kAcc * kTN <= 512, "accumulators fit in TMEM");
 
 // Row exponents: e_i with max_c |A(i,c)| < 2^e_i (frexp), -1000 for a zero row.
@@ -119,32 +113,6 @@ __global__ void k_rowexp(const unsigned long long* __restrict__ rowmax_bits, int
     if (m > 0.0) frexp(m, &e);
     rowexp[i] = e;
   }
-}
-
-// Balanced base-256 digits of x 2^(7 - e): T = round(|x| 2^(47 - e)) from the
-// FP64 bits with integer operations (|x| < 2^e, so T < 2^47), then digits from
-// the bottom: x 2^(7 - e) = sum_s d_s 2^(-8s) + O(2^-41), |d_s| <= 128.
-__device__ __forceinline__ void slice_digits(double xv, int e, int (&d)[kSlices]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  long long T = 0;
-  if (ex != 0 && e > -1000) {
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int rs = 1028 + e - ex;  // right shift of the 53-bit mantissa, >= 6
-    if (rs < 64) T = (long long)((mant + (1ull << (rs - 1))) >> rs);
-    if (bits >> 63) T = -T;
-  }
-#pragma unroll
-  for (int s = kSlices - 1; s >= 1; --s) {
-    const long long r = ((T + 128) & 255) - 128;
-    d[s] = (int)r;
-    T = (T - r) >> 8;
-  }
-  d[0] = (int)T;
-}
-
-__device__ __forceinline__ __nv_bfloat16 slice_value(int d, int s) {
-  return __float2bfloat16_rn(__int2float_rn(d) * __int_as_float((127 - 7 - 8 * s) << 23));  // d 2^(-7-8s)
 }
 
 // Slices of one unfolding, written K-major: S[s][row][c], row stride Kp (a
@@ -456,22 +424,6 @@ TcPlan tc_plan(const int n[3], int mode, int sm_count, int B = 1) {
   return p;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 // Slices of B instances, [b][s][row][Kp] bf16: dims (Kp, nrows, 6, B).
 CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long Kp, int nrows, int B,
                       int box_rows) {
@@ -491,7 +443,7 @@ CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long 
 // at S ([b][s][row][Kp]) and row exponents at rowexp ([b][row]).
 void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, long long* P, double* G, int* err,
                  cudaStream_t s) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
   const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, B, kTM);
   const CUtensorMap mapB = slice_map(enc, S, p.Kp, p.nrows, B, kTN);
@@ -554,6 +506,24 @@ void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double*
     TK_LAUNCH("k_slice");
   }
   run_tc_gram(p, B, S, rowexp, P, G, err, s);
+}
+
+SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B) {
+  const TcPlan p = tc_plan(n, mode, 152, B);
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    char* q = base + off;
+    off += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  carve(sizeof(unsigned long long) * B * p.nrows);
+  SliceView v;
+  v.rowexp = (const int*)carve(sizeof(int) * (size_t)B * p.nrows);
+  v.S = carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * p.nrows * p.Kp);
+  v.nrows = p.nrows;
+  v.Kp = p.Kp;
+  return v;
 }
 
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,

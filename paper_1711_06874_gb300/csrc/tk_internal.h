@@ -129,6 +129,22 @@ void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void
                       cudaStream_t s);
 void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
                        cudaStream_t s);
+// Where gram_sliced_batch left the slices of its last call in `scratch`:
+// S = [b][6][nrows][Kp] BF16 planes, rowexp = [b][nrows] row exponents.
+struct SliceView {
+  const int* rowexp;
+  const void* S;
+  int nrows;
+  long long Kp;
+};
+SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B);
+// (d) First TTM (mode 3) of Bg instances on the tensor cores from the mode-1
+// Gram slices of the bucket (Fh of instance amap[j] with h = (h1, h2, h3),
+// h3 % 8 == 0 and Kp == h2 h3): T1[j][(i, k)][c] = sum_l Fh[(i, k)][l]
+// Up[j][l][c] for c < R (Up: [j][h3][R] FP64).  scratch: ttm_sliced_scratch_bytes.
+size_t ttm_sliced_scratch_bytes(int h3, int R, int Bg);
+void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int Bg, int Btot, const double* Up, int R,
+                      double* T1, void* scratch, int* err, cudaStream_t s);
 // unit roundoff of the Gram of each precision (for the eps-unreachable flag)
 inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 : 0x1p-48; }
 

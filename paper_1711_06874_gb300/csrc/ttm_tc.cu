@@ -1,0 +1,309 @@
+// (d) First product of the TTM chain of the core (Sec. 3.1, 3.2):
+// T1 = Fh x_3 U_3^T, a (h1 h2) x h3 by h3 x R product, on the tcgen05 tensor
+// cores with FP64-class accuracy.  The A operand reuses the exact BF16 slices
+// of Fh that the mode-1 Gram made (rows i scaled by 2^-e_i; viewed with rows
+// (i, k) and K = l when the slice row length equals h2 h3); the B operand is
+// U_3 sliced per column c (scale 2^-f_c).  The 21 slice pairs with s + t <= 5
+// go to five FP32 TMEM accumulators (w = 0..3 exact, w = 4..5 merged) over
+// 256-deep chunks, moved to int64 in units of 2^-44 as in the Gram, and the
+// output is that integer times 2^(e_i + f_c - 44): no rounding but the slices'
+// own, the same for any batch.
+//
+// One CTA per 128 rows (i, k) of one instance: warp 0 issues the TMA loads
+// (6 slices x 128 rows of A, 6 x Np rows of B per 32-deep K block, two
+// stages), warp 1 owns TMEM and issues the MMAs, warps 2..17 drain TMEM
+// (one lane quadrant and Np/4 columns each).  Bounded waits as in the Gram.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "slices.cuh"
+#include "tc_common.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+namespace {
+
+constexpr int kTM = 128;       // rows (i, k) per CTA
+constexpr int kKB = 32;        // K per stage
+constexpr int kChunkBlocks = 8;  // 256-deep exact chunks
+constexpr int kStages = 2;
+constexpr int kMaxNp = 96;     // padded output columns (multiple of 32)
+constexpr int kAcc = 5;
+constexpr int kSliceBytesA = kTM * kKB * 2;                        // 8 KB
+constexpr int kOperandBytesA = kSlices * kSliceBytesA;             // 48 KB
+constexpr int kMaxOperandBytesB = kSlices * kMaxNp * kKB * 2;      // 36 KB
+constexpr int kStageBytes = kOperandBytesA + kMaxOperandBytesB;    // 84 KB
+constexpr int kThreads = 576;
+constexpr int kEpiWarps = 16;
+constexpr int kMaxEpiCols = kMaxNp / 4;  // 24
+constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(kAcc * kMaxNp <= 512, "accumulators fit in TMEM");
+
+struct TtmArgs {
+  int M;           // rows h1 h2
+  int h1, h2, h3;  // octant extents (K = h3)
+  int R, Np;       // output columns and their padding
+  int nkb;         // K blocks of 32
+  const int* amap;    // group instance -> bucket instance
+  const int* rowexp;  // bucket: [b][h1]
+  const int* colexp;  // group: [j][Np]
+  double* T1;         // group: [j][M][R]
+  int* err;
+};
+
+// Column slices of U (Up: [j][h3][R] FP64) -> colexp [j][Np], BS [j][6][Np][h3]
+// BF16; padding columns c >= R are zero.
+__global__ void k_bslice(const double* __restrict__ Up, int h3, int R, int Np, int* __restrict__ colexp,
+                         __nv_bfloat16* __restrict__ BS) {
+  __shared__ double red[32];
+  const int c = blockIdx.x, j = blockIdx.y;
+  const double* U = Up + (size_t)j * h3 * R;
+  const size_t plane = (size_t)Np * h3;
+  __nv_bfloat16* out = BS + (size_t)j * kSlices * plane + (size_t)c * h3;
+  double m = 0.0;
+  if (c < R)
+    for (int l = threadIdx.x; l < h3; l += blockDim.x) m = fmax(m, fabs(U[(size_t)l * R + c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double v = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+  int e = -1000;
+  if (v > 0.0) frexp(v, &e);
+  for (int l = threadIdx.x; l < h3; l += blockDim.x) {
+    int d[kSlices] = {0, 0, 0, 0, 0, 0};
+    if (c < R && e > -1000) slice_digits(U[(size_t)l * R + c], e, d);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) out[s * plane + l] = slice_value(d[s], s);
+  }
+  if (threadIdx.x == 0) colexp[(size_t)j * Np + c] = e;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_ttm_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, TtmArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+  uint64_t* full = bars;       // [kStages]
+  uint64_t* empty = bars + 2;  // [kStages]
+  uint64_t* acc_full = bars + 4;
+  uint64_t* acc_empty = bars + 5;
+  uint64_t* drain = bars + 6;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.z;  // instance of the group
+  const int row0 = blockIdx.x * kTM;
+  const int Np = args.Np;
+  const int sliceB = Np * kKB * 2;  // bytes of one B slice per stage
+  const int stage_tx = kOperandBytesA + kSlices * sliceB;
+  const int nkb = args.nkb;
+  const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kEpiWarps);
+    tc::mbar_init(drain, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const int inst = args.amap[j];
+      int issued = 0;
+      for (int k = 0; k < nkb; ++k) {
+        const int st = k % kStages;
+        const uint32_t use = k / kStages;
+        if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
+        unsigned char* sa = smem + st * kStageBytes;
+        tc::mbar_expect_tx(&full[st], stage_tx);
+        tc::tma_load_4d(sa, &tmapA, &full[st], k * kKB, row0, 0, inst);
+        tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], k * kKB, 0, 0, j);
+        issued = k + 1;
+      }
+      for (int k = max(0, issued - kStages); k < issued; ++k)
+        tc::mbar_wait(&full[k % kStages], (k / kStages) & 1, args.err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, Np);
+      bool ok = true;
+      int k = 0;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        if (ch > 0 && !tc::mbar_wait(acc_empty, (ch - 1) & 1, args.err)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int kend = min(nkb, (ch + 1) * kChunkBlocks);
+        uint32_t first_mask = (1u << kAcc) - 1;
+        for (; k < kend; ++k) {
+          const int st = k % kStages;
+          if (!tc::mbar_wait(&full[st], (k / kStages) & 1, args.err)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          unsigned char* sa = smem + st * kStageBytes;
+          unsigned char* sb = sa + kOperandBytesA;
+          const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
+          const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
+#pragma unroll 1
+          for (int pidx = 0; pidx < kPairs; ++pidx) {
+            const int s = kPairS[pidx], t = kPairT[pidx];
+            const int acc = (s + t < 4) ? s + t : 4;
+            const uint32_t dt = tmem + acc * Np;
+            const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
+            first_mask &= ~(1u << acc);
+            const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
+            const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
+            tc::mma_bf16(dt, da, db, idesc, accum);
+            tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+          }
+          tc::mma_commit(&empty[st]);
+        }
+        if (ok) tc::mma_commit(acc_full);
+      }
+      tc::mma_commit(drain);
+      tc::mbar_wait(drain, 0, args.err);
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> int64 -> FP64 ----------------
+    const int q = warp & 3;           // TMEM lane quadrant
+    const int grp = (warp - 2) >> 2;  // column group
+    const int cpg = Np / 4;           // 8, 16 or 24 columns
+    const int row = q * 32 + lane;
+    long long V[kMaxEpiCols];
+#pragma unroll
+    for (int c = 0; c < kMaxEpiCols; ++c) V[c] = 0;
+    bool ok = true;
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + grp * cpg;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!tc::mbar_wait(acc_full, ch & 1, args.err)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int hh = 0; hh < kMaxEpiCols / 8; ++hh) {
+        if (hh * 8 < cpg) {
+          uint32_t r[8];
+          tc::tmem_ld8(base + hh * 8, r);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 16384.0f) * (1LL << 30);
+          tc::tmem_ld8(base + Np + hh * 8, r);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 4194304.0f) * (1LL << 22);
+          tc::tmem_ld8(base + 2 * Np + hh * 8, r);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 1073741824.0f) * (1LL << 14);
+          tc::tmem_ld8(base + 3 * Np + hh * 8, r);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 274877906944.0f) * (1LL << 6);
+          tc::tmem_ld8(base + 4 * Np + hh * 8, r);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 17592186044416.0f);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty);
+    }
+    const int grow = row0 + row;
+    if (ok && grow < args.M) {
+      const int inst = args.amap[j];
+      const int e = args.rowexp[(size_t)inst * args.h1 + grow / args.h2];
+      const int* fexp = args.colexp + (size_t)j * Np;
+      double* out = args.T1 + ((size_t)j * args.M + grow) * args.R;
+#pragma unroll
+      for (int c = 0; c < kMaxEpiCols; ++c) {
+        const int col = grp * cpg + c;
+        if (c < cpg && col < args.R) {
+          const int f = fexp[col];
+          out[col] = (e > -1000 && f > -1000) ? ldexp((double)V[c], e + f - 44) : 0.0;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+CUtensorMap map4d(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* base, cuuint64_t d0, cuuint64_t d1,
+                  cuuint64_t d2, cuuint64_t d3, cuuint64_t s1, cuuint64_t s2, cuuint64_t s3, cuuint32_t b1) {
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  cuuint64_t dims[4] = {d0, d1, d2, d3};
+  cuuint64_t strides[3] = {s1, s2, s3};
+  cuuint32_t box[4] = {kKB, b1, (cuuint32_t)kSlices, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(TK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return map;
+}
+
+int padded_cols(int R) { return (R + 31) / 32 * 32; }
+
+}  // namespace
+
+size_t ttm_sliced_scratch_bytes(int h3, int R, int Bg) {
+  const int Np = padded_cols(R);
+  return carve_bytes<int>((size_t)Bg * Np) + carve_bytes<__nv_bfloat16>((size_t)Bg * kSlices * Np * h3) + 4096;
+}
+
+void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int Bg, int Btot, const double* Up, int R,
+                      double* T1, void* scratch, int* err, cudaStream_t s) {
+  const int h1 = h[0], h2 = h[1], h3 = h[2];
+  const int Np = padded_cols(R);
+  if (Np > kMaxNp || h3 % 8 != 0 || sv.Kp != (long long)h2 * h3 || sv.nrows != h1)
+    fail(TK_EINVAL, "sliced TTM: unsupported shape");
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  int* colexp = (int*)base;
+  __nv_bfloat16* BS = (__nv_bfloat16*)(base + carve_bytes<int>((size_t)Bg * Np));
+  k_bslice<<<dim3(Np, Bg), 128, 0, s>>>(Up, h3, R, Np, colexp, BS);
+  TK_LAUNCH("k_bslice");
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encode_fn();
+  if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t M = (cuuint64_t)h1 * h2;
+  // A: the Gram's slices [b][s][i][h2 h3] viewed as [b][s][(i, k)][l]
+  const CUtensorMap mapA = map4d(enc, sv.S, h3, M, kSlices, Btot, (cuuint64_t)h3 * 2, M * h3 * 2,
+                                 M * h3 * 2 * kSlices, kTM);
+  // B: [j][s][c][l]
+  const CUtensorMap mapB = map4d(enc, BS, h3, Np, kSlices, Bg, (cuuint64_t)h3 * 2, (cuuint64_t)Np * h3 * 2,
+                                 (cuuint64_t)Np * h3 * 2 * kSlices, Np);
+  once_per_device((const void*)&k_ttm_tc, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_ttm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  });
+  TtmArgs a{(int)M, h1, h2, h3, R, Np, (h3 + kKB - 1) / kKB, amap, sv.rowexp, colexp, T1, err};
+  k_ttm_tc<<<dim3((unsigned)((M + kTM - 1) / kTM), 1, Bg), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
+  TK_LAUNCH("k_ttm_tc");
+}
+
+}  // namespace tk
