@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, 
 // when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself,
 // or when both diagonal entries are below 64 u |A|_F (a plane inside the
 // rounding-noise block, whose vectors the matrix does not determine; its
-// trace is kept).  Sweeps stop when no rotation is applied.
+// trace is kept).  Before each sweep one pass over the upper triangle checks
+// whether any plane still needs a rotation; sweeps stop when none does (or
+// when a sweep applied none).
 // Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
 // ---------------------------------------------------------------------------
 struct JacProb {
@@ -304,6 +306,16 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   const double noise_diag = 0x1p-47 * normA;  // 64 u |A|_F
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
+    // a sweep runs only while some plane still needs a rotation (one pass over
+    // the upper triangle instead of a sweep that rotates nothing)
+    int need = 0;
+    for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
+      const int i = e / mp, j = e - (e / mp) * mp;
+      if (i < j && fabs(A[e]) > tau &&
+          !(fabs(A[i * mp + i]) <= noise_diag && fabs(A[j * mp + j]) <= noise_diag))
+        need = 1;
+    }
+    if (!__syncthreads_or(need)) break;
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int st = 0; st < mp - 1; ++st) {

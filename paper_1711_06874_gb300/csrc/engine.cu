@@ -96,6 +96,7 @@ BucketKey bucket_key(const SolveReq& r) {
 namespace {
 
 constexpr int kPhaseA = 16;  // eigenpairs of the first pass (enough for ranks <= 16)
+constexpr int kPhaseB = 40;  // second pass, for the instances that need more
 
 int roundup(int x, int q) { return (x + q - 1) / q * q; }
 
@@ -249,7 +250,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   for (int a = 0; a < nmodes; ++a)
     need += carve_bytes<double>((size_t)B * h[a] * h[a]) + carve_bytes<double>((size_t)B * mA[a]) +
             carve_bytes<double>((size_t)B * h[a] * mA[a]) + carve_bytes<double>(B) +
-            carve_bytes<double>((size_t)B * m[a]) + carve_bytes<double>((size_t)B * h[a] * m[a]);
+            2 * (carve_bytes<double>((size_t)B * m[a]) + carve_bytes<double>((size_t)B * h[a] * m[a]));
   pre.reserve(need + 4096, s);
   KernelDev* kd = pre.take<KernelDev>(B);
   double* table = pre.take<double>(std::max<long long>(1, Q * B));
@@ -263,14 +264,17 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   double* escr = pre.take<double>(eig_doubles);
   double* GJ = pre.take<double>((size_t)B * hmax * hmax);
   double* traceB = pre.take<double>(B);
-  double *G[3] = {}, *lamA[3] = {}, *VA[3] = {}, *traceA[3] = {}, *lamB[3] = {}, *VB[3] = {};
+  double *G[3] = {}, *lamA[3] = {}, *VA[3] = {}, *traceA[3] = {};
+  double *lamE[3][2] = {}, *VE[3][2] = {};  // escalation levels (mB, m)
   for (int a = 0; a < nmodes; ++a) {
     G[a] = pre.take<double>((size_t)B * h[a] * h[a]);
     lamA[a] = pre.take<double>((size_t)B * mA[a]);
     VA[a] = pre.take<double>((size_t)B * h[a] * mA[a]);
     traceA[a] = pre.take<double>(B);
-    lamB[a] = pre.take<double>((size_t)B * m[a]);
-    VB[a] = pre.take<double>((size_t)B * h[a] * m[a]);
+    for (int l = 0; l < 2; ++l) {
+      lamE[a][l] = pre.take<double>((size_t)B * m[a]);
+      VE[a][l] = pre.take<double>((size_t)B * h[a] * m[a]);
+    }
   }
   int* errflag = ints;
   int* rmaxv = ints + 16;           // [a][b]
@@ -317,7 +321,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   }
   std::vector<int> hA(12 * B + 1);
   std::vector<double> hnorm(B);
-  std::vector<std::vector<double>> hlamA(nmodes), hlamB(nmodes);
+  std::vector<std::vector<double>> hlamA(nmodes);
   TK_CUDA(cudaMemcpyAsync(hA.data(), outA, sizeof(int) * 4 * B * nmodes, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&hA[12 * B], errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(hnorm.data(), normF2, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
@@ -328,32 +332,47 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   TK_CUDA(cudaStreamSynchronize(s));
   if (hA[12 * B] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
 
-  // ---------------- escalation: all m pairs where the rank needs them ----------------
-  std::vector<std::vector<int>> J(nmodes);
-  std::vector<int> slotJ((size_t)B * 3, -1);  // position of instance b in mode a's escalated batch
-  bool any = false;
+  // ---------------- escalation ----------------
+  // Instances whose rank rule wants more pairs than a phase computed are
+  // gathered and solved again with more: min(m, 40), then m.
+  struct Phase {
+    int mp;
+    const double* lam;
+    const double* V;
+    std::vector<int> J;      // instances of this phase (bucket indices)
+    std::vector<int> out;    // [j][4] rank rule results
+    std::vector<double> hl;  // [j][mp] eigenvalues
+  };
+  std::vector<std::vector<Phase>> ph(nmodes);
   for (int a = 0; a < nmodes; ++a) {
-    if (mA[a] >= m[a]) continue;
-    for (int b = 0; b < B; ++b) {
-      const int rf = req[b].o.rfix[a];
-      const int needed = rf > 0 ? std::min(rf, m[a]) : hA[4 * B * a + 4 * b + 2];
-      if (needed > mA[a]) {
-        slotJ[(size_t)a * B + b] = (int)J[a].size();
-        J[a].push_back(b);
+    Phase p0;
+    p0.mp = mA[a];
+    p0.lam = lamA[a];
+    p0.V = VA[a];
+    p0.J.resize(B);
+    for (int b = 0; b < B; ++b) p0.J[b] = b;
+    p0.out.assign(hA.begin() + 4 * B * a, hA.begin() + 4 * B * (a + 1));
+    p0.hl = hlamA[a];
+    ph[a].push_back(std::move(p0));
+    const int levels[2] = {std::min(m[a], kPhaseB), m[a]};
+    for (int l = 0; l < 2; ++l) {
+      const Phase& prev = ph[a].back();
+      const int mp = levels[l];
+      if (mp <= prev.mp) continue;
+      std::vector<int> J;
+      for (size_t j = 0; j < prev.J.size(); ++j) {
+        const int b = prev.J[j];
+        const int rf = req[b].o.rfix[a];
+        const int needed = rf > 0 ? std::min(rf, m[a]) : prev.out[4 * j + 2];
+        if (needed > prev.mp) J.push_back(b);
       }
-    }
-    any = any || !J[a].empty();
-  }
-  std::vector<int> hB(12 * B, 0);
-  if (any) {
-    for (int a = 0; a < nmodes; ++a) {
-      const int nj = (int)J[a].size();
-      if (nj == 0) continue;
+      if (J.empty()) break;
+      const int nj = (int)J.size();
       // gathered parameters: idx, rmax, rfix (ints); |F|^2, eps (doubles)
       std::vector<int> ij(3 * nj);
       std::vector<double> dj(2 * nj);
       for (int j = 0; j < nj; ++j) {
-        const int b = J[a][j];
+        const int b = J[j];
         ij[j] = b;
         ij[nj + j] = req[b].o.rmax[a];
         ij[2 * nj + j] = req[b].o.rfix[a];
@@ -361,29 +380,41 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
         dj[nj + j] = req[b].o.eps;
       }
       int* ijd = stage;
-      double* njd = aux;
       TK_CUDA(cudaMemcpyAsync(ijd, ij.data(), sizeof(int) * 3 * nj, cudaMemcpyHostToDevice, s));
-      TK_CUDA(cudaMemcpyAsync(njd, dj.data(), sizeof(double) * nj, cudaMemcpyHostToDevice, s));
+      TK_CUDA(cudaMemcpyAsync(aux, dj.data(), sizeof(double) * nj, cudaMemcpyHostToDevice, s));
       TK_CUDA(cudaMemcpyAsync(epsv, dj.data() + nj, sizeof(double) * nj, cudaMemcpyHostToDevice, s));
       const long long per = (long long)h[a] * h[a];
       k_gather_mats<<<(unsigned)std::min<long long>((per * nj + 255) / 256, 4096), 256, 0, s>>>(G[a], ijd, nj, per,
                                                                                                GJ);
       TK_LAUNCH("k_gather_mats");
       if (pf) pf->begin(TK_STAGE_EIG, s);
-      sym_eig_batch(GJ, h[a], m[a], nj, lamB[a], VB[a], traceB, escr, s);
+      sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s);
       if (pf) pf->end(s);
       if (pf) pf->begin(TK_STAGE_RANK, s);
-      rank_rule_batch(lamB[a], m[a], traceB, njd, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj,
-                      outB + 4 * B * a, s);
+      rank_rule_batch(lamE[a][l], mp, traceB, aux, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj, outB, s);
       if (pf) pf->end(s);
-      // the next mode's staging reuses these buffers: wait for this mode's use
-      TK_CUDA(cudaMemcpyAsync(hB.data() + 4 * B * a, outB + 4 * B * a, sizeof(int) * 4 * nj, cudaMemcpyDeviceToHost,
-                              s));
-      hlamB[a].resize((size_t)nj * m[a]);
-      TK_CUDA(cudaMemcpyAsync(hlamB[a].data(), lamB[a], sizeof(double) * nj * m[a], cudaMemcpyDeviceToHost, s));
+      Phase p;
+      p.mp = mp;
+      p.lam = lamE[a][l];
+      p.V = VE[a][l];
+      p.J = J;
+      p.out.resize(4 * nj);
+      p.hl.resize((size_t)nj * mp);
+      // the staging buffers are reused by the next phase: wait for this one
+      TK_CUDA(cudaMemcpyAsync(p.out.data(), outB, sizeof(int) * 4 * nj, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaMemcpyAsync(p.hl.data(), lamE[a][l], sizeof(double) * nj * mp, cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaStreamSynchronize(s));
+      ph[a].push_back(std::move(p));
     }
   }
+  // the last phase that solved instance b for mode a, and b's position in it
+  std::vector<int> lastPh((size_t)B * 3, 0), lastPos((size_t)B * 3, 0);
+  for (int a = 0; a < nmodes; ++a)
+    for (size_t q = 0; q < ph[a].size(); ++q)
+      for (size_t j = 0; j < ph[a][q].J.size(); ++j) {
+        lastPh[(size_t)a * B + ph[a][q].J[j]] = (int)q;
+        lastPos[(size_t)a * B + ph[a][q].J[j]] = (int)j;
+      }
 
   // ---------------- results ----------------
   struct Final {
@@ -398,12 +429,12 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
     Final& f = fin[b];
     int rmx = 1;
     for (int a = 0; a < nmodes; ++a) {
-      const int j = slotJ[(size_t)a * B + b];
-      const int* o = (j >= 0) ? &hB[4 * B * a + 4 * j] : &hA[4 * B * a + 4 * b];
-      f.r[a] = o[0];
-      f.flags[a] = (unsigned)o[1];
-      f.V[a] = (j >= 0) ? VB[a] + (size_t)j * h[a] * m[a] : VA[a] + (size_t)b * h[a] * mA[a];
-      f.ldv[a] = (j >= 0) ? m[a] : mA[a];
+      const Phase& p = ph[a][lastPh[(size_t)a * B + b]];
+      const int j = lastPos[(size_t)a * B + b];
+      f.r[a] = p.out[4 * j];
+      f.flags[a] = (unsigned)p.out[4 * j + 1];
+      f.V[a] = p.V + (size_t)j * h[a] * p.mp;
+      f.ldv[a] = p.mp;
       rmx = std::max(rmx, f.r[a]);
     }
     for (int a = nmodes; a < 3; ++a) {
@@ -573,14 +604,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
       res->flags[a] = fin[b].flags[src];
       res->U[a] = rbase + offU[(size_t)b * 3 + src];
       res->Uh[a] = rbase + offUh[(size_t)b * 3 + src];
-      const int j = slotJ[(size_t)src * B + b];
-      if (j >= 0) {
-        res->m[a] = m[src];
-        res->lam[a].assign(hlamB[src].begin() + (size_t)j * m[src], hlamB[src].begin() + (size_t)(j + 1) * m[src]);
-      } else {
-        res->m[a] = mA[src];
-        res->lam[a].assign(hlamA[src].begin() + (size_t)b * mA[src], hlamA[src].begin() + (size_t)(b + 1) * mA[src]);
-      }
+      const Phase& p = ph[src][lastPh[(size_t)src * B + b]];
+      const int j = lastPos[(size_t)src * B + b];
+      res->m[a] = p.mp;
+      res->lam[a].assign(p.hl.begin() + (size_t)j * p.mp, p.hl.begin() + (size_t)(j + 1) * p.mp);
     }
     res->core = rbase + offC[b];
     outs[b] = res;
