@@ -95,7 +95,7 @@ BucketKey bucket_key(const SolveReq& r) {
 
 namespace {
 
-constexpr int kPhaseA = 16;  // eigenpairs of the first pass (enough for ranks <= 16)
+constexpr int kPhaseA = 12;  // eigenpairs of the first pass (enough for ranks <= 12)
 constexpr int kPhaseB = 40;  // second pass, for the instances that need more
 
 int roundup(int x, int q) { return (x + q - 1) / q * q; }

@@ -537,7 +537,11 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   const dim3 g = dispatch<false>(d, ErrRef{}, nullptr, s, false);
   const long long ctas = (long long)g.x * g.y * g.z;
   const long long outs = (long long)d.M * d.N * d.batch;
-  if (!d.fixed_order && ctas < 76 && outs <= (1LL << 18)) {
+  // one warp per output when the outputs are few: for fixed-order products the
+  // choice depends on the per-entry shape alone (never on the batch)
+  const bool warp = d.fixed_order ? ((long long)d.M * d.N <= 4096 && d.K >= 32)
+                                  : (ctas < 76 && outs <= (1LL << 18));
+  if (warp) {
     // few tiles: one warp per output keeps every SM busy
     const long long warps = outs;
     const unsigned blocks = (unsigned)std::min<long long>((warps + 7) / 8, 4096);
