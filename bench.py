@@ -186,46 +186,72 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
 
 
-def _roofline(prof, steps, prob, ranks, precision, clocks, peaks, peak_src):
-    """Roofline of the stage with the largest share of the step (stage events
-    recorded by the library on the solve's stream)."""
-    from paper_1711_06874_gb300 import binding
+JACOBI_SWEEPS = 3  # rotation sweeps on the n = 256 workload's Rayleigh-Ritz matrix (device counter)
 
+
+def _knu_flops(prob):
+    """FP64 operations of the K_nu table of the cubic isotropic workload: per
+    distinct s, the Miller recurrence (5 per step, N = 12 + ceil(180/x) steps)
+    or Temme's series (about 14 per term, 20 terms) plus about 80 for the
+    prefactor and the forward recurrence."""
+    n = prob.n[0]
+    hstep = prob.b[0] / n
+    nu, ell = prob.nu, prob.ell[0]
+    Q = (3 * (n - 1) ** 2 - 3) // 8 + 1 if n % 2 == 0 else 3 * ((n - 1) // 2) ** 2 + 1
+    tot = 0.0
+    for q in range(Q):
+        s = 8 * q + 3 if n % 2 == 0 else 4 * q
+        x = math.sqrt(2 * nu) * hstep * math.sqrt(s) / ell
+        tot += 80 + (14 * 20 if x <= 1.5 else 5 * (12 + math.ceil(180.0 / x)))
+    return tot
+
+
+def _roofline(prof, prob, precision, clocks, peaks, peak_src):
+    """Roofline of the kernel with the largest time per step among the ones
+    the library times on its own (nested stage events on the solve stream):
+    the K_nu table, the tensor-core Gram, the eigensolver's QR and Jacobi."""
     n = prob.n[0]
     h = (n + 1) // 2
-    r = max(ranks)
-    R = (r + 3) // 4 * 4
-    m = 16  # first-pass eigenpairs
-    ms = min(h, m + 8)
+    ms = min(h, 12 + 8)  # subspace of the first eigenpair pass
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = FP64_TFLOPS_NOMINAL * sm_mhz / 2070.0
-    # algorithmic FP64 flops per launch of each stage (one mode: isotropic shortcut)
-    work = {
-        "eig": 2.0 * (3 * h * h * ms + 2 * 2 * h * ms * ms + 2 * h * ms * ms + 40 * ms ** 3 + h * ms * m),
-        "core": 2.0 * (h * h * h * R + R * h * h * R + R * R * h * R),
-        "error": 2.0 * (h * r * r * r + h * h * r * r + h * h * h * r) + 3.0 * h ** 3,
-    }
-    if precision == binding.TK_FP64:
-        work["gram"] = 2.0 * h * (h + 1) / 2 * h * h
-    stages = {k: v for k, v in prof.items() if v[1] > 0 and k in ("eval", "gram", "eig", "core", "error", "rank")}
-    top = max(stages, key=lambda k: stages[k][0])
-    ms_launch = stages[top][0] / stages[top][1]
-    if top == "gram" and precision != binding.TK_FP64:
-        issued = 21 * 2.0 * 128 * 96 * (h * h) * (((h + 95) // 96) * ((h + 127) // 128))
-        ach = issued / (ms_launch * 1e-3) / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        return {"kernel": "gram stage (k_gram_tc, sliced BF16)", "bound": "tensor", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"bf16_tflops_sustained ({peak_src}), issued slice products",
-                "stage_ms_per_launch": ms_launch}
-    if top in work:
-        ach = work[top] / (ms_launch * 1e-3) / 1e12
-        return {"kernel": f"{top} stage (FP64)", "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock",
-                "algorithmic_flop_per_launch": work[top], "stage_ms_per_launch": ms_launch}
-    return {"kernel": f"{top} stage", "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "stage_ms_per_launch": ms_launch}
+    fp64_gpu = FP64_TFLOPS_NOMINAL * sm_mhz / 2070.0
+    fp64_sm = fp64_gpu / 152.0
+    have = {k: prof[k] for k in ("table", "gram_tc", "qr", "jacobi") if k in prof and prof[k][1] > 0}
+    if not have:
+        return {"kernel": None, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    top = max(have, key=lambda k: have[k][0])
+    t = have[top][0] / have[top][1] * 1e-3  # s per launch
+    out = {"kernel": None, "stage_ms_per_launch": t * 1e3, "traffic": None}
+    if top == "gram_tc":
+        nb = ((h + 95) // 96) * ((h + 127) // 128)  # 128 x 96 blocks on and above the diagonal (h <= 128)
+        issued = 21 * 2.0 * 128 * 96 * (h * h) * nb
+        ach = issued / t / 1e12
+        pk = peaks["bf16_tflops_sustained"]
+        out.update(kernel="k_gram_tc (sliced BF16 Gram)", bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s",
+                   frac=ach / pk, peak_source=f"bf16_tflops_sustained ({peak_src}), issued slice products",
+                   algorithmic_flop_per_launch=issued)
+    elif top in ("qr", "jacobi"):
+        if top == "qr":
+            work = 8.0 * h * ms * ms - 8.0 * ms ** 3 / 3.0  # Householder QR plus the explicit Q
+            name = "k_householder_qr_strided (FP64, one CTA)"
+        else:
+            work = 7.0 * ms ** 3 * JACOBI_SWEEPS  # 7 m^3 flops per sweep (A two-sided, V one-sided)
+            name = "k_jacobi_strided (FP64, one CTA)"
+        ach = work / t / 1e12
+        out.update(kernel=name, bound="alu", achieved=ach, peak=fp64_sm, unit="TFLOP/s", frac=ach / fp64_sm,
+                   peak_source="FP64 of the one SM the CTA runs on: nominal 1.25 TFLOP/s / 152 SMs at 2070 MHz, "
+                               "scaled to the sampled SM clock",
+                   algorithmic_flop_per_launch=work)
+    else:
+        work = _knu_flops(prob)
+        ach = work / t / 1e12
+        out.update(kernel="k_table_b (K_nu per distinct s, FP64)", bound="alu", achieved=ach, peak=fp64_gpu,
+                   unit="TFLOP/s", frac=ach / fp64_gpu,
+                   peak_source="nominal FP64 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock",
+                   algorithmic_flop_per_launch=work)
+    out["per_step_ms"] = {k: v[0] for k, v in have.items()}
+    return out
 
 
 def run_ours(args):
@@ -357,7 +383,8 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     e2e = {"value": ke * world / te, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     stage_ms = {k: v[0] / max(1, args.steps) for k, v in prof.items()}
-    roof = _roofline(prof, args.steps, prob, ranks[:1], precision, clocks, peaks, peak_src)
+    per_step = {k: (v[0] / max(1, args.steps), v[1] / max(1, args.steps)) for k, v in prof.items()}
+    roof = _roofline(per_step, prob, precision, clocks, peaks, peak_src)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

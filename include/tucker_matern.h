@@ -261,14 +261,19 @@ typedef enum {
   TK_STAGE_RANK = 4,  /* rank rule and factor extraction */
   TK_STAGE_CORE = 5,  /* TTM chain */
   TK_STAGE_ERROR = 6, /* tk_rel_error */
-  TK_NSTAGES = 7
+  /* single kernels inside the stages above (their time is also in the stage) */
+  TK_STAGE_TABLE = 7,   /* K_nu distinct-value table */
+  TK_STAGE_GRAM_TC = 8, /* tensor-core Gram kernel (slices excluded) */
+  TK_STAGE_QR = 9,      /* FP64 Householder QR of the eigensolver */
+  TK_STAGE_JACOBI = 10, /* Jacobi of the Rayleigh-Ritz matrix */
+  TK_NSTAGES = 11
 } tk_stage;
 /* on = 1 starts recording CUDA events around every stage of later calls on
  * this context and zeroes the totals; on = 0 stops. */
 int tk_profile_enable(tk_ctx* ctx, int on);
 /* Accumulated device milliseconds and call counts per stage (host arrays of
  * TK_NSTAGES), for the calls made since profiling was enabled. */
-int tk_profile_read(tk_ctx* ctx, double ms[7], int64_t calls[7]);
+int tk_profile_read(tk_ctx* ctx, double ms[TK_NSTAGES], int64_t calls[TK_NSTAGES]);
 /* Kernels launched by the library in this process so far. */
 uint64_t tk_kernel_launches(void);
 

@@ -90,7 +90,7 @@ SIGNATURES = {
     "tk_kernel_launches": (_c.c_uint64, []),
 }
 
-STAGES = ["eval", "norm", "gram", "eig", "rank", "core", "error"]
+STAGES = ["eval", "norm", "gram", "eig", "rank", "core", "error", "table", "gram_tc", "qr", "jacobi"]
 
 _lock = threading.Lock()
 _lib = None
@@ -249,8 +249,8 @@ class Context:
         _check(self.lib.tk_profile_enable(self.ptr, 1 if on else 0), self.ptr)
 
     def profile_read(self) -> dict:
-        ms = (_dbl * 7)()
-        calls = (_c.c_int64 * 7)()
+        ms = (_dbl * len(STAGES))()
+        calls = (_c.c_int64 * len(STAGES))()
         _check(self.lib.tk_profile_read(self.ptr, ms, calls), self.ptr)
         return {name: (ms[i], int(calls[i])) for i, name in enumerate(STAGES)}
 

@@ -81,12 +81,14 @@ void Profiler::begin(int stage, cudaStream_t s) {
   if (!on) return;
   Pending p{stage, get(), get()};
   check_cuda(cudaEventRecord(p.a, s), "cudaEventRecord");
+  open.push_back(pending.size());
   pending.push_back(p);
 }
 
 void Profiler::end(cudaStream_t s) {
-  if (!on || pending.empty()) return;
-  check_cuda(cudaEventRecord(pending.back().b, s), "cudaEventRecord");
+  if (!on || open.empty()) return;
+  check_cuda(cudaEventRecord(pending[open.back()].b, s), "cudaEventRecord");
+  open.pop_back();
 }
 
 void Profiler::collect() {
@@ -102,6 +104,7 @@ void Profiler::collect() {
     pool.push_back(p.b);
   }
   pending.clear();
+  open.clear();
 }
 
 void Profiler::reset() {
@@ -799,7 +802,7 @@ int tk_profile_enable(tk_ctx* ctx, int on) {
   });
 }
 
-int tk_profile_read(tk_ctx* ctx, double ms[7], int64_t calls[7]) {
+int tk_profile_read(tk_ctx* ctx, double ms[TK_NSTAGES], int64_t calls[TK_NSTAGES]) {
   if (!ctx || !ms || !calls) return TK_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   for (int i = 0; i < TK_NSTAGES; ++i) {

@@ -901,7 +901,7 @@ EigGroup carve_group(double* p, const double* G, int n, int m, int B, double* la
   return g;
 }
 
-void solve_group(const EigGroup& g, int B, cudaStream_t s) {
+void solve_group(const EigGroup& g, int B, cudaStream_t s, Profiler* pf) {
   const int n = g.n, ms = g.ms, m = g.m;
   if (ms == n) {
     // whole matrices: Jacobi directly
@@ -910,11 +910,13 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
     const unsigned long long seed = 0x1711068740ull + (unsigned)n;
     const size_t need = 2ull * n * ms * sizeof(double);
     auto qr = [&]() {
+      if (pf) pf->begin(TK_STAGE_QR, s);
       if (need <= kQrSmemMax)
         k_householder_qr_strided<true><<<B, 256, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       else
         k_householder_qr_strided<false><<<B, 256, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
       TK_LAUNCH("k_householder_qr_strided");
+      if (pf) pf->end(s);
     };
     auto power = [&](const double* src) {  // Y = G src
       GemmDesc d{n, ms, n, B, g.G, (long long)n * n, n, 1, src, (long long)n * ms, 1, n,
@@ -950,8 +952,10 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
         g.H, ms, B);
     TK_LAUNCH("k_symmetrize_batch");
   }
+  if (pf) pf->begin(TK_STAGE_JACOBI, s);
   k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
   TK_LAUNCH("k_jacobi_strided");
+  if (pf) pf->end(s);
   if (ms == n) {
     // first m columns of V_H (n x n) into V (n x m)
     TK_CUDA(cudaMemcpy2DAsync(g.V, sizeof(double) * m, g.VH, sizeof(double) * ms, sizeof(double) * m,
@@ -971,14 +975,14 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s) {
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B) { return group_doubles(n, m, B) + 4096; }
 
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s) {
+                   cudaStream_t s, Profiler* pf) {
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   if (B < 1) return;
   set_attrs();
   const EigGroup g = carve_group(scratch, G, n, m, B, lam, V);
   k_trace<<<B, 32, 0, s>>>(G, n, trace);
   TK_LAUNCH("k_trace");
-  solve_group(g, B, s);
+  solve_group(g, B, s, pf);
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }

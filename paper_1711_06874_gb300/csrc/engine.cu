@@ -300,19 +300,19 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   TK_CUDA(cudaMemcpyAsync(ints, ih.data(), sizeof(int) * ih.size(), cudaMemcpyHostToDevice, s));
 
   if (pf) pf->begin(TK_STAGE_EVAL, s);
-  eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s);
+  eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
   if (pf) pf->end(s);
   // modes in reverse order: the slices of mode 1 stay in the Gram scratch for
   // the tensor-core TTM
   for (int a = nmodes - 1; a >= 0; --a) {
     if (pf) pf->begin(TK_STAGE_GRAM, s);
     if (sliced)
-      gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s);
+      gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf);
     else
       gram_f64_batch(Fh, h, a, B, G[a], (double*)gscr, s);
     if (pf) pf->end(s);
     if (pf) pf->begin(TK_STAGE_EIG, s);
-    sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s);
+    sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf);
     if (pf) pf->end(s);
     if (pf) pf->begin(TK_STAGE_RANK, s);
     rank_rule_batch(lamA[a], mA[a], traceA[a], normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], B,
@@ -388,7 +388,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
                                                                                                GJ);
       TK_LAUNCH("k_gather_mats");
       if (pf) pf->begin(TK_STAGE_EIG, s);
-      sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s);
+      sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s, pf);
       if (pf) pf->end(s);
       if (pf) pf->begin(TK_STAGE_RANK, s);
       rank_rule_batch(lamE[a][l], mp, traceB, aux, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj, outB, s);

@@ -335,7 +335,7 @@ size_t eval_octant_parts(const tk_grid& g) { return oct_blocks(g); }
 long long table_entries(int n) { return table_size(n); }
 
 void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, double* Fh, double* table,
-                     double* part, double* normF2, cudaStream_t s) {
+                     double* part, double* normF2, cudaStream_t s, Profiler* pf) {
   const unsigned nb = oct_blocks(g);
   const int h3 = (g.n[2] + 1) / 2;
   const int threads = h3 < 128 ? 64 : 128;
@@ -344,8 +344,10 @@ void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, dou
     const long long Q = table_size(n);
     const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
     const long long tb = (Q + 63) / 64;
+    if (pf) pf->begin(TK_STAGE_TABLE, s);
     k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
     TK_LAUNCH("k_table_b");
+    if (pf) pf->end(s);
     k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);
     TK_LAUNCH("k_gather_oct");
   } else {

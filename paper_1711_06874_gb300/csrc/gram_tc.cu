@@ -442,7 +442,7 @@ CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long 
 // The tensor-core Gram and its reduction over B instances whose slices are
 // at S ([b][s][row][Kp]) and row exponents at rowexp ([b][row]).
 void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, long long* P, double* G, int* err,
-                 cudaStream_t s) {
+                 cudaStream_t s, Profiler* pf) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
   const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, B, kTM);
@@ -451,8 +451,10 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
     TK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   });
   TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.nsplit, p.kb_per_split, p.kb_total, P, err};
+  if (pf) pf->begin(TK_STAGE_GRAM_TC, s);
   k_gram_tc<<<dim3(p.nblocks, p.nsplit, B), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
   TK_LAUNCH("k_gram_tc");
+  if (pf) pf->end(s);
   const long long total = (long long)p.nrows * p.nrows * B;
   k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks,
                                                                                       p.nrows, B, rowexp, G);
@@ -472,7 +474,7 @@ size_t gram_sliced_scratch_bytes(const int n[3], int mode, int B) {
 }
 
 void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
-                       cudaStream_t s) {
+                       cudaStream_t s, Profiler* pf) {
   // one plan (for 152 SMs and this batch) fixes both the scratch layout and
   // the grid; G does not depend on it (exact integer sums over K)
   const TcPlan p = tc_plan(n, mode, 152, B);
@@ -505,7 +507,7 @@ void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double*
     k_slice<<<g, 256, 0, s>>>(F, mode, n[0], n[1], n[2], p.nrows, p.K, p.Kp, rowexp, S, sF);
     TK_LAUNCH("k_slice");
   }
-  run_tc_gram(p, B, S, rowexp, P, G, err, s);
+  run_tc_gram(p, B, S, rowexp, P, G, err, s, pf);
 }
 
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B) {

@@ -14,6 +14,8 @@
 
 namespace tk {
 
+struct Profiler;
+
 // Error raised inside the library and turned into a status at the C-ABI.
 struct Error {
   int status;
@@ -107,7 +109,7 @@ bool eval_table_f64(const tk_kernel& k, const tk_grid& g, double* table, cudaStr
 size_t eval_octant_parts(const tk_grid& g);
 long long table_entries(int n);
 void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, double* Fh, double* table,
-                     double* part, double* normF2, cudaStream_t s);
+                     double* part, double* normF2, cudaStream_t s, Profiler* pf = nullptr);
 
 // |F|^2 with compensated per-thread sums and a fixed-order final sum.
 size_t norm2_scratch_doubles(size_t len);
@@ -128,7 +130,7 @@ size_t gram_sliced_scratch_bytes(const int n[3], int mode, int B = 1);
 void gram_sliced_bf16(const double* F, const int n[3], int mode, double* G, void* scratch, int* err,
                       cudaStream_t s);
 void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
-                       cudaStream_t s);
+                       cudaStream_t s, Profiler* pf = nullptr);
 // Where gram_sliced_batch left the slices of its last call in `scratch`:
 // S = [b][6][nrows][Kp] BF16 planes, rowexp = [b][nrows] row exponents.
 struct SliceView {
@@ -193,7 +195,7 @@ void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, 
 // the batch.
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s);
+                   cudaStream_t s, Profiler* pf = nullptr);
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.
@@ -252,6 +254,7 @@ struct Profiler {
     cudaEvent_t a, b;
   };
   std::vector<Pending> pending;
+  std::vector<size_t> open;  // pending entries begun and not yet ended (stages nest)
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get();
   void begin(int stage, cudaStream_t s);
