@@ -138,9 +138,16 @@ def make_grid(prob: workloads.Problem) -> Grid:
     return Grid((_i32 * 3)(*prob.n), (_dbl * 3)(*prob.b), prob.grid)
 
 
+_DEFAULT_OPTS = None
+
+
 def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True, fold=True) -> Opts:
-    o = Opts()
-    load().tk_default_opts(_c.byref(o))
+    global _DEFAULT_OPTS
+    if _DEFAULT_OPTS is None:
+        d = Opts()
+        load().tk_default_opts(_c.byref(d))
+        _DEFAULT_OPTS = d
+    o = Opts.from_buffer_copy(_DEFAULT_OPTS)
     o.eps = prob.eps
     o.rmax = (_i32 * 3)(*prob.rmax)
     o.rfix = (_i32 * 3)(*rfix)
@@ -198,7 +205,7 @@ class Context:
         out = _vp()
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
-        return Result(self, out, prob)
+        return Result(self, out, prob, k, g)
 
     def batch(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, stream=None) -> list:
         """Independent solves in one call (tk_batch); one Result per problem.
@@ -286,6 +293,8 @@ class Result:
     ctx: Context
     ptr: _vp
     prob: workloads.Problem
+    kstruct: Kernel = None
+    gstruct: Grid = None
 
     def __del__(self):
         try:
@@ -334,7 +343,8 @@ class Result:
                self.ctx.ptr)
 
     def rel_error(self, stream=None) -> float:
-        k, g = make_kernel(self.prob), make_grid(self.prob)
+        k = self.kstruct if self.kstruct is not None else make_kernel(self.prob)
+        g = self.gstruct if self.gstruct is not None else make_grid(self.prob)
         v = _dbl(0)
         _check(self.ctx.lib.tk_rel_error(self.ctx.ptr, self.ptr, _c.byref(k), _c.byref(g), _c.byref(v),
                                          _stream_ptr(stream)), self.ctx.ptr)

@@ -478,7 +478,7 @@ tk_result* solve_one(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, 
   if (!fold_applicable(*grid, *opts)) return tucker_full(ctx, kernel, grid, opts, s);
   SolveReq rq{*kernel, *grid, *opts};
   tk_result* res = nullptr;
-  solve_bucket(ctx, ctx->ws, ctx->ws2, &ctx->prof, &rq, 1, &res, s);
+  solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, &ctx->prof, &rq, 1, &res, s);
   return res;
 }
 
@@ -543,7 +543,7 @@ int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* gr
           const int i = idx[c0 + j];
           rq[j] = SolveReq{kernels[i], grids[i], opts[i]};
         }
-        solve_bucket(ctx, ctx->ws, ctx->ws2, &ctx->prof, rq.data(), cnt, rs.data(), s);
+        solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, &ctx->prof, rq.data(), cnt, rs.data(), s);
         for (int j = 0; j < cnt; ++j) outs[idx[c0 + j]] = rs[j];
       }
     }
@@ -642,8 +642,7 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
       const bool tab = table_applicable(*kernel, *grid);
       const size_t Q = tab ? (size_t)table_entries(grid->n[0]) : 1;
       const size_t w1 = (size_t)h[0] * r[1] * r[2], w2 = (size_t)h[0] * h[1] * r[2];
-      GemmDesc d{h[0] * h[1], h[2], r[2], 1, nullptr, 0, r[2], 1, res->Uh[2], 0, 1, r[2], nullptr, 0, h[2], 1};
-      const size_t parts = gemm_err_partials(d);
+      const size_t parts = err_lowrank_partials(h[0] * h[1], h[2]);
       const size_t np = eval_octant_parts(*grid);
       ctx->ws.reserve(carve_bytes<KernelDev>(1) + carve_bytes<double>(H) + carve_bytes<double>(Q) +
                           carve_bytes<double>(w1) + carve_bytes<double>(w2) + carve_bytes<double>(parts) +
@@ -662,8 +661,8 @@ int tk_rel_error(tk_ctx* ctx, const tk_result* res, const tk_kernel* kernel, con
       ctx->prof.begin(TK_STAGE_ERROR, s);
       eval_octant_f64(kd, tab, *grid, 1, Fh, table, opart, sums + 4, s);
       recon_w2(res->core, r, res->Uh[0], r[0], res->Uh[1], r[1], h, W1, W2, s);
-      d.A = W2;
-      gemm_f64_err(d, Fh, nullptr, 0, part, sums, s);
+      // X = W2 Uh3^T (inner dimension r3), against Fh
+      err_lowrank_f64(W2, res->Uh[2], Fh, h[0] * h[1], h[2], r[2], part, sums, s);
       ctx->prof.end(s);
       double hs[2];
       TK_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));

@@ -47,6 +47,25 @@ static cudaStream_t free_stream(int device) {
   return s;
 }
 
+char* HostPinned::reserve(size_t need) {
+  if (need <= bytes) return p;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  bytes = 0;
+  const size_t want = std::max<size_t>(need, 64 << 10);
+  if (cudaMallocHost((void**)&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    fail(TK_ENOMEM, "cannot allocate pinned host staging");
+  }
+  bytes = want;
+  return p;
+}
+
+HostPinned::~HostPinned() {
+  if (p) cudaFreeHost(p);
+}
+
 DeviceBlock::~DeviceBlock() {
   if (ptr) {
     cudaSetDevice(device);
@@ -211,8 +230,8 @@ size_t bucket_bytes_per_instance(const BucketKey& k) {
   return b + 16384;
 }
 
-void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, const SolveReq* req, int B,
-                  tk_result** outs, cudaStream_t s) {
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, Profiler* pf,
+                  const SolveReq* req, int B, tk_result** outs, cudaStream_t s) {
   if (B < 1) return;
   const tk_grid& g = req[0].g;
   const BucketKey key = bucket_key(req[0]);
@@ -283,10 +302,32 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   int* outB = outA + 12 * B;        // [a][j][4]
   int* stage = outB + 12 * B;       // 3 B
 
-  // host-side parameters, one staged copy
-  std::vector<KernelDev> kdh(B);
-  std::vector<double> epsh(B);
-  std::vector<int> ih(16 + 6 * B, 0);
+  // pinned staging: parameters up; ranks, |F|^2 and eigenvalues down; then
+  // the descriptors of the second phase up
+  size_t lam_count = 0;
+  for (int a = 0; a < nmodes; ++a) lam_count += (size_t)B * mA[a];
+  const size_t pin_up = carve_bytes<KernelDev>(B) + carve_bytes<double>(B) + carve_bytes<int>(16 + 6 * B);
+  const size_t pin_down = carve_bytes<int>(12 * B + 1) + carve_bytes<double>(B) + carve_bytes<double>(lam_count);
+  const size_t pin_desc = carve_bytes<int>(B) + carve_bytes<UnfoldDesc>((size_t)B * nmodes) +
+                          carve_bytes<CoreDesc>(B) + carve_bytes<int>(1);
+  char* pbase = pin.reserve(pin_up + pin_down + pin_desc + 1024);
+  size_t poff = 0;
+  auto ptake = [&](size_t bytes) {
+    char* q = pbase + poff;
+    poff += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  KernelDev* kdh = (KernelDev*)ptake(sizeof(KernelDev) * B);
+  double* epsh = (double*)ptake(sizeof(double) * B);
+  int* ih = (int*)ptake(sizeof(int) * (16 + 6 * B));
+  int* hA = (int*)ptake(sizeof(int) * (12 * B + 1));
+  double* hnorm = (double*)ptake(sizeof(double) * B);
+  double* hlam = (double*)ptake(sizeof(double) * lam_count);
+  int* amaph = (int*)ptake(sizeof(int) * B);
+  UnfoldDesc* udh = (UnfoldDesc*)ptake(sizeof(UnfoldDesc) * B * nmodes);
+  CoreDesc* cdh = (CoreDesc*)ptake(sizeof(CoreDesc) * B);
+  int* herrp = (int*)ptake(sizeof(int));
+  std::memset(ih, 0, sizeof(int) * 16);
   for (int b = 0; b < B; ++b) {
     kdh[b] = make_kernel_dev(req[b].k);
     epsh[b] = req[b].o.eps;
@@ -295,9 +336,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
       ih[16 + 3 * B + a * B + b] = req[b].o.rfix[a];
     }
   }
-  TK_CUDA(cudaMemcpyAsync(kd, kdh.data(), sizeof(KernelDev) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(epsv, epsh.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(ints, ih.data(), sizeof(int) * ih.size(), cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(kd, kdh, sizeof(KernelDev) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(epsv, epsh, sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(ints, ih, sizeof(int) * (16 + 6 * B), cudaMemcpyHostToDevice, s));
 
   if (pf) pf->begin(TK_STAGE_EVAL, s);
   eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
@@ -319,17 +360,25 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
                     outA + 4 * B * a, s);
     if (pf) pf->end(s);
   }
-  std::vector<int> hA(12 * B + 1);
-  std::vector<double> hnorm(B);
   std::vector<std::vector<double>> hlamA(nmodes);
-  TK_CUDA(cudaMemcpyAsync(hA.data(), outA, sizeof(int) * 4 * B * nmodes, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(hA, outA, sizeof(int) * 4 * B * nmodes, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&hA[12 * B], errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaMemcpyAsync(hnorm.data(), normF2, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
-  for (int a = 0; a < nmodes; ++a) {
-    hlamA[a].resize((size_t)B * mA[a]);
-    TK_CUDA(cudaMemcpyAsync(hlamA[a].data(), lamA[a], sizeof(double) * B * mA[a], cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(hnorm, normF2, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  {
+    size_t off = 0;
+    for (int a = 0; a < nmodes; ++a) {
+      TK_CUDA(cudaMemcpyAsync(hlam + off, lamA[a], sizeof(double) * B * mA[a], cudaMemcpyDeviceToHost, s));
+      off += (size_t)B * mA[a];
+    }
   }
   TK_CUDA(cudaStreamSynchronize(s));
+  {
+    size_t off = 0;
+    for (int a = 0; a < nmodes; ++a) {
+      hlamA[a].assign(hlam + off, hlam + off + (size_t)B * mA[a]);
+      off += (size_t)B * mA[a];
+    }
+  }
   if (hA[12 * B] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
 
   // ---------------- escalation ----------------
@@ -351,7 +400,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
     p0.V = VA[a];
     p0.J.resize(B);
     for (int b = 0; b < B; ++b) p0.J[b] = b;
-    p0.out.assign(hA.begin() + 4 * B * a, hA.begin() + 4 * B * (a + 1));
+    p0.out.assign(hA + 4 * B * a, hA + 4 * B * (a + 1));
     p0.hl = hlamA[a];
     ph[a].push_back(std::move(p0));
     const int levels[2] = {std::min(m[a], kPhaseB), m[a]};
@@ -473,7 +522,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   std::map<int, std::vector<int>> groups;
   for (int b = 0; b < B; ++b) groups[fin[b].R].push_back(b);
   size_t ttm = 0;
-  std::vector<int> amaph;
+  std::vector<int> amapv;
   struct GroupBuf {
     int R, off, cnt;
     size_t up[3], t1, t2, cp;
@@ -483,11 +532,11 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   for (auto& kv : groups) {
     GroupBuf q{};
     q.R = kv.first;
-    q.off = (int)amaph.size();
+    q.off = (int)amapv.size();
     q.cnt = (int)kv.second.size();
     for (size_t j = 0; j < kv.second.size(); ++j) {
       posInGroup[kv.second[j]] = (int)j;
-      amaph.push_back(kv.second[j]);
+      amapv.push_back(kv.second[j]);
     }
     auto tput = [&](size_t cnt) {
       const size_t o = ttm;
@@ -518,8 +567,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   CoreDesc* cd = post.take<CoreDesc>(B);
   std::map<int, int> groupOf;
   for (size_t q = 0; q < gb.size(); ++q) groupOf[gb[q].R] = (int)q;
-  std::vector<UnfoldDesc> udh(ndesc);
-  std::vector<CoreDesc> cdh(B);
+  std::memcpy(amaph, amapv.data(), sizeof(int) * B);
   int Rmax = 4;
   for (int b = 0; b < B; ++b) {
     const GroupBuf& q = gb[groupOf[fin[b].R]];
@@ -540,9 +588,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
     cdh[b] = CoreDesc{tbase + q.cp + (size_t)pos * q.R * q.R * q.R, rbase + offC[b], q.R, fin[b].r[0], fin[b].r[1],
                       fin[b].r[2]};
   }
-  TK_CUDA(cudaMemcpyAsync(amap, amaph.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(ud, udh.data(), sizeof(UnfoldDesc) * ndesc, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(cd, cdh.data(), sizeof(CoreDesc) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(amap, amaph, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(ud, udh, sizeof(UnfoldDesc) * ndesc, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(cd, cdh, sizeof(CoreDesc) * B, cudaMemcpyHostToDevice, s));
   if (pf) pf->begin(TK_STAGE_RANK, s);
   k_unfold<<<dim3(Rmax, (unsigned)ndesc), 128, 0, s>>>(ud);
   TK_LAUNCH("k_unfold");
@@ -584,11 +632,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, co
   k_extract_core<<<dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), 256, 0, s>>>(cd);
   TK_LAUNCH("k_extract_core");
   if (pf) pf->end(s);
-  int herr = 0;
-  TK_CUDA(cudaMemcpyAsync(&herr, errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(herrp, errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   if (pf) pf->collect();
-  if (herr != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
+  if (*herrp != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
 
   for (int b = 0; b < B; ++b) {
     tk_result* res = new tk_result();

@@ -552,6 +552,96 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   dispatch<false>(d, ErrRef{}, nullptr, s, true);
 }
 
+// ---------------------------------------------------------------------------
+// Error of a rank-K product against a reference: sum (R - X)^2 and sum R^2
+// with X = W Ut^T (W: M x K, ld K; Ut: N x K, ld K; R: M x N row-major) for a
+// small K.  Each CTA takes 64 rows and 128 columns; W's rows and Ut's rows
+// (transposed) sit in shared memory; every thread forms 32 outputs as K-long
+// FMA chains and accumulates the two sums; the block partials go through the
+// same fixed-order final sum as the GEMM epilogue.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kErrRows = 64, kErrCols = 128;
+
+__global__ void __launch_bounds__(256) k_err_lowrank(const double* __restrict__ W, const double* __restrict__ Ut,
+                                                     const double* __restrict__ R, int M, int N, int K,
+                                                     double* __restrict__ partials) {
+  extern __shared__ double es[];
+  double* Ws = es;                   // [64][K]
+  double* Us = es + kErrRows * K;    // [K][128]
+  const int m0 = blockIdx.y * kErrRows, n0 = blockIdx.x * kErrCols;
+  for (int e = threadIdx.x; e < kErrRows * K; e += blockDim.x) {
+    const int i = e / K, k = e - i * K;
+    Ws[e] = (m0 + i < M) ? W[(long long)(m0 + i) * K + k] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kErrCols * K; e += blockDim.x) {
+    const int c = e / K, k = e - c * K;
+    Us[k * kErrCols + c] = (n0 + c < N) ? Ut[(long long)(n0 + c) * K + k] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x & (kErrCols - 1), r0 = threadIdx.x >> 7;  // 2 row phases
+  double ds = 0.0, fs = 0.0;
+  if (n0 + c < N) {
+    for (int i = r0; i < kErrRows && m0 + i < M; i += 2) {
+      const double* w = Ws + i * K;
+      double x = 0.0;
+      for (int k = 0; k < K; ++k) x = fma(w[k], Us[k * kErrCols + c], x);
+      const double r = R[(long long)(m0 + i) * N + n0 + c];
+      const double e = r - x;
+      ds = fma(e, e, ds);
+      fs = fma(r, r, fs);
+    }
+  }
+  // fixed-shape tree over the block, compensation carried along
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = ds;
+  red[1][threadIdx.x] = 0.0;
+  red[2][threadIdx.x] = fs;
+  red[3][threadIdx.x] = 0.0;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double s0 = red[0][threadIdx.x], c0 = red[1][threadIdx.x] + red[1][threadIdx.x + w];
+      neum(s0, c0, red[0][threadIdx.x + w]);
+      double s1 = red[2][threadIdx.x], c1 = red[3][threadIdx.x] + red[3][threadIdx.x + w];
+      neum(s1, c1, red[2][threadIdx.x + w]);
+      red[0][threadIdx.x] = s0;
+      red[1][threadIdx.x] = c0;
+      red[2][threadIdx.x] = s1;
+      red[3][threadIdx.x] = c1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long long blin = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    partials[4 * blin + 0] = red[0][0];
+    partials[4 * blin + 1] = red[1][0];
+    partials[4 * blin + 2] = red[2][0];
+    partials[4 * blin + 3] = red[3][0];
+  }
+}
+
+}  // namespace
+
+size_t err_lowrank_partials(int M, int N) {
+  return 4ull * ((N + kErrCols - 1) / kErrCols) * ((M + kErrRows - 1) / kErrRows);
+}
+
+void err_lowrank_f64(const double* W, const double* Ut, const double* R, int M, int N, int K, double* partials,
+                     double* out_dev, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)(kErrRows + kErrCols) * K;
+  if (K < 1 || smem > 200 * 1024) fail(TK_EINVAL, "err_lowrank: K out of range");
+  once_per_device((const void*)&k_err_lowrank, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_err_lowrank, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  const dim3 grid((N + kErrCols - 1) / kErrCols, (M + kErrRows - 1) / kErrRows);
+  k_err_lowrank<<<grid, 256, smem, s>>>(W, Ut, R, M, N, K, partials);
+  TK_LAUNCH("k_err_lowrank");
+  k_err_final<<<1, 1024, 0, s>>>(partials, (long long)grid.x * grid.y, out_dev);
+  TK_LAUNCH("k_err_final");
+}
+
 size_t gemm_err_partials(const GemmDesc& d) {
   const dim3 g = dispatch<true>(d, ErrRef{}, nullptr, nullptr, false);
   return 4ull * g.x * g.y * g.z;

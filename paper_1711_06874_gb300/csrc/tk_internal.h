@@ -51,6 +51,16 @@ struct Workspace {
   void release();
 };
 
+// Pinned host staging for the engine's small transfers (parameters,
+// descriptors, ranks), so that they are truly asynchronous; grows, never
+// shrinks.  Its owner must synchronise its stream before reusing it.
+struct HostPinned {
+  char* p = nullptr;
+  size_t bytes = 0;
+  char* reserve(size_t need);
+  ~HostPinned();
+};
+
 // Device memory shared by the results of one batched solve; freed with the
 // last of them.
 struct DeviceBlock {
@@ -180,6 +190,12 @@ size_t gemm_err_partials(const GemmDesc& d);
 void gemm_f64_err(const GemmDesc& d, const double* R, const double* table, int table_n, double* partials,
                   double* out_dev, cudaStream_t s);
 
+// sum (R - W Ut^T)^2 and sum R^2 for a small inner dimension K (W: M x K,
+// Ut: N x K, R: M x N); out_dev[0], out_dev[1] as gemm_f64_err.
+size_t err_lowrank_partials(int M, int N);
+void err_lowrank_f64(const double* W, const double* Ut, const double* R, int M, int N, int K, double* partials,
+                     double* out_dev, cudaStream_t s);
+
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
 void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
@@ -237,8 +253,8 @@ int validate_request(const tk_kernel* k, const tk_grid* g, const tk_opts* o);
 size_t bucket_bytes_per_instance(const BucketKey& key);
 // Solves B requests of one bucket (fold_applicable for all), enqueued on s;
 // synchronises s twice (ranks, then results).  outs[b] receives new results.
-void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, Profiler* pf, const SolveReq* req, int B,
-                  tk_result** outs, cudaStream_t s);
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, Profiler* pf,
+                  const SolveReq* req, int B, tk_result** outs, cudaStream_t s);
 
 }  // namespace tk
 
@@ -270,6 +286,7 @@ struct tk_ctx {
   std::mutex mu;
   tk::Workspace ws;   // stages before the rank decision
   tk::Workspace ws2;  // stages after it (sized from the ranks)
+  tk::HostPinned pin; // staging of the engine's small transfers
   std::string last_error;
   int sm_count = 0;
   tk::Profiler prof;
