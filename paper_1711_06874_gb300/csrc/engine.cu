@@ -248,7 +248,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   }
   const long long H = (long long)h[0] * h[1] * h[2];
   const long long Q = tab ? table_entries(n[0]) : 0;
-  const size_t nparts = eval_octant_parts(g);
+  // sampling fused with the mode-1 slicing: Fh is never stored (the Gram and
+  // the first TTM read the slices)
+  const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0;
+  const size_t nparts = std::max<size_t>(eval_octant_parts(g), (size_t)h[0]);
   size_t gram_bytes = 0, eig_doubles = 0;
   for (int a = 0; a < nmodes; ++a) {
     gram_bytes = std::max(gram_bytes, sliced ? gram_sliced_scratch_bytes(h, a, B)
@@ -262,7 +265,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   // ints: [0] timeout flag; rmax, rfix [mode][b]; outA, outB [mode][b][4];
   // staging of the escalated instances (index, rmax, rfix)
   const int nint = 16 + 33 * B;
-  size_t need = carve_bytes<KernelDev>(B) + carve_bytes<double>(Q * B) + carve_bytes<double>(H * B) +
+  size_t need = carve_bytes<KernelDev>(B) + carve_bytes<double>(Q * B) + carve_bytes<double>(fused ? 1 : H * B) +
                 carve_bytes<double>(nparts * B) + 3 * carve_bytes<double>(B) + carve_bytes<int>(nint) +
                 carve_bytes<char>(gram_bytes) + carve_bytes<double>(eig_doubles) +
                 carve_bytes<double>((size_t)B * hmax * hmax) + carve_bytes<double>(B);
@@ -273,7 +276,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   pre.reserve(need + 4096, s);
   KernelDev* kd = pre.take<KernelDev>(B);
   double* table = pre.take<double>(std::max<long long>(1, Q * B));
-  double* Fh = pre.take<double>(H * B);
+  double* Fh = pre.take<double>(fused ? 1 : H * B);
   double* part = pre.take<double>(nparts * B);
   double* normF2 = pre.take<double>(B);
   double* epsv = pre.take<double>(B);
@@ -341,13 +344,21 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   TK_CUDA(cudaMemcpyAsync(ints, ih, sizeof(int) * (16 + 6 * B), cudaMemcpyHostToDevice, s));
 
   if (pf) pf->begin(TK_STAGE_EVAL, s);
-  eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
+  if (fused) {
+    const SliceView v = gram_slices_view(gscr, h, 0, B);
+    eval_octant_slices(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part, normF2, s,
+                       pf);
+  } else {
+    eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
+  }
   if (pf) pf->end(s);
   // modes in reverse order: the slices of mode 1 stay in the Gram scratch for
   // the tensor-core TTM
   for (int a = nmodes - 1; a >= 0; --a) {
     if (pf) pf->begin(TK_STAGE_GRAM, s);
-    if (sliced)
+    if (fused)
+      gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf);
+    else if (sliced)
       gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf);
     else
       gram_f64_batch(Fh, h, a, B, G[a], (double*)gscr, s);

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "nu_consts.h"
+#include "slices.cuh"
 #include "tk_internal.h"
 
 namespace tk {
@@ -329,6 +330,85 @@ __global__ void __launch_bounds__(256) k_parts_final(const double* __restrict__ 
 static unsigned oct_blocks(const tk_grid& g) {
   const long long rows = (long long)((g.n[0] + 1) / 2) * ((g.n[1] + 1) / 2);
   return (unsigned)std::max<long long>(1, std::min<long long>(rows / 8, kEvalBlocks));
+}
+
+// One block per octant row i (mode-1 unfolding, K = h^2 columns (j, l)) of
+// instance blockIdx.y: values from the table, the row's largest magnitude and
+// sum of squares (first pass), then its six BF16 slices (second pass, values
+// recomputed from the table instead of stored).
+__global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict__ T, long long Q, int n, int h,
+                                                      long long Kp, int* __restrict__ rowexp,
+                                                      __nv_bfloat16* __restrict__ S, double* __restrict__ part) {
+  __shared__ double redm[32], reds[32];
+  __shared__ int eshared;
+  const int i = blockIdx.x, b = blockIdx.y;
+  const double* Tb = T + (size_t)b * Q;
+  const int even = (n % 2 == 0);
+  const int ai = 2 * i + even;
+  const int ti = even ? 1 : (i > 0);
+  const long long K = (long long)h * h;
+  auto value = [&](long long c) {
+    const int j = (int)(c / h), l = (int)(c - (long long)j * h);
+    const int aj = 2 * j + even, al = 2 * l + even;
+    const int sq = ai * ai + aj * aj + al * al;
+    const int tw = even ? 3 : ti + (j > 0) + (l > 0);
+    return __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2)) * fold_scale(tw);
+  };
+  double mx = 0.0, ss = 0.0;
+  for (long long c = threadIdx.x; c < K; c += blockDim.x) {
+    const double v = value(c);
+    mx = fmax(mx, fabs(v));
+    ss = fma(v, v, ss);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    redm[threadIdx.x >> 5] = mx;
+    reds[threadIdx.x >> 5] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0, t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, redm[w]);
+      t += reds[w];
+    }
+    int e = -1000;
+    if (m > 0.0) frexp(m, &e);
+    eshared = e;
+    rowexp[(size_t)b * h + i] = e;
+    part[(size_t)b * h + i] = t;
+  }
+  __syncthreads();
+  const int e = eshared;
+  const size_t plane = (size_t)h * Kp;
+  __nv_bfloat16* Sb = S + (size_t)b * kSlices * plane + (size_t)i * Kp;
+  for (long long c = threadIdx.x; c < Kp; c += blockDim.x) {
+    int d[kSlices] = {0, 0, 0, 0, 0, 0};
+    if (c < K && e > -1000) slice_digits(value(c), e, d);
+#pragma unroll
+    for (int s2 = 0; s2 < kSlices; ++s2) Sb[s2 * plane + c] = slice_value(d[s2], s2);
+  }
+}
+
+void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
+                        long long Kp, double* part, double* normF2, cudaStream_t s, Profiler* pf) {
+  const int n = g.n[0], h = (n + 1) / 2;
+  const long long Q = table_size(n);
+  const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
+  const long long tb = (Q + 63) / 64;
+  if (pf) pf->begin(TK_STAGE_TABLE, s);
+  k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
+  TK_LAUNCH("k_table_b");
+  if (pf) pf->end(s);
+  // rows of h^2 values: wide blocks when few rows must fill the GPU
+  const int threads = (h * B < 304) ? 1024 : 256;
+  k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
+  TK_LAUNCH("k_gather_slice");
+  k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);
+  TK_LAUNCH("k_parts_final");
 }
 
 size_t eval_octant_parts(const tk_grid& g) { return oct_blocks(g); }

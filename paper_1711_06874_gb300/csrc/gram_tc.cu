@@ -510,6 +510,25 @@ void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double*
   run_tc_gram(p, B, S, rowexp, P, G, err, s, pf);
 }
 
+// The Gram from slices already written into the scratch (by a sampling
+// kernel that sliced the mode-1 rows while it evaluated them).
+void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* err, cudaStream_t s,
+                          Profiler* pf) {
+  const TcPlan p = tc_plan(n, 0, 152, B);
+  char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    char* q = base + off;
+    off += (bytes + 255) & ~size_t(255);
+    return q;
+  };
+  carve(sizeof(unsigned long long) * B * p.nrows);
+  int* rowexp = (int*)carve(sizeof(int) * (size_t)B * p.nrows);
+  __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * p.nrows * p.Kp);
+  long long* P = (long long*)carve(sizeof(long long) * (size_t)B * p.nsplit * p.nblocks * kTM * kTN);
+  run_tc_gram(p, B, S, rowexp, P, G, err, s, pf);
+}
+
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B) {
   const TcPlan p = tc_plan(n, mode, 152, B);
   char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);

@@ -150,6 +150,17 @@ struct SliceView {
   long long Kp;
 };
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B);
+// The mode-1 Gram of B tensors whose slices and row exponents were already
+// written where gram_slices_view(scratch, n, 0, B) points.
+void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* err, cudaStream_t s,
+                          Profiler* pf = nullptr);
+// Sampling fused with the mode-1 slicing for cubic isotropic grids: the
+// distinct-value table, then per octant row i the values Fh(i, j, l) (never
+// stored), their largest magnitude (row exponent), their BF16 slices and
+// their sum of squares; normF2[b] = |F_b|^2.  rowexp: [b][h]; S: [b][6][h][Kp]
+// (zero beyond h^2); part: B x h doubles.
+void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
+                        long long Kp, double* part, double* normF2, cudaStream_t s, Profiler* pf = nullptr);
 // (d) First TTM (mode 3) of Bg instances on the tensor cores from the mode-1
 // Gram slices of the bucket (Fh of instance amap[j] with h = (h1, h2, h3),
 // h3 % 8 == 0 and Kp == h2 h3): T1[j][(i, k)][c] = sum_l Fh[(i, k)][l]
