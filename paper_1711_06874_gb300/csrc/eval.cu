@@ -403,8 +403,9 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
   TK_LAUNCH("k_table_b");
   if (pf) pf->end(s);
-  // rows of h^2 values: wide blocks when few rows must fill the GPU
-  const int threads = (h * B < 304) ? 1024 : 256;
+  // rows of h^2 values: wide blocks for long rows (a function of the shape
+  // alone, so that each instance's sums do not depend on the batch)
+  const int threads = (h >= 128) ? 1024 : 256;
   k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
   TK_LAUNCH("k_gather_slice");
   k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);
