@@ -98,7 +98,12 @@ typedef struct {
                                  sqrt(w_i w_j w_l) F (w = grid points an octant
                                  index stands for: 1 at the centre of an odd axis,
                                  else 2).  Skipped when rfix_k > ceil(n_k / 2). */
-  int32_t reserved[3];        /* must be zero */
+  int32_t with_error;         /* 1 (folded solves): also compute E = |F - X|_F / |F|_F
+                                 of Eq. (FNorm) as tk_rel_error does, from a second,
+                                 independent sampling of F that runs on a side
+                                 stream while the eigenpairs are computed; read it
+                                 with tk_result_rel_error */
+  int32_t reserved[2];        /* must be zero */
 } tk_opts;
 
 typedef struct tk_ctx tk_ctx;
@@ -145,6 +150,8 @@ int tk_core(const tk_result* res, double* dst, int on_device, void* stream);
 int tk_eigenvalues(const tk_result* res, int mode, double* dst, int count, int* written);
 /* |F|^2 of the sampled tensor (compensated FP64 sum), host scalar. */
 int tk_norm2(const tk_result* res, double* normF2);
+/* E computed during the solve (opts.with_error = 1); TK_EINVAL otherwise. */
+int tk_result_rel_error(const tk_result* res, double* rel_error);
 
 /* X = B x_1 U_1 x_2 U_2 x_3 U_3 into dst (device, n1 n2 n3 FP64). */
 int tk_reconstruct(tk_ctx* ctx, const tk_result* res, double* dst, void* stream);

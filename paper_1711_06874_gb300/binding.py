@@ -41,7 +41,7 @@ class Grid(_c.Structure):
 
 class Opts(_c.Structure):
     _fields_ = [("eps", _dbl), ("rmax", _i32 * 3), ("rfix", _i32 * 3), ("precision", _i32),
-                ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("reserved", _i32 * 3)]
+                ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("with_error", _i32), ("reserved", _i32 * 2)]
 
 
 class ServeOpts(_c.Structure):
@@ -67,6 +67,7 @@ SIGNATURES = {
     "tk_core": (_c.c_int, [_vp, _vp, _c.c_int, _vp]),
     "tk_eigenvalues": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
     "tk_norm2": (_c.c_int, [_vp, _c.POINTER(_dbl)]),
+    "tk_result_rel_error": (_c.c_int, [_vp, _c.POINTER(_dbl)]),
     "tk_reconstruct": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "tk_rel_error": (_c.c_int, [_vp, _vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(_dbl), _vp]),
     "tk_result_free": (None, [_vp]),
@@ -141,7 +142,8 @@ def make_grid(prob: workloads.Problem) -> Grid:
 _DEFAULT_OPTS = None
 
 
-def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True, fold=True) -> Opts:
+def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True, fold=True,
+              with_error=False) -> Opts:
     global _DEFAULT_OPTS
     if _DEFAULT_OPTS is None:
         d = Opts()
@@ -154,6 +156,7 @@ def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortc
     o.precision = precision
     o.isotropic_shortcut = 1 if shortcut else 0
     o.reflect_fold = 1 if fold else 0
+    o.with_error = 1 if with_error else 0
     return o
 
 
@@ -168,14 +171,15 @@ def _stream_ptr(stream) -> int | None:
 class BatchArgs:
     """The C structs of a batch of problems, marshalled once."""
 
-    def __init__(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None):
+    def __init__(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, with_error=False):
         self.probs = list(probs)
         self.count = len(self.probs)
         rfixes = rfixes or [(0, 0, 0)] * self.count
         n = max(self.count, 1)
         self.ks = (Kernel * n)(*[make_kernel(p) for p in self.probs])
         self.gs = (Grid * n)(*[make_grid(p) for p in self.probs])
-        self.os = (Opts * n)(*[make_opts(p, precision, rf, shortcut, fold) for p, rf in zip(self.probs, rfixes)])
+        self.os = (Opts * n)(*[make_opts(p, precision, rf, shortcut, fold, with_error)
+                               for p, rf in zip(self.probs, rfixes)])
 
 
 class Context:
@@ -200,18 +204,20 @@ class Context:
 
     # ---- whole solve -------------------------------------------------------
     def tucker(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True,
-               fold=True, stream=None) -> "Result":
-        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold)
+               fold=True, with_error=False, stream=None) -> "Result":
+        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold, with_error)
         out = _vp()
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
         return Result(self, out, prob, k, g)
 
-    def batch(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, stream=None) -> list:
+    def batch(self, probs, precision=TK_FP64, shortcut=True, fold=True, rfixes=None, with_error=False,
+              stream=None) -> list:
         """Independent solves in one call (tk_batch); one Result per problem.
         probs: a list of Problems, or BatchArgs built once beforehand.
         rfixes: optional per-problem fixed ranks (tuples of 3, 0 = eps rule)."""
-        args = probs if isinstance(probs, BatchArgs) else BatchArgs(probs, precision, shortcut, fold, rfixes)
+        args = probs if isinstance(probs, BatchArgs) else BatchArgs(probs, precision, shortcut, fold, rfixes,
+                                                                    with_error)
         cnt = args.count
         outs = (_vp * max(cnt, 1))()
         _check(self.lib.tk_batch(self.ptr, cnt, args.ks, args.gs, args.os, outs, _stream_ptr(stream)), self.ptr)
@@ -331,6 +337,13 @@ class Result:
         w = _c.c_int(0)
         _check(self.ctx.lib.tk_eigenvalues(self.ptr, int(mode), out.ctypes.data, count, _c.byref(w)))
         return out[: w.value].copy()
+
+    @property
+    def solve_error(self) -> float:
+        """E computed during the solve (with_error=True)."""
+        v = _dbl(0)
+        _check(self.ctx.lib.tk_result_rel_error(self.ptr, _c.byref(v)))
+        return v.value
 
     @property
     def norm2(self) -> float:

@@ -181,7 +181,8 @@ void check_opts(const tk_opts* o) {
   }
   if (o->precision != TK_FP64 && o->precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
   if (o->reflect_fold != 0 && o->reflect_fold != 1) fail(TK_EINVAL, "reflect_fold must be 0 or 1");
-  for (int i = 0; i < 3; ++i)
+  if (o->with_error != 0 && o->with_error != 1) fail(TK_EINVAL, "with_error must be 0 or 1");
+  for (int i = 0; i < 2; ++i)
     if (o->reserved[i] != 0) fail(TK_EINVAL, "reserved fields must be zero");
 }
 
@@ -478,7 +479,7 @@ tk_result* solve_one(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, 
   if (!fold_applicable(*grid, *opts)) return tucker_full(ctx, kernel, grid, opts, s);
   SolveReq rq{*kernel, *grid, *opts};
   tk_result* res = nullptr;
-  solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, &ctx->prof, &rq, 1, &res, s);
+  solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->prof, &rq, 1, &res, s);
   return res;
 }
 
@@ -543,7 +544,7 @@ int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* gr
           const int i = idx[c0 + j];
           rq[j] = SolveReq{kernels[i], grids[i], opts[i]};
         }
-        solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, &ctx->prof, rq.data(), cnt, rs.data(), s);
+        solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->prof, rq.data(), cnt, rs.data(), s);
         for (int j = 0; j < cnt; ++j) outs[idx[c0 + j]] = rs[j];
       }
     }
@@ -593,6 +594,12 @@ int tk_eigenvalues(const tk_result* res, int mode, double* dst, int count, int* 
   const int k = std::min<int>(count, (int)res->lam[mode].size());
   std::memcpy(dst, res->lam[mode].data(), sizeof(double) * k);
   if (written) *written = k;
+  return TK_OK;
+}
+
+int tk_result_rel_error(const tk_result* res, double* rel_error) {
+  if (!res || !rel_error || !res->has_error) return TK_EINVAL;
+  *rel_error = res->rel_error;
   return TK_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -45,6 +46,27 @@ static cudaStream_t free_stream(int device) {
   }
   streams[device] = s;
   return s;
+}
+
+void SideStream::ensure(int dev) {
+  if (s && device == dev) return;
+  if (s) {
+    cudaStreamDestroy(s);
+    cudaEventDestroy(start);
+    cudaEventDestroy(done);
+  }
+  device = dev;
+  TK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  TK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  TK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+}
+
+SideStream::~SideStream() {
+  if (s) {
+    cudaStreamDestroy(s);
+    cudaEventDestroy(start);
+    cudaEventDestroy(done);
+  }
 }
 
 char* HostPinned::reserve(size_t need) {
@@ -93,7 +115,7 @@ bool fold_applicable(const tk_grid& g, const tk_opts& o) {
 
 static auto key_tuple(const BucketKey& k) {
   return std::make_tuple(k.n[0], k.n[1], k.n[2], k.b[0], k.b[1], k.b[2], k.kind, k.precision, k.nmodes, k.tab,
-                         k.m[0], k.m[1], k.m[2]);
+                         k.m[0], k.m[1], k.m[2], k.err);
 }
 bool BucketKey::operator<(const BucketKey& o) const { return key_tuple(*this) < key_tuple(o); }
 bool BucketKey::operator==(const BucketKey& o) const { return key_tuple(*this) == key_tuple(o); }
@@ -109,6 +131,7 @@ BucketKey bucket_key(const SolveReq& r) {
   k.precision = r.o.precision;
   k.nmodes = shortcut_ok(r.k, r.g, r.o) ? 1 : 3;
   k.tab = table_applicable(r.k, r.g) ? 1 : 0;
+  k.err = r.o.with_error ? 1 : 0;
   return k;
 }
 
@@ -230,7 +253,7 @@ size_t bucket_bytes_per_instance(const BucketKey& k) {
   return b + 16384;
 }
 
-void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, Profiler* pf,
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, SideStream& side, Profiler* pf,
                   const SolveReq* req, int B, tk_result** outs, cudaStream_t s) {
   if (B < 1) return;
   const tk_grid& g = req[0].g;
@@ -251,6 +274,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   // sampling fused with the mode-1 slicing: Fh is never stored (the Gram and
   // the first TTM read the slices)
   const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0;
+  const bool with_err = key.err != 0;
   const size_t nparts = std::max<size_t>(eval_octant_parts(g), (size_t)h[0]);
   size_t gram_bytes = 0, eig_doubles = 0;
   for (int a = 0; a < nmodes; ++a) {
@@ -273,6 +297,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     need += carve_bytes<double>((size_t)B * h[a] * h[a]) + carve_bytes<double>((size_t)B * mA[a]) +
             carve_bytes<double>((size_t)B * h[a] * mA[a]) + carve_bytes<double>(B) +
             2 * (carve_bytes<double>((size_t)B * m[a]) + carve_bytes<double>((size_t)B * h[a] * m[a]));
+  if (with_err)
+    need += carve_bytes<double>(Q * B) + carve_bytes<double>(H * B) + carve_bytes<double>(nparts * B) +
+            carve_bytes<double>(B);
   pre.reserve(need + 4096, s);
   KernelDev* kd = pre.take<KernelDev>(B);
   double* table = pre.take<double>(std::max<long long>(1, Q * B));
@@ -298,6 +325,13 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       VE[a][l] = pre.take<double>((size_t)B * h[a] * m[a]);
     }
   }
+  double *tableE = nullptr, *FhE = nullptr, *partE = nullptr, *normE = nullptr;
+  if (with_err) {
+    tableE = pre.take<double>(std::max<long long>(1, Q * B));
+    FhE = pre.take<double>(H * B);
+    partE = pre.take<double>(nparts * B);
+    normE = pre.take<double>(B);
+  }
   int* errflag = ints;
   int* rmaxv = ints + 16;           // [a][b]
   int* rfixv = rmaxv + 3 * B;       // [a][b]
@@ -312,7 +346,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   const size_t pin_up = carve_bytes<KernelDev>(B) + carve_bytes<double>(B) + carve_bytes<int>(16 + 6 * B);
   const size_t pin_down = carve_bytes<int>(12 * B + 1) + carve_bytes<double>(B) + carve_bytes<double>(lam_count);
   const size_t pin_desc = carve_bytes<int>(B) + carve_bytes<UnfoldDesc>((size_t)B * nmodes) +
-                          carve_bytes<CoreDesc>(B) + carve_bytes<int>(1);
+                          carve_bytes<CoreDesc>(B) + carve_bytes<int>(1) + carve_bytes<double>(2 * (size_t)B);
   char* pbase = pin.reserve(pin_up + pin_down + pin_desc + 1024);
   size_t poff = 0;
   auto ptake = [&](size_t bytes) {
@@ -330,6 +364,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   UnfoldDesc* udh = (UnfoldDesc*)ptake(sizeof(UnfoldDesc) * B * nmodes);
   CoreDesc* cdh = (CoreDesc*)ptake(sizeof(CoreDesc) * B);
   int* herrp = (int*)ptake(sizeof(int));
+  double* hesum = (double*)ptake(sizeof(double) * 2 * B);
   std::memset(ih, 0, sizeof(int) * 16);
   for (int b = 0; b < B; ++b) {
     kdh[b] = make_kernel_dev(req[b].k);
@@ -343,6 +378,14 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   TK_CUDA(cudaMemcpyAsync(epsv, epsh, sizeof(double) * B, cudaMemcpyHostToDevice, s));
   TK_CUDA(cudaMemcpyAsync(ints, ih, sizeof(int) * (16 + 6 * B), cudaMemcpyHostToDevice, s));
 
+  if (with_err) {
+    // the error's own sampling of F, on the side stream while the solve runs
+    side.ensure(ctx->device);
+    TK_CUDA(cudaEventRecord(side.start, s));
+    TK_CUDA(cudaStreamWaitEvent(side.s, side.start, 0));
+    eval_octant_f64(kd, tab, g, B, FhE, tableE, partE, normE, side.s);
+    TK_CUDA(cudaEventRecord(side.done, side.s));
+  }
   if (pf) pf->begin(TK_STAGE_EVAL, s);
   if (fused) {
     const SliceView v = gram_slices_view(gscr, h, 0, B);
@@ -568,11 +611,23 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   if (tc_ttm)
     for (const GroupBuf& q : gb)
       if (q.R <= 96) ttm_scr = std::max(ttm_scr, ttm_sliced_scratch_bytes(h[2], q.R, q.cnt));
+  size_t errw = 0;  // W1, W2 of every group, for the error
+  const size_t eparts = err_lowrank_partials(h[0] * h[1], h[2]);
+  if (with_err)
+    for (const GroupBuf& q : gb)
+      errw += (((size_t)q.cnt * h[0] * q.R * q.R + 31) & ~size_t(31)) + (((size_t)q.cnt * h[0] * h[1] * q.R + 31) & ~size_t(31));
   post.reserve(carve_bytes<double>(ttm) + carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
-                   carve_bytes<CoreDesc>(B) + carve_bytes<char>(ttm_scr) + 4096,
+                   carve_bytes<CoreDesc>(B) + carve_bytes<char>(ttm_scr) +
+                   (with_err ? carve_bytes<double>(errw) + carve_bytes<double>((size_t)B * eparts) +
+                                   carve_bytes<double>(2 * (size_t)B)
+                             : 0) +
+                   4096,
                s);
   double* tbase = post.take<double>(std::max<size_t>(ttm, 1));
   char* tscr = post.take<char>(std::max<size_t>(ttm_scr, 1));
+  double* ewbase = with_err ? post.take<double>(std::max<size_t>(errw, 1)) : nullptr;
+  double* epart = with_err ? post.take<double>((size_t)B * eparts) : nullptr;
+  double* esum = with_err ? post.take<double>(2 * (size_t)B) : nullptr;
   int* amap = post.take<int>(B);
   UnfoldDesc* ud = post.take<UnfoldDesc>(ndesc);
   CoreDesc* cd = post.take<CoreDesc>(B);
@@ -643,7 +698,42 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   k_extract_core<<<dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), 256, 0, s>>>(cd);
   TK_LAUNCH("k_extract_core");
   if (pf) pf->end(s);
+  if (with_err) {
+    // X = B x_1 V_1 x_2 V_2 x_3 V_3 against the independent sampling, per
+    // rank group with the zero-padded factors (the padding adds exact zeros)
+    if (pf) pf->begin(TK_STAGE_ERROR, s);
+    TK_CUDA(cudaStreamWaitEvent(s, side.done, 0));
+    size_t woff = 0;
+    for (const GroupBuf& q : gb) {
+      const int R = q.R;
+      const double* Up0 = tbase + q.up[0];
+      const double* Up1 = tbase + q.up[nmodes == 1 ? 0 : 1];
+      const double* Up2 = tbase + q.up[nmodes == 1 ? 0 : 2];
+      const double* Cp = tbase + q.cp;
+      double* W1 = ewbase + woff;
+      woff += ((size_t)q.cnt * h[0] * R * R + 31) & ~size_t(31);
+      double* W2 = ewbase + woff;
+      woff += ((size_t)q.cnt * h[0] * h[1] * R + 31) & ~size_t(31);
+      // W1[i][(b,c)] = sum_a V1[i][a] B[a][(b,c)]
+      GemmDesc e1{h[0], R * R, R, q.cnt, Up0, (long long)h[0] * R, R, 1, Cp, (long long)R * R * R,
+                  (long long)R * R, 1, W1, (long long)h[0] * R * R, (long long)R * R, 1};
+      e1.fixed_order = 1;
+      gemm_f64(e1, s);
+      // W2[(i,k)][c] = sum_b V2[k][b] W1[i][b][c], one product per (instance, i)
+      GemmDesc e2{h[1], R, R, q.cnt * h[0], Up1, (long long)h[1] * R, R, 1, W1, (long long)h[0] * R * R, R, 1,
+                  W2, (long long)h[0] * h[1] * R, R, 1};
+      e2.batch2 = h[0];
+      e2.sBb2 = (long long)R * R;
+      e2.sCb2 = (long long)h[1] * R;
+      e2.fixed_order = 1;
+      gemm_f64(e2, s);
+      err_lowrank_batch(W2, (long long)h[0] * h[1] * R, Up2, (long long)h[2] * R, FhE, H, amap + q.off,
+                        h[0] * h[1], h[2], R, q.cnt, epart + (size_t)q.off * eparts, esum + 2 * (size_t)q.off, s);
+    }
+    if (pf) pf->end(s);
+  }
   TK_CUDA(cudaMemcpyAsync(herrp, errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (with_err) TK_CUDA(cudaMemcpyAsync(hesum, esum, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   if (pf) pf->collect();
   if (*herrp != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
@@ -668,6 +758,13 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       res->lam[a].assign(p.hl.begin() + (size_t)j * p.mp, p.hl.begin() + (size_t)(j + 1) * p.mp);
     }
     res->core = rbase + offC[b];
+    if (with_err) {
+      // group order: instance b sits at amapv position (group offset + position)
+      const GroupBuf& q = gb[groupOf[fin[b].R]];
+      const size_t slot = (size_t)q.off + posInGroup[b];
+      res->has_error = 1;
+      res->rel_error = std::sqrt(hesum[2 * slot] / hesum[2 * slot + 1]);
+    }
     outs[b] = res;
   }
 }

@@ -451,6 +451,41 @@ __global__ void __launch_bounds__(1024) k_err_final(const double* part, long lon
   }
 }
 
+// k_err_final for instance blockIdx.x of a batch (nparts partials each).
+__global__ void __launch_bounds__(1024) k_err_final_batch(const double* part, long long nparts, double* out) {
+  part += (long long)blockIdx.x * 4 * nparts;
+  double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+  for (long long b = threadIdx.x; b < nparts; b += blockDim.x) {
+    neum(s0, c0, part[4 * b]);
+    c0 += part[4 * b + 1];
+    neum(s1, c1, part[4 * b + 2]);
+    c1 += part[4 * b + 3];
+  }
+  __shared__ double red[4][1024];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = c0;
+  red[2][threadIdx.x] = s1;
+  red[3][threadIdx.x] = c1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a0 = red[0][threadIdx.x], a1 = red[1][threadIdx.x] + red[1][threadIdx.x + w];
+      neum(a0, a1, red[0][threadIdx.x + w]);
+      double b0 = red[2][threadIdx.x], b1 = red[3][threadIdx.x] + red[3][threadIdx.x + w];
+      neum(b0, b1, red[2][threadIdx.x + w]);
+      red[0][threadIdx.x] = a0;
+      red[1][threadIdx.x] = a1;
+      red[2][threadIdx.x] = b0;
+      red[3][threadIdx.x] = b1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = red[0][0] + red[1][0];
+    out[2 * blockIdx.x + 1] = red[2][0] + red[3][0];
+  }
+}
+
 // One warp per output element; lanes stride over K, fixed shuffle tree.
 __global__ void k_gemm_warp(GemmDesc d) {
   const long long per_batch = (long long)d.M * d.N;
@@ -566,8 +601,14 @@ constexpr int kErrRows = 64, kErrCols = 128;
 
 __global__ void __launch_bounds__(256) k_err_lowrank(const double* __restrict__ W, const double* __restrict__ Ut,
                                                      const double* __restrict__ R, int M, int N, int K,
-                                                     double* __restrict__ partials) {
+                                                     double* __restrict__ partials, long long sW, long long sU,
+                                                     long long sR, const int* __restrict__ amap) {
   extern __shared__ double es[];
+  // instance blockIdx.z of a batch
+  W += (long long)blockIdx.z * sW;
+  Ut += (long long)blockIdx.z * sU;
+  R += (amap ? (long long)amap[blockIdx.z] : (long long)blockIdx.z) * sR;
+  partials += (long long)blockIdx.z * 4 * gridDim.x * gridDim.y;
   double* Ws = es;                   // [64][K]
   double* Us = es + kErrRows * K;    // [K][128]
   const int m0 = blockIdx.y * kErrRows, n0 = blockIdx.x * kErrCols;
@@ -636,10 +677,25 @@ void err_lowrank_f64(const double* W, const double* Ut, const double* R, int M, 
     TK_CUDA(cudaFuncSetAttribute(k_err_lowrank, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
   const dim3 grid((N + kErrCols - 1) / kErrCols, (M + kErrRows - 1) / kErrRows);
-  k_err_lowrank<<<grid, 256, smem, s>>>(W, Ut, R, M, N, K, partials);
+  k_err_lowrank<<<grid, 256, smem, s>>>(W, Ut, R, M, N, K, partials, 0, 0, 0, nullptr);
   TK_LAUNCH("k_err_lowrank");
   k_err_final<<<1, 1024, 0, s>>>(partials, (long long)grid.x * grid.y, out_dev);
   TK_LAUNCH("k_err_final");
+}
+
+void err_lowrank_batch(const double* W, long long sW, const double* Ut, long long sU, const double* R, long long sR,
+                       const int* amap, int M, int N, int K, int B, double* partials, double* out_dev,
+                       cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)(kErrRows + kErrCols) * K;
+  if (K < 1 || smem > 200 * 1024) fail(TK_EINVAL, "err_lowrank: K out of range");
+  once_per_device((const void*)&k_err_lowrank, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_err_lowrank, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  const dim3 grid((N + kErrCols - 1) / kErrCols, (M + kErrRows - 1) / kErrRows, B);
+  k_err_lowrank<<<grid, 256, smem, s>>>(W, Ut, R, M, N, K, partials, sW, sU, sR, amap);
+  TK_LAUNCH("k_err_lowrank");
+  k_err_final_batch<<<B, 1024, 0, s>>>(partials, (long long)grid.x * grid.y, out_dev);
+  TK_LAUNCH("k_err_final_batch");
 }
 
 size_t gemm_err_partials(const GemmDesc& d) {

@@ -66,6 +66,7 @@ using namespace tk;
 struct WorkerState {
   Workspace pre, post;
   HostPinned pin;
+  SideStream side;
   cudaStream_t stream = nullptr;
 };
 
@@ -129,7 +130,7 @@ void tk_server::worker_main(int /*wid*/) {
     int status = TK_OK;
     try {
       if (!w.stream) fail(TK_ECUDA, "cannot create a worker stream");
-      solve_bucket(ctx, w.pre, w.post, w.pin, nullptr, reqs.data(), (int)reqs.size(), outs.data(), w.stream);
+      solve_bucket(ctx, w.pre, w.post, w.pin, w.side, nullptr, reqs.data(), (int)reqs.size(), outs.data(), w.stream);
     } catch (const Error& e) {
       status = e.status;
     } catch (...) {

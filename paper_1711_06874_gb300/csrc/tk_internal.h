@@ -61,6 +61,15 @@ struct HostPinned {
   ~HostPinned();
 };
 
+// A second stream with two events, for work that overlaps the solve.
+struct SideStream {
+  int device = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
+  void ensure(int dev);
+  ~SideStream();
+};
+
 // Device memory shared by the results of one batched solve; freed with the
 // last of them.
 struct DeviceBlock {
@@ -206,6 +215,11 @@ void gemm_f64_err(const GemmDesc& d, const double* R, const double* table, int t
 size_t err_lowrank_partials(int M, int N);
 void err_lowrank_f64(const double* W, const double* Ut, const double* R, int M, int N, int K, double* partials,
                      double* out_dev, cudaStream_t s);
+// The same for B entries: W + b sW, Ut + b sU, R + amap[b] sR; partials
+// [b][err_lowrank_partials(M, N)], out_dev [b][2].
+void err_lowrank_batch(const double* W, long long sW, const double* Ut, long long sU, const double* R, long long sR,
+                       const int* amap, int M, int N, int K, int B, double* partials, double* out_dev,
+                       cudaStream_t s);
 
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
@@ -252,7 +266,7 @@ bool fold_applicable(const tk_grid& g, const tk_opts& o);
 struct BucketKey {
   int n[3];
   double b[3];
-  int kind, precision, nmodes, tab, m[3];
+  int kind, precision, nmodes, tab, m[3], err;
   bool operator<(const BucketKey& o) const;
   bool operator==(const BucketKey& o) const;
 };
@@ -264,7 +278,7 @@ int validate_request(const tk_kernel* k, const tk_grid* g, const tk_opts* o);
 size_t bucket_bytes_per_instance(const BucketKey& key);
 // Solves B requests of one bucket (fold_applicable for all), enqueued on s;
 // synchronises s twice (ranks, then results).  outs[b] receives new results.
-void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, Profiler* pf,
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, SideStream& side, Profiler* pf,
                   const SolveReq* req, int B, tk_result** outs, cudaStream_t s);
 
 }  // namespace tk
@@ -298,6 +312,7 @@ struct tk_ctx {
   tk::Workspace ws;   // stages before the rank decision
   tk::Workspace ws2;  // stages after it (sized from the ranks)
   tk::HostPinned pin; // staging of the engine's small transfers
+  tk::SideStream side; // overlapped independent sampling (with_error)
   std::string last_error;
   int sm_count = 0;
   tk::Profiler prof;
@@ -318,5 +333,7 @@ struct tk_result {
   double normF2 = 0.0;
   int precision = 0;
   int fold = 0;
+  int has_error = 0;
+  double rel_error = 0.0;  // when has_error
   std::shared_ptr<tk::DeviceBlock> mem;  // when set, owns U, Uh and core (shared by a batch)
 };

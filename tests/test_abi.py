@@ -54,13 +54,13 @@ def test_struct_layouts_match_c(lib, tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "tucker_matern.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(tk_kernel), sizeof(tk_grid),"
         " sizeof(tk_opts), offsetof(tk_kernel, sigma2), offsetof(tk_grid, kind), offsetof(tk_opts, precision),"
-        " offsetof(tk_opts, reflect_fold), offsetof(tk_opts, reserved)); return 0;}\n")
+        " offsetof(tk_opts, reflect_fold), offsetof(tk_opts, with_error)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(binding.Kernel), ctypes.sizeof(binding.Grid), ctypes.sizeof(binding.Opts),
             binding.Kernel.sigma2.offset, binding.Grid.kind.offset, binding.Opts.precision.offset,
-            binding.Opts.reflect_fold.offset, binding.Opts.reserved.offset]
+            binding.Opts.reflect_fold.offset, binding.Opts.with_error.offset]
     assert got == want
 
 

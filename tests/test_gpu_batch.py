@@ -189,3 +189,22 @@ def test_sweep_256_n128_full_size(ctx, orc, wl):
         if ranks == ref["ranks"]:
             nF = math.sqrt(ref["normF2"])
             assert abs(np.linalg.norm(r.core()) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
+
+
+def test_error_during_solve(ctx, wl):
+    """E from the overlapped second sampling equals tk_rel_error's, alone and in a batch."""
+    from paper_1711_06874_gb300 import binding
+
+    probs = [wl.problem(0, nu=nu, ell=ell, n=n, eps=1e-6, rmax=24)
+             for nu, ell, n in ((1.2, 0.2, 48), (0.5, 0.3, 40), (2.0, 0.6, 48), (0.8, (0.3, 0.4, 0.5), (20, 24, 28)))]
+    for precision in (binding.TK_FP64, binding.TK_SLICED_BF16):
+        mixed = ctx.batch(probs, precision=precision, with_error=True)
+        for p, rm in zip(probs, mixed):
+            e_ref = rm.rel_error()
+            assert abs(rm.solve_error - e_ref) <= 1e-10 * e_ref, (p, rm.solve_error, e_ref)
+            alone = ctx.tucker(p, precision=precision, with_error=True)
+            assert alone.solve_error == rm.solve_error
+            assert np.array_equal(alone.core(), rm.core())
+        plain = ctx.tucker(probs[0], precision=precision)
+        with pytest.raises(binding.TuckerError):
+            plain.solve_error
