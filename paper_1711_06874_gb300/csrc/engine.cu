@@ -378,14 +378,6 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   TK_CUDA(cudaMemcpyAsync(epsv, epsh, sizeof(double) * B, cudaMemcpyHostToDevice, s));
   TK_CUDA(cudaMemcpyAsync(ints, ih, sizeof(int) * (16 + 6 * B), cudaMemcpyHostToDevice, s));
 
-  if (with_err) {
-    // the error's own sampling of F, on the side stream while the solve runs
-    side.ensure(ctx->device);
-    TK_CUDA(cudaEventRecord(side.start, s));
-    TK_CUDA(cudaStreamWaitEvent(side.s, side.start, 0));
-    eval_octant_f64(kd, tab, g, B, FhE, tableE, partE, normE, side.s);
-    TK_CUDA(cudaEventRecord(side.done, side.s));
-  }
   if (pf) pf->begin(TK_STAGE_EVAL, s);
   if (fused) {
     const SliceView v = gram_slices_view(gscr, h, 0, B);
@@ -395,6 +387,15 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
   }
   if (pf) pf->end(s);
+  if (with_err) {
+    // the error's own sampling of F, on the side stream while the Gram and the
+    // eigenpairs (a few SMs) run
+    side.ensure(ctx->device);
+    TK_CUDA(cudaEventRecord(side.start, s));
+    TK_CUDA(cudaStreamWaitEvent(side.s, side.start, 0));
+    eval_octant_f64(kd, tab, g, B, FhE, tableE, partE, normE, side.s);
+    TK_CUDA(cudaEventRecord(side.done, side.s));
+  }
   // modes in reverse order: the slices of mode 1 stay in the Gram scratch for
   // the tensor-core TTM
   for (int a = nmodes - 1; a >= 0; --a) {
