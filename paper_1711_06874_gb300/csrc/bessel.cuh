@@ -32,6 +32,14 @@
 #define TK_HD inline
 #endif
 
+#ifndef __CUDA_ARCH__
+// host builds (the constants' tests): 1 / sqrt(x)
+inline double tk_rsqrt_host(double x) { return 1.0 / sqrt(x); }
+#define TK_RSQRT(x) tk_rsqrt_host(x)
+#else
+#define TK_RSQRT(x) rsqrt(x)
+#endif
+
 // Terms of Temme's series and of the backward recurrence that are
 // precomputed per order, so the device loops need no division.
 constexpr int kTemmeTerms = 48;   // x <= 1.5 converges in about 25 terms
@@ -93,7 +101,9 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
   // sum_k C_k u_k on the way; S = sum / u_0 and U_1/U_0 = u_1 / u_0.
   // The recurrence reaches 1e-17 with N of about 12 + 180/x terms; values are
   // rescaled by 2^-600 whenever they pass 2^600.
-  const int N = 12 + (int)ceil(180.0 / x);  // at most 132 for x > 1.5
+  // N = 12 + ceil(180 / x) (at most 132 for x > 1.5) from an FP32 quotient,
+  // one step longer so that it is never below the FP64 value
+  const int N = 13 + (int)(180.0f / (float)x) < kMillerTerms - 1 ? 13 + (int)(180.0f / (float)x) : kMillerTerms - 1;
   const double mu2 = mu * mu;
   const double x2 = 2.0 * x;
   double u_next = 0.0, u = 1.0;  // u_{k+1}, u_k at k = N
@@ -115,7 +125,8 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
     }
   }
   const double inv_u0 = 1.0 / u;
-  const double k0 = sqrt(3.141592653589793238 / (2.0 * x)) / (acc * inv_u0);
+  // sqrt(pi / (2 x)) = sqrt(pi / 2) / sqrt(x)
+  const double k0 = 1.2533141373155003 * TK_RSQRT(x) / (acc * inv_u0);
   *kmu = k0;
   *kmu1 = k0 * (x + mu + 0.5 - (0.25 - mu2) * (u_next * inv_u0)) / x;
 }
@@ -125,8 +136,9 @@ TK_HD double tk_bessel_k_scaled(const tk_nu_consts& c, double x) {
   double km, kp;
   tk_bessel_k_pair_scaled(c, x, &km, &kp);
   if (c.nord == 0) return km;
+  const double two_over_x = 2.0 / x;
   for (int k = 1; k < c.nord; ++k) {
-    const double kn = km + (2.0 * (c.mu + (double)k) / x) * kp;
+    const double kn = km + ((c.mu + (double)k) * two_over_x) * kp;
     km = kp;
     kp = kn;
   }

@@ -624,14 +624,25 @@ __global__ void __launch_bounds__(256) k_err_lowrank(const double* __restrict__ 
   const int c = threadIdx.x & (kErrCols - 1), r0 = threadIdx.x >> 7;  // 2 row phases
   double ds = 0.0, fs = 0.0;
   if (n0 + c < N) {
-    for (int i = r0; i < kErrRows && m0 + i < M; i += 2) {
-      const double* w = Ws + i * K;
-      double x = 0.0;
-      for (int k = 0; k < K; ++k) x = fma(w[k], Us[k * kErrCols + c], x);
-      const double r = R[(long long)(m0 + i) * N + n0 + c];
-      const double e = r - x;
-      ds = fma(e, e, ds);
-      fs = fma(r, r, fs);
+    // four rows at a time: independent FMA chains
+    for (int i = r0; i < kErrRows; i += 8) {
+      const double* w0 = Ws + i * K;
+      double x[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < K; ++k) {
+        const double u = Us[k * kErrCols + c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = fma(w0[2 * q * K + k], u, x[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = m0 + i + 2 * q;
+        if (row < M) {
+          const double r = R[(long long)row * N + n0 + c];
+          const double e = r - x[q];
+          ds = fma(e, e, ds);
+          fs = fma(r, r, fs);
+        }
+      }
     }
   }
   // fixed-shape tree over the block, compensation carried along
