@@ -53,6 +53,22 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units of all ranks (independent replicas) per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -280,11 +296,7 @@ def run_ours(args):
             dist.barrier()
 
     def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dist, "cuda")
 
     def timed(step, steps, warmup, profile=False, cleanup=None):
         """Per-step CUDA events on the solve stream; L2 flushed between steps.
@@ -354,7 +366,7 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     sampler.start()
     ms, lat, launches, prof, (err, (ranks, flags)) = timed(lambda: solve(precision), args.steps, 0, profile=True)
     clocks = sampler.stop()
-    value = args.steps * world / (ms / 1000.0)
+    value = whole_job_rate(args.steps, world, ms / 1000.0)
 
     # the plain FP64 GPU path on the same workload (comparison of the metric)
     if precision != binding.TK_FP64:
