@@ -229,7 +229,10 @@ __device__ __forceinline__ double fold_scale(int twos) {
   return (twos == 3) ? 2.0 * r2 : (twos == 2) ? 2.0 : (twos == 1) ? r2 : 1.0;
 }
 
-__global__ void k_table_b(const KernelDev* __restrict__ kd, double hstep, int even, long long Q, double* T) {
+// Distinct values of instance blockIdx.y, times `scale` (one rounding, the
+// same as scaling each gathered value).
+__global__ void k_table_b(const KernelDev* __restrict__ kd, double hstep, int even, long long Q, double* T,
+                          double scale) {
   const int b = blockIdx.y;
   const KernelDev& k = kd[b];
   const double hs = hstep * k.inv_ell[0];
@@ -237,7 +240,8 @@ __global__ void k_table_b(const KernelDev* __restrict__ kd, double hstep, int ev
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
        q += (long long)gridDim.x * blockDim.x) {
     const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
-    T[q] = cov_value(k, hs * hs * s);
+    const double v = cov_value(k, hs * hs * s);
+    T[q] = (scale == 1.0) ? v : v * scale;
   }
 }
 
@@ -339,7 +343,10 @@ static unsigned oct_blocks(const tk_grid& g) {
 __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict__ T, long long Q, int n, int h,
                                                       long long Kp, int* __restrict__ rowexp,
                                                       __nv_bfloat16* __restrict__ S, double* __restrict__ part) {
-  __shared__ double redm[32], reds[32];
+  // For even n every octant point stands for 8 grid points and the table
+  // already holds 2 sqrt(2) C; for odd n the weight varies and is applied here.
+  __shared__ unsigned long long redm[32];
+  __shared__ double reds[32];
   __shared__ int eshared;
   const int i = blockIdx.x, b = blockIdx.y;
   const double* Tb = T + (size_t)b * Q;
@@ -351,17 +358,21 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
     const int j = (int)(c / h), l = (int)(c - (long long)j * h);
     const int aj = 2 * j + even, al = 2 * l + even;
     const int sq = ai * ai + aj * aj + al * al;
-    const int tw = even ? 3 : ti + (j > 0) + (l > 0);
-    return __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2)) * fold_scale(tw);
+    const double t = __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2));
+    return even ? t : t * fold_scale(ti + (j > 0) + (l > 0));
   };
-  double mx = 0.0, ss = 0.0;
+  // largest |value| by its bits (the order of non-negative doubles), sum of squares
+  unsigned long long mx = 0;
+  double ss = 0.0;
   for (long long c = threadIdx.x; c < K; c += blockDim.x) {
     const double v = value(c);
-    mx = fmax(mx, fabs(v));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    mx = bits > mx ? bits : mx;
     ss = fma(v, v, ss);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const unsigned long long om = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = om > mx ? om : mx;
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
   }
   if ((threadIdx.x & 31) == 0) {
@@ -370,13 +381,15 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0, t = 0.0;
+    unsigned long long m = 0;
+    double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      m = fmax(m, redm[w]);
+      m = redm[w] > m ? redm[w] : m;
       t += reds[w];
     }
     int e = -1000;
-    if (m > 0.0) frexp(m, &e);
+    const double mv = __longlong_as_double((long long)m);
+    if (mv > 0.0) frexp(mv, &e);
     eshared = e;
     rowexp[(size_t)b * h + i] = e;
     part[(size_t)b * h + i] = t;
@@ -400,7 +413,9 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
   const long long tb = (Q + 63) / 64;
   if (pf) pf->begin(TK_STAGE_TABLE, s);
-  k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
+  // even n: the table holds the octant values 2 sqrt(2) C directly
+  k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table,
+                                                                            n % 2 == 0 ? 2.8284271247461903 : 1.0);
   TK_LAUNCH("k_table_b");
   if (pf) pf->end(s);
   // rows of h^2 values: wide blocks for long rows (a function of the shape
@@ -426,7 +441,7 @@ void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, dou
     const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
     const long long tb = (Q + 63) / 64;
     if (pf) pf->begin(TK_STAGE_TABLE, s);
-    k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table);
+    k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table, 1.0);
     TK_LAUNCH("k_table_b");
     if (pf) pf->end(s);
     k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);
