@@ -240,8 +240,10 @@ def _roofline(prof, prob, precision, clocks, peaks, peak_src):
     t = have[top][0] / have[top][1] * 1e-3  # s per launch
     out = {"kernel": None, "stage_ms_per_launch": t * 1e3, "traffic": None}
     if top == "gram_tc":
-        nb = ((h + 95) // 96) * ((h + 127) // 128)  # 128 x 96 blocks on and above the diagonal (h <= 128)
-        issued = 21 * 2.0 * 128 * 96 * (h * h) * nb
+        # 128 x 64 blocks of G touching its upper triangle (i 128 < (j + 1) 64)
+        nrt, nct = (h + 127) // 128, (h + 63) // 64
+        nb = sum(max(0, nct - (i * 128) // 64) for i in range(nrt))
+        issued = 21 * 2.0 * 128 * 64 * (h * h) * nb
         ach = issued / t / 1e12
         pk = peaks["bf16_tflops_sustained"]
         out.update(kernel="k_gram_tc (sliced BF16 Gram)", bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s",

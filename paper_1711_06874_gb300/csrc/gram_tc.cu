@@ -24,14 +24,14 @@
 // correctly rounded value of the integer sum times 2^(e_i + e_j - 44), the
 // same for any split of K.
 //
-// Kernel layout (one CTA per 128 x 96 block of G touching its upper triangle,
+// Kernel layout (one CTA per 128 x 64 block of G touching its upper triangle,
 // and one K range):
-//   warp 0       TMA producer: 6 slices x 128 rows (A) and 6 x 96 rows (B) x
-//                32 K per stage, SWIZZLE_64B, two stages;
-//   warp 1       TMEM owner (5 accumulators of 96 columns) and the
+//   warp 0       TMA producer: 6 slices x 128 rows (A) and 6 x 64 rows (B) x
+//                32 K per stage, SWIZZLE_64B, three stages;
+//   warp 1       TMEM owner (5 accumulators of 64 columns) and the
 //                single-thread tcgen05.mma issuer (21 slice pairs x 2 K steps);
 //   warps 2..17  epilogue: TMEM -> registers -> int64, one TMEM lane quadrant
-//                and one 24-column group each.
+//                and one 16-column group each.
 // Every mbarrier wait is bounded; on a timeout the kernel raises a flag, lets
 // in-flight copies and MMAs finish (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -53,19 +53,19 @@ namespace tk {
 namespace {
 
 constexpr int kTM = 128;               // rows of a block of G (M)
-constexpr int kTN = 96;                // columns of a block of G (N)
+constexpr int kTN = 64;                // columns of a block of G (N)
 constexpr int kAcc = 5;                // accumulators: w = 0, 1, 2, 3 and w = 4..5
 constexpr int kKB = 32;                // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int kChunkBlocks = 8;        // 8 x 32 = 256 K per exact chunk
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kSliceBytesA = kTM * kKB * 2;            // 8 KB
-constexpr int kSliceBytesB = kTN * kKB * 2;            // 6 KB
+constexpr int kSliceBytesB = kTN * kKB * 2;            // 4 KB
 constexpr int kOperandBytesA = kSlices * kSliceBytesA;  // 48 KB
-constexpr int kOperandBytesB = kSlices * kSliceBytesB;  // 36 KB
-constexpr int kStageBytes = kOperandBytesA + kOperandBytesB;  // 84 KB
+constexpr int kOperandBytesB = kSlices * kSliceBytesB;  // 24 KB
+constexpr int kStageBytes = kOperandBytesA + kOperandBytesB;  // 72 KB
 constexpr int kThreads = 576;                          // 18 warps
 constexpr int kEpiWarps = 16;
-constexpr int kEpiCols = kTN / 4;                      // 24 columns per epilogue warp
+constexpr int kEpiCols = kTN / 4;                      // 16 columns per epilogue warp
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 
 static_assert(kAcc * kTN <= 512, "accumulators fit in TMEM");
@@ -162,16 +162,16 @@ __global__ void k_slice(const double* __restrict__ F, int mode, int n1, int n2, 
 
 struct TcArgs {
   int nrows;
-  int nrt, nct;           // row tiles (of 128) and column tiles (of 96)
+  int nrt, nct;           // row tiles (of 128) and column tiles (of 64)
   int nblocks;            // blocks of G touching the upper triangle
   int nsplit;             // K splits per instance
   int kblocks_per_split;  // k-blocks (of 32) per CTA
   int kblocks_total;
-  long long* partials;    // [instance][split][block][128][96], units of 2^-44
+  long long* partials;    // [instance][split][block][128][64], units of 2^-44
   int* err;
 };
 
-// Block b (in row-major order over blocks with i*128 < (j+1)*96) -> (i, j).
+// Block b (in row-major order over blocks with i*128 < (j+1)*64) -> (i, j).
 __host__ __device__ __forceinline__ void block_of(int b, int nrt, int nct, int& bi, int& bj) {
   for (int i = 0; i < nrt; ++i) {
     const int j0 = (i * kTM) / kTN;
@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
-  uint64_t* full = bars;            // [kStages]
-  uint64_t* empty = bars + 2;       // [kStages]
-  uint64_t* acc_full = bars + 4;
-  uint64_t* acc_empty = bars + 5;
-  uint64_t* drain = bars + 6;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+  uint64_t* full = bars;                 // [kStages]
+  uint64_t* empty = bars + kStages;      // [kStages]
+  uint64_t* acc_full = bars + 2 * kStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_full + 2;
+  uint32_t* tmem_slot = (uint32_t*)(acc_full + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int inst = blockIdx.z;  // instance of a batch (one slice tensor each)
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue: TMEM -> int64 ----------------
     const int q = warp & 3;             // TMEM lane quadrant of this warp
-    const int grp = (warp - 2) >> 2;    // 24-column group
+    const int grp = (warp - 2) >> 2;    // 16-column group
     const int row = q * 32 + lane;
     long long V[kEpiCols];
 #pragma unroll
