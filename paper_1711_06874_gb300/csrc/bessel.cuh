@@ -124,11 +124,13 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
       acc *= 0x1p-600;
     }
   }
-  const double inv_u0 = 1.0 / u;
-  // sqrt(pi / (2 x)) = sqrt(pi / 2) / sqrt(x)
-  const double k0 = 1.2533141373155003 * TK_RSQRT(x) / (acc * inv_u0);
-  *kmu = k0;
-  *kmu1 = k0 * (x + mu + 0.5 - (0.25 - mu2) * (u_next * inv_u0)) / x;
+  // K_mu e^x = sqrt(pi / (2 x)) u_0 / acc and
+  // K_{mu+1} e^x = K_mu e^x (x + mu + 1/2 - (1/4 - mu^2) u_1 / u_0) / x
+  //              = sqrt(pi / 2) x^(-1/2) ((x + mu + 1/2) u_0 - (1/4 - mu^2) u_1) / (x acc),
+  // with sqrt(pi / 2) = 1.2533...: one division for both
+  const double w = 1.2533141373155003 * TK_RSQRT(x) / (x * acc);
+  *kmu = w * x * u;
+  *kmu1 = w * fma(x + mu + 0.5, u, -(0.25 - mu2) * u_next);
 }
 
 // K_nu(x) e^x for the order in c (nu = nord + mu), x > 0.
@@ -136,6 +138,7 @@ TK_HD double tk_bessel_k_scaled(const tk_nu_consts& c, double x) {
   double km, kp;
   tk_bessel_k_pair_scaled(c, x, &km, &kp);
   if (c.nord == 0) return km;
+  if (c.nord == 1) return kp;
   const double two_over_x = 2.0 / x;
   for (int k = 1; k < c.nord; ++k) {
     const double kn = km + ((c.mu + (double)k) * two_over_x) * kp;

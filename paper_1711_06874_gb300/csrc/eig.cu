@@ -73,11 +73,12 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // Householder QR of a column-major n x m panel Y in shared memory, with the
-// explicit orthonormal factor Q (n x m, same layout) written to Qs.  Groups
-// of eight lanes own one column each (four columns per warp).  In step j the
-// group owning column j + 1 also takes that column's new squared norm and its
-// reflector scalars, so a step needs one barrier and no block-wide reduction:
-//   v = x + sign(x_0) |x| e_0, beta = 2 / v^T v, H_j = I - beta v v^T.
+// explicit orthonormal factor Q (n x m, same layout) written to Qs.  In step
+// j, H_j = I - beta v v^T with v = x + sign(x_0) |x| e_0, beta = 2 / v^T v,
+// is applied to the columns right of j.  Warp 0 alone (all 32 lanes) updates
+// column j + 1 and takes its new squared norm and reflector scalars, the
+// critical path of the next step; the other warps update columns j + 2 on in
+// groups of eight lanes (four columns per warp).  One barrier per step.
 template <class T>
 __device__ __forceinline__ void reflector(T alpha2, T x0, T& v0, T& beta) {
   if (!(alpha2 > T(0))) {
@@ -99,6 +100,12 @@ __device__ __forceinline__ T group_sum8(T d) {
 }
 
 template <class T>
+__device__ __forceinline__ T warp_sum32(T d) {
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  return d;
+}
+
+template <class T>
 __device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gsub = lane >> 3, l8 = lane & 7;
@@ -106,40 +113,54 @@ __device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
   if (w == 0) {
     T s2 = T(0);
     for (int i = lane; i < n; i += 32) s2 += Y[i] * Y[i];
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s2 = warp_sum32(s2);
     if (lane == 0) reflector(s2, Y[0], v0s[0], beta[0]);
   }
   __syncthreads();
   for (int j = 0; j < m; ++j) {
     const T* y = Y + (long long)j * n;
     const T v0 = v0s[j], bj = beta[j];
-    for (int cb = j + 1 + 4 * w; cb < m; cb += 4 * nw) {
-      const int c = cb + gsub;
-      const bool act = c < m;
-      T* xc = Y + (long long)(act ? c : j + 1) * n;
-      T d = T(0);
-      if (act && bj != T(0)) {
-        if (l8 == 0) d = v0 * xc[j];
-        for (int i = j + 1 + l8; i < n; i += 8) d += y[i] * xc[i];
-      }
-      d = group_sum8(d);
-      const T f = bj * d;
-      T s2 = T(0);
-      if (act) {
+    if (w == 0) {
+      if (j + 1 < m) {
+        T* xc = Y + (long long)(j + 1) * n;
+        T d = T(0);
+        if (bj != T(0)) {
+          if (lane == 0) d = v0 * xc[j];
+          for (int i = j + 1 + lane; i < n; i += 32) d += y[i] * xc[i];
+        }
+        d = warp_sum32(d);
+        const T f = bj * d;
+        T s2 = T(0);
         if (f != T(0)) {
-          if (l8 == 0) xc[j] -= f * v0;
-          for (int i = j + 1 + l8; i < n; i += 8) {
+          if (lane == 0) xc[j] -= f * v0;
+          for (int i = j + 1 + lane; i < n; i += 32) {
             const T x = xc[i] - f * y[i];
             xc[i] = x;
             s2 += x * x;
           }
         } else {
-          for (int i = j + 1 + l8; i < n; i += 8) s2 += xc[i] * xc[i];
+          for (int i = j + 1 + lane; i < n; i += 32) s2 += xc[i] * xc[i];
+        }
+        s2 = warp_sum32(s2);
+        if (lane == 0) reflector(s2, xc[j + 1], v0s[j + 1], beta[j + 1]);
+      }
+    } else if (bj != T(0)) {
+      for (int cb = j + 2 + 4 * (w - 1); cb < m; cb += 4 * (nw - 1)) {
+        const int c = cb + gsub;
+        const bool act = c < m;
+        T* xc = Y + (long long)(act ? c : j) * n;  // an idle group reads column j (read-only here)
+        T d = T(0);
+        if (act) {
+          if (l8 == 0) d = v0 * xc[j];
+          for (int i = j + 1 + l8; i < n; i += 8) d += y[i] * xc[i];
+        }
+        d = group_sum8(d);
+        const T f = bj * d;
+        if (act && f != T(0)) {
+          if (l8 == 0) xc[j] -= f * v0;
+          for (int i = j + 1 + l8; i < n; i += 8) xc[i] -= f * y[i];
         }
       }
-      s2 = group_sum8(s2);
-      // the group of column j + 1 sets that column's reflector for the next step
-      if (c == j + 1 && l8 == 0) reflector(s2, xc[j + 1], v0s[j + 1], beta[j + 1]);
     }
     if (threadIdx.x == 0) Y[(long long)j * n + j] = v0;  // head of v_j, read in the Q phase
     __syncthreads();
@@ -190,7 +211,16 @@ __device__ void qr_body(double* Yg, double* Qg, int n, int m) {
   double* Y = kShared ? qr_sm : Yg;
   double* Q = kShared ? qr_sm + (size_t)n * m : Qg;
   if (kShared) {
-    for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = Yg[e];
+    // eight loads in flight per thread
+    const int tot = n * m, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? Yg[e0 + u * nt] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * nt < tot) Y[e0 + u * nt] = v[u];
+    }
     __syncthreads();
   }
   qr_panel<double>(Y, Q, n, m, beta, v0s);
@@ -209,6 +239,33 @@ __global__ void __launch_bounds__(1024) k_householder_qr_strided(double* Y, doub
   qr_body<kShared>(Y + blockIdx.x * stride, Q + blockIdx.x * stride, n, m);
 }
 
+// Trace of the n x n matrix G by one warp: Neumaier pairs per lane over a
+// fixed stride, then a fixed shuffle tree; lane 0 holds the result.
+__device__ __forceinline__ double trace_warp(const double* G, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0, c = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double x = G[(long long)i * n + i];
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_xor_sync(0xffffffffu, s, o);
+    const double xc = __shfl_xor_sync(0xffffffffu, c, o);
+    const double t = s + x;
+    c += ((fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s) + xc;
+    s = t;
+  }
+  return s + c;
+}
+
+// trace of G + blockIdx.x n^2 (instance of a batch), one warp per instance.
+__global__ void k_trace(const double* G, int n, double* out) {
+  const double t = trace_warp(G + (size_t)blockIdx.x * n * n, n);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
 // ---------------------------------------------------------------------------
 // First pass of the subspace iteration in FP32 (one CTA per instance): G is
 // rounded to FP32 in shared memory, Y = G Omega (Omega from the hash, the
@@ -218,8 +275,10 @@ __global__ void __launch_bounds__(1024) k_householder_qr_strided(double* Y, doub
 // ---------------------------------------------------------------------------
 size_t start32_smem(int n, int ms) { return sizeof(float) * ((size_t)n * n + 2ull * n * ms); }
 
+// Also writes the trace of G to trace[blockIdx.x] when trace is given.
 __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, int n, int ms,
-                                                  unsigned long long seed, double* __restrict__ Q0) {
+                                                  unsigned long long seed, double* __restrict__ Q0,
+                                                  double* __restrict__ trace) {
   extern __shared__ float s32[];
   __shared__ float beta[kMaxM + 1];
   __shared__ float v0s[kMaxM + 1];
@@ -228,7 +287,22 @@ __global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, 
   float* W = Y + n * ms;       // Omega, then Q
   G += (size_t)blockIdx.x * n * n;
   Q0 += (size_t)blockIdx.x * n * ms;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Gs[e] = (float)G[e];
+  if (trace != nullptr && threadIdx.x < 32) {
+    const double t = trace_warp(G, n);
+    if (threadIdx.x == 0) trace[blockIdx.x] = t;
+  }
+  {
+    // eight loads in flight per thread
+    const int tot = n * n, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * nt < tot) Gs[e0 + u * nt] = (float)v[u];
+    }
+  }
   for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = (float)hash_uniform(seed, (unsigned long long)e);
   __syncthreads();
   // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i
@@ -466,28 +540,6 @@ __global__ void k_canonical_sign(double* V, int n, int m) {
   const bool flip = V[(long long)bi[0] * m + col] < 0.0;
   if (flip)
     for (int i = threadIdx.x; i < n; i += blockDim.x) V[(long long)i * m + col] = -V[(long long)i * m + col];
-}
-
-// trace of G + blockIdx.x n^2 (instance of a batch): Neumaier pairs per lane
-// over a fixed stride, then a fixed shuffle tree (one warp).
-__global__ void k_trace(const double* G, int n, double* out) {
-  G += (size_t)blockIdx.x * n * n;
-  const int lane = threadIdx.x;
-  double s = 0.0, c = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const double x = G[(long long)i * n + i];
-    const double t = s + x;
-    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-    s = t;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double x = __shfl_xor_sync(0xffffffffu, s, o);
-    const double xc = __shfl_xor_sync(0xffffffffu, c, o);
-    const double t = s + x;
-    c += ((fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s) + xc;
-    s = t;
-  }
-  if (lane == 0) out[blockIdx.x] = s + c;
 }
 
 __global__ void k_symmetrize(double* H, int m) {
@@ -901,7 +953,13 @@ EigGroup carve_group(double* p, const double* G, int n, int m, int B, double* la
   return g;
 }
 
-void solve_group(const EigGroup& g, int B, cudaStream_t s, Profiler* pf) {
+// The FP32 start (with the trace folded in) serves the subspace path when
+// its shared-memory image fits.
+bool uses_start32(int n, int ms) { return ms != n && start32_smem(n, ms) <= kStart32SmemMax; }
+
+// trace: written by the FP32 start kernel when that path runs (the caller
+// computes it otherwise).
+void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profiler* pf) {
   const int n = g.n, ms = g.ms, m = g.m;
   if (ms == n) {
     // whole matrices: Jacobi directly
@@ -924,9 +982,9 @@ void solve_group(const EigGroup& g, int B, cudaStream_t s, Profiler* pf) {
       d.fixed_order = 1;
       gemm_f64(d, s);
     };
-    if (start32_smem(n, ms) <= kStart32SmemMax) {
+    if (uses_start32(n, ms)) {
       // FP32 pass from the random block, then one FP64 pass
-      k_start32<<<B, 256, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q);
+      k_start32<<<B, 256, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q, trace);
       TK_LAUNCH("k_start32");
       power(g.Q);
       qr();
@@ -980,9 +1038,11 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
   if (B < 1) return;
   set_attrs();
   const EigGroup g = carve_group(scratch, G, n, m, B, lam, V);
-  k_trace<<<B, 32, 0, s>>>(G, n, trace);
-  TK_LAUNCH("k_trace");
-  solve_group(g, B, s, pf);
+  if (!uses_start32(n, g.ms)) {
+    k_trace<<<B, 32, 0, s>>>(G, n, trace);
+    TK_LAUNCH("k_trace");
+  }
+  solve_group(g, B, trace, s, pf);
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }

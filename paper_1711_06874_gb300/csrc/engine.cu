@@ -301,23 +301,27 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     need += carve_bytes<double>(Q * B) + carve_bytes<double>(H * B) + carve_bytes<double>(nparts * B) +
             carve_bytes<double>(B);
   pre.reserve(need + 4096, s);
+  // parameters (up), then the first phase's results (down): kd, eps, ints,
+  // |F|^2 and the phase-A eigenvalues are carved back to back, and the pinned
+  // staging mirrors that layout, so each direction is one copy
   KernelDev* kd = pre.take<KernelDev>(B);
+  double* epsv = pre.take<double>(B);
+  int* ints = pre.take<int>(nint);
+  double* normF2 = pre.take<double>(B);
+  double *lamA[3] = {};
+  for (int a = 0; a < nmodes; ++a) lamA[a] = pre.take<double>((size_t)B * mA[a]);
   double* table = pre.take<double>(std::max<long long>(1, Q * B));
   double* Fh = pre.take<double>(fused ? 1 : H * B);
   double* part = pre.take<double>(nparts * B);
-  double* normF2 = pre.take<double>(B);
-  double* epsv = pre.take<double>(B);
   double* aux = pre.take<double>(B);  // gathered |F|^2 / eps of the escalated instances
-  int* ints = pre.take<int>(nint);
   char* gscr = pre.take<char>(std::max<size_t>(gram_bytes, 1));
   double* escr = pre.take<double>(eig_doubles);
   double* GJ = pre.take<double>((size_t)B * hmax * hmax);
   double* traceB = pre.take<double>(B);
-  double *G[3] = {}, *lamA[3] = {}, *VA[3] = {}, *traceA[3] = {};
+  double *G[3] = {}, *VA[3] = {}, *traceA[3] = {};
   double *lamE[3][2] = {}, *VE[3][2] = {};  // escalation levels (mB, m)
   for (int a = 0; a < nmodes; ++a) {
     G[a] = pre.take<double>((size_t)B * h[a] * h[a]);
-    lamA[a] = pre.take<double>((size_t)B * mA[a]);
     VA[a] = pre.take<double>((size_t)B * h[a] * mA[a]);
     traceA[a] = pre.take<double>(B);
     for (int l = 0; l < 2; ++l) {
@@ -341,10 +345,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
 
   // pinned staging: parameters up; ranks, |F|^2 and eigenvalues down; then
   // the descriptors of the second phase up
-  size_t lam_count = 0;
-  for (int a = 0; a < nmodes; ++a) lam_count += (size_t)B * mA[a];
-  const size_t pin_up = carve_bytes<KernelDev>(B) + carve_bytes<double>(B) + carve_bytes<int>(16 + 6 * B);
-  const size_t pin_down = carve_bytes<int>(12 * B + 1) + carve_bytes<double>(B) + carve_bytes<double>(lam_count);
+  size_t pin_down = carve_bytes<int>(nint) + carve_bytes<double>(B);
+  for (int a = 0; a < nmodes; ++a) pin_down += carve_bytes<double>((size_t)B * mA[a]);
+  const size_t pin_up = carve_bytes<KernelDev>(B) + carve_bytes<double>(B);
   const size_t pin_desc = carve_bytes<int>(B) + carve_bytes<UnfoldDesc>((size_t)B * nmodes) +
                           carve_bytes<CoreDesc>(B) + carve_bytes<int>(1) + carve_bytes<double>(2 * (size_t)B);
   char* pbase = pin.reserve(pin_up + pin_down + pin_desc + 1024);
@@ -356,10 +359,13 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   };
   KernelDev* kdh = (KernelDev*)ptake(sizeof(KernelDev) * B);
   double* epsh = (double*)ptake(sizeof(double) * B);
-  int* ih = (int*)ptake(sizeof(int) * (16 + 6 * B));
-  int* hA = (int*)ptake(sizeof(int) * (12 * B + 1));
+  int* ih = (int*)ptake(sizeof(int) * nint);  // mirrors ints
   double* hnorm = (double*)ptake(sizeof(double) * B);
-  double* hlam = (double*)ptake(sizeof(double) * lam_count);
+  double* hlamA[3] = {};
+  for (int a = 0; a < nmodes; ++a) hlamA[a] = (double*)ptake(sizeof(double) * B * mA[a]);
+  const int* hA = ih + 16 + 6 * B;  // outA
+  if ((char*)hA - (char*)kdh != (char*)outA - (char*)kd || (char*)hnorm - (char*)kdh != (char*)normF2 - (char*)kd)
+    fail(TK_ECUDA, "pinned staging does not mirror the device parameters");
   int* amaph = (int*)ptake(sizeof(int) * B);
   UnfoldDesc* udh = (UnfoldDesc*)ptake(sizeof(UnfoldDesc) * B * nmodes);
   CoreDesc* cdh = (CoreDesc*)ptake(sizeof(CoreDesc) * B);
@@ -374,9 +380,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       ih[16 + 3 * B + a * B + b] = req[b].o.rfix[a];
     }
   }
-  TK_CUDA(cudaMemcpyAsync(kd, kdh, sizeof(KernelDev) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(epsv, epsh, sizeof(double) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(ints, ih, sizeof(int) * (16 + 6 * B), cudaMemcpyHostToDevice, s));
+  // kd, eps and the first 16 + 6 B ints (flag, rmax, rfix) in one copy
+  TK_CUDA(cudaMemcpyAsync(kd, kdh, (size_t)((char*)(ih + 16 + 6 * B) - (char*)kdh), cudaMemcpyHostToDevice, s));
 
   if (pf) pf->begin(TK_STAGE_EVAL, s);
   if (fused) {
@@ -415,26 +420,13 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                     outA + 4 * B * a, s);
     if (pf) pf->end(s);
   }
-  std::vector<std::vector<double>> hlamA(nmodes);
-  TK_CUDA(cudaMemcpyAsync(hA, outA, sizeof(int) * 4 * B * nmodes, cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaMemcpyAsync(&hA[12 * B], errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaMemcpyAsync(hnorm, normF2, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  // ints (flag, ranks), |F|^2 and the eigenvalues in one copy
   {
-    size_t off = 0;
-    for (int a = 0; a < nmodes; ++a) {
-      TK_CUDA(cudaMemcpyAsync(hlam + off, lamA[a], sizeof(double) * B * mA[a], cudaMemcpyDeviceToHost, s));
-      off += (size_t)B * mA[a];
-    }
+    const char* end = (const char*)(lamA[nmodes - 1] + (size_t)B * mA[nmodes - 1]);
+    TK_CUDA(cudaMemcpyAsync(ih, ints, (size_t)(end - (const char*)ints), cudaMemcpyDeviceToHost, s));
   }
   TK_CUDA(cudaStreamSynchronize(s));
-  {
-    size_t off = 0;
-    for (int a = 0; a < nmodes; ++a) {
-      hlamA[a].assign(hlam + off, hlam + off + (size_t)B * mA[a]);
-      off += (size_t)B * mA[a];
-    }
-  }
-  if (hA[12 * B] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+  if (ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
 
   // ---------------- escalation ----------------
   // Instances whose rank rule wants more pairs than a phase computed are
@@ -456,7 +448,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     p0.J.resize(B);
     for (int b = 0; b < B; ++b) p0.J[b] = b;
     p0.out.assign(hA + 4 * B * a, hA + 4 * B * (a + 1));
-    p0.hl = hlamA[a];
+    p0.hl.assign(hlamA[a], hlamA[a] + (size_t)B * mA[a]);
     ph[a].push_back(std::move(p0));
     const int levels[2] = {std::min(m[a], kPhaseB), m[a]};
     for (int l = 0; l < 2; ++l) {
@@ -655,9 +647,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     cdh[b] = CoreDesc{tbase + q.cp + (size_t)pos * q.R * q.R * q.R, rbase + offC[b], q.R, fin[b].r[0], fin[b].r[1],
                       fin[b].r[2]};
   }
-  TK_CUDA(cudaMemcpyAsync(amap, amaph, sizeof(int) * B, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(ud, udh, sizeof(UnfoldDesc) * ndesc, cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaMemcpyAsync(cd, cdh, sizeof(CoreDesc) * B, cudaMemcpyHostToDevice, s));
+  // amap, ud and cd are carved back to back here and in the pinned staging
+  if ((char*)cdh - (char*)amaph != (char*)cd - (char*)amap)
+    fail(TK_ECUDA, "pinned staging does not mirror the device descriptors");
+  TK_CUDA(cudaMemcpyAsync(amap, amaph, (size_t)((char*)(cdh + B) - (char*)amaph), cudaMemcpyHostToDevice, s));
   if (pf) pf->begin(TK_STAGE_RANK, s);
   k_unfold<<<dim3(Rmax, (unsigned)ndesc), 128, 0, s>>>(ud);
   TK_LAUNCH("k_unfold");

@@ -231,18 +231,42 @@ __device__ __forceinline__ double fold_scale(int twos) {
 
 // Distinct values of instance blockIdx.y, times `scale` (one rounding, the
 // same as scaling each gathered value).
-__global__ void k_table_b(const KernelDev* __restrict__ kd, double hstep, int even, long long Q, double* T,
-                          double scale) {
+// The table of instance blockIdx.y.  Values are taken in chunks of 32
+// consecutive q (one warp, similar arguments and so similar cost); small q
+// (small arguments: long recurrences) cost several times more than large q, so
+// chunks go to the W warps of the instance in snake order (round r gives chunk
+// r W + p to warp p for even r and to warp W - 1 - p for odd r), and warp p is
+// warp p / gridDim.x of block p % gridDim.x, so that consecutive chunks (the
+// most expensive ones first) land on different SMs: an SM's FP64 pipe is
+// shared by all of its warps.  Every value depends on its q alone, so the
+// assignment does not change any result.
+constexpr int kTableWarps = 4;  // warps per block
+
+__global__ void __launch_bounds__(32 * kTableWarps) k_table_b(const KernelDev* __restrict__ kd, double hstep,
+                                                             int even, long long Q, double* T, double scale) {
   const int b = blockIdx.y;
   const KernelDev& k = kd[b];
   const double hs = hstep * k.inv_ell[0];
   T += (size_t)b * Q;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
-       q += (long long)gridDim.x * blockDim.x) {
+  const long long W = (long long)gridDim.x * kTableWarps;
+  const long long w = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const long long nch = (Q + 31) / 32;
+  for (long long r = 0; r * W < nch; ++r) {
+    const long long c = r * W + ((r & 1) ? W - 1 - w : w);
+    const long long q = c * 32 + (threadIdx.x & 31);
+    if (c >= nch || q >= Q) continue;
     const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
     const double v = cov_value(k, hs * hs * s);
     T[q] = (scale == 1.0) ? v : v * scale;
   }
+}
+
+// Blocks per instance of k_table_b: one warp per SM sub-partition for a
+// single instance, fewer per instance in a batch (about four chunks per warp).
+static unsigned table_blocks(long long Q, int B) {
+  const long long nch = (Q + 31) / 32;
+  const long long want = (B == 1) ? 152 : (nch + 4 * kTableWarps - 1) / (4 * kTableWarps);
+  return (unsigned)std::max<long long>(1, std::min<long long>(want, (nch + kTableWarps - 1) / kTableWarps));
 }
 
 // Octant of the cubic isotropic grid from the distinct-value table: octant
@@ -353,22 +377,31 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
   const int even = (n % 2 == 0);
   const int ai = 2 * i + even;
   const int ti = even ? 1 : (i > 0);
-  const long long K = (long long)h * h;
-  auto value = [&](long long c) {
-    const int j = (int)(c / h), l = (int)(c - (long long)j * h);
+  const int K = h * h;
+  auto value = [&](int j, int l) {
     const int aj = 2 * j + even, al = 2 * l + even;
     const int sq = ai * ai + aj * aj + al * al;
     const double t = __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2));
     return even ? t : t * fold_scale(ti + (j > 0) + (l > 0));
   };
+  // column c = j h + l advances by blockDim.x per iteration: (j, l) advance
+  // by the quotient and remainder of that stride (no division in the loops)
+  const int dj = (int)blockDim.x / h, dl = (int)blockDim.x - dj * h;
+  const int j0 = (int)threadIdx.x / h, l0 = (int)threadIdx.x - j0 * h;
   // largest |value| by its bits (the order of non-negative doubles), sum of squares
   unsigned long long mx = 0;
   double ss = 0.0;
-  for (long long c = threadIdx.x; c < K; c += blockDim.x) {
-    const double v = value(c);
+  for (int c = threadIdx.x, j = j0, l = l0; c < K; c += blockDim.x) {
+    const double v = value(j, l);
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
     mx = bits > mx ? bits : mx;
     ss = fma(v, v, ss);
+    j += dj;
+    l += dl;
+    if (l >= h) {
+      l -= h;
+      ++j;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long om = __shfl_xor_sync(0xffffffffu, mx, o);
@@ -398,11 +431,17 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
   const int e = eshared;
   const size_t plane = (size_t)h * Kp;
   __nv_bfloat16* Sb = S + (size_t)b * kSlices * plane + (size_t)i * Kp;
-  for (long long c = threadIdx.x; c < Kp; c += blockDim.x) {
+  for (int c = threadIdx.x, j = j0, l = l0; c < Kp; c += blockDim.x) {
     int d[kSlices] = {0, 0, 0, 0, 0, 0};
-    if (c < K && e > -1000) slice_digits(value(c), e, d);
+    if (c < K && e > -1000) slice_digits(value(j, l), e, d);
 #pragma unroll
     for (int s2 = 0; s2 < kSlices; ++s2) Sb[s2 * plane + c] = slice_value(d[s2], s2);
+    j += dj;
+    l += dl;
+    if (l >= h) {
+      l -= h;
+      ++j;
+    }
   }
 }
 
@@ -411,11 +450,10 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   const int n = g.n[0], h = (n + 1) / 2;
   const long long Q = table_size(n);
   const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
-  const long long tb = (Q + 63) / 64;
   if (pf) pf->begin(TK_STAGE_TABLE, s);
   // even n: the table holds the octant values 2 sqrt(2) C directly
-  k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table,
-                                                                            n % 2 == 0 ? 2.8284271247461903 : 1.0);
+  k_table_b<<<dim3(table_blocks(Q, B), B), 32 * kTableWarps, 0, s>>>(kd, hstep, n % 2 == 0, Q, table,
+                                                                     n % 2 == 0 ? 2.8284271247461903 : 1.0);
   TK_LAUNCH("k_table_b");
   if (pf) pf->end(s);
   // rows of h^2 values: wide blocks for long rows (a function of the shape
@@ -439,9 +477,8 @@ void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, dou
     const int n = g.n[0];
     const long long Q = table_size(n);
     const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
-    const long long tb = (Q + 63) / 64;
     if (pf) pf->begin(TK_STAGE_TABLE, s);
-    k_table_b<<<dim3((unsigned)std::min<long long>(tb, 1024), B), 64, 0, s>>>(kd, hstep, n % 2 == 0, Q, table, 1.0);
+    k_table_b<<<dim3(table_blocks(Q, B), B), 32 * kTableWarps, 0, s>>>(kd, hstep, n % 2 == 0, Q, table, 1.0);
     TK_LAUNCH("k_table_b");
     if (pf) pf->end(s);
     k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);

@@ -367,34 +367,53 @@ __global__ void __launch_bounds__(kThreads, 1)
 // G_b[gi][gj] = G_b[gj][gi] = 2^(e_gi + e_gj - 44) sum_split P[b][split][block(gi, gj)][..],
 // gi <= gj, for every instance b (row exponents rowexp[b * n + i]).  The
 // integer partials (each below 2^62) are summed exactly as high and low
-// 32-bit halves and rounded to FP64 once.
+// 32-bit halves and rounded to FP64 once.  SG lanes share one entry, each
+// summing every SG-th split, and combine their integer sums by shuffles
+// (exact, so the result does not depend on SG).
+template <int SG>
 __global__ void k_tc_reduce(const long long* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
                             const int* __restrict__ rowexp, double* __restrict__ G) {
   const long long per = (long long)n * n;
   const long long total = per * B;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const long long r = e - (long long)b * per;
+  const int g = threadIdx.x % SG;
+  const long long stride = (long long)gridDim.x * blockDim.x / SG;
+  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / SG; e - (threadIdx.x % 32) / SG < total;
+       e += stride) {
+    // every lane of a warp runs the shuffles: lanes past the end add zeros
+    const bool live = e < total;
+    const int b = live ? (int)(e / per) : 0;
+    const long long r = live ? e - (long long)b * per : 0;
     const int gi = (int)(r / n), gj = (int)(r % n);
-    if (gi > gj) continue;
-    const int bi = gi / kTM, bj = gj / kTN;
-    const int blk = block_index(bi, bj, nct);
-    const size_t off = (size_t)(gi - bi * kTM) * kTN + (gj - bj * kTN);
+    const bool want = live && gi <= gj;
     long long hi = 0, lo = 0;
-    for (int sp = 0; sp < nsplit; ++sp) {
-      const long long v = P[(((size_t)b * nsplit + sp) * nblocks + blk) * kTM * kTN + off];
-      hi += v >> 32;          // floor(v / 2^32)
-      lo += v & 0xFFFFFFFFLL;  // v - 2^32 floor(v / 2^32), in [0, 2^32)
+    if (want) {
+      const int bi = gi / kTM, bj = gj / kTN;
+      const int blk = block_index(bi, bj, nct);
+      const size_t off = (size_t)(gi - bi * kTM) * kTN + (gj - bj * kTN);
+      const long long* src = P + ((size_t)b * nsplit * nblocks + blk) * kTM * kTN + off;
+      const size_t sstride = (size_t)nblocks * kTM * kTN;
+#pragma unroll 4
+      for (int sp = g; sp < nsplit; sp += SG) {
+        const long long v = src[sp * sstride];
+        hi += v >> 32;           // floor(v / 2^32)
+        lo += v & 0xFFFFFFFFLL;  // v - 2^32 floor(v / 2^32), in [0, 2^32)
+      }
     }
-    hi += lo >> 32;
-    lo &= 0xFFFFFFFFLL;
-    const double sum = fma((double)hi, 4294967296.0, (double)lo);  // one rounding
-    const int ei = rowexp[(size_t)b * n + gi], ej = rowexp[(size_t)b * n + gj];
-    const double v = (ei > -1000 && ej > -1000) ? ldexp(sum, ei + ej - 44) : 0.0;
-    double* Gb = G + (size_t)b * per;
-    Gb[(long long)gi * n + gj] = v;
-    Gb[(long long)gj * n + gi] = v;
+#pragma unroll
+    for (int o = SG / 2; o > 0; o >>= 1) {
+      hi += __shfl_xor_sync(0xffffffffu, hi, o);
+      lo += __shfl_xor_sync(0xffffffffu, lo, o);
+    }
+    if (want && g == 0) {
+      hi += lo >> 32;
+      lo &= 0xFFFFFFFFLL;
+      const double sum = fma((double)hi, 4294967296.0, (double)lo);  // one rounding
+      const int ei = rowexp[(size_t)b * n + gi], ej = rowexp[(size_t)b * n + gj];
+      const double v = (ei > -1000 && ej > -1000) ? ldexp(sum, ei + ej - 44) : 0.0;
+      double* Gb = G + (size_t)b * per;
+      Gb[(long long)gi * n + gj] = v;
+      Gb[(long long)gj * n + gi] = v;
+    }
   }
 }
 
@@ -456,8 +475,13 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
   TK_LAUNCH("k_gram_tc");
   if (pf) pf->end(s);
   const long long total = (long long)p.nrows * p.nrows * B;
-  k_tc_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks,
-                                                                                      p.nrows, B, rowexp, G);
+  if (p.nsplit >= 8) {
+    k_tc_reduce<8><<<(unsigned)std::min<long long>((8 * total + 255) / 256, 8192), 256, 0, s>>>(
+        P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G);
+  } else {
+    k_tc_reduce<1><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(
+        P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G);
+  }
   TK_LAUNCH("k_tc_reduce");
 }
 
