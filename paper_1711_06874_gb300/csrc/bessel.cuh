@@ -42,7 +42,7 @@ inline double tk_rsqrt_host(double x) { return 1.0 / sqrt(x); }
 
 // Terms of Temme's series and of the backward recurrence that are
 // precomputed per order, so the device loops need no division.
-constexpr int kTemmeTerms = 48;   // x <= 1.5 converges in about 25 terms
+constexpr int kTemmeTerms = 48;   // x <= 1.5 needs at most 14 terms
 constexpr int kMillerTerms = 133;  // N = 12 + ceil(180 / x) <= 132 for x > 1.5
 
 struct tk_nu_consts {
@@ -63,44 +63,73 @@ struct tk_nu_consts {
   double Mk[kMillerTerms];        // (k + 1/2)^2 - mu^2, the recurrence's second coefficient
 };
 
-// K_mu(x) and K_{mu+1}(x), both multiplied by e^x, for |mu| <= 1/2, x > 0.
-TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu, double* kmu1) {
+// Cost model.  An FP64 instruction occupies an SM sub-partition's FP64 unit
+// for about as long as 32 lanes take at two lanes per cycle per SM, whatever
+// the number of active lanes, so the routines below count FP64 instructions:
+// no convergence tests inside the loops (term counts come from FP32
+// estimates), no range checks inside the recurrence, one logarithm shared by
+// the series and the prefactor, and the e^x of the scaled functions folded
+// into the prefactor's exponential.
+
+// Temme's series for x <= 1.5, given lx = log(x):
+//   t0 = K_mu(x),  t1 = K_{mu+1}(x) x / 2  (both unscaled).
+// The terms needed for 1e-17 grow from 3 (x = 1e-3) to 12 (x = 1.5); the
+// count 1 + floor(6 + 6.5 sqrt(x)) keeps at least two in hand over
+// |mu| <= 1/2.
+TK_HD void tk_bessel_k_temme(const tk_nu_consts& c, double x, double lx, double* t0, double* t1) {
   const double mu = c.mu;
-  if (x <= 1.5) {
-    // Temme's series (the terms grow like I_mu(x) while K_mu falls like e^-x,
-    // so the series is kept to x <= 1.5 where that cancellation stays small).
-    const double lx = log(2.0 / x);
-    const double sig = mu * lx;
-    const double shs = (fabs(sig) < 1e-8) ? 1.0 + sig * sig / 6.0 : sinh(sig) / sig;
-    double f = c.mupi_sin * (cosh(sig) * c.gam1 + shs * lx * c.gam2);
-    const double e = exp(sig);  // (2/x)^mu
-    double p = 0.5 * e * c.gpmu;
-    double q = 0.5 / e * c.gmmu;
-    double ck = 1.0;
-    const double x2 = 0.25 * x * x;
-    double s0 = f, s1 = p;
-    for (int k = 1; k < kTemmeTerms; ++k) {
-      const double dk = (double)k;
-      f = (dk * f + p + q) * c.inv_k2mu2[k];
-      p *= c.inv_kmmu[k];
-      q *= c.inv_kpmu[k];
-      ck *= x2 * c.inv_k[k];
-      const double d0 = ck * f;
-      const double d1 = ck * (p - dk * f);
-      s0 += d0;
-      s1 += d1;
-      if (fabs(d0) < 1e-17 * fabs(s0) && fabs(d1) < 1e-17 * fabs(s1)) break;
-    }
-    const double ex = exp(x);
-    *kmu = s0 * ex;
-    *kmu1 = s1 * (2.0 / x) * ex;
-    return;
+  const double l2x = 0.69314718055994530942 - lx;  // log(2 / x)
+  const double sig = mu * l2x;
+  const double e = exp(sig);  // (2/x)^mu
+  const double ie = 1.0 / e;
+  // sinh(sig) / sig: its Taylor series where e - 1/e would cancel
+  double shs;
+  if (fabs(sig) < 0.5) {
+    const double t2 = sig * sig;
+    shs = 1.0 / 6402373705728000.0;  // 1 / 18!
+    // sum_{j <= 8} t2^j / (2j + 1)!, Horner from the top term
+    shs = fma(shs, t2, 1.0 / 355687428096000.0);
+    shs = fma(shs, t2, 1.0 / 1307674368000.0);
+    shs = fma(shs, t2, 1.0 / 6227020800.0);
+    shs = fma(shs, t2, 1.0 / 39916800.0);
+    shs = fma(shs, t2, 1.0 / 362880.0);
+    shs = fma(shs, t2, 1.0 / 5040.0);
+    shs = fma(shs, t2, 1.0 / 120.0);
+    shs = fma(shs, t2, 1.0 / 6.0);
+    shs = fma(shs, t2, 1.0);
+  } else {
+    shs = 0.5 * (e - ie) / sig;
   }
-  // Tricomi-U representation, Miller's backward recurrence on the
-  // unnormalised minimal solution u_k (u_{N+1} = 0, u_N = 1), accumulating
-  // sum_k C_k u_k on the way; S = sum / u_0 and U_1/U_0 = u_1 / u_0.
-  // The recurrence reaches 1e-17 with N of about 12 + 180/x terms; values are
-  // rescaled by 2^-600 whenever they pass 2^600.
+  const double ch = 0.5 * (e + ie);  // cosh(sig)
+  double f = c.mupi_sin * (ch * c.gam1 + shs * l2x * c.gam2);
+  double p = 0.5 * e * c.gpmu;
+  double q = 0.5 * ie * c.gmmu;
+  double ck = 1.0;
+  const double x2 = 0.25 * x * x;
+  double s0 = f, s1 = p;
+  const int K = 1 + (int)(6.0f + 6.5f * sqrtf((float)x));
+  double dk = 0.0;
+  for (int k = 1; k <= K; ++k) {
+    dk += 1.0;
+    f = fma(dk, f, p + q) * c.inv_k2mu2[k];
+    p *= c.inv_kmmu[k];
+    q *= c.inv_kpmu[k];
+    ck *= x2 * c.inv_k[k];
+    s0 = fma(ck, f, s0);
+    s1 = fma(ck, fma(-dk, f, p), s1);
+  }
+  *t0 = s0;
+  *t1 = s1;
+}
+
+// K_mu(x) e^x and K_{mu+1}(x) e^x for |mu| <= 1/2, x > 1.5, through the
+// Tricomi-U representation: Miller's backward recurrence on the unnormalised
+// minimal solution u_k (u_{N+1} = 0, u_N = 1), accumulating sum_k C_k u_k on
+// the way; S = sum / u_0 and U_1/U_0 = u_1 / u_0.  The recurrence reaches
+// 1e-17 with N of about 12 + 180/x terms.  |u_k| stays below 1e241 for every
+// N <= 132 (its largest growth is at the smallest x), so no rescaling is needed.
+TK_HD void tk_bessel_k_miller(const tk_nu_consts& c, double x, double* kmu, double* kmu1) {
+  const double mu = c.mu;
   // N = 12 + ceil(180 / x) (at most 132 for x > 1.5) from an FP32 quotient,
   // one step longer so that it is never below the FP64 value
   const int N = 13 + (int)(180.0f / (float)x) < kMillerTerms - 1 ? 13 + (int)(180.0f / (float)x) : kMillerTerms - 1;
@@ -116,13 +145,6 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
     u = u_prev;
     acc = fma(c.Ck[k - 1], u, acc);
     dk2 -= 2.0;
-    // |u| grows by at most 2 (k + x) per step (far below 2^100 for any x the
-    // grids produce): a check every 4 steps keeps it below 2^1000
-    if ((k & 3) == 0 && fabs(u) > 0x1p600) {
-      u *= 0x1p-600;
-      u_next *= 0x1p-600;
-      acc *= 0x1p-600;
-    }
   }
   // K_mu e^x = sqrt(pi / (2 x)) u_0 / acc and
   // K_{mu+1} e^x = K_mu e^x (x + mu + 1/2 - (1/4 - mu^2) u_1 / u_0) / x
@@ -133,12 +155,9 @@ TK_HD void tk_bessel_k_pair_scaled(const tk_nu_consts& c, double x, double* kmu,
   *kmu1 = w * fma(x + mu + 0.5, u, -(0.25 - mu2) * u_next);
 }
 
-// K_nu(x) e^x for the order in c (nu = nord + mu), x > 0.
-TK_HD double tk_bessel_k_scaled(const tk_nu_consts& c, double x) {
-  double km, kp;
-  tk_bessel_k_pair_scaled(c, x, &km, &kp);
-  if (c.nord == 0) return km;
-  if (c.nord == 1) return kp;
+// Forward recurrence K_{m+1} = K_{m-1} + (2m/x) K_m from K_mu, K_{mu+1} up to
+// the order nu = nord + mu (nord >= 2).
+TK_HD double tk_bessel_k_forward(const tk_nu_consts& c, double x, double km, double kp) {
   const double two_over_x = 2.0 / x;
   for (int k = 1; k < c.nord; ++k) {
     const double kn = km + ((c.mu + (double)k) * two_over_x) * kp;
@@ -149,8 +168,26 @@ TK_HD double tk_bessel_k_scaled(const tk_nu_consts& c, double x) {
 }
 
 // Matern covariance at z = sqrt(2 nu) r / ell; C(0) = sigma2 is the limit.
+//   C = sigma2 exp(pref_log + nu log z) K_nu(z),  pref_log = (1 - nu) ln 2 - log Gamma(nu).
 TK_HD double tk_matern_z(const tk_nu_consts& c, double sigma2, double z) {
   if (z <= 0.0) return sigma2;
-  const double lp = c.pref_log + c.nu * log(z) - z;
-  return sigma2 * exp(lp) * tk_bessel_k_scaled(c, z);
+  const double lz = log(z);
+  double lp = c.pref_log + c.nu * lz;
+  if (z <= 1.5) {
+    double t0, t1;
+    tk_bessel_k_temme(c, z, lz, &t0, &t1);
+    if (c.nord == 0) return sigma2 * exp(lp) * t0;
+    // K_{mu+1} = t1 (2 / z): the factor goes into the exponent
+    if (c.nord == 1) return sigma2 * exp(lp + 0.69314718055994530942 - lz) * t1;
+    return sigma2 * exp(lp) * tk_bessel_k_forward(c, z, t0, t1 * (2.0 / z));
+  }
+  lp -= z;  // the e^z of the scaled functions
+  // exp(lp) is zero below -745: the value is 0 (and the recurrence is never
+  // run on arguments that large)
+  if (lp < -800.0) return 0.0;
+  double km, kp;
+  tk_bessel_k_miller(c, z, &km, &kp);
+  if (c.nord == 0) return sigma2 * exp(lp) * km;
+  if (c.nord == 1) return sigma2 * exp(lp) * kp;
+  return sigma2 * exp(lp) * tk_bessel_k_forward(c, z, km, kp);
 }
