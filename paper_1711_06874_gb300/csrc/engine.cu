@@ -275,6 +275,12 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   // the first TTM read the slices)
   const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0;
   const bool with_err = key.err != 0;
+  // the error of a fused solve is taken against the Gram's slices in
+  // float-float arithmetic (FP32 range: every sigma2 within 2^-60 .. 2^60);
+  // otherwise against a second FP64 sampling on a side stream
+  bool err_ff = with_err && fused;
+  for (int b = 0; b < B && err_ff; ++b)
+    err_ff = req[b].k.sigma2 >= 0x1p-60 && req[b].k.sigma2 <= 0x1p60;
   const size_t nparts = std::max<size_t>(eval_octant_parts(g), (size_t)h[0]);
   size_t gram_bytes = 0, eig_doubles = 0;
   for (int a = 0; a < nmodes; ++a) {
@@ -392,7 +398,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
   }
   if (pf) pf->end(s);
-  if (with_err) {
+  if (with_err && !err_ff) {
     // the error's own sampling of F, on the side stream while the Gram and the
     // eigenpairs (a few SMs) run
     side.ensure(ctx->device);
@@ -606,13 +612,17 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       if (q.R <= 96) ttm_scr = std::max(ttm_scr, ttm_sliced_scratch_bytes(h[2], q.R, q.cnt));
   size_t errw = 0;  // W1, W2 of every group, for the error
   const size_t eparts = err_lowrank_partials(h[0] * h[1], h[2]);
+  size_t eff_scr = 0;  // float-float error scratch (largest group)
   if (with_err)
-    for (const GroupBuf& q : gb)
+    for (const GroupBuf& q : gb) {
       errw += (((size_t)q.cnt * h[0] * q.R * q.R + 31) & ~size_t(31)) + (((size_t)q.cnt * h[0] * h[1] * q.R + 31) & ~size_t(31));
+      if (err_ff && err_sliced_supported(h[0], q.R))
+        eff_scr = std::max(eff_scr, err_sliced_scratch_bytes(h[0], q.R, q.cnt));
+    }
   post.reserve(carve_bytes<double>(ttm) + carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
                    carve_bytes<CoreDesc>(B) + carve_bytes<char>(ttm_scr) +
                    (with_err ? carve_bytes<double>(errw) + carve_bytes<double>((size_t)B * eparts) +
-                                   carve_bytes<double>(2 * (size_t)B)
+                                   carve_bytes<double>(2 * (size_t)B) + carve_bytes<char>(eff_scr)
                              : 0) +
                    4096,
                s);
@@ -621,6 +631,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   double* ewbase = with_err ? post.take<double>(std::max<size_t>(errw, 1)) : nullptr;
   double* epart = with_err ? post.take<double>((size_t)B * eparts) : nullptr;
   double* esum = with_err ? post.take<double>(2 * (size_t)B) : nullptr;
+  char* effscr = (with_err && eff_scr) ? post.take<char>(eff_scr) : nullptr;
   int* amap = post.take<int>(B);
   UnfoldDesc* ud = post.take<UnfoldDesc>(ndesc);
   CoreDesc* cd = post.take<CoreDesc>(B);
@@ -696,7 +707,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     // X = B x_1 V_1 x_2 V_2 x_3 V_3 against the independent sampling, per
     // rank group with the zero-padded factors (the padding adds exact zeros)
     if (pf) pf->begin(TK_STAGE_ERROR, s);
-    TK_CUDA(cudaStreamWaitEvent(s, side.done, 0));
+    if (!err_ff) TK_CUDA(cudaStreamWaitEvent(s, side.done, 0));
+    bool fh_ready = !err_ff;  // the second sampling exists
     size_t woff = 0;
     for (const GroupBuf& q : gb) {
       const int R = q.R;
@@ -713,6 +725,15 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                   (long long)R * R, 1, W1, (long long)h[0] * R * R, (long long)R * R, 1};
       e1.fixed_order = 1;
       gemm_f64(e1, s);
+      if (err_ff && err_sliced_supported(h[0], R)) {
+        err_sliced_batch(sv, normF2, Up0, W1, h[0], R, q.cnt, amap + q.off, effscr, esum + 2 * (size_t)q.off, s);
+        continue;
+      }
+      if (!fh_ready) {
+        // a rank beyond the float-float kernel's range: sample F in FP64 now
+        eval_octant_f64(kd, tab, g, B, FhE, tableE, partE, normE, s);
+        fh_ready = true;
+      }
       // W2[(i,k)][c] = sum_b V2[k][b] W1[i][b][c], one product per (instance, i)
       GemmDesc e2{h[1], R, R, q.cnt * h[0], Up1, (long long)h[1] * R, R, 1, W1, (long long)h[0] * R * R, R, 1,
                   W2, (long long)h[0] * h[1] * R, R, 1};
