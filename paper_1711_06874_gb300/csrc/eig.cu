@@ -192,6 +192,204 @@ __device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
   }
 }
 
+// FP64 Householder factorisation for panels of at most 256 rows, with the
+// explicit factor formed by a second kernel over several SMs.  An FP64 warp
+// instruction occupies a sub-partition's FP64 unit for about 64 cycles
+// whatever the number of active lanes, so each step's critical path (column
+// j + 1, warp 0) keeps its rows in registers (kRPL = ceil(n / 32) per lane)
+// and carries no tests; the other warps take the columns j + 2 on in groups
+// of eight lanes.  On return Y holds the reflectors (v_j in rows j.. of
+// column j, head included) and betas[j] their scalars.
+template <int kRPL>
+__device__ void qr_factor64(double* Y, int n, int m, double* betas, double* beta, double* v0s) {
+  constexpr int kG = 4 * kRPL;  // rows per lane of an eight-lane group
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gsub = lane >> 3, l8 = lane & 7;
+  if (w == 0) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      const int i = lane + 32 * t;
+      const double x = (i < n) ? Y[i] : 0.0;
+      s2 = fma(x, x, s2);
+    }
+    s2 = warp_sum32(s2);
+    if (lane == 0) reflector(s2, Y[0], v0s[0], beta[0]);
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const double* y = Y + (long long)j * n;
+    const double v0 = v0s[j], bj = beta[j];
+    if (w == 0) {
+      if (j + 1 < m) {
+        double* xc = Y + (long long)(j + 1) * n;
+        double yv[kRPL], xv[kRPL];
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t) {
+          const int i = j + 1 + lane + 32 * t;
+          yv[t] = (i < n) ? y[i] : 0.0;
+          xv[t] = (i < n) ? xc[i] : 0.0;
+        }
+        const double head = (lane == 0) ? xc[j] : 0.0;
+        double d = v0 * head;
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t) d = fma(yv[t], xv[t], d);
+        d = warp_sum32(d);
+        const double f = bj * d;
+        if (lane == 0) xc[j] = fma(-f, v0, head);
+        double s2 = 0.0;
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t) {
+          const int i = j + 1 + lane + 32 * t;
+          xv[t] = fma(-f, yv[t], xv[t]);
+          s2 = fma(xv[t], xv[t], s2);
+          if (i < n) xc[i] = xv[t];
+        }
+        s2 = warp_sum32(s2);
+        if (lane == 0) reflector(s2, xv[0], v0s[j + 1], beta[j + 1]);  // xv[0] of lane 0: row j + 1
+      }
+    } else {
+      for (int cb = j + 2 + 4 * (w - 1); cb < m; cb += 4 * (nw - 1)) {
+        const int c = cb + gsub;
+        const bool act = c < m;
+        double* xc = Y + (long long)(act ? c : j) * n;  // an idle group reads column j (read-only here)
+        double yv[kG], xv[kG];
+#pragma unroll
+        for (int t = 0; t < kG; ++t) {
+          const int i = j + 1 + l8 + 8 * t;
+          const bool in = act && i < n;
+          yv[t] = in ? y[i] : 0.0;
+          xv[t] = in ? xc[i] : 0.0;
+        }
+        const double head = (act && l8 == 0) ? xc[j] : 0.0;
+        double d = v0 * head;
+#pragma unroll
+        for (int t = 0; t < kG; ++t) d = fma(yv[t], xv[t], d);
+        d = group_sum8(d);
+        const double f = bj * d;
+        if (act) {
+          if (l8 == 0) xc[j] = fma(-f, v0, head);
+#pragma unroll
+          for (int t = 0; t < kG; ++t) {
+            const int i = j + 1 + l8 + 8 * t;
+            if (i < n) xc[i] = fma(-f, yv[t], xv[t]);
+          }
+        }
+      }
+    }
+    if (threadIdx.x == 0) Y[(long long)j * n + j] = v0;  // head of v_j
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) betas[j] = beta[j];
+}
+
+// One panel per CTA: Y + b sY (n x m, column-major) in shared memory,
+// reflectors written back in place, scalars to betas + b sB.
+template <int kRPL>
+__global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, int n, int m, long long sY, long long sB) {
+  extern __shared__ double qf_sm[];
+  __shared__ double beta[kMaxM + 1];
+  __shared__ double v0s[kMaxM + 1];
+  Y += blockIdx.x * sY;
+  betas += blockIdx.x * sB;
+  {
+    // eight loads in flight per thread
+    const int tot = n * m, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? Y[e0 + u * nt] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * nt < tot) qf_sm[e0 + u * nt] = v[u];
+    }
+  }
+  __syncthreads();
+  qr_factor64<kRPL>(qf_sm, n, m, betas, beta, v0s);
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = qf_sm[e];
+}
+
+// Q = H_0 ... H_{m-1} [I; 0] column by column: column c is H_0 ... H_c e_c
+// (H_j e_c = e_c for j > c), one warp per column, four columns per CTA, so
+// the columns run on several SMs with no barrier between reflectors.  The
+// CTA keeps the reflectors it needs (0 .. its last column) in shared memory
+// with the rows above each head zeroed.  Instance blockIdx.y.
+template <int kRPL>
+__global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, const double* __restrict__ betas,
+                                                 double* __restrict__ Q, int n, int m, long long sY, long long sB,
+                                                 long long sQ) {
+  extern __shared__ double fq_sm[];
+  __shared__ double bs[kMaxM + 1];
+  Y += blockIdx.y * sY;
+  betas += blockIdx.y * sB;
+  Q += blockIdx.y * sQ;
+  const int c0 = blockIdx.x * 4;
+  const int cmax = min(m - 1, c0 + 3);
+  for (int e = threadIdx.x; e < (cmax + 1) * n; e += blockDim.x) {
+    const int j = e / n, i = e - j * n;
+    fq_sm[e] = (i >= j) ? Y[(long long)j * n + i] : 0.0;
+  }
+  for (int j = threadIdx.x; j <= cmax; j += blockDim.x) bs[j] = betas[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, c = c0 + (threadIdx.x >> 5);
+  if (c > cmax) return;
+  double q[kRPL];
+#pragma unroll
+  for (int t = 0; t < kRPL; ++t) q[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
+  for (int j = c; j >= 0; --j) {
+    const double* v = fq_sm + (long long)j * n;
+    double vv[kRPL];
+    double d = 0.0;
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      const int i = lane + 32 * t;
+      vv[t] = (i < n) ? v[i] : 0.0;
+      d = fma(vv[t], q[t], d);
+    }
+    d = warp_sum32(d);
+    const double f = bs[j] * d;
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) q[t] = fma(-f, vv[t], q[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < kRPL; ++t) {
+    const int i = lane + 32 * t;
+    if (i < n) Q[(long long)c * n + i] = q[t];
+  }
+}
+
+// Factorisation and factor of B panels (n x m at Y + b n m), the scalars in
+// betas + b sB, Q at Q + b n m; false when the shape is outside these kernels.
+template <int kRPL>
+void qr64_launch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
+  const size_t f_smem = sizeof(double) * (size_t)n * m;
+  const size_t q_smem = sizeof(double) * (size_t)n * std::min(m, 4 * ((m + 3) / 4));
+  once_per_device((const void*)&k_qr_factor64<kRPL>, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_qr_factor64<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    TK_CUDA(cudaFuncSetAttribute(k_form_q<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  k_qr_factor64<kRPL><<<B, 256, f_smem, s>>>(Y, betas, n, m, (long long)n * m, sB);
+  TK_LAUNCH("k_qr_factor64");
+  k_form_q<kRPL><<<dim3((m + 3) / 4, B), 128, q_smem, s>>>(Y, betas, Q, n, m, (long long)n * m, sB,
+                                                           (long long)n * m);
+  TK_LAUNCH("k_form_q");
+}
+
+bool qr64_batch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
+  if (n > 256 || sizeof(double) * (size_t)n * m > 200 * 1024) return false;
+  switch ((n + 31) / 32) {
+    case 1: qr64_launch<1>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 2: qr64_launch<2>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 3: qr64_launch<3>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 4: qr64_launch<4>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 5: qr64_launch<5>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 6: qr64_launch<6>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 7: qr64_launch<7>(Y, betas, Q, n, m, B, sB, s); return true;
+    case 8: qr64_launch<8>(Y, betas, Q, n, m, B, sB, s); return true;
+    default: return false;
+  }
+}
+
 // The panel Y (n x m) and the factor Q live in shared memory when 2 n m
 // doubles fit (otherwise in global memory).
 struct QrProb {
@@ -356,6 +554,66 @@ struct JacBatch {
   JacProb p[2];  // one problem per CTA
 };
 
+// Bit-level tests and conversions on the ALU pipes: GB300 spends about 64
+// sub-partition cycles on every FP64 warp instruction, compares included.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool is_zero_d(double x) { return abs_bits(x) == 0; }
+// Monotone integer key of a double (non-NaN): larger value, larger key.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
+}
+// x 2^-e as a float, truncated (steering only; zero below the float range).
+__device__ __forceinline__ float scaled_float(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int fe = ex - 1023 - e + 127;
+  if (ex == 0 || fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+}
+// A normal float (or zero) as the equal double.
+__device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// FP64 (c, s) with c^2 + s^2 = 1 to FP64 rounding from an FP32 rotation
+// (cf, sf): with delta = cf^2 + sf^2 - 1 (|delta| < 2^-21), c = cf (1 - kappa),
+// s = sf (1 - kappa), kappa = delta/2 - 3 delta^2/8 (the next term of
+// (1 + delta)^(-1/2) is below 2^-62).  delta and kappa are formed exactly
+// enough in float pairs (exact products, Knuth's two-sum), leaving two FP64
+// fused multiply-adds per value.
+__device__ __forceinline__ void exact_rotation(float cf, float sf, double& c, double& s) {
+  const float p1 = cf * cf, e1 = fmaf(cf, cf, -p1);
+  const float p2 = sf * sf, e2 = fmaf(sf, sf, -p2);
+  float sg, tg;
+  two_sum_f(p1, p2, sg, tg);
+  const float dh = sg - 1.0f;  // exact: sg lies within a factor 2 of 1
+  float u1, u2, w1, w2, dhi, dlo;
+  two_sum_f(tg, e1, u1, u2);
+  two_sum_f(u1, e2, w1, w2);
+  two_sum_f(dh, w1, dhi, dlo);
+  dlo += u2 + w2;
+  const float khi = 0.5f * dhi;
+  const float klo = fmaf(-0.375f * dhi, dhi, 0.5f * dlo);
+  const double c0 = float_to_double_bits(cf), s0 = float_to_double_bits(sf);
+  const double kh = float_to_double_bits(khi), kl = float_to_double_bits(klo);
+  c = fma(-c0, kl, fma(-c0, kh, c0));
+  s = fma(-s0, kl, fma(-s0, kh, s0));
+}
+
 __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, double* Vout, int* sweeps_out) {
   extern __shared__ double sm[];
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
@@ -376,8 +634,9 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   double fs = 0.0;
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) fs += A[e] * A[e];
   const double normA = sqrt(block_sum(fs, red));
-  const double tau = 0x1p-53 * normA;
-  const double noise_diag = 0x1p-47 * normA;  // 64 u |A|_F
+  // thresholds as bit patterns: |x| > t  <=>  abs_bits(x) > bits(t) for t >= 0
+  const unsigned long long tau_b = abs_bits(0x1p-53 * normA);
+  const unsigned long long noise_b = abs_bits(0x1p-47 * normA);  // 64 u |A|_F
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
     // a sweep runs only while some plane still needs a rotation (one pass over
@@ -385,8 +644,8 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
     int need = 0;
     for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
       const int i = e / mp, j = e - (e / mp) * mp;
-      if (i < j && fabs(A[e]) > tau &&
-          !(fabs(A[i * mp + i]) <= noise_diag && fabs(A[j * mp + j]) <= noise_diag))
+      if (i < j && abs_bits(A[e]) > tau_b &&
+          !(abs_bits(A[i * mp + i]) <= noise_b && abs_bits(A[j * mp + j]) <= noise_b))
         need = 1;
     }
     if (!__syncthreads_or(need)) break;
@@ -402,31 +661,23 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
         const int p = min(a, b), q = max(a, b);
         pp[k] = p;
         qq[k] = q;
-        const double apq = A[p * mp + q];
+        const double apq = A[p * mp + q], app = A[p * mp + p], aqq = A[q * mp + q];
         double c = 1.0, s = 0.0;
         // two indices whose diagonals both lie in the rounding noise of the
         // matrix are left alone: their eigenvectors carry no information
-        const bool noise = fabs(A[p * mp + p]) <= noise_diag && fabs(A[q * mp + q]) <= noise_diag;
-        if (fabs(apq) > tau && !noise) {
-          // The angle only steers convergence, so it is taken in FP32; (c, s)
-          // are then made orthonormal to FP64 precision by two Newton steps on
-          // c^2 + s^2 = 1, so the rotation applied is exactly orthogonal.
-          // scale by 2^-e (e the exponent of a_pq) so both fit FP32 at any |A|
-          const int e = ((__double2hiint(apq) >> 20) & 0x7FF) - 1023;
-          const double sc = __hiloint2double((1023 - e) << 20, 0);
-          const float theta = (float)((A[q * mp + q] - A[p * mp + p]) * sc) / (2.0f * (float)(apq * sc));
+        const bool noise = abs_bits(app) <= noise_b && abs_bits(aqq) <= noise_b;
+        if (abs_bits(apq) > tau_b && !noise) {
+          // The angle only steers convergence, so it is taken in FP32 from
+          // (a_qq - a_pp) and a_pq scaled by 2^-e (e the exponent of a_pq);
+          // (c, s) are then made orthonormal to FP64 precision, so the
+          // rotation applied is exactly orthogonal.
+          const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
+          const float theta = scaled_float(aqq - app, e) / (2.0f * scaled_float(apq, e));
           const float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
           const float cf = rsqrtf(fmaf(t, t, 1.0f));
-          c = (double)cf;
-          s = (double)(t * cf);
-#pragma unroll
-          for (int it = 0; it < 2; ++it) {
-            const double g = fma(c, c, s * s);
-            const double k = fma(-0.5, g, 1.5);
-            c *= k;
-            s *= k;
-          }
-          if (s != 0.0) *flag = 1;
+          const float sf = t * cf;
+          exact_rotation(cf, sf, c, s);
+          if (sf != 0.0f) *flag = 1;
         }
         cs[2 * k] = c;
         cs[2 * k + 1] = s;
@@ -444,7 +695,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           }
           const int b = a + r;
           const double ca = cs[2 * a], sa = cs[2 * a + 1], cb = cs[2 * b], sb = cs[2 * b + 1];
-          if (sa == 0.0 && sb == 0.0) continue;
+          if (is_zero_d(sa) && is_zero_d(sb)) continue;
           const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
           const double m00 = A[pa * mp + pb], m01 = A[pa * mp + qb], m10 = A[qa * mp + pb], m11 = A[qa * mp + qb];
           // rows: [c -s; s c] M
@@ -453,7 +704,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           // columns: (.) [c s; -s c]
           double n00 = cb * r00 - sb * r01, n01 = sb * r00 + cb * r01;
           double n10 = cb * r10 - sb * r11, n11 = sb * r10 + cb * r11;
-          if (a == b) n01 = n10 = 0.5 * (n01 + n10);  // keep the block exactly symmetric
+          if (a == b) n10 = n01;  // keep the block exactly symmetric
           A[pa * mp + pb] = n00;
           A[pa * mp + qb] = n01;
           A[qa * mp + pb] = n10;
@@ -468,7 +719,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           const int f = e - nblk;
           const int k = f / mp, row = f % mp;
           const double s = cs[2 * k + 1];
-          if (s == 0.0) continue;
+          if (is_zero_d(s)) continue;
           const double c = cs[2 * k];
           const int p = pp[k], q = qq[k];
           const double vp = V[row * mp + p], vq = V[row * mp + q];
@@ -484,13 +735,13 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   }
   // sort descending by rank counting (ties by index), drop the pad
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double li = A[i * mp + i];
+    const long long li = order_key(A[i * mp + i]);
     int pos = 0;
     for (int j = 0; j < m; ++j) {
-      const double lj = A[j * mp + j];
+      const long long lj = order_key(A[j * mp + j]);
       pos += (lj > li) || (lj == li && j < i);
     }
-    lam[pos] = li;
+    lam[pos] = A[i * mp + i];
     for (int r = 0; r < m; ++r) Vout[r * m + pos] = V[r * mp + i];
   }
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
@@ -969,11 +1220,14 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     const size_t need = 2ull * n * ms * sizeof(double);
     auto qr = [&]() {
       if (pf) pf->begin(TK_STAGE_QR, s);
-      if (need <= kQrSmemMax)
-        k_householder_qr_strided<true><<<B, 256, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
-      else
-        k_householder_qr_strided<false><<<B, 256, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
-      TK_LAUNCH("k_householder_qr_strided");
+      // the scalars go to H's storage, which the Rayleigh-Ritz step fills later
+      if (!qr64_batch(g.Y, g.H, g.Q, n, ms, B, (long long)ms * ms, s)) {
+        if (need <= kQrSmemMax)
+          k_householder_qr_strided<true><<<B, 256, need, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
+        else
+          k_householder_qr_strided<false><<<B, 256, 0, s>>>(g.Y, g.Q, n, ms, (long long)n * ms);
+        TK_LAUNCH("k_householder_qr_strided");
+      }
       if (pf) pf->end(s);
     };
     auto power = [&](const double* src) {  // Y = G src
