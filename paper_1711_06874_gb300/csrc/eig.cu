@@ -192,25 +192,27 @@ __device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
   }
 }
 
-// FP64 Householder factorisation for panels of at most 256 rows, with the
-// explicit factor formed by a second kernel over several SMs.  An FP64 warp
-// instruction occupies a sub-partition's FP64 unit for about 64 cycles
-// whatever the number of active lanes, so each step's critical path (column
-// j + 1, warp 0) keeps its rows in registers (kRPL = ceil(n / 32) per lane)
-// and carries no tests; the other warps take the columns j + 2 on in groups
-// of eight lanes.  On return Y holds the reflectors (v_j in rows j.. of
-// column j, head included) and betas[j] their scalars.
-template <int kRPL>
-__device__ void qr_factor64(double* Y, int n, int m, double* betas, double* beta, double* v0s) {
+// Householder factorisation of a panel of at most 256 rows held in shared
+// memory (column stride ld), FP64 for the subspace pass and FP32 for the
+// start.  An FP64 warp instruction occupies a sub-partition's FP64 unit for
+// about 64 cycles whatever the number of active lanes, so each step's
+// critical path (column j + 1, warp 0) keeps its rows in registers
+// (kRPL = ceil(n / 32) per lane) and carries no tests; the other warps take
+// the columns j + 2 on in groups of eight lanes.  ld is padded so that the
+// four groups of a warp read different shared-memory banks.  On return Y
+// holds the reflectors (v_j in rows j.. of column j, head included) and
+// betas[j] their scalars.
+template <class T, int kRPL>
+__device__ void qr_factor_reg(T* Y, int ld, int n, int m, T* betas, T* beta, T* v0s) {
   constexpr int kG = 4 * kRPL;  // rows per lane of an eight-lane group
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gsub = lane >> 3, l8 = lane & 7;
   if (w == 0) {
-    double s2 = 0.0;
+    T s2 = T(0);
 #pragma unroll
     for (int t = 0; t < kRPL; ++t) {
       const int i = lane + 32 * t;
-      const double x = (i < n) ? Y[i] : 0.0;
+      const T x = (i < n) ? Y[i] : T(0);
       s2 = fma(x, x, s2);
     }
     s2 = warp_sum32(s2);
@@ -218,26 +220,26 @@ __device__ void qr_factor64(double* Y, int n, int m, double* betas, double* beta
   }
   __syncthreads();
   for (int j = 0; j < m; ++j) {
-    const double* y = Y + (long long)j * n;
-    const double v0 = v0s[j], bj = beta[j];
+    const T* y = Y + (long long)j * ld;
+    const T v0 = v0s[j], bj = beta[j];
     if (w == 0) {
       if (j + 1 < m) {
-        double* xc = Y + (long long)(j + 1) * n;
-        double yv[kRPL], xv[kRPL];
+        T* xc = Y + (long long)(j + 1) * ld;
+        T yv[kRPL], xv[kRPL];
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) {
           const int i = j + 1 + lane + 32 * t;
-          yv[t] = (i < n) ? y[i] : 0.0;
-          xv[t] = (i < n) ? xc[i] : 0.0;
+          yv[t] = (i < n) ? y[i] : T(0);
+          xv[t] = (i < n) ? xc[i] : T(0);
         }
-        const double head = (lane == 0) ? xc[j] : 0.0;
-        double d = v0 * head;
+        const T head = (lane == 0) ? xc[j] : T(0);
+        T d = v0 * head;
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) d = fma(yv[t], xv[t], d);
         d = warp_sum32(d);
-        const double f = bj * d;
+        const T f = bj * d;
         if (lane == 0) xc[j] = fma(-f, v0, head);
-        double s2 = 0.0;
+        T s2 = T(0);
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) {
           const int i = j + 1 + lane + 32 * t;
@@ -252,21 +254,21 @@ __device__ void qr_factor64(double* Y, int n, int m, double* betas, double* beta
       for (int cb = j + 2 + 4 * (w - 1); cb < m; cb += 4 * (nw - 1)) {
         const int c = cb + gsub;
         const bool act = c < m;
-        double* xc = Y + (long long)(act ? c : j) * n;  // an idle group reads column j (read-only here)
-        double yv[kG], xv[kG];
+        T* xc = Y + (long long)(act ? c : j) * ld;  // an idle group reads column j (read-only here)
+        T yv[kG], xv[kG];
 #pragma unroll
         for (int t = 0; t < kG; ++t) {
           const int i = j + 1 + l8 + 8 * t;
           const bool in = act && i < n;
-          yv[t] = in ? y[i] : 0.0;
-          xv[t] = in ? xc[i] : 0.0;
+          yv[t] = in ? y[i] : T(0);
+          xv[t] = in ? xc[i] : T(0);
         }
-        const double head = (act && l8 == 0) ? xc[j] : 0.0;
-        double d = v0 * head;
+        const T head = (act && l8 == 0) ? xc[j] : T(0);
+        T d = v0 * head;
 #pragma unroll
         for (int t = 0; t < kG; ++t) d = fma(yv[t], xv[t], d);
         d = group_sum8(d);
-        const double f = bj * d;
+        const T f = bj * d;
         if (act) {
           if (l8 == 0) xc[j] = fma(-f, v0, head);
 #pragma unroll
@@ -277,10 +279,17 @@ __device__ void qr_factor64(double* Y, int n, int m, double* betas, double* beta
         }
       }
     }
-    if (threadIdx.x == 0) Y[(long long)j * n + j] = v0;  // head of v_j
+    if (threadIdx.x == 0) Y[(long long)j * ld + j] = v0;  // head of v_j
     __syncthreads();
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) betas[j] = beta[j];
+}
+
+// Column stride of a panel in shared memory: a group of eight lanes reads
+// 8 consecutive entries, and the four groups of a warp read four columns.
+template <class T>
+__host__ __device__ constexpr int panel_ld(int n) {
+  return sizeof(T) == 8 ? n + ((8 - n % 16) + 16) % 16 : n + ((8 - n % 32) + 32) % 32;
 }
 
 // One panel per CTA: Y + b sY (n x m, column-major) in shared memory,
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, i
   __shared__ double v0s[kMaxM + 1];
   Y += blockIdx.x * sY;
   betas += blockIdx.x * sB;
+  const int ld = panel_ld<double>(n);
   {
     // eight loads in flight per thread
     const int tot = n * m, nt = blockDim.x;
@@ -300,13 +310,15 @@ __global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, i
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? Y[e0 + u * nt] : 0.0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (e0 + u * nt < tot) qf_sm[e0 + u * nt] = v[u];
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nt;
+        if (e < tot) qf_sm[(e / n) * ld + e % n] = v[u];
+      }
     }
   }
   __syncthreads();
-  qr_factor64<kRPL>(qf_sm, n, m, betas, beta, v0s);
-  for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = qf_sm[e];
+  qr_factor_reg<double, kRPL>(qf_sm, ld, n, m, betas, beta, v0s);
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) Y[e] = qf_sm[(e / n) * ld + e % n];
 }
 
 // Q = H_0 ... H_{m-1} [I; 0] column by column: column c is H_0 ... H_c e_c
@@ -325,9 +337,19 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
   Q += blockIdx.y * sQ;
   const int c0 = blockIdx.x * 4;
   const int cmax = min(m - 1, c0 + 3);
-  for (int e = threadIdx.x; e < (cmax + 1) * n; e += blockDim.x) {
-    const int j = e / n, i = e - j * n;
-    fq_sm[e] = (i >= j) ? Y[(long long)j * n + i] : 0.0;
+  {
+    // eight loads in flight per thread
+    const int tot = (cmax + 1) * n, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? Y[e0 + u * nt] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nt;
+        if (e < tot) fq_sm[e] = (e % n >= e / n) ? v[u] : 0.0;
+      }
+    }
   }
   for (int j = threadIdx.x; j <= cmax; j += blockDim.x) bs[j] = betas[j];
   __syncthreads();
@@ -362,7 +384,7 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
 // betas + b sB, Q at Q + b n m; false when the shape is outside these kernels.
 template <int kRPL>
 void qr64_launch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
-  const size_t f_smem = sizeof(double) * (size_t)n * m;
+  const size_t f_smem = sizeof(double) * (size_t)panel_ld<double>(n) * m;
   const size_t q_smem = sizeof(double) * (size_t)n * std::min(m, 4 * ((m + 3) / 4));
   once_per_device((const void*)&k_qr_factor64<kRPL>, [] {
     TK_CUDA(cudaFuncSetAttribute(k_qr_factor64<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -376,7 +398,7 @@ void qr64_launch(double* Y, double* betas, double* Q, int n, int m, int B, long 
 }
 
 bool qr64_batch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
-  if (n > 256 || sizeof(double) * (size_t)n * m > 200 * 1024) return false;
+  if (n > 256 || sizeof(double) * (size_t)panel_ld<double>(n) * m > 200 * 1024) return false;
   switch ((n + 31) / 32) {
     case 1: qr64_launch<1>(Y, betas, Q, n, m, B, sB, s); return true;
     case 2: qr64_launch<2>(Y, betas, Q, n, m, B, sB, s); return true;
@@ -471,89 +493,6 @@ __global__ void k_trace(const double* G, int n, double* out) {
 // the start block Q0 (written in FP64, column-major n x ms) of the FP64 pass.
 // Only its span matters, and the FP64 pass that follows fixes its accuracy.
 // ---------------------------------------------------------------------------
-size_t start32_smem(int n, int ms) { return sizeof(float) * ((size_t)n * n + 2ull * n * ms); }
-
-// Also writes the trace of G to trace[blockIdx.x] when trace is given.
-__global__ void __launch_bounds__(1024) k_start32(const double* __restrict__ G, int n, int ms,
-                                                  unsigned long long seed, double* __restrict__ Q0,
-                                                  double* __restrict__ trace) {
-  extern __shared__ float s32[];
-  __shared__ float beta[kMaxM + 1];
-  __shared__ float v0s[kMaxM + 1];
-  float* Gs = s32;             // n x n
-  float* Y = Gs + n * n;       // n x ms, column-major
-  float* W = Y + n * ms;       // Omega, then Q
-  G += (size_t)blockIdx.x * n * n;
-  Q0 += (size_t)blockIdx.x * n * ms;
-  if (trace != nullptr && threadIdx.x < 32) {
-    const double t = trace_warp(G, n);
-    if (threadIdx.x == 0) trace[blockIdx.x] = t;
-  }
-  {
-    // eight loads in flight per thread
-    const int tot = n * n, nt = blockDim.x;
-    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (e0 + u * nt < tot) Gs[e0 + u * nt] = (float)v[u];
-    }
-  }
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = (float)hash_uniform(seed, (unsigned long long)e);
-  __syncthreads();
-  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i
-  // coalesced); four rows n4 apart per thread as independent chains
-  const int n4 = (n + 3) / 4;
-  for (int e = threadIdx.x; e < n4 * ms; e += blockDim.x) {
-    const int c = e / n4, i = e - c * n4;
-    const float* om = W + (long long)c * n;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    const int i1 = min(i + n4, n - 1), i2 = min(i + 2 * n4, n - 1), i3 = min(i + 3 * n4, n - 1);
-    for (int k = 0; k < n; ++k) {
-      const float o = om[k];
-      const float* gk = Gs + k * n;
-      a0 = fmaf(gk[i], o, a0);
-      a1 = fmaf(gk[i1], o, a1);
-      a2 = fmaf(gk[i2], o, a2);
-      a3 = fmaf(gk[i3], o, a3);
-    }
-    float* yc = Y + (long long)c * n;
-    yc[i] = a0;
-    if (i + n4 < n) yc[i + n4] = a1;
-    if (i + 2 * n4 < n) yc[i + 2 * n4] = a2;
-    if (i + 3 * n4 < n) yc[i + 3 * n4] = a3;
-  }
-  __syncthreads();
-  qr_panel<float>(Y, W, n, ms, beta, v0s);
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) Q0[e] = (double)W[e];
-}
-
-// ---------------------------------------------------------------------------
-// Cyclic Jacobi on a symmetric m x m matrix (row-major, ld = m) in one CTA.
-// Parallel ordering: the circle method pairs the mp (even) indices into
-// mp/2 disjoint planes per step, mp - 1 steps per sweep; each step applies
-// the mp/2 rotations to rows, then to columns and to V.  A rotation is skipped
-// when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself,
-// or when both diagonal entries are below 64 u |A|_F (a plane inside the
-// rounding-noise block, whose vectors the matrix does not determine; its
-// trace is kept).  Before each sweep one pass over the upper triangle checks
-// whether any plane still needs a rotation; sweeps stop when none does (or
-// when a sweep applied none).
-// Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
-// ---------------------------------------------------------------------------
-struct JacProb {
-  const double* H;
-  int m;
-  double* lam;
-  double* V;
-  int* sweeps;
-};
-struct JacBatch {
-  JacProb p[2];  // one problem per CTA
-};
-
 // Bit-level tests and conversions on the ALU pipes: GB300 spends about 64
 // sub-partition cycles on every FP64 warp instruction, compares included.
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
@@ -589,6 +528,173 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
+size_t start32_smem(int n, int ms) {
+  return sizeof(float) * ((size_t)n * n + (size_t)panel_ld<float>(n) * ms + (size_t)n * ms);
+}
+
+// FP64 -> FP32 by the bit pattern (truncated; zero below the FP32 range,
+// which holds every entry of a Gram matrix of FP32-range data): the start only
+// needs an approximation of G, and the conversion stays off the FP64 pipe.
+__device__ __forceinline__ float double_to_float_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int fe = ex - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+}
+
+// Uniform in [-1, 1) from the counter-based hash, in FP32.
+__device__ __forceinline__ float hash_uniform_f(unsigned long long seed, unsigned long long idx) {
+  unsigned long long z = seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)(unsigned)(z >> 40) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+// Also writes the trace of G to trace[blockIdx.x] when trace is given.
+// Y = G Omega in FP32, its Householder factorisation in registers (as the
+// FP64 pass) and the factor Q formed one warp per column (Q e_c =
+// H_0 ... H_c e_c, no barrier between reflectors); Q goes out in FP64.
+template <int kRPL>
+__global__ void __launch_bounds__(256) k_start32(const double* __restrict__ G, int n, int ms,
+                                                 unsigned long long seed, double* __restrict__ Q0,
+                                                 double* __restrict__ trace) {
+  extern __shared__ float s32[];
+  __shared__ float beta[kMaxM + 1];
+  __shared__ float v0s[kMaxM + 1];
+  __shared__ float bsm[kMaxM + 1];
+  const int ld = panel_ld<float>(n);
+  float* Gs = s32;           // n x n
+  float* Y = Gs + n * n;     // n x ms, column-major, stride ld
+  float* W = Y + ld * ms;    // Omega (n x ms)
+  G += (size_t)blockIdx.x * n * n;
+  Q0 += (size_t)blockIdx.x * n * ms;
+  if (trace != nullptr && threadIdx.x < 32) {
+    const double t = trace_warp(G, n);
+    if (threadIdx.x == 0) trace[blockIdx.x] = t;
+  }
+  {
+    // eight loads in flight per thread
+    const int tot = n * n, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * nt < tot) Gs[e0 + u * nt] = double_to_float_trunc(v[u]);
+    }
+  }
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = hash_uniform_f(seed, (unsigned long long)e);
+  __syncthreads();
+  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i
+  // coalesced); four rows n4 apart per thread as independent chains
+  const int n4 = (n + 3) / 4;
+  for (int e = threadIdx.x; e < n4 * ms; e += blockDim.x) {
+    const int c = e / n4, i = e - c * n4;
+    const float* om = W + (long long)c * n;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    const int i1 = min(i + n4, n - 1), i2 = min(i + 2 * n4, n - 1), i3 = min(i + 3 * n4, n - 1);
+    for (int k = 0; k < n; ++k) {
+      const float o = om[k];
+      const float* gk = Gs + k * n;
+      a0 = fmaf(gk[i], o, a0);
+      a1 = fmaf(gk[i1], o, a1);
+      a2 = fmaf(gk[i2], o, a2);
+      a3 = fmaf(gk[i3], o, a3);
+    }
+    float* yc = Y + (long long)c * ld;
+    yc[i] = a0;
+    if (i + n4 < n) yc[i + n4] = a1;
+    if (i + 2 * n4 < n) yc[i + 2 * n4] = a2;
+    if (i + 3 * n4 < n) yc[i + 3 * n4] = a3;
+  }
+  __syncthreads();
+  qr_factor_reg<float, kRPL>(Y, ld, n, ms, bsm, beta, v0s);
+  __syncthreads();
+  // Q e_c = H_0 ... H_c e_c, one warp per column (rows above each head are 0)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < ms; c += nw) {
+    float q[kRPL];
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) q[t] = (lane + 32 * t == c) ? 1.0f : 0.0f;
+    for (int j = c; j >= 0; --j) {
+      const float* v = Y + (long long)j * ld;
+      float vv[kRPL];
+      float d = 0.0f;
+#pragma unroll
+      for (int t = 0; t < kRPL; ++t) {
+        const int i = lane + 32 * t;
+        vv[t] = (i < n && i >= j) ? v[i] : 0.0f;
+        d = fmaf(vv[t], q[t], d);
+      }
+      d = warp_sum32(d);
+      const float f = bsm[j] * d;
+#pragma unroll
+      for (int t = 0; t < kRPL; ++t) q[t] = fmaf(-f, vv[t], q[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      const int i = lane + 32 * t;
+      if (i < n) Q0[(long long)c * n + i] = float_to_double_bits(q[t]);
+    }
+  }
+}
+
+// k_start32 for n <= 256 (kRPL = ceil(n / 32)).
+void start32_launch(const double* G, int n, int ms, int B, unsigned long long seed, double* Q0, double* trace,
+                    cudaStream_t s) {
+  const size_t smem = start32_smem(n, ms);
+  switch ((n + 31) / 32) {
+#define TK_START32_CASE(K)                                                                                   \
+  case K:                                                                                                    \
+    once_per_device((const void*)&k_start32<K>, [] {                                                         \
+      TK_CUDA(cudaFuncSetAttribute(k_start32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); \
+    });                                                                                                      \
+    k_start32<K><<<B, 256, smem, s>>>(G, n, ms, seed, Q0, trace);                                            \
+    break;
+    TK_START32_CASE(1)
+    TK_START32_CASE(2)
+    TK_START32_CASE(3)
+    TK_START32_CASE(4)
+    TK_START32_CASE(5)
+    TK_START32_CASE(6)
+    TK_START32_CASE(7)
+    TK_START32_CASE(8)
+#undef TK_START32_CASE
+    default:
+      fail(TK_EINVAL, "start32: n out of range");
+  }
+  TK_LAUNCH("k_start32");
+}
+
+// ---------------------------------------------------------------------------
+// Cyclic Jacobi on a symmetric m x m matrix (row-major, ld = m) in one CTA.
+// Parallel ordering: the circle method pairs the mp (even) indices into
+// mp/2 disjoint planes per step, mp - 1 steps per sweep; each step applies
+// the mp/2 rotations to rows, then to columns and to V.  A rotation is skipped
+// when |a_pq| <= 2^-53 |A|_F, below the rounding of the FP64 matrix itself,
+// or when both diagonal entries are below 64 u |A|_F (a plane inside the
+// rounding-noise block, whose vectors the matrix does not determine; its
+// trace is kept).  Before each sweep one pass over the upper triangle checks
+// whether any plane still needs a rotation; sweeps stop when none does (or
+// when a sweep applied none).
+// Output: lam (descending) and V (row-major m x m, eigenvectors as columns).
+// ---------------------------------------------------------------------------
+struct JacProb {
+  const double* H;
+  int m;
+  double* lam;
+  double* V;
+  int* sweeps;
+};
+struct JacBatch {
+  JacProb p[2];  // one problem per CTA
+};
+
 // FP64 (c, s) with c^2 + s^2 = 1 to FP64 rounding from an FP32 rotation
 // (cf, sf): with delta = cf^2 + sf^2 - 1 (|delta| < 2^-21), c = cf (1 - kappa),
 // s = sf (1 - kappa), kappa = delta/2 - 3 delta^2/8 (the next term of
@@ -1012,7 +1118,6 @@ static void set_attrs_once() {
                                (int)kQrSmemMax));
   TK_CUDA(cudaFuncSetAttribute(k_jacobi_strided, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)jacobi_smem(kMaxM)));
-  TK_CUDA(cudaFuncSetAttribute(k_start32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStart32SmemMax));
 }
 
 static void set_attrs() { once_per_device((const void*)&set_attrs_once, set_attrs_once); }
@@ -1206,7 +1311,7 @@ EigGroup carve_group(double* p, const double* G, int n, int m, int B, double* la
 
 // The FP32 start (with the trace folded in) serves the subspace path when
 // its shared-memory image fits.
-bool uses_start32(int n, int ms) { return ms != n && start32_smem(n, ms) <= kStart32SmemMax; }
+bool uses_start32(int n, int ms) { return ms != n && n <= 256 && start32_smem(n, ms) <= kStart32SmemMax; }
 
 // trace: written by the FP32 start kernel when that path runs (the caller
 // computes it otherwise).
@@ -1238,8 +1343,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     };
     if (uses_start32(n, ms)) {
       // FP32 pass from the random block, then one FP64 pass
-      k_start32<<<B, 256, start32_smem(n, ms), s>>>(g.G, n, ms, seed, g.Q, trace);
-      TK_LAUNCH("k_start32");
+      start32_launch(g.G, n, ms, B, seed, g.Q, trace, s);
       power(g.Q);
       qr();
     } else {
