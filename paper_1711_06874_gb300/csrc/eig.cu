@@ -724,17 +724,35 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   extern __shared__ double sm[];
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
   const int np = mp / 2;        // planes per step
+  const int nblk = np * (np + 1) / 2;
   double* A = sm;
   double* V = A + mp * mp;
-  double* cs = V + mp * mp;  // c, s per plane
-  int* pp = (int*)(cs + mp);
-  int* qq = pp + np;
-  int* flag = qq + np;
+  double* cs = V + mp * mp;                // c, s per plane
+  int* sched = (int*)(cs + mp);            // [step][plane]: p | q << 8
+  int* blk = sched + (mp - 1) * np;        // [block]: a | b << 8, upper blocks in order
+  int* stepf = blk + nblk;                 // [step]: some rotation in this step
+  int* flag = stepf + mp;
   __shared__ double red[33];
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
     const int i = e / mp, j = e % mp;
     A[e] = (i < m && j < m) ? Hin[i * m + j] : 0.0;
     V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  // the circle method's planes of every step, and the upper 2 x 2 blocks
+  for (int e = threadIdx.x; e < (mp - 1) * np; e += blockDim.x) {
+    const int st = e / np, k = e - st * np;
+    const int pos0 = k, pos1 = mp - 1 - k;
+    const int a = (pos0 == 0) ? 0 : 1 + (pos0 - 1 + st) % (mp - 1);
+    const int b = 1 + (pos1 - 1 + st) % (mp - 1);
+    sched[e] = min(a, b) | (max(a, b) << 8);
+  }
+  for (int e = threadIdx.x; e < nblk; e += blockDim.x) {
+    int a = 0, r = e;
+    while (r >= np - a) {
+      r -= np - a;
+      ++a;
+    }
+    blk[e] = a | ((a + r) << 8);
   }
   __syncthreads();
   double fs = 0.0;
@@ -743,6 +761,8 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   // thresholds as bit patterns: |x| > t  <=>  abs_bits(x) > bits(t) for t >= 0
   const unsigned long long tau_b = abs_bits(0x1p-53 * normA);
   const unsigned long long noise_b = abs_bits(0x1p-47 * normA);  // 64 u |A|_F
+  // f / mp for f < np mp by a 32-bit reciprocal (exact in this range)
+  const unsigned magic = (unsigned)((0xFFFFFFFFull + mp) / mp);
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
     // a sweep runs only while some plane still needs a rotation (one pass over
@@ -754,19 +774,16 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           !(abs_bits(A[i * mp + i]) <= noise_b && abs_bits(A[j * mp + j]) <= noise_b))
         need = 1;
     }
+    for (int e = threadIdx.x; e < mp; e += blockDim.x) stepf[e] = 0;
     if (!__syncthreads_or(need)) break;
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int st = 0; st < mp - 1; ++st) {
-      // planes of this step and their rotations
+      // rotations of this step's planes
       if (threadIdx.x < np) {
         const int k = threadIdx.x;
-        const int pos0 = k, pos1 = mp - 1 - k;
-        const int a = (pos0 == 0) ? 0 : 1 + (pos0 - 1 + st) % (mp - 1);
-        const int b = 1 + (pos1 - 1 + st) % (mp - 1);
-        const int p = min(a, b), q = max(a, b);
-        pp[k] = p;
-        qq[k] = q;
+        const int pq = sched[st * np + k];
+        const int p = pq & 0xFF, q = pq >> 8;
         const double apq = A[p * mp + q], app = A[p * mp + p], aqq = A[q * mp + q];
         double c = 1.0, s = 0.0;
         // two indices whose diagonals both lie in the rounding noise of the
@@ -783,51 +800,93 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           const float cf = rsqrtf(fmaf(t, t, 1.0f));
           const float sf = t * cf;
           exact_rotation(cf, sf, c, s);
-          if (sf != 0.0f) *flag = 1;
+          if (sf != 0.0f) {
+            *flag = 1;
+            stepf[st] = 1;
+          }
         }
         cs[2 * k] = c;
         cs[2 * k + 1] = s;
       }
       __syncthreads();
+      if (stepf[st] == 0) continue;  // no plane rotates: nothing to apply
       // A <- J^T A J on every 2 x 2 block (plane a rows, plane b columns),
-      // upper blocks computed and mirrored; V <- V J on plane column pairs
-      const int nblk = np * (np + 1) / 2;
-      for (int e = threadIdx.x; e < nblk + np * mp; e += blockDim.x) {
-        if (e < nblk) {
-          int a = 0, r = e;
-          while (r >= np - a) {
-            r -= np - a;
-            ++a;
+      // upper blocks computed and mirrored; one block row (two entries) per
+      // lane, the two rows of a block in adjacent lanes, which both read the
+      // block before either writes (__syncwarp).  V <- V J on plane column
+      // pairs.  Block rows go to the first half of the CTA and V to the
+      // second, so every sub-partition's FP64 unit gets a share of both.
+      const int half = blockDim.x >> 1;
+      if ((int)threadIdx.x < half) {
+        const int lane = threadIdx.x & 31;
+        for (int base = (int)threadIdx.x - lane; base < 2 * nblk; base += half) {
+          const int e = base + lane;
+          const bool valid = e < 2 * nblk;
+          int pa = 0, qa = 0, pb = 0, qb = 0, a = 0, b = 0;
+          double ca = 1.0, sa = 0.0, cb = 1.0, sb = 0.0, m00 = 0.0, m01 = 0.0, m10 = 0.0, m11 = 0.0;
+          bool still = true;
+          if (valid) {
+            const int ab = blk[e >> 1];
+            a = ab & 0xFF;
+            b = ab >> 8;
+            sa = cs[2 * a + 1];
+            sb = cs[2 * b + 1];
+            still = is_zero_d(sa) && is_zero_d(sb);  // both identities: nothing changes
+            if (!still) {
+              ca = cs[2 * a];
+              cb = cs[2 * b];
+              const int pqa = sched[st * np + a], pqb = sched[st * np + b];
+              pa = pqa & 0xFF;
+              qa = pqa >> 8;
+              pb = pqb & 0xFF;
+              qb = pqb >> 8;
+              m00 = A[pa * mp + pb];
+              m01 = A[pa * mp + qb];
+              m10 = A[qa * mp + pb];
+              m11 = A[qa * mp + qb];
+            }
           }
-          const int b = a + r;
-          const double ca = cs[2 * a], sa = cs[2 * a + 1], cb = cs[2 * b], sb = cs[2 * b + 1];
-          if (is_zero_d(sa) && is_zero_d(sb)) continue;
-          const int pa = pp[a], qa = qq[a], pb = pp[b], qb = qq[b];
-          const double m00 = A[pa * mp + pb], m01 = A[pa * mp + qb], m10 = A[qa * mp + pb], m11 = A[qa * mp + qb];
-          // rows: [c -s; s c] M
-          const double r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
-          const double r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
-          // columns: (.) [c s; -s c]
-          double n00 = cb * r00 - sb * r01, n01 = sb * r00 + cb * r01;
-          double n10 = cb * r10 - sb * r11, n11 = sb * r10 + cb * r11;
-          if (a == b) n10 = n01;  // keep the block exactly symmetric
-          A[pa * mp + pb] = n00;
-          A[pa * mp + qb] = n01;
-          A[qa * mp + pb] = n10;
-          A[qa * mp + qb] = n11;
-          if (a != b) {
-            A[pb * mp + pa] = n00;
-            A[qb * mp + pa] = n01;
-            A[pb * mp + qa] = n10;
-            A[qb * mp + qa] = n11;
+          __syncwarp();
+          if (valid && !still) {
+            if ((e & 1) == 0) {
+              // top row: [c -s] M, then the column rotation (.) [c s; -s c]
+              const double r0 = ca * m00 - sa * m10, r1 = ca * m01 - sa * m11;
+              const double n0 = cb * r0 - sb * r1, n1 = sb * r0 + cb * r1;
+              if (a == b) {
+                A[pa * mp + pa] = n0;
+                A[pa * mp + qa] = n1;
+                A[qa * mp + pa] = n1;  // the block stays exactly symmetric
+              } else {
+                A[pa * mp + pb] = n0;
+                A[pa * mp + qb] = n1;
+                A[pb * mp + pa] = n0;
+                A[qb * mp + pa] = n1;
+              }
+            } else {
+              // bottom row: [s c] M, then the column rotation
+              const double r0 = sa * m00 + ca * m10, r1 = sa * m01 + ca * m11;
+              const double n1 = sb * r0 + cb * r1;
+              if (a == b) {
+                A[qa * mp + qa] = n1;
+              } else {
+                const double n0 = cb * r0 - sb * r1;
+                A[qa * mp + pb] = n0;
+                A[qa * mp + qb] = n1;
+                A[pb * mp + qa] = n0;
+                A[qb * mp + qa] = n1;
+              }
+            }
           }
-        } else {
-          const int f = e - nblk;
-          const int k = f / mp, row = f % mp;
+          __syncwarp();
+        }
+      } else {
+        for (int f = threadIdx.x - half; f < np * mp; f += blockDim.x - half) {
+          const int k = (int)__umulhi((unsigned)f, magic), row = f - k * mp;
           const double s = cs[2 * k + 1];
           if (is_zero_d(s)) continue;
           const double c = cs[2 * k];
-          const int p = pp[k], q = qq[k];
+          const int pq = sched[st * np + k];
+          const int p = pq & 0xFF, q = pq >> 8;
           const double vp = V[row * mp + p], vq = V[row * mp + q];
           V[row * mp + p] = c * vp - s * vq;
           V[row * mp + q] = s * vp + c * vq;
@@ -1106,8 +1165,10 @@ static constexpr size_t kQrSmemMax = 200 * 1024;
 static constexpr size_t kStart32SmemMax = 200 * 1024;
 
 static size_t jacobi_smem(int m) {
-  const int mp = (m + 1) & ~1;
-  return (2ull * mp * mp + mp) * sizeof(double) + (mp + 4) * sizeof(int);
+  const int mp = (m + 1) & ~1, np = mp / 2;
+  // A, V, (c, s); the plane schedule, the block list, step flags and the sweep flag
+  return (2ull * mp * mp + mp) * sizeof(double) +
+         ((size_t)(mp - 1) * np + (size_t)np * (np + 1) / 2 + mp + 4) * sizeof(int);
 }
 
 static void set_attrs_once() {
