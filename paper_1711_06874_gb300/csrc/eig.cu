@@ -733,9 +733,10 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   int* stepf = blk + nblk;                 // [step]: some rotation in this step
   int* flag = stepf + mp;
   __shared__ double red[33];
+  // H symmetrised on load: A = (H + H^T) / 2
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
     const int i = e / mp, j = e % mp;
-    A[e] = (i < m && j < m) ? Hin[i * m + j] : 0.0;
+    A[e] = (i < m && j < m) ? 0.5 * (Hin[i * m + j] + Hin[j * m + i]) : 0.0;
     V[e] = (i == j) ? 1.0 : 0.0;
   }
   // the circle method's planes of every step, and the upper 2 x 2 blocks
@@ -956,33 +957,6 @@ __global__ void k_canonical_sign(double* V, int n, int m) {
   const bool flip = V[(long long)bi[0] * m + col] < 0.0;
   if (flip)
     for (int i = threadIdx.x; i < n; i += blockDim.x) V[(long long)i * m + col] = -V[(long long)i * m + col];
-}
-
-__global__ void k_symmetrize(double* H, int m) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
-    const int i = e / m, j = e % m;
-    if (i < j) {
-      const double v = 0.5 * (H[i * m + j] + H[j * m + i]);
-      H[i * m + j] = v;
-      H[j * m + i] = v;
-    }
-  }
-}
-
-__global__ void k_symmetrize_batch(double* H, int m, int B) {
-  const long long total = (long long)B * m * m;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long b = e / ((long long)m * m);
-    const int r = (int)(e - b * m * m);
-    const int i = r / m, j = r % m;
-    if (i < j) {
-      double* Hb = H + b * m * m;
-      const double v = 0.5 * (Hb[i * m + j] + Hb[j * m + i]);
-      Hb[i * m + j] = v;
-      Hb[j * m + i] = v;
-    }
-  }
 }
 
 __global__ void k_copy_rows(const double* G, double* H, int n) {
@@ -1274,8 +1248,6 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
     gemm_f64(d1, s);
     GemmDesc d2{ms, ms, n, 1, w[b].Q, 0, n, 1, w[b].W, 0, 1, n, w[b].H, 0, ms, 1};
     gemm_f64(d2, s);
-    k_symmetrize<<<4, 256, 0, s>>>(w[b].H, ms);
-    TK_LAUNCH("k_symmetrize");
     jb.p[t] = JacProb{w[b].H, ms, w[b].lsub, w[b].VH, (int*)(w[b].misc + 8)};
     smem = std::max(smem, jacobi_smem(ms));
   }
@@ -1425,9 +1397,6 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
                 g.H, (long long)ms * ms, ms, 1};
     d2.fixed_order = 1;
     gemm_f64(d2, s);
-    k_symmetrize_batch<<<(unsigned)std::min<long long>(((long long)B * ms * ms + 255) / 256, 4096), 256, 0, s>>>(
-        g.H, ms, B);
-    TK_LAUNCH("k_symmetrize_batch");
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
   k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);

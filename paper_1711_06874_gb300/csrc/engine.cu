@@ -720,15 +720,15 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       woff += ((size_t)q.cnt * h[0] * R * R + 31) & ~size_t(31);
       double* W2 = ewbase + woff;
       woff += ((size_t)q.cnt * h[0] * h[1] * R + 31) & ~size_t(31);
+      if (err_ff && err_sliced_supported(h[0], R)) {
+        err_sliced_batch(sv, normF2, Up0, Cp, h[0], R, q.cnt, amap + q.off, effscr, esum + 2 * (size_t)q.off, s);
+        continue;
+      }
       // W1[i][(b,c)] = sum_a V1[i][a] B[a][(b,c)]
       GemmDesc e1{h[0], R * R, R, q.cnt, Up0, (long long)h[0] * R, R, 1, Cp, (long long)R * R * R,
                   (long long)R * R, 1, W1, (long long)h[0] * R * R, (long long)R * R, 1};
       e1.fixed_order = 1;
       gemm_f64(e1, s);
-      if (err_ff && err_sliced_supported(h[0], R)) {
-        err_sliced_batch(sv, normF2, Up0, W1, h[0], R, q.cnt, amap + q.off, effscr, esum + 2 * (size_t)q.off, s);
-        continue;
-      }
       if (!fh_ready) {
         // a rank beyond the float-float kernel's range: sample F in FP64 now
         eval_octant_f64(kd, tab, g, B, FhE, tableE, partE, normE, s);

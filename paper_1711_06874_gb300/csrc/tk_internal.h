@@ -224,11 +224,11 @@ void err_lowrank_batch(const double* W, long long sW, const double* Ut, long lon
 // Error during a solve on the sliced path (isotropic, octant side h): the
 // octant residual against the Gram's slices sv, in float-float arithmetic, for
 // the cnt instances of one rank group (padded rank R <= 32, h a multiple of 8):
-// V [pos][h][R] the shared factor, W1 [pos][h][R][R] = B x_1 V;
+// V [pos][h][R] the shared factor, Bcore [pos][R][R][R] the padded core;
 // esum [pos][2] = (|Fh - Xh|^2, |Fh|^2) with |Fh|^2 from normF2[amap[pos]].
 bool err_sliced_supported(int h, int R);
 size_t err_sliced_scratch_bytes(int h, int R, int cnt);
-void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V, const double* W1, int h, int R,
+void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V, const double* Bcore, int h, int R,
                       int cnt, const int* amap, void* scratch, double* esum, cudaStream_t s);
 
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
