@@ -508,6 +508,54 @@ __global__ void k_gemm_warp(GemmDesc d) {
   }
 }
 
+// L lanes per output: lane q sums the terms k = q (mod L) as one FMA chain in
+// k order, and the L chains are added in a fixed xor tree.  L = 32 for
+// K >= 128 (short chains: these shapes are the large-n, few-instance,
+// latency-bound solves) and L = 4 below (two additions of overhead per output:
+// an FP64 warp instruction holds a sub-partition's FP64 unit for about 64
+// cycles whatever the number of active lanes, which counts in large batches).
+template <int L>
+__global__ void k_gemm_lanes(GemmDesc d) {
+  const long long per_batch = (long long)d.M * d.N;
+  const long long total = per_batch * d.batch;
+  const int q = threadIdx.x & (L - 1);
+  for (long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / L;
+       o - (long long)((threadIdx.x & 31) / L) < total; o += ((long long)gridDim.x * blockDim.x) / L) {
+    // every lane of a warp runs the shuffles: outputs past the end add zeros
+    const bool live = o < total;
+    double acc = 0.0;
+    long long coff = 0;
+    int i = 0, j = 0;
+    if (live) {
+      const long long b = o / per_batch;
+      const long long r = o - b * per_batch;
+      i = (int)(r / d.N);
+      j = (int)(r % d.N);
+      const double* A;
+      const double* B;
+      coff = batch_offsets(d, b, A, B);
+      A += (long long)i * d.sAi;
+      B += (long long)j * d.sBj;
+      int k = q;
+      // four terms per pass, loads first, FMAs in k order
+      for (; k + 3 * L < d.K; k += 4 * L) {
+        double a[4], bb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = A[(long long)(k + u * L) * d.sAk];
+          bb[u] = B[(long long)(k + u * L) * d.sBk];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma(a[u], bb[u], acc);
+      }
+      for (; k < d.K; k += L) acc = fma(A[(long long)k * d.sAk], B[(long long)k * d.sBk], acc);
+    }
+#pragma unroll
+    for (int off = 1; off < L; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (live && q == 0) d.C[coff + (long long)i * d.sCi + (long long)j * d.sCj] = acc;
+  }
+}
+
 // Output tiles (BM x BN); every one sums each output in the same k order.
 struct TileShape {
   int bm, bn;
@@ -572,10 +620,26 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   const dim3 g = dispatch<false>(d, ErrRef{}, nullptr, s, false);
   const long long ctas = (long long)g.x * g.y * g.z;
   const long long outs = (long long)d.M * d.N * d.batch;
-  // one warp per output when the outputs are few: for fixed-order products the
-  // choice depends on the per-entry shape alone (never on the batch)
-  const bool warp = d.fixed_order ? ((long long)d.M * d.N <= 4096 && d.K >= 32)
-                                  : (ctas < 76 && outs <= (1LL << 18));
+  // fixed-order products: several lanes per output for small per-entry shapes
+  // (their number set by K), tiles otherwise; the choice depends on the per-entry shape alone (never on
+  // the batch), so an entry's result does not either
+  if (d.fixed_order) {
+    if ((long long)d.M * d.N <= 4096 && d.K >= 32) {
+      const int L = d.K >= 128 ? 32 : 4;
+      const long long threads = (long long)L * outs;
+      const unsigned blocks = (unsigned)std::min<long long>((threads + 255) / 256, 8192);
+      if (L == 4)
+        k_gemm_lanes<4><<<blocks, 256, 0, s>>>(d);
+      else
+        k_gemm_lanes<32><<<blocks, 256, 0, s>>>(d);
+      TK_LAUNCH("k_gemm_lanes");
+      return;
+    }
+    dispatch<false>(d, ErrRef{}, nullptr, s, true);
+    return;
+  }
+  // one warp per output when the outputs are few
+  const bool warp = ctas < 76 && outs <= (1LL << 18);
   if (warp) {
     // few tiles: one warp per output keeps every SM busy
     const long long warps = outs;

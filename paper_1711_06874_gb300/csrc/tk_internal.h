@@ -183,7 +183,7 @@ inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 
 // General strided batched FP64 GEMM: C[z](i,j) = sum_k A[z](i,k) B[z](k,j).
 // Batch entry z = b1 batch2 + b2 has operand offsets b1 s_b + b2 s_b2 (A's b1
 // replaced by amap[b1] when amap is given).  Every output is one FMA chain in
-// k order (or, for few outputs, one warp per output with a fixed lane tree);
+// k order (or, for few outputs, a fixed split of k over several lanes);
 // fixed_order = 1 makes that choice from the per-entry shape alone, so that
 // each entry's result does not depend on the batch it is part of.
 struct GemmDesc {
