@@ -190,6 +190,19 @@ class Context:
         self.ptr = _vp()
         _check(self.lib.tk_create(_c.byref(self.ptr), int(device)))
         self.device = device
+        self._args = {}  # (problem, options) -> the C structs, built once
+
+    def _structs(self, prob, precision, rfix, shortcut, fold, with_error):
+        """The C structs of one solve, built once per distinct (problem, options):
+        building them costs more than a small solve's launches."""
+        key = (prob, precision, tuple(rfix), bool(shortcut), bool(fold), bool(with_error))
+        hit = self._args.get(key)
+        if hit is None:
+            if len(self._args) >= 256:
+                self._args.clear()
+            hit = (make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold, with_error))
+            self._args[key] = hit
+        return hit
 
     def close(self):
         if self.ptr is not None and self.ptr.value:
@@ -205,7 +218,7 @@ class Context:
     # ---- whole solve -------------------------------------------------------
     def tucker(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True,
                fold=True, with_error=False, stream=None) -> "Result":
-        k, g, o = make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold, with_error)
+        k, g, o = self._structs(prob, precision, rfix, shortcut, fold, with_error)
         out = _vp()
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
