@@ -529,7 +529,8 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 size_t start32_smem(int n, int ms) {
-  return sizeof(float) * ((size_t)n * n + (size_t)panel_ld<float>(n) * ms + (size_t)n * ms);
+  return sizeof(float) *
+         ((((size_t)n * n + 3) & ~size_t(3)) + (size_t)panel_ld<float>(n) * ms + (size_t)n * ((ms + 3) & ~3));
 }
 
 // FP64 -> FP32 by the bit pattern (truncated; zero below the FP32 range,
@@ -568,8 +569,8 @@ __global__ void __launch_bounds__(256) k_start32(const double* __restrict__ G, i
   __shared__ float bsm[kMaxM + 1];
   const int ld = panel_ld<float>(n);
   float* Gs = s32;           // n x n
-  float* Y = Gs + n * n;     // n x ms, column-major, stride ld
-  float* W = Y + ld * ms;    // Omega (n x ms)
+  float* Y = Gs + ((n * n + 3) & ~3);  // n x ms, column-major, stride ld (16-byte aligned)
+  float* W = Y + ld * ms;    // Omega ([k][c], stride (ms + 3) & ~3)
   G += (size_t)blockIdx.x * n * n;
   Q0 += (size_t)blockIdx.x * n * ms;
   if (trace != nullptr && threadIdx.x < 32) {
@@ -577,40 +578,80 @@ __global__ void __launch_bounds__(256) k_start32(const double* __restrict__ G, i
     if (threadIdx.x == 0) trace[blockIdx.x] = t;
   }
   {
-    // eight loads in flight per thread
+    // G in 16-byte loads (two entries), eight in flight per thread (n even;
+    // odd n loads entries one by one)
     const int tot = n * n, nt = blockDim.x;
-    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
-      double v[8];
+    if ((n & 1) == 0) {
+      const double2* G2 = reinterpret_cast<const double2*>(G);
+      const int tot2 = tot / 2;
+      for (int e0 = threadIdx.x; e0 < tot2; e0 += 8 * nt) {
+        double2 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
+        for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot2) ? __ldg(G2 + e0 + u * nt) : make_double2(0.0, 0.0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (e0 + u * nt < tot) Gs[e0 + u * nt] = double_to_float_trunc(v[u]);
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u * nt < tot2)
+            reinterpret_cast<float2*>(Gs)[e0 + u * nt] =
+                make_float2(double_to_float_trunc(v[u].x), double_to_float_trunc(v[u].y));
+      }
+    } else {
+      for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u * nt < tot) Gs[e0 + u * nt] = double_to_float_trunc(v[u]);
+      }
     }
   }
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) W[e] = hash_uniform_f(seed, (unsigned long long)e);
+  // Omega stored k-major ([k][c], stride ms4): four columns in one 16-byte load
+  const int ms4 = (ms + 3) & ~3;
+  for (int e = threadIdx.x; e < n * ms4; e += blockDim.x) {
+    const int k = e / ms4, c = e - k * ms4;
+    W[e] = (c < ms) ? hash_uniform_f(seed, (unsigned long long)c * n + k) : 0.0f;
+  }
   __syncthreads();
-  // Y(i, c) = sum_k G(k, i) Omega(k, c)  (G symmetric; consecutive i
-  // coalesced); four rows n4 apart per thread as independent chains
-  const int n4 = (n + 3) / 4;
-  for (int e = threadIdx.x; e < n4 * ms; e += blockDim.x) {
-    const int c = e / n4, i = e - c * n4;
-    const float* om = W + (long long)c * n;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    const int i1 = min(i + n4, n - 1), i2 = min(i + 2 * n4, n - 1), i3 = min(i + 3 * n4, n - 1);
-    for (int k = 0; k < n; ++k) {
-      const float o = om[k];
-      const float* gk = Gs + k * n;
-      a0 = fmaf(gk[i], o, a0);
-      a1 = fmaf(gk[i1], o, a1);
-      a2 = fmaf(gk[i2], o, a2);
-      a3 = fmaf(gk[i3], o, a3);
+  // Y(i, c) = sum_k G(k, i) Omega(k, c) (G symmetric), a 4 x 4 block of
+  // outputs per thread: rows i0..i0+3 and columns c0..c0+3 from two 16-byte
+  // shared loads per k
+  {
+    const int nb4 = (n + 3) / 4, cb4 = ms4 / 4;
+    for (int e = threadIdx.x; e < nb4 * cb4; e += blockDim.x) {
+      const int cb = e / nb4, ib = e - cb * nb4;
+      const int i0 = 4 * ib, c0 = 4 * cb;
+      float acc[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+      const bool full = i0 + 3 < n && (n & 3) == 0;
+      for (int k = 0; k < n; ++k) {
+        float g[4];
+        if (full) {
+          const float4 g4 = *reinterpret_cast<const float4*>(Gs + (size_t)k * n + i0);
+          g[0] = g4.x;
+          g[1] = g4.y;
+          g[2] = g4.z;
+          g[3] = g4.w;
+        } else {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) g[p] = (i0 + p < n) ? Gs[(size_t)k * n + i0 + p] : 0.0f;
+        }
+        const float4 o4 = *reinterpret_cast<const float4*>(W + (size_t)k * ms4 + c0);
+        const float o[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(g[p], o[q], acc[p][q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + q < ms)
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            if (i0 + p < n) Y[(size_t)(c0 + q) * ld + i0 + p] = acc[p][q];
     }
-    float* yc = Y + (long long)c * ld;
-    yc[i] = a0;
-    if (i + n4 < n) yc[i + n4] = a1;
-    if (i + 2 * n4 < n) yc[i + 2 * n4] = a2;
-    if (i + 3 * n4 < n) yc[i + 3 * n4] = a3;
   }
   __syncthreads();
   qr_factor_reg<float, kRPL>(Y, ld, n, ms, bsm, beta, v0s);
