@@ -139,6 +139,7 @@ namespace {
 
 constexpr int kPhaseA = 12;  // eigenpairs of the first pass (enough for ranks <= 12)
 constexpr int kPhaseB = 40;  // second pass, for the instances that need more
+constexpr int kSpecMaxBatch = 4;  // batches up to this size run the second phase speculatively
 
 int roundup(int x, int q) { return (x + q - 1) / q * q; }
 
@@ -157,16 +158,23 @@ __global__ void k_gather_mats(const double* __restrict__ src, const int* __restr
 // canonical signs: the entry of largest magnitude among the first ceil(n/2)
 // rows positive), Uh (h x r, the signed octant vectors) and Up (h x R, Uh
 // padded with zero columns for the batched TTM).
+// r: the rank, or (rdev given) its upper bound, the rank itself then being
+// read on the device from the rank rule's output (a solve launched before the
+// host knows its ranks).
 struct UnfoldDesc {
   const double* V;
   double* U;
   double* Uh;
   double* Up;
+  const int* rdev;
   int ldv, r, R, h, n;
 };
 
+__device__ __forceinline__ int rank_of(int r, const int* rdev) { return rdev ? min(*rdev, r) : r; }
+
 __global__ void k_unfold(const UnfoldDesc* __restrict__ descs) {
-  const UnfoldDesc d = descs[blockIdx.y];
+  UnfoldDesc d = descs[blockIdx.y];
+  d.r = rank_of(d.r, d.rdev);
   const int c = blockIdx.x;
   if (c >= d.R) return;
   if (c >= d.r) {
@@ -218,11 +226,15 @@ __global__ void k_unfold(const UnfoldDesc* __restrict__ descs) {
 struct CoreDesc {
   const double* src;  // R x R x R padded core
   double* dst;        // r1 x r2 x r3
+  const int* rdev[3]; // ranks on the device (see UnfoldDesc), or null
   int R, r1, r2, r3;
 };
 
 __global__ void k_extract_core(const CoreDesc* __restrict__ descs) {
-  const CoreDesc d = descs[blockIdx.y];
+  CoreDesc d = descs[blockIdx.y];
+  d.r1 = rank_of(d.r1, d.rdev[0]);
+  d.r2 = rank_of(d.r2, d.rdev[1]);
+  d.r3 = rank_of(d.r3, d.rdev[2]);
   const long long total = (long long)d.r1 * d.r2 * d.r3;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -426,13 +438,26 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                     outA + 4 * B * a, s);
     if (pf) pf->end(s);
   }
-  // ints (flag, ranks), |F|^2 and the eigenvalues in one copy
-  {
-    const char* end = (const char*)(lamA[nmodes - 1] + (size_t)B * mA[nmodes - 1]);
-    TK_CUDA(cudaMemcpyAsync(ih, ints, (size_t)(end - (const char*)ints), cudaMemcpyDeviceToHost, s));
+  // Small batches run the second phase speculatively: it is launched before
+  // the host sees the ranks (each of its kernels reads them on the device, the
+  // sizes are those of the largest rank phase A allows), on the assumption that
+  // no instance needs more eigenpairs than phase A computed.  The assumption is
+  // checked after the final synchronisation; when it fails the second phase
+  // runs again the ordinary way.  Every result of the second phase is
+  // independent of the padded rank R, so both ways give the same bits.
+  bool spec0 = B <= kSpecMaxBatch;
+  for (int b = 0; b < B && spec0; ++b)
+    for (int a = 0; a < nmodes; ++a)
+      if (req[b].o.rfix[a] > mA[a]) spec0 = false;
+  const char* ranks_end = (const char*)(lamA[nmodes - 1] + (size_t)B * mA[nmodes - 1]);
+  for (int attempt = spec0 ? 0 : 1; attempt < 2; ++attempt) {
+  const bool spec = attempt == 0;
+  if (!spec) {
+    // ints (flag, ranks), |F|^2 and the eigenvalues in one copy
+    TK_CUDA(cudaMemcpyAsync(ih, ints, (size_t)(ranks_end - (const char*)ints), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    if (ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
   }
-  TK_CUDA(cudaStreamSynchronize(s));
-  if (ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
 
   // ---------------- escalation ----------------
   // Instances whose rank rule wants more pairs than a phase computed are
@@ -453,11 +478,17 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     p0.V = VA[a];
     p0.J.resize(B);
     for (int b = 0; b < B; ++b) p0.J[b] = b;
-    p0.out.assign(hA + 4 * B * a, hA + 4 * B * (a + 1));
-    p0.hl.assign(hlamA[a], hlamA[a] + (size_t)B * mA[a]);
+    if (spec) {
+      // ranks not known yet: sizes for the largest, ranks read on the device
+      p0.out.assign((size_t)4 * B, 0);
+      for (int b = 0; b < B; ++b) p0.out[4 * b] = p0.out[4 * b + 2] = mA[a];
+    } else {
+      p0.out.assign(hA + 4 * B * a, hA + 4 * B * (a + 1));
+      p0.hl.assign(hlamA[a], hlamA[a] + (size_t)B * mA[a]);
+    }
     ph[a].push_back(std::move(p0));
     const int levels[2] = {std::min(m[a], kPhaseB), m[a]};
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < 2 && !spec; ++l) {
       const Phase& prev = ph[a].back();
       const int mp = levels[l];
       if (mp <= prev.mp) continue;
@@ -654,9 +685,16 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       d.U = rbase + offU[(size_t)b * 3 + a];
       d.Uh = rbase + offUh[(size_t)b * 3 + a];
       d.Up = tbase + q.up[a] + (size_t)pos * h[a] * q.R;
+      d.rdev = spec ? outA + 4 * ((size_t)a * B + b) : nullptr;
     }
-    cdh[b] = CoreDesc{tbase + q.cp + (size_t)pos * q.R * q.R * q.R, rbase + offC[b], q.R, fin[b].r[0], fin[b].r[1],
-                      fin[b].r[2]};
+    CoreDesc& c = cdh[b];
+    c.src = tbase + q.cp + (size_t)pos * q.R * q.R * q.R;
+    c.dst = rbase + offC[b];
+    for (int a = 0; a < 3; ++a) c.rdev[a] = spec ? outA + 4 * ((size_t)std::min(a, nmodes - 1) * B + b) : nullptr;
+    c.R = q.R;
+    c.r1 = fin[b].r[0];
+    c.r2 = fin[b].r[1];
+    c.r3 = fin[b].r[2];
   }
   // amap, ud and cd are carved back to back here and in the pinned staging
   if ((char*)cdh - (char*)amaph != (char*)cd - (char*)amap)
@@ -689,6 +727,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     GemmDesc d2{R, h[1] * R, h[0], q.cnt, Up0, (long long)h[0] * R, 1, R, T1, (long long)h[0] * h[1] * R,
                 (long long)h[1] * R, 1, T2, (long long)R * h[1] * R, (long long)h[1] * R, 1};
     d2.fixed_order = 1;
+    d2.tiles_only = 1;  // its outputs must not depend on the padded rank R
     gemm_f64(d2, s);
     // mode 2: B[a][b][c] = sum_k V2[k][b] T2[a][k][c], one product per (instance, a)
     GemmDesc d3{R, R, h[1], q.cnt * R, Up1, (long long)h[1] * R, 1, R, T2, (long long)R * h[1] * R, R, 1,
@@ -749,9 +788,37 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   }
   TK_CUDA(cudaMemcpyAsync(herrp, errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (with_err) TK_CUDA(cudaMemcpyAsync(hesum, esum, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, s));
+  if (spec) TK_CUDA(cudaMemcpyAsync(ih, ints, (size_t)(ranks_end - (const char*)ints), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   if (pf) pf->collect();
+  if (spec && ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
   if (*herrp != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
+  if (spec) {
+    // the assumption: no instance wants more pairs than phase A computed
+    bool holds = true;
+    for (int a = 0; a < nmodes && holds; ++a)
+      for (int b = 0; b < B && holds; ++b) {
+        const int rf = req[b].o.rfix[a];
+        const int needed = rf > 0 ? std::min(rf, m[a]) : hA[4 * ((size_t)a * B + b) + 2];
+        if (needed > mA[a]) holds = false;
+      }
+    if (!holds) continue;  // the results block is freed with mem
+    // the ranks, flags and eigenvalues the speculation did not know
+    for (int a = 0; a < nmodes; ++a) {
+      Phase& p0 = ph[a][0];
+      p0.out.assign(hA + 4 * B * a, hA + 4 * B * (a + 1));
+      p0.hl.assign(hlamA[a], hlamA[a] + (size_t)B * mA[a]);
+      for (int b = 0; b < B; ++b) {
+        fin[b].r[a] = p0.out[4 * b];
+        fin[b].flags[a] = (unsigned)p0.out[4 * b + 1];
+      }
+    }
+    for (int b = 0; b < B; ++b)
+      for (int a = nmodes; a < 3; ++a) {
+        fin[b].r[a] = fin[b].r[0];
+        fin[b].flags[a] = fin[b].flags[0];
+      }
+  }
 
   for (int b = 0; b < B; ++b) {
     tk_result* res = new tk_result();
@@ -781,6 +848,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       res->rel_error = std::sqrt(hesum[2 * slot] / hesum[2 * slot + 1]);
     }
     outs[b] = res;
+  }
+  return;
   }
 }
 

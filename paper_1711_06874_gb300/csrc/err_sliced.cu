@@ -155,7 +155,10 @@ __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
 #pragma unroll 1
     for (int jj = 0; jj < JB; ++jj) {
       // X = sum_c V(l, c) W2(j, c): leading products exact (p + e) and summed
-      // with Kahan's compensation, the small terms summed plainly
+      // with Kahan's compensation, the small terms summed plainly.  A zero
+      // product leaves the compensated pair as it is (a Kahan step with 0
+      // would renormalise it), so the zero-padded columns beyond the rank do
+      // not change any bit: the result does not depend on the padding R.
       float S = 0.0f, comp = 0.0f, lo = 0.0f;
 #pragma unroll
       for (int c = 0; c < kR; ++c) {
@@ -165,8 +168,10 @@ __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
           const float e = fmaf(vl[c].hi, w.hi, -p);
           const float y = __fsub_rn(p, comp);
           const float t = __fadd_rn(S, y);
-          comp = __fsub_rn(__fsub_rn(t, S), y);
-          S = t;
+          const float cn = __fsub_rn(__fsub_rn(t, S), y);
+          const bool nz = p != 0.0f;
+          S = nz ? t : S;
+          comp = nz ? cn : comp;
           lo += e + fmaf(vl[c].hi, w.lo, vl[c].lo * w.hi);
         }
       }

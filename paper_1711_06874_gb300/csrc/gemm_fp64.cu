@@ -624,7 +624,7 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
   // (their number set by K), tiles otherwise; the choice depends on the per-entry shape alone (never on
   // the batch), so an entry's result does not either
   if (d.fixed_order) {
-    if ((long long)d.M * d.N <= 4096 && d.K >= 32) {
+    if (!d.tiles_only && (long long)d.M * d.N <= 4096 && d.K >= 32) {
       const int L = d.K >= 128 ? 32 : 4;
       const long long threads = (long long)L * outs;
       const unsigned blocks = (unsigned)std::min<long long>((threads + 255) / 256, 8192);

@@ -185,7 +185,9 @@ inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 
 // replaced by amap[b1] when amap is given).  Every output is one FMA chain in
 // k order (or, for few outputs, a fixed split of k over several lanes);
 // fixed_order = 1 makes that choice from the per-entry shape alone, so that
-// each entry's result does not depend on the batch it is part of.
+// each entry's result does not depend on the batch it is part of; tiles_only
+// keeps one k-order chain per output for every shape, so that an output does
+// not depend on the size of its matrix either.
 struct GemmDesc {
   int M, N, K, batch;
   const double* A;
@@ -198,6 +200,7 @@ struct GemmDesc {
   long long sAb2 = 0, sBb2 = 0, sCb2 = 0;
   const int* amap = nullptr;
   int fixed_order = 0;
+  int tiles_only = 0;  // fixed order on tiles whatever the shape
 };
 void gemm_f64(const GemmDesc& d, cudaStream_t s);
 // Same product, but instead of storing C accumulates sum (R - C)^2 and sum R^2
