@@ -65,6 +65,7 @@ void once_per_device(const void* key, void (*fn)()) {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -304,6 +305,7 @@ void tk_destroy(tk_ctx* ctx) {
   tk_serve_stop(ctx);  // no-op when not serving
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  ctx->graphs.release();
   ctx->prof.release();
   ctx->ws.release();
   ctx->ws2.release();
@@ -479,7 +481,7 @@ tk_result* solve_one(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, 
   if (!fold_applicable(*grid, *opts)) return tucker_full(ctx, kernel, grid, opts, s);
   SolveReq rq{*kernel, *grid, *opts};
   tk_result* res = nullptr;
-  solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->prof, &rq, 1, &res, s);
+  solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->graphs, &ctx->prof, &rq, 1, &res, s);
   return res;
 }
 
@@ -544,7 +546,7 @@ int tk_batch(tk_ctx* ctx, int count, const tk_kernel* kernels, const tk_grid* gr
           const int i = idx[c0 + j];
           rq[j] = SolveReq{kernels[i], grids[i], opts[i]};
         }
-        solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->prof, rq.data(), cnt, rs.data(), s);
+        solve_bucket(ctx, ctx->ws, ctx->ws2, ctx->pin, ctx->side, &ctx->graphs, &ctx->prof, rq.data(), cnt, rs.data(), s);
         for (int j = 0; j < cnt; ++j) outs[idx[c0 + j]] = rs[j];
       }
     }

@@ -67,6 +67,7 @@ struct WorkerState {
   Workspace pre, post;
   HostPinned pin;
   SideStream side;
+  GraphCache graphs;
   cudaStream_t stream = nullptr;
 };
 
@@ -130,7 +131,7 @@ void tk_server::worker_main(int /*wid*/) {
     int status = TK_OK;
     try {
       if (!w.stream) fail(TK_ECUDA, "cannot create a worker stream");
-      solve_bucket(ctx, w.pre, w.post, w.pin, w.side, nullptr, reqs.data(), (int)reqs.size(), outs.data(), w.stream);
+      solve_bucket(ctx, w.pre, w.post, w.pin, w.side, &w.graphs, nullptr, reqs.data(), (int)reqs.size(), outs.data(), w.stream);
     } catch (const Error& e) {
       status = e.status;
     } catch (...) {
@@ -165,6 +166,7 @@ void tk_server::worker_main(int /*wid*/) {
     done_cv.notify_all();
   }
   lk.unlock();
+  w.graphs.release();
   w.pre.release();
   w.post.release();
   if (w.stream) {

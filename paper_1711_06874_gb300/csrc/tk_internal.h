@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -26,6 +27,7 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what);
 // Counts the library's kernel launches (diagnostics, tk_kernel_launches).
 void count_launch();
+void count_launches(unsigned long long k);  // k kernels of a replayed graph
 #define TK_CUDA(call) ::tk::check_cuda((call), #call)
 #define TK_LAUNCH(what) (::tk::count_launch(), ::tk::check_cuda(cudaGetLastError(), what))
 
@@ -59,6 +61,22 @@ struct HostPinned {
   size_t bytes = 0;
   char* reserve(size_t need);
   ~HostPinned();
+};
+
+// Instantiated CUDA graphs of whole solves, one per (bucket key, batch size,
+// error path).  A graph is valid only for the placement it was captured with:
+// the bases of the two device workspaces and of the pinned staging, whose
+// layout the capture baked into its kernels' arguments and copies.
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void* bases[3] = {};
+  unsigned long long kernels = 0;  // kernel nodes, for the launch count
+  int seen = 0;                    // plain runs of this plan so far
+};
+struct GraphCache {
+  std::map<std::vector<double>, SolveGraph> graphs;
+  void release();
+  ~GraphCache() { release(); }
 };
 
 // A second stream with two events, for work that overlaps the solve.
@@ -290,9 +308,11 @@ int validate_request(const tk_kernel* k, const tk_grid* g, const tk_opts* o);
 // and results), for admission.
 size_t bucket_bytes_per_instance(const BucketKey& key);
 // Solves B requests of one bucket (fold_applicable for all), enqueued on s;
-// synchronises s twice (ranks, then results).  outs[b] receives new results.
-void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, SideStream& side, Profiler* pf,
-                  const SolveReq* req, int B, tk_result** outs, cudaStream_t s);
+// synchronises s once (small batches whose ranks phase A covers) or twice
+// (ranks, then results).  outs[b] receives new results.  graphs (optional):
+// where repeated solves of one plan are replayed from.
+void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin, SideStream& side,
+                  GraphCache* graphs, Profiler* pf, const SolveReq* req, int B, tk_result** outs, cudaStream_t s);
 
 }  // namespace tk
 
@@ -326,6 +346,7 @@ struct tk_ctx {
   tk::Workspace ws2;  // stages after it (sized from the ranks)
   tk::HostPinned pin; // staging of the engine's small transfers
   tk::SideStream side; // overlapped independent sampling (with_error)
+  tk::GraphCache graphs; // replayed solves
   std::string last_error;
   int sm_count = 0;
   tk::Profiler prof;

@@ -9,7 +9,10 @@
   * a batch against the oracle, small instances element by element;
   * the 256-instance n = 128 parameter sweep at full size: sampled instances
     against the oracle, every instance for orthonormal factors, the HOSVD
-    bound and its rel_error.
+    bound and its rel_error;
+  * repeated solves of one plan (run plainly, captured into a CUDA graph,
+    replayed, recaptured after the workspaces moved): bitwise the same
+    results and the same kernel count every time.
 """
 import math
 
@@ -214,3 +217,38 @@ def test_error_during_solve(ctx, wl):
         plain = ctx.tucker(probs[0], precision=precision)
         with pytest.raises(binding.TuckerError):
             plain.solve_error
+
+
+def test_repeated_solves_replay_bitwise(ctx, wl):
+    """A small solve seen before runs as one CUDA graph (captured on its second
+    run, replayed after): every result is bitwise the plain run's, the kernel
+    count is the same, and a solve whose workspaces moved (a larger solve in
+    between grows them) is run plainly and captured again."""
+    from paper_1711_06874_gb300 import binding
+
+    cases = [
+        (wl.problem(0, nu=1.2, ell=0.2, n=48, eps=1e-6, rmax=24), binding.TK_SLICED_BF16, True),
+        (wl.problem(0, nu=0.5, ell=0.3, n=40, eps=1e-6, rmax=24), binding.TK_FP64, False),
+        (wl.problem(0, nu=0.8, ell=(0.3, 0.4, 0.5), n=(20, 24, 28), eps=1e-6, rmax=24), binding.TK_FP64, False),
+        (wl.problem(0, nu=0.6, ell=0.15, n=40, eps=1e-8, rmax=20), binding.TK_SLICED_BF16, True),  # ranks > 12
+    ]
+    for i, (p, prec, we) in enumerate(cases):
+        big = wl.problem(0, nu=1.2, ell=0.2, n=160 + 32 * i, eps=1e-6, rmax=24)  # larger each case
+        runs = []
+        for k in range(7):
+            if k == 4:
+                ctx.tucker(big, precision=prec, with_error=we).free()  # grows the workspaces
+            l0 = binding.Context.kernel_launches()
+            r = ctx.tucker(p, precision=prec, with_error=we)
+            runs.append((r, binding.Context.kernel_launches() - l0))
+        r0, k0 = runs[0]
+        for r, k in runs[1:]:
+            assert k == k0
+            assert r.ranks == r0.ranks
+            assert r.norm2 == r0.norm2
+            assert _same(r.core(), r0.core())
+            for a in range(3):
+                assert _same(r.factor(a), r0.factor(a)), a
+                assert _same(r.eigenvalues(a), r0.eigenvalues(a)), a
+            if we:
+                assert r.solve_error == r0.solve_error
