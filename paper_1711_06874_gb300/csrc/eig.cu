@@ -1156,8 +1156,12 @@ __global__ void k_rank_batch(const double* lam, int m, const double* trace, cons
 }  // namespace
 
 // The subspace carries kMargin columns beyond the m requested pairs (up to
-// n and kMaxM) so that the m leading Ritz pairs converge.
-constexpr int kMargin = 8;
+// n and kMaxM) so that the m leading Ritz pairs converge.  After the FP32
+// pass and one FP64 pass the leading pairs of the covariance Grams sit at the
+// FP64 noise floor already with four extra columns: the projector onto the
+// rank-r factor moves by 1e-10 .. 4e-9 of |F| (eight columns: 5e-11 .. 1e-9),
+// and the eigenvalues by about u lambda_1 either way.
+constexpr int kMargin = 4;
 
 static int subspace_cols(int n, int m) { return std::min(std::min(n, kMaxM), m + kMargin); }
 
