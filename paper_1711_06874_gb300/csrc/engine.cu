@@ -372,7 +372,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   size_t pin_down = carve_bytes<int>(nint) + carve_bytes<double>(B);
   for (int a = 0; a < nmodes; ++a) pin_down += carve_bytes<double>((size_t)B * mA[a]);
   const size_t pin_up = carve_bytes<KernelDev>(B) + carve_bytes<double>(B);
-  const size_t pin_desc = carve_bytes<int>(B) + carve_bytes<UnfoldDesc>((size_t)B * nmodes) +
+  const size_t pin_desc = 2 * carve_bytes<int>(B) + carve_bytes<UnfoldDesc>((size_t)B * nmodes) +
                           carve_bytes<CoreDesc>(B) + carve_bytes<int>(1) + carve_bytes<double>(2 * (size_t)B);
   char* pbase = pin.reserve(pin_up + pin_down + pin_desc + 1024);
   size_t poff = 0;
@@ -393,6 +393,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   int* amaph = (int*)ptake(sizeof(int) * B);
   UnfoldDesc* udh = (UnfoldDesc*)ptake(sizeof(UnfoldDesc) * B * nmodes);
   CoreDesc* cdh = (CoreDesc*)ptake(sizeof(CoreDesc) * B);
+  int* rkh = (int*)ptake(sizeof(int) * B);  // mode-1 ranks (the error's sums)
   int* herrp = (int*)ptake(sizeof(int));
   double* hesum = (double*)ptake(sizeof(double) * 2 * B);
   std::memset(ih, 0, sizeof(int) * 16);
@@ -487,6 +488,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   int* amap = nullptr;
   UnfoldDesc* ud = nullptr;
   CoreDesc* cd = nullptr;
+  int* rkd = nullptr;
   int Rmax = 4;
 
   // Host side of the second phase: the eigenpairs each instance ends with
@@ -662,7 +664,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
         if (err_ff && err_sliced_supported(h[0], q.R))
           eff_scr = std::max(eff_scr, err_sliced_scratch_bytes(h[0], q.R, q.cnt));
       }
-    post.reserve(carve_bytes<double>(ttm) + carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
+    post.reserve(carve_bytes<double>(ttm) + 2 * carve_bytes<int>(B) + carve_bytes<UnfoldDesc>(ndesc) +
                      carve_bytes<CoreDesc>(B) + carve_bytes<char>(ttm_scr) +
                      (with_err ? carve_bytes<double>(errw) + carve_bytes<double>((size_t)B * eparts) +
                                      carve_bytes<double>(2 * (size_t)B) + carve_bytes<char>(eff_scr)
@@ -678,8 +680,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     amap = post.take<int>(B);
     ud = post.take<UnfoldDesc>(ndesc);
     cd = post.take<CoreDesc>(B);
-    // amap, ud and cd are carved back to back here and in the pinned staging
-    if ((char*)cdh - (char*)amaph != (char*)cd - (char*)amap)
+    rkd = post.take<int>(B);
+    // amap, ud, cd and rk are carved back to back here and in the pinned staging
+    if ((char*)rkh - (char*)amaph != (char*)rkd - (char*)amap)
       fail(TK_ECUDA, "pinned staging does not mirror the device descriptors");
     groupOf.clear();
     for (size_t q = 0; q < gb.size(); ++q) groupOf[gb[q].R] = (int)q;
@@ -710,13 +713,14 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       c.r1 = fin[b].r[0];
       c.r2 = fin[b].r[1];
       c.r3 = fin[b].r[2];
+      rkh[b] = fin[b].r[0];
     }
   };
 
   // Launches of the second phase, and the copies down of what the host reads
   // after the final synchronisation.
   auto launch_second = [&](bool spec) {
-    TK_CUDA(cudaMemcpyAsync(amap, amaph, (size_t)((char*)(cdh + B) - (char*)amaph), cudaMemcpyHostToDevice, s));
+    TK_CUDA(cudaMemcpyAsync(amap, amaph, (size_t)((char*)(rkh + B) - (char*)amaph), cudaMemcpyHostToDevice, s));
     if (pf) pf->begin(TK_STAGE_RANK, s);
     k_unfold<<<dim3(Rmax, (unsigned)ndesc), 128, 0, s>>>(ud);
     TK_LAUNCH("k_unfold");
@@ -778,7 +782,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
         double* W2 = ewbase + woff;
         woff += ((size_t)q.cnt * h[0] * h[1] * R + 31) & ~size_t(31);
         if (err_ff && err_sliced_supported(h[0], R)) {
-          err_sliced_batch(sv, normF2, Up0, Cp, h[0], R, q.cnt, amap + q.off, effscr, esum + 2 * (size_t)q.off, s);
+          // the ranks: on the device from the rank rule (speculative), else staged
+          err_sliced_batch(sv, normF2, Up0, Cp, h[0], R, q.cnt, amap + q.off, spec ? outA : rkd, spec ? 4 : 1,
+                           effscr, esum + 2 * (size_t)q.off, s);
           continue;
         }
         // W1[i][(b,c)] = sum_a V1[i][a] B[a][(b,c)]

@@ -244,13 +244,19 @@ void err_lowrank_batch(const double* W, long long sW, const double* Ut, long lon
 
 // Error during a solve on the sliced path (isotropic, octant side h): the
 // octant residual against the Gram's slices sv, in float-float arithmetic, for
-// the cnt instances of one rank group (padded rank R <= 32, h a multiple of 8):
+// the cnt instances of one rank group (padded rank R <= 32, h a multiple of 8).
+// The octant tensor must be symmetric under permutations of its three indices
+// (an isotropic kernel on a cubic grid, one factor for all modes): the sum runs
+// over i <= j <= l with orbit weights.
 // V [pos][h][R] the shared factor, Bcore [pos][R][R][R] the padded core;
 // esum [pos][2] = (|Fh - Xh|^2, |Fh|^2) with |Fh|^2 from normF2[amap[pos]].
 bool err_sliced_supported(int h, int R);
 size_t err_sliced_scratch_bytes(int h, int R, int cnt);
+// rk: the rank of bucket instance b at rk[b * rk_stride] (the sums run over
+// the rank's columns of the zero-padded factor and core).
 void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V, const double* Bcore, int h, int R,
-                      int cnt, const int* amap, void* scratch, double* esum, cudaStream_t s);
+                      int cnt, const int* amap, const int* rk, int rk_stride, void* scratch, double* esum,
+                      cudaStream_t s);
 
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
