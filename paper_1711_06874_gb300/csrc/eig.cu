@@ -959,10 +959,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
   jacobi_body(p.H, p.m, p.lam, p.V, p.sweeps);
 }
 
-// One m x m problem per CTA: H + b * m^2 -> lam + b * m, V + b * m^2.
-__global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V) {
+__device__ void rank_warp(const double* lam, int m, double trace, double nf, double eps, int rmax, int rfix,
+                          double u_eff, int n_eig, int n_flag, int* out);
+
+// One m x m problem per CTA: H + b * m^2 -> lam + b * m, V + b * m^2.  With
+// rank.out set, warp 0 then applies the truncation rule to the leading mr
+// eigenvalues and trace[b].
+__global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V,
+                                                         RankArgs rank, int mr, const double* trace) {
   const long long b = blockIdx.x;
   jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr);
+  if (rank.out == nullptr) return;
+  __syncthreads();  // the sorted eigenvalues are in lam
+  if (threadIdx.x < 32)
+    rank_warp(lam + b * m, mr, trace[b], rank.normF2[b], rank.eps[b], rank.rmax[b], rank.rfix[b], rank.u_eff,
+              rank.n_eig, rank.n_flag, rank.out + 4 * b);
 }
 
 // Canonical sign of each column of V (n x m row-major, ld = m); instance blockIdx.y.
@@ -1096,7 +1107,8 @@ __global__ void k_persym_merge(const double* __restrict__ le, const double* __re
   }
 }
 
-// Truncation rule (Task 1, Sec. 2.1, with the HOSVD bound of Sec. 3.2):
+// Truncation rule (Task 1, Sec. 2.1, with the HOSVD bound of Sec. 3.2), in
+// compensated FP64 (the route of rank_warp below for non-finite inputs):
 // the smallest r >= 1 whose discarded sum, tail beyond the m computed
 // eigenvalues (trace - their sum) plus the clamped computed ones from r on,
 // summed smallest first, is <= eps^2 |F|^2 / 3; capped at rmax.
@@ -1137,19 +1149,124 @@ __device__ void rank_body(const double* lam, int m, double trace, double nf, dou
   out[1] = flags;
 }
 
-__global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2, double eps, int rmax,
-                       int rfix, double u_eff, int n, int* out) {
-  if (threadIdx.x == 0) rank_body(lam, m, trace[0], normF2[0], eps, rmax, rfix, u_eff, n, n, out);
+// 128-bit halves through warp shuffles.
+__device__ __forceinline__ __int128 shfl_down128(__int128 v, int off) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+  const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, off);
+  const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, off);
+  return (__int128)(((unsigned __int128)h2 << 64) | l2);
+}
+__device__ __forceinline__ __int128 shfl_xor128(__int128 v, int mask) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+  const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, mask);
+  const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, mask);
+  return (__int128)(((unsigned __int128)h2 << 64) | l2);
 }
 
-// One instance per thread: lam + b m, trace[b], normF2[b], eps[b], rmax[b],
+__device__ __forceinline__ int exp_field(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
+// v 2^sh truncated toward zero, as a signed 128-bit integer (zero and
+// subnormal v give 0); sh is chosen so that |v| 2^sh < 2^120.
+__device__ __forceinline__ __int128 fixed128(double v, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const int sft = ex - 1075 + sh;  // v = mant 2^(ex - 1075), at most 67 here
+  unsigned __int128 mg = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  if (sft >= 0)
+    mg <<= sft;
+  else
+    mg = (sft > -64) ? (mg >> -sft) : 0;
+  const __int128 r = (__int128)mg;
+  return (b >> 63) ? -r : r;
+}
+
+// The same rule, by one warp for one instance (all 32 lanes call it, lane 0
+// writes out), in exact fixed-point arithmetic: every input is scaled by one
+// power of two so that the largest lies below 2^120 and truncated to a
+// 128-bit integer (losing less than 2^-120 of the largest input each), after
+// which the sums and comparisons are exact.  Lane t holds lam[3t .. 3t + 2];
+// the discarded sums come from one suffix scan over the lanes.  m > 96 or a
+// non-finite input takes the FP64 route.
+__device__ void rank_warp(const double* lam, int m, double trace, double nf, double eps, int rmax, int rfix,
+                          double u_eff, int n_eig, int n_flag, int* out) {
+  const int lane = threadIdx.x & 31;
+  const double thr = eps * eps * nf / 3.0;
+  double v[3];
+  int emax = max(exp_field(trace), exp_field(thr));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int i = 3 * lane + k;
+    v[k] = (i < m) ? lam[i] : 0.0;
+    emax = max(emax, exp_field(v[k]));
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if (emax == 0x7FF || m > 96) {
+    if (lane == 0) rank_body(lam, m, trace, nf, eps, rmax, rfix, u_eff, n_eig, n_flag, out);
+    return;
+  }
+  const int sh = 1142 - emax;  // the largest input below 2^120
+  __int128 P[3], tot = 0, ptot = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const __int128 L = fixed128(v[k], sh);
+    P[k] = L > 0 ? L : 0;
+    tot += L;
+    ptot += P[k];
+  }
+  __int128 S = tot;  // sum of the m eigenvalues
+  for (int o = 16; o > 0; o >>= 1) S += shfl_xor128(S, o);
+  const __int128 TH = fixed128(thr, sh);
+  __int128 extra = fixed128(trace, sh) - S;  // the tail beyond the m computed
+  if (extra <= 0 || m >= n_eig) extra = 0;
+  // clamped sums over the lanes from this one up
+  __int128 suf = ptot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 x = shfl_down128(suf, o);
+    if (lane + o < 32) suf += x;
+  }
+  // the discarded sum from q on, q = 3 lane + 2 down to 3 lane; the smallest
+  // q in [1, m - 1] whose sum is within the threshold
+  __int128 run = extra + (suf - ptot);
+  int qbest = 0x7FFFFFFF;
+#pragma unroll
+  for (int k = 2; k >= 0; --k) {
+    const int q = 3 * lane + k;
+    run += P[k];
+    if (q >= 1 && q < m && run <= TH) qbest = q;
+  }
+  qbest = __reduce_min_sync(0xffffffffu, qbest);
+  if (lane == 0) {
+    int r = (qbest != 0x7FFFFFFF) ? qbest : (extra <= TH ? m : m + 1);
+    int flags = 0;
+    out[2] = r;  // before the cap; m + 1 means "more than the m computed"
+    if (rfix > 0) {
+      r = rfix < m ? rfix : m;
+    } else if (r > rmax) {
+      r = rmax;
+      flags |= TK_RANK_CAPPED;
+    }
+    if (thr < 10.0 * u_eff * (double)n_flag * nf) flags |= TK_EPS_UNREACHABLE_AT_PRECISION;
+    out[0] = r;
+    out[1] = flags;
+  }
+}
+
+__global__ void k_rank(const double* lam, int m, const double* trace, const double* normF2, double eps, int rmax,
+                       int rfix, double u_eff, int n, int* out) {
+  rank_warp(lam, m, trace[0], normF2[0], eps, rmax, rfix, u_eff, n, n, out);
+}
+
+// One instance per warp: lam + b m, trace[b], normF2[b], eps[b], rmax[b],
 // rfix[b], out + 4 b.
 __global__ void k_rank_batch(const double* lam, int m, const double* trace, const double* normF2, const double* epsv,
                              const int* rmaxv, const int* rfixv, double u_eff, int n_eig, int n_flag, int B,
                              int* out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B)
-    rank_body(lam + (size_t)b * m, m, trace[b], normF2[b], epsv[b], rmaxv[b], rfixv[b], u_eff, n_eig, n_flag,
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (b < B)  // uniform over the warp
+    rank_warp(lam + (size_t)b * m, m, trace[b], normF2[b], epsv[b], rmaxv[b], rfixv[b], u_eff, n_eig, n_flag,
               out + 4 * b);
 }
 
@@ -1393,7 +1510,7 @@ bool uses_start32(int n, int ms) { return ms != n && n <= 256 && start32_smem(n,
 
 // trace: written by the FP32 start kernel when that path runs (the caller
 // computes it otherwise).
-void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profiler* pf) {
+void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profiler* pf, const RankArgs* rank) {
   const int n = g.n, ms = g.ms, m = g.m;
   if (ms == n) {
     // whole matrices: Jacobi directly
@@ -1444,7 +1561,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     gemm_f64(d2, s);
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
-  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH);
+  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH, rank ? *rank : RankArgs{}, m, trace);
   TK_LAUNCH("k_jacobi_strided");
   if (pf) pf->end(s);
   if (ms == n) {
@@ -1466,7 +1583,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B) { return group_doubles(n, m, B) + 4096; }
 
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf) {
+                   cudaStream_t s, Profiler* pf, const RankArgs* rank) {
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   if (B < 1) return;
   set_attrs();
@@ -1475,7 +1592,7 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
     k_trace<<<B, 32, 0, s>>>(G, n, trace);
     TK_LAUNCH("k_trace");
   }
-  solve_group(g, B, trace, s, pf);
+  solve_group(g, B, trace, s, pf, rank);
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }
@@ -1483,8 +1600,7 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
 void rank_rule_batch(const double* lam, int m, const double* trace, const double* normF2, const double* eps,
                      const int* rmax, const int* rfix, double u_eff, int n_eig, int n_flag, int B, int* out,
                      cudaStream_t s) {
-  k_rank_batch<<<(B + 127) / 128, 128, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n_eig, n_flag, B,
-                                               out);
+  k_rank_batch<<<(B + 3) / 4, 128, 0, s>>>(lam, m, trace, normF2, eps, rmax, rfix, u_eff, n_eig, n_flag, B, out);
   TK_LAUNCH("k_rank_batch");
 }
 

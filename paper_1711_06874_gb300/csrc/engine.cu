@@ -439,12 +439,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       else
         gram_f64_batch(Fh, h, a, B, G[a], (double*)gscr, s);
       if (pf) pf->end(s);
+      // the eigensolver's Jacobi kernel also applies the rank rule
+      const RankArgs ra{normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], outA + 4 * B * a};
       if (pf) pf->begin(TK_STAGE_EIG, s);
-      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf);
-      if (pf) pf->end(s);
-      if (pf) pf->begin(TK_STAGE_RANK, s);
-      rank_rule_batch(lamA[a], mA[a], traceA[a], normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], B,
-                      outA + 4 * B * a, s);
+      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf, &ra);
       if (pf) pf->end(s);
     }
   };

@@ -271,9 +271,21 @@ void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, 
 // B instances with the same n and m: G [b][n][n] -> lam [b][m], V [b][n][m]
 // (canonical signs), trace [b].  Each instance's result is the same whatever
 // the batch.
+// With rank (optional), the Jacobi kernel also applies the truncation rule
+// to each instance's m eigenvalues and trace (as rank_rule_batch, with
+// rank->out + 4 b receiving instance b's results), saving a launch.
+struct RankArgs {
+  const double* normF2;  // [b]
+  const double* eps;     // [b]
+  const int* rmax;       // [b]
+  const int* rfix;       // [b]
+  double u_eff;
+  int n_eig, n_flag;
+  int* out;              // [b][4]
+};
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf = nullptr);
+                   cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr);
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.
