@@ -228,7 +228,7 @@ def _roofline(prof, prob, precision, clocks, peaks, peak_src):
     the K_nu table, the tensor-core Gram, the eigensolver's QR and Jacobi."""
     n = prob.n[0]
     h = (n + 1) // 2
-    ms = min(h, 12 + 8)  # subspace of the first eigenpair pass
+    ms = min(h, 12 + 4)  # subspace of the first eigenpair pass (12 pairs, 4 extra columns)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_gpu = FP64_TFLOPS_NOMINAL * sm_mhz / 2070.0
     fp64_sm = fp64_gpu / 152.0
@@ -252,7 +252,7 @@ def _roofline(prof, prob, precision, clocks, peaks, peak_src):
     elif top in ("qr", "jacobi"):
         if top == "qr":
             work = 8.0 * h * ms * ms - 8.0 * ms ** 3 / 3.0  # Householder QR plus the explicit Q
-            name = "k_householder_qr_strided (FP64, one CTA)"
+            name = "k_qr_factor64 + k_form_q (FP64, one CTA factorisation)"
         else:
             work = 7.0 * ms ** 3 * JACOBI_SWEEPS  # 7 m^3 flops per sweep (A two-sided, V one-sided)
             name = "k_jacobi_strided (FP64, one CTA)"

@@ -134,17 +134,18 @@ TK_HD void tk_bessel_k_miller(const tk_nu_consts& c, double x, double* kmu, doub
   // one step longer so that it is never below the FP64 value
   const int N = 13 + (int)(180.0f / (float)x) < kMillerTerms - 1 ? 13 + (int)(180.0f / (float)x) : kMillerTerms - 1;
   const double mu2 = mu * mu;
-  const double x2 = 2.0 * x;
   double u_next = 0.0, u = 1.0;  // u_{k+1}, u_k at k = N
   double acc = c.Ck[N];
-  double dk2 = 2.0 * (double)N;  // 2 k
+  // a = 2 (k + x): rounded once at k = N, then lowered by 2 per step, which
+  // is exact (a < 2^53), so the loop costs four FP64 instructions a step
+  double a = 2.0 * ((double)N + x);
   for (int k = N; k >= 1; --k) {
     // u_{k-1} = 2 (k + x) u_k - ((k + 1/2)^2 - mu^2) u_{k+1}
-    const double u_prev = fma(dk2 + x2, u, -c.Mk[k] * u_next);
+    const double u_prev = fma(a, u, -c.Mk[k] * u_next);
     u_next = u;
     u = u_prev;
     acc = fma(c.Ck[k - 1], u, acc);
-    dk2 -= 2.0;
+    a -= 2.0;
   }
   // K_mu e^x = sqrt(pi / (2 x)) u_0 / acc and
   // K_{mu+1} e^x = K_mu e^x (x + mu + 1/2 - (1/4 - mu^2) u_1 / u_0) / x

@@ -742,12 +742,17 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
         d1.fixed_order = 1;
         gemm_f64(d1, s);
       }
-      // mode 1: T2[a][(k,c)] = sum_i V1[i][a] T1[i][(k,c)]
-      GemmDesc d2{R, h[1] * R, h[0], q.cnt, Up0, (long long)h[0] * R, 1, R, T1, (long long)h[0] * h[1] * R,
-                  (long long)h[1] * R, 1, T2, (long long)R * h[1] * R, (long long)h[1] * R, 1};
-      d2.fixed_order = 1;
-      d2.tiles_only = 1;  // its outputs must not depend on the padded rank R
-      gemm_f64(d2, s);
+      // mode 1: T2[a][(k,c)] = sum_i V1[i][a] T1[i][(k,c)]; symmetric in
+      // (a, c) for an isotropic problem
+      if (nmodes == 1 && ttm2_sym_supported(h[0], R)) {
+        ttm2_sym_batch(Up0, T1, T2, h[0], R, q.cnt, s);
+      } else {
+        GemmDesc d2{R, h[1] * R, h[0], q.cnt, Up0, (long long)h[0] * R, 1, R, T1, (long long)h[0] * h[1] * R,
+                    (long long)h[1] * R, 1, T2, (long long)R * h[1] * R, (long long)h[1] * R, 1};
+        d2.fixed_order = 1;
+        d2.tiles_only = 1;  // its outputs must not depend on the padded rank R
+        gemm_f64(d2, s);
+      }
       // mode 2: B[a][b][c] = sum_k V2[k][b] T2[a][k][c], one product per (instance, a)
       GemmDesc d3{R, R, h[1], q.cnt * R, Up1, (long long)h[1] * R, 1, R, T2, (long long)R * h[1] * R, R, 1,
                   Cp, (long long)R * R * R, R, 1};

@@ -652,6 +652,87 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Second TTM of the isotropic core, T2(a, k, c) = sum_i V(i, a) T1(i, k, c).
+// F is symmetric under permutations of its indices and the three modes share
+// V, so T2(a, k, c) = sum_{i,l} V(i, a) V(l, c) F(i, k, l) = T2(c, k, a): only
+// a <= c is formed and mirrored (R (R + 1) / 2 of the R^2 pairs).  One CTA per
+// (k, instance) holds V and T1(:, k, :) in shared memory; each output is four
+// FMA chains over interleaved i (i = q mod 4), added in a fixed order.
+namespace {
+
+constexpr int kTtm2Threads = 256;
+
+__global__ void __launch_bounds__(kTtm2Threads) k_ttm2_sym(const double* __restrict__ V, const double* __restrict__ T1,
+                                                          double* __restrict__ T2, int h, int R) {
+  extern __shared__ double sm2[];
+  double* Vs = sm2;          // [i][a]
+  double* Ts = sm2 + h * R;  // [i][c]
+  const int k = blockIdx.x, pos = blockIdx.y;
+  V += (size_t)pos * h * R;
+  T1 += (size_t)pos * h * h * R;
+  T2 += (size_t)pos * R * h * R;
+  // both operands in 16-byte asynchronous copies, all in flight at once: V
+  // whole, T1(:, k, :) as h runs of R values (R a multiple of 4, so every run
+  // starts on a 16-byte boundary)
+  const int vp = h * R / 2, rp = R / 2;
+  for (int e = threadIdx.x; e < 2 * vp; e += blockDim.x) {
+    const double* src;
+    double* dst;
+    if (e < vp) {
+      src = V + 2 * e;
+      dst = Vs + 2 * e;
+    } else {
+      const int f = e - vp, i = f / rp, q = f - i * rp;
+      src = T1 + ((size_t)i * h + k) * R + 2 * q;
+      dst = Ts + (size_t)i * R + 2 * q;
+    }
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int npairs = R * (R + 1) / 2;
+  const int items = 4 * npairs, span = (items + 31) & ~31;  // whole warps in every pass
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    const bool valid = t < items;
+    const int p = valid ? t >> 2 : 0, q = t & 3;
+    // pair p -> (a, c), a <= c, row by row
+    int a = 0, rem = p;
+    while (rem >= R - a) {
+      rem -= R - a;
+      ++a;
+    }
+    const int c = a + rem;
+    double acc = 0.0;
+    if (valid)
+      for (int i = q; i < h; i += 4) acc = fma(Vs[i * R + a], Ts[i * R + c], acc);
+    // the four chains of an output sit in four adjacent lanes: a fixed tree
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (valid && q == 0) {
+      T2[((size_t)a * h + k) * R + c] = acc;
+      T2[((size_t)c * h + k) * R + a] = acc;
+    }
+  }
+}
+
+}  // namespace
+
+size_t ttm2_sym_smem(int h, int R) { return sizeof(double) * 2 * (size_t)h * R; }
+
+bool ttm2_sym_supported(int h, int R) { return R % 4 == 0 && ttm2_sym_smem(h, R) <= 96 * 1024; }
+
+void ttm2_sym_batch(const double* V, const double* T1, double* T2, int h, int R, int cnt, cudaStream_t s) {
+  if (!ttm2_sym_supported(h, R)) fail(TK_EINVAL, "ttm2_sym: shape out of range");
+  if ((((uintptr_t)V | (uintptr_t)T1) & 15) != 0) fail(TK_EINVAL, "ttm2_sym: operands not 16-byte aligned");
+  once_per_device((const void*)&k_ttm2_sym, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_ttm2_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+  });
+  k_ttm2_sym<<<dim3(h, cnt), kTtm2Threads, ttm2_sym_smem(h, R), s>>>(V, T1, T2, h, R);
+  TK_LAUNCH("k_ttm2_sym");
+}
+
+// ---------------------------------------------------------------------------
 // Error of a rank-K product against a reference: sum (R - X)^2 and sum R^2
 // with X = W Ut^T (W: M x K, ld K; Ut: N x K, ld K; R: M x N row-major) for a
 // small K.  Each CTA takes 64 rows and 128 columns; W's rows and Ut's rows

@@ -221,6 +221,12 @@ struct GemmDesc {
   int tiles_only = 0;  // fixed order on tiles whatever the shape
 };
 void gemm_f64(const GemmDesc& d, cudaStream_t s);
+// Second TTM of an isotropic core (F symmetric under index permutations, one
+// factor for all modes), for cnt instances: T2 [pos][a][k][c] =
+// sum_i V [pos][i][a] T1 [pos][i][k][c] with V h x R, T1 h x h x R; the pairs
+// a <= c are formed and mirrored.  Each output is a fixed-order sum.
+bool ttm2_sym_supported(int h, int R);
+void ttm2_sym_batch(const double* V, const double* T1, double* T2, int h, int R, int cnt, cudaStream_t s);
 // Same product, but instead of storing C accumulates sum (R - C)^2 and sum R^2
 // over all entries against the reference R (same layout as C); per-block
 // partials go to `partials` (2 * gridsize doubles), then a fixed-order sum
