@@ -1583,7 +1583,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B) { return group_doubles(n, m, B) + 4096; }
 
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf, const RankArgs* rank) {
+                   cudaStream_t s, Profiler* pf, const RankArgs* rank, bool signs) {
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   if (B < 1) return;
   set_attrs();
@@ -1593,6 +1593,7 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
     TK_LAUNCH("k_trace");
   }
   solve_group(g, B, trace, s, pf, rank);
+  if (!signs) return;
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");
 }

@@ -413,8 +413,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     if (pf) pf->begin(TK_STAGE_EVAL, s);
     if (fused) {
       const SliceView v = gram_slices_view(gscr, h, 0, B);
-      eval_octant_slices(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part, normF2, s,
-                         pf);
+      // |F|^2: summed by the Gram's reduction kernel below
+      eval_octant_slices(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part, nullptr,
+                         s, pf);
     } else {
       eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
     }
@@ -433,7 +434,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     for (int a = nmodes - 1; a >= 0; --a) {
       if (pf) pf->begin(TK_STAGE_GRAM, s);
       if (fused)
-        gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf);
+        gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf, NormParts{part, h[0], normF2});
       else if (sliced)
         gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf);
       else
@@ -442,7 +443,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       // the eigensolver's Jacobi kernel also applies the rank rule
       const RankArgs ra{normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], outA + 4 * B * a};
       if (pf) pf->begin(TK_STAGE_EIG, s);
-      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf, &ra);
+      // (the unfolding fixes the factors' signs: none here)
+      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf, &ra, false);
       if (pf) pf->end(s);
     }
   };
@@ -547,7 +549,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                                                                                                  per, GJ);
         TK_LAUNCH("k_gather_mats");
         if (pf) pf->begin(TK_STAGE_EIG, s);
-        sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s, pf);
+        sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s, pf, nullptr, false);
         if (pf) pf->end(s);
         if (pf) pf->begin(TK_STAGE_RANK, s);
         rank_rule_batch(lamE[a][l], mp, traceB, aux, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj, outB, s);

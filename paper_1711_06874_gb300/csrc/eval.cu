@@ -326,32 +326,10 @@ __global__ void k_eval_oct(const KernelDev* __restrict__ kd, GridDev g, double* 
   if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = t;
 }
 
-// |Fh|^2 of instance blockIdx.x from its nparts block partials: strided
-// Neumaier sums, then a fixed tree.
+// |Fh|^2 of instance blockIdx.x from its nparts block partials.
 __global__ void __launch_bounds__(256) k_parts_final(const double* __restrict__ part, int nparts,
                                                      double* __restrict__ out) {
-  __shared__ double rs[256], rc[256];
-  const double* p = part + (size_t)blockIdx.x * nparts;
-  double s = 0.0, c = 0.0;
-  for (int r = threadIdx.x; r < nparts; r += blockDim.x) {
-    const double x = p[r], t = s + x;
-    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-    s = t;
-  }
-  rs[threadIdx.x] = s;
-  rc[threadIdx.x] = c;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      double a = rs[threadIdx.x], ac = rc[threadIdx.x] + rc[threadIdx.x + w];
-      const double x = rs[threadIdx.x + w], t = a + x;
-      ac += (fabs(a) >= fabs(x)) ? (a - t) + x : (x - t) + a;
-      rs[threadIdx.x] = t;
-      rc[threadIdx.x] = ac;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[blockIdx.x] = rs[0] + rc[0];
+  norm_parts_block(part + (size_t)blockIdx.x * nparts, nparts, out + blockIdx.x);
 }
 
 // Blocks per instance: a function of the shape alone (about 8 rows each).
@@ -461,8 +439,10 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   const int threads = (h >= 128) ? 1024 : 256;
   k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
   TK_LAUNCH("k_gather_slice");
-  k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);
-  TK_LAUNCH("k_parts_final");
+  if (normF2 != nullptr) {
+    k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);
+    TK_LAUNCH("k_parts_final");
+  }
 }
 
 size_t eval_octant_parts(const tk_grid& g) { return oct_blocks(g); }

@@ -370,13 +370,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 // 32-bit halves and rounded to FP64 once.  SG lanes share one entry, each
 // summing every SG-th split, and combine their integer sums by shuffles
 // (exact, so the result does not depend on SG).
+// The last B blocks (with norm.part set) sum the instances' |F|^2 partials
+// instead (the grid-stride loop spans the first nred blocks).
 template <int SG>
 __global__ void k_tc_reduce(const long long* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
-                            const int* __restrict__ rowexp, double* __restrict__ G) {
+                            const int* __restrict__ rowexp, double* __restrict__ G, int nred, NormParts norm) {
+  if ((int)blockIdx.x >= nred) {
+    const int b = blockIdx.x - nred;
+    norm_parts_block(norm.part + (size_t)b * norm.nparts, norm.nparts, norm.normF2 + b);
+    return;
+  }
   const long long per = (long long)n * n;
   const long long total = per * B;
   const int g = threadIdx.x % SG;
-  const long long stride = (long long)gridDim.x * blockDim.x / SG;
+  const long long stride = (long long)nred * blockDim.x / SG;
   for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / SG; e - (threadIdx.x % 32) / SG < total;
        e += stride) {
     // every lane of a warp runs the shuffles: lanes past the end add zeros
@@ -461,7 +468,7 @@ CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long 
 // The tensor-core Gram and its reduction over B instances whose slices are
 // at S ([b][s][row][Kp]) and row exponents at rowexp ([b][row]).
 void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, long long* P, double* G, int* err,
-                 cudaStream_t s, Profiler* pf) {
+                 cudaStream_t s, Profiler* pf, NormParts norm = NormParts{nullptr, 0, nullptr}) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
   const CUtensorMap mapA = slice_map(enc, S, p.Kp, p.nrows, B, kTM);
@@ -475,12 +482,15 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
   TK_LAUNCH("k_gram_tc");
   if (pf) pf->end(s);
   const long long total = (long long)p.nrows * p.nrows * B;
+  const int extra = norm.part != nullptr ? B : 0;
   if (p.nsplit >= 8) {
-    k_tc_reduce<8><<<(unsigned)std::min<long long>((8 * total + 255) / 256, 8192), 256, 0, s>>>(
-        P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G);
+    const int nred = (int)std::min<long long>((8 * total + 255) / 256, 8192);
+    k_tc_reduce<8><<<(unsigned)(nred + extra), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G,
+                                                           nred, norm);
   } else {
-    k_tc_reduce<1><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(
-        P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G);
+    const int nred = (int)std::min<long long>((total + 255) / 256, 8192);
+    k_tc_reduce<1><<<(unsigned)(nred + extra), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G,
+                                                           nred, norm);
   }
   TK_LAUNCH("k_tc_reduce");
 }
@@ -537,7 +547,7 @@ void gram_sliced_batch(const double* F, const int n[3], int mode, int B, double*
 // The Gram from slices already written into the scratch (by a sampling
 // kernel that sliced the mode-1 rows while it evaluated them).
 void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* err, cudaStream_t s,
-                          Profiler* pf) {
+                          Profiler* pf, NormParts norm) {
   const TcPlan p = tc_plan(n, 0, 152, B);
   char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   size_t off = 0;
@@ -550,7 +560,7 @@ void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* 
   int* rowexp = (int*)carve(sizeof(int) * (size_t)B * p.nrows);
   __nv_bfloat16* S = (__nv_bfloat16*)carve(sizeof(__nv_bfloat16) * (size_t)B * kSlices * p.nrows * p.Kp);
   long long* P = (long long*)carve(sizeof(long long) * (size_t)B * p.nsplit * p.nblocks * kTM * kTN);
-  run_tc_gram(p, B, S, rowexp, P, G, err, s, pf);
+  run_tc_gram(p, B, S, rowexp, P, G, err, s, pf, norm);
 }
 
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B) {

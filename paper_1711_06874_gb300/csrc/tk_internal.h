@@ -177,15 +177,52 @@ struct SliceView {
   long long Kp;
 };
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B);
+// |F|^2 partials of an instance summed by one CTA of 256 threads (strided
+// Neumaier sums, then a fixed tree): out = sum of p[0 .. nparts).
+struct NormParts {
+  const double* part;  // [b][nparts]
+  int nparts;
+  double* normF2;      // [b]
+};
+#ifdef __CUDACC__
+// One CTA of 256 threads: *out = sum of p[0 .. nparts), strided Neumaier sums
+// then a fixed tree (the same bits whichever kernel runs it).
+__device__ inline void norm_parts_block(const double* p, int nparts, double* out) {
+  __shared__ double rs[256], rc[256];
+  double sm = 0.0, c = 0.0;
+  for (int r = threadIdx.x; r < nparts; r += blockDim.x) {
+    const double x = p[r], t = sm + x;
+    c += (fabs(sm) >= fabs(x)) ? (sm - t) + x : (x - t) + sm;
+    sm = t;
+  }
+  rs[threadIdx.x] = sm;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      double a = rs[threadIdx.x], ac = rc[threadIdx.x] + rc[threadIdx.x + w];
+      const double x = rs[threadIdx.x + w], t = a + x;
+      ac += (fabs(a) >= fabs(x)) ? (a - t) + x : (x - t) + a;
+      rs[threadIdx.x] = t;
+      rc[threadIdx.x] = ac;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = rs[0] + rc[0];
+}
+#endif
 // The mode-1 Gram of B tensors whose slices and row exponents were already
-// written where gram_slices_view(scratch, n, 0, B) points.
+// written where gram_slices_view(scratch, n, 0, B) points.  With norm.part
+// set, the Gram's reduction kernel also sums each instance's |F|^2 partials.
 void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* err, cudaStream_t s,
-                          Profiler* pf = nullptr);
+                          Profiler* pf = nullptr, NormParts norm = NormParts{nullptr, 0, nullptr});
 // Sampling fused with the mode-1 slicing for cubic isotropic grids: the
 // distinct-value table, then per octant row i the values Fh(i, j, l) (never
 // stored), their largest magnitude (row exponent), their BF16 slices and
 // their sum of squares; normF2[b] = |F_b|^2.  rowexp: [b][h]; S: [b][6][h][Kp]
 // (zero beyond h^2); part: B x h doubles.
+// With normF2 == nullptr the partials are left for the Gram's reduction
+// (gram_sliced_prepared with NormParts{part, h, normF2}).
 void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
                         long long Kp, double* part, double* normF2, cudaStream_t s, Profiler* pf = nullptr);
 // (d) First TTM (mode 3) of Bg instances on the tensor cores from the mode-1
@@ -275,7 +312,7 @@ void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double*
 void sym_eig_topm_persym(const double* G, int n, int m, double* lam, double* V, double* trace_out, int* safe,
                          double* scratch, cudaStream_t s);
 // B instances with the same n and m: G [b][n][n] -> lam [b][m], V [b][n][m]
-// (canonical signs), trace [b].  Each instance's result is the same whatever
+// (canonical signs unless signs = false), trace [b].  Each instance's result is the same whatever
 // the batch.
 // With rank (optional), the Jacobi kernel also applies the truncation rule
 // to each instance's m eigenvalues and trace (as rank_rule_batch, with
@@ -290,8 +327,10 @@ struct RankArgs {
   int* out;              // [b][4]
 };
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
+// signs = false leaves the eigenvectors' signs as the solver produced them
+// (for callers that fix the signs themselves, such as the factor unfolding).
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr);
+                   cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr, bool signs = true);
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.
