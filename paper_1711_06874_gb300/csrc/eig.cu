@@ -528,10 +528,7 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
-size_t start32_smem(int n, int ms) {
-  return sizeof(float) *
-         ((((size_t)n * n + 3) & ~size_t(3)) + (size_t)panel_ld<float>(n) * ms + (size_t)n * ((ms + 3) & ~3));
-}
+size_t start32_smem(int n, int ms) { return sizeof(float) * (size_t)panel_ld<float>(n) * ms; }
 
 // FP64 -> FP32 by the bit pattern (truncated; zero below the FP32 range,
 // which holds every entry of a Gram matrix of FP32-range data): the start only
@@ -555,103 +552,66 @@ __device__ __forceinline__ float hash_uniform_f(unsigned long long seed, unsigne
   return (float)(unsigned)(z >> 40) * (2.0f / 16777216.0f) - 1.0f;
 }
 
-// Also writes the trace of G to trace[blockIdx.x] when trace is given.
-// Y = G Omega in FP32, its Householder factorisation in registers (as the
-// FP64 pass) and the factor Q formed one warp per column (Q e_c =
-// H_0 ... H_c e_c, no barrier between reflectors); Q goes out in FP64.
-template <int kRPL>
-__global__ void __launch_bounds__(256) k_start32(const double* __restrict__ G, int n, int ms,
-                                                 unsigned long long seed, double* __restrict__ Q0,
-                                                 double* __restrict__ trace) {
-  extern __shared__ float s32[];
-  __shared__ float beta[kMaxM + 1];
-  __shared__ float v0s[kMaxM + 1];
-  __shared__ float bsm[kMaxM + 1];
-  const int ld = panel_ld<float>(n);
-  float* Gs = s32;           // n x n
-  float* Y = Gs + ((n * n + 3) & ~3);  // n x ms, column-major, stride ld (16-byte aligned)
-  float* W = Y + ld * ms;    // Omega ([k][c], stride (ms + 3) & ~3)
-  G += (size_t)blockIdx.x * n * n;
-  Q0 += (size_t)blockIdx.x * n * ms;
-  if (trace != nullptr && threadIdx.x < 32) {
-    const double t = trace_warp(G, n);
-    if (threadIdx.x == 0) trace[blockIdx.x] = t;
-  }
-  {
-    // G in 16-byte loads (two entries), eight in flight per thread (n even;
-    // odd n loads entries one by one)
-    const int tot = n * n, nt = blockDim.x;
-    if ((n & 1) == 0) {
-      const double2* G2 = reinterpret_cast<const double2*>(G);
-      const int tot2 = tot / 2;
-      for (int e0 = threadIdx.x; e0 < tot2; e0 += 8 * nt) {
-        double2 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot2) ? __ldg(G2 + e0 + u * nt) : make_double2(0.0, 0.0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (e0 + u * nt < tot2)
-            reinterpret_cast<float2*>(Gs)[e0 + u * nt] =
-                make_float2(double_to_float_trunc(v[u].x), double_to_float_trunc(v[u].y));
-      }
-    } else {
-      for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? __ldg(G + e0 + u * nt) : 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (e0 + u * nt < tot) Gs[e0 + u * nt] = double_to_float_trunc(v[u]);
-      }
-    }
-  }
-  // Omega stored k-major ([k][c], stride ms4): four columns in one 16-byte load
+// Y = G Omega in FP32 for the rows [8 blockIdx.x, +8) of instance
+// blockIdx.y, G converted by its bits and Omega drawn from the counter-based
+// hash; G is symmetric, so Y(i, c) = sum_k G(i, k) Omega(k, c), each output
+// one FMA chain in k order.  Block 0 also writes the trace of G when trace is
+// given.  Y goes to Yg [b][c][i] (ld n).  Many CTAs share the product, so
+// reading G is no longer one SM's job.
+constexpr int kGoRows = 8;
+
+size_t gomega32_smem(int n, int ms) {
+  return sizeof(float) * ((size_t)kGoRows * n + (size_t)n * ((ms + 3) & ~3));
+}
+
+__global__ void __launch_bounds__(256) k_gomega32(const double* __restrict__ G, int n, int ms,
+                                                  unsigned long long seed, float* __restrict__ Yg,
+                                                  double* __restrict__ trace) {
+  extern __shared__ float so[];
   const int ms4 = (ms + 3) & ~3;
+  float* Gr = so;               // rows i0 .. i0 + 7 of G
+  float* W = so + kGoRows * n;  // Omega [k][c], stride ms4
+  const int b = blockIdx.y, i0 = blockIdx.x * kGoRows;
+  const int rows = min(kGoRows, n - i0);
+  G += (size_t)b * n * n;
+  if (trace != nullptr && blockIdx.x == 0 && threadIdx.x < 32) {
+    const double t = trace_warp(G, n);
+    if (threadIdx.x == 0) trace[b] = t;
+  }
+  const double* Gi = G + (size_t)i0 * n;  // the rows are contiguous
+  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) Gr[e] = double_to_float_trunc(__ldg(Gi + e));
   for (int e = threadIdx.x; e < n * ms4; e += blockDim.x) {
     const int k = e / ms4, c = e - k * ms4;
     W[e] = (c < ms) ? hash_uniform_f(seed, (unsigned long long)c * n + k) : 0.0f;
   }
   __syncthreads();
-  // Y(i, c) = sum_k G(k, i) Omega(k, c) (G symmetric), a 4 x 4 block of
-  // outputs per thread: rows i0..i0+3 and columns c0..c0+3 from two 16-byte
-  // shared loads per k
-  {
-    const int nb4 = (n + 3) / 4, cb4 = ms4 / 4;
-    for (int e = threadIdx.x; e < nb4 * cb4; e += blockDim.x) {
-      const int cb = e / nb4, ib = e - cb * nb4;
-      const int i0 = 4 * ib, c0 = 4 * cb;
-      float acc[4][4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
-      const bool full = i0 + 3 < n && (n & 3) == 0;
-      for (int k = 0; k < n; ++k) {
-        float g[4];
-        if (full) {
-          const float4 g4 = *reinterpret_cast<const float4*>(Gs + (size_t)k * n + i0);
-          g[0] = g4.x;
-          g[1] = g4.y;
-          g[2] = g4.z;
-          g[3] = g4.w;
-        } else {
-#pragma unroll
-          for (int p = 0; p < 4; ++p) g[p] = (i0 + p < n) ? Gs[(size_t)k * n + i0 + p] : 0.0f;
-        }
-        const float4 o4 = *reinterpret_cast<const float4*>(W + (size_t)k * ms4 + c0);
-        const float o[4] = {o4.x, o4.y, o4.z, o4.w};
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(g[p], o[q], acc[p][q]);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c0 + q < ms)
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-            if (i0 + p < n) Y[(size_t)(c0 + q) * ld + i0 + p] = acc[p][q];
-    }
+  for (int t = threadIdx.x; t < rows * ms; t += blockDim.x) {
+    const int c = t / rows, r = t - c * rows;
+    const float* g = Gr + (size_t)r * n;
+    float acc = 0.0f;
+    for (int k = 0; k < n; ++k) acc = fmaf(g[k], W[(size_t)k * ms4 + c], acc);
+    Yg[((size_t)b * ms + c) * n + i0 + r] = acc;
+  }
+}
+
+// The FP32 start block from Y = G Omega (k_gomega32): Householder
+// factorisation in registers (as the FP64 pass) and the factor Q formed one
+// warp per column (Q e_c = H_0 ... H_c e_c, no barrier between reflectors);
+// Q goes out in FP64.
+template <int kRPL>
+__global__ void __launch_bounds__(256) k_start32(const float* __restrict__ Yg, int n, int ms,
+                                                 double* __restrict__ Q0) {
+  extern __shared__ float s32[];
+  __shared__ float beta[kMaxM + 1];
+  __shared__ float v0s[kMaxM + 1];
+  __shared__ float bsm[kMaxM + 1];
+  const int ld = panel_ld<float>(n);
+  float* Y = s32;  // n x ms, column-major, stride ld
+  Yg += (size_t)blockIdx.x * ms * n;
+  Q0 += (size_t)blockIdx.x * n * ms;
+  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    Y[(size_t)c * ld + i] = Yg[e];
   }
   __syncthreads();
   qr_factor_reg<float, kRPL>(Y, ld, n, ms, bsm, beta, v0s);
@@ -687,7 +647,12 @@ __global__ void __launch_bounds__(256) k_start32(const double* __restrict__ G, i
 
 // k_start32 for n <= 256 (kRPL = ceil(n / 32)).
 void start32_launch(const double* G, int n, int ms, int B, unsigned long long seed, double* Q0, double* trace,
-                    cudaStream_t s) {
+                    float* Yscr, cudaStream_t s) {
+  once_per_device((const void*)&k_gomega32, [] {
+    TK_CUDA(cudaFuncSetAttribute(k_gomega32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  k_gomega32<<<dim3((n + kGoRows - 1) / kGoRows, B), 256, gomega32_smem(n, ms), s>>>(G, n, ms, seed, Yscr, trace);
+  TK_LAUNCH("k_gomega32");
   const size_t smem = start32_smem(n, ms);
   switch ((n + 31) / 32) {
 #define TK_START32_CASE(K)                                                                                   \
@@ -695,7 +660,7 @@ void start32_launch(const double* G, int n, int ms, int B, unsigned long long se
     once_per_device((const void*)&k_start32<K>, [] {                                                         \
       TK_CUDA(cudaFuncSetAttribute(k_start32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); \
     });                                                                                                      \
-    k_start32<K><<<B, 256, smem, s>>>(G, n, ms, seed, Q0, trace);                                            \
+    k_start32<K><<<B, 256, smem, s>>>(Yscr, n, ms, Q0);                                                      \
     break;
     TK_START32_CASE(1)
     TK_START32_CASE(2)
@@ -1506,7 +1471,9 @@ EigGroup carve_group(double* p, const double* G, int n, int m, int B, double* la
 
 // The FP32 start (with the trace folded in) serves the subspace path when
 // its shared-memory image fits.
-bool uses_start32(int n, int ms) { return ms != n && n <= 256 && start32_smem(n, ms) <= kStart32SmemMax; }
+bool uses_start32(int n, int ms) {
+  return ms != n && n <= 256 && start32_smem(n, ms) <= kStart32SmemMax && gomega32_smem(n, ms) <= kStart32SmemMax;
+}
 
 // trace: written by the FP32 start kernel when that path runs (the caller
 // computes it otherwise).
@@ -1538,7 +1505,8 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     };
     if (uses_start32(n, ms)) {
       // FP32 pass from the random block, then one FP64 pass
-      start32_launch(g.G, n, ms, B, seed, g.Q, trace, s);
+      // (Y's storage holds the FP32 product until the FP64 pass writes it)
+      start32_launch(g.G, n, ms, B, seed, g.Q, trace, reinterpret_cast<float*>(g.Y), s);
       power(g.Q);
       qr();
     } else {
