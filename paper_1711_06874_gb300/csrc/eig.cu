@@ -726,7 +726,13 @@ __device__ __forceinline__ void exact_rotation(float cf, float sf, double& c, do
   s = fma(-s0, kl, fma(-s0, kh, s0));
 }
 
-__device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, double* Vout, int* sweeps_out) {
+// u_data: the relative accuracy of the matrix's data (2^-53 for FP64 data,
+// 2^-48 for a Gram from the BF16 slices): a plane is rotated only while its
+// off-diagonal entry exceeds u_data |A|_F, below which the data do not
+// determine it, and two indices whose diagonals both lie below
+// 64 u_data |A|_F (the noise block) are left alone.
+__device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, double* Vout, int* sweeps_out,
+                            double u_data) {
   extern __shared__ double sm[];
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
   const int np = mp / 2;        // planes per step
@@ -766,8 +772,8 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) fs += A[e] * A[e];
   const double normA = sqrt(block_sum(fs, red));
   // thresholds as bit patterns: |x| > t  <=>  abs_bits(x) > bits(t) for t >= 0
-  const unsigned long long tau_b = abs_bits(0x1p-53 * normA);
-  const unsigned long long noise_b = abs_bits(0x1p-47 * normA);  // 64 u |A|_F
+  const unsigned long long tau_b = abs_bits(u_data * normA);
+  const unsigned long long noise_b = abs_bits(64.0 * u_data * normA);
   // f / mp for f < np mp by a 32-bit reciprocal (exact in this range)
   const unsigned magic = (unsigned)((0xFFFFFFFFull + mp) / mp);
   int sweep = 0;
@@ -921,7 +927,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
 
 __global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
   const JacProb& p = batch.p[blockIdx.x];
-  jacobi_body(p.H, p.m, p.lam, p.V, p.sweeps);
+  jacobi_body(p.H, p.m, p.lam, p.V, p.sweeps, 0x1p-53);
 }
 
 __device__ void rank_warp(const double* lam, int m, double trace, double nf, double eps, int rmax, int rfix,
@@ -931,9 +937,10 @@ __device__ void rank_warp(const double* lam, int m, double trace, double nf, dou
 // rank.out set, warp 0 then applies the truncation rule to the leading mr
 // eigenvalues and trace[b].
 __global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V,
-                                                         RankArgs rank, int mr, const double* trace) {
+                                                         RankArgs rank, int mr, const double* trace,
+                                                         double u_data) {
   const long long b = blockIdx.x;
-  jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr);
+  jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr, u_data);
   if (rank.out == nullptr) return;
   __syncthreads();  // the sorted eigenvalues are in lam
   if (threadIdx.x < 32)
@@ -1477,7 +1484,8 @@ bool uses_start32(int n, int ms) {
 
 // trace: written by the FP32 start kernel when that path runs (the caller
 // computes it otherwise).
-void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profiler* pf, const RankArgs* rank) {
+void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profiler* pf, const RankArgs* rank,
+                 double u_data) {
   const int n = g.n, ms = g.ms, m = g.m;
   if (ms == n) {
     // whole matrices: Jacobi directly
@@ -1529,7 +1537,8 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     gemm_f64(d2, s);
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
-  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH, rank ? *rank : RankArgs{}, m, trace);
+  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH, rank ? *rank : RankArgs{}, m, trace,
+                                                    u_data);
   TK_LAUNCH("k_jacobi_strided");
   if (pf) pf->end(s);
   if (ms == n) {
@@ -1551,7 +1560,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B) { return group_doubles(n, m, B) + 4096; }
 
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf, const RankArgs* rank, bool signs) {
+                   cudaStream_t s, Profiler* pf, const RankArgs* rank, bool signs, double u_data) {
   if (m < 1 || m > kMaxM || m > n) fail(TK_EINVAL, "sym_eig: need 1 <= m <= min(n, 96)");
   if (B < 1) return;
   set_attrs();
@@ -1560,7 +1569,7 @@ void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V,
     k_trace<<<B, 32, 0, s>>>(G, n, trace);
     TK_LAUNCH("k_trace");
   }
-  solve_group(g, B, trace, s, pf, rank);
+  solve_group(g, B, trace, s, pf, rank, u_data);
   if (!signs) return;
   k_canonical_sign<<<dim3(m, B), 256, 0, s>>>(V, n, m);
   TK_LAUNCH("k_canonical_sign");

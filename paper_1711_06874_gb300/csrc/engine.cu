@@ -444,7 +444,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       const RankArgs ra{normF2, epsv, rmaxv + a * B, rfixv + a * B, u_eff, h[a], n[a], outA + 4 * B * a};
       if (pf) pf->begin(TK_STAGE_EIG, s);
       // (the unfolding fixes the factors' signs: none here)
-      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf, &ra, false);
+      sym_eig_batch(G[a], h[a], mA[a], B, lamA[a], VA[a], traceA[a], escr, s, pf, &ra, false, u_eff);
       if (pf) pf->end(s);
     }
   };
@@ -549,7 +549,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                                                                                                  per, GJ);
         TK_LAUNCH("k_gather_mats");
         if (pf) pf->begin(TK_STAGE_EIG, s);
-        sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s, pf, nullptr, false);
+        sym_eig_batch(GJ, h[a], mp, nj, lamE[a][l], VE[a][l], traceB, escr, s, pf, nullptr, false, u_eff);
         if (pf) pf->end(s);
         if (pf) pf->begin(TK_STAGE_RANK, s);
         rank_rule_batch(lamE[a][l], mp, traceB, aux, epsv, ijd + nj, ijd + 2 * nj, u_eff, h[a], n[a], nj, outB, s);

@@ -329,8 +329,11 @@ struct RankArgs {
 size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
 // signs = false leaves the eigenvectors' signs as the solver produced them
 // (for callers that fix the signs themselves, such as the factor unfolding).
+// u_data: relative accuracy of G (gram_u_eff of its precision); the Jacobi
+// rotations stop at that level.
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
-                   cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr, bool signs = true);
+                   cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr, bool signs = true,
+                   double u_data = 0x1p-53);
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.
