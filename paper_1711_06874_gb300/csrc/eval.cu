@@ -423,6 +423,99 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
   }
 }
 
+__global__ void __launch_bounds__(1024) k_gather_slice2(const double* __restrict__ T, long long Q, int n, int h,
+                                                      long long Kp, int* __restrict__ rowexp,
+                                                      __nv_bfloat16* __restrict__ S, double* __restrict__ part) {
+  // For even n every octant point stands for 8 grid points and the table
+  // already holds 2 sqrt(2) C; for odd n the weight varies and is applied here.
+  __shared__ unsigned long long redm[32];
+  __shared__ double reds[32];
+  __shared__ int eshared;
+  const int i = blockIdx.x, b = blockIdx.y;
+  const double* Tb = T + (size_t)b * Q;
+  const int even = (n % 2 == 0);
+  const int ai = 2 * i + even;
+  const int ti = even ? 1 : (i > 0);
+  const int K = h * h;
+  auto value = [&](int j, int l) {
+    const int aj = 2 * j + even, al = 2 * l + even;
+    const int sq = ai * ai + aj * aj + al * al;
+    const double t = __ldg(Tb + (even ? (sq - 3) >> 3 : sq >> 2));
+    return even ? t : t * fold_scale(ti + (j > 0) + (l > 0));
+  };
+  // h even: each thread takes column pairs (c, c + 1) = (j h + l, j h + l + 1)
+  // of one row j; the pair index advances by blockDim.x per iteration, (j, l)
+  // by the quotient and remainder of that stride (no division in the loops)
+  const int step = 2 * (int)blockDim.x;
+  const int dj = step / h, dl = step - dj * h;
+  const int j0 = 2 * (int)threadIdx.x / h, l0 = 2 * (int)threadIdx.x - j0 * h;
+  // largest |value| by its bits (the order of non-negative doubles), sum of
+  // squares in pair order
+  unsigned long long mx = 0;
+  double ss = 0.0;
+  for (int c = 2 * threadIdx.x, j = j0, l = l0; c < K; c += step) {
+    const double v0 = value(j, l), v1 = value(j, l + 1);
+    const unsigned long long b0 = (unsigned long long)__double_as_longlong(v0) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b1 = (unsigned long long)__double_as_longlong(v1) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b0 > mx ? b0 : mx;
+    mx = b1 > mx ? b1 : mx;
+    ss = fma(v0, v0, ss);
+    ss = fma(v1, v1, ss);
+    j += dj;
+    l += dl;
+    if (l >= h) {
+      l -= h;
+      ++j;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long om = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = om > mx ? om : mx;
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    redm[threadIdx.x >> 5] = mx;
+    reds[threadIdx.x >> 5] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = redm[w] > m ? redm[w] : m;
+      t += reds[w];
+    }
+    int e = -1000;
+    const double mv = __longlong_as_double((long long)m);
+    if (mv > 0.0) frexp(mv, &e);
+    eshared = e;
+    rowexp[(size_t)b * h + i] = e;
+    part[(size_t)b * h + i] = t;
+  }
+  __syncthreads();
+  const int e = eshared;
+  const size_t plane = (size_t)h * Kp;
+  __nv_bfloat16* Sb = S + (size_t)b * kSlices * plane + (size_t)i * Kp;
+  for (int c = 2 * threadIdx.x, j = j0, l = l0; c < Kp; c += step) {
+    int d0[kSlices] = {0, 0, 0, 0, 0, 0}, d1[kSlices] = {0, 0, 0, 0, 0, 0};
+    if (c < K && e > -1000) {
+      slice_digits(value(j, l), e, d0);
+      slice_digits(value(j, l + 1), e, d1);
+    }
+    // both columns of a slice in one 4-byte store (c even, Kp even)
+#pragma unroll
+    for (int s2 = 0; s2 < kSlices; ++s2)
+      *reinterpret_cast<__nv_bfloat162*>(Sb + s2 * plane + c) =
+          __halves2bfloat162(slice_value(d0[s2], s2), slice_value(d1[s2], s2));
+    j += dj;
+    l += dl;
+    if (l >= h) {
+      l -= h;
+      ++j;
+    }
+  }
+}
+
 void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
                         long long Kp, double* part, double* normF2, cudaStream_t s, Profiler* pf) {
   const int n = g.n[0], h = (n + 1) / 2;
@@ -437,7 +530,10 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   // rows of h^2 values: wide blocks for long rows (a function of the shape
   // alone, so that each instance's sums do not depend on the batch)
   const int threads = (h >= 128) ? 1024 : 256;
-  k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
+  if (h % 2 == 0)
+    k_gather_slice2<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
+  else
+    k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
   TK_LAUNCH("k_gather_slice");
   if (normF2 != nullptr) {
     k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);

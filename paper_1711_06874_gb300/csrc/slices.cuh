@@ -32,6 +32,7 @@ static_assert(kPairs == (kMaxWeight + 1) * (kMaxWeight + 2) / 2, "pair table cov
 // Balanced base-256 digits of x 2^(7 - e): T = round(|x| 2^(47 - e)) from the
 // FP64 bits with integer operations (|x| < 2^e, so T < 2^47), then digits from
 // the bottom: x 2^(7 - e) = sum_s d_s 2^(-8s) + O(2^-41), |d_s| <= 128.
+static_assert(kSlices == 6, "slice_digits cuts T into 3 + 3 digits");
 __device__ __forceinline__ void slice_digits(double xv, int e, int (&d)[kSlices]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
   const int ex = (int)((bits >> 52) & 0x7FF);
@@ -42,13 +43,26 @@ __device__ __forceinline__ void slice_digits(double xv, int e, int (&d)[kSlices]
     if (rs < 64) T = (long long)((mant + (1ull << (rs - 1))) >> rs);
     if (bits >> 63) T = -T;
   }
+  // in 32-bit arithmetic: T = hi 2^24 + lo with lo balanced in [-2^23, 2^23);
+  // the three low digits come from lo (their carry goes to hi), the other
+  // three from hi; the same digits as cutting T from the bottom in 64 bits
+  const int lo = (int)((T + 0x800000) & 0xFFFFFF) - 0x800000;
+  int hi = (int)((T - lo) >> 24);
+  int t = lo;
 #pragma unroll
-  for (int s = kSlices - 1; s >= 1; --s) {
-    const long long r = ((T + 128) & 255) - 128;
-    d[s] = (int)r;
-    T = (T - r) >> 8;
+  for (int s = kSlices - 1; s >= 3; --s) {
+    const int r = ((t + 128) & 255) - 128;
+    d[s] = r;
+    t = (t - r) >> 8;
   }
-  d[0] = (int)T;
+  hi += t;
+#pragma unroll
+  for (int s = 2; s >= 1; --s) {
+    const int r = ((hi + 128) & 255) - 128;
+    d[s] = r;
+    hi = (hi - r) >> 8;
+  }
+  d[0] = hi;
 }
 
 __device__ __forceinline__ __nv_bfloat16 slice_value(int d, int s) {
