@@ -721,9 +721,12 @@ __device__ __forceinline__ void exact_rotation(float cf, float sf, double& c, do
   const float khi = 0.5f * dhi;
   const float klo = fmaf(-0.375f * dhi, dhi, 0.5f * dlo);
   const double c0 = float_to_double_bits(cf), s0 = float_to_double_bits(sf);
-  const double kh = float_to_double_bits(khi), kl = float_to_double_bits(klo);
-  c = fma(-c0, kl, fma(-c0, kh, c0));
-  s = fma(-s0, kl, fma(-s0, kh, s0));
+  // kappa = khi + klo in FP64 (exact while the two lie within 29 binary
+  // places of each other, and below 2^-53 kappa off otherwise): three FP64
+  // instructions for the pair, one rounding each
+  const double kappa = float_to_double_bits(khi) + float_to_double_bits(klo);
+  c = fma(-c0, kappa, c0);
+  s = fma(-s0, kappa, s0);
 }
 
 // u_data: the relative accuracy of the matrix's data (2^-53 for FP64 data,
@@ -808,8 +811,9 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
           // (c, s) are then made orthonormal to FP64 precision, so the
           // rotation applied is exactly orthogonal.
           const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
-          const float theta = scaled_float(aqq - app, e) / (2.0f * scaled_float(apq, e));
-          const float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+          // (fast approximate quotients: the angle only has to be close)
+          const float theta = __fdividef(scaled_float(aqq - app, e), 2.0f * scaled_float(apq, e));
+          const float t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
           const float cf = rsqrtf(fmaf(t, t, 1.0f));
           const float sf = t * cf;
           exact_rotation(cf, sf, c, s);
