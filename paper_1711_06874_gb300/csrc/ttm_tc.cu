@@ -9,10 +9,13 @@
 // output is that integer times 2^(e_i + f_c - 44): no rounding but the slices'
 // own, the same for any batch.
 //
-// One CTA per 128 rows (i, k) of one instance: warp 0 issues the TMA loads
-// (6 slices x 128 rows of A, 6 x Np rows of B per 32-deep K block, two
-// stages), warp 1 owns TMEM and issues the MMAs, warps 2..17 drain TMEM
-// (one lane quadrant and Np/4 columns each).  Bounded waits as in the Gram.
+// A CTA streams a run of consecutive (instance, 128-row tile) pairs of the
+// group (about one run per SM): warp 0 issues the TMA loads (6 slices x 128
+// rows of A, 6 x Np rows of B per 32-deep K block, two stages, the ring
+// running on across tiles, so the next tile's loads overlap this tile's
+// drain), warp 1 owns TMEM and issues the MMAs, warps 2..17 drain TMEM (one
+// lane quadrant and Np/4 columns each) and write each tile's rows.  Bounded
+// waits as in the Gram.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -51,6 +54,9 @@ struct TtmArgs {
   int h1, h2, h3;  // octant extents (K = h3)
   int R, Np;       // output columns and their padding
   int nkb;         // K blocks of 32
+  int ntiles;      // row tiles of kTM per instance
+  int tiles_per_cta;  // consecutive (instance, tile) pairs a CTA streams
+  int Bg;             // instances of the group
   const int* amap;    // group instance -> bucket instance
   const int* rowexp;  // bucket: [b][h1]
   const int* colexp;  // group: [j][Np]
@@ -99,8 +105,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = (uint32_t*)(bars + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.z;  // instance of the group
-  const int row0 = blockIdx.x * kTM;
+  // this CTA's run of (instance, tile) pairs u = j ntiles + tile
+  const int u0 = blockIdx.x * args.tiles_per_cta;
+  const int u1 = min(args.Bg * args.ntiles, u0 + args.tiles_per_cta);
   const int Np = args.Np;
   const int sliceB = Np * kKB * 2;  // bytes of one B slice per stage
   const int stage_tx = kOperandBytesA + kSlices * sliceB;
@@ -126,124 +133,139 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const int inst = args.amap[j];
-      int issued = 0;
-      for (int k = 0; k < nkb; ++k) {
-        const int st = k % kStages;
-        const uint32_t use = k / kStages;
-        if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
-        unsigned char* sa = smem + st * kStageBytes;
-        tc::mbar_expect_tx(&full[st], stage_tx);
-        tc::tma_load_4d(sa, &tmapA, &full[st], k * kKB, row0, 0, inst);
-        tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], k * kKB, 0, 0, j);
-        issued = k + 1;
+      int g = 0, issued = 0;  // stage uses, over all tiles of the run
+      bool ok = true;
+      for (int u = u0; u < u1 && ok; ++u) {
+        const int j = u / args.ntiles, row0 = (u - j * args.ntiles) * kTM;
+        const int inst = args.amap[j];
+        for (int k = 0; k < nkb; ++k, ++g) {
+          const int st = g % kStages;
+          const uint32_t use = g / kStages;
+          if (g >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + st * kStageBytes;
+          tc::mbar_expect_tx(&full[st], stage_tx);
+          tc::tma_load_4d(sa, &tmapA, &full[st], k * kKB, row0, 0, inst);
+          tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], k * kKB, 0, 0, j);
+          issued = g + 1;
+        }
       }
-      for (int k = max(0, issued - kStages); k < issued; ++k)
-        tc::mbar_wait(&full[k % kStages], (k / kStages) & 1, args.err);
+      for (int q = max(0, issued - kStages); q < issued; ++q)
+        tc::mbar_wait(&full[q % kStages], (q / kStages) & 1, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, Np);
       bool ok = true;
-      int k = 0;
-      for (int ch = 0; ch < nchunks && ok; ++ch) {
-        if (ch > 0 && !tc::mbar_wait(acc_empty, (ch - 1) & 1, args.err)) {
-          ok = false;
-          break;
-        }
-        tc::fence_after_sync();
-        const int kend = min(nkb, (ch + 1) * kChunkBlocks);
-        uint32_t first_mask = (1u << kAcc) - 1;
-        for (; k < kend; ++k) {
-          const int st = k % kStages;
-          if (!tc::mbar_wait(&full[st], (k / kStages) & 1, args.err)) {
+      int g = 0, gc = 0;  // stage uses and accumulator rounds over the run
+      for (int u = u0; u < u1 && ok; ++u) {
+        int k = 0;
+        for (int ch = 0; ch < nchunks && ok; ++ch, ++gc) {
+          if (gc > 0 && !tc::mbar_wait(acc_empty, (gc - 1) & 1, args.err)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          unsigned char* sa = smem + st * kStageBytes;
-          unsigned char* sb = sa + kOperandBytesA;
-          const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
-          const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
+          const int kend = min(nkb, (ch + 1) * kChunkBlocks);
+          uint32_t first_mask = (1u << kAcc) - 1;
+          for (; k < kend; ++k, ++g) {
+            const int st = g % kStages;
+            if (!tc::mbar_wait(&full[st], (g / kStages) & 1, args.err)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            unsigned char* sa = smem + st * kStageBytes;
+            unsigned char* sb = sa + kOperandBytesA;
+            const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
+            const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
 #pragma unroll 1
-          for (int pidx = 0; pidx < kPairs; ++pidx) {
-            const int s = kPairS[pidx], t = kPairT[pidx];
-            const int acc = (s + t < 4) ? s + t : 4;
-            const uint32_t dt = tmem + acc * Np;
-            const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
-            first_mask &= ~(1u << acc);
-            const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
-            const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
-            tc::mma_bf16(dt, da, db, idesc, accum);
-            tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+            for (int pidx = 0; pidx < kPairs; ++pidx) {
+              const int s = kPairS[pidx], t = kPairT[pidx];
+              const int acc = (s + t < 4) ? s + t : 4;
+              const uint32_t dt = tmem + acc * Np;
+              const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
+              first_mask &= ~(1u << acc);
+              const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
+              const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
+              tc::mma_bf16(dt, da, db, idesc, accum);
+              tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+            }
+            tc::mma_commit(&empty[st]);
           }
-          tc::mma_commit(&empty[st]);
+          if (ok) tc::mma_commit(acc_full);
         }
-        if (ok) tc::mma_commit(acc_full);
       }
       tc::mma_commit(drain);
       tc::mbar_wait(drain, 0, args.err);
     }
   } else {
-    // ---------------- epilogue: TMEM -> int64 -> FP64 ----------------
+    // ---------------- epilogue: TMEM -> int64 -> FP64, per tile ----------------
     const int q = warp & 3;           // TMEM lane quadrant
     const int grp = (warp - 2) >> 2;  // column group
     const int cpg = Np / 4;           // 8, 16 or 24 columns
     const int row = q * 32 + lane;
-    long long V[kMaxEpiCols];
-#pragma unroll
-    for (int c = 0; c < kMaxEpiCols; ++c) V[c] = 0;
-    bool ok = true;
     const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + grp * cpg;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (!tc::mbar_wait(acc_full, ch & 1, args.err)) {
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
+    bool ok = true;
+    int gc = 0;
+    for (int u = u0; u < u1 && ok; ++u) {
+      long long V[kMaxEpiCols];
 #pragma unroll
-      for (int hh = 0; hh < kMaxEpiCols / 8; ++hh) {
-        if (hh * 8 < cpg) {
-          uint32_t r[8];
-          tc::tmem_ld8(base + hh * 8, r);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 16384.0f) * (1LL << 30);
-          tc::tmem_ld8(base + Np + hh * 8, r);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 4194304.0f) * (1LL << 22);
-          tc::tmem_ld8(base + 2 * Np + hh * 8, r);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 1073741824.0f) * (1LL << 14);
-          tc::tmem_ld8(base + 3 * Np + hh * 8, r);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 274877906944.0f) * (1LL << 6);
-          tc::tmem_ld8(base + 4 * Np + hh * 8, r);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 17592186044416.0f);
+      for (int c = 0; c < kMaxEpiCols; ++c) V[c] = 0;
+      for (int ch = 0; ch < nchunks; ++ch, ++gc) {
+        if (!tc::mbar_wait(acc_full, gc & 1, args.err)) {
+          ok = false;
+          break;
         }
-      }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty);
-    }
-    const int grow = row0 + row;
-    if (ok && grow < args.M) {
-      const int inst = args.amap[j];
-      const int e = args.rowexp[(size_t)inst * args.h1 + grow / args.h2];
-      const int* fexp = args.colexp + (size_t)j * Np;
-      double* out = args.T1 + ((size_t)j * args.M + grow) * args.R;
+        tc::fence_after_sync();
 #pragma unroll
-      for (int c = 0; c < kMaxEpiCols; ++c) {
-        const int col = grp * cpg + c;
-        if (c < cpg && col < args.R) {
-          const int f = fexp[col];
-          out[col] = (e > -1000 && f > -1000) ? ldexp((double)V[c], e + f - 44) : 0.0;
+        for (int hh = 0; hh < kMaxEpiCols / 8; ++hh) {
+          if (hh * 8 < cpg) {
+            uint32_t r[8];
+            tc::tmem_ld8(base + hh * 8, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 16384.0f) * (1LL << 30);
+            tc::tmem_ld8(base + Np + hh * 8, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 4194304.0f) * (1LL << 22);
+            tc::tmem_ld8(base + 2 * Np + hh * 8, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 1073741824.0f) * (1LL << 14);
+            tc::tmem_ld8(base + 3 * Np + hh * 8, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 274877906944.0f) * (1LL << 6);
+            tc::tmem_ld8(base + 4 * Np + hh * 8, r);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 17592186044416.0f);
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(acc_empty);
+      }
+      if (!ok) break;
+      const int j = u / args.ntiles;
+      const int grow = (u - j * args.ntiles) * kTM + row;
+      if (grow < args.M) {
+        const int inst = args.amap[j];
+        const int e = args.rowexp[(size_t)inst * args.h1 + grow / args.h2];
+        const int* fexp = args.colexp + (size_t)j * Np;
+        double* out = args.T1 + ((size_t)j * args.M + grow) * args.R;
+#pragma unroll
+        for (int c = 0; c < kMaxEpiCols; ++c) {
+          const int col = grp * cpg + c;
+          if (c < cpg && col < args.R) {
+            const int f = fexp[col];
+            out[col] = (e > -1000 && f > -1000) ? ldexp((double)V[c], e + f - 44) : 0.0;
+          }
         }
       }
     }
@@ -301,8 +323,22 @@ void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int 
   once_per_device((const void*)&k_ttm_tc, [] {
     TK_CUDA(cudaFuncSetAttribute(k_ttm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   });
-  TtmArgs a{(int)M, h1, h2, h3, R, Np, (h3 + kKB - 1) / kKB, amap, sv.rowexp, colexp, T1, err};
-  k_ttm_tc<<<dim3((unsigned)((M + kTM - 1) / kTM), 1, Bg), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
+  // about one run of consecutive (instance, tile) pairs per SM
+  static const int sms = [] {
+    int d = 0, v = 0;
+    if (cudaGetDevice(&d) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+      cudaGetLastError();
+      v = 152;
+    }
+    return std::max(v, 1);
+  }();
+  const int ntiles = (int)((M + kTM - 1) / kTM);
+  const long long total = (long long)ntiles * Bg;
+  const int tpc = (int)std::max<long long>(1, (total + sms - 1) / sms);
+  const unsigned nctas = (unsigned)((total + tpc - 1) / tpc);
+  TtmArgs a{(int)M, h1, h2, h3, R, Np, (h3 + kKB - 1) / kKB, ntiles, tpc, Bg, amap, sv.rowexp, colexp, T1, err};
+  k_ttm_tc<<<nctas, kThreads, kSmemBytes, s>>>(mapA, mapB, a);
   TK_LAUNCH("k_ttm_tc");
 }
 
