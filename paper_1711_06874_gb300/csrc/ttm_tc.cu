@@ -97,12 +97,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
-  uint64_t* full = bars;       // [kStages]
-  uint64_t* empty = bars + 2;  // [kStages]
-  uint64_t* acc_full = bars + 4;
-  uint64_t* acc_empty = bars + 5;
-  uint64_t* drain = bars + 6;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 8);
+  uint64_t* full = bars;           // [kStages]
+  uint64_t* empty = bars + 2;      // [kStages]
+  uint64_t* acc_full = bars + 4;   // [2]: per accumulator set
+  uint64_t* acc_empty = bars + 6;  // [2]
+  uint64_t* drain = bars + 8;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 10);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this CTA's run of (instance, tile) pairs u = j ntiles + tile
@@ -113,14 +113,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int stage_tx = kOperandBytesA + kSlices * sliceB;
   const int nkb = args.nkb;
   const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
+  // two accumulator sets in TMEM when they fit: the MMAs of one round then
+  // run while the epilogue drains the previous round
+  const int acc_cols = kAcc * Np;
+  const int nbuf = (2 * acc_cols <= 512) ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kEpiWarps);
+    }
     tc::mbar_init(drain, 1);
     tc::fence_barrier_init();
   }
@@ -164,11 +170,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = u0; u < u1 && ok; ++u) {
         int k = 0;
         for (int ch = 0; ch < nchunks && ok; ++ch, ++gc) {
-          if (gc > 0 && !tc::mbar_wait(acc_empty, (gc - 1) & 1, args.err)) {
+          // round gc uses set gc % nbuf, drained (gc / nbuf) times before
+          const int ab = gc % nbuf, ause = gc / nbuf;
+          if (ause > 0 && !tc::mbar_wait(&acc_empty[ab], (ause - 1) & 1, args.err)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
+          const uint32_t tset = tmem + ab * acc_cols;
           const int kend = min(nkb, (ch + 1) * kChunkBlocks);
           uint32_t first_mask = (1u << kAcc) - 1;
           for (; k < kend; ++k, ++g) {
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int pidx = 0; pidx < kPairs; ++pidx) {
               const int s = kPairS[pidx], t = kPairT[pidx];
               const int acc = (s + t < 4) ? s + t : 4;
-              const uint32_t dt = tmem + acc * Np;
+              const uint32_t dt = tset + acc * Np;
               const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
               first_mask &= ~(1u << acc);
               const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc::mma_commit(&empty[st]);
           }
-          if (ok) tc::mma_commit(acc_full);
+          if (ok) tc::mma_commit(&acc_full[ab]);
         }
       }
       tc::mma_commit(drain);
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int grp = (warp - 2) >> 2;  // column group
     const int cpg = Np / 4;           // 8, 16 or 24 columns
     const int row = q * 32 + lane;
-    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + grp * cpg;
+    const uint32_t base0 = tmem + ((uint32_t)(q * 32) << 16) + grp * cpg;
     bool ok = true;
     int gc = 0;
     for (int u = u0; u < u1 && ok; ++u) {
@@ -216,11 +225,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < kMaxEpiCols; ++c) V[c] = 0;
       for (int ch = 0; ch < nchunks; ++ch, ++gc) {
-        if (!tc::mbar_wait(acc_full, gc & 1, args.err)) {
+        const int ab = gc % nbuf;
+        if (!tc::mbar_wait(&acc_full[ab], (gc / nbuf) & 1, args.err)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
+        const uint32_t base = base0 + ab * acc_cols;
 #pragma unroll
         for (int hh = 0; hh < kMaxEpiCols / 8; ++hh) {
           if (hh * 8 < cpg) {
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(acc_empty);
+        if (lane == 0) tc::mbar_arrive(&acc_empty[ab]);
       }
       if (!ok) break;
       const int j = u / args.ntiles;
