@@ -399,6 +399,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   std::memset(ih, 0, sizeof(int) * 16);
   for (int b = 0; b < B; ++b) {
     kdh[b] = make_kernel_dev(req[b].k);
+    if (tab) set_table_split(kdh[b], g);
     epsh[b] = req[b].o.eps;
     for (int a = 0; a < 3; ++a) {
       ih[16 + a * B + b] = req[b].o.rmax[a];

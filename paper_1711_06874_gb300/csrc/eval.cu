@@ -68,6 +68,19 @@ static inline long long table_size(int n) {
   return 3 * h * h + 1;
 }
 
+void set_table_split(KernelDev& d, const tk_grid& g) {
+  d.tsplit = 0;
+  if (d.kind != TK_MATERN) return;
+  const int n = g.n[0];
+  const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
+  const double zs = d.sqrt2nu * hstep * d.inv_ell[0];  // z = zs sqrt(s) for table entry s
+  if (!(zs > 0.0)) return;
+  const double thr = (1.5 / zs) * (1.5 / zs);         // s beyond which z > 1.5
+  const double qb = (n % 2 == 0) ? std::floor((thr - 3.0) / 8.0) + 1.0 : std::floor(thr / 4.0) + 1.0;
+  const double Q = (double)table_size(n);
+  d.tsplit = (long long)std::min(std::max(qb, 0.0), Q);
+}
+
 size_t eval_scratch_doubles(const tk_kernel& k, const tk_grid& g) {
   return table_applicable(k, g) ? (size_t)table_size(g.n[0]) : 0;
 }
@@ -250,11 +263,16 @@ __global__ void __launch_bounds__(32 * kTableWarps) k_table_b(const KernelDev* _
   T += (size_t)b * Q;
   const long long W = (long long)gridDim.x * kTableWarps;
   const long long w = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  const long long nch = (Q + 31) / 32;
+  // chunks of 32 entries on each side of tsplit (Temme's range, then the
+  // Miller recurrence's), so that no warp runs both branches
+  const long long qb = k.tsplit < 0 ? 0 : (k.tsplit > Q ? Q : k.tsplit);
+  const long long nchA = (qb + 31) / 32;
+  const long long nch = nchA + (Q - qb + 31) / 32;
   for (long long r = 0; r * W < nch; ++r) {
     const long long c = r * W + ((r & 1) ? W - 1 - w : w);
-    const long long q = c * 32 + (threadIdx.x & 31);
-    if (c >= nch || q >= Q) continue;
+    if (c >= nch) continue;
+    const long long q = ((c < nchA) ? 32 * c : qb + 32 * (c - nchA)) + (threadIdx.x & 31);
+    if (q >= ((c < nchA) ? qb : Q)) continue;
     const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
     const double v = cov_value(k, hs * hs * s);
     T[q] = (scale == 1.0) ? v : v * scale;

@@ -109,6 +109,7 @@ struct KernelDev {
   double p;
   double inv_ell[3];
   double sqrt2nu;
+  long long tsplit;  // distinct-value table: first entry past Temme's range (0: none)
   tk_nu_consts nuc;
 };
 
@@ -123,6 +124,10 @@ struct GridDev {
 };
 
 KernelDev make_kernel_dev(const tk_kernel& k);
+// For the distinct-value table of the cubic isotropic grid g: the first
+// entry whose Matern argument exceeds Temme's range (z > 1.5), where the
+// table's warps start a new chunk so that none runs both branches.
+void set_table_split(KernelDev& d, const tk_grid& g);
 GridDev make_grid_dev(const tk_grid& g);
 bool table_applicable(const tk_kernel& k, const tk_grid& g);
 
