@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kb1 = min(kb0 + args.kblocks_per_split, args.kblocks_total);
   const int nkb = kb1 - kb0;
   const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
+  // one row block holds every row (nrows <= kTM): the B rows bj kTN .. + kTN
+  // are rows of the A tile already in shared memory, so B is not loaded
+  const bool b_in_a = args.nrt == 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -249,9 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t use = k / kStages;
         if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
         unsigned char* sa = smem + st * kStageBytes;
-        tc::mbar_expect_tx(&full[st], kStageBytes);
+        tc::mbar_expect_tx(&full[st], b_in_a ? kOperandBytesA : kStageBytes);
         tc::tma_load_4d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0, inst);
-        tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0, inst);
+        if (!b_in_a)
+          tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0, inst);
         issued = k + 1;
       }
       // copies still in flight must land before the CTA exits
@@ -280,7 +284,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::fence_after_sync();
           unsigned char* sa = smem + st * kStageBytes;
-          unsigned char* sb = sa + kOperandBytesA;
+          // B: its own tile, or rows bj kTN .. of the A tile (the same 64-byte
+          // swizzle: the offset is a multiple of the 512-byte pattern)
+          unsigned char* sb = b_in_a ? sa + bj * kTN * (kKB * 2) : sa + kOperandBytesA;
+          const int sliceB = b_in_a ? kSliceBytesA : kSliceBytesB;
           // descriptors of slice 0; slice s and K step kk add (s * slice bytes + kk * 32 B) / 16
           const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
           const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
             first_mask &= ~(1u << acc);
             const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
-            const uint64_t db = db0 + (uint64_t)(t * (kSliceBytesB >> 4));
+            const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
             tc::mma_bf16(dt, da, db, idesc, accum);
             tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
           }
