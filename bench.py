@@ -394,8 +394,7 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     for _ in range(ke):
         res = ctx.tucker(prob, precision=precision, with_error=True, stream=stream)
         e = res.solve_error
-        U = [res.factor(a) for a in range(3)]
-        B = res.core()
+        *U, B = res.factors_and_core(stream=stream)
         d2h = sum(u.nbytes for u in U) + B.nbytes + 8
         res.free()
     torch.cuda.synchronize()

@@ -144,6 +144,13 @@ int tk_ranks(const tk_result* res, int32_t r[3], uint32_t flags[3]);
 int tk_factor(const tk_result* res, int mode, double* dst, int on_device, void* stream);
 /* Core B (r1 x r2 x r3, row-major) into dst. */
 int tk_core(const tk_result* res, double* dst, int on_device, void* stream);
+/* The whole decomposition of Sec. 3.2 (U_1, U_2, U_3 and B, layouts as
+ * tk_factor and tk_core) into host memory with one device-to-host copy and
+ * one synchronisation of `stream`: the result's factors and core are staged
+ * together in pinned memory owned by the context, then copied out.  Any of
+ * the four destinations may be NULL (not copied).  Thread-safe with respect
+ * to other calls on the same context. */
+int tk_result_copy(const tk_result* res, double* U1, double* U2, double* U3, double* core, void* stream);
 /* Leading eigenvalues of G_mode (descending) computed by the solve; writes
  * min(count, available) values to the host array dst and returns that number
  * through *written. */

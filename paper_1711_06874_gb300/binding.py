@@ -65,6 +65,7 @@ SIGNATURES = {
     "tk_ranks": (_c.c_int, [_vp, _c.POINTER(_i32), _c.POINTER(_u32)]),
     "tk_factor": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int, _vp]),
     "tk_core": (_c.c_int, [_vp, _vp, _c.c_int, _vp]),
+    "tk_result_copy": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "tk_eigenvalues": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int, _c.POINTER(_c.c_int)]),
     "tk_norm2": (_c.c_int, [_vp, _c.POINTER(_dbl)]),
     "tk_result_rel_error": (_c.c_int, [_vp, _c.POINTER(_dbl)]),
@@ -344,6 +345,15 @@ class Result:
         out = np.empty(tuple(r), np.float64)
         _check(self.ctx.lib.tk_core(self.ptr, out.ctypes.data, 0, None), self.ctx.ptr)
         return out
+
+    def factors_and_core(self, stream=None):
+        """(U_1, U_2, U_3, B) on the host through one staged copy (tk_result_copy)."""
+        r, _ = self.ranks
+        U = [np.empty((self.prob.n[a], r[a]), np.float64) for a in range(3)]
+        B = np.empty(tuple(r), np.float64)
+        _check(self.ctx.lib.tk_result_copy(self.ptr, U[0].ctypes.data, U[1].ctypes.data, U[2].ctypes.data,
+                                           B.ctypes.data, _stream_ptr(stream)), self.ctx.ptr)
+        return U[0], U[1], U[2], B
 
     def eigenvalues(self, mode: int, count: int = 96) -> np.ndarray:
         out = np.empty(count, np.float64)

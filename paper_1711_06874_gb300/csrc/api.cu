@@ -591,6 +591,48 @@ int tk_core(const tk_result* res, double* dst, int on_device, void* stream) {
   });
 }
 
+int tk_result_copy(const tk_result* res, double* U1, double* U2, double* U3, double* core, void* stream) {
+  if (!res || !res->ctx) return TK_EINVAL;
+  tk_ctx* ctx = res->ctx;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    double* dst[4] = {U1, U2, U3, core};
+    const double* src[4] = {res->U[0], res->U[1], res->U[2], res->core};
+    size_t cnt[4];
+    for (int a = 0; a < 3; ++a) cnt[a] = (size_t)res->n[a] * res->r[a];
+    cnt[3] = (size_t)res->r[0] * res->r[1] * res->r[2];
+    // the span of device memory holding what is asked for (one block per
+    // result: one copy), each distinct source staged once
+    const double* lo = nullptr;
+    const double* hi = nullptr;
+    for (int q = 0; q < 4; ++q) {
+      if (!dst[q] || !src[q] || cnt[q] == 0) continue;
+      if (!lo || src[q] < lo) lo = src[q];
+      if (!hi || src[q] + cnt[q] > hi) hi = src[q] + cnt[q];
+    }
+    if (!lo) return;
+    const size_t span = (size_t)(hi - lo);
+    // one staged copy only within the result's own block of device memory
+    const char* b0 = res->mem ? static_cast<const char*>(res->mem->ptr) : nullptr;
+    const bool in_block = b0 && (const char*)lo >= b0 && (const char*)hi <= b0 + res->mem->bytes;
+    if (!in_block || span > (size_t)64 << 20) {
+      // separate allocations, or a span above 512 MB: copy each part
+      for (int q = 0; q < 4; ++q)
+        if (dst[q] && src[q] && cnt[q])
+          TK_CUDA(cudaMemcpyAsync(dst[q], src[q], sizeof(double) * cnt[q], cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      return;
+    }
+    double* stage = reinterpret_cast<double*>(ctx->pin_out.reserve(sizeof(double) * span));
+    TK_CUDA(cudaMemcpyAsync(stage, lo, sizeof(double) * span, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < 4; ++q)
+      if (dst[q] && src[q] && cnt[q]) std::memcpy(dst[q], stage + (src[q] - lo), sizeof(double) * cnt[q]);
+  });
+}
+
 int tk_eigenvalues(const tk_result* res, int mode, double* dst, int count, int* written) {
   if (!res || !dst || mode < 0 || mode > 2 || count < 0) return TK_EINVAL;
   const int k = std::min<int>(count, (int)res->lam[mode].size());

@@ -622,6 +622,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       mem->ptr = nullptr;
       fail(TK_ENOMEM, "cannot allocate the results of a batch");
     }
+    mem->bytes = sizeof(double) * std::max<size_t>(tot, 1);
     rbase = static_cast<double*>(mem->ptr);
 
     // rank groups (padded rank R), each one chain of batched TTMs

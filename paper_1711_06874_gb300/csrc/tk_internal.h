@@ -93,6 +93,7 @@ struct SideStream {
 struct DeviceBlock {
   int device = 0;
   void* ptr = nullptr;
+  size_t bytes = 0;
   ~DeviceBlock();
 };
 
@@ -416,6 +417,7 @@ struct tk_ctx {
   tk::Workspace ws;   // stages before the rank decision
   tk::Workspace ws2;  // stages after it (sized from the ranks)
   tk::HostPinned pin; // staging of the engine's small transfers
+  tk::HostPinned pin_out; // staging of tk_result_copy
   tk::SideStream side; // overlapped independent sampling (with_error)
   tk::GraphCache graphs; // replayed solves
   std::string last_error;

@@ -252,3 +252,21 @@ def test_repeated_solves_replay_bitwise(ctx, wl):
                 assert _same(r.eigenvalues(a), r0.eigenvalues(a)), a
             if we:
                 assert r.solve_error == r0.solve_error
+
+
+def test_result_copy_matches_accessors(ctx, wl):
+    """tk_result_copy (one staged copy of U_1, U_2, U_3 and B) gives the bytes
+    tk_factor and tk_core give: for a folded solve, for instances of a batch
+    sharing one device block, and for an unfolded solve whose parts are
+    separate allocations."""
+    from paper_1711_06874_gb300 import binding
+
+    probs = [wl.problem(0, nu=1.2, ell=0.2, n=48, eps=1e-6, rmax=24),
+             wl.problem(0, nu=0.8, ell=(0.3, 0.4, 0.5), n=(20, 24, 28), eps=1e-6, rmax=24)]
+    results = list(ctx.batch(probs, precision=binding.TK_SLICED_BF16))
+    results.append(ctx.tucker(probs[0], precision=binding.TK_FP64, fold=False))
+    for r in results:
+        U1, U2, U3, B = r.factors_and_core()
+        for a, U in enumerate((U1, U2, U3)):
+            assert _same(U, r.factor(a)), a
+        assert _same(B, r.core())
