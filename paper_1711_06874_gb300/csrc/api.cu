@@ -828,7 +828,7 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
       if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
       if (rr[a] < 1 || rr[a] > nn[a]) fail(TK_EINVAL, "need 1 <= r <= n");
     }
-    if (precision != TK_FP64) fail(TK_EINVAL, "only TK_FP64 is available in this build");
+    if (precision != TK_FP64) fail(TK_EINVAL, "only TK_FP64 is available through this entry point");
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
     ctx->ws.reserve(carve_bytes<double>((size_t)nn[0] * nn[1] * rr[2]) +

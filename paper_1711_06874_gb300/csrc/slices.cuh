@@ -70,7 +70,7 @@ __device__ __forceinline__ __nv_bfloat16 slice_value(int d, int s) {
 }
 
 
-// The driver's cuTensorMapEncodeTiled, looked up once per process.
+// The CUDA driver API entry cuTensorMapEncodeTiled, looked up once per process.
 inline PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
