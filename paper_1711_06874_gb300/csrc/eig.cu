@@ -87,8 +87,12 @@ __device__ __forceinline__ void reflector(T alpha2, T x0, T& v0, T& beta) {
     return;
   }
   const T alpha = sqrt(alpha2);
-  v0 = x0 + (x0 >= T(0) ? alpha : -alpha);
-  beta = T(2) / (alpha2 - x0 * x0 + v0 * v0);
+  // v0 = x0 + sign(x0) alpha (the sign from the bit pattern), and
+  // 2 / (alpha^2 - x0^2 + v0^2) = 1 / (alpha (alpha + |x0|)) exactly: fewer
+  // FP64 instructions, no cancellation either way
+  const bool neg = sizeof(T) == 8 ? (__double_as_longlong((double)x0) < 0) : (__float_as_int((float)x0) < 0);
+  v0 = x0 + (neg ? -alpha : alpha);
+  beta = T(1) / (alpha * (alpha + (neg ? -x0 : x0)));
 }
 
 template <class T>
