@@ -300,6 +300,7 @@ __host__ __device__ constexpr int panel_ld(int n) {
 // reflectors written back in place, scalars to betas + b sB.
 template <int kRPL>
 __global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, int n, int m, long long sY, long long sB) {
+  TK_PDL_ENTRY();
   extern __shared__ double qf_sm[];
   __shared__ double beta[kMaxM + 1];
   __shared__ double v0s[kMaxM + 1];
@@ -334,6 +335,7 @@ template <int kRPL>
 __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, const double* __restrict__ betas,
                                                  double* __restrict__ Q, int n, int m, long long sY, long long sB,
                                                  long long sQ) {
+  TK_PDL_ENTRY();
   extern __shared__ double fq_sm[];
   __shared__ double bs[kMaxM + 1];
   Y += blockIdx.y * sY;
@@ -394,11 +396,10 @@ void qr64_launch(double* Y, double* betas, double* Q, int n, int m, int B, long 
     TK_CUDA(cudaFuncSetAttribute(k_qr_factor64<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     TK_CUDA(cudaFuncSetAttribute(k_form_q<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
-  k_qr_factor64<kRPL><<<B, 256, f_smem, s>>>(Y, betas, n, m, (long long)n * m, sB);
-  TK_LAUNCH("k_qr_factor64");
-  k_form_q<kRPL><<<dim3((m + 3) / 4, B), 128, q_smem, s>>>(Y, betas, Q, n, m, (long long)n * m, sB,
+  launch_pdl("k_qr_factor64", k_qr_factor64<kRPL>, dim3(B), dim3(256), f_smem, s, Y, betas, n, m, (long long)n * m, sB);
+  launch_pdl("k_form_q", k_form_q<kRPL>, dim3((m + 3) / 4, B), dim3(128), q_smem, s, Y, betas, Q, n, m,
+             (long long)n * m, sB,
                                                            (long long)n * m);
-  TK_LAUNCH("k_form_q");
 }
 
 bool qr64_batch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
@@ -571,6 +572,7 @@ size_t gomega32_smem(int n, int ms) {
 __global__ void __launch_bounds__(256) k_gomega32(const double* __restrict__ G, int n, int ms,
                                                   unsigned long long seed, float* __restrict__ Yg,
                                                   double* __restrict__ trace) {
+  TK_PDL_ENTRY();
   extern __shared__ float so[];
   const int ms4 = (ms + 3) & ~3;
   float* Gr = so;               // rows i0 .. i0 + 7 of G
@@ -605,6 +607,7 @@ __global__ void __launch_bounds__(256) k_gomega32(const double* __restrict__ G, 
 template <int kRPL>
 __global__ void __launch_bounds__(256) k_start32(const float* __restrict__ Yg, int n, int ms,
                                                  double* __restrict__ Q0) {
+  TK_PDL_ENTRY();
   extern __shared__ float s32[];
   __shared__ float beta[kMaxM + 1];
   __shared__ float v0s[kMaxM + 1];
@@ -655,8 +658,8 @@ void start32_launch(const double* G, int n, int ms, int B, unsigned long long se
   once_per_device((const void*)&k_gomega32, [] {
     TK_CUDA(cudaFuncSetAttribute(k_gomega32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
-  k_gomega32<<<dim3((n + kGoRows - 1) / kGoRows, B), 256, gomega32_smem(n, ms), s>>>(G, n, ms, seed, Yscr, trace);
-  TK_LAUNCH("k_gomega32");
+  launch_pdl("k_gomega32", k_gomega32, dim3((n + kGoRows - 1) / kGoRows, B), dim3(256), gomega32_smem(n, ms), s, G, n,
+             ms, seed, Yscr, trace);
   const size_t smem = start32_smem(n, ms);
   switch ((n + 31) / 32) {
 #define TK_START32_CASE(K)                                                                                   \
@@ -664,7 +667,7 @@ void start32_launch(const double* G, int n, int ms, int B, unsigned long long se
     once_per_device((const void*)&k_start32<K>, [] {                                                         \
       TK_CUDA(cudaFuncSetAttribute(k_start32<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); \
     });                                                                                                      \
-    k_start32<K><<<B, 256, smem, s>>>(Yscr, n, ms, Q0);                                                      \
+    launch_pdl("k_start32", k_start32<K>, dim3(B), dim3(256), smem, s, Yscr, n, ms, Q0);                      \
     break;
     TK_START32_CASE(1)
     TK_START32_CASE(2)
@@ -678,7 +681,6 @@ void start32_launch(const double* G, int n, int ms, int B, unsigned long long se
     default:
       fail(TK_EINVAL, "start32: n out of range");
   }
-  TK_LAUNCH("k_start32");
 }
 
 // ---------------------------------------------------------------------------
@@ -947,6 +949,7 @@ __device__ void rank_warp(const double* lam, int m, double trace, double nf, dou
 __global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V,
                                                          RankArgs rank, int mr, const double* trace,
                                                          double u_data) {
+  TK_PDL_ENTRY();
   const long long b = blockIdx.x;
   jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr, u_data);
   if (rank.out == nullptr) return;
@@ -1545,9 +1548,9 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     gemm_f64(d2, s);
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
-  k_jacobi_strided<<<B, 256, jacobi_smem(ms), s>>>(g.H, ms, g.lsub, g.VH, rank ? *rank : RankArgs{}, m, trace,
+  launch_pdl("k_jacobi_strided", k_jacobi_strided, dim3(B), dim3(256), jacobi_smem(ms), s, g.H, ms, g.lsub, g.VH,
+             rank ? *rank : RankArgs{}, m, trace,
                                                     u_data);
-  TK_LAUNCH("k_jacobi_strided");
   if (pf) pf->end(s);
   if (ms == n) {
     // first m columns of V_H (n x n) into V (n x m)

@@ -179,6 +179,7 @@ struct UnfoldDesc {
 __device__ __forceinline__ int rank_of(int r, const int* rdev) { return rdev ? min(*rdev, r) : r; }
 
 __global__ void k_unfold(const UnfoldDesc* __restrict__ descs) {
+  TK_PDL_ENTRY();
   UnfoldDesc d = descs[blockIdx.y];
   d.r = rank_of(d.r, d.rdev);
   const int c = blockIdx.x;
@@ -237,6 +238,7 @@ struct CoreDesc {
 };
 
 __global__ void k_extract_core(const CoreDesc* __restrict__ descs) {
+  TK_PDL_ENTRY();
   CoreDesc d = descs[blockIdx.y];
   d.r1 = rank_of(d.r1, d.rdev[0]);
   d.r2 = rank_of(d.r2, d.rdev[1]);
@@ -724,8 +726,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   auto launch_second = [&](bool spec) {
     TK_CUDA(cudaMemcpyAsync(amap, amaph, (size_t)((char*)(rkh + B) - (char*)amaph), cudaMemcpyHostToDevice, s));
     if (pf) pf->begin(TK_STAGE_RANK, s);
-    k_unfold<<<dim3(Rmax, (unsigned)ndesc), 128, 0, s>>>(ud);
-    TK_LAUNCH("k_unfold");
+    launch_pdl("k_unfold", k_unfold, dim3(Rmax, (unsigned)ndesc), dim3(128), 0, s, ud);
     if (pf) pf->end(s);
     if (pf) pf->begin(TK_STAGE_CORE, s);
     for (const GroupBuf& q : gb) {
@@ -767,8 +768,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       d3.fixed_order = 1;
       gemm_f64(d3, s);
     }
-    k_extract_core<<<dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), 256, 0, s>>>(cd);
-    TK_LAUNCH("k_extract_core");
+    launch_pdl("k_extract_core", k_extract_core,
+               dim3((unsigned)std::min(64, std::max(1, Rmax * Rmax * Rmax / 256 + 1)), B), dim3(256), 0, s, cd);
     if (pf) pf->end(s);
     if (with_err) {
       // X = B x_1 V_1 x_2 V_2 x_3 V_3 against the independent sampling, per

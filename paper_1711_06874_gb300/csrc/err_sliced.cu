@@ -176,6 +176,7 @@ __device__ __forceinline__ float residual(const FF x, const __nv_bfloat16* sp, i
 // thread per (b, c).
 template <int kR>
 __global__ void __launch_bounds__(kR * kR) k_err_w1(ErrSlicedArgs a) {
+  TK_PDL_ENTRY();
   __shared__ FF Vi[kR];
   const int h = a.h, R = a.R;
   const int i = blockIdx.x, pos = blockIdx.y;
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kR * kR) k_err_w1(ErrSlicedArgs a) {
 // |Fh - Xh|^2 of each instance: its partials in a fixed order (a strided
 // sum per thread, then a fixed tree), with |Fh|^2 beside it.
 __global__ void __launch_bounds__(kErrThreads) k_err_final(ErrSlicedArgs a, int nparts) {
+  TK_PDL_ENTRY();
   __shared__ double redd[kErrThreads];
   const int pos = blockIdx.x;
   const double* parts = a.partials + (size_t)pos * nparts;
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kErrThreads) k_err_final(ErrSlicedArgs a, int 
 
 template <int kR>
 __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
+  TK_PDL_ENTRY();
   __shared__ FF W1s[kR * kR];     // W1(i, b, c)
   __shared__ FF Vj[kJB * kR];     // V(j0 + jj, b)
   __shared__ FF W2s[kJB * kR];    // W2(j0 + jj, c)
@@ -339,12 +342,9 @@ static void err_launch(const ErrSlicedArgs& a, int cnt, cudaStream_t s) {
     TK_CUDA(cudaFuncSetAttribute(k_err_sliced<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kErrSmemMax));
   });
   const size_t smem = sizeof(__nv_bfloat16) * kSlices * (size_t)a.jbs * a.h;
-  k_err_w1<kR><<<dim3(a.h, cnt), kR * kR, 0, s>>>(a);
-  TK_LAUNCH("k_err_w1");
-  k_err_sliced<kR><<<dim3(a.h / a.jbs, a.h, cnt), kErrThreads, smem, s>>>(a);
-  TK_LAUNCH("k_err_sliced");
-  k_err_final<<<cnt, kErrThreads, 0, s>>>(a, a.h * (a.h / a.jbs));
-  TK_LAUNCH("k_err_final");
+  launch_pdl("k_err_w1", k_err_w1<kR>, dim3(a.h, cnt), dim3(kR * kR), 0, s, a);
+  launch_pdl("k_err_sliced", k_err_sliced<kR>, dim3(a.h / a.jbs, a.h, cnt), dim3(kErrThreads), smem, s, a);
+  launch_pdl("k_err_final", k_err_final, dim3(cnt), dim3(kErrThreads), 0, s, a, a.h * (a.h / a.jbs));
 }
 
 void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V, const double* Bcore, int h, int R,

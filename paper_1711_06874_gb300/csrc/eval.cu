@@ -257,6 +257,7 @@ constexpr int kTableWarps = 4;  // warps per block
 
 __global__ void __launch_bounds__(32 * kTableWarps) k_table_b(const KernelDev* __restrict__ kd, double hstep,
                                                              int even, long long Q, double* T, double scale) {
+  TK_PDL_ENTRY();
   const int b = blockIdx.y;
   const KernelDev& k = kd[b];
   const double hs = hstep * k.inv_ell[0];
@@ -363,6 +364,7 @@ static unsigned oct_blocks(const tk_grid& g) {
 __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict__ T, long long Q, int n, int h,
                                                       long long Kp, int* __restrict__ rowexp,
                                                       __nv_bfloat16* __restrict__ S, double* __restrict__ part) {
+  TK_PDL_ENTRY();
   // For even n every octant point stands for 8 grid points and the table
   // already holds 2 sqrt(2) C; for odd n the weight varies and is applied here.
   __shared__ unsigned long long redm[32];
@@ -444,6 +446,7 @@ __global__ void __launch_bounds__(1024) k_gather_slice(const double* __restrict_
 __global__ void __launch_bounds__(1024) k_gather_slice2(const double* __restrict__ T, long long Q, int n, int h,
                                                       long long Kp, int* __restrict__ rowexp,
                                                       __nv_bfloat16* __restrict__ S, double* __restrict__ part) {
+  TK_PDL_ENTRY();
   // For even n every octant point stands for 8 grid points and the table
   // already holds 2 sqrt(2) C; for odd n the weight varies and is applied here.
   __shared__ unsigned long long redm[32];
@@ -541,18 +544,19 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
   if (pf) pf->begin(TK_STAGE_TABLE, s);
   // even n: the table holds the octant values 2 sqrt(2) C directly
-  k_table_b<<<dim3(table_blocks(Q, B), B), 32 * kTableWarps, 0, s>>>(kd, hstep, n % 2 == 0, Q, table,
+  launch_pdl("k_table_b", k_table_b, dim3(table_blocks(Q, B), B), dim3(32 * kTableWarps), 0, s, kd, hstep, n % 2 == 0,
+             Q, table,
                                                                      n % 2 == 0 ? 2.8284271247461903 : 1.0);
-  TK_LAUNCH("k_table_b");
   if (pf) pf->end(s);
   // rows of h^2 values: wide blocks for long rows (a function of the shape
   // alone, so that each instance's sums do not depend on the batch)
   const int threads = (h >= 128) ? 1024 : 256;
   if (h % 2 == 0)
-    k_gather_slice2<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
+    launch_pdl("k_gather_slice2", k_gather_slice2, dim3(h, B), dim3(threads), 0, s, table, Q, n, h, Kp, rowexp,
+               (__nv_bfloat16*)S, part);
   else
-    k_gather_slice<<<dim3(h, B), threads, 0, s>>>(table, Q, n, h, Kp, rowexp, (__nv_bfloat16*)S, part);
-  TK_LAUNCH("k_gather_slice");
+    launch_pdl("k_gather_slice", k_gather_slice, dim3(h, B), dim3(threads), 0, s, table, Q, n, h, Kp, rowexp,
+               (__nv_bfloat16*)S, part);
   if (normF2 != nullptr) {
     k_parts_final<<<B, 256, 0, s>>>(part, h, normF2);
     TK_LAUNCH("k_parts_final");
@@ -572,8 +576,8 @@ void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, dou
     const long long Q = table_size(n);
     const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
     if (pf) pf->begin(TK_STAGE_TABLE, s);
-    k_table_b<<<dim3(table_blocks(Q, B), B), 32 * kTableWarps, 0, s>>>(kd, hstep, n % 2 == 0, Q, table, 1.0);
-    TK_LAUNCH("k_table_b");
+    launch_pdl("k_table_b", k_table_b, dim3(table_blocks(Q, B), B), dim3(32 * kTableWarps), 0, s, kd, hstep,
+               n % 2 == 0, Q, table, 1.0);
     if (pf) pf->end(s);
     k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);
     TK_LAUNCH("k_gather_oct");

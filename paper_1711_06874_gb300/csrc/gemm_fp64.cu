@@ -331,6 +331,7 @@ __device__ __forceinline__ long long batch_offsets(const GemmDesc& d, long long 
 
 template <int BM, int BN, bool kErr>
 __global__ void __launch_bounds__(NT) k_gemm_f64(GemmDesc d, ErrRef ref, double* __restrict__ partials) {
+  TK_PDL_ENTRY();
   constexpr int RM = BM / 16, RN = BN / 16;
   __shared__ double As[KS][BM + 1];
   __shared__ double Bs[KS][BN + 1];
@@ -516,6 +517,7 @@ __global__ void k_gemm_warp(GemmDesc d) {
 // cycles whatever the number of active lanes, which counts in large batches).
 template <int L>
 __global__ void k_gemm_lanes(GemmDesc d) {
+  TK_PDL_ENTRY();
   const long long per_batch = (long long)d.M * d.N;
   const long long total = per_batch * d.batch;
   const int q = threadIdx.x & (L - 1);
@@ -591,8 +593,7 @@ dim3 grid_of(const GemmDesc& d) {
 
 template <int BM, int BN, bool kErr>
 void launch(const GemmDesc& d, const ErrRef& R, double* partials, cudaStream_t s) {
-  k_gemm_f64<BM, BN, kErr><<<grid_of<BM, BN>(d), NT, 0, s>>>(d, R, partials);
-  TK_LAUNCH("k_gemm_f64");
+  launch_pdl("k_gemm_f64", k_gemm_f64<BM, BN, kErr>, dim3(grid_of<BM, BN>(d)), dim3(NT), 0, s, d, R, partials);
 }
 
 template <int I, bool kErr>
@@ -629,10 +630,9 @@ void gemm_f64(const GemmDesc& d, cudaStream_t s) {
       const long long threads = (long long)L * outs;
       const unsigned blocks = (unsigned)std::min<long long>((threads + 255) / 256, 8192);
       if (L == 4)
-        k_gemm_lanes<4><<<blocks, 256, 0, s>>>(d);
+        launch_pdl("k_gemm_lanes", k_gemm_lanes<4>, dim3(blocks), dim3(256), 0, s, d);
       else
-        k_gemm_lanes<32><<<blocks, 256, 0, s>>>(d);
-      TK_LAUNCH("k_gemm_lanes");
+        launch_pdl("k_gemm_lanes", k_gemm_lanes<32>, dim3(blocks), dim3(256), 0, s, d);
       return;
     }
     dispatch<false>(d, ErrRef{}, nullptr, s, true);
@@ -664,6 +664,7 @@ constexpr int kTtm2Threads = 256;
 
 __global__ void __launch_bounds__(kTtm2Threads) k_ttm2_sym(const double* __restrict__ V, const double* __restrict__ T1,
                                                           double* __restrict__ T2, int h, int R) {
+  TK_PDL_ENTRY();
   extern __shared__ double sm2[];
   double* Vs = sm2;          // [i][a]
   double* Ts = sm2 + h * R;  // [i][c]
@@ -728,8 +729,7 @@ void ttm2_sym_batch(const double* V, const double* T1, double* T2, int h, int R,
   once_per_device((const void*)&k_ttm2_sym, [] {
     TK_CUDA(cudaFuncSetAttribute(k_ttm2_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
   });
-  k_ttm2_sym<<<dim3(h, cnt), kTtm2Threads, ttm2_sym_smem(h, R), s>>>(V, T1, T2, h, R);
-  TK_LAUNCH("k_ttm2_sym");
+  launch_pdl("k_ttm2_sym", k_ttm2_sym, dim3(h, cnt), dim3(kTtm2Threads), ttm2_sym_smem(h, R), s, V, T1, T2, h, R);
 }
 
 // ---------------------------------------------------------------------------

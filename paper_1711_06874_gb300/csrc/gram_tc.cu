@@ -205,6 +205,7 @@ __device__ __forceinline__ int block_index(int i, int j, int nct) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, TcArgs args) {
+  TK_PDL_ENTRY();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int SG>
 __global__ void k_tc_reduce(const long long* __restrict__ P, int nsplit, int nct, int nblocks, int n, int B,
                             const int* __restrict__ rowexp, double* __restrict__ G, int nred, NormParts norm) {
+  TK_PDL_ENTRY();
   if ((int)blockIdx.x >= nred) {
     const int b = blockIdx.x - nred;
     norm_parts_block(norm.part + (size_t)b * norm.nparts, norm.nparts, norm.normF2 + b);
@@ -485,21 +487,21 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
   });
   TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.nsplit, p.kb_per_split, p.kb_total, P, err};
   if (pf) pf->begin(TK_STAGE_GRAM_TC, s);
-  k_gram_tc<<<dim3(p.nblocks, p.nsplit, B), kThreads, kSmemBytes, s>>>(mapA, mapB, a);
-  TK_LAUNCH("k_gram_tc");
+  launch_pdl("k_gram_tc", k_gram_tc, dim3(p.nblocks, p.nsplit, B), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
   if (pf) pf->end(s);
   const long long total = (long long)p.nrows * p.nrows * B;
   const int extra = norm.part != nullptr ? B : 0;
   if (p.nsplit >= 8) {
     const int nred = (int)std::min<long long>((8 * total + 255) / 256, 8192);
-    k_tc_reduce<8><<<(unsigned)(nred + extra), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G,
+    launch_pdl("k_tc_reduce", k_tc_reduce<8>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, p.nsplit, p.nct,
+               p.nblocks, p.nrows, B, rowexp, G,
                                                            nred, norm);
   } else {
     const int nred = (int)std::min<long long>((total + 255) / 256, 8192);
-    k_tc_reduce<1><<<(unsigned)(nred + extra), 256, 0, s>>>(P, p.nsplit, p.nct, p.nblocks, p.nrows, B, rowexp, G,
+    launch_pdl("k_tc_reduce", k_tc_reduce<1>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, p.nsplit, p.nct,
+               p.nblocks, p.nrows, B, rowexp, G,
                                                            nred, norm);
   }
-  TK_LAUNCH("k_tc_reduce");
 }
 
 }  // namespace

@@ -29,7 +29,35 @@ void check_cuda(cudaError_t e, const char* what);
 void count_launch();
 void count_launches(unsigned long long k);  // k kernels of a replayed graph
 #define TK_CUDA(call) ::tk::check_cuda((call), #call)
+
+// Programmatic dependent launch.  A kernel of the solve's chain is launched
+// with programmatic stream serialisation and starts with TK_PDL_ENTRY(): it
+// waits there until the previous kernel on the stream has finished and its
+// writes are visible, so its launch may be processed while the previous grid
+// drains (a no-op for a kernel launched without the attribute).  No kernel
+// lets its dependents start early: CTAs of the next kernel parked on the wait
+// cost more than the overlap gained (measured on the n = 256 solve).
+#define TK_PDL_ENTRY() asm volatile("griddepcontrol.wait;" ::: "memory")
 #define TK_LAUNCH(what) (::tk::count_launch(), ::tk::check_cuda(cudaGetLastError(), what))
+
+// Launches kernel k (which must begin with TK_PDL_ENTRY()) on stream s with
+// programmatic stream serialisation allowed; counts it like TK_LAUNCH.
+template <typename... KArgs, typename... Args>
+void launch_pdl(const char* what, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  check_cuda(cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...), what);
+  count_launch();
+}
 
 // Runs fn once for each (key, current CUDA device) pair, thread-safe; for
 // per-device settings such as a kernel's shared-memory limit.

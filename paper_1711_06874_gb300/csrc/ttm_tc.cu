@@ -68,6 +68,7 @@ struct TtmArgs {
 // BF16; padding columns c >= R are zero.
 __global__ void k_bslice(const double* __restrict__ Up, int h3, int R, int Np, int* __restrict__ colexp,
                          __nv_bfloat16* __restrict__ BS) {
+  TK_PDL_ENTRY();
   __shared__ double red[32];
   const int c = blockIdx.x, j = blockIdx.y;
   const double* U = Up + (size_t)j * h3 * R;
@@ -94,6 +95,7 @@ __global__ void k_bslice(const double* __restrict__ Up, int h3, int R, int Np, i
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, TtmArgs args) {
+  TK_PDL_ENTRY();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
@@ -320,8 +322,7 @@ void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int 
   char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   int* colexp = (int*)base;
   __nv_bfloat16* BS = (__nv_bfloat16*)(base + carve_bytes<int>((size_t)Bg * Np));
-  k_bslice<<<dim3(Np, Bg), 128, 0, s>>>(Up, h3, R, Np, colexp, BS);
-  TK_LAUNCH("k_bslice");
+  launch_pdl("k_bslice", k_bslice, dim3(Np, Bg), dim3(128), 0, s, Up, h3, R, Np, colexp, BS);
   PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encode_fn();
   if (!enc) fail(TK_ECUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t M = (cuuint64_t)h1 * h2;
@@ -349,8 +350,7 @@ void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int 
   const int tpc = (int)std::max<long long>(1, (total + sms - 1) / sms);
   const unsigned nctas = (unsigned)((total + tpc - 1) / tpc);
   TtmArgs a{(int)M, h1, h2, h3, R, Np, (h3 + kKB - 1) / kKB, ntiles, tpc, Bg, amap, sv.rowexp, colexp, T1, err};
-  k_ttm_tc<<<nctas, kThreads, kSmemBytes, s>>>(mapA, mapB, a);
-  TK_LAUNCH("k_ttm_tc");
+  launch_pdl("k_ttm_tc", k_ttm_tc, dim3(nctas), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
 }
 
 }  // namespace tk

@@ -230,7 +230,7 @@ def test_repeated_solves_replay_bitwise(ctx, wl):
         (wl.problem(0, nu=1.2, ell=0.2, n=48, eps=1e-6, rmax=24), binding.TK_SLICED_BF16, True),
         (wl.problem(0, nu=0.5, ell=0.3, n=40, eps=1e-6, rmax=24), binding.TK_FP64, False),
         (wl.problem(0, nu=0.8, ell=(0.3, 0.4, 0.5), n=(20, 24, 28), eps=1e-6, rmax=24), binding.TK_FP64, False),
-        (wl.problem(0, nu=0.6, ell=0.15, n=40, eps=1e-8, rmax=20), binding.TK_SLICED_BF16, True),  # ranks > 12
+        (wl.problem(0, nu=0.6, ell=0.15, n=40, eps=1e-8, rmax=20), binding.TK_FP64, False),  # ranks > 12
     ]
     for i, (p, prec, we) in enumerate(cases):
         big = wl.problem(0, nu=1.2, ell=0.2, n=160 + 32 * i, eps=1e-6, rmax=24)  # larger each case
