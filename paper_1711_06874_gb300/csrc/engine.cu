@@ -146,6 +146,7 @@ namespace {
 constexpr int kPhaseA = 12;  // eigenpairs of the first pass (enough for ranks <= 12)
 constexpr int kPhaseB = 40;  // second pass, for the instances that need more
 constexpr int kSpecMaxBatch = 4;  // batches up to this size run the second phase speculatively
+constexpr size_t kMaxGraphs = 64;   // captured plans kept per cache
 
 int roundup(int x, int q) { return (x + q - 1) / q * q; }
 
@@ -852,6 +853,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
                                       (double)key.kind, (double)key.precision, (double)nmodes, (double)key.tab,
                                       (double)m[0], (double)m[1], (double)m[2], (double)key.err, (double)B,
                                       (double)err_ff};
+      // a bounded cache: a server meeting many plans starts afresh
+      if (graphs->graphs.size() >= kMaxGraphs && graphs->graphs.find(gk) == graphs->graphs.end())
+        graphs->release();
       sg = &graphs->graphs[gk];
       const void* bases[3] = {pre.base, post.base, pin.p};
       if (sg->exec && (bases[0] != sg->bases[0] || bases[1] != sg->bases[1] || bases[2] != sg->bases[2])) {
