@@ -47,8 +47,11 @@ typedef enum {
  *              r_A^2 = sum_a x_a^2 / ell_a^2 (A = diag(1/ell_a^2)).
  *  TK_SLATER_P Sec. 3.7, Eq. (exp_p): C = sigma2 exp(-r_A^p).
  *  TK_GAUSSIAN the nu -> infinity limit of Sec. 2.2: C = sigma2 exp(-r_A^2);
- *              a rank-one tensor (Sec. 4.4). */
-typedef enum { TK_MATERN = 0, TK_SLATER_P = 1, TK_GAUSSIAN = 2 } tk_kind;
+ *              a rank-one tensor (Sec. 4.4).
+ *  TK_MATERN_SD the 3D spectral density of the Matern covariance, Sec. 3.7,
+ *              Eq. (SD_matern) with d = 3: f = sigma2 / (alpha^2 + r_A^2)^(nu + 3/2),
+ *              alpha > 0 given in the field p (the paper's constant C is sigma2). */
+typedef enum { TK_MATERN = 0, TK_SLATER_P = 1, TK_GAUSSIAN = 2, TK_MATERN_SD = 3 } tk_kind;
 
 /* Grid kinds.  Coordinates of axis a, 0-based index i:
  *  TK_CELL_CENTRED x_i = -b_a + (i + 1/2) 2 b_a / n_a
@@ -73,7 +76,7 @@ typedef struct {
   double nu;        /* Matern smoothness, > 0 */
   double ell[3];    /* per-axis length scale, > 0 */
   double sigma2;    /* variance, > 0 */
-  double p;         /* p-Slater exponent, > 0 */
+  double p;         /* p-Slater exponent, or alpha of TK_MATERN_SD; > 0 */
 } tk_kernel;
 
 typedef struct {

@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MATERN, SLATER_P, GAUSSIAN = 0, 1, 2
+MATERN, SLATER_P, GAUSSIAN, MATERN_SD = 0, 1, 2, 3
 CELL, VERTEX = 0, 1
 RANK_CAPPED, EPS_UNREACHABLE = 1, 2
 

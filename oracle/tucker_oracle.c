@@ -128,6 +128,9 @@ double or_kernel_value(const or_kernel* k, const double x[3]) {
       return k->sigma2 * exp(-pow(ra, k->p));
     case OR_GAUSSIAN:
       return k->sigma2 * exp(-ra2);
+    case OR_MATERN_SD:
+      /* Eq. (SD_matern), d = 3 */
+      return k->sigma2 / pow(k->p * k->p + ra2, k->nu + 1.5);
     default:
       return NAN;
   }

@@ -19,10 +19,12 @@
 extern "C" {
 #endif
 
-/* Covariance kinds.  OR_MATERN: Sec. 2.2, Eq. (Matern).  OR_SLATER_P: the
+/* Covariance kinds.  OR_MATERN_SD: the 3D spectral density of the Matern
+ * covariance, Sec. 3.7, Eq. (SD_matern) with d = 3, C = sigma2, alpha = p:
+ * sigma2 / (alpha^2 + r_A^2)^(nu + 3/2).  OR_MATERN: Sec. 2.2, Eq. (Matern).  OR_SLATER_P: the
  * p-Slater function of Sec. 3.7, Eq. (exp_p).  OR_GAUSSIAN: the nu -> infinity
  * limit named in Sec. 2.2, written exp(-|x|^2/ell^2) (rank one, Sec. 4.4). */
-enum { OR_MATERN = 0, OR_SLATER_P = 1, OR_GAUSSIAN = 2 };
+enum { OR_MATERN = 0, OR_SLATER_P = 1, OR_GAUSSIAN = 2, OR_MATERN_SD = 3 };
 /* Grid kinds.  OR_CELL: x_i = -b + (i + 1/2) 2b/n.  OR_VERTEX: Eq. (grid_points),
  * x_i = -b + (i - 1) h, h = 2b/(n - 1), with 1-based i. */
 enum { OR_CELL = 0, OR_VERTEX = 1 };

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtucker_matern.so")
 
 TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_ETIMEOUT, TK_EBUSY, TK_ENOTFOUND = range(7)
-TK_MATERN, TK_SLATER_P, TK_GAUSSIAN = 0, 1, 2
+TK_MATERN, TK_SLATER_P, TK_GAUSSIAN, TK_MATERN_SD = 0, 1, 2, 3
 TK_CELL_CENTRED, TK_VERTEX = 0, 1
 TK_FP64, TK_SLICED_BF16 = 0, 1
 SLICED_AVAILABLE = True  # tensor-core Gram from exact BF16 slices is built

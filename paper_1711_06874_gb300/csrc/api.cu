@@ -155,13 +155,16 @@ int guard(tk_ctx* ctx, Fn&& fn) {
 
 void check_kernel(const tk_kernel* k) {
   if (!k) fail(TK_EINVAL, "kernel is NULL");
-  if (k->kind < TK_MATERN || k->kind > TK_GAUSSIAN) fail(TK_EINVAL, "unknown kernel kind");
+  if (k->kind < TK_MATERN || k->kind > TK_MATERN_SD) fail(TK_EINVAL, "unknown kernel kind");
   for (int a = 0; a < 3; ++a)
     if (!(k->ell[a] > 0.0) || !std::isfinite(k->ell[a])) fail(TK_EINVAL, "ell must be > 0");
   if (!(k->sigma2 > 0.0) || !std::isfinite(k->sigma2)) fail(TK_EINVAL, "sigma2 must be > 0");
   if (k->kind == TK_MATERN && (!(k->nu > 0.0) || !(k->nu <= 50.0)))
     fail(TK_EINVAL, "nu must be in (0, 50]");
   if (k->kind == TK_SLATER_P && (!(k->p > 0.0) || !(k->p <= 8.0))) fail(TK_EINVAL, "p must be in (0, 8]");
+  if (k->kind == TK_MATERN_SD && (!(k->nu > 0.0) || !(k->nu <= 50.0)))
+    fail(TK_EINVAL, "nu must be in (0, 50]");
+  if (k->kind == TK_MATERN_SD && (!(k->p > 0.0) || !std::isfinite(k->p))) fail(TK_EINVAL, "alpha (p) must be > 0");
 }
 
 void check_grid(const tk_grid* g) {

@@ -28,7 +28,7 @@ KernelDev make_kernel_dev(const tk_kernel& k) {
   d.p = k.p;
   for (int a = 0; a < 3; ++a) d.inv_ell[a] = 1.0 / k.ell[a];
   d.sqrt2nu = (k.kind == TK_MATERN) ? std::sqrt(2.0 * k.nu) : 0.0;
-  d.nuc = make_nu_consts(k.kind == TK_MATERN ? k.nu : 0.5);
+  d.nuc = make_nu_consts(k.kind == TK_MATERN || k.kind == TK_MATERN_SD ? k.nu : 0.5);
   return d;
 }
 
@@ -59,6 +59,8 @@ __device__ __forceinline__ double cov_value(const KernelDev& k, double ra2) {
   const double ra = sqrt(ra2);
   if (k.kind == TK_MATERN) return tk_matern_z(k.nuc, k.sigma2, k.sqrt2nu * ra);
   if (k.kind == TK_SLATER_P) return (ra2 == 0.0) ? k.sigma2 : k.sigma2 * exp(-pow(ra, k.p));
+  // Eq. (SD_matern), d = 3: sigma2 (alpha^2 + r_A^2)^-(nu + 3/2)
+  if (k.kind == TK_MATERN_SD) return k.sigma2 * exp(-(k.nuc.nu + 1.5) * log(fma(k.p, k.p, ra2)));
   return k.sigma2 * exp(-ra2);
 }
 

@@ -12,7 +12,7 @@ import dataclasses
 
 import numpy as np
 
-MATERN, SLATER_P, GAUSSIAN = 0, 1, 2
+MATERN, SLATER_P, GAUSSIAN, MATERN_SD = 0, 1, 2, 3
 CELL, VERTEX = 0, 1
 
 

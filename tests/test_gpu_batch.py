@@ -274,3 +274,34 @@ def test_result_copy_matches_accessors(ctx, wl):
         for a, U in enumerate((U1, U2, U3)):
             assert _same(U, r.factor(a)), a
         assert _same(B, r.core())
+
+
+@pytest.mark.parametrize("precision_name", ["TK_FP64", "TK_SLICED_BF16"])
+def test_spectral_density_matches_oracle(ctx, orc, wl, precision_name):
+    """The spectral density of Eq. (SD_matern) through the whole solve (the
+    paper's alpha = 0.1 and alpha = 100 with nu = 0.4, and a middle case):
+    ranks as the oracle's unless at a threshold, |F|^2, the core norm, the
+    reconstruction and E against the oracle's."""
+    from paper_1711_06874_gb300 import binding
+
+    precision = getattr(binding, precision_name)
+    u = U64 if precision == binding.TK_FP64 else U_SLICED
+    probs = [wl.problem(wl.MATERN_SD, nu=0.4, p=alpha, n=n, eps=1e-6, rmax=24)
+             for alpha, n in ((0.1, 36), (1.0, 32), (100.0, 40))]
+    res = ctx.batch(probs, precision=precision, with_error=True)
+    for p, r in zip(probs, res):
+        ref = orc.hosvd(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc), p.eps, rmax=list(p.rmax))
+        ranks, _ = r.ranks
+        if ranks != ref["ranks"]:
+            assert any(near_threshold(ref["lam"][a], ref["normF2"], p.eps, ref["ranks"][a]) for a in range(3))
+            continue
+        nF = math.sqrt(ref["normF2"])
+        assert abs(r.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
+        assert abs(np.linalg.norm(r.core()) - math.sqrt(ref["core_norm2"])) <= max(1e-12, 100 * u) * nF
+        U = [r.factor(a) for a in range(3)]
+        X = orc.reconstruct(r.core(), U, p.n)
+        Xo = orc.reconstruct(ref["core"], ref["U"], p.n)
+        assert np.linalg.norm(X - Xo) <= max(1e-12, 100 * u / p.eps) * nF
+        F = orc.tensor(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc))
+        e_or = orc.rel_error(F, X)
+        assert abs(r.solve_error - e_or) <= 1e-5 * e_or + 1e-15

@@ -59,6 +59,8 @@ EVAL_CASES = [
     dict(kind=0, nu=1.7, ell=(0.2, 0.35, 0.5), n=(20, 24, 28)),  # general per-point path
     dict(kind=1, p=0.2, ell=1.0, n=24, b=5.0, grid=1),        # p-Slater
     dict(kind=2, ell=0.4, n=(17, 9, 30), b=(1.0, 0.5, 2.0)),  # Gaussian, non-cubic
+    dict(kind=3, nu=0.4, p=0.1, n=40),                        # spectral density, table path
+    dict(kind=3, nu=1.3, p=2.0, ell=(0.5, 0.8, 1.0), n=(20, 24, 28)),  # spectral density, general path
 ]
 
 

@@ -423,3 +423,43 @@ def test_planted_wrong_sign_in_bessel_is_caught(orc):
     nu, z = 1.2, 0.7
     kp, km, k0 = (orc.bessel_k(nu + 1, z), orc.bessel_k(nu - 1, z), orc.bessel_k(nu, z))
     assert abs((kp + km) - 2 * nu / z * k0) > 1e-3 * kp
+
+
+# ---------------------------------------------------------------------------
+# Spectral density of the Matern covariance (Sec. 3.7, Eq. (SD_matern), d = 3)
+# ---------------------------------------------------------------------------
+def test_spectral_density_closed_values(orc):
+    """nu = 1/2 makes the exponent nu + 3/2 = 2: on the 3-point vertex grid of
+    [-1, 1] with alpha = 1 the values are 1/(1 + r^2)^2 at r^2 = 0, 1, 2, 3."""
+    k = orc.make_kernel(orc.MATERN_SD, nu=0.5, ell=1.0, sigma2=2.0, p=1.0)
+    F = orc.tensor(k, orc.make_grid([3, 3, 3], b=[1.0, 1.0, 1.0], kind=1))
+    assert F[1, 1, 1] == 2.0
+    assert F[2, 1, 1] == 0.5 and F[1, 0, 1] == 0.5
+    assert abs(F[2, 2, 1] - 2.0 / 9.0) <= 1e-16
+    assert F[0, 2, 0] == 2.0 / 16.0
+
+
+def test_spectral_density_scaling_law(orc):
+    """f_{alpha,nu}(x) = alpha^-(2 nu + 3) f_{1,nu}(x / alpha): the tensor on the
+    box b with alpha equals the alpha = 1 tensor on the box b / alpha times
+    alpha^-(2 nu + 3), for several nu and alpha (pins the exponent and where
+    alpha enters)."""
+    for nu, alpha in ((0.4, 0.1), (1.3, 2.0), (2.5, 100.0)):
+        b = 1.0
+        Fa = orc.tensor(orc.make_kernel(orc.MATERN_SD, nu=nu, ell=1.0, p=alpha),
+                        orc.make_grid([9, 10, 11], b=[b, b, b], kind=0))
+        F1 = orc.tensor(orc.make_kernel(orc.MATERN_SD, nu=nu, ell=1.0, p=1.0),
+                        orc.make_grid([9, 10, 11], b=[b / alpha] * 3, kind=0))
+        np.testing.assert_allclose(Fa, F1 * alpha ** (-(2 * nu + 3)), rtol=1e-13, atol=0)
+
+
+def test_spectral_density_anisotropic_scaling(orc):
+    """The anisotropic distance r_A^2 = sum x_a^2 / ell_a^2 of Sec. 2.2: scaling
+    axis a of the box by ell_a leaves the tensor of ell = (ell_1, ell_2, ell_3)
+    equal to the isotropic ell = 1 tensor."""
+    ell = (0.5, 2.0, 3.0)
+    Fa = orc.tensor(orc.make_kernel(orc.MATERN_SD, nu=0.7, ell=list(ell), p=0.3),
+                    orc.make_grid([7, 8, 9], b=list(ell), kind=0))
+    F1 = orc.tensor(orc.make_kernel(orc.MATERN_SD, nu=0.7, ell=1.0, p=0.3),
+                    orc.make_grid([7, 8, 9], b=[1.0, 1.0, 1.0], kind=0))
+    np.testing.assert_allclose(Fa, F1, rtol=1e-14, atol=0)
