@@ -67,8 +67,11 @@ typedef enum { TK_FP64 = 0, TK_SLICED_BF16 = 1 } tk_precision;
 
 /* Result flags, per mode. */
 enum {
-  TK_RANK_CAPPED = 1u,                /* the eps rule wanted more than rmax */
-  TK_EPS_UNREACHABLE_AT_PRECISION = 2u /* eps^2 |F|^2 / 3 is below 10 u_eff n |F|^2 */
+  TK_RANK_CAPPED = 1u,                 /* the eps rule wanted more than rmax */
+  TK_EPS_UNREACHABLE_AT_PRECISION = 2u, /* eps^2 |F|^2 / 3 is below 10 u_eff n |F|^2 */
+  TK_SOLVED_AGAIN_IN_FP64 = 4u         /* a TK_SLICED_BF16 solve with with_error = 1 whose E came
+                                          out above eps (ranks from the eps rule, none capped) was
+                                          solved again with the FP64 Gram: this is that result */
 };
 
 typedef struct {

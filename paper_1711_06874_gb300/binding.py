@@ -24,7 +24,7 @@ TK_MATERN, TK_SLATER_P, TK_GAUSSIAN, TK_MATERN_SD = 0, 1, 2, 3
 TK_CELL_CENTRED, TK_VERTEX = 0, 1
 TK_FP64, TK_SLICED_BF16 = 0, 1
 SLICED_AVAILABLE = True  # tensor-core Gram from exact BF16 slices is built
-TK_RANK_CAPPED, TK_EPS_UNREACHABLE_AT_PRECISION = 1, 2
+TK_RANK_CAPPED, TK_EPS_UNREACHABLE_AT_PRECISION, TK_SOLVED_AGAIN_IN_FP64 = 1, 2, 4
 
 # every function the header declares, with (restype, argtypes)
 _c = ctypes

@@ -305,3 +305,32 @@ def test_spectral_density_matches_oracle(ctx, orc, wl, precision_name):
         F = orc.tensor(wl.oracle_kernel(p, orc), wl.oracle_grid(p, orc))
         e_or = orc.rel_error(F, X)
         assert abs(r.solve_error - e_or) <= 1e-5 * e_or + 1e-15
+
+
+def test_sliced_error_above_eps_is_solved_again_in_fp64(ctx, wl):
+    """The spectral density at n = 256 (nu = 0.4, alpha = 0.1) is a case where
+    the sliced Gram's E lands above eps = 1e-6 although the rank rule's sums
+    do not: with with_error the instance comes back solved again with the FP64
+    Gram (flag TK_SOLVED_AGAIN_IN_FP64), with E <= eps and the bytes of a plain
+    FP64 solve.  A Matern instance in the same batch keeps its sliced result."""
+    from paper_1711_06874_gb300 import binding
+
+    sd = wl.problem(wl.MATERN_SD, nu=0.4, p=0.1, n=256, eps=1e-6, rmax=24)
+    mat = wl.problem(0, nu=1.2, ell=0.2, n=64, eps=1e-6, rmax=24)
+    res = ctx.batch([sd, mat], precision=binding.TK_SLICED_BF16, with_error=True)
+    r_sd, r_mat = res[0], res[1]
+    _, f_sd = r_sd.ranks
+    _, f_mat = r_mat.ranks
+    assert all(f & binding.TK_SOLVED_AGAIN_IN_FP64 for f in f_sd)
+    assert not any(f & binding.TK_SOLVED_AGAIN_IN_FP64 for f in f_mat)
+    assert r_sd.solve_error <= sd.eps
+    assert r_mat.solve_error <= mat.eps
+    ref = ctx.tucker(sd, precision=binding.TK_FP64, with_error=True)
+    assert r_sd.ranks[0] == ref.ranks[0]
+    assert r_sd.solve_error == ref.solve_error
+    for a in range(3):
+        assert _same(r_sd.factor(a), ref.factor(a)), a
+    assert _same(r_sd.core(), ref.core())
+    one = ctx.tucker(sd, precision=binding.TK_SLICED_BF16, with_error=True)
+    assert all(f & binding.TK_SOLVED_AGAIN_IN_FP64 for f in one.ranks[1])
+    assert one.solve_error <= sd.eps
