@@ -88,6 +88,8 @@ def _load():
             "or_tucker_point": (d, [p, p, p, i, p, i, p, i, p]),
             "or_rel_error": (d, [p, p, ctypes.c_longlong]),
             "or_hosvd": (i, [kp, gp, d, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "or_ttm": (None, [p, p, i, p, i, i, p]),
+            "or_hooi": (i, [p, p, p, p, p, p, i, p, p]),
             "or_num_threads": (i, []),
         }
         for name, (res, args) in sig.items():
@@ -239,6 +241,34 @@ def rel_error(F: np.ndarray, X: np.ndarray) -> float:
     F = _f64(F)
     X = _f64(X)
     return _load().or_rel_error(_ptr(F), _ptr(X), F.size)
+
+
+def ttm(X: np.ndarray, mode: int, U: np.ndarray) -> np.ndarray:
+    """Y = X x_mode U^T for U of shape (X.shape[mode], r)."""
+    X = _f64(X)
+    U = _f64(U)
+    d = _i32(X.shape)
+    shape = list(X.shape)
+    shape[mode] = U.shape[1]
+    Y = np.empty(shape, np.float64)
+    _load().or_ttm(_ptr(X), _ptr(d), int(mode), _ptr(U), U.shape[1], U.shape[1], _ptr(Y))
+    return Y
+
+
+def hooi(F: np.ndarray, U, sweeps: int):
+    """Tucker-ALS (Sec. 3.2) from the starting factors U (n_k x r_k): returns
+    (factors, core, core_norm2 after each mode update)."""
+    F = _f64(F)
+    n = _i32(F.shape)
+    U = [_f64(u).copy() for u in U]
+    r = _i32([u.shape[1] for u in U])
+    B = np.empty(tuple(int(v) for v in r), np.float64)
+    hist = np.empty(max(3 * sweeps, 1), np.float64)
+    rc = _load().or_hooi(_ptr(F), _ptr(n), _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), _ptr(r), int(sweeps), _ptr(B),
+                         _ptr(hist))
+    if rc != 0:
+        raise MemoryError("oracle hooi failed")
+    return U, B, hist[: 3 * sweeps]
 
 
 def hosvd(kernel: Kernel, grid: Grid, eps: float, rmax=None, rfix=None) -> dict:

@@ -533,3 +533,81 @@ int or_hosvd(const or_kernel* k, const or_grid* g, double eps, const int rmax[3]
   free(F);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tucker-ALS (Sec. 3.2, second part of the algorithm).                      */
+/* Parity: pinned by the d = 2 reduction (from a random start the sweeps     */
+/* reach the Eckart-Young optimum of the matrix SVD), exact recovery of a    */
+/* tensor of exact multilinear rank after one sweep from a random start,     */
+/* the monotone core norm, |F|^2 = |B|^2 + |F - X|^2, and the HOSVD factors  */
+/* of a rank-one tensor as a fixed point.                                    */
+/* ------------------------------------------------------------------------ */
+void or_ttm(const double* X, const int d[3], int mode, const double* U, int ld, int r, double* Y) {
+  int e[3] = {d[0], d[1], d[2]};
+  e[mode] = r;
+  long long outer = 1, inner = 1;
+  for (int a = 0; a < mode; ++a) outer *= d[a];
+  for (int a = mode + 1; a < 3; ++a) inner *= d[a];
+  const int m = d[mode];
+  (void)e;
+  /* Y[o][c][t] = sum_i X[o][i][t] U[i][c] */
+#pragma omp parallel for schedule(static)
+  for (long long o = 0; o < outer; ++o)
+    for (int c = 0; c < r; ++c)
+      for (long long t = 0; t < inner; ++t) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += X[(o * m + i) * inner + t] * U[(long long)i * ld + c];
+        Y[(o * r + c) * inner + t] = s;
+      }
+}
+
+int or_hooi(const double* F, const int n[3], double* U1, double* U2, double* U3, const int r[3], int sweeps,
+            double* B, double* core_norm2) {
+  double* U[3] = {U1, U2, U3};
+  int nmax = n[0];
+  for (int a = 1; a < 3; ++a)
+    if (n[a] > nmax) nmax = n[a];
+  long long big = 0;
+  for (int k = 0; k < 3; ++k) {
+    /* the largest of the two intermediates of mode k's projections */
+    int d[3] = {n[0], n[1], n[2]};
+    int first = (k == 2) ? 0 : 2;
+    d[first] = r[first];
+    long long sz = (long long)d[0] * d[1] * d[2];
+    if (sz > big) big = sz;
+  }
+  double* T = (double*)malloc(sizeof(double) * (size_t)big);
+  double* Y = (double*)malloc(sizeof(double) * (size_t)big);
+  double* sig = (double*)malloc(sizeof(double) * (size_t)nmax);
+  double* W = (double*)malloc(sizeof(double) * (size_t)nmax * nmax);
+  if (!T || !Y || !sig || !W) {
+    free(T);
+    free(Y);
+    free(sig);
+    free(W);
+    return -1;
+  }
+  for (int sweep = 0; sweep < sweeps; ++sweep)
+    for (int k = 0; k < 3; ++k) {
+      /* single-hole tensor: every mode but k mapped into its subspace */
+      const int m1 = (k == 2) ? 0 : 2, m2 = (k == 1) ? 0 : 1;
+      int d[3] = {n[0], n[1], n[2]};
+      or_ttm(F, d, m1, U[m1], r[m1], r[m1], T);
+      d[m1] = r[m1];
+      or_ttm(T, d, m2, U[m2], r[m2], r[m2], Y);
+      d[m2] = r[m2];
+      /* U_k: leading left singular vectors of the mode-k unfolding of Y */
+      or_unfolding_svd(Y, d, k, sig, W);
+      nacc c2 = {0.0, 0.0};
+      for (int a = 0; a < r[k]; ++a) nacc_add(&c2, sig[a] * sig[a]);
+      if (core_norm2) core_norm2[sweep * 3 + k] = nacc_val(&c2);
+      for (int i = 0; i < n[k]; ++i)
+        for (int a = 0; a < r[k]; ++a) U[k][(long long)i * r[k] + a] = W[(long long)i * n[k] + a];
+    }
+  or_core(F, n, U1, r[0], U2, r[1], U3, r[2], r, B);
+  free(T);
+  free(Y);
+  free(sig);
+  free(W);
+  return 0;
+}

@@ -95,6 +95,21 @@ int or_hosvd(const or_kernel* k, const or_grid* g, double eps, const int rmax[3]
              int ranks[3], int flags[3], double* U1, double* U2, double* U3, double* lam1,
              double* lam2, double* lam3, double* B, double* out);
 
+/* Mode-m product Y = X x_m U^T (Sec. 3.1): X has dims d[3], U is d[m] x ld
+ * row-major with its first r columns used; Y has dims d with d[m] replaced by r. */
+void or_ttm(const double* X, const int d[3], int mode, const double* U, int ld, int r, double* Y);
+
+/* Tucker-ALS (Sec. 3.2): `sweeps` sweeps over the modes 1, 2, 3 in order.  For
+ * mode k the single-hole tensor Y_k = F x_{m != k} U_m^T is formed and U_k is
+ * replaced by the r_k leading left singular vectors of its mode-k unfolding
+ * (one-sided Jacobi, canonical signs).  U_k: n_k x r_k row-major, in and out.
+ * B (r1 r2 r3) = F x_1 U1^T x_2 U2^T x_3 U3^T with the final factors.
+ * core_norm2 (3 * sweeps, may be NULL): the sum of the r_k leading squared
+ * singular values after each update, which is |F x_1 U1^T x_2 U2^T x_3 U3^T|^2
+ * with the factors of that moment.  Returns 0, or -1 if memory ran out. */
+int or_hooi(const double* F, const int n[3], double* U1, double* U2, double* U3, const int r[3], int sweeps,
+            double* B, double* core_norm2);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus

@@ -463,3 +463,118 @@ def test_spectral_density_anisotropic_scaling(orc):
     F1 = orc.tensor(orc.make_kernel(orc.MATERN_SD, nu=0.7, ell=1.0, p=0.3),
                     orc.make_grid([7, 8, 9], b=[1.0, 1.0, 1.0], kind=0))
     np.testing.assert_allclose(Fa, F1, rtol=1e-14, atol=0)
+
+
+# --------------------------------------------------------------------------
+# Tucker-ALS (Sec. 3.2, the alternating sweeps after the HOSVD)
+# --------------------------------------------------------------------------
+def _orthonormal(rng, n, r):
+    q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return q
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_ttm_matches_einsum(orc, mode):
+    rng = np.random.default_rng(40 + mode)
+    X = rng.standard_normal((5, 6, 7))
+    U = rng.standard_normal((X.shape[mode], 3))
+    spec = {0: "ijk,ia->ajk", 1: "ijk,ja->iak", 2: "ijk,ka->ija"}[mode]
+    np.testing.assert_allclose(orc.ttm(X, mode, U), np.einsum(spec, X, U), rtol=0, atol=1e-13)
+
+
+def test_hooi_matrix_case_reaches_eckart_young(orc):
+    """With n3 = 1 the tensor is a matrix A and the sweeps are subspace
+    iteration on A: from a random start they reach the Eckart-Young optimum,
+    |B|^2 = sum of the r leading sigma_i^2 of A, and U1, U2 span A's leading
+    singular subspaces."""
+    rng = np.random.default_rng(7)
+    n1, n2, r = 9, 11, 3
+    s = 2.0 ** -np.arange(n1)
+    A = _orthonormal(rng, n1, n1) @ np.diag(s) @ _orthonormal(rng, n2, n1).T
+    F = A.reshape(n1, n2, 1)
+    U0 = [_orthonormal(rng, n1, r), _orthonormal(rng, n2, r), np.ones((1, 1))]
+    U, B, hist = orc.hooi(F, U0, sweeps=40)
+    assert abs(hist[-1] - np.sum(s[:r] ** 2)) <= 1e-13 * np.sum(s ** 2)
+    assert abs(orc.norm2(B) - np.sum(s[:r] ** 2)) <= 1e-13 * np.sum(s ** 2)
+    Us, _, Vt = np.linalg.svd(A)
+    np.testing.assert_allclose(U[0] @ U[0].T, Us[:, :r] @ Us[:, :r].T, atol=1e-10)
+    np.testing.assert_allclose(U[1] @ U[1].T, Vt[:r].T @ Vt[:r], atol=1e-10)
+
+
+def test_hooi_recovers_exact_multilinear_rank(orc):
+    """F = G x_1 A x_2 B x_3 C has multilinear rank (3, 4, 2): one sweep from a
+    random start already spans each range (the single-hole unfoldings have the
+    column space of the factor), so X = F to rounding."""
+    rng = np.random.default_rng(11)
+    n, r = (7, 8, 9), (3, 4, 2)
+    G = rng.standard_normal(r)
+    Q = [_orthonormal(rng, n[a], r[a]) for a in range(3)]
+    F = np.einsum("abc,ia,jb,kc->ijk", G, *Q)
+    U0 = [_orthonormal(rng, n[a], r[a]) for a in range(3)]
+    U, B, hist = orc.hooi(F, U0, sweeps=1)
+    X = orc.reconstruct(B, U, n)
+    assert orc.rel_error(F, X) <= 1e-13
+    assert abs(hist[-1] - orc.norm2(F)) <= 1e-13 * orc.norm2(F)
+    for a in range(3):
+        np.testing.assert_allclose(U[a] @ U[a].T, Q[a] @ Q[a].T, atol=1e-12)
+
+
+def test_hooi_is_monotone_and_orthogonal_on_covariance(orc):
+    """From the HOSVD factors of an anisotropic Matern tensor: each update
+    maximises |B| over one factor, so the history never decreases and starts
+    at or above the HOSVD core norm; X is an orthogonal projection of F, so
+    |F|^2 = |B|^2 + |F - X|^2; E does not exceed the HOSVD's."""
+    k = orc.make_kernel(orc.MATERN, nu=0.7, ell=[0.3, 0.5, 0.8])
+    g = orc.make_grid([14, 16, 18], b=[1.0, 1.0, 1.0])
+    F = orc.tensor(k, g)
+    ref = orc.hosvd(k, g, 1e-3, rfix=[4, 3, 2])
+    U, B, hist = orc.hooi(F, ref["U"], sweeps=4)
+    nF2 = ref["normF2"]
+    assert hist[0] >= ref["core_norm2"] - 1e-14 * nF2
+    assert np.all(np.diff(hist) >= -1e-14 * nF2)
+    assert hist[-1] > ref["core_norm2"]
+    X = orc.reconstruct(B, U, g.n)
+    d2 = orc.norm2(F - X)
+    assert abs(nF2 - orc.norm2(B) - d2) <= 1e-12 * nF2
+    assert orc.rel_error(F, X) <= ref["rel_error"]
+    for a in range(3):
+        np.testing.assert_allclose(U[a].T @ U[a], np.eye(U[a].shape[1]), atol=1e-13)
+
+
+def test_hooi_keeps_the_rank_one_gaussian(orc):
+    """The Gaussian exp(-r^2) is a product of three vectors: its HOSVD factors
+    at rank (1, 1, 1) are already optimal, so the sweeps leave them and the
+    core unchanged and X = F."""
+    k = orc.make_kernel(orc.GAUSSIAN, ell=[0.4, 0.6, 0.9])
+    g = orc.make_grid([10, 11, 12], b=[1.0, 1.0, 1.0])
+    F = orc.tensor(k, g)
+    ref = orc.hosvd(k, g, 1e-3, rfix=[1, 1, 1])
+    U, B, _ = orc.hooi(F, ref["U"], sweeps=2)
+    for a in range(3):
+        np.testing.assert_allclose(U[a], ref["U"][a], rtol=0, atol=1e-14)
+    assert abs(B.item() - ref["core"].item()) <= 1e-14 * abs(ref["core"].item())
+    assert orc.rel_error(F, orc.reconstruct(B, U, g.n)) <= 1e-14
+
+
+def test_planted_als_ordering_mistake_is_caught(orc):
+    """A sweep that keeps the trailing instead of the leading singular vectors
+    (a sort-order mistake) fails the exact-rank recovery pin, which the same
+    sweep with the leading vectors passes."""
+    rng = np.random.default_rng(11)
+    n, r = (7, 8, 9), (3, 4, 2)
+    G = rng.standard_normal(r)
+    Q = [_orthonormal(rng, n[a], r[a]) for a in range(3)]
+    F = np.einsum("abc,ia,jb,kc->ijk", G, *Q)
+    U0 = [_orthonormal(rng, n[a], r[a]) for a in range(3)]
+
+    def sweep(pick):
+        U = [u.copy() for u in U0]
+        for k in range(3):
+            m1, m2 = [a for a in range(3) if a != k]
+            Y = orc.ttm(orc.ttm(F, m1, U[m1]), m2, U[m2])
+            _, W = orc.unfolding_svd(Y, k)
+            U[k] = pick(W, r[k])
+        return orc.rel_error(F, orc.reconstruct(orc.core(F, U, r), U, n))
+
+    assert sweep(lambda W, q: W[:, :q]) <= 1e-13
+    assert sweep(lambda W, q: W[:, -q:]) > 1e-3
