@@ -9,10 +9,12 @@ subtraction.  --workload sweep: one step = the 256-instance n = 128 parameter
 sweep in one tk_batch call.  --workload serving: the 2000-request Poisson
 stream replayed in real time through the serving loop.  --workload spectral:
 the default step on the Matern spectral density of Eq. (SD_matern), nu = 0.4,
-alpha = 0.1 (FP64 Gram unless --precision says otherwise).
+alpha = 0.1 (FP64 Gram unless --precision says otherwise).  --workload als:
+one Tucker-ALS sweep (Sec. 3.2) of the default workload's tensor, from its
+HOSVD factors, through tk_als.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload single|sweep|serving|spectral]
+                    [--workload single|sweep|serving|spectral|als]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs independent
 replicas of the workload (the path has no exchange step) and rank 0 prints.
@@ -43,6 +45,9 @@ SWEEP = ("256 Matern instances, n=128^3 cell-centred grid on [-1,1]^3, nu~U[0.3,
 SERVING = ("2000 requests, Poisson arrivals 200/s, n uniform over {64,128,256,384}, nu~U[0.3,2.5], "
            "ell~logU[0.05,1], eps over {1e-4,1e-6,1e-8}, rank cap 64, seeded PCG64(6874); "
            "replayed in real time through the serving loop")
+ALS_METRIC = "Tucker-ALS sweeps/s (modes 1, 2, 3 and the core) on the n=256 Matern tensor, FP64"
+ALS_WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, F resident on the device; "
+                "one tk_als sweep from the FP64 HOSVD's rank-11 factors (eps=1e-6) per step")
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 at 2070 MHz (nominal; the pipe the eigensolver and TTMs run on)
 
 
@@ -54,7 +59,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "sliced"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral"])
+    p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral", "als"])
     return p.parse_args()
 
 
@@ -344,6 +349,8 @@ def run_ours(args):
     if args.workload in ("single", "spectral"):
         line = bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier,
                             allmax, world, peaks, peak_src)
+    elif args.workload == "als":
+        line = bench_als(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks)
     elif args.workload == "sweep":
         line = bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, world, peaks,
                            peak_src)
@@ -439,6 +446,105 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
+    return line
+
+
+def _als_flops(n, r):
+    """Algorithmic FP64 work of one sweep: the two contractions over F
+    (F x_3 U3^T serves modes 1 and 2, F x_1 U1^T mode 3), the second
+    products, the three Grams of the single-hole unfoldings and the core."""
+    n1, n2, n3 = n
+    r1, r2, r3 = r
+    big = 2.0 * n1 * n2 * n3 * (r3 + r1)
+    small = 2.0 * (n1 * n2 * r2 * r3 + r1 * n1 * n2 * r3 + r1 * r2 * n2 * n3)
+    grams = 2.0 * (n1 * n1 * r2 * r3 + n2 * n2 * r1 * r3 + n3 * n3 * r1 * r2)
+    return big + small + grams + 2.0 * r1 * r2 * r3 * n3
+
+
+def bench_als(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks):
+    rank, local_rank, _ = dist_info()
+    prob = workloads.matern_n256(1e-6)
+    res = ctx.tucker(prob, precision=binding.TK_FP64)
+    ranks, _ = res.ranks
+    U0h = [res.factor(a) for a in range(3)]
+    hosvd_core2 = float((res.core() ** 2).sum())
+    res.free()
+    n = tuple(prob.n)
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.eval(prob, F)
+    U0 = [torch.from_numpy(u).cuda() for u in U0h]
+    U = [u.clone() for u in U0]
+    B = torch.empty(ranks, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            for a in range(3):
+                U[a].copy_(U0[a])
+        return ctx.als(F, U, B, 1, stream=stream)
+
+    sampler = ClockSampler(local_rank)
+    for _ in range(args.warmup):
+        step()
+    sampler.start()
+    ms, lat, launches, _, hist = timed(step, args.steps, 0)
+    clocks = sampler.stop()
+    value = whole_job_rate(args.steps, world, ms / 1000.0)
+
+    # end to end with host buffers: F and the starting factors in, factors and core out
+    Fh = F.cpu().pin_memory()
+    Uh = [u.pin_memory() for u in (torch.from_numpy(x) for x in U0h)]
+    Bh = torch.empty(ranks, dtype=torch.float64).pin_memory()
+    Uo = [torch.empty_like(u).pin_memory() for u in Uh]
+    h2d = Fh.numel() * 8 + sum(u.numel() * 8 for u in Uh)
+    d2h = Bh.numel() * 8 + sum(u.numel() * 8 for u in Uo)
+    torch.cuda.synchronize()
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            F.copy_(Fh, non_blocking=True)
+            for a in range(3):
+                U[a].copy_(Uh[a], non_blocking=True)
+        ctx.als(F, U, B, 1, stream=stream)
+        with torch.cuda.stream(stream):
+            for a in range(3):
+                Uo[a].copy_(U[a], non_blocking=True)
+            Bh.copy_(B, non_blocking=True)
+        stream.synchronize()
+    te = allmax(time.perf_counter() - te)
+    e2e = {"value": args.steps * world / te, "unit": "sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    flop = _als_flops(n, ranks)
+    step_ms = ms / args.steps
+    sm = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = FP64_TFLOPS_NOMINAL * sm / 2070.0
+    achieved = flop / (step_ms * 1e-3) / 1e12
+    roof = {"kernel": "tk_als sweep (whole call: two FP64 contractions over F, three eigensolves)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "GPU FP64: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled SM clock",
+            "algorithmic_flop_per_launch": flop}
+    line = {
+        "metric": ALS_METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ALS_WORKLOAD, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (512 MB written on the solve stream, outside the step events)",
+                   "ranks": ranks},
+        "core_norm2": {"hosvd": hosvd_core2, "after_sweep": [float(x) for x in hist]},
+        "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        Fo = oracle.tensor(workloads.oracle_kernel(prob, oracle), workloads.oracle_grid(prob, oracle))
+        t = time.perf_counter()
+        oracle.hooi(Fo, U0h, 1)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "sweeps/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"one whole oracle sweep of the bench tensor ({dt:.1f} s)"}
     return line
 
 

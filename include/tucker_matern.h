@@ -252,6 +252,27 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
                 const double* U2, const double* U3, const int32_t r[3], int precision, double* B,
                 void* stream);
 
+/* Tucker-ALS (Sec. 3.2): `sweeps` alternating sweeps refining the orthonormal
+ * factors U_k (device, n_k x r_k row-major, updated in place; the HOSVD's
+ * factors are the usual start) of the device tensor F (n[0] n[1] n[2] FP64,
+ * row-major, last index fastest).  A sweep visits modes 1, 2, 3 in order;
+ * mode k forms the single-hole tensor Y_k = F x_{m != k} U_m^T (the other
+ * modes mapped into their current subspaces) and replaces U_k by the r_k
+ * leading left singular vectors of Y_k's mode-k unfolding, computed in FP64
+ * as the leading eigenvectors of that unfolding's Gram (canonical signs as
+ * tk_sym_eig's).  B (device, r1 r2 r3) = F x_1 U1^T x_2 U2^T x_3 U3^T with the
+ * final factors (sweeps = 0: the core of the given factors).
+ * core_norm2 (host, 3 * sweeps doubles, may be NULL) receives the sum of the
+ * r_k leading eigenvalues after each mode update, i.e. |B|^2 for the factors
+ * of that moment; in exact arithmetic it never decreases.
+ * Needs 1 <= n_k <= 1024, 1 <= r_k <= min(n_k, 96), r_k <= r_m r_l for the
+ * other two modes (a multilinear rank), 0 <= sweeps <= 64; TK_EINVAL
+ * otherwise.  The covariance tensors of this library have fast-decaying
+ * unfolding spectra, which the subspace eigensolver relies on for n_k > 32.
+ * Synchronous with respect to `stream`. */
+int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double* U2, double* U3,
+           const int32_t r[3], int sweeps, double* B, double* core_norm2, void* stream);
+
 /* Allocation-free variant of tk_gram with precision TK_FP64 (no counterpart
  * in the paper).  Some callers cannot allocate device memory: code embedded in
  * a host application whose own allocator has reserved the GPU's memory,

@@ -80,6 +80,8 @@ SIGNATURES = {
     "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
                                _vp, _vp]),
     "tk_gram_noalloc": (_c.c_int, [_vp, _c.POINTER(_i32), _c.c_int, _vp, _vp]),
+    "tk_als": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int, _vp,
+                          _c.POINTER(_dbl), _vp]),
     "tk_default_serve_opts": (None, [_c.POINTER(ServeOpts)]),
     "tk_serve_start": (_c.c_int, [_vp, _c.POINTER(ServeOpts)]),
     "tk_serve_stop": (_c.c_int, [_vp]),
@@ -306,6 +308,17 @@ class Context:
         _check(self.lib.tk_ttm_core(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(),
                                     U[2].data_ptr(), r, int(precision), B.data_ptr(), _stream_ptr(stream)),
                self.ptr)
+
+    def als(self, F, U, B, sweeps: int, stream=None):
+        """Tucker-ALS sweeps on the device tensor F: the device factors U[k]
+        (n_k x r_k) are updated in place, B (r1 x r2 x r3) receives the core.
+        Returns the core norm^2 after each mode update (numpy, 3 * sweeps)."""
+        n = (_i32 * 3)(*F.shape)
+        r = (_i32 * 3)(*B.shape)
+        hist = (_dbl * max(3 * sweeps, 1))()
+        _check(self.lib.tk_als(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(), U[2].data_ptr(), r,
+                               int(sweeps), B.data_ptr(), hist, _stream_ptr(stream)), self.ptr)
+        return np.array(hist[: 3 * sweeps], dtype=np.float64)
 
 
 @dataclass

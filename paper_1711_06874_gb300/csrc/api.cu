@@ -844,6 +844,49 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
   });
 }
 
+int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double* U2, double* U3, const int32_t r[3],
+           int sweeps, double* B, double* core_norm2, void* stream) {
+  if (!ctx || !F || !n || !U1 || !U2 || !U3 || !r || !B) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return guard(ctx, [&] {
+    int nn[3] = {n[0], n[1], n[2]}, rr[3] = {r[0], r[1], r[2]};
+    for (int a = 0; a < 3; ++a) {
+      if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
+      if (rr[a] < 1 || rr[a] > std::min(nn[a], kAlsLamStride)) fail(TK_EINVAL, "need 1 <= r <= min(n, 96)");
+    }
+    for (int a = 0; a < 3; ++a)
+      if ((long long)rr[a] > (long long)rr[(a + 1) % 3] * rr[(a + 2) % 3])
+        fail(TK_EINVAL, "r is not a multilinear rank (r_k > r_m r_l)");
+    if (sweeps < 0 || sweeps > 64) fail(TK_EINVAL, "need 0 <= sweeps <= 64");
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    size_t sz[kAlsBuffers];
+    als_sizes(nn, rr, sz);
+    const size_t nlam = (size_t)std::max(sweeps, 1) * 3 * kAlsLamStride;
+    size_t total = carve_bytes<double>(nlam);
+    for (int i = 0; i < kAlsBuffers; ++i) total += carve_bytes<double>(std::max<size_t>(sz[i], 1));
+    ctx->ws.reserve(total, s);
+    double* buf[kAlsBuffers];
+    for (int i = 0; i < kAlsBuffers; ++i) buf[i] = ctx->ws.take<double>(std::max<size_t>(sz[i], 1));
+    double* lam_log = ctx->ws.take<double>(nlam);
+    const AlsBuffers w{buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
+    double* const U[3] = {U1, U2, U3};
+    als_f64(F, nn, U, rr, sweeps, B, lam_log, w, s);
+    if (core_norm2 && sweeps > 0) {
+      std::vector<double> h(nlam);
+      TK_CUDA(cudaMemcpyAsync(h.data(), lam_log, sizeof(double) * nlam, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      for (int t = 0; t < 3 * sweeps; ++t) {
+        const int k = t % 3;
+        double acc = 0.0;  // descending eigenvalues, summed from the smallest kept one
+        for (int i = rr[k] - 1; i >= 0; --i) acc += h[(size_t)t * kAlsLamStride + i];
+        core_norm2[t] = acc;
+      }
+    }
+    TK_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 int tk_profile_enable(tk_ctx* ctx, int on) {
   if (!ctx) return TK_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);

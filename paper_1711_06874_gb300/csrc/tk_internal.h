@@ -335,6 +335,20 @@ void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V
                       int cnt, const int* amap, const int* rk, int rk_stride, void* scratch, double* esum,
                       cudaStream_t s);
 
+// Tucker-ALS (Sec. 3.2): `sweeps` sweeps over modes 1, 2, 3 updating U[k]
+// (device, n_k x r_k row-major) in place, then B (r1 r2 r3).  lam_log gets
+// the r_k leading eigenvalues of each update's Gram at
+// lam_log[(sweep * 3 + k) * kAlsLamStride].  Buffer sizes (doubles) in the
+// order of AlsBuffers come from als_sizes.
+constexpr int kAlsBuffers = 6;
+constexpr int kAlsLamStride = 96;
+struct AlsBuffers {
+  double *T1, *Y, *W, *G, *gram_scr, *eig_scr;
+};
+void als_sizes(const int n[3], const int r[3], size_t out[kAlsBuffers]);
+void als_f64(const double* F, const int n[3], double* const U[3], const int r[3], int sweeps, double* B,
+             double* lam_log, const AlsBuffers& w, cudaStream_t s);
+
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
 void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
