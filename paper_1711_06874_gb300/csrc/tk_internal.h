@@ -335,20 +335,6 @@ void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V
                       int cnt, const int* amap, const int* rk, int rk_stride, void* scratch, double* esum,
                       cudaStream_t s);
 
-// Tucker-ALS (Sec. 3.2): `sweeps` sweeps over modes 1, 2, 3 updating U[k]
-// (device, n_k x r_k row-major) in place, then B (r1 r2 r3).  lam_log gets
-// the r_k leading eigenvalues of each update's Gram at
-// lam_log[(sweep * 3 + k) * kAlsLamStride].  Buffer sizes (doubles) in the
-// order of AlsBuffers come from als_sizes.
-constexpr int kAlsBuffers = 6;
-constexpr int kAlsLamStride = 96;
-struct AlsBuffers {
-  double *T1, *Y, *W, *G, *gram_scr, *eig_scr;
-};
-void als_sizes(const int n[3], const int r[3], size_t out[kAlsBuffers]);
-void als_f64(const double* F, const int n[3], double* const U[3], const int r[3], int sweeps, double* B,
-             double* lam_log, const AlsBuffers& w, cudaStream_t s);
-
 // (c) leading m eigenpairs of a symmetric PSD matrix, FP64.
 size_t sym_eig_scratch_doubles(int n, int m);
 void sym_eig_topm(const double* G, int n, int m, double* lam, double* V, double* trace_out,
@@ -382,6 +368,20 @@ size_t sym_eig_batch_scratch_doubles(int n, int m, int B);
 void sym_eig_batch(const double* G, int n, int m, int B, double* lam, double* V, double* trace, double* scratch,
                    cudaStream_t s, Profiler* pf = nullptr, const RankArgs* rank = nullptr, bool signs = true,
                    double u_data = 0x1p-53);
+// Tucker-ALS (Sec. 3.2): `sweeps` sweeps over modes 1, 2, 3 updating U[k]
+// (device, n_k x r_k row-major) in place, then B (r1 r2 r3).  lam_log gets
+// the r_k leading eigenvalues of each update's Gram at
+// lam_log[(sweep * 3 + k) * kAlsLamStride].  Buffer sizes (doubles) in the
+// order of AlsBuffers come from als_sizes.
+constexpr int kAlsBuffers = 6;
+constexpr int kAlsLamStride = 96;
+struct AlsBuffers {
+  double *T1, *Y, *W, *G, *eig_scr, *trace;
+};
+void als_sizes(const int n[3], const int r[3], size_t out[kAlsBuffers]);
+void als_f64(const double* F, const int n[3], double* const U[3], const int r[3], int sweeps, double* B,
+             double* lam_log, const AlsBuffers& w, cudaStream_t s);
+
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.
