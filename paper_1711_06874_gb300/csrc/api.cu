@@ -871,7 +871,7 @@ int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double*
     double* lam_log = ctx->ws.take<double>(nlam);
     const AlsBuffers w{buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
     double* const U[3] = {U1, U2, U3};
-    als_f64(F, nn, U, rr, sweeps, B, lam_log, w, s);
+    als_f64(F, nn, U, rr, sweeps, B, lam_log, w, ctx->sm_count, s);
     if (core_norm2 && sweeps > 0) {
       std::vector<double> h(nlam);
       TK_CUDA(cudaMemcpyAsync(h.data(), lam_log, sizeof(double) * nlam, cudaMemcpyDeviceToHost, s));

@@ -380,7 +380,7 @@ struct AlsBuffers {
 };
 void als_sizes(const int n[3], const int r[3], size_t out[kAlsBuffers]);
 void als_f64(const double* F, const int n[3], double* const U[3], const int r[3], int sweeps, double* B,
-             double* lam_log, const AlsBuffers& w, cudaStream_t s);
+             double* lam_log, const AlsBuffers& w, int sm_count, cudaStream_t s);
 
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
