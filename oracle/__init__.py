@@ -14,6 +14,7 @@ unpinned.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -269,6 +270,59 @@ def hooi(F: np.ndarray, U, sweeps: int):
     if rc != 0:
         raise MemoryError("oracle hooi failed")
     return U, B, hist[: 3 * sweeps]
+
+
+def coarser_grid(grid: Grid) -> Grid:
+    """The next coarser grid of the dyadic hierarchy (Sec. 3.2, multigrid
+    Tucker): the same box with half the cells per axis (cell-centred n -> n/2,
+    vertex n -> (n - 1)/2 + 1)."""
+    n = [int(v) for v in grid.n]
+    if grid.kind == VERTEX:
+        if any(v < 3 or (v - 1) % 2 for v in n):
+            raise ValueError("vertex grid: n - 1 must be even and n >= 3")
+        nc = [(v - 1) // 2 + 1 for v in n]
+    else:
+        if any(v < 2 or v % 2 for v in n):
+            raise ValueError("cell-centred grid: n must be even")
+        nc = [v // 2 for v in n]
+    return make_grid(nc, b=[float(v) for v in grid.b], kind=int(grid.kind))
+
+
+def interp_factor(U: np.ndarray, xc: np.ndarray, xf: np.ndarray) -> np.ndarray:
+    """Each column of U (given at the coarse points xc) at the fine points xf,
+    linearly between the two coarse points around x (continued linearly
+    beyond the outermost ones)."""
+    U = _f64(U)
+    nc = len(xc)
+    out = np.empty((len(xf), U.shape[1]), np.float64)
+    for i, x in enumerate(xf):
+        p = (x - xc[0]) / (xc[1] - xc[0])
+        j = min(max(int(math.floor(p)), 0), nc - 2)
+        t = p - j
+        out[i] = (1.0 - t) * U[j] + t * U[j + 1]
+    return out
+
+
+def multigrid(kernel: Kernel, grid: Grid, eps: float, levels: int, sweeps: int, rmax=None, rfix=None) -> dict:
+    """Multigrid Tucker (Sec. 3.2): the HOSVD on the coarsest of levels + 1
+    dyadically refined grids only; on each finer grid the factors from the
+    grid below, interpolated and orthonormalised, start `sweeps` Tucker-ALS
+    sweeps on that grid's tensor.  The ranks are the coarse HOSVD's."""
+    grids = [grid]
+    for _ in range(levels):
+        grids.insert(0, coarser_grid(grids[0]))
+    coarse = hosvd(kernel, grids[0], eps, rmax=rmax, rfix=rfix)
+    U = coarse["U"]
+    for lv, g in enumerate(grids):
+        if lv > 0:
+            prev = grids[lv - 1]
+            U = [np.linalg.qr(interp_factor(U[a], grid_axis(prev.kind, prev.n[a], prev.b[a]),
+                                            grid_axis(g.kind, g.n[a], g.b[a])))[0] for a in range(3)]
+        F = tensor(kernel, g)
+        U, B, hist = hooi(F, U, sweeps)
+    X = reconstruct(B, U, list(grid.n))
+    return {"ranks": coarse["ranks"], "U": U, "core": B, "core_norm2_hist": hist, "rel_error": rel_error(F, X),
+            "normF2": norm2(F), "coarse": coarse}
 
 
 def hosvd(kernel: Kernel, grid: Grid, eps: float, rmax=None, rfix=None) -> dict:

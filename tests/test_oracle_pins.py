@@ -578,3 +578,79 @@ def test_planted_als_ordering_mistake_is_caught(orc):
 
     assert sweep(lambda W, q: W[:, :q]) <= 1e-13
     assert sweep(lambda W, q: W[:, -q:]) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Multigrid Tucker (Sec. 3.2: HOSVD on the coarsest grid, interpolated
+# subspaces and ALS on the finer ones)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,nf", [(0, 16), (1, 17)])
+def test_interp_factor_reproduces_affine_columns(orc, kind, nf):
+    """Linear interpolation (and its linear continuation at the ends) is exact
+    on affine functions of x, on both grid kinds."""
+    gf = orc.make_grid(nf, b=1.3, kind=kind)
+    gc = orc.coarser_grid(gf)
+    xc = orc.grid_axis(kind, gc.n[0], 1.3)
+    xf = orc.grid_axis(kind, nf, 1.3)
+    U = np.stack([np.ones_like(xc), xc, 2.0 - 0.5 * xc], axis=1)
+    want = np.stack([np.ones_like(xf), xf, 2.0 - 0.5 * xf], axis=1)
+    np.testing.assert_allclose(orc.interp_factor(U, xc, xf), want, rtol=0, atol=1e-14)
+
+
+def test_planted_interpolation_coordinates_are_caught(orc):
+    """Interpolating on the vertex coordinates of a cell-centred grid fails
+    the affine pin."""
+    xc = orc.grid_axis(orc.CELL, 8, 1.0)
+    xf_wrong = orc.grid_axis(orc.VERTEX, 16, 1.0)
+    xf = orc.grid_axis(orc.CELL, 16, 1.0)
+    got = orc.interp_factor(xc[:, None], xc, xf_wrong)
+    assert np.abs(got[:, 0] - xf).max() > 1e-3
+
+
+def test_multigrid_coarser_grid_sizes(orc):
+    g = orc.coarser_grid(orc.make_grid([64, 32, 16]))
+    assert list(g.n) == [32, 16, 8]
+    g = orc.coarser_grid(orc.make_grid([65, 33, 17], kind=orc.VERTEX))
+    assert list(g.n) == [33, 17, 9]
+    with pytest.raises(ValueError):
+        orc.coarser_grid(orc.make_grid([15, 16, 16]))
+
+
+def test_multigrid_rank_one_gaussian_is_exact(orc):
+    """The Gaussian is separable: from the coarse rank-one factors the fine
+    sweeps recover it to rounding."""
+    k = orc.make_kernel(orc.GAUSSIAN, ell=[0.5, 0.7, 0.9])
+    out = orc.multigrid(k, orc.make_grid([32, 32, 32]), 1e-3, levels=2, sweeps=1, rfix=[1, 1, 1])
+    assert out["rel_error"] <= 1e-13
+
+
+def test_multigrid_reaches_the_fine_grid_als_result(orc):
+    """From interpolated coarse subspaces, the sweeps on the finest grid reach
+    the result of the same number of sweeps started from the fine grid's own
+    HOSVD (E to 1e-6 relative, factors to small angles), and E is the fine
+    HOSVD's or better."""
+    k = orc.make_kernel(orc.MATERN, nu=0.8, ell=[0.3, 0.4, 0.5])
+    g = orc.make_grid([32, 28, 24])
+    rf = [5, 5, 4]
+    mg = orc.multigrid(k, g, 1e-3, levels=2, sweeps=6, rfix=rf)
+    fine = orc.hosvd(k, g, 1e-3, rfix=rf)
+    F = orc.tensor(k, g)
+    U, B, _ = orc.hooi(F, fine["U"], 6)
+    e_als = orc.rel_error(F, orc.reconstruct(B, U, g.n))
+    assert abs(mg["rel_error"] - e_als) <= 1e-6 * e_als
+    assert mg["rel_error"] <= fine["rel_error"] * (1 + 1e-9)
+    for a in range(3):
+        s = np.linalg.svd(mg["U"][a] - U[a] @ (U[a].T @ mg["U"][a]), compute_uv=False)
+        assert s.max() <= 1e-5
+
+
+def test_multigrid_without_levels_is_hosvd_then_als(orc):
+    k = orc.make_kernel(orc.MATERN, nu=1.3, ell=[0.3, 0.35, 0.4])
+    g = orc.make_grid([12, 14, 16])
+    mg = orc.multigrid(k, g, 1e-4, levels=0, sweeps=2, rmax=[6, 6, 6])
+    ref = orc.hosvd(k, g, 1e-4, rmax=[6, 6, 6])
+    U, B, _ = orc.hooi(orc.tensor(k, g), ref["U"], 2)
+    assert mg["ranks"] == ref["ranks"]
+    for a in range(3):
+        assert np.array_equal(mg["U"][a], U[a])
+    assert np.array_equal(mg["core"], B)
