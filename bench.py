@@ -11,10 +11,13 @@ stream replayed in real time through the serving loop.  --workload spectral:
 the default step on the Matern spectral density of Eq. (SD_matern), nu = 0.4,
 alpha = 0.1 (FP64 Gram unless --precision says otherwise).  --workload als:
 one Tucker-ALS sweep (Sec. 3.2) of the default workload's tensor, from its
-HOSVD factors, through tk_als.
+HOSVD factors, through tk_als.  --workload multigrid: one multigrid Tucker
+solve (Sec. 3.2) of the default workload, the HOSVD on the 64^3 grid and one
+Tucker-ALS sweep on each of the 64^3, 128^3 and 256^3 grids, through
+tk_multigrid.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload single|sweep|serving|spectral|als]
+                    [--workload single|sweep|serving|spectral|als|multigrid]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs independent
 replicas of the workload (the path has no exchange step) and rank 0 prints.
@@ -48,6 +51,10 @@ SERVING = ("2000 requests, Poisson arrivals 200/s, n uniform over {64,128,256,38
 ALS_METRIC = "Tucker-ALS sweeps/s (modes 1, 2, 3 and the core) on the n=256 Matern tensor, FP64"
 ALS_WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, F resident on the device; "
                 "one tk_als sweep from the FP64 HOSVD's rank-11 factors (eps=1e-6) per step")
+MG_METRIC = "Multigrid Tucker solves/s (HOSVD on 64^3, one ALS sweep per grid) on the n=256 Matern tensor, FP64"
+MG_WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, eps=1e-6 ranks from the "
+               "64^3 HOSVD, levels=2 (64 -> 128 -> 256), 1 sweep per grid, F sampled on the device per grid")
+MG_LEVELS, MG_SWEEPS = 2, 1
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 at 2070 MHz (nominal; the pipe the eigensolver and TTMs run on)
 
 
@@ -59,7 +66,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "sliced"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral", "als"])
+    p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral", "als",
+                                                                       "multigrid"])
     return p.parse_args()
 
 
@@ -349,6 +357,8 @@ def run_ours(args):
     if args.workload in ("single", "spectral"):
         line = bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier,
                             allmax, world, peaks, peak_src)
+    elif args.workload == "multigrid":
+        line = bench_multigrid(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks)
     elif args.workload == "als":
         line = bench_als(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks)
     elif args.workload == "sweep":
@@ -545,6 +555,75 @@ def bench_als(args, torch, binding, workloads, ctx, stream, timed, barrier, allm
         dt = time.perf_counter() - t
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "sweeps/s", "cores": oracle.num_threads(),
                                 "kind": "oracle", "sample": f"one whole oracle sweep of the bench tensor ({dt:.1f} s)"}
+    return line
+
+
+def bench_multigrid(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks):
+    rank, local_rank, _ = dist_info()
+    prob = workloads.matern_n256(1e-6)
+
+    def step():
+        return ctx.multigrid(prob, MG_LEVELS, MG_SWEEPS, precision=binding.TK_FP64, stream=stream)
+
+    def done(res):
+        ranks = res.ranks[0]
+        res.free()
+        return ranks
+
+    sampler = ClockSampler(local_rank)
+    for _ in range(args.warmup):
+        done(step())
+    sampler.start()
+    ms, lat, launches, _, ranks = timed(step, args.steps, 0, cleanup=done)
+    clocks = sampler.stop()
+    value = whole_job_rate(args.steps, world, ms / 1000.0)
+    ranks = list(ranks)
+
+    # end to end: the request in, the factors and core out to host memory
+    d2h = 8 * (ranks[0] * ranks[1] * ranks[2] + sum(prob.n[a] * ranks[a] for a in range(3)))
+    torch.cuda.synchronize()
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        res = step()
+        res.factors_and_core(stream=stream)
+        res.free()
+    te = allmax(time.perf_counter() - te)
+    e2e = {"value": args.steps * world / te, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h}
+
+    # algorithmic FP64 work: one ALS sweep per grid (the 64^3 HOSVD is small next to it)
+    n = tuple(prob.n)
+    flop = sum(_als_flops(tuple(v >> (MG_LEVELS - lv) for v in n), ranks) for lv in range(MG_LEVELS + 1))
+    step_ms = ms / args.steps
+    sm = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = FP64_TFLOPS_NOMINAL * sm / 2070.0
+    achieved = flop / (step_ms * 1e-3) / 1e12
+    roof = {"kernel": "tk_multigrid (whole call: ALS contractions over F on three grids, K_nu sampling, HOSVD "
+                      "on 64^3)", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "GPU FP64: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled SM clock",
+            "algorithmic_flop_per_launch": flop}
+    line = {
+        "metric": MG_METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": MG_WORKLOAD, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (512 MB written on the solve stream, outside the step events)",
+                   "ranks": ranks},
+        "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t = time.perf_counter()
+        oracle.multigrid(workloads.oracle_kernel(prob, oracle), workloads.oracle_grid(prob, oracle), prob.eps,
+                         MG_LEVELS, MG_SWEEPS, rmax=list(prob.rmax))
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"one whole oracle multigrid solve of the bench workload "
+                                                            f"({dt:.1f} s)"}
     return line
 
 

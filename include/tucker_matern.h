@@ -273,6 +273,28 @@ int tk_ttm_core(tk_ctx* ctx, const double* F, const int32_t n[3], const double* 
 int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double* U2, double* U3,
            const int32_t r[3], int sweeps, double* B, double* core_norm2, void* stream);
 
+/* Multigrid Tucker (Sec. 3.2): the HOSVD (as tk_tucker, with `opts`) only on
+ * the coarsest of levels + 1 dyadically refined grids, the finest being
+ * `grid`; each coarser grid has half the cells per axis over the same box
+ * (cell-centred n -> n / 2, vertex n -> (n - 1) / 2 + 1).  On every grid,
+ * coarsest first, the current factors start `sweeps` Tucker-ALS sweeps on
+ * that grid's collocation tensor (as tk_als); between grids each factor
+ * column is carried to the finer grid by linear interpolation between the
+ * two coarse points around each fine point (continued linearly past the
+ * outermost ones) and the columns are orthonormalised.  The ranks and flags
+ * are the coarse HOSVD's.
+ * On TK_OK *out owns device copies of the finest grid's U_k (n_k x r_k) and
+ * B (r1 x r2 x r3), read as any result (tk_factor, tk_core, tk_result_copy,
+ * tk_reconstruct, tk_rel_error); tk_norm2 gives |F|^2 of the finest tensor
+ * and tk_eigenvalues the r_k eigenvalues of mode k's last update.
+ * Needs 0 <= levels <= 8 and 1 <= sweeps <= 64, every level's grid valid
+ * (n >= 2; cell-centred: even n at every grid but the coarsest; vertex: odd
+ * n likewise) and the coarse ranks a multilinear rank (r_k <= r_m r_l);
+ * TK_EINVAL otherwise.  Holds one FP64 tensor of the finest grid in the
+ * context's workspace.  Synchronous with respect to `stream`. */
+int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts, int levels,
+                 int sweeps, tk_result** out, void* stream);
+
 /* Allocation-free variant of tk_gram with precision TK_FP64 (no counterpart
  * in the paper).  Some callers cannot allocate device memory: code embedded in
  * a host application whose own allocator has reserved the GPU's memory,

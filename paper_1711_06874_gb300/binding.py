@@ -80,6 +80,8 @@ SIGNATURES = {
     "tk_ttm_core": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int,
                                _vp, _vp]),
     "tk_gram_noalloc": (_c.c_int, [_vp, _c.POINTER(_i32), _c.c_int, _vp, _vp]),
+    "tk_multigrid": (_c.c_int, [_vp, _c.POINTER(Kernel), _c.POINTER(Grid), _c.POINTER(Opts), _c.c_int, _c.c_int,
+                                _c.POINTER(_vp), _vp]),
     "tk_als": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int, _vp,
                           _c.POINTER(_dbl), _vp]),
     "tk_default_serve_opts": (None, [_c.POINTER(ServeOpts)]),
@@ -308,6 +310,16 @@ class Context:
         _check(self.lib.tk_ttm_core(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(),
                                     U[2].data_ptr(), r, int(precision), B.data_ptr(), _stream_ptr(stream)),
                self.ptr)
+
+    def multigrid(self, prob: workloads.Problem, levels: int, sweeps: int, precision=TK_FP64, rfix=(0, 0, 0),
+                  shortcut=True, fold=True, stream=None) -> "Result":
+        """Multigrid Tucker (tk_multigrid): HOSVD on the grid `levels` dyadic
+        coarsenings below prob's, then `sweeps` Tucker-ALS sweeps per grid."""
+        k, g, o = self._structs(prob, precision, rfix, shortcut, fold, False)
+        out = _vp()
+        _check(self.lib.tk_multigrid(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), int(levels), int(sweeps),
+                                     _c.byref(out), _stream_ptr(stream)), self.ptr)
+        return Result(self, out, prob, k, g)
 
     def als(self, F, U, B, sweeps: int, stream=None):
         """Tucker-ALS sweeps on the device tensor F: the device factors U[k]

@@ -887,6 +887,122 @@ int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double*
   });
 }
 
+int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts, int levels,
+                 int sweeps, tk_result** out, void* stream) {
+  if (!ctx || !out) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  tk_result* coarse = nullptr;
+  tk_result* res = nullptr;
+  int rc = guard(ctx, [&] {
+    check_kernel(kernel);
+    check_grid(grid);
+    check_opts(opts);
+    if (levels < 0 || levels > 8) fail(TK_EINVAL, "need 0 <= levels <= 8");
+    if (sweeps < 1 || sweeps > 64) fail(TK_EINVAL, "need 1 <= sweeps <= 64");
+    const bool vertex = (grid->kind == TK_VERTEX);
+    // g[0] is the coarsest grid, g[levels] the requested one
+    std::vector<tk_grid> g((size_t)levels + 1);
+    g[levels] = *grid;
+    for (int lv = levels; lv > 0; --lv) {
+      tk_grid c = g[lv];
+      for (int a = 0; a < 3; ++a) {
+        const int nf = g[lv].n[a];
+        if (vertex ? (nf % 2 == 0) : (nf % 2 != 0))
+          fail(TK_EINVAL, vertex ? "multigrid on a vertex grid needs odd n at every refined level"
+                                 : "multigrid on a cell-centred grid needs even n at every refined level");
+        c.n[a] = vertex ? (nf - 1) / 2 + 1 : nf / 2;
+      }
+      check_grid(&c);
+      g[lv - 1] = c;
+    }
+    set_device(ctx);
+    cudaStream_t s = as_stream(stream);
+    coarse = solve_one(ctx, kernel, &g[0], opts, s);
+    int r[3];
+    for (int a = 0; a < 3; ++a) r[a] = coarse->r[a];
+    for (int a = 0; a < 3; ++a) {
+      if (r[a] > std::min(kAlsLamStride, kMgMaxRank)) fail(TK_EINVAL, "coarse rank above 96");
+      if ((long long)r[a] > (long long)r[(a + 1) % 3] * r[(a + 2) % 3])
+        fail(TK_EINVAL, "the coarse ranks are not a multilinear rank (r_k > r_m r_l)");
+    }
+    const int* nfin = grid->n;
+    const size_t Nf = (size_t)nfin[0] * nfin[1] * nfin[2];
+    // second workspace: F of the grid being refined (the finest is largest),
+    // |F|^2, and two factor sets that alternate between grids
+    size_t need = carve_bytes<double>(Nf) + carve_bytes<double>(1);
+    for (int set = 0; set < 2; ++set)
+      for (int a = 0; a < 3; ++a) need += carve_bytes<double>((size_t)nfin[a] * r[a]);
+    ctx->ws2.reserve(need, s);
+    double* F = ctx->ws2.take<double>(Nf);
+    double* normF2 = ctx->ws2.take<double>(1);
+    double* Uset[2][3];
+    for (int set = 0; set < 2; ++set)
+      for (int a = 0; a < 3; ++a) Uset[set][a] = ctx->ws2.take<double>((size_t)nfin[a] * r[a]);
+    for (int a = 0; a < 3; ++a)
+      TK_CUDA(cudaMemcpyAsync(Uset[0][a], coarse->U[a], sizeof(double) * (size_t)g[0].n[a] * r[a],
+                              cudaMemcpyDeviceToDevice, s));
+    res = new tk_result();
+    res->ctx = ctx;
+    res->precision = TK_FP64;
+    for (int a = 0; a < 3; ++a) {
+      res->n[a] = nfin[a];
+      res->r[a] = r[a];
+      res->m[a] = r[a];
+      res->flags[a] = coarse->flags[a];
+      TK_CUDA(cudaMalloc(&res->U[a], sizeof(double) * (size_t)nfin[a] * r[a]));
+    }
+    TK_CUDA(cudaMalloc(&res->core, sizeof(double) * (size_t)r[0] * r[1] * r[2]));
+    const size_t nlam = (size_t)sweeps * 3 * kAlsLamStride;
+    std::vector<double> lam_h(nlam);
+    int cur = 0;
+    for (int lv = 0; lv <= levels; ++lv) {
+      if (lv > 0) {
+        const double* const from[3] = {Uset[cur][0], Uset[cur][1], Uset[cur][2]};
+        mg_prolong_orth(from, g[lv - 1].n, Uset[1 - cur], g[lv].n, r, vertex ? 1 : 0, s);
+        cur = 1 - cur;
+      }
+      const tk_grid& gl = g[lv];
+      ctx->ws.reserve(carve_bytes<double>(eval_scratch_doubles(*kernel, gl) + 1) +
+                          carve_bytes<double>(eval_rowsq_doubles(gl)),
+                      s);
+      double* table = ctx->ws.take<double>(eval_scratch_doubles(*kernel, gl) + 1);
+      double* rowsq = ctx->ws.take<double>(eval_rowsq_doubles(gl));
+      eval_tensor_f64(*kernel, gl, F, table, s, rowsq, lv == levels ? normF2 : nullptr);
+      size_t sz[kAlsBuffers];
+      als_sizes(gl.n, r, sz);
+      size_t total = carve_bytes<double>(nlam);
+      for (int i = 0; i < kAlsBuffers; ++i) total += carve_bytes<double>(std::max<size_t>(sz[i], 1));
+      ctx->ws.reserve(total, s);
+      double* buf[kAlsBuffers];
+      for (int i = 0; i < kAlsBuffers; ++i) buf[i] = ctx->ws.take<double>(std::max<size_t>(sz[i], 1));
+      double* lam_log = ctx->ws.take<double>(nlam);
+      const AlsBuffers w{buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
+      double* const U[3] = {Uset[cur][0], Uset[cur][1], Uset[cur][2]};
+      als_f64(F, gl.n, U, r, sweeps, res->core, lam_log, w, ctx->sm_count, s);
+      if (lv == levels)
+        TK_CUDA(cudaMemcpyAsync(lam_h.data(), lam_log, sizeof(double) * nlam, cudaMemcpyDeviceToHost, s));
+    }
+    for (int a = 0; a < 3; ++a)
+      TK_CUDA(cudaMemcpyAsync(res->U[a], Uset[cur][a], sizeof(double) * (size_t)nfin[a] * r[a],
+                              cudaMemcpyDeviceToDevice, s));
+    double nrm = 0.0;
+    TK_CUDA(cudaMemcpyAsync(&nrm, normF2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    res->normF2 = nrm;
+    for (int k = 0; k < 3; ++k) {
+      const double* l = lam_h.data() + (size_t)((sweeps - 1) * 3 + k) * kAlsLamStride;
+      res->lam[k].assign(l, l + r[k]);
+    }
+  });
+  if (coarse) tk_result_free(coarse);
+  if (rc != TK_OK) {
+    if (res) tk_result_free(res);
+    return rc;
+  }
+  *out = res;
+  return TK_OK;
+}
+
 int tk_profile_enable(tk_ctx* ctx, int on) {
   if (!ctx) return TK_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);

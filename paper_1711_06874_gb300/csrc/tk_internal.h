@@ -382,6 +382,14 @@ void als_sizes(const int n[3], const int r[3], size_t out[kAlsBuffers]);
 void als_f64(const double* F, const int n[3], double* const U[3], const int r[3], int sweeps, double* B,
              double* lam_log, const AlsBuffers& w, int sm_count, cudaStream_t s);
 
+// Multigrid Tucker (Sec. 3.2): the factors Uc[k] (device, nc_k x r_k) of a
+// grid, linearly interpolated to the next finer grid of the dyadic hierarchy
+// (cell-centred n_f = 2 n_c, vertex n_f - 1 = 2 (n_c - 1)) and orthonormalised,
+// into Uf[k] (device, nf_k x r_k).  One launch for the three modes.
+constexpr int kMgMaxRank = 96;
+void mg_prolong_orth(const double* const Uc[3], const int nc[3], double* const Uf[3], const int nf[3],
+                     const int r[3], int vertex, cudaStream_t s);
+
 // rank rule for B instances: out [b * 4 + 0..2] as rank_rule, with eps [b],
 // rmax [b], rfix [b]; n_eig is the order of the eigenproblems, n_flag the n
 // of the precision flag.

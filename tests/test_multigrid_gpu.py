@@ -1,0 +1,134 @@
+"""Multigrid Tucker (Sec. 3.2) through tk_multigrid against the oracle's.
+
+Both sides take the HOSVD on the coarsest grid, carry the factors up the
+dyadic hierarchy by linear interpolation and orthonormalisation, and run the
+same Tucker-ALS sweeps on every grid.  The two orthonormalisations may give
+different bases of the same span, which the sweeps do not see (the update of
+a mode reads the other factors only through their spans, and never reads its
+own starting factor).  The oracle takes each update from the one-sided Jacobi
+SVD of the single-hole unfolding, the CUDA path from the eigenvectors of
+that unfolding's FP64 Gram, so factors are compared by principal angles, and
+the core and E to tolerances that cover the different roundings (as the ALS
+parity tests do).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests._util import U64, near_threshold, principal_sines
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_06874_gb300 import binding
+
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def wl():
+    from paper_1711_06874_gb300 import workloads
+
+    return workloads
+
+
+def _check(ctx, orc, wl, prob, levels, sweeps, rfix=(0, 0, 0)):
+    from paper_1711_06874_gb300 import binding
+
+    k, g = wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc)
+    res = ctx.multigrid(prob, levels, sweeps, precision=binding.TK_FP64, rfix=rfix)
+    ranks, _ = res.ranks
+    ranks = list(ranks)
+    use_rfix = list(rfix) if any(rfix) else None
+    mo = orc.multigrid(k, g, prob.eps, levels, sweeps, rmax=list(prob.rmax), rfix=use_rfix)
+    if mo["ranks"] != ranks:
+        # only where the coarse oracle's discarded sum sits at the eps threshold
+        co = mo["coarse"]
+        for a in range(3):
+            if ranks[a] != mo["ranks"][a]:
+                assert abs(ranks[a] - mo["ranks"][a]) == 1
+                assert near_threshold(co["lam"][a], co["normF2"], prob.eps, mo["ranks"][a]), a
+        mo = orc.multigrid(k, g, prob.eps, levels, sweeps, rmax=list(prob.rmax), rfix=ranks)
+    U = [res.factor(a) for a in range(3)]
+    B = res.core()
+    F = orc.tensor(k, g)
+    nF2 = orc.norm2(F)
+    assert abs(res.norm2 - nF2) <= 1e-13 * nF2
+    hist = mo["core_norm2_hist"]
+    for a in range(3):
+        np.testing.assert_allclose(U[a].T @ U[a], np.eye(ranks[a]), atol=1e-12)
+        # eigenvalues of the last update of mode a sum to that update's |B|^2
+        lam = res.eigenvalues(a, ranks[a])
+        assert abs(lam.sum() - hist[3 * (sweeps - 1) + a]) <= 1e-9 * nF2
+        # Davis-Kahan bound of the last update's Gram error, as in the ALS tests
+        m1, m2 = [b for b in range(3) if b != a]
+        Y = orc.ttm(orc.ttm(F, m1, mo["U"][m1]), m2, mo["U"][m2])
+        sv2 = orc.unfolding_svd(Y, a)[0] ** 2
+        gap = min((sv2[i] - sv2[i + 1]) / sv2[0] for i in range(ranks[a]))
+        assert principal_sines(mo["U"][a], U[a]).max() <= max(1e-9, 100 * U64 / gap), (a, gap)
+    # B is the core of the returned factors
+    np.testing.assert_allclose(B, orc.core(F, U, ranks), rtol=0, atol=1e-12 * math.sqrt(nF2))
+    e = orc.rel_error(F, orc.reconstruct(B, U, list(prob.n)))
+    e_o = mo["rel_error"]
+    assert abs(e - e_o) <= 1e-6 * e_o + 1e-14, (e, e_o)
+    # the library's own Eq. (FNorm) on the result agrees with the oracle's
+    assert abs(res.rel_error() - e) <= 1e-6 * e + 1e-14
+    return res, mo
+
+
+MG_CASES = [
+    # general K_nu, isotropic, eps rule, two coarsenings (32 -> 16 -> 8)
+    dict(kind=0, nu=1.2, ell=0.3, n=32, grid=0, eps=1e-6, levels=2, sweeps=2, rfix=(0, 0, 0)),
+    # Slater on the vertex grid (33 -> 17 -> 9), fixed ranks
+    dict(kind=1, nu=0.5, ell=0.4, n=33, grid=1, eps=1e-6, levels=2, sweeps=1, rfix=(5, 5, 5)),
+    # anisotropic lengths and unequal n (32, 24, 16 -> 16, 12, 8)
+    dict(kind=0, nu=0.7, ell=(0.3, 0.5, 0.8), n=(32, 24, 16), grid=0, eps=1e-5, levels=1, sweeps=2,
+         rfix=(0, 0, 0)),
+    # no coarsening: the HOSVD followed by the sweeps
+    dict(kind=0, nu=2.5, ell=0.25, n=20, grid=0, eps=1e-6, levels=0, sweeps=1, rfix=(0, 0, 0)),
+    # Matern spectral density (Eq. SD_matern), ragged n at the coarse level (40 -> 20 -> 10)
+    dict(kind=3, nu=0.4, ell=1.0, n=40, grid=0, eps=1e-5, levels=2, sweeps=1, rfix=(4, 4, 4)),
+]
+
+
+@pytest.mark.parametrize("case", MG_CASES, ids=lambda c: f"kind{c['kind']}-grid{c['grid']}-L{c['levels']}")
+def test_multigrid_matches_oracle(ctx, orc, wl, case):
+    prob = wl.problem(case["kind"], nu=case["nu"], ell=case["ell"], p=1.0, n=case["n"], grid=case["grid"],
+                      eps=case["eps"], rmax=20)
+    _check(ctx, orc, wl, prob, case["levels"], case["sweeps"], case["rfix"])
+
+
+def test_multigrid_separable_gaussian_is_exact(ctx, orc, wl):
+    """exp(-|x|^2 / ell^2) is a product of one-dimensional factors: rank
+    (1, 1, 1), and the interpolated start is refined to the exact factors."""
+    prob = wl.problem(wl.GAUSSIAN, ell=(0.5, 0.7, 0.9), n=(16, 24, 32), eps=1e-6, rmax=4)
+    res, _ = _check(ctx, orc, wl, prob, 2, 1)
+    assert list(res.ranks[0]) == [1, 1, 1]
+    assert res.rel_error() <= 1e-13
+
+
+def test_multigrid_rejects_grids_that_do_not_halve(ctx, wl):
+    from paper_1711_06874_gb300 import binding
+
+    with pytest.raises(binding.TuckerError):
+        ctx.multigrid(wl.problem(n=30, eps=1e-4), 2, 1)  # 30 -> 15 is odd at a refined level
+    with pytest.raises(binding.TuckerError):
+        ctx.multigrid(wl.problem(n=32, grid=wl.VERTEX, eps=1e-4), 1, 1)  # even n on a vertex grid
+    with pytest.raises(binding.TuckerError):
+        ctx.multigrid(wl.problem(n=16, eps=1e-4), 1, 0)  # needs at least one sweep
+
+
+def test_multigrid_bench_workload_full_size(ctx, orc, wl):
+    """The n = 256 Matern workload (nu = 1.2, ell = 0.2, eps = 1e-6) with the
+    HOSVD on the 64^3 grid and one sweep per grid, in the launch
+    configuration the benchmark's multigrid workload times."""
+    _check(ctx, orc, wl, wl.matern_n256(1e-6), 2, 1)
