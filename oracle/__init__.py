@@ -5,7 +5,10 @@ Tucker/HOSVD of covariance tensors in arXiv:1711.06874.  Only the test suite,
 ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg use it; the
 CUDA library never imports, links or calls anything here.
 
-Parity status of each routine (what pins it) is listed in the C source.  The
+Parity status of each routine (what pins it) is listed in the C source.
+The multigrid Tucker and the canonical-to-Tucker routines at the end of this
+file are written in Python over those routines and LAPACK's SVD (numpy);
+their pins are in the test suite (test_oracle_pins.py).  The
 value of the Tucker tensor at the origin compared with the printed table of
 Sec. 4 (Table zero_points) is a sanity check only: the paper does not state
 the box size or whether ALS followed the HOSVD, so that comparison is parity
@@ -353,3 +356,116 @@ def hosvd(kernel: Kernel, grid: Grid, eps: float, rmax=None, rfix=None) -> dict:
         "rel_error": float(out[1]),
         "core_norm2": float(out[2]),
     }
+
+
+# ---------------------------------------------------------------------------
+# Canonical-to-Tucker (C2T) of Sec. 3.4: the Tucker approximation of a tensor
+# given in the canonical format A = C x_1 U1 x_2 U2 x_3 U3, C = diag(c)
+# (Eq. Can_Contr, Sec. 3.1), without forming or unfolding A.  The initial
+# guess is the reduced HOSVD (RHOSVD): the leading left singular vectors of
+# each side matrix U_l; Tucker-ALS sweeps follow, each single-hole unfolding
+# taken in the canonical format.  The SVDs are LAPACK's (numpy).
+# ---------------------------------------------------------------------------
+
+
+def _canonical_signs(Z: np.ndarray) -> np.ndarray:
+    """Each column's entry of largest magnitude among the first ceil(n/2)
+    made positive (the lowest index on a tie), as for the HOSVD factors."""
+    Z = Z.copy()
+    h = (Z.shape[0] + 1) // 2
+    for j in range(Z.shape[1]):
+        i = int(np.argmax(np.abs(Z[:h, j])))
+        if Z[i, j] < 0:
+            Z[:, j] = -Z[:, j]
+    return Z
+
+
+def cp_full(c, U) -> np.ndarray:
+    """The full tensor a(i1, i2, i3) = sum_k c_k U1[i1, k] U2[i2, k] U3[i3, k]."""
+    c = _f64(c)
+    out = np.zeros((U[0].shape[0], U[1].shape[0], U[2].shape[0]), np.float64)
+    for k in range(c.size):
+        out += c[k] * np.multiply.outer(np.multiply.outer(U[0][:, k], U[1][:, k]), U[2][:, k])
+    return out
+
+
+def cp_norm2(c, U) -> float:
+    """|A|_F^2 = sum_{k, k'} c_k c_k' prod_l <u_k^(l), u_k'^(l)>."""
+    c = _f64(c)
+    G = np.outer(c, c)
+    for l in range(3):
+        G = G * (U[l].T @ U[l])
+    return float(G.sum())
+
+
+def cp_core(c, W) -> np.ndarray:
+    """Core of the projection: B = sum_k c_k W1[:, k] o W2[:, k] o W3[:, k],
+    with W_l = Z_l^T U_l (r_l x R)."""
+    return cp_full(c, W)
+
+
+def rhosvd(c, U, eps: float, rmax=None, rfix=None) -> dict:
+    """Reduced HOSVD of the canonical tensor (c, U): Z_l = leading left
+    singular vectors of U_l (unit columns).  Rank rule: r_l is the smallest r
+    whose discarded singular values satisfy sqrt(sum_{k>r} s_k^2) <=
+    eps |A| / (3 |c|), so that the RHOSVD bound |A - A_r| <= |c| sum_l
+    sqrt(sum_{k>r_l} s_{l,k}^2) guarantees E <= eps; capped at rmax, replaced
+    by rfix where that is > 0.  Core B = A x_1 Z1^T x_2 Z2^T x_3 Z3^T,
+    formed in the canonical format."""
+    c = _f64(c)
+    U = [_f64(u) for u in U]
+    normA2 = cp_norm2(c, U)
+    cn = float(np.linalg.norm(c))
+    tol = eps * math.sqrt(max(normA2, 0.0)) / (3.0 * cn) if cn > 0 else 0.0
+    Z, W, sv, ranks, delta = [], [], [], [], []
+    for l in range(3):
+        Ul, s, _ = np.linalg.svd(U[l], full_matrices=False)
+        tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1])  # tail[r] = sqrt(sum_{k >= r} s_k^2)
+        r = s.size
+        for q in range(1, s.size + 1):
+            if q == s.size or tail[q] <= tol:
+                r = q
+                break
+        if rmax is not None:
+            r = min(r, int(rmax[l] if np.ndim(rmax) else rmax))
+        if rfix is not None and int(rfix[l]) > 0:
+            r = min(int(rfix[l]), s.size)
+        Zl = _canonical_signs(Ul[:, :r])
+        Z.append(Zl)
+        W.append(Zl.T @ U[l])
+        sv.append(s)
+        ranks.append(r)
+        delta.append(float(tail[r]) if r < s.size else 0.0)
+    return {"ranks": ranks, "U": Z, "W": W, "sv": sv, "core": cp_core(c, W), "normA2": normA2,
+            "bound": cn * sum(delta)}
+
+
+def c2t(c, U, eps: float, sweeps: int, rmax=None, rfix=None) -> dict:
+    """Canonical-to-Tucker (Sec. 3.4): the RHOSVD as the initial guess, then
+    `sweeps` Tucker-ALS sweeps over modes 1, 2, 3 (each update using the
+    factors already updated in the sweep).  The single-hole tensor of mode l,
+    A x_m Z_m^T x_q Z_q^T (m < q the other modes), has the mode-l unfolding
+    M[i, a r_q + b] = sum_k U_l[i, k] c_k W_m[a, k] W_q[b, k]; Z_l becomes its
+    r_l leading left singular vectors.  Returns the factors, the core and
+    |B|^2 after each mode update (the sum of the kept squared singular
+    values)."""
+    c = _f64(c)
+    U = [_f64(u) for u in U]
+    init = rhosvd(c, U, eps, rmax=rmax, rfix=rfix)
+    r = init["ranks"]
+    for l in range(3):
+        if r[l] > r[(l + 1) % 3] * r[(l + 2) % 3]:
+            raise ValueError("the RHOSVD ranks are not a multilinear rank (r_l > r_m r_q)")
+    Z = [z.copy() for z in init["U"]]
+    W = [w.copy() for w in init["W"]]
+    hist = []
+    for _ in range(sweeps):
+        for l in range(3):
+            m, q = [a for a in range(3) if a != l]
+            KR = (W[m][:, None, :] * W[q][None, :, :]).reshape(r[m] * r[q], c.size)  # Khatri-Rao, row a r_q + b
+            M = (U[l] * c[None, :]) @ KR.T
+            Ul, s, _ = np.linalg.svd(M, full_matrices=False)
+            Z[l] = _canonical_signs(Ul[:, : r[l]])
+            W[l] = Z[l].T @ U[l]
+            hist.append(float((s[: r[l]] ** 2).sum()))
+    return {"ranks": r, "U": Z, "core": cp_core(c, W), "core_norm2_hist": np.array(hist), "rhosvd": init}

@@ -654,3 +654,153 @@ def test_multigrid_without_levels_is_hosvd_then_als(orc):
     for a in range(3):
         assert np.array_equal(mg["U"][a], U[a])
     assert np.array_equal(mg["core"], B)
+
+
+# ---- canonical-to-Tucker (Sec. 3.4) -----------------------------------------
+
+
+def _cp():
+    from paper_1711_06874_gb300 import cp_inputs
+
+    return cp_inputs
+
+
+def test_newton_sinc_cp_is_one_over_r(orc):
+    """The sinc expansion of Eq. sinc_Newt with h_M = 3 log(M) / M, M = 64,
+    reproduces 1/|x| at every grid point with |x| >= 0.5 (the quadrature's
+    truncation and discretisation errors are both below 1e-13 there)."""
+    cp = _cp()
+    n = 24
+    c, U = cp.newton_sinc_cp(n, 64)
+    A = orc.cp_full(c, U)
+    x = cp.grid_points(n)
+    r = np.sqrt(x[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2)
+    far = r >= 0.5
+    assert np.max(np.abs(A[far] * r[far] - 1.0)) <= 1e-13
+    for u in U:
+        np.testing.assert_allclose(np.linalg.norm(u, axis=0), 1.0, atol=1e-14)
+
+
+def test_cp_norm_is_the_full_tensor_norm(orc):
+    c, U = _cp().random_cp(3, (7, 8, 9), 6)
+    assert abs(orc.cp_norm2(c, U) - orc.norm2(orc.cp_full(c, U))) <= 1e-13 * orc.norm2(orc.cp_full(c, U))
+
+
+def test_rhosvd_core_is_the_projection_of_the_full_tensor(orc):
+    """B formed in the canonical format equals the full tensor's TTM chain
+    with the same factors (a dropped weight or a transposed W fails)."""
+    c, U = _cp().random_cp(5, (9, 10, 11), 7)
+    res = orc.rhosvd(c, U, 1e-3, rfix=[3, 4, 5])
+    A = orc.cp_full(c, U)
+    np.testing.assert_allclose(res["core"], orc.core(A, res["U"], res["ranks"]), rtol=0,
+                               atol=1e-13 * math.sqrt(orc.norm2(A)))
+    for l, z in enumerate(res["U"]):
+        np.testing.assert_allclose(z.T @ z, np.eye(res["ranks"][l]), atol=1e-13)
+        # the factors span the side matrix's leading left singular subspace
+        Ul = np.linalg.svd(U[l])[0][:, : res["ranks"][l]]
+        assert _principal_sines(Ul, z).max() <= 1e-12
+
+
+def test_rhosvd_error_bound_and_eps_rule(orc):
+    """|A - A_r| <= |c| sum_l sqrt(sum_{k > r_l} s_{l,k}^2) (the RHOSVD bound),
+    for fixed ranks and for the eps rule, which then meets E <= eps."""
+    c, U = _cp().random_cp(9, (12, 13, 14), 10)
+    A = orc.cp_full(c, U)
+    for kw in (dict(rfix=[3, 4, 5]), dict(rfix=[6, 2, 4])):
+        res = orc.rhosvd(c, U, 1e-3, **kw)
+        X = orc.reconstruct(res["core"], res["U"], A.shape)
+        err = math.sqrt(orc.norm2(A - X))
+        assert err <= res["bound"] * (1 + 1e-12)
+        assert err > 0
+    cs, Us = _cp().newton_sinc_cp(16, 12)
+    As = orc.cp_full(cs, Us)
+    for eps in (1e-3, 1e-6):
+        res = orc.rhosvd(cs, Us, eps)
+        X = orc.reconstruct(res["core"], res["U"], As.shape)
+        assert orc.rel_error(As, X) <= eps
+        assert res["bound"] <= eps * math.sqrt(res["normA2"]) * (1 + 1e-12)
+        assert max(res["ranks"]) < 16
+
+
+def test_rhosvd_exact_on_side_matrices_of_low_column_rank(orc):
+    """Side matrices of column rank (2, 3, 4): those are the ranks at a tiny
+    eps, and the Tucker tensor is exact; a rank-one CP tensor gives (1, 1, 1)."""
+    c, U = _cp().random_cp(13, (10, 11, 12), 9, col_rank=(2, 3, 4))
+    A = orc.cp_full(c, U)
+    res = orc.rhosvd(c, U, 1e-10)
+    assert res["ranks"] == [2, 3, 4]
+    assert orc.rel_error(A, orc.reconstruct(res["core"], res["U"], A.shape)) <= 1e-13
+    c1, U1 = _cp().random_cp(17, (6, 7, 8), 1)
+    res1 = orc.rhosvd(c1, U1, 1e-12)
+    assert res1["ranks"] == [1, 1, 1]
+    assert abs(abs(res1["core"].item()) - abs(c1[0])) <= 1e-14 * abs(c1[0])
+
+
+def test_c2t_sweeps_are_the_full_tensor_sweeps(orc):
+    """The C2T sweeps in the canonical format give the factors, core and
+    core-norm history of Tucker-ALS on the full tensor from the same start
+    (the single-hole unfolding built from the side matrices is the full
+    tensor's, up to a column order)."""
+    cp = _cp()
+    for c, U, rfix in (cp.newton_sinc_cp((14, 16, 18), 10) + ([4, 5, 6],),
+                       cp.random_cp(21, (9, 10, 11), 8) + ([3, 4, 3],)):
+        A = orc.cp_full(c, U)
+        out = orc.c2t(c, U, 1e-3, 2, rfix=rfix)
+        Uo, Bo, ho = orc.hooi(A, out["rhosvd"]["U"], 2)
+        nA2 = orc.norm2(A)
+        np.testing.assert_allclose(out["core_norm2_hist"], ho, rtol=0, atol=1e-12 * nA2)
+        for l in range(3):
+            assert _principal_sines(Uo[l], out["U"][l]).max() <= 1e-9
+        np.testing.assert_allclose(out["core"], orc.core(A, out["U"], out["ranks"]), rtol=0,
+                                   atol=1e-12 * math.sqrt(nA2))
+        e = orc.rel_error(A, orc.reconstruct(out["core"], out["U"], A.shape))
+        e0 = orc.rel_error(A, orc.reconstruct(out["rhosvd"]["core"], out["rhosvd"]["U"], A.shape))
+        assert e <= e0 * (1 + 1e-9)
+
+
+def test_rhosvd_bound_is_attained(orc):
+    """A case where the RHOSVD bound holds with equality: modes 2 and 3 are
+    exactly rank one, mode 1 has two unit columns at angle theta, and c is
+    the side matrix's second right singular vector, so the discarded part is
+    s_2 |c| exactly (an off-by-one in the discarded tail fails here)."""
+    n, th = 5, 0.7
+    rng = np.random.default_rng(23)
+    u1 = np.zeros(n)
+    u1[0] = 1.0
+    u2 = np.zeros(n)
+    u2[0], u2[1] = math.cos(th), math.sin(th)
+    v = rng.standard_normal(6)
+    w = rng.standard_normal(7)
+    U = [np.stack([u1, u2], 1), np.stack([v, v], 1) / np.linalg.norm(v), np.stack([w, w], 1) / np.linalg.norm(w)]
+    c = np.linalg.svd(U[0])[2][1].copy()  # unit vector
+    res = orc.rhosvd(c, U, 0.0, rfix=[1, 1, 1])
+    A = orc.cp_full(c, U)
+    err = math.sqrt(orc.norm2(A - orc.reconstruct(res["core"], res["U"], A.shape)))
+    s2 = math.sqrt(1.0 - math.cos(th))  # singular values of [u1 u2]: sqrt(1 +- cos theta)
+    assert abs(err - s2) <= 1e-13
+    assert abs(res["bound"] - s2) <= 1e-13
+
+
+def test_rhosvd_eps_rule_shares_eps_over_three_modes(orc):
+    """Side matrices with dense, geometrically decaying spectra (ratio 0.6):
+    every mode's discarded part of the bound is within eps |A| / 3, which
+    the next smaller rank would exceed, so the whole bound is within eps |A|."""
+    rng = np.random.default_rng(29)
+    c = np.abs(rng.standard_normal(30)) + 0.5
+    U = []
+    for _ in range(3):
+        Q1 = np.linalg.qr(rng.standard_normal((30, 30)))[0]
+        Q2 = np.linalg.qr(rng.standard_normal((30, 30)))[0]
+        M = Q1 @ np.diag(0.6 ** np.arange(30)) @ Q2.T
+        U.append(M / np.linalg.norm(M, axis=0))
+    nA = math.sqrt(orc.cp_norm2(c, U))
+    cn = float(np.linalg.norm(c))
+    for eps in (1e-2, 1e-4):
+        res = orc.rhosvd(c, U, eps)
+        assert res["bound"] <= eps * nA * (1 + 1e-12)
+        for l in range(3):
+            s = np.linalg.svd(U[l], compute_uv=False)
+            r = res["ranks"][l]
+            assert 1 <= r < 30
+            assert cn * math.sqrt(float((s[r:] ** 2).sum())) <= eps * nA / 3 * (1 + 1e-12)
+            assert cn * math.sqrt(float((s[r - 1:] ** 2).sum())) > eps * nA / 3
