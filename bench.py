@@ -240,28 +240,40 @@ def _knu_flops(prob):
     return tot
 
 
-def _roofline(prof, prob, precision, clocks, peaks, peak_src):
+def _gram_tc_issued(h):
+    """BF16 flops the tensor-core Gram issues for one h x h octant Gram: 21
+    slice pairs on every 128 x 64 block touching the upper triangle."""
+    nrt, nct = (h + 127) // 128, (h + 63) // 64
+    nb = sum(max(0, nct - (i * 128) // 64) for i in range(nrt))
+    return 21 * 2.0 * 128 * 64 * (h * h) * nb
+
+
+def _roofline(prof, prob, precision, clocks, peaks, peak_src, instances=1):
     """Roofline of the kernel with the largest time per step among the ones
-    the library times on its own (nested stage events on the solve stream):
-    the K_nu table, the tensor-core Gram, the eigensolver's QR and Jacobi."""
+    the library times on their own (nested stage events on the solve stream):
+    the K_nu table, the tensor-core Gram, the eigensolver's QR and Jacobi.
+    Every fraction is against the whole GPU's peak of the pipe the kernel is
+    bound by; `instances` problems of the same shape share each launch."""
     n = prob.n[0]
     h = (n + 1) // 2
     ms = min(h, 12 + 4)  # subspace of the first eigenpair pass (12 pairs, 4 extra columns)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_gpu = FP64_TFLOPS_NOMINAL * sm_mhz / 2070.0
-    fp64_sm = fp64_gpu / 152.0
+    fp64_src = ("GPU FP64: nominal 1.25 TFLOP/s at 2070 MHz (152 SMs x 2 FMA/clk x 2 flop; an FMA-chain probe "
+                "measured 1.19), scaled to the sampled SM clock")
     have = {k: prof[k] for k in ("table", "gram_tc", "qr", "jacobi") if k in prof and prof[k][1] > 0}
     if not have:
         return {"kernel": None, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
     top = max(have, key=lambda k: have[k][0])
     t = have[top][0] / have[top][1] * 1e-3  # s per launch
-    out = {"kernel": None, "stage_ms_per_launch": t * 1e3, "traffic": None}
+    if instances > 1 and top in ("qr", "jacobi"):
+        # instances needing more pairs run the stage again on a subset: take the
+        # whole step's stage time against the first pass's work (a lower bound)
+        t = have[top][0] * 1e-3
+    out = {"kernel": None, "stage_ms_per_launch": t * 1e3, "traffic": None, "instances_per_launch": instances}
     if top == "gram_tc":
-        # 128 x 64 blocks of G touching its upper triangle (i 128 < (j + 1) 64)
-        nrt, nct = (h + 127) // 128, (h + 63) // 64
-        nb = sum(max(0, nct - (i * 128) // 64) for i in range(nrt))
-        issued = 21 * 2.0 * 128 * 64 * (h * h) * nb
+        issued = _gram_tc_issued(h) * instances
         ach = issued / t / 1e12
         pk = peaks["bf16_tflops_sustained"]
         out.update(kernel="k_gram_tc (sliced BF16 Gram)", bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s",
@@ -270,23 +282,29 @@ def _roofline(prof, prob, precision, clocks, peaks, peak_src):
     elif top in ("qr", "jacobi"):
         if top == "qr":
             work = 8.0 * h * ms * ms - 8.0 * ms ** 3 / 3.0  # Householder QR plus the explicit Q
-            name = "k_qr_factor64 + k_form_q (FP64, one CTA factorisation)"
+            name = "k_qr_factor64 + k_form_q (FP64 Householder QR of the subspace block)"
         else:
             work = 7.0 * ms ** 3 * JACOBI_SWEEPS  # 7 m^3 flops per sweep (A two-sided, V one-sided)
-            name = "k_jacobi_strided (FP64, one CTA)"
+            name = "k_jacobi_strided (FP64 Jacobi of the Rayleigh-Ritz matrix)"
+        work *= instances
         ach = work / t / 1e12
-        out.update(kernel=name, bound="alu", achieved=ach, peak=fp64_sm, unit="TFLOP/s", frac=ach / fp64_sm,
-                   peak_source="FP64 of the one SM the CTA runs on: nominal 1.25 TFLOP/s / 152 SMs at 2070 MHz, "
-                               "scaled to the sampled SM clock",
+        out.update(kernel=name, bound="alu", achieved=ach, peak=fp64_gpu, unit="TFLOP/s", frac=ach / fp64_gpu,
+                   frac_of_the_sms_used=ach / (fp64_gpu * min(152, instances) / 152.0),
+                   peak_source=fp64_src + "; frac_of_the_sms_used: against the FP64 of the SMs the launch occupies "
+                                          "(one CTA per instance), a diagnosis only",
                    algorithmic_flop_per_launch=work)
     else:
-        work = _knu_flops(prob)
+        work = _knu_flops(prob) * instances
         ach = work / t / 1e12
         out.update(kernel="k_table_b (K_nu per distinct s, FP64)", bound="alu", achieved=ach, peak=fp64_gpu,
-                   unit="TFLOP/s", frac=ach / fp64_gpu,
-                   peak_source="nominal FP64 1.25 TFLOP/s at 2070 MHz scaled to the sampled SM clock",
-                   algorithmic_flop_per_launch=work)
+                   unit="TFLOP/s", frac=ach / fp64_gpu, peak_source=fp64_src, algorithmic_flop_per_launch=work)
     out["per_step_ms"] = {k: v[0] for k, v in have.items()}
+    if "gram_tc" in have and top != "gram_tc":
+        tg = have["gram_tc"][0] / have["gram_tc"][1] * 1e-3
+        issued = _gram_tc_issued(h) * instances
+        out["gram_tc"] = {"achieved": issued / tg / 1e12, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                          "frac": issued / tg / 1e12 / peaks["bf16_tflops_sustained"],
+                          "ms_per_launch": tg * 1e3, "algorithmic_flop_per_launch": issued}
     return out
 
 
@@ -365,7 +383,8 @@ def run_ours(args):
         line = bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, world, peaks,
                            peak_src)
     else:
-        line = bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax)
+        line = bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax, peaks,
+                             peak_src)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -645,9 +664,12 @@ def bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stre
 
     sampler = ClockSampler(local_rank)
     sampler.start()
-    ms, lat, launches, prof, ranks = timed(step, args.steps, args.warmup, profile=True, cleanup=cleanup)
+    ms, lat, launches, _, ranks = timed(step, args.steps, args.warmup, cleanup=cleanup)
     clocks = sampler.stop()
     value = len(probs) * args.steps * world / (ms / 1000.0)
+    # per-stage device times from a separate pass with the library's stage events on
+    kprof = max(2, min(args.steps, 3))
+    _, _, _, prof, _ = timed(step, kprof, 0, profile=True, cleanup=cleanup)
     # accuracy of every instance, outside the timed region
     rs = ctx.batch(probs, precision=precision, stream=stream)
     errs = [r.rel_error(stream=stream) for r in rs]
@@ -671,7 +693,10 @@ def bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stre
         "ranks": {"min": min(ranks), "max": max(ranks), "mean": sum(ranks) / len(ranks)},
         "rel_error": {"max": max(errs), "within_eps_or_capped": ok, "count": len(errs)},
         "fp64_path": fp64, "gpu_launches": launches,
-        "stages_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in prof.items()}, "clocks": clocks,
+        "stages_ms_per_step": {k: v[0] / kprof for k, v in prof.items()},
+        "roofline": _roofline({k: (v[0] / kprof, v[1] / kprof) for k, v in prof.items()},
+                              probs[0], precision, clocks, peaks, peak_src, instances=len(probs)),
+        "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -688,18 +713,22 @@ def bench_sweep(args, torch, binding, workloads, ctx, precision, prec_name, stre
     return line
 
 
-def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax):
+def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, world, allmax, peaks, peak_src):
     rank, local_rank, _ = dist_info()
     stream = workloads.serving_stream()
 
-    def replay(p, reqs):
+    def replay(p, reqs, realtime=True):
+        """Submits the requests at their arrival times (realtime) or all at once
+        (saturated: the queue never runs dry); throughput = requests / time from
+        the first submission to the end of the last request's batch."""
         ctx.serve_start(workers=2)
         t0 = time.perf_counter()
         tickets = []
         for at, q in reqs:
-            d = at - (time.perf_counter() - t0)
-            if d > 0:
-                time.sleep(d)
+            if realtime:
+                d = at - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
             tickets.append((time.perf_counter() - t0, ctx.submit(q, precision=p)))
         lats, ends = [], []
         for ts, t in tickets:
@@ -712,12 +741,19 @@ def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, wo
         span = max(ends)
         return len(reqs) / span, lats, stats
 
+    def summary(v, lats, stats):
+        lm = [1000 * x for x in lats]
+        return {"value": v * world, "latency_ms": {"p50": statistics.median(lm), "p99": _pct(lm, 0.99),
+                                                   "max": max(lm)}, "batches": stats["batches"],
+                "max_batch_seen": stats["max_batch_seen"]}
+
     # warm-up: a few requests of every size
     warm = [(0.0, workloads.problem(0, nu=1.0, ell=0.3, n=n, eps=1e-6, rmax=64)) for n in (64, 128, 256, 384)]
     replay(precision, warm)
     sampler = ClockSampler(local_rank)
     sampler.start()
     value, lats, stats = replay(precision, stream)
+    sat = {prec_name: summary(*replay(precision, stream, realtime=False))}
     clocks = sampler.stop()
     fp64 = None
     if precision != binding.TK_FP64:
@@ -725,6 +761,21 @@ def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, wo
         v64, l64, s64 = replay(binding.TK_FP64, stream)
         fp64 = {"value": v64, "latency_ms": {"p50": 1000 * statistics.median(l64), "p99": 1000 * _pct(l64, 0.99)},
                 "batches": s64["batches"]}
+        sat["fp64"] = summary(*replay(binding.TK_FP64, stream, realtime=False))
+        sat["speedup_over_fp64"] = sat[prec_name]["value"] / sat["fp64"]["value"]
+    sat["note"] = ("the same 2000 requests submitted all at once (closed queue, above capacity): solves/s from the "
+                   "first submission to the last result, latency from submission to the end of the request's batch")
+    # the stream's costliest requests (n = 384) as one profiled tk_batch: the
+    # serving path's dominant kernel and its roofline
+    big = [q for _, q in stream if q.n[0] == 384][:16]
+    ctx.profile(True)
+    for r in ctx.batch(big, precision=precision):
+        r.free()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    roof = _roofline(prof, big[0], precision, clocks, peaks, peak_src, instances=len(big))
+    roof["sample"] = f"one profiled tk_batch of the stream's first {len(big)} n=384 requests"
     lat_ms = [1000 * x for x in lats]
     return {
         "metric": "Matern Tucker-HOSVD serving solves/s with p50/p99 latency", "value": value * world,
@@ -734,7 +785,7 @@ def bench_serving(args, torch, binding, workloads, ctx, precision, prec_name, wo
         "config": {"workload": SERVING, "precision": prec_name, "workers": 2,
                    "l2": "requests of up to 24 MB octant tensors stream through; no flush"},
         "latency_ms": {"p50": statistics.median(lat_ms), "p99": _pct(lat_ms, 0.99), "max": max(lat_ms)},
-        "serve_stats": stats, "fp64_path": fp64, "clocks": clocks,
+        "serve_stats": stats, "fp64_path": fp64, "saturated": sat, "roofline": roof, "clocks": clocks,
     }
 
 

@@ -305,10 +305,12 @@ int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, cons
  * array that every GPU loading this library holds until the process exits;
  * n[a] must lie in [1, 1024] (TK_EINVAL otherwise), which always fits.
  * F (device, n[0] n[1] n[2] FP64) and G (device, n_mode x n_mode FP64) are the
- * caller's; the result equals tk_gram's.  Runs on the current CUDA device and
- * only enqueues on `stream` (no synchronisation).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Calls share the array, which keeps the
+ * caller's; the result equals tk_gram's up to rounding: when tk_gram's K
+ * split would need more partial sums than the array holds, fewer and longer
+ * splits are taken, which changes the summation order.  Runs on the current
+ * CUDA device and only enqueues on `stream` (no synchronisation).  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls share the array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU race. */
 int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, void* stream);
 

@@ -19,7 +19,7 @@ import math
 import numpy as np
 import pytest
 
-from tests._util import U64, near_threshold, principal_sines, separated_prefix
+from tests._util import U64, angle_tol, compare_solution, principal_sines, separated_prefix
 
 pytestmark = pytest.mark.gpu
 
@@ -132,53 +132,8 @@ def test_ttm_core_matches_oracle(ctx, orc, shape, r):
 # ---------------------------------------------------------------------------
 # Whole solve against the oracle
 # ---------------------------------------------------------------------------
-def angle_tol(lam, rp, precision_u):
-    """1e-10, or the Davis-Kahan bound sin(theta) <= |dG| / gap when that is
-    larger: a Gram of unit roundoff u is off by |dG| ~ 10 u lam_1, so the
-    leading vectors are fixed only to 10 u / (smallest relative gap of the first
-    rp eigenvalues) by the matrix itself (the oracle's too).  For the FP64 path
-    this exceeds 1e-10 only for gaps below 1.1e-5 lam_1."""
-    lam = np.asarray(lam)
-    gap = min((lam[i] - lam[i + 1]) / lam[0] for i in range(rp))
-    return max(1e-10, 10 * precision_u / gap)
-
-
 def _compare_solution(orc, wl, res, prob, precision_u=U64):
-    kern, grid = wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc)
-    ref = orc.hosvd(kern, grid, prob.eps, rmax=list(prob.rmax))
-    ranks, flags = res.ranks
-    for a in range(3):
-        if ranks[a] != ref["ranks"][a]:
-            both_capped = ranks[a] == prob.rmax[a] and ref["ranks"][a] == prob.rmax[a]
-            ok = (abs(ranks[a] - ref["ranks"][a]) <= 1
-                  and near_threshold(ref["lam"][a], ref["normF2"], prob.eps, ref["ranks"][a]))
-            assert both_capped or ok or (ref["flags"][a] & 2 and flags[a] & 2), (a, ranks, ref["ranks"])
-    F = orc.tensor(kern, grid)
-    nF = math.sqrt(ref["normF2"])
-    assert abs(res.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
-    U = [res.factor(a) for a in range(3)]
-    B = res.core()
-    for a in range(3):
-        np.testing.assert_allclose(U[a].T @ U[a], np.eye(ranks[a]), atol=1e-13)
-    # core norm
-    if ranks == ref["ranks"]:
-        assert abs(np.linalg.norm(B) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
-        X = orc.reconstruct(B, U, prob.n)
-        Xo = orc.reconstruct(ref["core"], ref["U"], prob.n)
-        tol = max(1e-12, 100 * precision_u / max(prob.eps, 1e-300))
-        assert np.linalg.norm(X - Xo) <= tol * nF
-        for a in range(3):
-            rp = min(separated_prefix(ref["lam"][a][: ranks[a] + 1]), ranks[a])
-            if rp:
-                tol_a = angle_tol(ref["lam"][a], rp, precision_u)
-                assert principal_sines(ref["U"][a][:, :rp], U[a][:, :rp]).max() <= tol_a
-    # error: GPU rel_error (direct subtraction on the device) vs the oracle's on the GPU factors
-    e_gpu = res.rel_error()
-    e_or = orc.rel_error(F, orc.reconstruct(B, U, prob.n))
-    assert abs(e_gpu - e_or) <= 1e-10 * e_or + 1e-15
-    if not any(flags):
-        assert e_gpu <= prob.eps * (1 + 1e-6)
-    return ref, e_gpu
+    return compare_solution(orc, wl, res, prob, precision_u)
 
 
 @pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
@@ -351,25 +306,29 @@ def test_tucker_sliced_ragged_matches_oracle(ctx, orc, wl, case):
 
 
 def test_tucker_bench_workload_full_size(ctx, orc, wl):
-    """The benchmark's n = 256 workload in its launch configuration, both paths, against the oracle."""
+    """The benchmark's n = 256 workload in its launch configuration, both paths,
+    against the oracle.  FP64 path: the small cases' bar (compare_solution:
+    ranks, |F|^2, core norm, |X - X_or| <= max(1e-12, 100 u / eps) |F|,
+    principal angles in all three modes, E of the GPU's factors), plus the
+    eigenvalues to 1e-13 lam_1.  Sliced path: the same with u = 2^-48 and
+    E <= 2 E_oracle."""
     from paper_1711_06874_gb300 import binding
 
     prob = wl.matern_n256(1e-6)
     ref = orc.hosvd(wl.oracle_kernel(prob, orc), wl.oracle_grid(prob, orc), prob.eps, rmax=list(prob.rmax))
-    nF = math.sqrt(ref["normF2"])
     for precision in (binding.TK_FP64, binding.TK_SLICED_BF16):
         res = ctx.tucker(prob, precision=precision)
-        ranks, flags = res.ranks
+        ranks, _ = res.ranks
         assert ranks == ref["ranks"], (precision, ranks, ref["ranks"])
-        assert abs(res.norm2 - ref["normF2"]) <= 1e-13 * ref["normF2"]
-        B = res.core()
-        assert abs(np.linalg.norm(B) - math.sqrt(ref["core_norm2"])) <= 1e-12 * nF
-        U = [res.factor(a) for a in range(3)]
-        rp = min(separated_prefix(ref["lam"][0][: ranks[0] + 1]), ranks[0])
         u = U64 if precision == binding.TK_FP64 else U_SLICED
-        assert principal_sines(ref["U"][0][:, :rp], U[0][:, :rp]).max() <= angle_tol(ref["lam"][0], rp, u)
-        e = res.rel_error()
+        _, e = compare_solution(orc, wl, res, prob, precision_u=u, ref=ref)
         assert e <= prob.eps and e <= 2 * ref["rel_error"], (precision, e, ref["rel_error"])
-        lam = res.eigenvalues(0)
-        k = min(len(lam), ranks[0] + 2)
-        np.testing.assert_allclose(lam[:k], ref["lam"][0][:k], rtol=0, atol=1e-13 * ref["lam"][0][0])
+        if precision == binding.TK_FP64:
+            # both FP64 routes take the factors from a Gram of rounding ~u lam_1:
+            # E agrees to second order in the subspace error
+            assert abs(e - ref["rel_error"]) <= 1e-2 * ref["rel_error"], (e, ref["rel_error"])
+        for a in range(3):
+            lam = res.eigenvalues(a)
+            k = min(len(lam), ranks[a] + 2)
+            np.testing.assert_allclose(lam[:k], ref["lam"][a][:k], rtol=0, atol=1e-13 * ref["lam"][a][0])
+        res.free()

@@ -1,7 +1,10 @@
 """Serving loop (tk_serve_start / tk_submit / tk_poll) on the GPU.
 
-  * every result of a concurrent mix is bitwise the one tk_tucker returns for
-    that request alone, and requests were in fact batched together;
+  * every result of a concurrent mix is checked against the FP64 oracle's
+    HOSVD of that request (ranks, |F|^2, core norm, reconstruction, principal
+    angles, E; the small cases' tolerances) and is bitwise the one tk_tucker
+    returns for that request alone, and requests were in fact batched
+    together; a second mix includes n = 128 requests;
   * a short Poisson stream replayed in real time completes with positive
     latencies;
   * argument and state errors come back as status codes.
@@ -10,6 +13,8 @@ import time
 
 import numpy as np
 import pytest
+
+from tests._util import U64, compare_solution
 
 pytestmark = pytest.mark.gpu
 
@@ -34,11 +39,14 @@ def wl():
     return workloads
 
 
-def _mix(wl, count=40, seed=5):
+U_SLICED = 2.0 ** -48
+
+
+def _mix(wl, count=40, seed=5, sizes=(32, 48, 64)):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
-        n = int(rng.choice([32, 48, 64]))
+        n = int(rng.choice(sizes))
         nu = float(rng.uniform(0.3, 2.5))
         ell = float(np.exp(rng.uniform(np.log(0.05), 0.0)))
         eps = float(rng.choice([1e-4, 1e-6, 1e-8]))
@@ -47,11 +55,13 @@ def _mix(wl, count=40, seed=5):
 
 
 @pytest.mark.parametrize("precision_name", ["TK_SLICED_BF16", "TK_FP64"])
-def test_serve_mix_equals_alone(ctx, wl, precision_name):
+@pytest.mark.parametrize("mix", ["small", "with_n128"])
+def test_serve_mix_matches_oracle_and_alone(ctx, orc, wl, precision_name, mix):
     from paper_1711_06874_gb300 import binding
 
     precision = getattr(binding, precision_name)
-    probs = _mix(wl)
+    u = U64 if precision == binding.TK_FP64 else U_SLICED
+    probs = _mix(wl) if mix == "small" else _mix(wl, count=12, seed=11, sizes=(64, 128))
     ctx.serve_start(workers=2, max_batch=64)
     tickets = [ctx.submit(p, precision=precision) for p in probs]
     got = []
@@ -65,12 +75,18 @@ def test_serve_mix_equals_alone(ctx, wl, precision_name):
     assert stats["max_batch_seen"] > 1 and stats["batches"] < len(probs)
     for p, (res, lat) in zip(probs, got):
         assert lat > 0.0
+        ref, e = compare_solution(orc, wl, res, p, precision_u=u)
+        if precision != binding.TK_FP64:
+            # the sliced Gram's E against the oracle's (unless flagged below its precision)
+            assert e <= 2 * ref["rel_error"] or any(res.ranks[1]), (p, e, ref["rel_error"])
         alone = ctx.tucker(p, precision=precision)
         assert res.ranks == alone.ranks
         assert res.norm2 == alone.norm2
         assert np.array_equal(res.core(), alone.core())
         for a in range(3):
             assert np.array_equal(res.factor(a), alone.factor(a))
+        alone.free()
+        res.free()
 
 
 def test_serve_poisson_stream_small(ctx, wl):

@@ -135,4 +135,8 @@ def test_multigrid_bench_workload_full_size(ctx, orc, wl):
     by about 1e-13 lambda_1 here, so the FP64 Gram's error (10 u lambda_1)
     turns it by up to 10 u lambda_1 / gap, which moves E^2 by the square of
     that angle times the gap: a few parts in 1e6 of E, not 1e-6."""
-    _check(ctx, orc, wl, wl.matern_n256(1e-6), 2, 1, e_rtol=1e-4)
+    prob = wl.matern_n256(1e-6)
+    res, mo = _check(ctx, orc, wl, prob, 2, 1, e_rtol=1e-4)
+    e = res.rel_error()
+    print(f"multigrid n=256: E {e:.10e} oracle {mo['rel_error']:.10e} "
+          f"relative deviation {abs(e - mo['rel_error']) / mo['rel_error']:.3e}")

@@ -7,7 +7,10 @@ pointers).  tk_gram_noalloc serves them: it keeps its split-K partial sums in
 a fixed device array inside the library.  This test calls it through the
 C-ABI twice in a row, on different inputs, and checks each result against
 tk_gram (precision TK_FP64) within the Gram tolerance of the parity tests,
-1e-13 max|G|.  It then rejects an out-of-range size.  The file's name makes
+1e-13 max|G|.  The 256^3 tensor is large enough that the default K split's
+partial sums would not fit the fixed array, so the entry point takes fewer,
+longer splits there (its summation order then differs from tk_gram's).  It
+then rejects an out-of-range size.  The file's name makes
 pytest collect it last.
 """
 import ctypes
@@ -30,8 +33,9 @@ def test_noalloc_gram_matches_tk_gram_on_two_calls_in_a_row():
     ctx = binding.Context(0)
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(2024)
-    # two different shapes back to back; the second must not see the first's partial sums
-    for shape in [(70, 45, 33), (130, 9, 64)]:
+    # different shapes back to back; none may see an earlier call's partial sums.
+    # (256, 256, 256) takes the longer-split branch in every mode.
+    for shape in [(70, 45, 33), (130, 9, 64), (256, 256, 256), (40, 20, 30)]:
         F = torch.from_numpy(rng.random(shape)).cuda()
         n = (ctypes.c_int32 * 3)(*shape)
         for mode in range(3):
