@@ -58,12 +58,20 @@ typedef enum { TK_MATERN = 0, TK_SLATER_P = 1, TK_GAUSSIAN = 2, TK_MATERN_SD = 3
  *  TK_VERTEX       x_i = -b_a + i 2 b_a / (n_a - 1)   (Sec. 3.7, Eq. (grid_points)) */
 typedef enum { TK_CELL_CENTRED = 0, TK_VERTEX = 1 } tk_grid_kind;
 
-/* Arithmetic of the two contractions (Gram and core).  The eigensolve and the
- * rank decision are FP64 in every mode.
+/* Arithmetic of the Gram G_k = F_(k) F_(k)^T (Sec. 3.2) and of the core.  The
+ * eigensolve and the rank decision are FP64 in every mode.
  *  TK_FP64        FP64 on the CUDA cores (the plain path).
  *  TK_SLICED_BF16 Gram as exact products of 8-bit BF16 slices on the tcgen05
- *                 tensor cores, FP32 chunk sums promoted to FP64 (FP64-class). */
-typedef enum { TK_FP64 = 0, TK_SLICED_BF16 = 1 } tk_precision;
+ *                 tensor cores, FP32 chunk sums promoted to FP64 (FP64-class).
+ *  TK_BF16X3      Gram on the tcgen05 tensor cores from a two-term BF16 split
+ *                 of each (FP32-rounded) entry, x ~ hi + lo, with the three
+ *                 products hi hi + hi lo + lo hi summed in FP32 (about 2^-16
+ *                 of each product).  Core by the FP64 TTM chain.
+ *  TK_TF32X3      the same with a two-term TF32 split (kind::tf32, about 2^-21).
+ * The two split variants have FP32-class Grams: their eigenvectors, and E, are
+ * resolved only to about the square root of that accuracy, and the rank rule
+ * flags (TK_EPS_UNREACHABLE_AT_PRECISION) an eps below it. */
+typedef enum { TK_FP64 = 0, TK_SLICED_BF16 = 1, TK_BF16X3 = 2, TK_TF32X3 = 3 } tk_precision;
 
 /* Result flags, per mode. */
 enum {
@@ -109,7 +117,13 @@ typedef struct {
                                  independent sampling of F that runs on a side
                                  stream while the eigenpairs are computed; read it
                                  with tk_result_rel_error */
-  int32_t reserved[2];        /* must be zero */
+  int32_t fused_eval;         /* 1 (tk_default_opts): on the sliced path of a cubic
+                                 isotropic grid, sample F and cut its BF16 slices
+                                 in one kernel, so the octant tensor is never
+                                 stored; 0: sample the FP64 octant tensor into
+                                 device memory first, then slice it (the
+                                 materialised path, kept for comparison) */
+  int32_t reserved[1];        /* must be zero */
 } tk_opts;
 
 typedef struct tk_ctx tk_ctx;
@@ -124,8 +138,8 @@ const char* tk_version(void);
 int tk_create(tk_ctx** ctx, int device);
 /* Frees the context and its workspace; results created on it must be freed first. */
 void tk_destroy(tk_ctx* ctx);
-/* Default options: eps 1e-6, rmax 32, rfix 0, TK_SLICED_BF16, shortcut and
- * fold on. */
+/* Default options: eps 1e-6, rmax 32, rfix 0, TK_SLICED_BF16, shortcut, fold
+ * and fused_eval on. */
 void tk_default_opts(tk_opts* opts);
 
 /* ---------------------------------------------------------------------------
@@ -294,6 +308,36 @@ int tk_als(tk_ctx* ctx, const double* F, const int32_t n[3], double* U1, double*
  * context's workspace.  Synchronous with respect to `stream`. */
 int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts, int levels,
                  int sweeps, tk_result** out, void* stream);
+
+/* Canonical-to-Tucker (Sec. 3.4): the Tucker approximation of a tensor given
+ * in the canonical format of Eq. (Can_Contr),
+ *   A(i1, i2, i3) = sum_{k<R} c_k U1[i1][k] U2[i2][k] U3[i3][k],
+ * without forming or unfolding A.  c (device, R) are the weights and U_l
+ * (device, n_l x R row-major) the side matrices (unit columns are the usual
+ * normalisation; the rule below holds for any).  The initial factors come
+ * from the reduced HOSVD: Z_l spans the r_l leading left singular vectors of
+ * U_l alone (computed as the leading eigenvectors of U_l U_l^T in FP64), r_l
+ * being the smallest r whose discarded singular values satisfy
+ * (sum_{k>=r} s_k^2)^(1/2) <= eps |A| / (3 |c|) (so that the RHOSVD bound
+ * |A - A_r| <= |c| sum_l (sum_{k>=r_l} s_{l,k}^2)^(1/2) gives E <= eps), capped
+ * at rmax_l (TK_RANK_CAPPED) and replaced by rfix_l where rfix_l > 0.  Then
+ * `sweeps` Tucker-ALS sweeps (modes 1, 2, 3 in order), each mode's single-hole
+ * unfolding U_l diag(c) (W_m (.) W_q)^T formed from the side matrices
+ * (W_j = Z_j^T U_j, (.) the Khatri-Rao product); Z_l becomes its r_l leading
+ * left singular vectors (eigenvectors of its FP64 Gram, signs as tk_tucker's).
+ * The core B = sum_k c_k W1[:, k] o W2[:, k] o W3[:, k].
+ * rmax, rfix: host arrays of 3 or NULL (rmax: min(n_l, R, 96); rfix: 0),
+ * 1 <= rmax <= 96, 0 <= rfix <= 96.  Needs 1 <= R <= 4096, 1 <= n_l <= 1024,
+ * eps >= 0, 0 <= sweeps <= 64 and the ranks a multilinear rank (r_l <= r_m r_q);
+ * TK_EINVAL otherwise.  On TK_OK *out owns device copies of the Z_l (n_l x r_l)
+ * and B (r1 x r2 x r3), read as any result; tk_norm2 gives |A|^2 (from the
+ * side matrices' Grams) and tk_eigenvalues the r_l squared singular values of
+ * mode l's last update.  core_norm2 (host, 3 sweeps doubles, may be NULL)
+ * receives |B|^2 after each mode update.  tk_rel_error does not apply (A is
+ * not a sampled covariance).  Synchronous with respect to `stream`. */
+int tk_c2t(tk_ctx* ctx, int R, const double* c, const double* U1, const double* U2, const double* U3,
+           const int32_t n[3], double eps, const int32_t rmax[3], const int32_t rfix[3], int sweeps,
+           tk_result** out, double* core_norm2, void* stream);
 
 /* Allocation-free variant of tk_gram with precision TK_FP64 (no counterpart
  * in the paper).  Some callers cannot allocate device memory: code embedded in

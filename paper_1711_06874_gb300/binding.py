@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtucker_matern.so")
 TK_OK, TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_ETIMEOUT, TK_EBUSY, TK_ENOTFOUND = range(7)
 TK_MATERN, TK_SLATER_P, TK_GAUSSIAN, TK_MATERN_SD = 0, 1, 2, 3
 TK_CELL_CENTRED, TK_VERTEX = 0, 1
-TK_FP64, TK_SLICED_BF16 = 0, 1
+TK_FP64, TK_SLICED_BF16, TK_BF16X3, TK_TF32X3 = 0, 1, 2, 3
 SLICED_AVAILABLE = True  # tensor-core Gram from exact BF16 slices is built
 TK_RANK_CAPPED, TK_EPS_UNREACHABLE_AT_PRECISION, TK_SOLVED_AGAIN_IN_FP64 = 1, 2, 4
 
@@ -41,7 +41,8 @@ class Grid(_c.Structure):
 
 class Opts(_c.Structure):
     _fields_ = [("eps", _dbl), ("rmax", _i32 * 3), ("rfix", _i32 * 3), ("precision", _i32),
-                ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("with_error", _i32), ("reserved", _i32 * 2)]
+                ("isotropic_shortcut", _i32), ("reflect_fold", _i32), ("with_error", _i32), ("fused_eval", _i32),
+                ("reserved", _i32 * 1)]
 
 
 class ServeOpts(_c.Structure):
@@ -84,6 +85,8 @@ SIGNATURES = {
                                 _c.POINTER(_vp), _vp]),
     "tk_als": (_c.c_int, [_vp, _vp, _c.POINTER(_i32), _vp, _vp, _vp, _c.POINTER(_i32), _c.c_int, _vp,
                           _c.POINTER(_dbl), _vp]),
+    "tk_c2t": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp, _c.POINTER(_i32), _dbl, _c.POINTER(_i32),
+                          _c.POINTER(_i32), _c.c_int, _c.POINTER(_vp), _c.POINTER(_dbl), _vp]),
     "tk_default_serve_opts": (None, [_c.POINTER(ServeOpts)]),
     "tk_serve_start": (_c.c_int, [_vp, _c.POINTER(ServeOpts)]),
     "tk_serve_stop": (_c.c_int, [_vp]),
@@ -148,7 +151,7 @@ _DEFAULT_OPTS = None
 
 
 def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True, fold=True,
-              with_error=False) -> Opts:
+              with_error=False, fused_eval=True) -> Opts:
     global _DEFAULT_OPTS
     if _DEFAULT_OPTS is None:
         d = Opts()
@@ -162,6 +165,7 @@ def make_opts(prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortc
     o.isotropic_shortcut = 1 if shortcut else 0
     o.reflect_fold = 1 if fold else 0
     o.with_error = 1 if with_error else 0
+    o.fused_eval = 1 if fused_eval else 0
     return o
 
 
@@ -197,15 +201,16 @@ class Context:
         self.device = device
         self._args = {}  # (problem, options) -> the C structs, built once
 
-    def _structs(self, prob, precision, rfix, shortcut, fold, with_error):
+    def _structs(self, prob, precision, rfix, shortcut, fold, with_error, fused_eval=True):
         """The C structs of one solve, built once per distinct (problem, options):
         building them costs more than a small solve's launches."""
-        key = (prob, precision, tuple(rfix), bool(shortcut), bool(fold), bool(with_error))
+        key = (prob, precision, tuple(rfix), bool(shortcut), bool(fold), bool(with_error), bool(fused_eval))
         hit = self._args.get(key)
         if hit is None:
             if len(self._args) >= 256:
                 self._args.clear()
-            hit = (make_kernel(prob), make_grid(prob), make_opts(prob, precision, rfix, shortcut, fold, with_error))
+            hit = (make_kernel(prob), make_grid(prob),
+                   make_opts(prob, precision, rfix, shortcut, fold, with_error, fused_eval))
             self._args[key] = hit
         return hit
 
@@ -222,8 +227,8 @@ class Context:
 
     # ---- whole solve -------------------------------------------------------
     def tucker(self, prob: workloads.Problem, precision=TK_FP64, rfix=(0, 0, 0), shortcut=True,
-               fold=True, with_error=False, stream=None) -> "Result":
-        k, g, o = self._structs(prob, precision, rfix, shortcut, fold, with_error)
+               fold=True, with_error=False, stream=None, fused_eval=True) -> "Result":
+        k, g, o = self._structs(prob, precision, rfix, shortcut, fold, with_error, fused_eval)
         out = _vp()
         _check(self.lib.tk_tucker(self.ptr, _c.byref(k), _c.byref(g), _c.byref(o), _c.byref(out),
                                   _stream_ptr(stream)), self.ptr)
@@ -331,6 +336,20 @@ class Context:
         _check(self.lib.tk_als(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(), U[2].data_ptr(), r,
                                int(sweeps), B.data_ptr(), hist, _stream_ptr(stream)), self.ptr)
         return np.array(hist[: 3 * sweeps], dtype=np.float64)
+
+    def c2t(self, c, U, eps: float, sweeps: int, rmax=None, rfix=None, stream=None):
+        """Canonical-to-Tucker (tk_c2t) of the device CP tensor (c: R, U[l]:
+        n_l x R).  Returns (Result, core norm^2 after each mode update)."""
+        R = int(c.shape[0])
+        n = (_i32 * 3)(*(int(u.shape[0]) for u in U))
+        rm = (_i32 * 3)(*rmax) if rmax is not None else None
+        rf = (_i32 * 3)(*rfix) if rfix is not None else None
+        hist = (_dbl * max(3 * sweeps, 1))()
+        out = _vp()
+        _check(self.lib.tk_c2t(self.ptr, R, c.data_ptr(), U[0].data_ptr(), U[1].data_ptr(), U[2].data_ptr(), n,
+                               float(eps), rm, rf, int(sweeps), _c.byref(out), hist, _stream_ptr(stream)), self.ptr)
+        prob = workloads.problem(n=tuple(int(v) for v in n), eps=eps)
+        return Result(self, out, prob), np.array(hist[: 3 * sweeps], dtype=np.float64)
 
 
 @dataclass

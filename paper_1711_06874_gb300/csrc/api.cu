@@ -183,11 +183,11 @@ void check_opts(const tk_opts* o) {
     if (o->rmax[a] < 1 || o->rmax[a] > kMaxRank) fail(TK_EINVAL, "rmax must be in [1, 88]");
     if (o->rfix[a] < 0 || o->rfix[a] > kMaxRank) fail(TK_EINVAL, "rfix must be in [0, 88]");
   }
-  if (o->precision != TK_FP64 && o->precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
+  if (o->precision < TK_FP64 || o->precision > TK_TF32X3) fail(TK_EINVAL, "unknown precision");
   if (o->reflect_fold != 0 && o->reflect_fold != 1) fail(TK_EINVAL, "reflect_fold must be 0 or 1");
   if (o->with_error != 0 && o->with_error != 1) fail(TK_EINVAL, "with_error must be 0 or 1");
-  for (int i = 0; i < 2; ++i)
-    if (o->reserved[i] != 0) fail(TK_EINVAL, "reserved fields must be zero");
+  if (o->fused_eval != 0 && o->fused_eval != 1) fail(TK_EINVAL, "fused_eval must be 0 or 1");
+  if (o->reserved[0] != 0) fail(TK_EINVAL, "reserved fields must be zero");
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -277,6 +277,7 @@ void tk_default_opts(tk_opts* o) {
   o->precision = TK_SLICED_BF16;
   o->isotropic_shortcut = 1;
   o->reflect_fold = 1;
+  o->fused_eval = 1;
 }
 
 int tk_create(tk_ctx** out, int device) {
@@ -349,8 +350,9 @@ tk_result* tucker_full(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid
     const bool sliced = (o.precision == TK_SLICED_BF16);
     size_t gram_scr = 0, eig_scr = 0;
     for (int a = 0; a < nmodes; ++a) {
-      gram_scr = std::max(gram_scr, sliced ? (gram_sliced_scratch_bytes(n, a) + 7) / 8
-                                           : gram_f64_scratch_doubles(n, a));
+      gram_scr = std::max(gram_scr, sliced                     ? (gram_sliced_scratch_bytes(n, a) + 7) / 8
+                                    : is_split3(o.precision) ? (gram_split3_scratch_bytes(n, a, 1, o.precision) + 7) / 8
+                                                             : gram_f64_scratch_doubles(n, a));
       eig_scr = std::max(eig_scr, sym_eig_scratch_doubles(n[a], m[a]));
     }
     int rcap[3];
@@ -399,6 +401,8 @@ tk_result* tucker_full(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid
       pf.begin(TK_STAGE_GRAM, s);
       if (sliced)
         gram_sliced_bf16(F, n, a, G[a], gscr, ranks_dev + 16, s);
+      else if (is_split3(o.precision))
+        gram_split3_batch(F, n, a, 1, G[a], gscr, ranks_dev + 16, s, nullptr, o.precision);
       else
         gram_f64(F, n, a, G[a], gscr, s);
       pf.end(s);
@@ -784,10 +788,21 @@ int tk_gram(tk_ctx* ctx, const double* F, const int32_t n[3], int mode, int prec
     int nn[3] = {n[0], n[1], n[2]};
     for (int a = 0; a < 3; ++a)
       if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
-    if (precision != TK_FP64 && precision != TK_SLICED_BF16) fail(TK_EINVAL, "unknown precision");
+    if (precision < TK_FP64 || precision > TK_TF32X3) fail(TK_EINVAL, "unknown precision");
     set_device(ctx);
     cudaStream_t s = as_stream(stream);
-    if (precision == TK_FP64) {
+    if (is_split3(precision)) {
+      const size_t b = gram_split3_scratch_bytes(nn, mode, 1, precision);
+      ctx->ws.reserve(carve_bytes<char>(b) + carve_bytes<int>(4), s);
+      char* scr = ctx->ws.take<char>(b);
+      int* err = ctx->ws.take<int>(4);
+      TK_CUDA(cudaMemsetAsync(err, 0, sizeof(int) * 4, s));
+      gram_split3_batch(F, nn, mode, 1, G, scr, err, s, nullptr, precision);
+      int h = 0;
+      TK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      if (h != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+    } else if (precision == TK_FP64) {
       ctx->ws.reserve(carve_bytes<double>(gram_f64_scratch_doubles(nn, mode)), s);
       double* scr = ctx->ws.take<double>(gram_f64_scratch_doubles(nn, mode));
       gram_f64(F, nn, mode, G, scr, s);
@@ -999,6 +1014,34 @@ int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, cons
     if (res) tk_result_free(res);
     return rc;
   }
+  *out = res;
+  return TK_OK;
+}
+
+int tk_c2t(tk_ctx* ctx, int R, const double* c, const double* U1, const double* U2, const double* U3,
+           const int32_t n[3], double eps, const int32_t rmax[3], const int32_t rfix[3], int sweeps,
+           tk_result** out, double* core_norm2, void* stream) {
+  if (!ctx || !out || !c || !U1 || !U2 || !U3 || !n) return TK_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  tk_result* res = nullptr;
+  int rc = guard(ctx, [&] {
+    if (R < 1 || R > 4096) fail(TK_EINVAL, "need 1 <= R <= 4096");
+    int nn[3], rm[3], rf[3];
+    for (int a = 0; a < 3; ++a) {
+      nn[a] = n[a];
+      if (nn[a] < 1 || nn[a] > kMaxN) fail(TK_EINVAL, "n must be in [1, 1024]");
+      rm[a] = rmax ? rmax[a] : std::min(std::min(nn[a], R), 96);
+      rf[a] = rfix ? rfix[a] : 0;
+      if (rm[a] < 1 || rm[a] > 96) fail(TK_EINVAL, "need 1 <= rmax <= 96");
+      if (rf[a] < 0 || rf[a] > 96) fail(TK_EINVAL, "need 0 <= rfix <= 96");
+    }
+    if (!(eps >= 0.0) || !std::isfinite(eps)) fail(TK_EINVAL, "eps must be >= 0");
+    if (sweeps < 0 || sweeps > 64) fail(TK_EINVAL, "need 0 <= sweeps <= 64");
+    set_device(ctx);
+    const double* const U[3] = {U1, U2, U3};
+    res = c2t_solve(ctx, R, c, U, nn, eps, rm, rf, sweeps, core_norm2, as_stream(stream));
+  });
+  if (rc != TK_OK) return rc;
   *out = res;
   return TK_OK;
 }

@@ -121,7 +121,7 @@ bool fold_applicable(const tk_grid& g, const tk_opts& o) {
 
 static auto key_tuple(const BucketKey& k) {
   return std::make_tuple(k.n[0], k.n[1], k.n[2], k.b[0], k.b[1], k.b[2], k.kind, k.precision, k.nmodes, k.tab,
-                         k.m[0], k.m[1], k.m[2], k.err);
+                         k.m[0], k.m[1], k.m[2], k.err, k.fz);
 }
 bool BucketKey::operator<(const BucketKey& o) const { return key_tuple(*this) < key_tuple(o); }
 bool BucketKey::operator==(const BucketKey& o) const { return key_tuple(*this) == key_tuple(o); }
@@ -138,6 +138,7 @@ BucketKey bucket_key(const SolveReq& r) {
   k.nmodes = shortcut_ok(r.k, r.g, r.o) ? 1 : 3;
   k.tab = table_applicable(r.k, r.g) ? 1 : 0;
   k.err = r.o.with_error ? 1 : 0;
+  k.fz = r.o.fused_eval ? 1 : 0;
   return k;
 }
 
@@ -266,7 +267,9 @@ size_t bucket_bytes_per_instance(const BucketKey& k) {
     const int m = k.m[a];
     b += 8 * (3ull * h[a] * h[a] + 2ull * h[a] * m);           // G, gathered G, V
     b += 8 * sym_eig_batch_scratch_doubles(h[a], m, 1);
-    b += (k.precision == TK_SLICED_BF16) ? gram_sliced_scratch_bytes(h, a, 1) : 8 * gram_f64_scratch_doubles(h, a, 1);
+    b += (k.precision == TK_SLICED_BF16) ? gram_sliced_scratch_bytes(h, a, 1)
+         : is_split3(k.precision)         ? gram_split3_scratch_bytes(h, a, 1, k.precision)
+                                          : 8 * gram_f64_scratch_doubles(h, a, 1);
   }
   const int R = roundup(std::max(k.m[0], std::max(k.m[1], k.m[2])), 4);
   b += 8 * ((size_t)h[0] * h[1] * R + (size_t)R * h[1] * R + (size_t)R * R * R + 3ull * h[0] * R);  // TTM
@@ -294,7 +297,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   const long long Q = tab ? table_entries(n[0]) : 0;
   // sampling fused with the mode-1 slicing: Fh is never stored (the Gram and
   // the first TTM read the slices)
-  const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0;
+  const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0 && key.fz;
   const bool with_err = key.err != 0;
   // the error of a fused solve is taken against the Gram's slices in
   // float-float arithmetic (FP32 range: every sigma2 within 2^-60 .. 2^60);
@@ -305,8 +308,9 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   const size_t nparts = std::max<size_t>(eval_octant_parts(g), (size_t)h[0]);
   size_t gram_bytes = 0, eig_doubles = 0;
   for (int a = 0; a < nmodes; ++a) {
-    gram_bytes = std::max(gram_bytes, sliced ? gram_sliced_scratch_bytes(h, a, B)
-                                             : 8 * gram_f64_scratch_doubles(h, a, B));
+    gram_bytes = std::max(gram_bytes, sliced                       ? gram_sliced_scratch_bytes(h, a, B)
+                                      : is_split3(key.precision) ? gram_split3_scratch_bytes(h, a, B, key.precision)
+                                                                 : 8 * gram_f64_scratch_doubles(h, a, B));
     eig_doubles = std::max(eig_doubles, sym_eig_batch_scratch_doubles(h[a], m[a], B));
   }
   int hmax = 0;
@@ -441,6 +445,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
         gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf, NormParts{part, h[0], normF2});
       else if (sliced)
         gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf);
+      else if (is_split3(key.precision))
+        gram_split3_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf, key.precision);
       else
         gram_f64_batch(Fh, h, a, B, G[a], (double*)gscr, s);
       if (pf) pf->end(s);
@@ -852,7 +858,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       const std::vector<double> gk = {(double)n[0], (double)n[1], (double)n[2], key.b[0], key.b[1], key.b[2],
                                       (double)key.kind, (double)key.precision, (double)nmodes, (double)key.tab,
                                       (double)m[0], (double)m[1], (double)m[2], (double)key.err, (double)B,
-                                      (double)err_ff};
+                                      (double)err_ff, (double)fused};
       // a bounded cache: a server meeting many plans starts afresh
       if (graphs->graphs.size() >= kMaxGraphs && graphs->graphs.find(gk) == graphs->graphs.end())
         graphs->release();

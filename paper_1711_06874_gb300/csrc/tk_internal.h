@@ -267,7 +267,29 @@ size_t ttm_sliced_scratch_bytes(int h3, int R, int Bg);
 void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int Bg, int Btot, const double* Up, int R,
                       double* T1, void* scratch, int* err, cudaStream_t s);
 // unit roundoff of the Gram of each precision (for the eps-unreachable flag)
-inline double gram_u_eff(int precision) { return precision == TK_FP64 ? 0x1p-53 : 0x1p-48; }
+inline double gram_u_eff(int precision) {
+  switch (precision) {
+    case TK_FP64: return 0x1p-53;
+    case TK_BF16X3: return 0x1p-16;
+    case TK_TF32X3: return 0x1p-21;
+    default: return 0x1p-48;
+  }
+}
+// (b) Gram from a two-term BF16 or TF32 split and three products with FP32
+// accumulation on the tensor cores (TK_BF16X3, TK_TF32X3), B instances of F
+// ([b][n1 n2 n3] FP64), G: [b][n_mode][n_mode].
+bool is_split3(int precision);
+size_t gram_split3_scratch_bytes(const int n[3], int mode, int B, int precision);
+void gram_split3_batch(const double* F, const int n[3], int mode, int B, double* G, void* scratch, int* err,
+                       cudaStream_t s, Profiler* pf, int precision);
+
+// Canonical-to-Tucker (Sec. 3.4): the reduced HOSVD of the canonical tensor
+// (c, U_1, U_2, U_3) (device; U_l n_l x R row-major) and `sweeps` Tucker-ALS
+// sweeps in the canonical format; returns a new result (factors, core, |A|^2,
+// the last update's eigenvalues).  hist_out (host, 3 sweeps, may be NULL)
+// receives |B|^2 after each mode update.  Synchronises s.
+tk_result* c2t_solve(tk_ctx* ctx, int R, const double* c, const double* const U[3], const int n[3], double eps,
+                     const int rmax[3], const int rfix[3], int sweeps, double* hist_out, cudaStream_t s);
 
 // General strided batched FP64 GEMM: C[z](i,j) = sum_k A[z](i,k) B[z](k,j).
 // Batch entry z = b1 batch2 + b2 has operand offsets b1 s_b + b2 s_b2 (A's b1
@@ -419,7 +441,7 @@ bool fold_applicable(const tk_grid& g, const tk_opts& o);
 struct BucketKey {
   int n[3];
   double b[3];
-  int kind, precision, nmodes, tab, m[3], err;
+  int kind, precision, nmodes, tab, m[3], err, fz;  // fz: fused sampling and slicing allowed
   bool operator<(const BucketKey& o) const;
   bool operator==(const BucketKey& o) const;
 };
