@@ -157,12 +157,18 @@ void tk_default_opts(tk_opts* opts);
 int tk_tucker(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, const tk_opts* opts,
               tk_result** out, void* stream);
 
-/* Ranks and flags of a result (host arrays of 3). */
+/* Ranks and flags of a result (host arrays of 3): the Tucker rank
+ * (r1, r2, r3) of Sec. 3.1. */
 int tk_ranks(const tk_result* res, int32_t r[3], uint32_t flags[3]);
-/* Factor U_mode (n_mode x r_mode, row-major, orthonormal columns) into dst.
- * on_device: 1 = dst is device memory, 0 = host memory. */
+/* Factor U_mode of the Tucker format (Sec. 3.1: the orthonormal side matrix
+ * V^(l) of mode l; Sec. 3.2: the leading left singular vectors of the
+ * unfolding), n_mode x r_mode, row-major, orthonormal columns, into dst.
+ * on_device: 1 = dst is device memory, 0 = host memory.  TK_EINVAL for a
+ * mode outside 0..2. */
 int tk_factor(const tk_result* res, int mode, double* dst, int on_device, void* stream);
-/* Core B (r1 x r2 x r3, row-major) into dst. */
+/* Core B of the Tucker format (Sec. 3.1, the core tensor beta of the
+ * decomposition; Sec. 3.2, B = F x_1 U_1^T x_2 U_2^T x_3 U_3^T), r1 x r2 x r3
+ * row-major, into dst (on_device as tk_factor). */
 int tk_core(const tk_result* res, double* dst, int on_device, void* stream);
 /* The whole decomposition of Sec. 3.2 (U_1, U_2, U_3 and B, layouts as
  * tk_factor and tk_core) into host memory with one device-to-host copy and
@@ -180,7 +186,9 @@ int tk_norm2(const tk_result* res, double* normF2);
 /* E computed during the solve (opts.with_error = 1); TK_EINVAL otherwise. */
 int tk_result_rel_error(const tk_result* res, double* rel_error);
 
-/* X = B x_1 U_1 x_2 U_2 x_3 U_3 into dst (device, n1 n2 n3 FP64). */
+/* The Tucker tensor of Sec. 3.1, X = B x_1 U_1 x_2 U_2 x_3 U_3 (the
+ * rank-(r1, r2, r3) approximation whose error Eq. (FNorm) measures), into dst
+ * (device, n1 n2 n3 FP64, row-major, caller-owned). */
 int tk_reconstruct(tk_ctx* ctx, const tk_result* res, double* dst, void* stream);
 /* Eq. (FNorm): |F - X|_F / |F|_F by direct subtraction with compensated FP64
  * sums, where F is resampled from (kernel, grid) and X is never stored.
@@ -357,6 +365,20 @@ int tk_c2t(tk_ctx* ctx, int R, const double* c, const double* U1, const double* 
  * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls share the array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU race. */
 int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, void* stream);
+
+/* Autotuning (no counterpart in the paper) of the K split of the sliced
+ * tensor-core Gram.  Its result does not depend on the split (exact integer
+ * chunk sums), so the split is chosen for speed alone: with on = 1, the first
+ * Gram of each (SM count, rows, K, instances) shape, outside stream capture,
+ * also times 2, 4 and 8 times as many 256-deep chunks per CTA as the default
+ * plan (which aims at one wave of CTAs) with CUDA events on the solve's
+ * stream, which it synchronises, and keeps the fastest for every later call.
+ * The choices are process-wide.  cache_path (may be NULL: keep the current
+ * file and choices; "": none, and forget the choices) names a JSON file of
+ * {"<shape key>": chunks per CTA} whose choices replace the ones held now and
+ * which is rewritten after every new choice.  *entries (may be NULL) receives
+ * the number of choices held.  on = 0 stops tuning and uses the default plan. */
+int tk_tune(tk_ctx* ctx, int on, const char* cache_path, int* entries);
 
 /* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): per-stage device time and the

@@ -87,6 +87,7 @@ SIGNATURES = {
                           _c.POINTER(_dbl), _vp]),
     "tk_c2t": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp, _c.POINTER(_i32), _dbl, _c.POINTER(_i32),
                           _c.POINTER(_i32), _c.c_int, _c.POINTER(_vp), _c.POINTER(_dbl), _vp]),
+    "tk_tune": (_c.c_int, [_vp, _c.c_int, _c.c_char_p, _c.POINTER(_c.c_int)]),
     "tk_default_serve_opts": (None, [_c.POINTER(ServeOpts)]),
     "tk_serve_start": (_c.c_int, [_vp, _c.POINTER(ServeOpts)]),
     "tk_serve_stop": (_c.c_int, [_vp]),
@@ -336,6 +337,13 @@ class Context:
         _check(self.lib.tk_als(self.ptr, F.data_ptr(), n, U[0].data_ptr(), U[1].data_ptr(), U[2].data_ptr(), r,
                                int(sweeps), B.data_ptr(), hist, _stream_ptr(stream)), self.ptr)
         return np.array(hist[: 3 * sweeps], dtype=np.float64)
+
+    def tune(self, on: bool = True, cache_path=None) -> int:
+        """Autotuning of the sliced Gram's K split (tk_tune); returns the choices held."""
+        k = _c.c_int(0)
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(self.lib.tk_tune(self.ptr, 1 if on else 0, path, _c.byref(k)), self.ptr)
+        return int(k.value)
 
     def c2t(self, c, U, eps: float, sweeps: int, rmax=None, rfix=None, stream=None):
         """Canonical-to-Tucker (tk_c2t) of the device CP tensor (c: R, U[l]:

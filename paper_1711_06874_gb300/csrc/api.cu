@@ -1046,6 +1046,14 @@ int tk_c2t(tk_ctx* ctx, int R, const double* c, const double* U1, const double* 
   return TK_OK;
 }
 
+int tk_tune(tk_ctx* ctx, int on, const char* cache_path, int* entries) {
+  if (!ctx || (on != 0 && on != 1)) return TK_EINVAL;
+  return guard(ctx, [&] {
+    gram_tune_config(on != 0, cache_path);
+    if (entries) *entries = gram_tune_entries();
+  });
+}
+
 int tk_profile_enable(tk_ctx* ctx, int on) {
   if (!ctx) return TK_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);

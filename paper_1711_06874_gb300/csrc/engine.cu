@@ -838,7 +838,27 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   // checked after the final synchronisation; when it fails the second phase
   // runs again the ordinary way.  Every result of the second phase is
   // independent of the padded rank R, so both ways give the same bits.
+  // Larger batches speculate too once the last batch of the same plan held
+  // the assumption (a parameter sweep repeated, a steady serving mix), and
+  // stop when one fails: the failed speculation costs a second phase.
+  const std::vector<double> plan_key = {(double)n[0], (double)n[1], (double)n[2], key.b[0], key.b[1], key.b[2],
+                                        (double)key.kind, (double)key.precision, (double)nmodes, (double)key.tab,
+                                        (double)m[0], (double)m[1], (double)m[2], (double)key.err,
+                                        (double)err_ff, (double)fused};
+  auto phase_a_covers = [&]() {
+    for (int a = 0; a < nmodes; ++a)
+      for (int b = 0; b < B; ++b) {
+        const int rf = req[b].o.rfix[a];
+        const int needed = rf > 0 ? std::min(rf, m[a]) : hA[4 * ((size_t)a * B + b) + 2];
+        if (needed > mA[a]) return false;
+      }
+    return true;
+  };
   bool spec = B <= kSpecMaxBatch;
+  if (!spec && graphs) {
+    const auto it = graphs->spec_ok.find(plan_key);
+    spec = it != graphs->spec_ok.end() && it->second;
+  }
   for (int b = 0; b < B && spec; ++b)
     for (int a = 0; a < nmodes; ++a)
       if (req[b].o.rfix[a] > mA[a]) spec = false;
@@ -918,13 +938,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     if (ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
     if (*herrp != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core TTM ran out");
     // the assumption: no instance wants more pairs than phase A computed
-    bool holds = true;
-    for (int a = 0; a < nmodes && holds; ++a)
-      for (int b = 0; b < B && holds; ++b) {
-        const int rf = req[b].o.rfix[a];
-        const int needed = rf > 0 ? std::min(rf, m[a]) : hA[4 * ((size_t)a * B + b) + 2];
-        if (needed > mA[a]) holds = false;
-      }
+    const bool holds = phase_a_covers();
+    if (graphs) graphs->spec_ok[plan_key] = holds;
     if (holds) {
       // the ranks, flags and eigenvalues the speculation did not know
       for (int a = 0; a < nmodes; ++a) {
@@ -954,6 +969,7 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
       TK_CUDA(cudaMemcpyAsync(ih, ints, (size_t)(ranks_end - (const char*)ints), cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaStreamSynchronize(s));
       if (ih[0] != 0) fail(TK_ETIMEOUT, "a bounded wait in the tensor-core Gram ran out");
+      if (graphs) graphs->spec_ok[plan_key] = phase_a_covers();
     }
     plan_second(false);
     launch_second(false);

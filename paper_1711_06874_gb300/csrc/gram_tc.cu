@@ -41,8 +41,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "slices.cuh"
 #include "tc_common.cuh"
@@ -459,6 +463,78 @@ TcPlan tc_plan(const int n[3], int mode, int sm_count, int B = 1) {
   return p;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuning of the K split.  The Gram does not depend on how K is split
+// (exact integer chunk sums), so the split is free to pick for speed alone.
+// The default plan aims at one wave of CTAs; when tuning is on, the first
+// launch of a (SMs, rows, K, instances) shape also times 2, 4 and 8 times as
+// many chunks per CTA (fewer CTAs, longer pipelines; never more partial sums
+// than the default, so the scratch sizing holds) with CUDA events and keeps
+// the fastest.  Choices live in a process-wide table, optionally read from and
+// written to a JSON file ({"<key>": chunks per split, ...}).
+// ---------------------------------------------------------------------------
+struct TuneTable {
+  std::mutex mu;
+  bool on = false;
+  std::string path;
+  std::map<std::string, int> cps;  // chunks per split
+};
+TuneTable& tune_table() {
+  static TuneTable t;
+  return t;
+}
+
+std::string tune_key(int sm_count, const TcPlan& p, int B) {
+  return "sm" + std::to_string(sm_count) + "/gram_tc/rows" + std::to_string(p.nrows) + "/K" + std::to_string(p.K) +
+         "/B" + std::to_string(B);
+}
+
+void tune_save_locked(const TuneTable& t) {
+  if (t.path.empty()) return;
+  const std::string tmp = t.path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : t.cps)
+    std::fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < t.cps.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), t.path.c_str());
+}
+
+// Entries of the form "key": integer (the format tune_save_locked writes).
+void tune_load_locked(TuneTable& t) {
+  if (t.path.empty()) return;
+  FILE* f = std::fopen(t.path.c_str(), "r");
+  if (!f) return;
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  size_t pos = 0;
+  while ((pos = text.find('"', pos)) != std::string::npos) {
+    const size_t end = text.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const std::string key = text.substr(pos + 1, end - pos - 1);
+    const size_t colon = text.find(':', end);
+    if (colon == std::string::npos) break;
+    const int v = std::atoi(text.c_str() + colon + 1);
+    if (v > 0) t.cps[key] = v;
+    pos = text.find_first_of(",}", colon);
+    if (pos == std::string::npos) break;
+  }
+}
+
+TcPlan with_chunks_per_split(TcPlan p, int cps) {
+  const int chunks = (p.kb_total + kChunkBlocks - 1) / kChunkBlocks;
+  cps = std::max(1, std::min(cps, std::min(chunks, 256)));
+  p.kb_per_split = cps * kChunkBlocks;
+  p.nsplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;
+  return p;
+}
+
 // Slices of B instances, [b][s][row][Kp] bf16: dims (Kp, nrows, 6, B).
 CUtensorMap slice_map(PFN_cuTensorMapEncodeTiled_v12000 enc, void* S, long long Kp, int nrows, int B,
                       int box_rows) {
@@ -485,26 +561,85 @@ void run_tc_gram(const TcPlan& p, int B, __nv_bfloat16* S, const int* rowexp, lo
   once_per_device((const void*)&k_gram_tc, [] {
     TK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   });
-  TcArgs a{p.nrows, p.nrt, p.nct, p.nblocks, p.nsplit, p.kb_per_split, p.kb_total, P, err};
+  TcPlan q = p;
+  {
+    TuneTable& t = tune_table();
+    std::lock_guard<std::mutex> lock(t.mu);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (t.on && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+      const std::string key = tune_key(152, p, B);
+      auto it = t.cps.find(key);
+      if (it == t.cps.end()) {
+        const int c0 = p.kb_per_split / kChunkBlocks;
+        int best = c0;
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        TK_CUDA(cudaEventCreate(&e0));
+        TK_CUDA(cudaEventCreate(&e1));
+        for (int f = 1; f <= 8; f *= 2) {
+          const TcPlan c = with_chunks_per_split(p, c0 * f);
+          if (f > 1 && c.nsplit == with_chunks_per_split(p, c0 * f / 2).nsplit) break;
+          TcArgs ca{c.nrows, c.nrt, c.nct, c.nblocks, c.nsplit, c.kb_per_split, c.kb_total, P, err};
+          float ms = 0.0f;
+          for (int rep = 0; rep < 4; ++rep) {  // one warm-up, three timed
+            TK_CUDA(cudaEventRecord(e0, s));
+            launch_pdl("k_gram_tc", k_gram_tc, dim3(c.nblocks, c.nsplit, B), dim3(kThreads), kSmemBytes, s, mapA,
+                       mapB, ca);
+            TK_CUDA(cudaEventRecord(e1, s));
+            TK_CUDA(cudaEventSynchronize(e1));
+            float t_ms = 0.0f;
+            TK_CUDA(cudaEventElapsedTime(&t_ms, e0, e1));
+            if (rep > 0) ms += t_ms;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = c0 * f;
+          }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        it = t.cps.emplace(key, best).first;
+        tune_save_locked(t);
+      }
+      q = with_chunks_per_split(p, it->second);
+      if (q.nsplit > p.nsplit) q = p;  // a stored choice never needs more partials than reserved
+    }
+  }
+  TcArgs a{q.nrows, q.nrt, q.nct, q.nblocks, q.nsplit, q.kb_per_split, q.kb_total, P, err};
   if (pf) pf->begin(TK_STAGE_GRAM_TC, s);
-  launch_pdl("k_gram_tc", k_gram_tc, dim3(p.nblocks, p.nsplit, B), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
+  launch_pdl("k_gram_tc", k_gram_tc, dim3(q.nblocks, q.nsplit, B), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
   if (pf) pf->end(s);
-  const long long total = (long long)p.nrows * p.nrows * B;
+  const long long total = (long long)q.nrows * q.nrows * B;
   const int extra = norm.part != nullptr ? B : 0;
-  if (p.nsplit >= 8) {
+  if (q.nsplit >= 8) {
     const int nred = (int)std::min<long long>((8 * total + 255) / 256, 8192);
-    launch_pdl("k_tc_reduce", k_tc_reduce<8>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, p.nsplit, p.nct,
-               p.nblocks, p.nrows, B, rowexp, G,
-                                                           nred, norm);
+    launch_pdl("k_tc_reduce", k_tc_reduce<8>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, q.nsplit, q.nct,
+               q.nblocks, q.nrows, B, rowexp, G, nred, norm);
   } else {
     const int nred = (int)std::min<long long>((total + 255) / 256, 8192);
-    launch_pdl("k_tc_reduce", k_tc_reduce<1>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, p.nsplit, p.nct,
-               p.nblocks, p.nrows, B, rowexp, G,
-                                                           nred, norm);
+    launch_pdl("k_tc_reduce", k_tc_reduce<1>, dim3((unsigned)(nred + extra)), dim3(256), 0, s, P, q.nsplit, q.nct,
+               q.nblocks, q.nrows, B, rowexp, G, nred, norm);
   }
 }
 
 }  // namespace
+
+void gram_tune_config(bool on, const char* path) {
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lock(t.mu);
+  t.on = on;
+  if (path != nullptr) {  // a new cache file: its choices replace the ones held
+    t.path = path;
+    t.cps.clear();
+    tune_load_locked(t);
+  }
+}
+
+int gram_tune_entries() {
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lock(t.mu);
+  return (int)t.cps.size();
+}
 
 size_t gram_sliced_scratch_bytes(const int n[3], int mode, int B) {
   const TcPlan p = tc_plan(n, mode, 152, B);

@@ -103,6 +103,10 @@ struct SolveGraph {
 };
 struct GraphCache {
   std::map<std::vector<double>, SolveGraph> graphs;
+  // per bucket plan (any batch size): whether the last batch needed no more
+  // eigenpairs than the first pass computes (batches above the small-batch
+  // size then run their second phase speculatively)
+  std::map<std::vector<double>, bool> spec_ok;
   void release();
   ~GraphCache() { release(); }
 };
@@ -211,6 +215,11 @@ struct SliceView {
   long long Kp;
 };
 SliceView gram_slices_view(void* scratch, const int n[3], int mode, int B);
+// Autotuning of the sliced Gram's K split (process-wide): on/off, and the
+// JSON cache file to read now and to write after each new choice (NULL: keep
+// the current file, "" : none).  gram_tune_entries: choices held.
+void gram_tune_config(bool on, const char* path);
+int gram_tune_entries();
 // |F|^2 partials of an instance summed by one CTA of 256 threads (strided
 // Neumaier sums, then a fixed tree): out = sum of p[0 .. nparts).
 struct NormParts {

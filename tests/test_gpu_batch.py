@@ -334,3 +334,44 @@ def test_sliced_error_above_eps_is_solved_again_in_fp64(ctx, wl):
     one = ctx.tucker(sd, precision=binding.TK_SLICED_BF16, with_error=True)
     assert all(f & binding.TK_SOLVED_AGAIN_IN_FP64 for f in one.ranks[1])
     assert one.solve_error <= sd.eps
+
+
+def test_large_batch_speculation_and_replay_bitwise(ctx, wl):
+    """Batches above the small-batch size speculate once a batch of the same
+    plan needed no more eigenpairs than the first pass computes, and are then
+    captured and replayed as one CUDA graph: every repetition gives the bits
+    of the first (plain) run and of each instance alone.  A batch of the same
+    plan whose instances need more pairs (eps = 1e-10) makes the speculation
+    fail; it is redone the ordinary way and still matches each instance alone."""
+    from paper_1711_06874_gb300 import binding
+
+    rng = np.random.default_rng(77)
+    probs = [wl.problem(0, nu=float(rng.uniform(0.8, 2.5)), ell=float(rng.uniform(0.3, 0.8)), n=48, eps=1e-5,
+                        rmax=24) for _ in range(16)]
+    for precision in (binding.TK_SLICED_BF16, binding.TK_FP64):
+        args = binding.BatchArgs(probs, precision=precision)
+        runs = [ctx.batch(args) for _ in range(4)]  # plain, speculative plain, captured, replayed
+        assert max(r.ranks[0][0] for r in runs[0]) <= 12  # the first pass covers every instance
+        for rep in runs[1:]:
+            for r0, r in zip(runs[0], rep):
+                assert r.ranks == r0.ranks and r.norm2 == r0.norm2
+                assert _same(r.core(), r0.core())
+                for a in range(3):
+                    assert _same(r.factor(a), r0.factor(a))
+        for p, r in zip(probs[:4], runs[3][:4]):
+            alone = ctx.tucker(p, precision=precision)
+            assert _same(r.core(), alone.core())
+            assert _same(r.factor(0), alone.factor(0))
+        # the same plan with instances that need more than the first pass's pairs
+        tight = [wl.problem(0, nu=0.5 + 0.02 * i, ell=0.12, n=48, eps=1e-10, rmax=24) for i in range(16)]
+        rt = ctx.batch(tight, precision=precision)
+        assert max(r.ranks[0][0] for r in rt) > 12
+        for p, r in zip(tight[:4], rt[:4]):
+            alone = ctx.tucker(p, precision=precision)
+            assert r.ranks == alone.ranks
+            assert _same(r.core(), alone.core())
+            assert _same(r.factor(0), alone.factor(0))
+        # and the plan speculates again only after a batch that held
+        again = ctx.batch(args)
+        for r0, r in zip(runs[0], again):
+            assert _same(r.core(), r0.core())
