@@ -14,10 +14,15 @@ one Tucker-ALS sweep (Sec. 3.2) of the default workload's tensor, from its
 HOSVD factors, through tk_als.  --workload multigrid: one multigrid Tucker
 solve (Sec. 3.2) of the default workload, the HOSVD on the 64^3 grid and one
 Tucker-ALS sweep on each of the 64^3, 128^3 and 256^3 grids, through
-tk_multigrid.
+tk_multigrid.  --workload n512: the n = 512 solve (nu = 2.5, ell = 0.1), fused
+sampling and slicing against the materialised octant tensor.  --workload
+slater64: the n = 64 Slater solve (nu = 1/2, ell = 0.3, eps = 1e-8, FP64).
+--workload c2t: canonical-to-Tucker (Sec. 3.4) of the sinc CP of 1/|x| on the
+256^3 grid through tk_c2t.  --eps overrides the eps of the single-solve
+workloads.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload single|sweep|serving|spectral|als|multigrid]
+                    [--workload single|sweep|serving|spectral|als|multigrid|n512|slater64|c2t] [--eps E]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs independent
 replicas of the workload (the path has no exchange step) and rank 0 prints.
@@ -33,6 +38,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -55,6 +62,16 @@ MG_METRIC = "Multigrid Tucker solves/s (HOSVD on 64^3, one ALS sweep per grid) o
 MG_WORKLOAD = ("Matern nu=1.2 ell=0.2 sigma2=1, n=256^3 cell-centred grid on [-1,1]^3, eps=1e-6 ranks from the "
                "64^3 HOSVD, levels=2 (64 -> 128 -> 256), 1 sweep per grid, F sampled on the device per grid")
 MG_LEVELS, MG_SWEEPS = 2, 1
+N512_METRIC = "Matern Tucker-HOSVD solves/s, n=512 (nu=2.5, ell=0.1, eps=1e-6); p50/p99 latency"
+N512_WORKLOAD = ("Matern nu=2.5 ell=0.1 sigma2=1, n=512^3 cell-centred grid on [-1,1]^3, eps={eps:g}, rank cap 64; "
+                 "one solve (sample, Gram, eigenpairs, ranks, core, rel_error) per step")
+C1_METRIC = "Slater (Matern nu=1/2) Tucker-HOSVD solves/s, n=64, eps=1e-8, FP64; p50/p99 latency"
+C1_WORKLOAD = ("Matern nu=0.5 (Slater) ell=0.3 sigma2=1, n=64^3 cell-centred grid on [-1,1]^3, eps={eps:g}, "
+               "rank cap 20; one solve (sample, Gram, eigenpairs, ranks, core, rel_error) per step")
+C2T_METRIC = "Canonical-to-Tucker (Sec. 3.4) solves/s: RHOSVD + 1 ALS sweep of the sinc CP of 1/|x|, FP64"
+C2T_WORKLOAD = ("sinc CP of the Newton kernel 1/|x| (M=64, R=129 terms, h_M = 3 log(M)/M), collocated on the "
+                "256^3 cell-centred grid on [-1,1]^3, eps=1e-6, one tk_c2t call (RHOSVD and 1 sweep) per step, "
+                "CP input resident on the device")
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 at 2070 MHz (nominal; the pipe the eigensolver and TTMs run on)
 
 
@@ -67,7 +84,8 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "sliced", "bf16x3", "tf32x3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral", "als",
-                                                                       "multigrid"])
+                                                                       "multigrid", "n512", "slater64", "c2t"])
+    p.add_argument("--eps", type=float, default=None, help="eps of the single-solve workloads (default: theirs)")
     return p.parse_args()
 
 
@@ -327,6 +345,8 @@ def run_ours(args):
     torch.cuda.set_device(local_rank)
     ctx = binding.Context(local_rank)
     prec_name = args.precision
+    if prec_name == "auto" and args.workload == "slater64":
+        prec_name = "fp64"  # the FP64 configuration of the small Slater case
     if prec_name == "auto" and args.workload == "spectral":
         # the sliced Gram flags eps = 1e-6 as below its accuracy on this sharply
         # peaked function and its E lands above 1e-6: the FP64 Gram meets it
@@ -378,12 +398,16 @@ def run_ours(args):
         return allmax(sum(lat)), lat, launches, prof, out
 
     peaks, peak_src = load_peaks()
-    # the sliced Gram's K split picked by timing (its result does not depend on it)
+    # the sliced Gram's K split picked by timing (its result does not depend on
+    # it); not while serving, where every new batch size would pause to time
     tune_path = os.path.join(tempfile.gettempdir(), f"tk_tune_{os.getpid()}.json")
-    ctx.tune(True, tune_path)
-    if args.workload in ("single", "spectral"):
+    if args.workload != "serving":
+        ctx.tune(True, tune_path)
+    if args.workload in ("single", "spectral", "n512", "slater64"):
         line = bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier,
                             allmax, world, peaks, peak_src)
+    elif args.workload == "c2t":
+        line = bench_c2t(args, torch, binding, ctx, stream, timed, barrier, allmax, world, peaks)
     elif args.workload == "multigrid":
         line = bench_multigrid(args, torch, binding, workloads, ctx, stream, timed, barrier, allmax, world, peaks)
     elif args.workload == "als":
@@ -401,7 +425,7 @@ def run_ours(args):
         os.unlink(tune_path)
     line.setdefault("config", {})["autotune"] = {
         "what": "K split of the sliced tensor-core Gram chosen by timing (the Gram does not depend on it)",
-        "chunks_of_256_per_cta": chosen}
+        "chunks_of_256_per_cta": chosen} if args.workload != "serving" else "off (default splits while serving)"
     ctx.tune(False, "")
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -415,14 +439,25 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
                  peaks, peak_src):
     rank, local_rank, _ = dist_info()
     spectral = args.workload == "spectral"
+    wk = args.workload
     # the spectral density workload: the paper's nu = 0.4 with its smaller alpha
-    prob = (workloads.problem(workloads.MATERN_SD, nu=0.4, p=0.1, n=256, eps=1e-6, rmax=64) if spectral
-            else workloads.matern_n256(1e-6))
+    if spectral:
+        prob = workloads.problem(workloads.MATERN_SD, nu=0.4, p=0.1, n=256, eps=args.eps or 1e-6, rmax=64)
+        metric, workload = SPECTRAL_METRIC, SPECTRAL_WORKLOAD
+    elif wk == "n512":
+        prob = workloads.matern_n512(args.eps or 1e-6)
+        metric, workload = N512_METRIC, N512_WORKLOAD.format(eps=prob.eps)
+    elif wk == "slater64":
+        prob = workloads.slater_n64(args.eps or 1e-8)
+        metric, workload = C1_METRIC, C1_WORKLOAD.format(eps=prob.eps)
+    else:
+        prob = workloads.matern_n256(args.eps or 1e-6)
+        metric, workload = METRIC, WORKLOAD.replace("eps=1e-6", f"eps={prob.eps:g}")
 
-    def solve(p):
+    def solve(p, fused=True):
         # E from a second, independent sampling of F that the library runs on a
         # side stream while the eigenpairs are computed
-        res = ctx.tucker(prob, precision=p, with_error=True, stream=stream)
+        res = ctx.tucker(prob, precision=p, with_error=True, stream=stream, fused_eval=fused)
         err = res.solve_error
         ranks = res.ranks
         res.free()
@@ -448,10 +483,19 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     else:
         fp64 = {"value": value, "ms_per_step": ms / args.steps, "rel_error": err, "note": "this line is the FP64 path"}
 
+    # n = 512: the sampling and slicing fused (the default) against the octant
+    # tensor materialised first, the same solve otherwise
+    materialised = None
+    if wk == "n512" and precision == binding.TK_SLICED_BF16:
+        kmt = max(3, min(args.steps, 10))
+        msm, latm, _, _, (errm, _) = timed(lambda: solve(precision, fused=False), kmt, 1)
+        materialised = {"value": kmt * world / (msm / 1000.0), "ms_per_step": msm / kmt, "rel_error": errm,
+                        "latency_ms": {"p50": statistics.median(latm), "p99": _pct(latm, 0.99)},
+                        "note": "fused_eval=0: FP64 octant tensor sampled into HBM, then sliced"}
     # the two FP32-class split variants on the same workload: reported with
     # their measured E, outside the metric when E misses eps
     variants = {}
-    if not spectral:
+    if not spectral and wk != "slater64":
         for vname, vp in (("bf16x3", binding.TK_BF16X3), ("tf32x3", binding.TK_TF32X3)):
             if vp == precision:
                 continue
@@ -492,23 +536,123 @@ def bench_single(args, torch, binding, workloads, ctx, precision, prec_name, str
     else:
         roof = _roofline(per_step, prob, precision, clocks, peaks, peak_src)
     line = {
-        "metric": SPECTRAL_METRIC if spectral else METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "metric": metric, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": _dtype(binding, precision),
         "data": "synthetic",
-        "config": {"workload": SPECTRAL_WORKLOAD if spectral else WORKLOAD, "precision": prec_name,
+        "config": {"workload": workload, "precision": prec_name,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (512 MB written on the solve stream, outside the step events)",
                    "isotropic_shortcut": True, "reflect_fold": True},
         "rel_error": err, "ranks": ranks, "flags": flags,
         "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
-        "fp64_path": fp64, "precision_variants": variants, "e2e": e2e, "gpu_launches": launches,
+        "fp64_path": fp64, "precision_variants": variants, "materialised": materialised, "e2e": e2e,
+        "gpu_launches": launches,
         "stages_ms_per_step": stage_ms,
         "roofline": roof, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob)
+        if wk == "n512":
+            # the whole oracle solve at n = 512 takes minutes: the same problem at
+            # n = 256, scaled by (512 / 256)^4, the growth of its Gram
+            small = workloads.problem(prob.kind, nu=prob.nu, ell=prob.ell[0], n=256, eps=prob.eps, rmax=64)
+            cb = cpu_baseline(small)
+            cb["value"] /= 16.0
+            cb["sample"] = ("extrapolated: " + cb["sample"].replace("bench workload", "n=256 solve of the same "
+                            "parameters") + ", rate divided by (512/256)^4 = 16 (the Gram's n^4 cost)")
+            line["cpu_baseline"] = cb
+        else:
+            line["cpu_baseline"] = cpu_baseline(prob)
+    return line
+
+
+def _c2t_flops(n, R, r, sweeps):
+    """Algorithmic FP64 work of one tk_c2t call: the side matrices' Grams for
+    |A|^2 (R x R) and for the RHOSVD (n x n), then per sweep and mode the
+    single-hole unfolding M (n x r_m r_q), its Gram and W = Z^T U; the core."""
+    f = sum(2.0 * n[l] * R * R + 2.0 * n[l] * n[l] * R + 2.0 * r[l] * n[l] * R for l in range(3))
+    for _ in range(sweeps):
+        for l in range(3):
+            m, q = [a for a in range(3) if a != l]
+            rmq = r[m] * r[q]
+            f += 2.0 * n[l] * R * rmq + 2.0 * n[l] * n[l] * rmq + 2.0 * r[l] * n[l] * R + 2.0 * rmq * R
+    return f + 2.0 * R * r[0] * r[1] * r[2]
+
+
+def bench_c2t(args, torch, binding, ctx, stream, timed, barrier, allmax, world, peaks):
+    rank, local_rank, _ = dist_info()
+    from paper_1711_06874_gb300 import cp_inputs
+
+    n, M, eps, sweeps = 256, 64, args.eps or 1e-6, 1
+    c, U = cp_inputs.newton_sinc_cp(n, M)
+    R = c.size
+    cd = torch.from_numpy(c).cuda()
+    Ud = [torch.from_numpy(np.ascontiguousarray(u)).cuda() for u in U]
+
+    def step():
+        res, hist = ctx.c2t(cd, Ud, eps, sweeps, stream=stream)
+        return res
+
+    def done(res):
+        r = res.ranks[0]
+        res.free()
+        return r
+
+    sampler = ClockSampler(local_rank)
+    for _ in range(args.warmup):
+        done(step())
+    sampler.start()
+    ms, lat, launches, _, ranks = timed(step, args.steps, 0, cleanup=done)
+    clocks = sampler.stop()
+    value = whole_job_rate(args.steps, world, ms / 1000.0)
+    ranks = list(ranks)
+    # end to end: the CP input in from pinned host memory, factors and core out
+    ch = torch.from_numpy(c).pin_memory()
+    Uh = [torch.from_numpy(np.ascontiguousarray(u)).pin_memory() for u in U]
+    h2d = ch.numel() * 8 + sum(u.numel() * 8 for u in Uh)
+    d2h = 8 * (ranks[0] * ranks[1] * ranks[2] + sum(n * r for r in ranks))
+    torch.cuda.synchronize()
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            cd.copy_(ch, non_blocking=True)
+            for a in range(3):
+                Ud[a].copy_(Uh[a], non_blocking=True)
+        res, _ = ctx.c2t(cd, Ud, eps, sweeps, stream=stream)
+        res.factors_and_core(stream=stream)
+        res.free()
+    te = allmax(time.perf_counter() - te)
+    e2e = {"value": args.steps * world / te, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    flop = _c2t_flops((n, n, n), R, ranks, sweeps)
+    step_ms = ms / args.steps
+    sm = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = FP64_TFLOPS_NOMINAL * sm / 2070.0
+    achieved = flop / (step_ms * 1e-3) / 1e12
+    roof = {"kernel": "tk_c2t (whole call: FP64 Grams, single-hole unfoldings, subspace eigensolves)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "algorithmic_flop_per_launch": flop,
+            "peak_source": "GPU FP64: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled SM clock"}
+    line = {
+        "metric": C2T_METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": C2T_WORKLOAD.replace("eps=1e-6", f"eps={eps:g}"), "precision": "fp64",
+                   "parallelism": f"replicas x{world}", "l2": "CP input 0.8 MB resident; no flush", "ranks": ranks},
+        "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99)},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t = time.perf_counter()
+        oracle.c2t(c, U, eps, sweeps)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"one whole oracle c2t of the bench input ({dt:.2f} s, "
+                                                            f"LAPACK SVDs through numpy)"}
     return line
 
 

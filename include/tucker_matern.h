@@ -369,7 +369,8 @@ int tk_gram_noalloc(const double* F, const int32_t n[3], int mode, double* G, vo
 /* Autotuning (no counterpart in the paper) of the K split of the sliced
  * tensor-core Gram.  Its result does not depend on the split (exact integer
  * chunk sums), so the split is chosen for speed alone: with on = 1, the first
- * Gram of each (SM count, rows, K, instances) shape, outside stream capture,
+ * Gram of each (SM count, rows, K, instances rounded up to a power of two)
+ * shape, outside stream capture,
  * also times 2, 4 and 8 times as many 256-deep chunks per CTA as the default
  * plan (which aims at one wave of CTAs) with CUDA events on the solve's
  * stream, which it synchronises, and keeps the fastest for every later call.

@@ -188,43 +188,52 @@ tk_result* c2t_solve(tk_ctx* ctx, int R, const double* c, const double* const U[
   TK_CUDA(cudaMemcpyAsync(ch.data(), c, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&normA2, small, sizeof(double), cudaMemcpyDeviceToHost, s));
 
-  // ---- reduced HOSVD: leading eigenpairs of U_l U_l^T, rank rule on the host
-  std::vector<double> lh[3];
-  double tr[3];
-  for (int l = 0; l < 3; ++l) {
-    gram_of_rows(U[l], n[l], R, G, s);
-    sym_eig_batch(G, n[l], meig[l], 1, lam + l * 96, V + (size_t)l * nmax * 96, trace + l, escr, s);
-    lh[l].resize(mcap[l]);
-  }
-  for (int l = 0; l < 3; ++l)
-    TK_CUDA(cudaMemcpyAsync(lh[l].data(), lam + l * 96, sizeof(double) * mcap[l], cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaMemcpyAsync(tr, trace, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  // ---- reduced HOSVD: leading eigenpairs of U_l U_l^T, rank rule on the host.
+  // Above 96 rows the subspace solver runs with 16 pairs, then 48, then the
+  // cap, until the rule finds its rank among the pairs computed.
   TK_CUDA(cudaStreamSynchronize(s));
   double cn2 = 0.0;
   for (int k = 0; k < R; ++k) cn2 += ch[k] * ch[k];
   const double cn = std::sqrt(cn2);
   const double tol = cn > 0.0 ? eps * std::sqrt(std::max(normA2, 0.0)) / (3.0 * cn) : 0.0;
+  std::vector<double> lh[3];
   int r[3];
   unsigned flags[3] = {0, 0, 0};
   for (int l = 0; l < 3; ++l) {
     const int full = std::min(n[l], R);
-    const double total = tr[l];
+    const int need_fix = (rfix_in && rfix_in[l] > 0) ? std::min(rfix_in[l], full) : 0;
+    gram_of_rows(U[l], n[l], R, G, s);
     int q = 0;
-    // smallest q >= 1 with (sum_{k>=q} s_k^2)^(1/2) <= tol, the tail taken as
-    // trace - sum_{k<q} s_k^2 (q = full keeps everything)
-    for (int cand = 1; cand <= mcap[l]; ++cand) {
-      if (cand == full || std::sqrt(std::max(0.0, total - host_sum(lh[l].data(), 0, cand))) <= tol) {
-        q = cand;
-        break;
+    const int rounds[3] = {16, 48, 96};
+    for (int ri = 0; ri < 3; ++ri) {
+      int mr = n[l] <= 96 ? meig[l] : std::min(mcap[l], std::max(rounds[ri], need_fix));
+      if (ri > 0 && n[l] > 96 && mr <= meig[l]) continue;  // this round adds no pairs
+      meig[l] = mr;
+      sym_eig_batch(G, n[l], mr, 1, lam + l * 96, V + (size_t)l * nmax * 96, trace + l, escr, s);
+      const int mh = std::min(mr, mcap[l]);
+      lh[l].assign(mh, 0.0);
+      double total = 0.0;
+      TK_CUDA(cudaMemcpyAsync(lh[l].data(), lam + l * 96, sizeof(double) * mh, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaMemcpyAsync(&total, trace + l, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      // smallest q >= 1 with (sum_{k>=q} s_k^2)^(1/2) <= tol, the tail taken as
+      // trace - sum_{k<q} s_k^2 (q = full keeps everything)
+      q = 0;
+      for (int cand = 1; cand <= mh; ++cand) {
+        if (cand == full || std::sqrt(std::max(0.0, total - host_sum(lh[l].data(), 0, cand))) <= tol) {
+          q = cand;
+          break;
+        }
       }
+      if (q > 0 || mh >= mcap[l] || n[l] <= 96) break;
     }
     if (q == 0) q = full;  // the rule wants more pairs than the cap allows
     if (q > rcap[l]) {
       flags[l] |= TK_RANK_CAPPED;
       q = rcap[l];
     }
-    if (rfix_in && rfix_in[l] > 0) q = std::min(rfix_in[l], full);
-    r[l] = std::min(q, mcap[l]);
+    if (need_fix > 0) q = need_fix;
+    r[l] = std::min(q, std::min(meig[l], mcap[l]));
   }
   for (int l = 0; l < 3; ++l)
     if ((long long)r[l] > (long long)r[(l + 1) % 3] * r[(l + 2) % 3])

@@ -484,9 +484,12 @@ TuneTable& tune_table() {
   return t;
 }
 
+// Batch sizes share a choice within powers of two.
 std::string tune_key(int sm_count, const TcPlan& p, int B) {
+  int bb = 1;
+  while (bb < B) bb <<= 1;
   return "sm" + std::to_string(sm_count) + "/gram_tc/rows" + std::to_string(p.nrows) + "/K" + std::to_string(p.K) +
-         "/B" + std::to_string(B);
+         "/B" + std::to_string(bb);
 }
 
 void tune_save_locked(const TuneTable& t) {

@@ -39,7 +39,7 @@ def ctx():
 
 
 def _cp():
-    from tests import cp_inputs
+    from paper_1711_06874_gb300 import cp_inputs
 
     return cp_inputs
 

@@ -660,7 +660,7 @@ def test_multigrid_without_levels_is_hosvd_then_als(orc):
 
 
 def _cp():
-    from tests import cp_inputs
+    from paper_1711_06874_gb300 import cp_inputs
 
     return cp_inputs
 
