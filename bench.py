@@ -83,6 +83,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "sliced", "bf16x3", "tf32x3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="default K splits (for profiling runs)")
     p.add_argument("--workload", default="single", choices=["single", "sweep", "serving", "spectral", "als",
                                                                        "multigrid", "n512", "slater64", "c2t"])
     p.add_argument("--eps", type=float, default=None, help="eps of the single-solve workloads (default: theirs)")
@@ -401,7 +402,8 @@ def run_ours(args):
     # the sliced Gram's K split picked by timing (its result does not depend on
     # it); not while serving, where every new batch size would pause to time
     tune_path = os.path.join(tempfile.gettempdir(), f"tk_tune_{os.getpid()}.json")
-    if args.workload != "serving":
+    tuning = args.workload != "serving" and not args.no_tune
+    if tuning:
         ctx.tune(True, tune_path)
     if args.workload in ("single", "spectral", "n512", "slater64"):
         line = bench_single(args, torch, binding, workloads, ctx, precision, prec_name, stream, timed, barrier,
@@ -425,7 +427,7 @@ def run_ours(args):
         os.unlink(tune_path)
     line.setdefault("config", {})["autotune"] = {
         "what": "K split of the sliced tensor-core Gram chosen by timing (the Gram does not depend on it)",
-        "chunks_of_256_per_cta": chosen} if args.workload != "serving" else "off (default splits while serving)"
+        "chunks_of_256_per_cta": chosen} if tuning else "off (default splits)"
     ctx.tune(False, "")
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -298,6 +298,10 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   // sampling fused with the mode-1 slicing: Fh is never stored (the Gram and
   // the first TTM read the slices)
   const bool fused = sliced && tab && nmodes == 1 && h[0] % 8 == 0 && key.fz;
+  // even n: row exponents and |F|^2 from the table (its entries' multiplicities
+  // cached per context), then one pass that only gathers and slices
+  const bool one_pass = fused && n[0] % 2 == 0;
+  const int* counts = one_pass ? table_counts(ctx->mult, n[0], s) : nullptr;
   const bool with_err = key.err != 0;
   // the error of a fused solve is taken against the Gram's slices in
   // float-float arithmetic (FP32 range: every sigma2 within 2^-60 .. 2^60);
@@ -305,7 +309,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
   bool err_ff = with_err && fused;
   for (int b = 0; b < B && err_ff; ++b)
     err_ff = req[b].k.sigma2 >= 0x1p-60 && req[b].k.sigma2 <= 0x1p60;
-  const size_t nparts = std::max<size_t>(eval_octant_parts(g), (size_t)h[0]);
+  const size_t nparts = std::max<size_t>(std::max<size_t>(eval_octant_parts(g), (size_t)h[0]),
+                                         tab && n[0] % 2 == 0 ? (size_t)table_parts(n[0]) : 1);
   size_t gram_bytes = 0, eig_doubles = 0;
   for (int a = 0; a < nmodes; ++a) {
     gram_bytes = std::max(gram_bytes, sliced                       ? gram_sliced_scratch_bytes(h, a, B)
@@ -421,9 +426,13 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     if (pf) pf->begin(TK_STAGE_EVAL, s);
     if (fused) {
       const SliceView v = gram_slices_view(gscr, h, 0, B);
-      // |F|^2: summed by the Gram's reduction kernel below
-      eval_octant_slices(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part, nullptr,
-                         s, pf);
+      // |F|^2: its partials summed by the Gram's reduction kernel below
+      if (one_pass)
+        eval_octant_slices8(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part, counts,
+                            s, pf);
+      else
+        eval_octant_slices(kd, g, B, table, const_cast<int*>(v.rowexp), const_cast<void*>(v.S), v.Kp, part,
+                           nullptr, s, pf);
     } else {
       eval_octant_f64(kd, tab, g, B, Fh, table, part, normF2, s, pf);
     }
@@ -442,7 +451,8 @@ void solve_bucket(tk_ctx* ctx, Workspace& pre, Workspace& post, HostPinned& pin,
     for (int a = nmodes - 1; a >= 0; --a) {
       if (pf) pf->begin(TK_STAGE_GRAM, s);
       if (fused)
-        gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf, NormParts{part, h[0], normF2});
+        gram_sliced_prepared(h, B, G[a], gscr, errflag, s, pf,
+                             NormParts{part, one_pass ? (int)table_parts(n[0]) : h[0], normF2});
       else if (sliced)
         gram_sliced_batch(Fh, h, a, B, G[a], gscr, errflag, s, pf);
       else if (is_split3(key.precision))

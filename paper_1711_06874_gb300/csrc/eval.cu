@@ -257,8 +257,13 @@ __device__ __forceinline__ double fold_scale(int twos) {
 // assignment does not change any result.
 constexpr int kTableWarps = 4;  // warps per block
 
+// With counts set (the multiplicity of each entry among the octant's points),
+// each chunk c also writes part[b][c] = sum of T[q]^2 counts[q] over its 32
+// entries (a fixed warp tree of Neumaier pairs): the |F|^2 partials, one slot
+// per chunk in a stride of table_parts(Q) slots (the unused last slot zero).
 __global__ void __launch_bounds__(32 * kTableWarps) k_table_b(const KernelDev* __restrict__ kd, double hstep,
-                                                             int even, long long Q, double* T, double scale) {
+                                                             int even, long long Q, double* T, double scale,
+                                                             const int* __restrict__ counts, double* part) {
   TK_PDL_ENTRY();
   const int b = blockIdx.y;
   const KernelDev& k = kd[b];
@@ -266,19 +271,37 @@ __global__ void __launch_bounds__(32 * kTableWarps) k_table_b(const KernelDev* _
   T += (size_t)b * Q;
   const long long W = (long long)gridDim.x * kTableWarps;
   const long long w = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int lane = threadIdx.x & 31;
   // chunks of 32 entries on each side of tsplit (Temme's range, then the
   // Miller recurrence's), so that no warp runs both branches
   const long long qb = k.tsplit < 0 ? 0 : (k.tsplit > Q ? Q : k.tsplit);
   const long long nchA = (qb + 31) / 32;
   const long long nch = nchA + (Q - qb + 31) / 32;
+  const long long stride = (Q + 31) / 32 + 1;
+  if (counts != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    for (long long c = nch; c < stride; ++c) part[(size_t)b * stride + c] = 0.0;
   for (long long r = 0; r * W < nch; ++r) {
     const long long c = r * W + ((r & 1) ? W - 1 - w : w);
     if (c >= nch) continue;
-    const long long q = ((c < nchA) ? 32 * c : qb + 32 * (c - nchA)) + (threadIdx.x & 31);
-    if (q >= ((c < nchA) ? qb : Q)) continue;
-    const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
-    const double v = cov_value(k, hs * hs * s);
-    T[q] = (scale == 1.0) ? v : v * scale;
+    const long long q = ((c < nchA) ? 32 * c : qb + 32 * (c - nchA)) + lane;
+    const bool live = q < ((c < nchA) ? qb : Q);
+    double v = 0.0;
+    if (live) {
+      const double s = even ? (double)(8 * q + 3) : (double)(4 * q);
+      v = cov_value(k, hs * hs * s);
+      v = (scale == 1.0) ? v : v * scale;
+      T[q] = v;
+    }
+    if (counts != nullptr) {
+      double sm = live ? v * v * (double)__ldg(counts + q) : 0.0, cm = 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double x = __shfl_xor_sync(0xffffffffu, sm, o), xc = __shfl_xor_sync(0xffffffffu, cm, o);
+        const double u = sm + x;
+        cm += xc + ((fabs(sm) >= fabs(x)) ? (sm - u) + x : (x - u) + sm);
+        sm = u;
+      }
+      if (lane == 0) part[(size_t)b * stride + c] = sm + cm;
+    }
   }
 }
 
@@ -547,8 +570,7 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   if (pf) pf->begin(TK_STAGE_TABLE, s);
   // even n: the table holds the octant values 2 sqrt(2) C directly
   launch_pdl("k_table_b", k_table_b, dim3(table_blocks(Q, B), B), dim3(32 * kTableWarps), 0, s, kd, hstep, n % 2 == 0,
-             Q, table,
-                                                                     n % 2 == 0 ? 2.8284271247461903 : 1.0);
+             Q, table, n % 2 == 0 ? 2.8284271247461903 : 1.0, (const int*)nullptr, (double*)nullptr);
   if (pf) pf->end(s);
   // rows of h^2 values: wide blocks for long rows (a function of the shape
   // alone, so that each instance's sums do not depend on the batch)
@@ -565,7 +587,121 @@ void eval_octant_slices(const KernelDev* kd, const tk_grid& g, int B, double* ta
   }
 }
 
+// counts[q] += 1 for every octant point (i, j, l) of an even grid, q its table
+// entry (a = 2 index + 1, q = (a_i^2 + a_j^2 + a_l^2 - 3) / 8).
+__global__ void k_table_counts(int h, int* __restrict__ counts) {
+  const long long total = (long long)h * h * h;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ((long long)h * h));
+    const int rem = (int)(e - (long long)i * h * h);
+    const int j = rem / h, l = rem - j * h;
+    const int ai = 2 * i + 1, aj = 2 * j + 1, al = 2 * l + 1;
+    atomicAdd(counts + ((ai * ai + aj * aj + al * al - 3) >> 3), 1);
+  }
+}
+
+// The six BF16 slices of octant row blockIdx.x of instance blockIdx.y (even
+// n, h a multiple of 8), eight consecutive columns (one table row j) a thread
+// and item: the eight gathers first, then the digits, then six 16-byte
+// stores.  The row exponent: row i holds the table entries q >= q_min(i) =
+// ((2i + 1)^2 - 1) / 8 = i (i + 1) / 2 (its entry j = l = 0), and every
+// covariance here decreases with the radius, so its largest entry is
+// T[q_min(i)]: e is the binary exponent of T[q_min(i)] (1 + 2^-40), the
+// factor keeping 2^e above the row even where neighbouring entries of a flat
+// table agree to the last bits.  Block i also writes it to rowexp.
+__global__ void __launch_bounds__(1024) k_gather_slice8(const double* __restrict__ T, long long Q, int h, long long Kp,
+                                                       int* __restrict__ rowexp, __nv_bfloat16* __restrict__ S) {
+  TK_PDL_ENTRY();
+  const int i = blockIdx.x, b = blockIdx.y;
+  const double* Tb = T + (size_t)b * Q;
+  int e = -1000;
+  {
+    const double top = fabs(__ldg(Tb + (long long)i * (i + 1) / 2)) * (1.0 + 0x1p-40);
+    if (top > 0.0) frexp(top, &e);
+  }
+  if (threadIdx.x == 0) rowexp[(size_t)b * h + i] = e;
+  const int ai = 2 * i + 1;
+  const long long K = (long long)h * h;
+  const size_t plane = (size_t)h * Kp;
+  __nv_bfloat16* Sb = S + (size_t)b * kSlices * plane + (size_t)i * Kp;
+  for (long long g = threadIdx.x; 8 * g < Kp; g += blockDim.x) {
+    const long long c = 8 * g;
+    uint32_t w[kSlices][4];
+    if (c < K && e > -1000) {
+      const int j = (int)(c / h), l0 = (int)(c - (long long)j * h);
+      const int aj = 2 * j + 1;
+      const int base = ai * ai + aj * aj - 3;
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int al = 2 * (l0 + u) + 1;
+        v[u] = __ldg(Tb + ((base + al * al) >> 3));
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        int d0[kSlices], d1[kSlices];
+        slice_digits(v[u], e, d0);
+        slice_digits(v[u + 1], e, d1);
+#pragma unroll
+        for (int s2 = 0; s2 < kSlices; ++s2) {
+          const __nv_bfloat162 pr = __halves2bfloat162(slice_value(d0[s2], s2), slice_value(d1[s2], s2));
+          w[s2][u >> 1] = *reinterpret_cast<const uint32_t*>(&pr);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int s2 = 0; s2 < kSlices; ++s2) w[s2][0] = w[s2][1] = w[s2][2] = w[s2][3] = 0u;
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < kSlices; ++s2)
+      *reinterpret_cast<uint4*>(Sb + s2 * plane + c) = make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+  }
+}
+
+MultCache::~MultCache() {
+  for (auto& kv : counts)
+    if (kv.second) cudaFree(kv.second);
+}
+
+const int* table_counts(MultCache& cache, int n, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(cache.mu);
+  auto it = cache.counts.find(n);
+  if (it != cache.counts.end()) return it->second;
+  if (n % 2 != 0) fail(TK_EINVAL, "table_counts: even n only");
+  const long long Q = table_size(n);
+  int* c = nullptr;
+  TK_CUDA(cudaMalloc(&c, sizeof(int) * (size_t)Q));
+  TK_CUDA(cudaMemsetAsync(c, 0, sizeof(int) * (size_t)Q, s));
+  const int h = n / 2;
+  const long long total = (long long)h * h * h;
+  k_table_counts<<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, s>>>(h, c);
+  TK_LAUNCH("k_table_counts");
+  TK_CUDA(cudaStreamSynchronize(s));  // other streams of the context read it next
+  cache.counts[n] = c;
+  return c;
+}
+
+void eval_octant_slices8(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
+                         long long Kp, double* part, const int* counts, cudaStream_t s, Profiler* pf) {
+  const int n = g.n[0], h = n / 2;
+  if (n % 2 != 0 || h % 8 != 0) fail(TK_EINVAL, "eval_octant_slices8: even n, h a multiple of 8");
+  const long long Q = table_size(n);
+  const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
+  if (pf) pf->begin(TK_STAGE_TABLE, s);
+  // even n: the table holds the octant values 2 sqrt(2) C directly
+  launch_pdl("k_table_b", k_table_b, dim3(table_blocks(Q, B), B), dim3(32 * kTableWarps), 0, s, kd, hstep, 1, Q,
+             table, 2.8284271247461903, counts, part);
+  if (pf) pf->end(s);
+  // one thread per group of eight columns, up to 1024 a row
+  const long long groups = (long long)h * h / 8;
+  const unsigned threads = (unsigned)std::min<long long>(1024, (groups + 31) / 32 * 32);
+  launch_pdl("k_gather_slice8", k_gather_slice8, dim3(h, B), dim3(threads), 0, s, (const double*)table, Q, h, Kp,
+             rowexp, (__nv_bfloat16*)S);
+}
+
 size_t eval_octant_parts(const tk_grid& g) { return oct_blocks(g); }
+long long table_parts(int n) { return (table_size(n) + 31) / 32 + 1; }
 long long table_entries(int n) { return table_size(n); }
 
 void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, double* Fh, double* table,
@@ -579,7 +715,7 @@ void eval_octant_f64(const KernelDev* kd, bool tab, const tk_grid& g, int B, dou
     const double hstep = (g.kind == TK_VERTEX) ? g.b[0] / (double)(n - 1) : g.b[0] / (double)n;
     if (pf) pf->begin(TK_STAGE_TABLE, s);
     launch_pdl("k_table_b", k_table_b, dim3(table_blocks(Q, B), B), dim3(32 * kTableWarps), 0, s, kd, hstep,
-               n % 2 == 0, Q, table, 1.0);
+               n % 2 == 0, Q, table, 1.0, (const int*)nullptr, (double*)nullptr);
     if (pf) pf->end(s);
     k_gather_oct<<<dim3(nb, B), threads, 0, s>>>(table, Q, n, (n + 1) / 2, Fh, part);
     TK_LAUNCH("k_gather_oct");

@@ -61,7 +61,8 @@ constexpr int kTN = 64;                // columns of a block of G (N)
 constexpr int kAcc = 5;                // accumulators: w = 0, 1, 2, 3 and w = 4..5
 constexpr int kKB = 32;                // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int kChunkBlocks = 8;        // 8 x 32 = 256 K per exact chunk
-constexpr int kStages = 3;
+constexpr int kStages = 3;                             // stages of A and B tiles
+constexpr int kMaxStages = 4;                          // stages of A tiles alone (B rows taken from A)
 constexpr int kSliceBytesA = kTM * kKB * 2;            // 8 KB
 constexpr int kSliceBytesB = kTN * kKB * 2;            // 4 KB
 constexpr int kOperandBytesA = kSlices * kSliceBytesA;  // 48 KB
@@ -213,9 +214,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
-  uint64_t* full = bars;                 // [kStages]
-  uint64_t* empty = bars + kStages;      // [kStages]
-  uint64_t* acc_full = bars + 2 * kStages;
+  uint64_t* full = bars;                 // [kMaxStages]
+  uint64_t* empty = bars + kMaxStages;      // [kMaxStages]
+  uint64_t* acc_full = bars + 2 * kMaxStages;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_full + 2;
   uint32_t* tmem_slot = (uint32_t*)(acc_full + 4);
@@ -231,9 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   // one row block holds every row (nrows <= kTM): the B rows bj kTN .. + kTN
   // are rows of the A tile already in shared memory, so B is not loaded
   const bool b_in_a = args.nrt == 1;
+  // without a B tile a stage is the A operand alone: one more stage fits
+  const int nst = b_in_a ? kMaxStages : kStages;
+  const int sstride = b_in_a ? kOperandBytesA : kStageBytes;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -253,10 +257,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int issued = 0;
       for (int k = 0; k < nkb; ++k) {
-        const int st = k % kStages;
-        const uint32_t use = k / kStages;
-        if (k >= kStages && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
-        unsigned char* sa = smem + st * kStageBytes;
+        const int st = k % nst;
+        const uint32_t use = k / nst;
+        if (k >= nst && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
+        unsigned char* sa = smem + st * sstride;
         tc::mbar_expect_tx(&full[st], b_in_a ? kOperandBytesA : kStageBytes);
         tc::tma_load_4d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0, inst);
         if (!b_in_a)
@@ -264,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         issued = k + 1;
       }
       // copies still in flight must land before the CTA exits
-      for (int k = max(0, issued - kStages); k < issued; ++k)
-        tc::mbar_wait(&full[k % kStages], (k / kStages) & 1, args.err);
+      for (int k = max(0, issued - nst); k < issued; ++k)
+        tc::mbar_wait(&full[k % nst], (k / nst) & 1, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -282,13 +286,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int kend = min(nkb, (ch + 1) * kChunkBlocks);
         uint32_t first_mask = (1u << kAcc) - 1;  // accumulator not yet written in this chunk
         for (; k < kend; ++k) {
-          const int st = k % kStages;
-          if (!tc::mbar_wait(&full[st], (k / kStages) & 1, args.err)) {
+          const int st = k % nst;
+          if (!tc::mbar_wait(&full[st], (k / nst) & 1, args.err)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          unsigned char* sa = smem + st * kStageBytes;
+          unsigned char* sa = smem + st * sstride;
           // B: its own tile, or rows bj kTN .. of the A tile (the same 64-byte
           // swizzle: the offset is a multiple of the 512-byte pattern)
           unsigned char* sb = b_in_a ? sa + bj * kTN * (kKB * 2) : sa + kOperandBytesA;

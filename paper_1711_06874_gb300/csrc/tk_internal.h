@@ -16,6 +16,7 @@
 namespace tk {
 
 struct Profiler;
+struct MultCache;
 
 // Error raised inside the library and turned into a status at the C-ABI.
 struct Error {
@@ -259,6 +260,20 @@ __device__ inline void norm_parts_block(const double* p, int nparts, double* out
 // set, the Gram's reduction kernel also sums each instance's |F|^2 partials.
 void gram_sliced_prepared(const int n[3], int B, double* G, void* scratch, int* err, cudaStream_t s,
                           Profiler* pf = nullptr, NormParts norm = NormParts{nullptr, 0, nullptr});
+// One-pass sampling and slicing for cubic isotropic grids with even n and
+// h = n / 2 a multiple of 8: the distinct-value table, with the |F|^2
+// partials of its chunks from the multiplicity of each entry (part:
+// [b][table_parts(n)], summed by the Gram's reduction as
+// NormParts{part, table_parts(n), normF2}), then the six BF16 slices of every
+// row in one pass, eight columns a thread, the row exponent from the row's
+// first table entry (its largest: every covariance here decreases with the
+// radius).
+long long table_parts(int n);
+void eval_octant_slices8(const KernelDev* kd, const tk_grid& g, int B, double* table, int* rowexp, void* S,
+                         long long Kp, double* part, const int* counts, cudaStream_t s, Profiler* pf = nullptr);
+// The multiplicities of the table entries of an even n, cached in `cache`;
+// synchronises s the first time for an n (not inside a stream capture).
+const int* table_counts(MultCache& cache, int n, cudaStream_t s);
 // Sampling fused with the mode-1 slicing for cubic isotropic grids: the
 // distinct-value table, then per octant row i the values Fh(i, j, l) (never
 // stored), their largest magnitude (row exponent), their BF16 slices and
@@ -492,9 +507,21 @@ struct Profiler {
 };
 }  // namespace tk
 
+namespace tk {
+// Multiplicities of the distinct-value table of an even cubic grid (how many
+// octant points share each table entry), one device array per n, kept for
+// the context's life.
+struct MultCache {
+  std::mutex mu;
+  std::map<int, int*> counts;  // n -> [table entries]
+  ~MultCache();
+};
+}  // namespace tk
+
 struct tk_ctx {
   int device = 0;
   std::mutex mu;
+  tk::MultCache mult;  // table multiplicities (|F|^2 of the one-pass slicing)
   tk::Workspace ws;   // stages before the rank decision
   tk::Workspace ws2;  // stages after it (sized from the ranks)
   tk::HostPinned pin; // staging of the engine's small transfers
