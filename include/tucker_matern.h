@@ -328,7 +328,10 @@ int tk_multigrid(tk_ctx* ctx, const tk_kernel* kernel, const tk_grid* grid, cons
  * being the smallest r whose discarded singular values satisfy
  * (sum_{k>=r} s_k^2)^(1/2) <= eps |A| / (3 |c|) (so that the RHOSVD bound
  * |A - A_r| <= |c| sum_l (sum_{k>=r_l} s_{l,k}^2)^(1/2) gives E <= eps), capped
- * at rmax_l (TK_RANK_CAPPED) and replaced by rfix_l where rfix_l > 0.  Then
+ * at rmax_l (TK_RANK_CAPPED) and replaced by rfix_l where rfix_l > 0.  A
+ * discarded sum_k s_k^2 at or below n_l u |U_l|_F^2 (u = 2^-53, the rounding
+ * level of the FP64 Gram's eigenvalues) counts as zero, and a tolerance below
+ * that level sets TK_EPS_UNREACHABLE_AT_PRECISION.  Then
  * `sweeps` Tucker-ALS sweeps (modes 1, 2, 3 in order), each mode's single-hole
  * unfolding U_l diag(c) (W_m (.) W_q)^T formed from the side matrices
  * (W_j = Z_j^T U_j, (.) the Khatri-Rao product); Z_l becomes its r_l leading

@@ -216,11 +216,23 @@ tk_result* c2t_solve(tk_ctx* ctx, int R, const double* c, const double* const U[
       TK_CUDA(cudaMemcpyAsync(lh[l].data(), lam + l * 96, sizeof(double) * mh, cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaMemcpyAsync(&total, trace + l, sizeof(double), cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaStreamSynchronize(s));
-      // smallest q >= 1 with (sum_{k>=q} s_k^2)^(1/2) <= tol, the tail taken as
-      // trace - sum_{k<q} s_k^2 (q = full keeps everything)
+      // smallest q >= 1 with (sum_{k>=q} s_k^2)^(1/2) <= tol (q = full keeps
+      // everything).  With every eigenvalue computed the tail is the sum of
+      // the discarded ones (negative rounding clamped to zero, summed from the
+      // smallest); otherwise trace - sum_{k<q} s_k^2.  The Gram's eigenvalues
+      // carry rounding of about n u trace (u = 2^-53): a tail at or below
+      // that floor cannot be told from zero, so it meets any tolerance, and a
+      // tolerance below the floor is flagged as unreachable in FP64.
+      const double floor2 = (double)n[l] * 0x1p-53 * total;
+      const double thr2 = std::max(tol * tol, floor2);
+      if (tol * tol < floor2) flags[l] |= TK_EPS_UNREACHABLE_AT_PRECISION;
+      std::vector<double> suffix(mh + 1, 0.0);  // suffix[k] = sum_{j>=k} max(s_j^2, 0)
+      for (int k = mh - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + std::max(lh[l][k], 0.0);
       q = 0;
       for (int cand = 1; cand <= mh; ++cand) {
-        if (cand == full || std::sqrt(std::max(0.0, total - host_sum(lh[l].data(), 0, cand))) <= tol) {
+        const double tail =
+            mh == n[l] ? suffix[cand] : std::max(0.0, total - host_sum(lh[l].data(), 0, cand));
+        if (cand == full || tail <= thr2) {
           q = cand;
           break;
         }

@@ -503,7 +503,6 @@ __global__ void k_trace(const double* G, int n, double* out) {
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
-__device__ __forceinline__ bool is_zero_d(double x) { return abs_bits(x) == 0; }
 // Monotone integer key of a double (non-NaN): larger value, larger key.
 __device__ __forceinline__ long long order_key(double x) {
   const long long b = __double_as_longlong(x);
@@ -735,24 +734,91 @@ __device__ __forceinline__ void exact_rotation(float cf, float sf, double& c, do
   s = fma(-s0, kappa, s0);
 }
 
+// Named CTA barriers (PTX bar.sync / bar.arrive): the count is in threads, a
+// multiple of 32, and every lane of a warp executes the instruction.
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+constexpr int kJacobiThreads = 256;  // warps 0..3 rotate A, warps 4..7 update V
+
+// (c, s) of the planes of step st (one lane per plane, warp 0): written to
+// cs[2k], cs[2k + 1]; a step with some rotation is marked in stepf[st] and
+// the sweep in *flag.
+__device__ __forceinline__ void jacobi_rotations(const double* A, int mp, int np, const int* sched, int st,
+                                                 double* cs, unsigned long long tau_b,
+                                                 unsigned long long noise_b, int* stepf, int* flag) {
+  for (int k = threadIdx.x & 31; k < np; k += 32) {
+    const int pq = sched[st * np + k];
+    const int p = pq & 0xFF, q = pq >> 8;
+    const double apq = A[p * mp + q], app = A[p * mp + p], aqq = A[q * mp + q];
+    double c = 1.0, s = 0.0;
+    // two indices whose diagonals both lie in the rounding noise of the
+    // matrix are left alone: their eigenvectors carry no information
+    const bool noise = abs_bits(app) <= noise_b && abs_bits(aqq) <= noise_b;
+    if (abs_bits(apq) > tau_b && !noise) {
+      // The angle only steers convergence, so it is taken in FP32 from
+      // (a_qq - a_pp) and a_pq scaled by 2^-e (e the exponent of a_pq);
+      // (c, s) are then made orthonormal to FP64 precision, so the rotation
+      // applied is exactly orthogonal.
+      const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
+      // (fast approximate quotients: the angle only has to be close)
+      const float theta = __fdividef(scaled_float(aqq - app, e), 2.0f * scaled_float(apq, e));
+      // |theta| <= |A|_F / (u_data |A|_F) < 2^53, so 1 + theta^2 stays finite
+      const float w = fmaf(theta, theta, 1.0f);
+      const float t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fmaf(w, rsqrtf(w), fabsf(theta)));
+      const float cf = rsqrtf(fmaf(t, t, 1.0f));
+      const float sf = t * cf;
+      exact_rotation(cf, sf, c, s);
+      if (sf != 0.0f) {
+        *flag = 1;
+        stepf[st] = 1;
+      }
+    }
+    cs[2 * k] = c;
+    cs[2 * k + 1] = s;
+  }
+}
+
 // u_data: the relative accuracy of the matrix's data (2^-53 for FP64 data,
 // 2^-48 for a Gram from the BF16 slices): a plane is rotated only while its
 // off-diagonal entry exceeds u_data |A|_F, below which the data do not
 // determine it, and two indices whose diagonals both lie below
 // 64 u_data |A|_F (the noise block) are left alone.
+//
+// Cyclic Jacobi with the circle method's parallel ordering (mp/2 disjoint
+// planes a step).  The CTA has 256 threads in two groups: warps 0..3 apply
+// each step's rotations to A (A <- J^T A J on the 2 x 2 blocks of the upper
+// triangle, one block row per lane, the same eight FP64 instructions on
+// every lane), and warp 0 then takes the next step's rotations from the
+// updated A; warps 4..7 apply each step's rotations to V (V <- V J) while
+// warp 0 works out the next ones.  The SM issues FP64 warp instructions at
+// about one per 19 cycles, each taking some 64 cycles, so V's update is kept
+// out of the phase in which A's update (the next rotations' input) runs.
+// Step i's (c, s) sit in one of two slots; named barrier 1 (all 256 threads;
+// warp 0 only arrives) publishes them, barrier 2 (all 256; warps 1..3 only
+// arrive) tells warp 0 and the V warps that A is updated.
 __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, double* Vout, int* sweeps_out,
                             double u_data) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const int mp = (m + 1) & ~1;  // padded to even; the pad row/column is zero
   const int np = mp / 2;        // planes per step
   const int nblk = np * (np + 1) / 2;
+  const int nsteps = mp - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* A = sm;
   double* V = A + mp * mp;
-  double* cs = V + mp * mp;                // c, s per plane
-  int* sched = (int*)(cs + mp);            // [step][plane]: p | q << 8
+  double* cs = V + mp * mp;                // two slots of (c, s) per plane
+  int* sched = (int*)(cs + 2 * mp);        // [step][plane]: p | q << 8
   int* blk = sched + (mp - 1) * np;        // [block]: a | b << 8, upper blocks in order
   int* stepf = blk + nblk;                 // [step]: some rotation in this step
-  int* flag = stepf + mp;
+  int* stepneed = stepf + mp;              // [step]: a plane above the threshold at the sweep's start
+  int* steplist = stepneed + mp;           // the sweep's steps in order
+  int* flag = steplist + mp;               // some rotation in this sweep
+  int* nlist = flag + 1;                   // length of steplist
   __shared__ double red[33];
   // H symmetrised on load: A = (H + H^T) / 2
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
@@ -785,138 +851,147 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   const unsigned long long noise_b = abs_bits(64.0 * u_data * normA);
   // f / mp for f < np mp by a 32-bit reciprocal (exact in this range)
   const unsigned magic = (unsigned)((0xFFFFFFFFull + mp) / mp);
+  const int group_t = threadIdx.x & 127;  // thread index within its group
+  // with at most 128 block rows each lane of warps 0..3 keeps its one block
+  const bool one_item = 2 * nblk <= 128;
+  const int ab_own = (one_item && warp < 4 && group_t < 2 * nblk) ? blk[group_t >> 1] : 0;
+  // step of the plane (p, q), p < q, in the circle method's schedule:
+  // q mod (mp - 1) for p = 0, else (p + q) / 2 mod (mp - 1) (mp - 1 is odd,
+  // and mp / 2 is the inverse of 2 modulo it)
+  const int half_mp = mp / 2;
+  for (int e = threadIdx.x; e < mp; e += blockDim.x) stepneed[e] = 0;
+  __syncthreads();
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
-    // a sweep runs only while some plane still needs a rotation (one pass over
-    // the upper triangle instead of a sweep that rotates nothing)
+    // A sweep runs only while some plane still needs a rotation, and only
+    // the steps holding such a plane at the start of the sweep (the others
+    // would rotate nothing, or planes that an earlier rotation of this sweep
+    // lifted above the threshold: the next sweep's check sees those).
     int need = 0;
     for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
       const int i = e / mp, j = e - (e / mp) * mp;
       if (i < j && abs_bits(A[e]) > tau_b &&
-          !(abs_bits(A[i * mp + i]) <= noise_b && abs_bits(A[j * mp + j]) <= noise_b))
+          !(abs_bits(A[i * mp + i]) <= noise_b && abs_bits(A[j * mp + j]) <= noise_b)) {
         need = 1;
+        stepneed[i == 0 ? j % nsteps : ((i + j) * half_mp) % nsteps] = 1;
+      }
     }
-    for (int e = threadIdx.x; e < mp; e += blockDim.x) stepf[e] = 0;
     if (!__syncthreads_or(need)) break;
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
-    for (int st = 0; st < mp - 1; ++st) {
-      // rotations of this step's planes
-      if (threadIdx.x < np) {
-        const int k = threadIdx.x;
-        const int pq = sched[st * np + k];
-        const int p = pq & 0xFF, q = pq >> 8;
-        const double apq = A[p * mp + q], app = A[p * mp + p], aqq = A[q * mp + q];
-        double c = 1.0, s = 0.0;
-        // two indices whose diagonals both lie in the rounding noise of the
-        // matrix are left alone: their eigenvectors carry no information
-        const bool noise = abs_bits(app) <= noise_b && abs_bits(aqq) <= noise_b;
-        if (abs_bits(apq) > tau_b && !noise) {
-          // The angle only steers convergence, so it is taken in FP32 from
-          // (a_qq - a_pp) and a_pq scaled by 2^-e (e the exponent of a_pq);
-          // (c, s) are then made orthonormal to FP64 precision, so the
-          // rotation applied is exactly orthogonal.
-          const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
-          // (fast approximate quotients: the angle only has to be close)
-          const float theta = __fdividef(scaled_float(aqq - app, e), 2.0f * scaled_float(apq, e));
-          const float t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-          const float cf = rsqrtf(fmaf(t, t, 1.0f));
-          const float sf = t * cf;
-          exact_rotation(cf, sf, c, s);
-          if (sf != 0.0f) {
-            *flag = 1;
-            stepf[st] = 1;
+    if (warp == 0) {
+      // the list of the sweep's steps, in order; flags cleared for the next
+      int cnt = 0;
+      for (int st0 = 0; st0 < nsteps; st0 += 32) {
+        const int st = st0 + lane;
+        const bool on = st < nsteps && stepneed[st] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) steplist[cnt + __popc(bal & ((1u << lane) - 1u))] = st;
+        cnt += __popc(bal);
+        if (st < nsteps) {
+          stepneed[st] = 0;
+          stepf[st] = 0;
+        }
+      }
+      if (lane == 0) {
+        *flag = 0;
+        *nlist = cnt;
+      }
+      __syncwarp();
+      jacobi_rotations(A, mp, np, sched, steplist[0], cs, tau_b, noise_b, stepf, flag);
+      __syncwarp();
+    }
+    for (int i = 0;; ++i) {
+      // barrier 1: step i's (c, s), stepf, the list and its length are written
+      if (warp == 0)
+        bar_arrive_n(1, kJacobiThreads);
+      else
+        bar_sync_n(1, kJacobiThreads);
+      const int st = steplist[i];
+      const bool last = i + 1 == *nlist;
+      const bool any = stepf[st] != 0;  // no plane rotates: nothing to apply
+      const double* csr = cs + (i & 1) * mp;
+      if (warp < 4) {
+        if (any) {
+          // block row e: block e/2 = (a, b), row p_a (even e) or q_a (odd e);
+          // the two rows of a block sit in adjacent lanes, which both read the
+          // block before either writes (__syncwarp).  An identity rotation
+          // (c = 1, s = 0) leaves the values bit for bit, so no lane tests for
+          // it.
+          for (int base = group_t - lane; base < 2 * nblk; base += 128) {
+            const int e = base + lane;
+            const bool valid = e < 2 * nblk;
+            const bool bottom = (e & 1) != 0;
+            const int ab = !valid ? 0 : (one_item ? ab_own : blk[e >> 1]);
+            const int a = ab & 0xFF, b = ab >> 8;
+            const double2 csa = *reinterpret_cast<const double2*>(csr + 2 * a);
+            const double2 csb = *reinterpret_cast<const double2*>(csr + 2 * b);
+            const int pqa = sched[st * np + a], pqb = sched[st * np + b];
+            const int pa = pqa & 0xFF, qa = pqa >> 8, pb = pqb & 0xFF, qb = pqb >> 8;
+            const int ra = bottom ? qa : pa;
+            const int oa = bottom ? pa : qa;
+            double o0 = 0.0, o1 = 0.0, x0 = 0.0, x1 = 0.0;
+            if (valid) {
+              o0 = A[ra * mp + pb];  // own row
+              o1 = A[ra * mp + qb];
+              x0 = A[oa * mp + pb];  // the block's other row
+              x1 = A[oa * mp + qb];
+            }
+            __syncwarp();
+            if (valid) {
+              // row rotation: top [c -s], bottom [s c] of the block's two rows,
+              // i.e. c * own + (-+ s) * other; then the column rotation
+              // (.) [c s; -s c]
+              const double sae = __longlong_as_double(__double_as_longlong(csa.y) ^
+                                                      (bottom ? 0ll : (long long)0x8000000000000000ull));
+              const double r0 = fma(sae, x0, csa.x * o0), r1 = fma(sae, x1, csa.x * o1);
+              const double n0 = fma(-csb.y, r1, csb.x * r0), n1 = fma(csb.y, r0, csb.x * r1);
+              if (a == b) {
+                if (!bottom) {
+                  A[pa * mp + pa] = n0;
+                  A[pa * mp + qa] = n1;
+                  A[qa * mp + pa] = n1;  // the block stays exactly symmetric
+                } else {
+                  A[qa * mp + qa] = n1;
+                }
+              } else {
+                A[ra * mp + pb] = n0;
+                A[ra * mp + qb] = n1;
+                A[pb * mp + ra] = n0;
+                A[qb * mp + ra] = n1;
+              }
+            }
+            __syncwarp();
           }
         }
-        cs[2 * k] = c;
-        cs[2 * k + 1] = s;
-      }
-      __syncthreads();
-      if (stepf[st] == 0) continue;  // no plane rotates: nothing to apply
-      // A <- J^T A J on every 2 x 2 block (plane a rows, plane b columns),
-      // upper blocks computed and mirrored; one block row (two entries) per
-      // lane, the two rows of a block in adjacent lanes, which both read the
-      // block before either writes (__syncwarp).  V <- V J on plane column
-      // pairs.  Block rows go to the first half of the CTA and V to the
-      // second, so every sub-partition's FP64 unit gets a share of both.
-      const int half = blockDim.x >> 1;
-      if ((int)threadIdx.x < half) {
-        const int lane = threadIdx.x & 31;
-        for (int base = (int)threadIdx.x - lane; base < 2 * nblk; base += half) {
-          const int e = base + lane;
-          const bool valid = e < 2 * nblk;
-          int pa = 0, qa = 0, pb = 0, qb = 0, a = 0, b = 0;
-          double ca = 1.0, sa = 0.0, cb = 1.0, sb = 0.0, m00 = 0.0, m01 = 0.0, m10 = 0.0, m11 = 0.0;
-          bool still = true;
-          if (valid) {
-            const int ab = blk[e >> 1];
-            a = ab & 0xFF;
-            b = ab >> 8;
-            sa = cs[2 * a + 1];
-            sb = cs[2 * b + 1];
-            still = is_zero_d(sa) && is_zero_d(sb);  // both identities: nothing changes
-            if (!still) {
-              ca = cs[2 * a];
-              cb = cs[2 * b];
-              const int pqa = sched[st * np + a], pqb = sched[st * np + b];
-              pa = pqa & 0xFF;
-              qa = pqa >> 8;
-              pb = pqb & 0xFF;
-              qb = pqb >> 8;
-              m00 = A[pa * mp + pb];
-              m01 = A[pa * mp + qb];
-              m10 = A[qa * mp + pb];
-              m11 = A[qa * mp + qb];
-            }
-          }
+        // barrier 2: A holds step i's result (warps 1..3 arrive; warp 0 and
+        // the V warps wait), so V's update runs beside the next rotations
+        if (warp == 0) {
+          bar_sync_n(2, kJacobiThreads);
+          if (!last)
+            jacobi_rotations(A, mp, np, sched, steplist[i + 1], cs + ((i + 1) & 1) * mp, tau_b, noise_b, stepf,
+                             flag);
           __syncwarp();
-          if (valid && !still) {
-            if ((e & 1) == 0) {
-              // top row: [c -s] M, then the column rotation (.) [c s; -s c]
-              const double r0 = ca * m00 - sa * m10, r1 = ca * m01 - sa * m11;
-              const double n0 = cb * r0 - sb * r1, n1 = sb * r0 + cb * r1;
-              if (a == b) {
-                A[pa * mp + pa] = n0;
-                A[pa * mp + qa] = n1;
-                A[qa * mp + pa] = n1;  // the block stays exactly symmetric
-              } else {
-                A[pa * mp + pb] = n0;
-                A[pa * mp + qb] = n1;
-                A[pb * mp + pa] = n0;
-                A[qb * mp + pa] = n1;
-              }
-            } else {
-              // bottom row: [s c] M, then the column rotation
-              const double r0 = sa * m00 + ca * m10, r1 = sa * m01 + ca * m11;
-              const double n1 = sb * r0 + cb * r1;
-              if (a == b) {
-                A[qa * mp + qa] = n1;
-              } else {
-                const double n0 = cb * r0 - sb * r1;
-                A[qa * mp + pb] = n0;
-                A[qa * mp + qb] = n1;
-                A[pb * mp + qa] = n0;
-                A[qb * mp + qa] = n1;
-              }
-            }
-          }
-          __syncwarp();
+        } else {
+          bar_arrive_n(2, kJacobiThreads);
         }
       } else {
-        for (int f = threadIdx.x - half; f < np * mp; f += blockDim.x - half) {
-          const int k = (int)__umulhi((unsigned)f, magic), row = f - k * mp;
-          const double s = cs[2 * k + 1];
-          if (is_zero_d(s)) continue;
-          const double c = cs[2 * k];
-          const int pq = sched[st * np + k];
-          const int p = pq & 0xFF, q = pq >> 8;
-          const double vp = V[row * mp + p], vq = V[row * mp + q];
-          V[row * mp + p] = c * vp - s * vq;
-          V[row * mp + q] = s * vp + c * vq;
+        bar_sync_n(2, kJacobiThreads);
+        // V <- V J on warps 5..7: warp 4 shares warp 0's sub-partition, whose
+        // FP64 unit the next rotations use meanwhile
+        if (any && warp > 4) {
+          for (int f = (int)threadIdx.x - 160; f < np * mp; f += 96) {
+            const int k = (int)__umulhi((unsigned)f, magic), row = f - k * mp;
+            const double2 c_s = *reinterpret_cast<const double2*>(csr + 2 * k);
+            const int pq = sched[st * np + k];
+            const int p = pq & 0xFF, q = pq >> 8;
+            const double vp = V[row * mp + p], vq = V[row * mp + q];
+            V[row * mp + p] = fma(-c_s.y, vq, c_s.x * vp);
+            V[row * mp + q] = fma(c_s.y, vp, c_s.x * vq);
+          }
         }
       }
-      __syncthreads();
+      if (last) break;
     }
+    __syncthreads();  // V holds the sweep's last step
     const int any = *flag;
     __syncthreads();
     if (!any) break;
@@ -935,8 +1010,9 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
-__global__ void __launch_bounds__(1024) k_jacobi(JacBatch batch) {
-  const JacProb& p = batch.p[blockIdx.x];
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(JacBatch batch) {
+  // (a constant index into the parameter block: no local copy of the batch)
+  const JacProb& p = blockIdx.x == 0 ? batch.p[0] : batch.p[1];
   jacobi_body(p.H, p.m, p.lam, p.V, p.sweeps, 0x1p-53);
 }
 
@@ -946,7 +1022,7 @@ __device__ void rank_warp(const double* lam, int m, double trace, double nf, dou
 // One m x m problem per CTA: H + b * m^2 -> lam + b * m, V + b * m^2.  With
 // rank.out set, warp 0 then applies the truncation rule to the leading mr
 // eigenvalues and trace[b].
-__global__ void __launch_bounds__(1024) k_jacobi_strided(const double* H, int m, double* lam, double* V,
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi_strided(const double* H, int m, double* lam, double* V,
                                                          RankArgs rank, int mr, const double* trace,
                                                          double u_data) {
   TK_PDL_ENTRY();
@@ -1285,9 +1361,11 @@ static constexpr size_t kStart32SmemMax = 200 * 1024;
 
 static size_t jacobi_smem(int m) {
   const int mp = (m + 1) & ~1, np = mp / 2;
-  // A, V, (c, s); the plane schedule, the block list, step flags and the sweep flag
-  return (2ull * mp * mp + mp) * sizeof(double) +
-         ((size_t)(mp - 1) * np + (size_t)np * (np + 1) / 2 + mp + 4) * sizeof(int);
+  // A, V, two slots of (c, s); the plane schedule, the block list, three
+  // per-step arrays (rotation flags, need flags, the sweep's step list), the
+  // sweep flag and the list length
+  return (2ull * mp * mp + 2ull * mp) * sizeof(double) +
+         ((size_t)(mp - 1) * np + (size_t)np * (np + 1) / 2 + 3 * (size_t)mp + 4) * sizeof(int);
 }
 
 static void set_attrs_once() {
@@ -1343,7 +1421,7 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
       smem = std::max(smem, jacobi_smem(n));
     }
     if (nj) {
-      k_jacobi<<<nj, 256, smem, s>>>(jb);
+      k_jacobi<<<nj, kJacobiThreads, smem, s>>>(jb);
       TK_LAUNCH("k_jacobi");
     }
     for (int b = 0; b < count; ++b) {
@@ -1396,7 +1474,7 @@ static void eig_batch(EigProb* pr, int count, cudaStream_t s) {
     jb.p[t] = JacProb{w[b].H, ms, w[b].lsub, w[b].VH, (int*)(w[b].misc + 8)};
     smem = std::max(smem, jacobi_smem(ms));
   }
-  k_jacobi<<<nr, 256, smem, s>>>(jb);
+  k_jacobi<<<nr, kJacobiThreads, smem, s>>>(jb);
   TK_LAUNCH("k_jacobi");
   for (int t = 0; t < nr; ++t) {
     const int b = idx[t], n = pr[b].n, ms = w[b].ms, m = pr[b].m;
@@ -1548,7 +1626,7 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     gemm_f64(d2, s);
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
-  launch_pdl("k_jacobi_strided", k_jacobi_strided, dim3(B), dim3(256), jacobi_smem(ms), s, g.H, ms, g.lsub, g.VH,
+  launch_pdl("k_jacobi_strided", k_jacobi_strided, dim3(B), dim3(kJacobiThreads), jacobi_smem(ms), s, g.H, ms, g.lsub, g.VH,
              rank ? *rank : RankArgs{}, m, trace,
                                                     u_data);
   if (pf) pf->end(s);

@@ -130,6 +130,9 @@ def test_c2t_exact_on_low_column_rank(ctx, orc):
     res, _, e = _check(ctx, orc, c, U, 1e-10, 1, e_abs=1e-12)
     assert res.ranks[0] == [2, 3, 4]
     assert e <= 1e-12
+    # eps^2 |A|^2 / (9 |c|^2) lies below the FP64 Gram's rounding level
+    # n_l u |U_l|^2: the discarded noise counts as zero, and the flag says so
+    assert all(f & 2 for f in res.ranks[1])
 
 
 def test_c2t_rank_cap_flag(ctx, orc):
