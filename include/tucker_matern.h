@@ -401,7 +401,9 @@ typedef enum {
   TK_STAGE_GRAM_TC = 8, /* tensor-core Gram kernel (slices excluded) */
   TK_STAGE_QR = 9,      /* FP64 Householder QR of the eigensolver */
   TK_STAGE_JACOBI = 10, /* Jacobi of the Rayleigh-Ritz matrix */
-  TK_NSTAGES = 11
+  TK_STAGE_START = 11,  /* FP32 start block of the eigensolver (G Omega, its QR, Q0) */
+  TK_STAGE_EIG_GEMM = 12, /* the eigensolver's FP64 products (G Q0, G Q, Q^T G Q, Q V_H) */
+  TK_NSTAGES = 13
 } tk_stage;
 /* on = 1 starts recording CUDA events around every stage of later calls on
  * this context and zeroes the totals; on = 0 stops. */

@@ -100,7 +100,8 @@ SIGNATURES = {
     "tk_kernel_launches": (_c.c_uint64, []),
 }
 
-STAGES = ["eval", "norm", "gram", "eig", "rank", "core", "error", "table", "gram_tc", "qr", "jacobi"]
+STAGES = ["eval", "norm", "gram", "eig", "rank", "core", "error", "table", "gram_tc", "qr", "jacobi", "start",
+          "eig_gemm"]
 
 _lock = threading.Lock()
 _lib = None

@@ -745,6 +745,32 @@ __device__ __forceinline__ void bar_arrive_n(int id, int count) {
 
 constexpr int kJacobiThreads = 256;  // warps 0..3 rotate A, warps 4..7 update V
 
+// Rotation (c, s) of the plane with entries a_pp, a_qq, a_pq (c = 1, s = 0
+// below the thresholds); true when it rotates.
+__device__ __forceinline__ bool plane_rotation(double app, double aqq, double apq, unsigned long long tau_b,
+                                               unsigned long long noise_b, double& c, double& s) {
+  c = 1.0;
+  s = 0.0;
+  // two indices whose diagonals both lie in the rounding noise of the matrix
+  // are left alone: their eigenvectors carry no information
+  const bool noise = abs_bits(app) <= noise_b && abs_bits(aqq) <= noise_b;
+  if (abs_bits(apq) <= tau_b || noise) return false;
+  // The angle only steers convergence, so it is taken in FP32 from
+  // (a_qq - a_pp) and a_pq scaled by 2^-e (e the exponent of a_pq); (c, s)
+  // are then made orthonormal to FP64 precision, so the rotation applied is
+  // exactly orthogonal.
+  const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
+  // (fast approximate quotients: the angle only has to be close)
+  const float theta = __fdividef(scaled_float(aqq - app, e), 2.0f * scaled_float(apq, e));
+  // |theta| <= |A|_F / (u_data |A|_F) < 2^53, so 1 + theta^2 stays finite
+  const float w = fmaf(theta, theta, 1.0f);
+  const float t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fmaf(w, rsqrtf(w), fabsf(theta)));
+  const float cf = rsqrtf(fmaf(t, t, 1.0f));
+  const float sf = t * cf;
+  exact_rotation(cf, sf, c, s);
+  return sf != 0.0f;
+}
+
 // (c, s) of the planes of step st (one lane per plane, warp 0): written to
 // cs[2k], cs[2k + 1]; a step with some rotation is marked in stepf[st] and
 // the sweep in *flag.
@@ -754,33 +780,77 @@ __device__ __forceinline__ void jacobi_rotations(const double* A, int mp, int np
   for (int k = threadIdx.x & 31; k < np; k += 32) {
     const int pq = sched[st * np + k];
     const int p = pq & 0xFF, q = pq >> 8;
-    const double apq = A[p * mp + q], app = A[p * mp + p], aqq = A[q * mp + q];
-    double c = 1.0, s = 0.0;
-    // two indices whose diagonals both lie in the rounding noise of the
-    // matrix are left alone: their eigenvectors carry no information
-    const bool noise = abs_bits(app) <= noise_b && abs_bits(aqq) <= noise_b;
-    if (abs_bits(apq) > tau_b && !noise) {
-      // The angle only steers convergence, so it is taken in FP32 from
-      // (a_qq - a_pp) and a_pq scaled by 2^-e (e the exponent of a_pq);
-      // (c, s) are then made orthonormal to FP64 precision, so the rotation
-      // applied is exactly orthogonal.
-      const int e = (int)((abs_bits(apq) >> 52) & 0x7FF) - 1023;
-      // (fast approximate quotients: the angle only has to be close)
-      const float theta = __fdividef(scaled_float(aqq - app, e), 2.0f * scaled_float(apq, e));
-      // |theta| <= |A|_F / (u_data |A|_F) < 2^53, so 1 + theta^2 stays finite
-      const float w = fmaf(theta, theta, 1.0f);
-      const float t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fmaf(w, rsqrtf(w), fabsf(theta)));
-      const float cf = rsqrtf(fmaf(t, t, 1.0f));
-      const float sf = t * cf;
-      exact_rotation(cf, sf, c, s);
-      if (sf != 0.0f) {
-        *flag = 1;
-        stepf[st] = 1;
-      }
+    double c, s;
+    if (plane_rotation(A[p * mp + p], A[q * mp + q], A[p * mp + q], tau_b, noise_b, c, s)) {
+      *flag = 1;
+      stepf[st] = 1;
     }
     cs[2 * k] = c;
     cs[2 * k + 1] = s;
   }
+}
+
+// Row e of the 2 x 2 blocks of step st (block e / 2 = planes (a, b), a <= b;
+// row p_a for even e, q_a for odd e): with the two (c, s), the new entries in
+// columns p_b and q_b, n0 and n1, of J^T A J.  The same FMAs serve the
+// update of A and the look-ahead of the next rotations, so both see the same
+// bits.  Reads of A only.
+struct BlockRow {
+  int r, pb, qb, pa, qa, a, b;
+  bool bottom;
+};
+__device__ __forceinline__ BlockRow block_row(int ab, bool bottom, const int* sched_st) {
+  BlockRow br;
+  br.a = ab & 0xFF;
+  br.b = ab >> 8;
+  const int pqa = sched_st[br.a], pqb = sched_st[br.b];
+  br.pa = pqa & 0xFF;
+  br.qa = pqa >> 8;
+  br.pb = pqb & 0xFF;
+  br.qb = pqb >> 8;
+  br.bottom = bottom;
+  br.r = bottom ? br.qa : br.pa;
+  return br;
+}
+__device__ __forceinline__ void block_row_values(const BlockRow& br, const double* A, int mp, const double* csr,
+                                                 double& n0, double& n1) {
+  const double2 csa = *reinterpret_cast<const double2*>(csr + 2 * br.a);
+  const double2 csb = *reinterpret_cast<const double2*>(csr + 2 * br.b);
+  const int oa = br.bottom ? br.pa : br.qa;
+  const double o0 = A[br.r * mp + br.pb], o1 = A[br.r * mp + br.qb];  // own row
+  const double x0 = A[oa * mp + br.pb], x1 = A[oa * mp + br.qb];      // the block's other row
+  // row rotation: top [c -s], bottom [s c] of the block's two rows, i.e.
+  // c * own + (-+ s) * other; then the column rotation (.) [c s; -s c]
+  const double sae = __longlong_as_double(__double_as_longlong(csa.y) ^
+                                          (br.bottom ? 0ll : (long long)0x8000000000000000ull));
+  const double r0 = fma(sae, x0, csa.x * o0), r1 = fma(sae, x1, csa.x * o1);
+  n0 = fma(-csb.y, r1, csb.x * r0);
+  n1 = fma(csb.y, r0, csb.x * r1);
+}
+// n1 (col_q) or n0 of block_row_values, by the same operations, in two
+// parts: the reads (block_row_load) and the arithmetic (block_row_value).
+struct BlockRowIn {
+  double2 csa, csb;
+  double o0, o1, x0, x1;
+};
+__device__ __forceinline__ BlockRowIn block_row_load(const BlockRow& br, const double* A, int mp,
+                                                     const double* csr) {
+  BlockRowIn in;
+  in.csa = *reinterpret_cast<const double2*>(csr + 2 * br.a);
+  in.csb = *reinterpret_cast<const double2*>(csr + 2 * br.b);
+  const int oa = br.bottom ? br.pa : br.qa;
+  in.o0 = A[br.r * mp + br.pb];
+  in.o1 = A[br.r * mp + br.qb];
+  in.x0 = A[oa * mp + br.pb];
+  in.x1 = A[oa * mp + br.qb];
+  return in;
+}
+__device__ __forceinline__ double block_row_value(const BlockRowIn& in, bool bottom, bool col_q) {
+  const double sae = __longlong_as_double(__double_as_longlong(in.csa.y) ^
+                                          (bottom ? 0ll : (long long)0x8000000000000000ull));
+  const double r0 = fma(sae, in.x0, in.csa.x * in.o0), r1 = fma(sae, in.x1, in.csa.x * in.o1);
+  const double sb = col_q ? in.csb.y : -in.csb.y;
+  return fma(sb, col_q ? r0 : r1, in.csb.x * (col_q ? r1 : r0));
 }
 
 // u_data: the relative accuracy of the matrix's data (2^-53 for FP64 data,
@@ -819,6 +889,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   int* steplist = stepneed + mp;           // the sweep's steps in order
   int* flag = steplist + mp;               // some rotation in this sweep
   int* nlist = flag + 1;                   // length of steplist
+  int* where = nlist + 1;                  // [step][index]: plane | 256 for the plane's q
   __shared__ double red[33];
   // H symmetrised on load: A = (H + H^T) / 2
   for (int e = threadIdx.x; e < mp * mp; e += blockDim.x) {
@@ -851,15 +922,28 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
   const unsigned long long noise_b = abs_bits(64.0 * u_data * normA);
   // f / mp for f < np mp by a 32-bit reciprocal (exact in this range)
   const unsigned magic = (unsigned)((0xFFFFFFFFull + mp) / mp);
-  const int group_t = threadIdx.x & 127;  // thread index within its group
-  // with at most 128 block rows each lane of warps 0..3 keeps its one block
-  const bool one_item = 2 * nblk <= 128;
-  const int ab_own = (one_item && warp < 4 && group_t < 2 * nblk) ? blk[group_t >> 1] : 0;
   // step of the plane (p, q), p < q, in the circle method's schedule:
   // q mod (mp - 1) for p = 0, else (p + q) / 2 mod (mp - 1) (mp - 1 is odd,
   // and mp / 2 is the inverse of 2 modulo it)
   const int half_mp = mp / 2;
+  // Look-ahead (3 np <= 32): warp 0 forms the three entries a_pp, a_qq, a_pq
+  // of each next plane from the A before this step and this step's (c, s)
+  // (the same FMAs as the update), and the next rotations from them, while
+  // warps 1..3 update A.  Otherwise warps 0..3 update A and warp 0 then
+  // reads the updated A.
+  const bool look = 3 * np <= 32;
+  const int a_t0 = look ? 32 : 0, a_nt = look ? 96 : 128;  // A's update: first thread, threads
+  const int a_t = (int)threadIdx.x - a_t0;
+  // with at most a_nt block rows each updating lane keeps its one block
+  const bool one_item = 2 * nblk <= a_nt;
+  const int ab_own = (one_item && a_t >= 0 && a_t < 2 * nblk && warp < 4) ? blk[a_t >> 1] : 0;
   for (int e = threadIdx.x; e < mp; e += blockDim.x) stepneed[e] = 0;
+  // where[st][x]: plane of index x in step st, | 256 when x is its q
+  for (int e = threadIdx.x; e < (mp - 1) * np; e += blockDim.x) {
+    const int st = e / np, k = e - st * np;
+    where[st * mp + (sched[e] & 0xFF)] = k;
+    where[st * mp + (sched[e] >> 8)] = k | 256;
+  }
   __syncthreads();
   int sweep = 0;
   for (sweep = 1; sweep <= 60; ++sweep) {
@@ -900,8 +984,9 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
       __syncwarp();
     }
     for (int i = 0;; ++i) {
-      // barrier 1: step i's (c, s), stepf, the list and its length are written
-      if (warp == 0)
+      // barrier 1: step i's (c, s), stepf, the list and its length are
+      // written (and, with the look-ahead, step i - 1's update of A is done)
+      if (warp == 0 && !look)
         bar_arrive_n(1, kJacobiThreads);
       else
         bar_sync_n(1, kJacobiThreads);
@@ -909,79 +994,105 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
       const bool last = i + 1 == *nlist;
       const bool any = stepf[st] != 0;  // no plane rotates: nothing to apply
       const double* csr = cs + (i & 1) * mp;
-      if (warp < 4) {
+      const int* sched_st = sched + st * np;
+      if (look && warp == 0) {
+        // entry lane l: plane l / 3 of the next step, entry l % 3 (a_pp,
+        // a_qq, a_pq), taken from the block row that the update writes it from
+        double v = 0.0;
+        const int st1 = last ? st : steplist[i + 1];
+        const bool act = !last && lane < 3 * np;
+        BlockRow br{};
+        bool col_q = false;
+        if (act) {
+          const int pq1 = sched[st1 * np + lane / 3];
+          const int which = lane - 3 * (lane / 3);
+          int x = pq1 & 0xFF, y = pq1 >> 8;  // (p', q')
+          if (which == 0) y = x;
+          if (which == 1) x = y;
+          const int* wst = where + st * mp;
+          int wx = wst[x], wy = wst[y];
+          if ((wy & 0xFF) < (wx & 0xFF)) {  // the row is the index in the lower plane
+            const int tt = wx;
+            wx = wy;
+            wy = tt;
+          }
+          const int pa = wx & 0xFF, pb = wy & 0xFF;
+          br = block_row(pa | (pb << 8), (wx >> 8) != 0, sched_st);
+          col_q = (wy >> 8) != 0;
+        }
+        BlockRowIn in{};
+        if (act) in = block_row_load(br, A, mp, csr);
+        // the update of A may start once these reads are done (barrier 2:
+        // warp 0 arrives, a release of its reads; warps 1..3 wait)
+        bar_arrive_n(2, 128);
+        if (act) v = block_row_value(in, br.bottom, col_q);
+        const double app = __shfl_sync(0xffffffffu, v, 3 * lane);
+        const double aqq = __shfl_sync(0xffffffffu, v, 3 * lane + 1);
+        const double apq = __shfl_sync(0xffffffffu, v, 3 * lane + 2);
+        if (!last && lane < np) {
+          double c, sn;
+          if (plane_rotation(app, aqq, apq, tau_b, noise_b, c, sn)) {
+            *flag = 1;
+            stepf[st1] = 1;
+          }
+          double* csw = cs + ((i + 1) & 1) * mp;
+          csw[2 * lane] = c;
+          csw[2 * lane + 1] = sn;
+        }
+        __syncwarp();
+      } else if (warp < 4) {
+        if (look) bar_sync_n(2, 128);  // warp 0 has read the entries it needs
         if (any) {
-          // block row e: block e/2 = (a, b), row p_a (even e) or q_a (odd e);
-          // the two rows of a block sit in adjacent lanes, which both read the
-          // block before either writes (__syncwarp).  An identity rotation
-          // (c = 1, s = 0) leaves the values bit for bit, so no lane tests for
-          // it.
-          for (int base = group_t - lane; base < 2 * nblk; base += 128) {
+          // block rows: the two rows of a block sit in adjacent lanes, which
+          // both read the block before either writes (__syncwarp).  An
+          // identity rotation (c = 1, s = 0) leaves the values bit for bit.
+          for (int base = a_t - lane; base < 2 * nblk; base += a_nt) {
             const int e = base + lane;
             const bool valid = e < 2 * nblk;
-            const bool bottom = (e & 1) != 0;
             const int ab = !valid ? 0 : (one_item ? ab_own : blk[e >> 1]);
-            const int a = ab & 0xFF, b = ab >> 8;
-            const double2 csa = *reinterpret_cast<const double2*>(csr + 2 * a);
-            const double2 csb = *reinterpret_cast<const double2*>(csr + 2 * b);
-            const int pqa = sched[st * np + a], pqb = sched[st * np + b];
-            const int pa = pqa & 0xFF, qa = pqa >> 8, pb = pqb & 0xFF, qb = pqb >> 8;
-            const int ra = bottom ? qa : pa;
-            const int oa = bottom ? pa : qa;
-            double o0 = 0.0, o1 = 0.0, x0 = 0.0, x1 = 0.0;
-            if (valid) {
-              o0 = A[ra * mp + pb];  // own row
-              o1 = A[ra * mp + qb];
-              x0 = A[oa * mp + pb];  // the block's other row
-              x1 = A[oa * mp + qb];
-            }
+            const BlockRow br = block_row(ab, (e & 1) != 0, sched_st);
+            double n0 = 0.0, n1 = 0.0;
+            if (valid) block_row_values(br, A, mp, csr, n0, n1);
             __syncwarp();
             if (valid) {
-              // row rotation: top [c -s], bottom [s c] of the block's two rows,
-              // i.e. c * own + (-+ s) * other; then the column rotation
-              // (.) [c s; -s c]
-              const double sae = __longlong_as_double(__double_as_longlong(csa.y) ^
-                                                      (bottom ? 0ll : (long long)0x8000000000000000ull));
-              const double r0 = fma(sae, x0, csa.x * o0), r1 = fma(sae, x1, csa.x * o1);
-              const double n0 = fma(-csb.y, r1, csb.x * r0), n1 = fma(csb.y, r0, csb.x * r1);
-              if (a == b) {
-                if (!bottom) {
-                  A[pa * mp + pa] = n0;
-                  A[pa * mp + qa] = n1;
-                  A[qa * mp + pa] = n1;  // the block stays exactly symmetric
+              if (br.a == br.b) {
+                if (!br.bottom) {
+                  A[br.pa * mp + br.pa] = n0;
+                  A[br.pa * mp + br.qa] = n1;
+                  A[br.qa * mp + br.pa] = n1;  // the block stays exactly symmetric
                 } else {
-                  A[qa * mp + qa] = n1;
+                  A[br.qa * mp + br.qa] = n1;
                 }
               } else {
-                A[ra * mp + pb] = n0;
-                A[ra * mp + qb] = n1;
-                A[pb * mp + ra] = n0;
-                A[qb * mp + ra] = n1;
+                A[br.r * mp + br.pb] = n0;
+                A[br.r * mp + br.qb] = n1;
+                A[br.pb * mp + br.r] = n0;
+                A[br.qb * mp + br.r] = n1;
               }
             }
             __syncwarp();
           }
         }
-        // barrier 2: A holds step i's result (warps 1..3 arrive; warp 0 and
-        // the V warps wait), so V's update runs beside the next rotations
-        if (warp == 0) {
-          bar_sync_n(2, kJacobiThreads);
-          if (!last)
-            jacobi_rotations(A, mp, np, sched, steplist[i + 1], cs + ((i + 1) & 1) * mp, tau_b, noise_b, stepf,
-                             flag);
-          __syncwarp();
-        } else {
-          bar_arrive_n(2, kJacobiThreads);
+        if (!look) {
+          // barrier 2: A holds step i's result (warps 1..3 arrive; warp 0 and
+          // the V warps wait), so V's update runs beside the next rotations
+          if (warp == 0) {
+            bar_sync_n(2, kJacobiThreads);
+            if (!last)
+              jacobi_rotations(A, mp, np, sched, steplist[i + 1], cs + ((i + 1) & 1) * mp, tau_b, noise_b,
+                               stepf, flag);
+            __syncwarp();
+          } else {
+            bar_arrive_n(2, kJacobiThreads);
+          }
         }
       } else {
-        bar_sync_n(2, kJacobiThreads);
-        // V <- V J on warps 5..7: warp 4 shares warp 0's sub-partition, whose
-        // FP64 unit the next rotations use meanwhile
-        if (any && warp > 4) {
-          for (int f = (int)threadIdx.x - 160; f < np * mp; f += 96) {
+        if (!look) bar_sync_n(2, kJacobiThreads);
+        if (any) {
+          for (int f = (int)threadIdx.x - 128; f < np * mp; f += 128) {
             const int k = (int)__umulhi((unsigned)f, magic), row = f - k * mp;
             const double2 c_s = *reinterpret_cast<const double2*>(csr + 2 * k);
-            const int pq = sched[st * np + k];
+            const int pq = sched_st[k];
             const int p = pq & 0xFF, q = pq >> 8;
             const double vp = V[row * mp + p], vq = V[row * mp + q];
             V[row * mp + p] = fma(-c_s.y, vq, c_s.x * vp);
@@ -991,7 +1102,7 @@ __device__ void jacobi_body(const double* __restrict__ Hin, int m, double* lam, 
       }
       if (last) break;
     }
-    __syncthreads();  // V holds the sweep's last step
+    __syncthreads();  // A and V hold the sweep's last step
     const int any = *flag;
     __syncthreads();
     if (!any) break;
@@ -1363,9 +1474,10 @@ static size_t jacobi_smem(int m) {
   const int mp = (m + 1) & ~1, np = mp / 2;
   // A, V, two slots of (c, s); the plane schedule, the block list, three
   // per-step arrays (rotation flags, need flags, the sweep's step list), the
-  // sweep flag and the list length
+  // sweep flag, the list length and each index's plane per step
   return (2ull * mp * mp + 2ull * mp) * sizeof(double) +
-         ((size_t)(mp - 1) * np + (size_t)np * (np + 1) / 2 + 3 * (size_t)mp + 4) * sizeof(int);
+         ((size_t)(mp - 1) * np + (size_t)np * (np + 1) / 2 + 3 * (size_t)mp + 2 + (size_t)(mp - 1) * mp) *
+             sizeof(int);
 }
 
 static void set_attrs_once() {
@@ -1598,12 +1710,16 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
       GemmDesc d{n, ms, n, B, g.G, (long long)n * n, n, 1, src, (long long)n * ms, 1, n,
                  g.Y, (long long)n * ms, 1, n};
       d.fixed_order = 1;
+      if (pf) pf->begin(TK_STAGE_EIG_GEMM, s);
       gemm_f64(d, s);
+      if (pf) pf->end(s);
     };
     if (uses_start32(n, ms)) {
       // FP32 pass from the random block, then one FP64 pass
       // (Y's storage holds the FP32 product until the FP64 pass writes it)
+      if (pf) pf->begin(TK_STAGE_START, s);
       start32_launch(g.G, n, ms, B, seed, g.Q, trace, reinterpret_cast<float*>(g.Y), s);
+      if (pf) pf->end(s);
       power(g.Q);
       qr();
     } else {
@@ -1619,11 +1735,13 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     GemmDesc d1{n, ms, n, B, g.G, (long long)n * n, n, 1, g.Q, (long long)n * ms, 1, n,
                 g.W, (long long)n * ms, 1, n};
     d1.fixed_order = 1;
+    if (pf) pf->begin(TK_STAGE_EIG_GEMM, s);
     gemm_f64(d1, s);
     GemmDesc d2{ms, ms, n, B, g.Q, (long long)n * ms, n, 1, g.W, (long long)n * ms, 1, n,
                 g.H, (long long)ms * ms, ms, 1};
     d2.fixed_order = 1;
     gemm_f64(d2, s);
+    if (pf) pf->end(s);
   }
   if (pf) pf->begin(TK_STAGE_JACOBI, s);
   launch_pdl("k_jacobi_strided", k_jacobi_strided, dim3(B), dim3(kJacobiThreads), jacobi_smem(ms), s, g.H, ms, g.lsub, g.VH,
@@ -1638,7 +1756,9 @@ void solve_group(const EigGroup& g, int B, double* trace, cudaStream_t s, Profil
     GemmDesc d3{n, m, ms, B, g.Q, (long long)n * ms, 1, n, g.VH, (long long)ms * ms, ms, 1,
                 g.V, (long long)n * m, m, 1};
     d3.fixed_order = 1;
+    if (pf) pf->begin(TK_STAGE_EIG_GEMM, s);
     gemm_f64(d3, s);
+    if (pf) pf->end(s);
   }
   TK_CUDA(cudaMemcpy2DAsync(g.lam, sizeof(double) * m, g.lsub, sizeof(double) * ms, sizeof(double) * m, B,
                             cudaMemcpyDeviceToDevice, s));
