@@ -14,10 +14,16 @@
 //                   integer multiple of 2^(-14-8w) of at most 2^24 of those
 //                   units while (w+1) * 256 * 2^14 <= 2^24, i.e. for 256-deep
 //                   K chunks (the tensor core's FP32 sums are exact there);
-//   w = 4, 5     -> one FP32 accumulator; the tensor core truncates, which
-//                   costs about 2^-17 of a term that is 2^-32 of the leading one;
+//   w = 4, 5     -> one FP32 accumulator each; the tensor core truncates,
+//                   which costs about 2^-17 of terms that are 2^-32 and 2^-40
+//                   of the leading one;
 //   w >= 6       -> dropped (2^-48 of the leading term).
-// Every 256-deep K chunk the epilogue warps move the five accumulators into a
+// The six B slices of a stage sit one after the other in shared memory, so
+// B_0 .. B_{5-s} read as one operand of 64 (6 - s) rows: one MMA per A slice
+// s (two where N would pass 256) forms every pair (s, t) at once into the
+// accumulators w = s .. 5, which lie side by side in TMEM -- 8 MMAs per
+// 16-deep K step instead of 21, each reading the A slice once.
+// Every 256-deep K chunk the epilogue warps move the six accumulators into a
 // 64-bit integer accumulator in units of 2^-44 (exact for w <= 3), so the
 // chunk sums carry no rounding; the split-K partials stay 64-bit integers and
 // are summed exactly (in two 32-bit halves), so each entry of G is the
@@ -28,8 +34,8 @@
 // and one K range):
 //   warp 0       TMA producer: 6 slices x 128 rows (A) and 6 x 64 rows (B) x
 //                32 K per stage, SWIZZLE_64B, three stages;
-//   warp 1       TMEM owner (5 accumulators of 64 columns) and the
-//                single-thread tcgen05.mma issuer (21 slice pairs x 2 K steps);
+//   warp 1       TMEM owner (6 accumulators of 64 columns) and the
+//                single-thread tcgen05.mma issuer (8 MMAs x 2 K steps);
 //   warps 2..17  epilogue: TMEM -> registers -> int64, one TMEM lane quadrant
 //                and one 16-column group each.
 // Every mbarrier wait is bounded; on a timeout the kernel raises a flag, lets
@@ -58,11 +64,10 @@ namespace {
 
 constexpr int kTM = 128;               // rows of a block of G (M)
 constexpr int kTN = 64;                // columns of a block of G (N)
-constexpr int kAcc = 5;                // accumulators: w = 0, 1, 2, 3 and w = 4..5
+constexpr int kAcc = 6;                // accumulators: w = 0 .. 5
 constexpr int kKB = 32;                // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int kChunkBlocks = 8;        // 8 x 32 = 256 K per exact chunk
 constexpr int kStages = 3;                             // stages of A and B tiles
-constexpr int kMaxStages = 4;                          // stages of A tiles alone (B rows taken from A)
 constexpr int kSliceBytesA = kTM * kKB * 2;            // 8 KB
 constexpr int kSliceBytesB = kTN * kKB * 2;            // 4 KB
 constexpr int kOperandBytesA = kSlices * kSliceBytesA;  // 48 KB
@@ -214,9 +219,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
-  uint64_t* full = bars;                 // [kMaxStages]
-  uint64_t* empty = bars + kMaxStages;      // [kMaxStages]
-  uint64_t* acc_full = bars + 2 * kMaxStages;
+  uint64_t* full = bars;                 // [kStages]
+  uint64_t* empty = bars + kStages;      // [kStages]
+  uint64_t* acc_full = bars + 2 * kStages;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_full + 2;
   uint32_t* tmem_slot = (uint32_t*)(acc_full + 4);
@@ -229,12 +234,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kb1 = min(kb0 + args.kblocks_per_split, args.kblocks_total);
   const int nkb = kb1 - kb0;
   const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
-  // one row block holds every row (nrows <= kTM): the B rows bj kTN .. + kTN
-  // are rows of the A tile already in shared memory, so B is not loaded
-  const bool b_in_a = args.nrt == 1;
-  // without a B tile a stage is the A operand alone: one more stage fits
-  const int nst = b_in_a ? kMaxStages : kStages;
-  const int sstride = b_in_a ? kOperandBytesA : kStageBytes;
+  const int nst = kStages;
+  const int sstride = kStageBytes;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -261,10 +262,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t use = k / nst;
         if (k >= nst && !tc::mbar_wait(&empty[st], (use - 1) & 1, args.err)) break;
         unsigned char* sa = smem + st * sstride;
-        tc::mbar_expect_tx(&full[st], b_in_a ? kOperandBytesA : kStageBytes);
+        tc::mbar_expect_tx(&full[st], kStageBytes);
         tc::tma_load_4d(sa, &tmapA, &full[st], (kb0 + k) * kKB, bi * kTM, 0, inst);
-        if (!b_in_a)
-          tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0, inst);
+        tc::tma_load_4d(sa + kOperandBytesA, &tmapB, &full[st], (kb0 + k) * kKB, bj * kTN, 0, inst);
         issued = k + 1;
       }
       // copies still in flight must land before the CTA exits
@@ -274,7 +274,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
       bool ok = true;
       int k = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
@@ -284,8 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_after_sync();
         const int kend = min(nkb, (ch + 1) * kChunkBlocks);
-        uint32_t first_mask = (1u << kAcc) - 1;  // accumulator not yet written in this chunk
-        for (; k < kend; ++k) {
+        for (int k0 = k; k < kend; ++k) {
           const int st = k % nst;
           if (!tc::mbar_wait(&full[st], (k / nst) & 1, args.err)) {
             ok = false;
@@ -293,24 +291,27 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::fence_after_sync();
           unsigned char* sa = smem + st * sstride;
-          // B: its own tile, or rows bj kTN .. of the A tile (the same 64-byte
-          // swizzle: the offset is a multiple of the 512-byte pattern)
-          unsigned char* sb = b_in_a ? sa + bj * kTN * (kKB * 2) : sa + kOperandBytesA;
-          const int sliceB = b_in_a ? kSliceBytesA : kSliceBytesB;
+          unsigned char* sb = sa + kOperandBytesA;
           // descriptors of slice 0; slice s and K step kk add (s * slice bytes + kk * 32 B) / 16
           const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
           const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
-#pragma unroll 1
-          for (int pidx = 0; pidx < kPairs; ++pidx) {
-            const int s = kPairS[pidx], t = kPairT[pidx];
-            const int acc = (s + t < 4) ? s + t : 4;
-            const uint32_t dt = tmem + acc * kTN;
-            const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
-            first_mask &= ~(1u << acc);
-            const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
-            const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
-            tc::mma_bf16(dt, da, db, idesc, accum);
-            tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            // the chunk's first K step starts the accumulators: the two MMAs of
+            // A slice 0 write every w = 0 .. 5 before any other MMA adds to it
+            const uint32_t acc_on = (k == k0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              // (A slice, first B slice, B slices): accumulators w = s + t0 ..
+              const int sl = e < 2 ? 0 : (e < 4 ? 1 : e - 2);
+              const int t0 = (e == 1 || e == 3) ? 4 : 0;
+              const int nt = e == 0 || e == 2 || e == 4 ? 4 : (e == 1 ? 2 : (e == 3 ? 1 : 6 - sl));
+              const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN * nt);
+              const uint32_t dt = tmem + (uint32_t)((sl + t0) * kTN);
+              const uint64_t da = da0 + (uint64_t)(sl * (kSliceBytesA >> 4) + 2 * kk);
+              const uint64_t db = db0 + (uint64_t)(t0 * (kSliceBytesB >> 4) + 2 * kk);
+              tc::mma_bf16(dt, da, db, idesc, sl == 0 ? acc_on : 1u);
+            }
           }
           tc::mma_commit(&empty[st]);  // frees the stage once these MMAs finish
         }
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc::fence_after_sync();
       // w = 0..3 are integer multiples of 2^(-14-8w): exact into units of
-      // 2^-44; the w = 4..5 accumulator is rounded to that unit
+      // 2^-44; the w = 4 and w = 5 accumulators are rounded to that unit
 #pragma unroll
       for (int h = 0; h < kEpiCols / 8; ++h) {
         uint32_t r[8];
@@ -358,6 +359,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 8; ++j)
           V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 274877906944.0f) * (1LL << 6);
         tc::tmem_ld8(base + 4 * kTN + h * 8, r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 17592186044416.0f);
+        tc::tmem_ld8(base + 5 * kTN + h * 8, r);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           V[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j]) * 17592186044416.0f);
