@@ -4,10 +4,12 @@
 // of Fh that the mode-1 Gram made (rows i scaled by 2^-e_i; viewed with rows
 // (i, k) and K = l when the slice row length equals h2 h3); the B operand is
 // U_3 sliced per column c (scale 2^-f_c).  The 21 slice pairs with s + t <= 5
-// go to five FP32 TMEM accumulators (w = 0..3 exact, w = 4..5 merged) over
-// 256-deep chunks, moved to int64 in units of 2^-44 as in the Gram, and the
-// output is that integer times 2^(e_i + f_c - 44): no rounding but the slices'
-// own, the same for any batch.
+// go to FP32 TMEM accumulators per weight w = s + t (w = 0..3 exact; w = 4, 5
+// apart for Np <= 64, where one MMA per A slice covers its B slices 0 .. 5 - s
+// as in the Gram, and merged for Np = 96, one MMA per pair) over 256-deep
+// chunks, moved to int64 in units of 2^-44 as in the Gram, and the output is
+// that integer times 2^(e_i + f_c - 44): no rounding but the slices' own, the
+// same for any batch.
 //
 // A CTA streams a run of consecutive (instance, 128-row tile) pairs of the
 // group (about one run per SM): warp 0 issues the TMA loads (6 slices x 128
@@ -117,7 +119,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nchunks = (nkb + kChunkBlocks - 1) / kChunkBlocks;
   // two accumulator sets in TMEM when they fit: the MMAs of one round then
   // run while the epilogue drains the previous round
-  const int acc_cols = kAcc * Np;
+  // Np <= 64: six accumulators (w = 4 and 5 apart) side by side, so that one
+  // MMA per A slice s covers the B slices 0 .. 5 - s (they lie one after the
+  // other in shared memory: N = Np (6 - s), split at 256); Np = 96: five
+  // accumulators (w = 4, 5 merged) and one MMA per slice pair
+  const bool wide = 6 * Np <= 512;
+  const int nacc = wide ? 6 : kAcc;
+  const int acc_cols = nacc * Np;
   const int nbuf = (2 * acc_cols <= 512) ? 2 : 1;
 
   if (threadIdx.x == 0) {
@@ -193,17 +201,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             unsigned char* sb = sa + kOperandBytesA;
             const uint64_t da0 = tc::smem_desc(sa, 512, tc::kSwizzle64B);
             const uint64_t db0 = tc::smem_desc(sb, 512, tc::kSwizzle64B);
+            if (wide) {
+              const int ppm = 256 / Np;  // B slices per MMA
 #pragma unroll 1
-            for (int pidx = 0; pidx < kPairs; ++pidx) {
-              const int s = kPairS[pidx], t = kPairT[pidx];
-              const int acc = (s + t < 4) ? s + t : 4;
-              const uint32_t dt = tset + acc * Np;
-              const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
-              first_mask &= ~(1u << acc);
-              const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
-              const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
-              tc::mma_bf16(dt, da, db, idesc, accum);
-              tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+              for (int kk = 0; kk < 2; ++kk) {
+                // the chunk's first K step starts the accumulators: A slice 0's
+                // MMAs write every w = 0 .. 5 before any other MMA adds to it
+                const uint32_t acc_on = (first_mask != 0 && kk == 0) ? 0u : 1u;
+#pragma unroll 1
+                for (int sl = 0; sl < kSlices; ++sl) {
+                  for (int t0 = 0; t0 < kSlices - sl; t0 += ppm) {
+                    const int nt = min(ppm, kSlices - sl - t0);
+                    const uint32_t dt = tset + (uint32_t)((sl + t0) * Np);
+                    const uint64_t da = da0 + (uint64_t)(sl * (kSliceBytesA >> 4) + 2 * kk);
+                    const uint64_t db = db0 + (uint64_t)(t0 * (sliceB >> 4) + 2 * kk);
+                    tc::mma_bf16(dt, da, db, tc::idesc_bf16_f32(kTM, nt * Np), sl == 0 ? acc_on : 1u);
+                  }
+                }
+              }
+              first_mask = 0;
+            } else {
+#pragma unroll 1
+              for (int pidx = 0; pidx < kPairs; ++pidx) {
+                const int s = kPairS[pidx], t = kPairT[pidx];
+                const int acc = (s + t < 4) ? s + t : 4;
+                const uint32_t dt = tset + acc * Np;
+                const uint32_t accum = ((first_mask >> acc) & 1u) ? 0u : 1u;
+                first_mask &= ~(1u << acc);
+                const uint64_t da = da0 + (uint64_t)(s * (kSliceBytesA >> 4));
+                const uint64_t db = db0 + (uint64_t)(t * (sliceB >> 4));
+                tc::mma_bf16(dt, da, db, idesc, accum);
+                tc::mma_bf16(dt, da + 2, db + 2, idesc, 1u);
+              }
             }
             tc::mma_commit(&empty[st]);
           }
@@ -258,6 +287,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 8; ++c)
               V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 17592186044416.0f);
+            if (wide) {
+              tc::tmem_ld8(base + 5 * Np + hh * 8, r);
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                V[hh * 8 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * 17592186044416.0f);
+            }
           }
         }
         tc::fence_before_sync();
