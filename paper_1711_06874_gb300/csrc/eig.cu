@@ -590,12 +590,20 @@ __global__ void __launch_bounds__(256) k_gomega32(const double* __restrict__ G, 
     W[e] = (c < ms) ? hash_uniform_f(seed, (unsigned long long)c * n + k) : 0.0f;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < rows * ms; t += blockDim.x) {
-    const int c = t / rows, r = t - c * rows;
+  // warp r takes row i0 + r; lane l column c = 16 cg + (l & 15) over the k of
+  // parity l >> 4, and the two halves meet by a shuffle
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = w; r < rows; r += nw) {
     const float* g = Gr + (size_t)r * n;
-    float acc = 0.0f;
-    for (int k = 0; k < n; ++k) acc = fmaf(g[k], W[(size_t)k * ms4 + c], acc);
-    Yg[((size_t)b * ms + c) * n + i0 + r] = acc;
+    for (int c0 = 0; c0 < ms; c0 += 16) {
+      const int c = c0 + (lane & 15);
+      const float* wc = W + min(c, ms4 - 1);
+      float acc = 0.0f;
+#pragma unroll 8
+      for (int k = lane >> 4; k < n; k += 2) acc = fmaf(g[k], wc[(size_t)k * ms4], acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+      if (lane < 16 && c < ms) Yg[((size_t)b * ms + c) * n + i0 + r] = acc;
+    }
   }
 }
 
@@ -615,38 +623,67 @@ __global__ void __launch_bounds__(256) k_start32(const float* __restrict__ Yg, i
   float* Y = s32;  // n x ms, column-major, stride ld
   Yg += (size_t)blockIdx.x * ms * n;
   Q0 += (size_t)blockIdx.x * n * ms;
-  for (int e = threadIdx.x; e < n * ms; e += blockDim.x) {
-    const int c = e / n, i = e - c * n;
-    Y[(size_t)c * ld + i] = Yg[e];
+  {
+    // eight loads in flight per thread
+    const int tot = n * ms, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * nt) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (e0 + u * nt < tot) ? Yg[e0 + u * nt] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nt;
+        if (e < tot) Y[(size_t)(e / n) * ld + e % n] = v[u];
+      }
+    }
   }
   __syncthreads();
   qr_factor_reg<float, kRPL>(Y, ld, n, ms, bsm, beta, v0s);
   __syncthreads();
-  // Q e_c = H_0 ... H_c e_c, one warp per column (rows above each head are 0)
+  // Q e_c = H_0 ... H_c e_c (rows above each head are 0): warp w forms the
+  // columns c1 = c and c2 = c + nw together, two independent chains
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c = threadIdx.x >> 5; c < ms; c += nw) {
-    float q[kRPL];
+  for (int c1 = threadIdx.x >> 5; c1 < ms; c1 += 2 * nw) {
+    const int c2 = c1 + nw;
+    const bool two = c2 < ms;
+    const int ctop = two ? c2 : c1;
+    float q1[kRPL], q2[kRPL];
 #pragma unroll
-    for (int t = 0; t < kRPL; ++t) q[t] = (lane + 32 * t == c) ? 1.0f : 0.0f;
-    for (int j = c; j >= 0; --j) {
+    for (int t = 0; t < kRPL; ++t) {
+      q1[t] = (lane + 32 * t == c1) ? 1.0f : 0.0f;
+      q2[t] = (lane + 32 * t == c2) ? 1.0f : 0.0f;
+    }
+    for (int j = ctop; j >= 0; --j) {
       const float* v = Y + (long long)j * ld;
       float vv[kRPL];
-      float d = 0.0f;
+      float d1 = 0.0f, d2 = 0.0f;
 #pragma unroll
       for (int t = 0; t < kRPL; ++t) {
         const int i = lane + 32 * t;
         vv[t] = (i < n && i >= j) ? v[i] : 0.0f;
-        d = fmaf(vv[t], q[t], d);
+        d1 = fmaf(vv[t], q1[t], d1);
+        d2 = fmaf(vv[t], q2[t], d2);
       }
-      d = warp_sum32(d);
-      const float f = bsm[j] * d;
 #pragma unroll
-      for (int t = 0; t < kRPL; ++t) q[t] = fmaf(-f, vv[t], q[t]);
+      for (int o = 16; o > 0; o >>= 1) {
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      }
+      // H_j acts on column c only for j <= c (uniform across the warp)
+      const float f1 = j <= c1 ? bsm[j] * d1 : 0.0f, f2 = bsm[j] * d2;
+#pragma unroll
+      for (int t = 0; t < kRPL; ++t) {
+        q1[t] = fmaf(-f1, vv[t], q1[t]);
+        q2[t] = fmaf(-f2, vv[t], q2[t]);
+      }
     }
 #pragma unroll
     for (int t = 0; t < kRPL; ++t) {
       const int i = lane + 32 * t;
-      if (i < n) Q0[(long long)c * n + i] = float_to_double_bits(q[t]);
+      if (i < n) {
+        Q0[(long long)c1 * n + i] = float_to_double_bits(q1[t]);
+        if (two) Q0[(long long)c2 * n + i] = float_to_double_bits(q2[t]);
+      }
     }
   }
 }

@@ -145,5 +145,34 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// v 2^k as a double, rounded to nearest (ties to even) as (double)v then an
+// exact ldexp would round it, from the integer bits alone: the FP64 pipe of
+// this GPU is narrow, and an epilogue that converts every output there waits
+// on it.  Results outside the normal range take the FP64 route.
+__device__ __forceinline__ double i64_scaled(long long v, int k) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
+  unsigned long long a = sign ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int msb = 63 - __clzll((long long)a);
+  int e = msb + k + 1023;  // biased exponent of the leading bit
+  unsigned long long q;    // 53 significant bits, the leading one at bit 52
+  if (msb <= 52) {
+    q = a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    q = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) {
+      ++q;
+      if (q >> 53) {
+        q >>= 1;
+        ++e;
+      }
+    }
+  }
+  if (e <= 0 || e >= 2047) return ldexp((double)v, k);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (q & 0x000FFFFFFFFFFFFFull)));
+}
+
 }  // namespace tc
 }  // namespace tk

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int col = grp * cpg + c;
           if (c < cpg && col < args.R) {
             const int f = fexp[col];
-            out[col] = (e > -1000 && f > -1000) ? ldexp((double)V[c], e + f - 44) : 0.0;
+            out[col] = (e > -1000 && f > -1000) ? tc::i64_scaled(V[c], e + f - 44) : 0.0;
           }
         }
       }
