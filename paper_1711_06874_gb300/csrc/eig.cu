@@ -208,9 +208,7 @@ __device__ void qr_panel(T* Y, T* Qs, int n, int m, T* beta, T* v0s) {
 // betas[j] their scalars.
 template <class T, int kRPL>
 __device__ void qr_factor_reg(T* Y, int ld, int n, int m, T* betas, T* beta, T* v0s) {
-  constexpr int kG = 4 * kRPL;  // rows per lane of an eight-lane group
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gsub = lane >> 3, l8 = lane & 7;
   if (w == 0) {
     T s2 = T(0);
 #pragma unroll
@@ -255,29 +253,43 @@ __device__ void qr_factor_reg(T* Y, int ld, int n, int m, T* betas, T* beta, T* 
         if (lane == 0) reflector(s2, xv[0], v0s[j + 1], beta[j + 1]);  // xv[0] of lane 0: row j + 1
       }
     } else {
-      for (int cb = j + 2 + 4 * (w - 1); cb < m; cb += 4 * (nw - 1)) {
-        const int c = cb + gsub;
+      // Columns j + 2 on: groups of kL lanes, one column each.  FP64 takes
+      // 16-lane groups (22 FP64 instructions a warp for two columns, where
+      // 8-lane groups take 37 for four) and fills the warps sharing warp 0's
+      // sub-partition last: the FP64 unit of a sub-partition issues one warp
+      // instruction about every 64 cycles, and warp 0's chain is the critical
+      // path.  FP32 keeps 8-lane groups.
+      constexpr int kL = sizeof(T) == 8 ? 16 : 8;  // lanes per column
+      constexpr int kGpw = 32 / kL;                 // columns per warp and round
+      constexpr int kGr = 32 * kRPL / kL;           // rows per lane
+      const int gq = lane / kL, lq = lane % kL;
+      const int ntw = nw - 1;
+      int tw = w - 1;
+      if (sizeof(T) == 8) tw = (w & 3) ? w - 1 - (w >> 2) : (ntw - (ntw >> 2)) + (w >> 2) - 1;
+      for (int cb = j + 2 + kGpw * tw; cb < m; cb += kGpw * ntw) {
+        const int c = cb + gq;
         const bool act = c < m;
         T* xc = Y + (long long)(act ? c : j) * ld;  // an idle group reads column j (read-only here)
-        T yv[kG], xv[kG];
+        T yv[kGr], xv[kGr];
 #pragma unroll
-        for (int t = 0; t < kG; ++t) {
-          const int i = j + 1 + l8 + 8 * t;
+        for (int t = 0; t < kGr; ++t) {
+          const int i = j + 1 + lq + kL * t;
           const bool in = act && i < n;
           yv[t] = in ? y[i] : T(0);
           xv[t] = in ? xc[i] : T(0);
         }
-        const T head = (act && l8 == 0) ? xc[j] : T(0);
+        const T head = (act && lq == 0) ? xc[j] : T(0);
         T d = v0 * head;
 #pragma unroll
-        for (int t = 0; t < kG; ++t) d = fma(yv[t], xv[t], d);
-        d = group_sum8(d);
+        for (int t = 0; t < kGr; ++t) d = fma(yv[t], xv[t], d);
+#pragma unroll
+        for (int o = kL / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         const T f = bj * d;
         if (act) {
-          if (l8 == 0) xc[j] = fma(-f, v0, head);
+          if (lq == 0) xc[j] = fma(-f, v0, head);
 #pragma unroll
-          for (int t = 0; t < kG; ++t) {
-            const int i = j + 1 + l8 + 8 * t;
+          for (int t = 0; t < kGr; ++t) {
+            const int i = j + 1 + lq + kL * t;
             if (i < n) xc[i] = fma(-f, yv[t], xv[t]);
           }
         }
@@ -327,10 +339,11 @@ __global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, i
 }
 
 // Q = H_0 ... H_{m-1} [I; 0] column by column: column c is H_0 ... H_c e_c
-// (H_j e_c = e_c for j > c), one warp per column, four columns per CTA, so
-// the columns run on several SMs with no barrier between reflectors.  The
-// CTA keeps the reflectors it needs (0 .. its last column) in shared memory
-// with the rows above each head zeroed.  Instance blockIdx.y.
+// (H_j e_c = e_c for j > c), one CTA per column, so the columns run on
+// separate SMs with no barrier between reflectors: the CTA's four warps stage
+// the reflectors 0 .. c in shared memory (rows above each head zeroed) and
+// warp 0 alone applies them (a second warp on the SM would share the FP64
+// issue the chain waits on).  Instance blockIdx.y.
 template <int kRPL>
 __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, const double* __restrict__ betas,
                                                  double* __restrict__ Q, int n, int m, long long sY, long long sB,
@@ -341,8 +354,7 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
   Y += blockIdx.y * sY;
   betas += blockIdx.y * sB;
   Q += blockIdx.y * sQ;
-  const int c0 = blockIdx.x * 4;
-  const int cmax = min(m - 1, c0 + 3);
+  const int cmax = blockIdx.x;
   {
     // eight loads in flight per thread
     const int tot = (cmax + 1) * n, nt = blockDim.x;
@@ -359,8 +371,8 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
   }
   for (int j = threadIdx.x; j <= cmax; j += blockDim.x) bs[j] = betas[j];
   __syncthreads();
-  const int lane = threadIdx.x & 31, c = c0 + (threadIdx.x >> 5);
-  if (c > cmax) return;
+  const int lane = threadIdx.x & 31, c = cmax;
+  if (threadIdx.x >= 32) return;
   double q[kRPL];
 #pragma unroll
   for (int t = 0; t < kRPL; ++t) q[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
@@ -391,13 +403,13 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
 template <int kRPL>
 void qr64_launch(double* Y, double* betas, double* Q, int n, int m, int B, long long sB, cudaStream_t s) {
   const size_t f_smem = sizeof(double) * (size_t)panel_ld<double>(n) * m;
-  const size_t q_smem = sizeof(double) * (size_t)n * std::min(m, 4 * ((m + 3) / 4));
+  const size_t q_smem = sizeof(double) * (size_t)n * m;
   once_per_device((const void*)&k_qr_factor64<kRPL>, [] {
     TK_CUDA(cudaFuncSetAttribute(k_qr_factor64<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     TK_CUDA(cudaFuncSetAttribute(k_form_q<kRPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
   launch_pdl("k_qr_factor64", k_qr_factor64<kRPL>, dim3(B), dim3(256), f_smem, s, Y, betas, n, m, (long long)n * m, sB);
-  launch_pdl("k_form_q", k_form_q<kRPL>, dim3((m + 3) / 4, B), dim3(128), q_smem, s, Y, betas, Q, n, m,
+  launch_pdl("k_form_q", k_form_q<kRPL>, dim3(m, B), dim3(128), q_smem, s, Y, betas, Q, n, m,
              (long long)n * m, sB,
                                                            (long long)n * m);
 }
