@@ -122,6 +122,7 @@ struct ErrSlicedArgs {
   int rk_stride;
   int jbs;                 // rows j per CTA
   FF* W1;                  // group: [pos][h][kR][kR]
+  FF* VF;                  // group: [pos][h][kR], V in float-float (zero past the rank)
   double* partials;        // group: [pos][h][h / jbs]
   double* esum;            // group: [pos][2]
 };
@@ -183,8 +184,11 @@ __global__ void __launch_bounds__(kR * kR) k_err_w1(ErrSlicedArgs a) {
   const int r = err_rank(a, a.amap[pos]);
   const double* V = a.V + (size_t)pos * h * R;
   const double* Bc = a.B + (size_t)pos * R * R * R;
-  if (threadIdx.x < kR)
-    Vi[threadIdx.x] = ((int)threadIdx.x < r) ? ff_from_double(V[(size_t)i * R + threadIdx.x]) : FF{0.0f, 0.0f};
+  if (threadIdx.x < kR) {
+    const FF v = ((int)threadIdx.x < r) ? ff_from_double(V[(size_t)i * R + threadIdx.x]) : FF{0.0f, 0.0f};
+    Vi[threadIdx.x] = v;
+    a.VF[((size_t)pos * h + i) * kR + threadIdx.x] = v;  // for k_err_sliced: converted once
+  }
   __syncthreads();
   const int bb = threadIdx.x / kR, c = threadIdx.x - bb * kR;
   FF acc{0.0f, 0.0f};
@@ -230,13 +234,12 @@ __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
   __shared__ FF Vj[kJB * kR];     // V(j0 + jj, b)
   __shared__ FF W2s[kJB * kR];    // W2(j0 + jj, c)
   __shared__ float red[kErrThreads / 32];
-  const int h = a.h, R = a.R;
+  const int h = a.h;
   const int jb = blockIdx.x, i = blockIdx.y, pos = blockIdx.z;
   const int JB = a.jbs;
   const int j0 = jb * JB;
   const int b = a.amap[pos];
   const int r = err_rank(a, b);
-  const double* V = a.V + (size_t)pos * h * R;
   const int jlo = max(i - j0, 0);  // first row of the block with j >= i
   float acc2 = 0.0f;
   bool zero_row = false;
@@ -255,10 +258,8 @@ __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
     }
     const FF* W1 = a.W1 + ((size_t)pos * h + i) * kR * kR;
     for (int e = threadIdx.x; e < kR * kR; e += blockDim.x) W1s[e] = W1[e];
-    for (int e = threadIdx.x; e < JB * kR; e += blockDim.x) {
-      const int jj = e / kR, c = e - jj * kR;
-      Vj[e] = (c < r) ? ff_from_double(V[(size_t)(j0 + jj) * R + c]) : FF{0.0f, 0.0f};
-    }
+    const FF* VF = a.VF + (size_t)pos * h * kR;
+    for (int e = threadIdx.x; e < JB * kR; e += blockDim.x) Vj[e] = VF[(size_t)j0 * kR + e];
     __syncthreads();
     // W2(j, c) = sum_b V(j, b) W1(i, b, c), rows j >= i
     for (int e = jlo * kR + threadIdx.x; e < JB * kR; e += blockDim.x) {
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kErrThreads) k_err_sliced(ErrSlicedArgs a) {
       if (jend <= jlo) continue;
       FF vl[kR];
 #pragma unroll
-      for (int c = 0; c < kR; ++c) vl[c] = (c < r) ? ff_from_double(V[(size_t)l * R + c]) : FF{0.0f, 0.0f};
+      for (int c = 0; c < kR; ++c) vl[c] = VF[(size_t)l * kR + c];
       // two rows j at a time (independent chains), accumulated in row order;
       // each entry weighted by the size of its orbit (i <= j <= l here)
       int jj = jlo;
@@ -331,7 +332,8 @@ bool err_sliced_supported(int h, int R) { return err_rows(h) > 0 && R >= 1 && R 
 
 size_t err_sliced_scratch_bytes(int h, int R, int cnt) {
   const int kr = err_kr(R);
-  return carve_bytes<double>((size_t)cnt * h * (h / 8)) + carve_bytes<FF>((size_t)cnt * h * kr * kr) + 1024;
+  return carve_bytes<double>((size_t)cnt * h * (h / 8)) + carve_bytes<FF>((size_t)cnt * h * kr * kr) +
+         carve_bytes<FF>((size_t)cnt * h * kr) + 1024;
 }
 
 constexpr size_t kErrSmemMax = 100 * 1024;  // staged slices: 6 JB h BF16 values
@@ -356,9 +358,11 @@ void err_sliced_batch(const SliceView& sv, const double* normF2, const double* V
   char* base = (char*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   const int jbs = err_rows(h);
   double* parts = (double*)base;
+  const int kr = err_kr(R);
   FF* w1 = (FF*)(base + carve_bytes<double>((size_t)cnt * h * (h / 8)));
+  FF* vf = (FF*)((char*)w1 + carve_bytes<FF>((size_t)cnt * h * kr * kr));
   ErrSlicedArgs a{(const __nv_bfloat16*)sv.S, sv.Kp, sv.rowexp, normF2, h, R, V, Bcore, amap, rk, rk_stride, jbs, w1,
-                  parts, esum};
+                  vf, parts, esum};
   switch (err_kr(R)) {
     case 8: err_launch<8>(a, cnt, s); break;
     case 12: err_launch<12>(a, cnt, s); break;
