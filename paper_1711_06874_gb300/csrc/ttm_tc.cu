@@ -47,7 +47,6 @@ constexpr int kMaxOperandBytesB = kSlices * kMaxNp * kKB * 2;      // 36 KB
 constexpr int kStageBytes = kOperandBytesA + kMaxOperandBytesB;    // 84 KB
 constexpr int kThreads = 576;
 constexpr int kEpiWarps = 16;
-constexpr int kMaxEpiCols = kMaxNp / 4;  // 24
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 static_assert(kAcc * kMaxNp <= 512, "accumulators fit in TMEM");
 
@@ -95,6 +94,9 @@ __global__ void k_bslice(const double* __restrict__ Up, int h3, int R, int Np, i
   if (threadIdx.x == 0) colexp[(size_t)j * Np + c] = e;
 }
 
+// kE: columns per epilogue warp, Np / 4 (8, 16 or 24), so that the
+// epilogue's registers are sized for the group's padding
+template <int kE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, TtmArgs args) {
   TK_PDL_ENTRY();
@@ -251,10 +253,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t base0 = tmem + ((uint32_t)(q * 32) << 16) + grp * cpg;
     bool ok = true;
     int gc = 0;
+    int jprev = -1;
+    int fx[kE];  // column exponents of this warp's columns, per instance
     for (int u = u0; u < u1 && ok; ++u) {
-      long long V[kMaxEpiCols];
+      // this tile's scales, read before the accumulators are waited for (the
+      // L2 round trips overlap the MMAs instead of following the drain)
+      const int j = u / args.ntiles;
+      const int grow = (u - j * args.ntiles) * kTM + row;
+      const int inst = args.amap[j];
+      const int e = (grow < args.M) ? args.rowexp[(size_t)inst * args.h1 + grow / args.h2] : -1000;
+      if (j != jprev) {
+        const int* fexp = args.colexp + (size_t)j * Np;
 #pragma unroll
-      for (int c = 0; c < kMaxEpiCols; ++c) V[c] = 0;
+        for (int c = 0; c < kE; ++c) {
+          const int col = grp * cpg + c;
+          fx[c] = (c < cpg && col < args.R) ? fexp[col] : -1000;
+        }
+        jprev = j;
+      }
+      long long V[kE];
+#pragma unroll
+      for (int c = 0; c < kE; ++c) V[c] = 0;
       for (int ch = 0; ch < nchunks; ++ch, ++gc) {
         const int ab = gc % nbuf;
         if (!tc::mbar_wait(&acc_full[ab], (gc / nbuf) & 1, args.err)) {
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after_sync();
         const uint32_t base = base0 + ab * acc_cols;
 #pragma unroll
-        for (int hh = 0; hh < kMaxEpiCols / 8; ++hh) {
+        for (int hh = 0; hh < kE / 8; ++hh) {
           if (hh * 8 < cpg) {
             uint32_t r[8];
             tc::tmem_ld8(base + hh * 8, r);
@@ -300,18 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&acc_empty[ab]);
       }
       if (!ok) break;
-      const int j = u / args.ntiles;
-      const int grow = (u - j * args.ntiles) * kTM + row;
       if (grow < args.M) {
-        const int inst = args.amap[j];
-        const int e = args.rowexp[(size_t)inst * args.h1 + grow / args.h2];
-        const int* fexp = args.colexp + (size_t)j * Np;
         double* out = args.T1 + ((size_t)j * args.M + grow) * args.R;
 #pragma unroll
-        for (int c = 0; c < kMaxEpiCols; ++c) {
+        for (int c = 0; c < kE; ++c) {
           const int col = grp * cpg + c;
           if (c < cpg && col < args.R) {
-            const int f = fexp[col];
+            const int f = fx[c];
             out[col] = (e > -1000 && f > -1000) ? tc::i64_scaled(V[c], e + f - 44) : 0.0;
           }
         }
@@ -322,6 +336,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+template <int kE>
+void ttm_attrs() {
+  TK_CUDA(cudaFuncSetAttribute(k_ttm_tc<kE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
 }
 
 CUtensorMap map4d(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* base, cuuint64_t d0, cuuint64_t d1,
@@ -367,9 +386,8 @@ void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int 
   // B: [j][s][c][l]
   const CUtensorMap mapB = map4d(enc, BS, h3, Np, kSlices, Bg, (cuuint64_t)h3 * 2, (cuuint64_t)Np * h3 * 2,
                                  (cuuint64_t)Np * h3 * 2 * kSlices, Np);
-  once_per_device((const void*)&k_ttm_tc, [] {
-    TK_CUDA(cudaFuncSetAttribute(k_ttm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-  });
+  const auto kern = Np == 32 ? k_ttm_tc<8> : Np == 64 ? k_ttm_tc<16> : k_ttm_tc<24>;
+  once_per_device((const void*)kern, Np == 32 ? ttm_attrs<8> : Np == 64 ? ttm_attrs<16> : ttm_attrs<24>);
   // about one run of consecutive (instance, tile) pairs per SM
   static const int sms = [] {
     int d = 0, v = 0;
@@ -385,7 +403,7 @@ void ttm_mode3_sliced(const SliceView& sv, const int h[3], const int* amap, int 
   const int tpc = (int)std::max<long long>(1, (total + sms - 1) / sms);
   const unsigned nctas = (unsigned)((total + tpc - 1) / tpc);
   TtmArgs a{(int)M, h1, h2, h3, R, Np, (h3 + kKB - 1) / kKB, ntiles, tpc, Bg, amap, sv.rowexp, colexp, T1, err};
-  launch_pdl("k_ttm_tc", k_ttm_tc, dim3(nctas), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
+  launch_pdl("k_ttm_tc", kern, dim3(nctas), dim3(kThreads), kSmemBytes, s, mapA, mapB, a);
 }
 
 }  // namespace tk
