@@ -313,6 +313,7 @@ __host__ __device__ constexpr int panel_ld(int n) {
 template <int kRPL>
 __global__ void __launch_bounds__(256) k_qr_factor64(double* Y, double* betas, int n, int m, long long sY, long long sB) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   extern __shared__ double qf_sm[];
   __shared__ double beta[kMaxM + 1];
   __shared__ double v0s[kMaxM + 1];
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(128) k_form_q(const double* __restrict__ Y, co
                                                  double* __restrict__ Q, int n, int m, long long sY, long long sB,
                                                  long long sQ) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   extern __shared__ double fq_sm[];
   __shared__ double bs[kMaxM + 1];
   Y += blockIdx.y * sY;
@@ -584,6 +586,7 @@ __global__ void __launch_bounds__(256) k_gomega32(const double* __restrict__ G, 
                                                   unsigned long long seed, float* __restrict__ Yg,
                                                   double* __restrict__ trace) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   extern __shared__ float so[];
   const int ms4 = (ms + 3) & ~3;
   float* Gr = so;               // rows i0 .. i0 + 7 of G
@@ -627,6 +630,7 @@ template <int kRPL>
 __global__ void __launch_bounds__(256) k_start32(const float* __restrict__ Yg, int n, int ms,
                                                  double* __restrict__ Q0) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   extern __shared__ float s32[];
   __shared__ float beta[kMaxM + 1];
   __shared__ float v0s[kMaxM + 1];
@@ -1186,6 +1190,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_strided(const double*
                                                          RankArgs rank, int mr, const double* trace,
                                                          double u_data) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   const long long b = blockIdx.x;
   jacobi_body(H + b * m * m, m, lam + b * m, V + b * m * m, nullptr, u_data);
   if (rank.out == nullptr) return;

@@ -182,6 +182,7 @@ __device__ __forceinline__ int rank_of(int r, const int* rdev) { return rdev ? m
 
 __global__ void k_unfold(const UnfoldDesc* __restrict__ descs) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   UnfoldDesc d = descs[blockIdx.y];
   d.r = rank_of(d.r, d.rdev);
   const int c = blockIdx.x;
@@ -241,6 +242,7 @@ struct CoreDesc {
 
 __global__ void k_extract_core(const CoreDesc* __restrict__ descs) {
   TK_PDL_ENTRY();
+  TK_PDL_EARLY_IF_SMALL();
   CoreDesc d = descs[blockIdx.y];
   d.r1 = rank_of(d.r1, d.rdev[0]);
   d.r2 = rank_of(d.r2, d.rdev[1]);

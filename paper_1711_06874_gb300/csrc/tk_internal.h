@@ -35,10 +35,20 @@ void count_launches(unsigned long long k);  // k kernels of a replayed graph
 // with programmatic stream serialisation and starts with TK_PDL_ENTRY(): it
 // waits there until the previous kernel on the stream has finished and its
 // writes are visible, so its launch may be processed while the previous grid
-// drains (a no-op for a kernel launched without the attribute).  No kernel
-// lets its dependents start early: CTAs of the next kernel parked on the wait
-// cost more than the overlap gained (measured on the n = 256 solve).
+// drains (a no-op for a kernel launched without the attribute).  Kernels of
+// many CTAs do not let their dependents start early: CTAs of the next kernel
+// parked on the wait cost more than the overlap gained (measured on the
+// n = 256 solve).  The eigensolver chain's kernels that run on a few SMs
+// (one CTA per instance and a single instance) do, with
+// TK_PDL_EARLY_IF_SMALL() after TK_PDL_ENTRY(): the next kernel's launch is
+// then processed while they run on otherwise idle SMs, and its CTAs still
+// wait for this grid to finish before they read anything.
 #define TK_PDL_ENTRY() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define TK_PDL_EARLY_IF_SMALL()                                  \
+  do {                                                           \
+    if (gridDim.x * gridDim.y * gridDim.z <= 32)                 \
+      asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+  } while (0)
 #define TK_LAUNCH(what) (::tk::count_launch(), ::tk::check_cuda(cudaGetLastError(), what))
 
 // Launches kernel k (which must begin with TK_PDL_ENTRY()) on stream s with
