@@ -139,6 +139,10 @@ TK_HD void tk_bessel_k_miller(const tk_nu_consts& c, double x, double* kmu, doub
   // a = 2 (k + x): rounded once at k = N, then lowered by 2 per step, which
   // is exact (a < 2^53), so the loop costs four FP64 instructions a step
   double a = 2.0 * ((double)N + x);
+  // unrolled so that the next steps' coefficient loads are issued ahead of
+  // the recurrence's dependent FMA (the operations and their order are as
+  // written)
+#pragma unroll 4
   for (int k = N; k >= 1; --k) {
     // u_{k-1} = 2 (k + x) u_k - ((k + 1/2)^2 - mu^2) u_{k+1}
     const double u_prev = fma(a, u, -c.Mk[k] * u_next);
